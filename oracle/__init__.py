@@ -1,0 +1,218 @@
+"""Python handle on the Jiffy oracle (plain single-threaded C, jiffy_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it to check and time the CUDA library.
+The library itself never imports this package. Nothing here is shared with
+the CUDA path: the C file is compiled on its own with gcc.
+
+The oracle follows the paper (Ford & Ford, arXiv 2209.08196) step by step:
+quantization (Sec. III-A/B), zero bitmask (Sec. III-C), trial I/P selection
+(Sec. III-E), mask XOR (Sec. III-D), compaction, residual, delta, ZigZag
+(Eq. 1) and PFOR-style packing (Sec. II).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "jiffy_oracle.c")
+_LIB = os.path.join(_HERE, "libjiffy_oracle.so")
+
+ERR_CAPACITY = 2
+ERR_CORRUPT = 3
+
+_DT = {1: np.uint8, 2: np.uint16, 4: np.uint32}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99, no target-specific flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        u32, i32, u64, i64, vp, sz = (ctypes.c_uint32, ctypes.c_int32, ctypes.c_uint64,
+                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t)
+        L.jo_quantize.restype = u32
+        L.jo_quantize.argtypes = [u32, u32, u32]
+        L.jo_zigzag.restype = u32
+        L.jo_zigzag.argtypes = [i32]
+        L.jo_unzigzag.restype = i32
+        L.jo_unzigzag.argtypes = [u32]
+        L.jo_block_body_bytes.restype = u32
+        L.jo_block_body_bytes.argtypes = [vp, u32, u32]
+        L.jo_best_b.restype = u32
+        L.jo_best_b.argtypes = [vp, u32]
+        L.jo_pack_block.restype = u32
+        L.jo_pack_block.argtypes = [vp, u32, u32, vp]
+        L.jo_create.restype = vp
+        L.jo_create.argtypes = [u32, u32, u32, vp, vp, u32, i32]
+        L.jo_destroy.restype = None
+        L.jo_destroy.argtypes = [vp]
+        L.jo_reset.restype = None
+        L.jo_reset.argtypes = [vp]
+        L.jo_encode.restype = i64
+        L.jo_encode.argtypes = [vp, vp, vp, sz, vp]
+        L.jo_decode.restype = i64
+        L.jo_decode.argtypes = [vp, vp, sz, vp]
+        L.jo_trial_cost.restype = u64
+        L.jo_trial_cost.argtypes = [u32, u32, u32, u32, u32, vp, vp, ctypes.c_int]
+        L.jo_section_split.restype = u64
+        L.jo_section_split.argtypes = [u32, u32, u32, u32, vp, vp, ctypes.c_int, vp, vp]
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def quantize(v: int, P: int, s: int) -> int:
+    return lib().jo_quantize(v, P, s)
+
+
+def zigzag(x: int) -> int:
+    return lib().jo_zigzag(x)
+
+
+def unzigzag(z: int) -> int:
+    return lib().jo_unzigzag(z)
+
+
+def block_body_bytes(z, b: int) -> int:
+    z = np.ascontiguousarray(z, dtype=np.uint32)
+    return lib().jo_block_body_bytes(_ptr(z), len(z), b)
+
+
+def best_b(z) -> int:
+    z = np.ascontiguousarray(z, dtype=np.uint32)
+    return lib().jo_best_b(_ptr(z), len(z))
+
+
+def pack_block(z, b: int) -> bytes:
+    z = np.ascontiguousarray(z, dtype=np.uint32)
+    out = np.zeros(4 + 4 * 128 + 4 * 32 + 4 * 128 + 64, dtype=np.uint8)
+    n = lib().jo_pack_block(_ptr(z), len(z), b, _ptr(out))
+    return out[:n].tobytes()
+
+
+def trial_cost(cur: np.ndarray, prev: np.ndarray, P: int, mode: int, test_lines: int = 4) -> int:
+    H, W = cur.shape
+    cur = np.ascontiguousarray(cur)
+    prev = np.ascontiguousarray(prev, dtype=cur.dtype)
+    return lib().jo_trial_cost(H, W, cur.itemsize, P, test_lines, _ptr(cur), _ptr(prev), mode)
+
+
+def section_split(cur: np.ndarray, prev: np.ndarray, P: int, mode: int):
+    """(section bytes, mask-part bytes, block bytes) of one attribute-scan coded in a forced mode."""
+    H, W = cur.shape
+    cur = np.ascontiguousarray(cur)
+    prev = np.ascontiguousarray(prev, dtype=cur.dtype)
+    m = ctypes.c_uint64(0)
+    d = ctypes.c_uint64(0)
+    sec = lib().jo_section_split(H, W, cur.itemsize, P, _ptr(cur), _ptr(prev), mode,
+                                 ctypes.addressof(m), ctypes.addressof(d))
+    return sec, m.value, d.value
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int):
+        super().__init__("oracle error %d" % code)
+        self.code = code
+
+
+class Codec:
+    """One stateful oracle stream (encoder or decoder role; the state is the
+    previous scan's quantized values, Sec. III-D)."""
+
+    def __init__(self, H: int, W: int, attrs, test_lines: int = 4, force_mode: int = -1):
+        self.H, self.W = H, W
+        self.attrs = [(int(s), int(p)) for s, p in attrs]
+        self.A = len(self.attrs)
+        dt = np.array([s for s, _ in self.attrs], dtype=np.uint8)
+        pr = np.array([p for _, p in self.attrs], dtype=np.uint32)
+        self._h = lib().jo_create(H, W, self.A, _ptr(dt), _ptr(pr), test_lines, force_mode)
+        if not self._h:
+            raise ValueError("invalid oracle configuration")
+
+    def close(self):
+        if self._h:
+            lib().jo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def reset(self):
+        lib().jo_reset(self._h)
+
+    def bound(self) -> int:
+        nw = (self.W + 31) // 32
+        row = 4 * ((nw + 15) // 16) + 4 * nw + 4 * ((self.W + 127) // 128) + 4 * self.W
+        return 16 + 8 * self.A + 8 + 12 * self.A + self.A * (8 * self.H + self.H * row)
+
+    def encode(self, planes, return_modes: bool = False):
+        arrs = []
+        for (s, _), p in zip(self.attrs, planes):
+            a = np.ascontiguousarray(p, dtype=_DT[s])
+            assert a.shape == (self.H, self.W)
+            arrs.append(a)
+        ptrs = (ctypes.c_void_p * self.A)(*[_ptr(a) for a in arrs])
+        out = np.zeros(self.bound(), dtype=np.uint8)
+        modes = np.zeros(self.A, dtype=np.uint8)
+        n = lib().jo_encode(self._h, ptrs, _ptr(out), out.nbytes, _ptr(modes))
+        if n < 0:
+            raise OracleError(-n)
+        b = out[:n].tobytes()
+        return (b, [int(m) for m in modes]) if return_modes else b
+
+    def decode(self, buf: bytes):
+        """Decodes one frame (plus the stream header before the first one);
+        returns (planes, bytes consumed)."""
+        src = np.frombuffer(buf, dtype=np.uint8)
+        if src.size == 0:
+            src = np.zeros(1, dtype=np.uint8)
+        outs = [np.zeros((self.H, self.W), dtype=_DT[s]) for s, _ in self.attrs]
+        ptrs = (ctypes.c_void_p * self.A)(*[_ptr(o) for o in outs])
+        n = lib().jo_decode(self._h, _ptr(src), len(buf), ptrs)
+        if n < 0:
+            raise OracleError(-n)
+        return outs, int(n)
+
+
+def encode_sequence(H, W, attrs, scans, test_lines=4, force_mode=-1):
+    """Encodes scans (a list of per-scan plane lists) as one stream; returns
+    (bytes of the whole stream, per-frame byte lengths, per-frame modes)."""
+    c = Codec(H, W, attrs, test_lines, force_mode)
+    parts, lens, modes = [], [], []
+    for planes in scans:
+        b, m = c.encode(planes, return_modes=True)
+        parts.append(b)
+        lens.append(len(b))
+        modes.append(m)
+    c.close()
+    return b"".join(parts), lens, modes
+
+
+def decode_sequence(H, W, attrs, buf: bytes, n_scans: int):
+    c = Codec(H, W, attrs)
+    out, pos = [], 0
+    for _ in range(n_scans):
+        planes, n = c.decode(buf[pos:])
+        out.append(planes)
+        pos += n
+    c.close()
+    return out, pos
