@@ -1,0 +1,164 @@
+/*
+ * jiffy.h -- C ABI of the GB300 Jiffy LiDAR scan codec.
+ *
+ * Jiffy (Ford & Ford, "Lossless SIMD Compression of LiDAR Range and Attribute
+ * Scan Sequences", arXiv 2209.08196) compresses sequences of LiDAR scans held
+ * as H x W images of unsigned integers (rows = beams, columns = azimuth), one
+ * image ("plane") per attribute: range, second-return range, signal,
+ * reflectivity, ambient, ... (Sec. III-A, Sec. IV-B). Per attribute and scan
+ * it quantizes to a precision (Sec. III-B), extracts and codes the zero
+ * bitmask (Sec. III-C), removes the zero samples, forms intra-scan (I) or
+ * predicted-scan (P) residuals (Sec. III-C, III-D) chosen by trial
+ * compression (Sec. III-E), delta and ZigZag (Eq. 1) codes them and packs
+ * them in frames of 128 integers with exceptions (PFOR, Sec. II).
+ *
+ * Every stage runs in this library's CUDA kernels on one GPU. All functions
+ * take plain pointers and sizes. "device" pointers are CUDA device memory of
+ * the stream's device; "host" pointers are ordinary CPU memory. A `cuda_stream`
+ * argument is a cudaStream_t passed as void* (NULL = the legacy default
+ * stream); work is enqueued on it in stream order.
+ *
+ * Byte layout (the paper leaves it open; this library's format, version 1,
+ * little-endian, every section 4-byte aligned):
+ *   stream header (before the first frame after create/reset), 16 + 8A bytes:
+ *     "JFY1", u16 version = 1, u16 A, u32 H, u32 W,
+ *     per attribute { u8 dtype_bytes, u8 zigzag variant = 1 (Eq. 1), u16 0,
+ *                     u32 precision }   (Sec. III-A: precision is stored)
+ *   frame, one per scan: header 8 + 12A bytes
+ *     u32 frame_bytes, u32 scan_index (frames since create/reset),
+ *     per attribute { u8 mode (0 = I, 1 = P), 3 x u8 0, u32 section_bytes,
+ *                     u32 nnz }
+ *   then per attribute a section: a row table of H x { u32 end, u32 carry }
+ *     (end = byte end of the row's chunk counted from the first chunk; carry
+ *     = the residual preceding the row's first residual in the scan's flat
+ *     nonzero vector, 0 if none) and H row chunks:
+ *     mask class words (2 bits per 32-sample mask word: 0 = all clear,
+ *     1 = all valid bits set, 2 = literal follows), literal mask words,
+ *     block headers {u8 b, u8 exceptions, u8 high bits, u8 0}, block bodies
+ *     (low bits, exception positions, exception high bits).
+ *
+ * Errors: every function returns a jiffy_status; nothing aborts. A failed
+ * call leaves the stream's state (previous scan, frame counter) unchanged.
+ * Thread safety: a jiffy_stream may be used by one host thread at a time;
+ * different streams are independent.
+ */
+#ifndef JIFFY_H
+#define JIFFY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  JIFFY_OK = 0,
+  JIFFY_ERR_INVALID_ARG = 1, /* bad pointer, size, shape, dtype or option */
+  JIFFY_ERR_CAPACITY = 2,    /* output buffer too small; required size reported */
+  JIFFY_ERR_CORRUPT = 3,     /* malformed or mismatching input stream */
+  JIFFY_ERR_STATE = 4,       /* call not valid in the stream's current state */
+  JIFFY_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  JIFFY_ERR_CUDA = 6,        /* a CUDA runtime call failed */
+  JIFFY_ERR_NOMEM = 7        /* device or host allocation failed */
+} jiffy_status;
+
+typedef enum { JIFFY_ENCODER = 0, JIFFY_DECODER = 1 } jiffy_role;
+
+/* One attribute plane: sample size (1, 2 or 4 bytes, unsigned) and the
+ * quantization precision P >= 1 (Sec. III-B). The encoder codes
+ * q = min(floor((v + floor(P/2)) / P), floor(max/P)) and the decoder returns
+ * q * P; |v - q*P| <= P/2 wherever the clamp does not act (Sec. IV-G). */
+typedef struct {
+  uint32_t dtype_bytes;
+  uint32_t precision;
+} jiffy_attr_desc;
+
+/* test_lines: number of scanlines of the trial compression (Sec. III-E;
+ * Sec. IV-E uses 4); rows floor((2k+1)H/(2L)), k < L. force_mode: -1 picks I
+ * or P per attribute and scan by trial, 0 forces I, 1 forces P (the first
+ * frame after create/reset is always I). */
+typedef struct {
+  uint32_t test_lines;
+  int32_t force_mode;
+} jiffy_options;
+
+typedef struct jiffy_stream jiffy_stream;
+
+/* Creates a codec stream on CUDA device `device`: the encoder or decoder of
+ * one sensor's scan sequence with H x W planes and n_attr attributes.
+ * 1 <= H <= 4096, 1 <= W <= 16384, 1 <= n_attr <= 64. opt may be NULL
+ * (test_lines = 4, force_mode = -1). The stream owns its device state (the
+ * previous scan of every attribute, Sec. III-D) and scratch; *out receives
+ * the handle. Errors: INVALID_ARG, NOMEM, CUDA. */
+jiffy_status jiffy_stream_create(jiffy_stream** out, jiffy_role role, uint32_t H, uint32_t W,
+                                 uint32_t n_attr, const jiffy_attr_desc* attrs,
+                                 const jiffy_options* opt, int device);
+
+/* Releases the stream and its device memory (synchronizes its device). */
+void jiffy_stream_destroy(jiffy_stream* s);
+
+/* Forgets the previous scan: the next frame is an I frame preceded by a new
+ * stream header (a resume point). */
+jiffy_status jiffy_stream_reset(jiffy_stream* s);
+
+/* Upper bound of the bytes n_scans frames (plus a stream header) can take. */
+size_t jiffy_max_encoded_size(uint32_t H, uint32_t W, uint32_t n_attr, const jiffy_attr_desc* attrs,
+                              uint32_t n_scans);
+
+/* Encodes one scan. planes: host array of n_attr device pointers, each an
+ * H x W row-major dense plane of dtype_bytes samples (borrowed for the call).
+ * out: device buffer of out_capacity bytes, 16-byte aligned. On JIFFY_OK,
+ * *out_len (host) = bytes written (the stream header is included before the
+ * first frame). On JIFFY_ERR_CAPACITY, *out_len = bytes required and nothing
+ * valid is written. Synchronizes cuda_stream before returning. */
+jiffy_status jiffy_encode(jiffy_stream* s, const void* const* planes, void* out, size_t out_capacity,
+                          size_t* out_len, void* cuda_stream);
+
+/* Encodes n_scans consecutive scans of the stream in one pass (the P
+ * prediction of scan t uses scan t-1's input, Sec. III-D, so all scans are
+ * coded in parallel). planes: host array of n_scans * n_attr device pointers,
+ * scan-major (planes[t * n_attr + a]). frame_offsets (host, nullable, n_scans
+ * + 1 entries) receives the byte offset of each frame in out and the total
+ * length last. Otherwise as jiffy_encode. */
+jiffy_status jiffy_encode_seq(jiffy_stream* s, uint32_t n_scans, const void* const* planes, void* out,
+                              size_t out_capacity, uint64_t* frame_offsets, size_t* out_len,
+                              void* cuda_stream);
+
+/* Decodes one frame (preceded by the stream header for the first frame after
+ * create/reset) of in_len bytes at device pointer in (4-byte aligned) into
+ * planes_out (host array of n_attr device pointers, H x W dense). Errors:
+ * CORRUPT (malformed frame, shape/dtype/precision mismatch with the stream
+ * header, wrong scan index), TIMEOUT, CUDA. Synchronizes cuda_stream. */
+jiffy_status jiffy_decode(jiffy_stream* s, const void* in, size_t in_len, void* const* planes_out,
+                          void* cuda_stream);
+
+/* Decodes n_scans consecutive frames. frame_offsets (host, n_scans + 1
+ * entries) gives each frame's byte offset in `in` and the end of the last
+ * one, as returned by jiffy_encode_seq. planes_out: n_scans * n_attr device
+ * pointers, scan-major. Scans are decoded in parallel; a P frame's rows wait
+ * on the same rows of the previous frame. Synchronizes cuda_stream. */
+jiffy_status jiffy_decode_seq(jiffy_stream* s, uint32_t n_scans, const void* in, size_t in_len,
+                              const uint64_t* frame_offsets, void* const* planes_out, void* cuda_stream);
+
+/* Per-kernel device timing (CUDA events recorded around each kernel launch
+ * on the call's cuda_stream). enable != 0 turns it on for later calls. */
+jiffy_status jiffy_stream_set_profiling(jiffy_stream* s, int enable);
+
+/* Device milliseconds of each kernel launched by the stream's last
+ * successful call, in launch order (encode: trial, encode, finalize;
+ * decode: decode). Writes min(n, count) values to ms (host) and returns the
+ * count (0 if profiling is off or no call completed). */
+uint32_t jiffy_stream_kernel_times(const jiffy_stream* s, float* ms, uint32_t n);
+
+/* Frames coded since create/reset (the next frame's scan_index). */
+uint32_t jiffy_stream_frame_index(const jiffy_stream* s);
+
+/* Human-readable name of a status code (static string). */
+const char* jiffy_status_string(jiffy_status st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JIFFY_H */

@@ -1,0 +1,242 @@
+// Device-side building blocks of the Jiffy codec kernels (sm_103a).
+//
+// Jiffy: Ford & Ford, arXiv 2209.08196. Quantization (Sec. III-B), ZigZag
+// (Eq. 1), PFOR-style block sizing (Sec. II) and the prefix/look-back
+// machinery the encoder and decoder kernels share.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "jiffy_types.h"
+
+namespace jiffy {
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t warp_id() { return threadIdx.x >> 5; }
+
+__device__ __forceinline__ uint32_t load_sample(const uint8_t* row, uint32_t s, uint32_t x) {
+  if (s == 4) return reinterpret_cast<const uint32_t*>(row)[x];
+  if (s == 2) return reinterpret_cast<const uint16_t*>(row)[x];
+  return row[x];
+}
+
+// Loads that bypass L1: used for data another CTA wrote during this kernel.
+__device__ __forceinline__ uint32_t load_sample_cg(const uint8_t* row, uint32_t s, uint32_t x) {
+  if (s == 4) return __ldcg(reinterpret_cast<const unsigned int*>(row) + x);
+  if (s == 2) return __ldcg(reinterpret_cast<const unsigned short*>(row) + x);
+  return __ldcg(reinterpret_cast<const unsigned char*>(row) + x);
+}
+
+__device__ __forceinline__ void store_sample(uint8_t* row, uint32_t s, uint32_t x, uint32_t v) {
+  if (s == 4) reinterpret_cast<uint32_t*>(row)[x] = v;
+  else if (s == 2) reinterpret_cast<uint16_t*>(row)[x] = (uint16_t)v;
+  else row[x] = (uint8_t)v;
+}
+
+// Quantization, Sec. III-B: q = min(floor((v + floor(P/2)) / P), floor(max/P)).
+// The division uses the round-up reciprocal m = ceil(2^64/P) (Granlund and
+// Montgomery, "Division by invariant integers using multiplication", 1994):
+// for a dividend n < 2^33 the product n*m/2^64 exceeds n/P by less than
+// 2^-31 <= 1/P, which never crosses the next integer, so the high word of
+// n*m is exactly floor(n/P) for P <= 2^31. Larger P leave q in {0, 1, 2}.
+__device__ __forceinline__ uint32_t quantize(uint32_t v, const AttrDev& a) {
+  if (a.P == 1) return v;
+  unsigned long long n = (unsigned long long)v + (a.P >> 1);
+  uint32_t q;
+  if (a.P <= 0x80000000u) q = (uint32_t)__umul64hi(n, a.magic);
+  else q = (uint32_t)(n >= a.P) + (uint32_t)(n >= 2ull * a.P);
+  return q < a.qmax ? q : a.qmax;
+}
+
+// ZigZag, Eq. 1: 2|x| + [x < 0] with x the residual read as a signed 32-bit
+// value; everything modulo 2^32 (so ZigZag(-2^31) = 1).
+__device__ __forceinline__ uint32_t zigzag(uint32_t d) {
+  bool neg = (int32_t)d < 0;
+  uint32_t mag = neg ? 0u - d : d;
+  return (mag << 1) + (neg ? 1u : 0u);
+}
+
+// Inverse of Eq. 1: even z -> z/2; odd z -> -(z >> 1), except z = 1, whose
+// magnitude 2^31 wrapped to 0 in the forward map.
+__device__ __forceinline__ uint32_t unzigzag(uint32_t z) {
+  uint32_t m = z >> 1;
+  if (z & 1u) return 0u - (m ? m : 0x80000000u);
+  return m;
+}
+
+__device__ __forceinline__ uint32_t bit_width(uint32_t x) { return 32u - __clz(x); }
+
+// Body bytes of a block of n values coded with width b, e exceptions and
+// widest value wmax bits (Sec. II, PFOR: low bits for all, exceptions apart).
+__device__ __forceinline__ uint32_t block_body_bytes(uint32_t n, uint32_t b, uint32_t e, uint32_t wmax) {
+  uint32_t bytes = 4u * ((n * b + 31u) >> 5);
+  if (e) bytes += 4u * ((e + 3u) >> 2) + 4u * ((e * (wmax - b) + 31u) >> 5);
+  return bytes;
+}
+
+struct BlockChoice {
+  uint32_t b, e, hb, bytes;
+};
+
+// Warp-wide choice of the block width. Lane l holds values l, l+32, l+64,
+// l+96 of a block of n <= 128 values (zero past n). Picks the b in [0, wmax]
+// with the fewest body bytes, the smallest b on ties.
+__device__ __forceinline__ BlockChoice choose_block(const uint32_t (&z)[4], uint32_t n) {
+  const uint32_t lane = lane_id();
+  uint32_t w[4];
+  uint32_t wm = 0;
+#pragma unroll
+  for (int m = 0; m < 4; m++) {
+    w[m] = (lane + 32u * m < n) ? bit_width(z[m]) : 0u;
+    wm = max(wm, w[m]);
+  }
+  const uint32_t wmax = __reduce_max_sync(0xffffffffu, wm);
+  BlockChoice best{0, 0, 0, 0xffffffffu};
+  for (uint32_t b = 0; b <= wmax; b++) {
+    uint32_t e = 0;
+#pragma unroll
+    for (int m = 0; m < 4; m++) e += __popc(__ballot_sync(0xffffffffu, w[m] > b));
+    uint32_t bytes = block_body_bytes(n, b, e, wmax);
+    if (bytes < best.bytes) best = BlockChoice{b, e, e ? wmax - b : 0u, bytes};
+    if (e == 0) break;  // larger b only grows the low part
+  }
+  return best;
+}
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const uint32_t lane = lane_id();
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= (uint32_t)o) v += t;
+  }
+  return v;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v) { return __reduce_add_sync(0xffffffffu, v); }
+
+// In-place exclusive prefix sum of a[0..n) in shared memory; returns the
+// total. Every thread of the CTA calls it. tmp: kWarps + 1 words.
+__device__ inline uint32_t block_excl_scan(uint32_t* a, uint32_t n, uint32_t* tmp) {
+  const uint32_t per = (n + kThreads - 1) / kThreads;
+  const uint32_t beg = min(threadIdx.x * per, n), end = min(beg + per, n);
+  uint32_t sum = 0;
+  for (uint32_t i = beg; i < end; i++) sum += a[i];
+  uint32_t incl = warp_incl_scan(sum);
+  if (lane_id() == 31) tmp[warp_id()] = incl;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t w = threadIdx.x < (uint32_t)kWarps ? tmp[threadIdx.x] : 0u;
+    uint32_t wi = warp_incl_scan(w);
+    if (threadIdx.x < (uint32_t)kWarps) tmp[threadIdx.x] = wi - w;
+    if (threadIdx.x == kWarps - 1) tmp[kWarps] = wi;
+  }
+  __syncthreads();
+  uint32_t run = tmp[warp_id()] + incl - sum;
+  for (uint32_t i = beg; i < end; i++) {
+    uint32_t v = a[i];
+    a[i] = run;
+    run += v;
+  }
+  uint32_t total = tmp[kWarps];
+  __syncthreads();
+  return total;
+}
+
+// ---- decoupled look-back (Merrill & Garland, "Single-pass Parallel Prefix
+// Scan with Decoupled Look-back", 2016) over 64-bit status words:
+// bits 62..63 = flag (0 empty, 1 aggregate, 2 inclusive prefix, 3 error),
+// bits 0..61 = value.
+constexpr unsigned long long kStAgg = 1ull << 62;
+constexpr unsigned long long kStInc = 2ull << 62;
+constexpr unsigned long long kStErr = 3ull << 62;
+constexpr unsigned long long kStValMask = (1ull << 62) - 1;
+
+__device__ __forceinline__ unsigned long long st_load(const unsigned long long* p) {
+  return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+__device__ __forceinline__ void st_publish(unsigned long long* p, unsigned long long v) {
+  __threadfence();
+  atomicExch(p, v);
+}
+
+// Spins (bounded) until status word idx is non-empty.
+__device__ __forceinline__ unsigned long long st_wait(const unsigned long long* st, uint32_t idx, bool& timeout) {
+  unsigned long long s = st_load(st + idx);
+  if (s >> 62) return s;
+  unsigned long long t0 = global_timer_ns();
+  uint32_t ns = 32;
+  while (!((s = st_load(st + idx)) >> 62)) {
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+    if (global_timer_ns() - t0 > kSpinLimitNs) {
+      timeout = true;
+      return kStErr;
+    }
+  }
+  return s;
+}
+
+// Warp 0 only. Exclusive prefix of item k over items [seg_start, k), summing
+// aggregates until an inclusive prefix is found. Returns false on an error
+// or timeout upstream.
+__device__ inline bool lookback_sum(const unsigned long long* st, uint32_t k, uint32_t seg_start,
+                                    unsigned long long& excl) {
+  const uint32_t lane = lane_id();
+  unsigned long long acc = 0;
+  int64_t j = (int64_t)k - 1;
+  while (j >= (int64_t)seg_start) {
+    int64_t idx = j - (int64_t)lane;
+    bool timeout = false;
+    unsigned long long s = idx >= (int64_t)seg_start ? st_wait(st, (uint32_t)idx, timeout) : kStInc;
+    bool bad = (s >> 62) == 3ull;
+    if (__any_sync(0xffffffffu, bad)) return false;
+    uint32_t inc = __ballot_sync(0xffffffffu, (s >> 62) == 2ull);
+    unsigned long long v = s & kStValMask;
+    if (inc) {
+      uint32_t first = __ffs(inc) - 1;
+      if (lane > first) v = 0;
+    }
+    // 64-bit warp sum
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    acc += v;
+    if (inc) break;
+    j -= 32;
+  }
+  excl = acc;
+  return true;
+}
+
+// Warp 0 only. "Last valid" look-back used for the delta carry: value bit 32
+// = has-a-residual, bits 0..31 = the last residual. Walks back to the nearest
+// predecessor that has a residual or holds an inclusive value; the segment
+// start counts as a residual of 0 (e[-1] = 0).
+__device__ inline bool lookback_last(const unsigned long long* st, uint32_t k, uint32_t seg_start,
+                                     uint32_t& carry) {
+  const uint32_t lane = lane_id();
+  int64_t j = (int64_t)k - 1;
+  while (true) {
+    int64_t idx = j - (int64_t)lane;
+    bool timeout = false;
+    unsigned long long s = idx >= (int64_t)seg_start ? st_wait(st, (uint32_t)idx, timeout)
+                                                     : (kStInc | (1ull << 32));
+    bool bad = (s >> 62) == 3ull;
+    if (__any_sync(0xffffffffu, bad)) return false;
+    uint32_t stop = __ballot_sync(0xffffffffu, ((s >> 62) == 2ull) || ((s >> 32) & 1ull));
+    if (stop) {
+      uint32_t first = __ffs(stop) - 1;
+      carry = __shfl_sync(0xffffffffu, (uint32_t)s, first);
+      return true;
+    }
+    j -= 32;
+  }
+}
+
+}  // namespace jiffy

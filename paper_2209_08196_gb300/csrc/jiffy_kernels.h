@@ -1,0 +1,66 @@
+// Launch parameters of the Jiffy kernels, shared by the kernels and the
+// host-side API in this directory.
+#pragma once
+
+#include <cstdint>
+
+#include "jiffy_types.h"
+
+namespace jiffy {
+
+struct EncParams {
+  uint32_t H, W, A, T;
+  uint32_t nw, ncls;             // mask words per row, class words per row
+  uint32_t frame0;               // scan index of the call's first frame
+  uint32_t shdr;                 // stream header bytes at the start of out (0 or 16 + 8A)
+  uint32_t fhdr;                 // frame header bytes (8 + 12A)
+  uint32_t test_lines;
+  int32_t force_mode;
+  uint32_t n_items;              // T * A * H row items
+  const AttrDev* attrs;          // [A]
+  const uint8_t* const* cur;     // [T*A] current planes
+  const uint8_t* const* prev;    // [T*A] previous planes: t = 0 -> stored q (or null), else raw t-1
+  uint8_t* const* state_next;    // [A] receives q of the last scan
+  uint8_t* out;
+  unsigned long long cap;
+  uint32_t* modes;               // [T*A]
+  uint32_t* row_bytes;           // [n_items]
+  uint32_t* row_nnz;             // [n_items]
+  uint32_t* row_carry;           // [n_items]
+  unsigned long long* st_carry;  // [n_items] look-back status (delta carry)
+  unsigned long long* st_bytes;  // [n_items] look-back status (byte offsets)
+  uint32_t* ticket;
+  uint32_t* err;
+  unsigned long long* frame_off; // [T+1]
+};
+
+struct DecParams {
+  uint32_t H, W, A, T;
+  uint32_t nw, ncls;
+  uint32_t frame0;
+  uint32_t fhdr;
+  uint32_t check_shdr;           // validate the stream header at in[0]
+  uint32_t n_items;
+  const AttrDev* attrs;
+  const uint8_t* in;
+  unsigned long long in_len;
+  const unsigned long long* off; // [T+1] frame offsets in `in`
+  uint8_t* const* outp;          // [T*A] output planes
+  const uint8_t* const* state;   // [A] previous decoded planes (for the call's first frame)
+  uint8_t* const* state_next;    // [A] receives the last frame's planes
+  uint32_t* done;                // [n_items] row-done flags
+  uint32_t* ticket;
+  uint32_t* err;
+};
+
+size_t enc_smem_bytes_host(uint32_t W);
+size_t trial_smem_bytes_host(uint32_t W);
+size_t dec_smem_bytes_host(uint32_t W);
+
+// Launchers (return a cudaError_t as int). ev: null, or events (cudaEvent_t
+// as void*) recorded before each kernel and after the last one (encode: 4,
+// decode: 2).
+int launch_encode(const EncParams& p, void* stream, void* const* ev);
+int launch_decode(const DecParams& p, void* stream, void* const* ev);
+
+}  // namespace jiffy

@@ -1,0 +1,49 @@
+// Constants and plain types shared by the Jiffy kernels and the host API.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#if defined(__CUDACC__)
+#define JIFFY_HD __host__ __device__
+#else
+#define JIFFY_HD
+#endif
+
+namespace jiffy {
+
+constexpr int kThreads = 256;          // threads per CTA of every row kernel
+constexpr int kWarps = kThreads / 32;
+constexpr uint32_t kMaxW = 16384;      // columns
+constexpr uint32_t kMaxH = 4096;       // rows
+constexpr uint32_t kMaxAttr = 64;
+constexpr uint32_t kMaxTestLines = 64;
+constexpr uint32_t kBlockN = 128;      // values per packing block (Sec. II frames of 128)
+constexpr uint32_t kSegWords = 8;      // mask words per warp per pass over a row
+
+// bits of the device error word
+enum : uint32_t { kErrCorrupt = 1u, kErrCapacity = 2u, kErrTimeout = 4u };
+
+// Wall-clock bound of every spin-wait (ns); a wait that runs out sets
+// kErrTimeout and the kernel returns instead of hanging.
+constexpr unsigned long long kSpinLimitNs = 2000000000ull;
+
+struct AttrDev {
+  uint32_t s;                 // bytes per sample: 1, 2 or 4
+  uint32_t P;                 // precision
+  uint32_t qmax;              // floor(max_sample / P)
+  uint32_t pad;
+  unsigned long long magic;   // ceil(2^64 / P), for 2 <= P <= 2^31
+};
+
+JIFFY_HD inline uint32_t ceil_div_u32(uint32_t a, uint32_t b) { return (a + b - 1) / b; }
+
+// Worst-case bytes of one row chunk: class words, literals, block headers and
+// bodies (with b = wmax a block of m values never exceeds 4m bytes and the
+// chosen b never needs more).
+JIFFY_HD inline uint32_t row_bound_bytes(uint32_t W) {
+  uint32_t nw = ceil_div_u32(W, 32);
+  return 4u * ceil_div_u32(nw, 16) + 4u * nw + 4u * ceil_div_u32(W, kBlockN) + 4u * W;
+}
+
+}  // namespace jiffy

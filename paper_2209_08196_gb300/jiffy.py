@@ -1,0 +1,242 @@
+"""Python binding of the Jiffy C ABI (include/jiffy.h), argument marshalling
+only: every step of encode and decode runs in the CUDA kernels of
+libjiffy_gb300.so. PyTorch supplies device memory and streams.
+
+The functions keep the C names. Planes are CUDA tensors of H x W samples
+with 1, 2 or 4 bytes per element (uint8, int16/uint16, int32/uint32: only
+the bytes matter); byte buffers are uint8 CUDA tensors. There is no CPU
+fallback: without the built library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libjiffy_gb300.so")
+
+JIFFY_ENCODER, JIFFY_DECODER = 0, 1
+STATUS = {
+    0: "JIFFY_OK", 1: "JIFFY_ERR_INVALID_ARG", 2: "JIFFY_ERR_CAPACITY", 3: "JIFFY_ERR_CORRUPT",
+    4: "JIFFY_ERR_STATE", 5: "JIFFY_ERR_TIMEOUT", 6: "JIFFY_ERR_CUDA", 7: "JIFFY_ERR_NOMEM",
+}
+
+
+class JiffyError(RuntimeError):
+    def __init__(self, status: int, what: str = "", required: int | None = None):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        self.required = required
+        super().__init__("%s%s: %s" % (what + ": " if what else "", self.name, _lib().jiffy_status_string(status).decode()))
+
+
+class _AttrDesc(ctypes.Structure):
+    _fields_ = [("dtype_bytes", ctypes.c_uint32), ("precision", ctypes.c_uint32)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("test_lines", ctypes.c_uint32), ("force_mode", ctypes.c_int32)]
+
+
+_L = None
+
+
+def _lib() -> ctypes.CDLL:
+    global _L
+    if _L is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libjiffy_gb300.so is not built (run paper_2209_08196_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u32, i32, sz, u64p = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32, ctypes.c_size_t, ctypes.POINTER(ctypes.c_uint64)
+        L.jiffy_status_string.restype = ctypes.c_char_p
+        L.jiffy_status_string.argtypes = [ctypes.c_int]
+        L.jiffy_stream_create.restype = ctypes.c_int
+        L.jiffy_stream_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, u32, u32, u32, ctypes.POINTER(_AttrDesc),
+                                          ctypes.POINTER(_Options), ctypes.c_int]
+        L.jiffy_stream_destroy.restype = None
+        L.jiffy_stream_destroy.argtypes = [vp]
+        L.jiffy_stream_reset.restype = ctypes.c_int
+        L.jiffy_stream_reset.argtypes = [vp]
+        L.jiffy_stream_frame_index.restype = u32
+        L.jiffy_stream_frame_index.argtypes = [vp]
+        L.jiffy_stream_set_profiling.restype = ctypes.c_int
+        L.jiffy_stream_set_profiling.argtypes = [vp, ctypes.c_int]
+        L.jiffy_stream_kernel_times.restype = u32
+        L.jiffy_stream_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), u32]
+        L.jiffy_max_encoded_size.restype = sz
+        L.jiffy_max_encoded_size.argtypes = [u32, u32, u32, ctypes.POINTER(_AttrDesc), u32]
+        L.jiffy_encode.restype = ctypes.c_int
+        L.jiffy_encode.argtypes = [vp, ctypes.POINTER(vp), vp, sz, ctypes.POINTER(sz), vp]
+        L.jiffy_encode_seq.restype = ctypes.c_int
+        L.jiffy_encode_seq.argtypes = [vp, u32, ctypes.POINTER(vp), vp, sz, u64p, ctypes.POINTER(sz), vp]
+        L.jiffy_decode.restype = ctypes.c_int
+        L.jiffy_decode.argtypes = [vp, vp, sz, ctypes.POINTER(vp), vp]
+        L.jiffy_decode_seq.restype = ctypes.c_int
+        L.jiffy_decode_seq.argtypes = [vp, u32, vp, sz, u64p, ctypes.POINTER(vp), vp]
+        _L = L
+    return _L
+
+
+def loaded_library_path() -> str:
+    _lib()
+    return LIB_PATH
+
+
+def _attrs(attrs):
+    arr = (_AttrDesc * len(attrs))()
+    for i, (s, p) in enumerate(attrs):
+        arr[i].dtype_bytes = int(s)
+        arr[i].precision = int(p)
+    return arr
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _check_plane(t: torch.Tensor, H: int, W: int, s: int, what: str):
+    if not t.is_cuda or t.element_size() != s or not t.is_contiguous() or t.numel() != H * W:
+        raise ValueError("%s: expected a contiguous CUDA tensor of %d x %d %d-byte samples, got %s %s %s"
+                         % (what, H, W, s, tuple(t.shape), t.dtype, t.device))
+
+
+class Handle:
+    """An opaque jiffy_stream* with the configuration it was created with."""
+
+    def __init__(self, ptr, role, H, W, attrs, device):
+        self.ptr, self.role, self.H, self.W, self.attrs, self.device = ptr, role, H, W, list(attrs), device
+
+    @property
+    def A(self):
+        return len(self.attrs)
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _L is not None:
+            _L.jiffy_stream_destroy(self.ptr)
+            self.ptr = None
+
+
+def jiffy_stream_create(role: int, H: int, W: int, attrs, test_lines: int = 4, force_mode: int = -1,
+                        device: int = 0) -> Handle:
+    L = _lib()
+    h = ctypes.c_void_p()
+    opt = _Options(test_lines, force_mode)
+    st = L.jiffy_stream_create(ctypes.byref(h), role, H, W, len(attrs), _attrs(attrs), ctypes.byref(opt), device)
+    if st != 0:
+        raise JiffyError(st, "jiffy_stream_create")
+    return Handle(h.value, role, H, W, attrs, device)
+
+
+def jiffy_stream_destroy(h: Handle):
+    if h.ptr:
+        _lib().jiffy_stream_destroy(h.ptr)
+        h.ptr = None
+
+
+def jiffy_stream_reset(h: Handle):
+    st = _lib().jiffy_stream_reset(h.ptr)
+    if st != 0:
+        raise JiffyError(st, "jiffy_stream_reset")
+
+
+def jiffy_stream_frame_index(h: Handle) -> int:
+    return _lib().jiffy_stream_frame_index(h.ptr)
+
+
+def jiffy_stream_set_profiling(h: Handle, enable: bool = True):
+    st = _lib().jiffy_stream_set_profiling(h.ptr, int(bool(enable)))
+    if st != 0:
+        raise JiffyError(st, "jiffy_stream_set_profiling")
+
+
+def jiffy_stream_kernel_times(h: Handle):
+    """Device ms of each kernel of the last call (launch order)."""
+    buf = (ctypes.c_float * 8)()
+    n = _lib().jiffy_stream_kernel_times(h.ptr, buf, 8)
+    return [float(buf[i]) for i in range(min(n, 8))]
+
+
+def jiffy_max_encoded_size(H: int, W: int, attrs, n_scans: int = 1) -> int:
+    return _lib().jiffy_max_encoded_size(H, W, len(attrs), _attrs(attrs), n_scans)
+
+
+def _ptr_array(tensors):
+    return (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+
+
+def jiffy_encode(h: Handle, planes, out: torch.Tensor, stream=None) -> int:
+    """Encodes one scan (list of A planes) into out (uint8 CUDA tensor);
+    returns the bytes written."""
+    for a, (p, (s, _)) in enumerate(zip(planes, h.attrs)):
+        _check_plane(p, h.H, h.W, s, "plane %d" % a)
+    n = ctypes.c_size_t(0)
+    st = _lib().jiffy_encode(h.ptr, _ptr_array(planes), out.data_ptr(), out.numel() * out.element_size(),
+                             ctypes.byref(n), _stream_ptr(stream))
+    if st != 0:
+        raise JiffyError(st, "jiffy_encode", required=n.value if st == 2 else None)
+    return n.value
+
+
+def _seq_planes(h: Handle, planes):
+    """planes: list over attributes of T x H x W tensors, or list over scans
+    of lists over attributes. Returns (T, flat scan-major list)."""
+    if isinstance(planes[0], torch.Tensor) and len(planes) == h.A and planes[0].dim() == 3:
+        T = planes[0].shape[0]
+        flat = []
+        for t in range(T):
+            for a in range(h.A):
+                flat.append(planes[a][t])
+        return T, flat
+    T = len(planes)
+    return T, [p for scan in planes for p in scan]
+
+
+def jiffy_encode_seq(h: Handle, planes, out: torch.Tensor, stream=None):
+    """Encodes T consecutive scans in one pass; returns (total bytes, list of
+    T + 1 frame offsets)."""
+    T, flat = _seq_planes(h, planes)
+    for i, p in enumerate(flat):
+        _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "plane %d" % i)
+    offs = (ctypes.c_uint64 * (T + 1))()
+    n = ctypes.c_size_t(0)
+    st = _lib().jiffy_encode_seq(h.ptr, T, _ptr_array(flat), out.data_ptr(), out.numel() * out.element_size(),
+                                 offs, ctypes.byref(n), _stream_ptr(stream))
+    if st != 0:
+        raise JiffyError(st, "jiffy_encode_seq", required=n.value if st == 2 else None)
+    return n.value, list(offs)
+
+
+def jiffy_decode(h: Handle, buf: torch.Tensor, length: int, planes_out, stream=None):
+    """Decodes one frame of `length` bytes at the start of buf into planes_out."""
+    for a, (p, (s, _)) in enumerate(zip(planes_out, h.attrs)):
+        _check_plane(p, h.H, h.W, s, "output plane %d" % a)
+    st = _lib().jiffy_decode(h.ptr, buf.data_ptr(), length, _ptr_array(planes_out), _stream_ptr(stream))
+    if st != 0:
+        raise JiffyError(st, "jiffy_decode")
+
+
+def jiffy_decode_seq(h: Handle, buf: torch.Tensor, length: int, offsets, planes_out, stream=None):
+    """Decodes T frames whose byte offsets (T + 1 entries) are `offsets`."""
+    T, flat = _seq_planes(h, planes_out)
+    if len(offsets) != T + 1:
+        raise ValueError("need T + 1 frame offsets")
+    for i, p in enumerate(flat):
+        _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "output plane %d" % i)
+    offs = (ctypes.c_uint64 * (T + 1))(*[int(o) for o in offsets])
+    st = _lib().jiffy_decode_seq(h.ptr, T, buf.data_ptr(), length, offs, _ptr_array(flat), _stream_ptr(stream))
+    if st != 0:
+        raise JiffyError(st, "jiffy_decode_seq")
+
+
+TORCH_DTYPE = {1: torch.uint8, 2: torch.int16, 4: torch.int32}
+
+
+def empty_planes(h: Handle, T: int | None = None, device=None):
+    """Output planes for h: a list over attributes of (T x) H x W tensors."""
+    dev = device if device is not None else torch.device("cuda", h.device)
+    shape = (h.H, h.W) if T is None else (T, h.H, h.W)
+    return [torch.empty(shape, dtype=TORCH_DTYPE[s], device=dev) for s, _ in h.attrs]
