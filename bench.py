@@ -99,9 +99,9 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def make_workload(device: str, seed: int):
+def make_workload(device: str, seed: int, n_scans: int = 100):
     from paper_2209_08196_gb300 import synth
-    cfg = synth.config_multi_attr(seed=seed)
+    cfg = synth.config_multi_attr(seed=seed, n_scans=n_scans)
     seq = synth.ScanSequence(cfg, device=device)
     scans = [seq.scan(t, as_numpy=False) for t in range(cfg.n_scans)]
     return cfg, synth.attr_descs(cfg), scans
@@ -178,6 +178,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
+    ap.add_argument("--scans", type=int, default=100, help="scans per step (100 = the benchmark workload)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -197,7 +199,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     jbuild.build()
     dev = "cuda:%d" % local
-    cfg, attrs, scans = make_workload(dev, seed=0 + rank)
+    cfg, attrs, scans = make_workload(dev, seed=0 + rank, n_scans=args.scans)
     T, H, W, A = cfg.n_scans, cfg.H, cfg.W, len(attrs)
     raw_bytes = sum(p.numel() * p.element_size() for s in scans for p in s)
     enc = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, attrs, device=local)
@@ -282,23 +284,25 @@ def main():
             h.copy_(o, non_blocking=True)
         return nn
 
-    for _ in range(2):
-        e2e_step()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        nn = e2e_step()
-    e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": px_step * world / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
-           "h2d_bytes_per_step": raw_bytes + nn, "d2h_bytes_per_step": nn + raw_bytes}
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(2):
+            e2e_step()
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            nn = e2e_step()
+        e1.record(stream)
+        barrier()
+        e2e_ms = e0.elapsed_time(e1) / args.steps
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": px_step * world / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": raw_bytes + nn, "d2h_bytes_per_step": nn + raw_bytes}
 
     # roofline of the dominant kernel: algorithmic bytes / CUDA-event duration
     avg = {k: statistics.mean(v) for k, v in ktimes.items()}
@@ -325,7 +329,7 @@ def main():
                            "raw_bytes_per_step": raw_bytes, "l2": "inputs larger than L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 4 * args.steps,
+                "gpu_launches": 4 * args.steps * (2 if e2e else 1),
                 "detail": {"kernels": kernels, "compression": modes, "stream_bytes": n,
                            "encode_gpoints_s": px_step / (avg["k_trial"] + avg["k_encode"] + avg["k_finalize"]) / 1e6,
                            "decode_gpoints_s": px_step / avg["k_decode"] / 1e6,
