@@ -75,6 +75,9 @@ def _lib() -> ctypes.CDLL:
         L.jiffy_decode.argtypes = [vp, vp, sz, ctypes.POINTER(vp), vp]
         L.jiffy_decode_seq.restype = ctypes.c_int
         L.jiffy_decode_seq.argtypes = [vp, u32, vp, sz, u64p, ctypes.POINTER(vp), vp]
+        L.jiffy_decode_frame_noalloc.restype = ctypes.c_int
+        L.jiffy_decode_frame_noalloc.argtypes = [vp, sz, u32, u32, u32, ctypes.POINTER(_AttrDesc), u32,
+                                                 ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         _L = L
     return _L
 
@@ -230,6 +233,25 @@ def jiffy_decode_seq(h: Handle, buf: torch.Tensor, length: int, offsets, planes_
     st = _lib().jiffy_decode_seq(h.ptr, T, buf.data_ptr(), length, offs, _ptr_array(flat), _stream_ptr(stream))
     if st != 0:
         raise JiffyError(st, "jiffy_decode_seq")
+
+
+def jiffy_decode_frame_noalloc(buf: torch.Tensor, length: int, H: int, W: int, attrs, scan_index: int,
+                               prev_planes, planes_out, stream=None):
+    """Decodes one frame without a stream handle and without allocating
+    device memory (for callers that may not allocate once running). Pass the
+    previous frame's decoded planes as prev_planes (or None when the frame has
+    no P attribute)."""
+    for a, (p, (s, _)) in enumerate(zip(planes_out, attrs)):
+        _check_plane(p, H, W, s, "output plane %d" % a)
+    prev = None
+    if prev_planes is not None:
+        for a, (p, (s, _)) in enumerate(zip(prev_planes, attrs)):
+            _check_plane(p, H, W, s, "previous plane %d" % a)
+        prev = _ptr_array(prev_planes)
+    st = _lib().jiffy_decode_frame_noalloc(buf.data_ptr(), length, H, W, len(attrs), _attrs(attrs), scan_index,
+                                           prev, _ptr_array(planes_out), _stream_ptr(stream))
+    if st != 0:
+        raise JiffyError(st, "jiffy_decode_frame_noalloc")
 
 
 TORCH_DTYPE = {1: torch.uint8, 2: torch.int16, 4: torch.int32}
