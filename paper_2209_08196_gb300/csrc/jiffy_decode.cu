@@ -1,333 +1,382 @@
 // Jiffy decoder kernel (sm_103a): the encoder's steps run backwards
 // ("straightforward reversal", Sec. III-C).
 //
-// One CTA per row item (scan t, attribute a, row r), taken in ticket order so
-// that every item it may wait on started earlier. Rows decode independently:
-// the row table gives each row's chunk and the residual its first delta
-// continues from. A P row (Sec. III-D) waits for the same row of scan t-1
-// (bounded spin on a done flag) and reads it back from the previous frame's
-// output. Per row: bounds-checked header and row-table parse -> chunk staged
-// in shared memory -> mask words from class codes and literals, XOR with the
-// previous scan's mask for P -> nonzero counts and positions (popc) -> block
-// headers -> unpack low bits and patch exceptions (Sec. II) -> inverse
-// ZigZag (Eq. 1) -> inclusive prefix sum from the carry (inverse delta,
-// mod 2^32) -> + previous value for P -> scatter into the dense row and scale
-// by the precision (Sec. III-A).
+// One warp per row item (scan t, attribute a, row r). Warps take items in
+// batches from an atomic ticket, in increasing order, so every item a warp
+// may wait on was handed out earlier. Rows decode independently: the row
+// table gives each row's chunk and the residual its first delta continues
+// from. A P row (Sec. III-D) waits for the same row of scan t-1 (bounded spin
+// on a done flag) and reads it back from the previous frame's output. There
+// is no CTA-wide barrier: a warp never waits for another warp of its CTA.
+//
+// Per row, each lane owns 8 consecutive pixels (one byte of the zero bitmask)
+// in each 256-pixel step:
+//   lane 0   parses and bounds-checks the frame header and row-table entry
+//   lanes    class words -> literal prefix (Sec. III-C mask code)
+//   pass 1   own mask byte from its class code / literal, XOR with the
+//            previous scan's bits for P (Sec. III-D); nonzero counts
+//   lanes    block headers validated and sized (Sec. II, PFOR blocks)
+//   unpack   block by block, lane per value: funnel bit extract, exception
+//            high parts patched in shared memory, inverse ZigZag (Eq. 1),
+//            warp scans from the row's carry -> residuals (inverse delta)
+//   scatter  warp scan of counts -> compacted index of each own pixel; +
+//            previous pixel for P; x precision (Sec. III-A); vector stores
+// The chunk is read through L1 (__ldg); the row's residuals (compacted order)
+// and mask bytes live in per-warp shared memory.
 #include "jiffy_device.cuh"
 #include "jiffy_kernels.h"
 
 namespace jiffy {
 
-struct DecSmem {
-  uint32_t* stage;  // row chunk words [row_bound/4]
-  uint32_t* z;      // values [W]
-  uint32_t* vprev;  // previous scan's row [W]
-  uint32_t* mask;   // mask words [nw]
-  uint32_t* base;   // per word nonzero count -> exclusive base [nw]
-  uint32_t* boff;   // per block body bytes -> offsets [nbmax]
-};
+namespace {
 
-__host__ __device__ inline size_t dec_smem_bytes(uint32_t W) {
-  uint32_t nw = ceil_div_u32(W, 32), nbmax = ceil_div_u32(W, kBlockN);
-  return 4ull * (row_bound_bytes(W) / 4u + 2ull * W + 2ull * nw + nbmax);
-}
-
-__device__ inline DecSmem dec_smem_carve(uint32_t* p, uint32_t W) {
-  uint32_t nw = ceil_div_u32(W, 32), nbmax = ceil_div_u32(W, kBlockN);
-  DecSmem S;
-  S.stage = p; p += row_bound_bytes(W) / 4u;
-  S.z = p; p += W;
-  S.vprev = p; p += W;
-  S.mask = p; p += nw;
-  S.base = p; p += nw;
-  S.boff = p; p += nbmax;
-  (void)p;
-  return S;
-}
+constexpr uint32_t kDecBatch = 4;  // row items per ticket
 
 __device__ __forceinline__ uint32_t ld_in_u32(const uint8_t* in, unsigned long long at) {
-  return *reinterpret_cast<const uint32_t*>(in + at);
+  return __ldg(reinterpret_cast<const unsigned int*>(in + at));
 }
 
-// Bits [bitpos, bitpos + nbits) of a least-significant-bit-first word stream.
-__device__ __forceinline__ uint32_t extract_bits(const uint32_t* w, uint32_t bitpos, uint32_t nbits) {
-  if (nbits == 0) return 0u;
-  const uint32_t i = bitpos >> 5, sh = bitpos & 31u;
-  uint32_t v = w[i] >> sh;
-  if (sh + nbits > 32u) v |= w[i + 1] << (32u - sh);
-  return nbits >= 32u ? v : (v & ((1u << nbits) - 1u));
+__device__ __forceinline__ uint32_t valid_word_bits(uint32_t W, uint32_t nw, uint32_t j) {
+  return (j + 1 < nw || (W & 31u) == 0) ? 0xffffffffu : ((1u << (W & 31u)) - 1u);
 }
 
-__global__ void __launch_bounds__(kThreads) k_decode(DecParams p) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_tmp[kWarps + 1];
-  __shared__ uint32_t s_item, s_bad, s_mode, s_clen, s_carry, s_nlit, s_litpre[33];
-  __shared__ unsigned long long s_chunk;
+__device__ __forceinline__ uint32_t literal_bits(uint32_t cwd) { return (cwd >> 1) & ~cwd & 0x55555555u; }
 
-  if (threadIdx.x == 0) {
-    s_item = atomicAdd(p.ticket, 1u);
-    s_bad = 0;
-  }
-  __syncthreads();
-  const uint32_t k = s_item;
+}  // namespace
+
+// Per-warp shared memory (byte offsets): the row's residuals in compacted
+// order (one u32 per pixel at most), then its mask bytes.
+struct DecWarpLayout {
+  uint32_t ebuf, mbytes, bytes;
+};
+
+__host__ __device__ inline DecWarpLayout dec_warp_layout(uint32_t W) {
+  DecWarpLayout L;
+  L.ebuf = 0;
+  L.mbytes = 4u * W;
+  L.bytes = (L.mbytes + ceil_div_u32(W, 8u) + 15u) & ~15u;
+  return L;
+}
+
+// One row item, samples of S bytes (compile-time, so each warp runs one
+// compact path).
+__device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k, uint32_t* ebuf, uint8_t* mbytes) {
+  const uint32_t S = p.attrs[(k / p.H) % p.A].s;
+  const uint32_t lane = lane_id();
   const uint32_t H = p.H, W = p.W, A = p.A, nw = p.nw, ncls = p.ncls;
+  const uint32_t niter = ceil_div_u32(W, 256u);
   const uint32_t r = k % H, ta = k / H, a = ta % A, t = ta / A;
   const AttrDev at = p.attrs[a];
-  const size_t rowb = (size_t)W * at.s;
-  DecSmem S = dec_smem_carve(smem, W);
+    const size_t rowb = (size_t)W * S;
 
-  // ---- frame header and row table (warp 0), every field bounds-checked
-  if (threadIdx.x < 32) {
-    const uint32_t lane = lane_id();
-    const unsigned long long f0 = p.off[t], f1 = p.off[t + 1];
-    bool bad = false;
-    // per-attribute header fields, lane l covers attributes l and l + 32
-    unsigned long long sb_before = 0, sb_total = 0;
-    uint32_t my_mode = 0, my_sb = 0;
-    for (uint32_t aa = lane; aa < A; aa += 32) {
-      const uint32_t m = ld_in_u32(p.in, f0 + 8ull + 12ull * aa);
-      const uint32_t sb = ld_in_u32(p.in, f0 + 12ull + 12ull * aa);
-      if ((m & 0xffffff00u) || (m & 0xffu) > 1u) bad = true;
-      sb_total += sb;  // sections are small: no wrap for valid frames; checked below
-      if (aa < a) sb_before += sb;
-      if (aa == a) { my_mode = m & 0xffu; my_sb = sb; }
-      if (sb < 8u * H || (sb & 3u)) bad = true;
+  // ---- frame header and row-table entry; status 1 = malformed, 2 = timed out
+  const unsigned long long f0 = p.off[t], f1 = p.off[t + 1];
+  bool hbad = false;
+  unsigned long long sb_before = 0, sb_total = 0;
+  uint32_t my_mode = 0, my_sb = 0;
+  for (uint32_t aa = lane; aa < A; aa += 32) {
+    const uint32_t m = ld_in_u32(p.in, f0 + 8ull + 12ull * aa);
+    const uint32_t sb = ld_in_u32(p.in, f0 + 12ull + 12ull * aa);
+    if ((m & 0xffffff00u) || (m & 0xffu) > 1u || sb < 8u * H || (sb & 3u)) hbad = true;
+    sb_total += sb;
+    if (aa < a) sb_before += sb;
+    if (aa == a) { my_mode = m & 0xffu; my_sb = sb; }
+  }
+  hbad = __any_sync(0xffffffffu, hbad);
+  for (int o = 16; o > 0; o >>= 1) {
+    sb_total += __shfl_xor_sync(0xffffffffu, sb_total, o);
+    sb_before += __shfl_xor_sync(0xffffffffu, sb_before, o);
+  }
+  const uint32_t mode = __shfl_sync(0xffffffffu, my_mode, a & 31u);
+  my_sb = __shfl_sync(0xffffffffu, my_sb, a & 31u);
+  uint32_t status = 0, clen = 0, carry = 0;
+  unsigned long long chunk_off = 0;
+  if (lane == 0) {
+    bool bad = hbad;
+    const uint32_t frame_bytes = ld_in_u32(p.in, f0);
+    const uint32_t scan = ld_in_u32(p.in, f0 + 4);
+    if (frame_bytes != f1 - f0 || scan != p.frame0 + t || sb_total + p.fhdr != frame_bytes) bad = true;
+    if (mode == 1u && p.frame0 + t == 0) bad = true;
+    if (!bad) {
+      const unsigned long long sec = f0 + p.fhdr + sb_before;
+      const uint32_t data_len = my_sb - 8u * H;
+      const uint32_t end = ld_in_u32(p.in, sec + 8ull * r);
+      carry = ld_in_u32(p.in, sec + 8ull * r + 4);
+      const uint32_t start = r ? ld_in_u32(p.in, sec + 8ull * (r - 1)) : 0u;
+      if (start > end || end > data_len || (r + 1 == H && end != data_len) || ((start | end) & 3u) ||
+          end - start > row_bound_bytes(W) || end - start < 4u * ncls)
+        bad = true;
+      clen = end - start;
+      chunk_off = sec + 8ull * H + start;
     }
-    bad = __any_sync(0xffffffffu, bad);
-    unsigned long long tot = sb_total;
-    for (int o = 16; o > 0; o >>= 1) {
-      tot += __shfl_xor_sync(0xffffffffu, tot, o);
-      sb_before += __shfl_xor_sync(0xffffffffu, sb_before, o);
-    }
-    my_mode = __shfl_sync(0xffffffffu, my_mode, a & 31u);
-    my_sb = __shfl_sync(0xffffffffu, my_sb, a & 31u);
-    if (lane == 0) {
-      const uint32_t frame_bytes = ld_in_u32(p.in, f0);
-      const uint32_t scan = ld_in_u32(p.in, f0 + 4);
-      if (frame_bytes != f1 - f0 || scan != p.frame0 + t || tot + p.fhdr != frame_bytes) bad = true;
-      if (my_mode == 1u && p.frame0 + t == 0) bad = true;
-      uint32_t clen = 0, carry = 0;
-      unsigned long long chunk = 0;
-      if (!bad) {
-        const unsigned long long sec = f0 + p.fhdr + sb_before;
-        const uint32_t data_len = my_sb - 8u * H;
-        const uint32_t end = ld_in_u32(p.in, sec + 8ull * r);
-        carry = ld_in_u32(p.in, sec + 8ull * r + 4);
-        const uint32_t start = r ? ld_in_u32(p.in, sec + 8ull * (r - 1)) : 0u;
-        if (start > end || end > data_len || (r + 1 == H && end != data_len) || ((start | end) & 3u) ||
-            end - start > row_bound_bytes(W) || end - start < 4u * ncls)
+    if (k == 0 && p.check_shdr && !bad) {  // stream header: shape, dtypes, precisions
+      if (ld_in_u32(p.in, 0) != 0x3159464Au || ld_in_u32(p.in, 4) != (1u | (A << 16)) ||
+          ld_in_u32(p.in, 8) != H || ld_in_u32(p.in, 12) != W)
+        bad = true;
+      for (uint32_t aa = 0; aa < A && !bad; aa++) {
+        if (ld_in_u32(p.in, 16 + 8ull * aa) != (p.attrs[aa].s | (1u << 8)) ||
+            ld_in_u32(p.in, 20 + 8ull * aa) != p.attrs[aa].P)
           bad = true;
-        clen = end - start;
-        chunk = sec + 8ull * H + start;
       }
-      if (k == 0 && p.check_shdr && !bad) {  // stream header: shape, dtypes, precisions
-        if (ld_in_u32(p.in, 0) != 0x3159464Au || ld_in_u32(p.in, 4) != (1u | (A << 16)) ||
-            ld_in_u32(p.in, 8) != H || ld_in_u32(p.in, 12) != W)
-          bad = true;
-        for (uint32_t aa = 0; aa < A && !bad; aa++) {
-          if (ld_in_u32(p.in, 16 + 8ull * aa) != (p.attrs[aa].s | (1u << 8)) ||
-              ld_in_u32(p.in, 20 + 8ull * aa) != p.attrs[aa].P)
-            bad = true;
+    }
+    status = bad ? 1u : 0u;
+    // a P row waits for the same row of the previous frame (bounded)
+    if (!bad && mode == 1u && t > 0) {
+      const volatile uint32_t* flag = p.done + (k - A * H);
+      if (!*flag) {
+        const unsigned long long t0 = global_timer_ns();
+        uint32_t ns = 32;
+        while (!*flag) {
+          __nanosleep(ns);
+          if (ns < 1024) ns <<= 1;
+          if (global_timer_ns() - t0 > kSpinLimitNs) {
+            atomicOr(p.err, kErrTimeout);
+            status = 2u;
+            break;
+          }
         }
       }
-      s_bad = bad;
-      s_mode = my_mode;
-      s_clen = clen;
-      s_carry = carry;
-      s_chunk = chunk;
+      __threadfence();
     }
   }
-  __syncthreads();
-  const uint32_t mode = s_mode;
-  bool ok = !s_bad;
+  status = __shfl_sync(0xffffffffu, status, 0);
+  clen = __shfl_sync(0xffffffffu, clen, 0);
+  carry = __shfl_sync(0xffffffffu, carry, 0);
+  chunk_off = __shfl_sync(0xffffffffu, chunk_off, 0);
+  if (mode == 1u) __threadfence();  // every lane orders its reads of the previous row after the flag
 
-  // ---- P rows wait for the same row of the previous frame (bounded)
-  if (ok && mode == 1u && t > 0 && threadIdx.x == 0) {
-    const uint32_t* flag = p.done + (k - A * H);
-    if (!*reinterpret_cast<const volatile uint32_t*>(flag)) {
-      const unsigned long long t0 = global_timer_ns();
-      uint32_t ns = 32;
-      while (!*reinterpret_cast<const volatile uint32_t*>(flag)) {
-        __nanosleep(ns);
-        if (ns < 1024) ns <<= 1;
-        if (global_timer_ns() - t0 > kSpinLimitNs) {
-          atomicOr(p.err, kErrTimeout);
-          s_bad = 2;
-          break;
+  const uint32_t* chunk = reinterpret_cast<const uint32_t*>(p.in + chunk_off);
+  bool bad = status != 0;
+  if (!bad) prefetch_l1(chunk, clen);
+  // ---- class words: class 3 and bits past nw are invalid; literal prefix
+  uint32_t cw = 0, lit = 0;
+  if (!bad && lane < ncls) {
+    cw = __ldg(chunk + lane);
+    uint32_t used = 0xffffffffu;
+    const uint32_t nslots = min(16u, nw - 16u * lane);
+    if (nslots < 16u) used = (1u << (2u * nslots)) - 1u;
+    lit = __popc(literal_bits(cw));
+    if (((cw >> 1) & cw & 0x55555555u) || (cw & ~used)) bad = true;
+  }
+  const uint32_t litincl = warp_incl_scan(lit);
+  const uint32_t litpre = litincl - lit;
+  const uint32_t nlit = __shfl_sync(0xffffffffu, litincl, 31);
+  bad = __any_sync(0xffffffffu, bad) || 4u * (ncls + nlit) > clen;
+  {  // a literal last mask word may not set bits past W
+    const uint32_t j = nw - 1;
+    const uint32_t cwj = __shfl_sync(0xffffffffu, cw, (j >> 4) & 31u);
+    const uint32_t lpj = __shfl_sync(0xffffffffu, litpre, (j >> 4) & 31u);
+    if (!bad && (W & 31u) && ((cwj >> (2u * (j & 15u))) & 3u) == 2u) {
+      const uint32_t li = lpj + __popc(literal_bits(cwj) & ((1u << (2u * (j & 15u))) - 1u));
+      if (__ldg(chunk + ncls + li) & ~valid_word_bits(W, nw, j)) bad = true;
+    }
+  }
+
+  uint8_t* orow = p.outp[ta] + r * rowb;
+  uint8_t* srow = (t + 1 == p.T) ? p.state_next[a] + r * rowb : nullptr;
+  const uint8_t* prow = mode == 1u ? (t > 0 ? p.outp[(t - 1) * A + a] : p.state[a]) + r * rowb : nullptr;
+  const bool vec_prev = prow && vec_ok(prow, S);
+  const bool vec_out = vec_ok(orow, S) && (!srow || vec_ok(srow, S));
+
+  // ---- pass 1: own mask bytes (1 = zero sample) and nonzero counts
+  uint32_t cnt = 0;
+  if (!bad) {
+    for (uint32_t it = 0; it < niter; it++) {
+      const uint32_t x0 = 256u * it + 8u * lane;
+      const uint32_t j = x0 >> 5;
+      const uint32_t cwj = __shfl_sync(0xffffffffu, cw, (j >> 4) & 31u);
+      const uint32_t lpj = __shfl_sync(0xffffffffu, litpre, (j >> 4) & 31u);
+      if (x0 < W) {
+        const uint32_t sl = 2u * (j & 15u), cls = (cwj >> sl) & 3u;
+        uint32_t X = 0;
+        if (cls == 1u) X = valid_word_bits(W, nw, j);
+        else if (cls == 2u) X = __ldg(chunk + ncls + lpj + __popc(literal_bits(cwj) & ((1u << sl) - 1u)));
+        const uint32_t nv = min(8u, W - x0), vm = (1u << nv) - 1u;
+        uint32_t mb = (X >> (x0 & 31u)) & 0xffu;
+        if (mode == 1u) {
+          uint32_t pv[8];
+          load8<true>(prow, S, x0, nv, vec_prev, pv);
+          uint32_t pm = 0;
+#pragma unroll
+          for (int i = 0; i < 8; i++) pm |= (uint32_t)(pv[i] == 0u) << i;
+          mb ^= pm;  // Sec. III-D: undo the XOR with the previous scan's mask
         }
+        mb = (mb & vm) | (0xffu & ~vm);  // pixels past W count as zero samples
+        mbytes[x0 >> 3] = (uint8_t)mb;
+        cnt += __popc(~mb & 0xffu);
       }
     }
-    __threadfence();
   }
-  __syncthreads();
-  ok = !s_bad;
+  const uint32_t n = warp_sum(cnt);
+  const uint32_t nb = ceil_div_u32(n, kBlockN);
 
-  uint32_t n = 0, nlit = 0, nb = 0;
-  if (ok) {
-    // ---- stage the chunk and (P) the previous row
-    const uint32_t clen = s_clen;
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(p.in + s_chunk);
-    for (uint32_t i = threadIdx.x; i < clen / 4u; i += kThreads) S.stage[i] = src[i];
-    if (mode == 1u) {
-      const uint8_t* prow = (t > 0 ? p.outp[(t - 1) * A + a] : p.state[a]) + r * rowb;
-      for (uint32_t x = threadIdx.x; x < W; x += kThreads) S.vprev[x] = load_sample_cg(prow, at.s, x);
-    }
-    __syncthreads();
-    // ---- literal counts per class word (2-bit class 2 = literal, 3 = invalid)
-    if (threadIdx.x < 32) {
-      const uint32_t lane = lane_id();
-      uint32_t lit = 0;
-      bool bad = false;
-      if (lane < ncls) {
-        const uint32_t cw = S.stage[lane];
-        uint32_t used = 0xffffffffu;  // class slots past nw must be 0
-        const uint32_t nslots = min(16u, nw - 16u * lane);
-        if (nslots < 16u) used = (1u << (2u * nslots)) - 1u;
-        lit = __popc((cw >> 1) & ~cw & 0x55555555u);
-        if (((cw >> 1) & cw & 0x55555555u) || (cw & ~used)) bad = true;
-      }
-      const uint32_t incl = warp_incl_scan(lit);
-      if (lane < ncls) s_litpre[lane] = incl - lit;
-      bad = __any_sync(0xffffffffu, bad);
-      if (lane == 31) {
-        s_nlit = incl;
-        if (bad || 4u * (ncls + incl) > clen) s_bad = 1;
+  // ---- block headers (lane l: blocks 4l .. 4l+3): validate, size the
+  //      bodies, check they fill the chunk exactly
+  const uint32_t hdr0 = ncls + nlit;
+  if (!bad && 4u * (hdr0 + nb) > clen) bad = true;
+  {
+    uint32_t mysum = 0;
+    bool lbad = false;
+#pragma unroll
+    for (uint32_t q = 0; q < 4; q++) {
+      const uint32_t blk = 4u * lane + q;
+      if (!bad && blk < nb) {
+        const uint32_t h = __ldg(chunk + hdr0 + blk);
+        const uint32_t b = h & 0xffu, e = (h >> 8) & 0xffu, hb = (h >> 16) & 0xffu;
+        const uint32_t m = min(kBlockN, n - blk * kBlockN);
+        if ((h >> 24) || b > 32u || hb > 32u || b + hb > 32u || e > m || ((e == 0u) != (hb == 0u))) lbad = true;
+        mysum += block_body_bytes(m, min(b, 32u), min(e, m), min(b + hb, 32u)) / 4u;
       }
     }
-    __syncthreads();
-    ok = !s_bad;
+    bad = __any_sync(0xffffffffu, bad || lbad);
+    if (!bad && 4u * (hdr0 + nb + warp_sum(mysum)) != clen) bad = true;
   }
-  if (ok) {
-    nlit = s_nlit;
-    // ---- mask words: decoded class/literal, XOR previous mask for P
-    for (uint32_t j = warp_id(); j < nw; j += kWarps) {
-      const uint32_t x = 32u * j + lane_id();
-      const uint32_t valid = (j + 1 < nw || (W & 31u) == 0) ? 0xffffffffu : ((1u << (W & 31u)) - 1u);
-      const uint32_t cw = S.stage[j >> 4];
-      const uint32_t sl = 2u * (j & 15u);
-      const uint32_t cls = (cw >> sl) & 3u;
-      uint32_t X = 0;
-      if (cls == 1u) X = valid;
-      else if (cls == 2u) {
-        const uint32_t li = s_litpre[j >> 4] + __popc((cw >> 1) & ~cw & 0x55555555u & ((1u << sl) - 1u));
-        X = S.stage[ncls + li];
-        if (X & ~valid) s_bad = 1;
-      }
-      uint32_t M = X;
-      if (mode == 1u) M ^= __ballot_sync(0xffffffffu, x < W && S.vprev[x] == 0u);
-      if (lane_id() == 0) {
-        S.mask[j] = M;
-        S.base[j] = __popc(~M & valid);
-      }
-    }
-    __syncthreads();
-    n = block_excl_scan(S.base, nw, s_tmp);
-    nb = ceil_div_u32(n, kBlockN);
-    if (4u * (ncls + nlit + nb) > s_clen) s_bad = 1;
-    __syncthreads();
-    ok = !s_bad;
-  }
-  if (ok) {
-    // ---- block headers
-    const uint32_t* hdr = S.stage + ncls + nlit;
-    for (uint32_t blk = threadIdx.x; blk < nb; blk += kThreads) {
-      const uint32_t h = hdr[blk];
-      const uint32_t b = h & 0xffu, e = (h >> 8) & 0xffu, hb = (h >> 16) & 0xffu;
-      const uint32_t m = min(kBlockN, n - blk * kBlockN);
-      if ((h >> 24) || b > 32u || hb > 32u || b + hb > 32u || e > m || ((e == 0u) != (hb == 0u))) s_bad = 1;
-      S.boff[blk] = block_body_bytes(m, min(b, 32u), min(e, m), min(b + hb, 32u));
-    }
-    __syncthreads();
-    const uint32_t body = block_excl_scan(S.boff, nb, s_tmp);
-    if (4u * (ncls + nlit + nb) + body != s_clen) s_bad = 1;
-    __syncthreads();
-    ok = !s_bad;
-  }
-  if (ok) {
-    // ---- unpack: warp per block
-    const uint32_t* hdr = S.stage + ncls + nlit;
-    for (uint32_t blk = warp_id(); blk < nb; blk += kWarps) {
-      const uint32_t h = hdr[blk];
+
+  // ---- unpack block by block (lane l: values l, l+32, l+64, l+96):
+  //      funnel bit extract, exceptions patched in shared memory, inverse
+  //      ZigZag (Eq. 1) and the inverse delta from the row's carry
+  if (!bad) {
+    uint32_t bodyw = hdr0 + nb;  // word offset of the current block's body
+    uint32_t erun = carry;
+    bool xbad = false;
+    const uint32_t last_word = clen / 4u - 1u;
+    for (uint32_t blk = 0; blk < nb; blk++) {
+      const uint32_t h = __ldg(chunk + hdr0 + blk);
       const uint32_t b = h & 0xffu, e = (h >> 8) & 0xffu, hb = (h >> 16) & 0xffu;
       const uint32_t base = blk * kBlockN, m = min(kBlockN, n - base);
-      const uint32_t* body = S.stage + ncls + nlit + nb + S.boff[blk] / 4u;
-      for (uint32_t i = lane_id(); i < m; i += 32) S.z[base + i] = extract_bits(body, i * b, b);
-      __syncwarp();
+      const uint32_t bmask = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
+      const uint32_t low_words = (m * b + 31u) >> 5;
+      if (b) {
+#pragma unroll
+        for (uint32_t q = 0; q < 4; q++) {
+          const uint32_t i = lane + 32u * q;
+          if (i < m) {
+            const uint32_t bit = i * b, wi = bodyw + (bit >> 5);
+            const uint32_t lo = __ldg(chunk + wi), hi = __ldg(chunk + min(wi + 1u, last_word));
+            ebuf[base + i] = __funnelshift_r(lo, hi, bit & 31u) & bmask;
+          }
+        }
+      } else {
+        for (uint32_t i = lane; i < m; i += 32) ebuf[base + i] = 0u;
+      }
       if (e) {
-        const uint32_t low_words = (m * b + 31u) >> 5;
-        const uint8_t* pos = reinterpret_cast<const uint8_t*>(body + low_words);
-        const uint32_t* high = body + low_words + ((e + 3u) >> 2);
-        for (uint32_t j = lane_id(); j < e; j += 32) {
-          const uint32_t ps = pos[j];
-          if (ps >= m || (j > 0 && ps <= pos[j - 1])) s_bad = 1;
-          else S.z[base + ps] |= extract_bits(high, j * hb, hb) << b;
+        __syncwarp();
+        const uint8_t* pos = reinterpret_cast<const uint8_t*>(chunk + bodyw + low_words);
+        const uint32_t hw = bodyw + low_words + ((e + 3u) >> 2);
+        const uint32_t hmask = hb >= 32u ? 0xffffffffu : ((1u << hb) - 1u);
+        for (uint32_t jx = lane; jx < e; jx += 32) {
+          const uint32_t ps = __ldg(pos + jx);
+          if (ps >= m || (jx > 0 && ps <= __ldg(pos + jx - 1))) {
+            xbad = true;
+          } else {
+            const uint32_t bit = jx * hb, wi = hw + (bit >> 5);
+            const uint32_t lo = __ldg(chunk + wi), hi = __ldg(chunk + min(wi + 1u, last_word));
+            ebuf[base + ps] |= (__funnelshift_r(lo, hi, bit & 31u) & hmask) << b;
+          }
         }
       }
       __syncwarp();
-    }
-    __syncthreads();
-    ok = !s_bad;
-  }
-  if (ok) {
-    // ---- inverse ZigZag + inclusive prefix from the carry (mod 2^32)
-    const uint32_t per = (n + kThreads - 1) / kThreads;
-    const uint32_t beg = min(threadIdx.x * per, n), end = min(beg + per, n);
-    uint32_t sum = 0;
-    for (uint32_t i = beg; i < end; i++) sum += unzigzag(S.z[i]);
-    const uint32_t incl = warp_incl_scan(sum);
-    if (lane_id() == 31) s_tmp[warp_id()] = incl;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const uint32_t w = threadIdx.x < (uint32_t)kWarps ? s_tmp[threadIdx.x] : 0u;
-      const uint32_t wi = warp_incl_scan(w);
-      if (threadIdx.x < (uint32_t)kWarps) s_tmp[threadIdx.x] = wi - w;
-    }
-    __syncthreads();
-    uint32_t run = s_carry + s_tmp[warp_id()] + incl - sum;
-    for (uint32_t i = beg; i < end; i++) {
-      run += unzigzag(S.z[i]);
-      S.z[i] = run;
-    }
-    __syncthreads();
-    // ---- scatter, + previous value (P), times the precision
-    uint8_t* orow = p.outp[ta] + r * rowb;
-    uint8_t* srow = (t + 1 == p.T) ? p.state_next[a] + r * rowb : nullptr;
-    const uint32_t P = at.P;
-    for (uint32_t j = warp_id(); j < nw; j += kWarps) {
-      const uint32_t x = 32u * j + lane_id();
-      if (x < W) {
-        const uint32_t M = S.mask[j];
-        uint32_t v = 0;
-        if (!((M >> lane_id()) & 1u)) {
-          const uint32_t kk = S.base[j] + __popc(~M & ((1u << lane_id()) - 1u));
-          v = S.z[kk] * P;
-          if (mode == 1u) v += S.vprev[x];
-        }
-        store_sample(orow, at.s, x, v);
-        if (srow) store_sample(srow, at.s, x, v);
+#pragma unroll
+      for (uint32_t q = 0; q < 4; q++) {
+        const uint32_t i = lane + 32u * q;
+        const uint32_t d = i < m ? unzigzag(ebuf[base + i]) : 0u;
+        uint32_t tot;
+        const uint32_t ex = warp_excl_scan(d, tot);
+        if (i < m) ebuf[base + i] = erun + ex + d;
+        erun += tot;
       }
+      bodyw += block_body_bytes(m, b, e, b + hb) / 4u;
     }
-  } else if (threadIdx.x == 0 && s_bad == 1) {
-    atomicOr(p.err, kErrCorrupt);
+    bad = __any_sync(0xffffffffu, xbad);
+    __syncwarp();
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicExch(p.done + k, 1u);
+
+  // ---- scatter by position: + previous pixel (P), x precision (Sec. III-A)
+  if (!bad) {
+    const uint32_t Pq = at.P;
+    uint32_t kbase = 0;
+    for (uint32_t it = 0; it < niter; it++) {
+      const uint32_t x0 = 256u * it + 8u * lane;
+      const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
+      const uint32_t mb = nv ? mbytes[x0 >> 3] : 0xffu;
+      uint32_t segn;
+      uint32_t kk = kbase + warp_excl_scan(__popc(~mb & 0xffu), segn);
+      uint32_t pv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (mode == 1u && nv) load8<true>(prow, S, x0, nv, vec_prev, pv);
+      uint32_t out[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        const bool nzb = !((mb >> i) & 1u);
+        const uint32_t e = nzb ? ebuf[kk] : 0u;
+        out[i] = nzb ? e * Pq + pv[i] : 0u;
+        kk += nzb ? 1u : 0u;
+      }
+      if (nv) {
+        store8(orow, S, x0, nv, vec_out, out);
+        if (srow) store8(srow, S, x0, nv, vec_out, out);
+      }
+      kbase += segn;
+    }
+  }
+  if (lane == 0 && bad && status != 2u) atomicOr(p.err, kErrCorrupt);
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) atomicExch(p.done + k, 1u);
+}
+
+template <int WPC>
+__global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t lane = lane_id();
+  const DecWarpLayout lay = dec_warp_layout(p.W);
+  uint8_t* wb = reinterpret_cast<uint8_t*>(smem) + warp_id() * lay.bytes;
+  uint32_t* ebuf = reinterpret_cast<uint32_t*>(wb + lay.ebuf);
+  uint8_t* mbytes = wb + lay.mbytes;
+  while (true) {
+    uint32_t kb = 0;
+    if (lane == 0) kb = atomicAdd(p.ticket, kDecBatch);
+    kb = __shfl_sync(0xffffffffu, kb, 0);
+    if (kb >= p.n_items) break;
+    const uint32_t kend = min(kb + kDecBatch, p.n_items);
+    for (uint32_t k = kb; k < kend; k++) {
+      decode_item(p, k, ebuf, mbytes);
+    }
   }
 }
 
-size_t dec_smem_bytes_host(uint32_t W) { return dec_smem_bytes(W); }
+size_t dec_smem_bytes_host(uint32_t W) { return dec_warp_layout(W).bytes; }
+
+template <int WPC>
+static int launch_decode_t(const DecParams& p, cudaStream_t st) {
+  const DecWarpLayout L = dec_warp_layout(p.W);
+  if (L.bytes & 15u) return (int)cudaErrorInvalidValue;  // per-warp regions must stay 16-byte aligned
+  const size_t smem = (size_t)WPC * L.bytes;
+  cudaError_t e = cudaFuncSetAttribute(k_decode<WPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_decode<WPC>, WPC * 32, smem)) != cudaSuccess)
+    return (int)e;
+  // enough warps to fill the GPU; warps beyond the work find the ticket spent
+  const uint32_t want = ceil_div_u32(p.n_items, kDecBatch * WPC);
+  const uint32_t grid = max(1u, min(want, (uint32_t)(max(per_sm, 1) * sms)));
+  k_decode<WPC><<<grid, WPC * 32, smem, st>>>(p);
+  return (int)cudaGetLastError();
+}
 
 int launch_decode(const DecParams& p, void* stream, void* const* ev) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const size_t smem = dec_smem_bytes(p.W);
-  cudaError_t e = cudaFuncSetAttribute(k_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return (int)e;
   if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[0]), st);
-  k_decode<<<p.n_items, kThreads, smem, st>>>(p);
+  // warps per CTA from the per-warp shared memory (row-sized residual buffer)
+  const size_t per_warp = dec_warp_layout(p.W).bytes;
+  int rc;
+  if (8 * per_warp <= 100 * 1024) rc = launch_decode_t<8>(p, st);
+  else if (4 * per_warp <= 100 * 1024) rc = launch_decode_t<4>(p, st);
+  else if (2 * per_warp <= 100 * 1024) rc = launch_decode_t<2>(p, st);
+  else rc = launch_decode_t<1>(p, st);
   if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[1]), st);
-  return (int)cudaGetLastError();
+  return rc;
 }
 
 }  // namespace jiffy

@@ -40,6 +40,158 @@ __device__ __forceinline__ void store_sample(uint8_t* row, uint32_t s, uint32_t 
   else row[x] = (uint8_t)v;
 }
 
+__device__ __forceinline__ uint32_t warp_incl_scan_fwd(uint32_t v) {
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= (uint32_t)o) v += t;
+  }
+  return v;
+}
+
+// Warp-wide prefetch of [p, p + bytes) into L1, one 128-byte line per lane per
+// round: a single round of independent requests instead of many dependent
+// ones later.
+__device__ __forceinline__ void prefetch_l1(const void* p, uint32_t bytes) {
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(p) & ~uintptr_t(127);
+  const uintptr_t a1 = reinterpret_cast<uintptr_t>(p) + bytes;
+  for (uintptr_t a = a0 + 128u * (threadIdx.x & 31u); a < a1; a += 32u * 128u)
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+}
+
+// Groups of 8 consecutive samples move as one vector when the group is
+// aligned: 32 bytes (u32), 16 bytes (u16) or 8 bytes (u8). Group starts are
+// multiples of 8 samples, so a vector-aligned row base suffices.
+__device__ __forceinline__ bool vec_ok(const void* row, uint32_t s) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(row);
+  return s == 1 ? (a & 7u) == 0 : (a & 15u) == 0;
+}
+
+// Loads the nvalid (<= 8) samples from pixel x0 (missing ones read as 0);
+// CG bypasses L1 (data other CTAs wrote during this kernel).
+// Scalar paths for ragged or unaligned groups (rare), kept out of line so the
+// hot loops stay small.
+template <bool CG>
+static __device__ __noinline__ void load8_slow(const uint8_t* row, uint32_t s, uint32_t x0, uint32_t nvalid, uint32_t* v) {
+  for (uint32_t i = 0; i < 8; i++)
+    v[i] = i < nvalid ? (CG ? load_sample_cg(row, s, x0 + i) : load_sample(row, s, x0 + i)) : 0u;
+}
+
+static __device__ __noinline__ void store8_slow(uint8_t* row, uint32_t s, uint32_t x0, uint32_t nvalid, const uint32_t* v) {
+  for (uint32_t i = 0; i < nvalid; i++) store_sample(row, s, x0 + i, v[i]);
+}
+
+template <bool CG>
+__device__ __forceinline__ void load8(const uint8_t* row, uint32_t s, uint32_t x0, uint32_t nvalid, bool vec,
+                                      uint32_t (&v)[8]) {
+  if (vec && nvalid == 8) {
+    if (s == 4) {
+      const uint4* q = reinterpret_cast<const uint4*>(row + 4ull * x0);
+      const uint4 a = CG ? __ldcg(q) : q[0];
+      const uint4 b = CG ? __ldcg(q + 1) : q[1];
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else if (s == 2) {
+      const uint4* q = reinterpret_cast<const uint4*>(row + 2ull * x0);
+      const uint4 a = CG ? __ldcg(q) : q[0];
+      const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int i = 0; i < 4; i++) { v[2 * i] = w[i] & 0xffffu; v[2 * i + 1] = w[i] >> 16; }
+    } else {
+      const uint2* q = reinterpret_cast<const uint2*>(row + x0);
+      const uint2 a = CG ? __ldcg(q) : q[0];
+#pragma unroll
+      for (int i = 0; i < 4; i++) { v[i] = (a.x >> (8 * i)) & 0xffu; v[4 + i] = (a.y >> (8 * i)) & 0xffu; }
+    }
+    return;
+  }
+  uint32_t tmp[8];
+  load8_slow<CG>(row, s, x0, nvalid, tmp);
+#pragma unroll
+  for (int i = 0; i < 8; i++) v[i] = tmp[i];
+}
+
+__device__ __forceinline__ void store8(uint8_t* row, uint32_t s, uint32_t x0, uint32_t nvalid, bool vec,
+                                       const uint32_t (&v)[8]) {
+  if (vec && nvalid == 8) {
+    if (s == 4) {
+      uint4* q = reinterpret_cast<uint4*>(row + 4ull * x0);
+      q[0] = make_uint4(v[0], v[1], v[2], v[3]);
+      q[1] = make_uint4(v[4], v[5], v[6], v[7]);
+    } else if (s == 2) {
+      uint4* q = reinterpret_cast<uint4*>(row + 2ull * x0);
+      q[0] = make_uint4((v[0] & 0xffffu) | (v[1] << 16), (v[2] & 0xffffu) | (v[3] << 16),
+                        (v[4] & 0xffffu) | (v[5] << 16), (v[6] & 0xffffu) | (v[7] << 16));
+    } else {
+      uint2* q = reinterpret_cast<uint2*>(row + x0);
+      q[0] = make_uint2((v[0] & 0xffu) | ((v[1] & 0xffu) << 8) | ((v[2] & 0xffu) << 16) | (v[3] << 24),
+                        (v[4] & 0xffu) | ((v[5] & 0xffu) << 8) | ((v[6] & 0xffu) << 16) | (v[7] << 24));
+    }
+    return;
+  }
+  uint32_t tmp[8];
+#pragma unroll
+  for (int i = 0; i < 8; i++) tmp[i] = v[i];
+  store8_slow(row, s, x0, nvalid, tmp);
+}
+
+// Compile-time sample width variants (S = 1, 2 or 4 bytes).
+template <uint32_t S, bool CG>
+__device__ __forceinline__ void load8s(const uint8_t* row, uint32_t x0, uint32_t nvalid, bool vec, uint32_t (&v)[8]) {
+  if (vec && nvalid == 8) {
+    if constexpr (S == 4) {
+      const uint4* q = reinterpret_cast<const uint4*>(row + 4ull * x0);
+      const uint4 a = CG ? __ldcg(q) : q[0];
+      const uint4 b = CG ? __ldcg(q + 1) : q[1];
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else if constexpr (S == 2) {
+      const uint4* q = reinterpret_cast<const uint4*>(row + 2ull * x0);
+      const uint4 a = CG ? __ldcg(q) : q[0];
+      const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int i = 0; i < 4; i++) { v[2 * i] = w[i] & 0xffffu; v[2 * i + 1] = w[i] >> 16; }
+    } else {
+      const uint2* q = reinterpret_cast<const uint2*>(row + x0);
+      const uint2 a = CG ? __ldcg(q) : q[0];
+#pragma unroll
+      for (int i = 0; i < 4; i++) { v[i] = (a.x >> (8 * i)) & 0xffu; v[4 + i] = (a.y >> (8 * i)) & 0xffu; }
+    }
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; i++)
+    v[i] = (uint32_t)i < nvalid ? (CG ? load_sample_cg(row, S, x0 + i) : load_sample(row, S, x0 + i)) : 0u;
+}
+
+template <uint32_t S>
+__device__ __forceinline__ void store8s(uint8_t* row, uint32_t x0, uint32_t nvalid, bool vec, const uint32_t (&v)[8]) {
+  if (vec && nvalid == 8) {
+    if constexpr (S == 4) {
+      uint4* q = reinterpret_cast<uint4*>(row + 4ull * x0);
+      q[0] = make_uint4(v[0], v[1], v[2], v[3]);
+      q[1] = make_uint4(v[4], v[5], v[6], v[7]);
+    } else if constexpr (S == 2) {
+      uint4* q = reinterpret_cast<uint4*>(row + 2ull * x0);
+      q[0] = make_uint4((v[0] & 0xffffu) | (v[1] << 16), (v[2] & 0xffffu) | (v[3] << 16),
+                        (v[4] & 0xffffu) | (v[5] << 16), (v[6] & 0xffffu) | (v[7] << 16));
+    } else {
+      uint2* q = reinterpret_cast<uint2*>(row + x0);
+      q[0] = make_uint2((v[0] & 0xffu) | ((v[1] & 0xffu) << 8) | ((v[2] & 0xffu) << 16) | (v[3] << 24),
+                        (v[4] & 0xffu) | ((v[5] & 0xffu) << 8) | ((v[6] & 0xffu) << 16) | (v[7] << 24));
+    }
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 8; i++)
+    if ((uint32_t)i < nvalid) store_sample(row, S, x0 + i, v[i]);
+}
+
+__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t& total) {
+  const uint32_t incl = warp_incl_scan_fwd(v);
+  total = __shfl_sync(0xffffffffu, incl, 31);
+  return incl - v;
+}
+
 // Quantization, Sec. III-B: q = min(floor((v + floor(P/2)) / P), floor(max/P)).
 // The division uses the round-up reciprocal m = ceil(2^64/P) (Granlund and
 // Montgomery, "Division by invariant integers using multiplication", 1994):
@@ -86,28 +238,46 @@ struct BlockChoice {
 };
 
 // Warp-wide choice of the block width. Lane l holds values l, l+32, l+64,
-// l+96 of a block of n <= 128 values (zero past n). Picks the b in [0, wmax]
-// with the fewest body bytes, the smallest b on ties.
-__device__ __forceinline__ BlockChoice choose_block(const uint32_t (&z)[4], uint32_t n) {
+// l+96 of a block of n <= 128 values (zero past n); hist is a per-warp shared
+// scratch of 33 words. Builds the histogram of value widths (one shared write
+// per distinct width per pass, grouped with __match_any_sync), turns it into
+// e_b = #values wider than b with a suffix sum across lanes (lane l <-> width
+// l + 1), prices every candidate b in [0, wmax] in parallel (lane b) and takes
+// the cheapest, the smallest b on ties: the same choice as an exhaustive
+// search over b.
+__device__ __forceinline__ BlockChoice choose_block(const uint32_t (&z)[4], uint32_t n, uint32_t* hist) {
   const uint32_t lane = lane_id();
-  uint32_t w[4];
-  uint32_t wm = 0;
+  hist[lane] = 0;
+  if (lane == 0) hist[32] = 0;
+  __syncwarp();
 #pragma unroll
   for (int m = 0; m < 4; m++) {
-    w[m] = (lane + 32u * m < n) ? bit_width(z[m]) : 0u;
-    wm = max(wm, w[m]);
+    const uint32_t w = (lane + 32u * m < n) ? bit_width(z[m]) : 0u;
+    const uint32_t grp = __match_any_sync(0xffffffffu, w);
+    if (lane == (uint32_t)(__ffs(grp) - 1)) hist[w] += __popc(grp);
+    __syncwarp();
   }
-  const uint32_t wmax = __reduce_max_sync(0xffffffffu, wm);
-  BlockChoice best{0, 0, 0, 0xffffffffu};
-  for (uint32_t b = 0; b <= wmax; b++) {
-    uint32_t e = 0;
+  const uint32_t c = hist[lane + 1];  // values of width lane + 1
+  const uint32_t present = __ballot_sync(0xffffffffu, c != 0u);
+  const uint32_t wmax = present ? 32u - __clz(present) : 0u;
+  uint32_t e = c;  // -> number of values wider than lane
 #pragma unroll
-    for (int m = 0; m < 4; m++) e += __popc(__ballot_sync(0xffffffffu, w[m] > b));
-    uint32_t bytes = block_body_bytes(n, b, e, wmax);
-    if (bytes < best.bytes) best = BlockChoice{b, e, e ? wmax - b : 0u, bytes};
-    if (e == 0) break;  // larger b only grows the low part
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_down_sync(0xffffffffu, e, o);
+    if (lane + o < 32u) e += t;
   }
-  return best;
+  uint32_t key = 0xffffffffu;
+  if (lane <= wmax) key = (block_body_bytes(n, lane, e, wmax) << 6) | lane;
+  key = __reduce_min_sync(0xffffffffu, key);
+  if (wmax == 32u) key = min(key, ((4u * n) << 6) | 32u);  // b = 32: no exceptions
+  const uint32_t b = key & 63u;
+  const uint32_t eb = __shfl_sync(0xffffffffu, e, b & 31u);
+  BlockChoice r;
+  r.b = b;
+  r.e = b < 32u ? eb : 0u;
+  r.hb = r.e ? wmax - b : 0u;
+  r.bytes = key >> 6;
+  return r;
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {

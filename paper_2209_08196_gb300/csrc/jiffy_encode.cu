@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_trial(EncParams p) {
   __shared__ unsigned long long s_cost[2];
   __shared__ uint32_t s_rows[kMaxTestLines];
   __shared__ uint32_t s_nrows;
+  __shared__ uint32_t s_hist[kWarps][33];
 
   const uint32_t ta = blockIdx.x;
   const uint32_t t = ta / p.A, a = ta % p.A;
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_trial(EncParams p) {
         uint32_t i = base + lane_id() + 32u * q;
         z[q] = (i - base) < m ? zigzag(e[i] - (i ? e[i - 1] : carry)) : 0u;
       }
-      BlockChoice c = choose_block(z, m);
+      BlockChoice c = choose_block(z, m, s_hist[warp_id()]);
       if (lane_id() == 0) {
         if (mode) cost_p += 4u + c.bytes;
         else cost_i += 4u + c.bytes;
@@ -186,231 +187,286 @@ __global__ void __launch_bounds__(kThreads) k_trial(EncParams p) {
 }
 
 // ----------------------------------------------------------------------------
-// k_encode: one CTA per row item k = (t, a, r), ticket order.
+// k_encode: one warp per row item k = (t, a, r), items taken one at a time
+// from an atomic ticket so that every item a warp waits on (look-backs over
+// earlier items) was handed out earlier. No CTA-wide barrier.
 // ----------------------------------------------------------------------------
-struct EncSmem {
-  uint32_t* e;      // compacted residuals [W]
-  uint32_t* z;      // ZigZag deltas [W]
-  uint32_t* coded;  // coded mask words [nw]
-  uint32_t* aux;    // literal prefix scratch [nw]
-  uint32_t* bhdr;   // block headers [nbmax]
-  uint32_t* boff;   // block body bytes -> offsets [nbmax]
-  uint32_t* xhigh;  // per-warp exception high parts [kWarps][128]
-  uint8_t* xpos;    // per-warp exception positions [kWarps][128]
-  uint32_t* stage;  // staged row chunk [row_bound/4]
+
+// Per-warp shared memory (byte offsets): ZigZag values of the row, coded mask
+// words, per-block {header, body byte offset}, width histogram, and the body
+// of the block being packed.
+struct EncWarpLayout {
+  uint32_t z, coded, meta, hist, pbuf, bytes;
 };
 
-__host__ __device__ inline size_t enc_smem_bytes(uint32_t W) {
-  uint32_t nw = ceil_div_u32(W, 32), nbmax = ceil_div_u32(W, kBlockN);
-  size_t words = 2ull * W + 2ull * nw + 2ull * nbmax + kWarps * 128ull + kWarps * 32ull +
-                 row_bound_bytes(W) / 4u;
-  return words * 4u;
+__host__ __device__ inline EncWarpLayout enc_warp_layout(uint32_t W) {
+  const uint32_t nbmax = ceil_div_u32(W, kBlockN), nw = ceil_div_u32(W, 32);
+  auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
+  EncWarpLayout L;
+  L.z = 0;
+  L.coded = a16(4u * W);
+  L.meta = a16(L.coded + 4u * nw);
+  L.hist = a16(L.meta + 8u * nbmax);
+  L.pbuf = a16(L.hist + 4u * 36u);
+  L.bytes = a16(L.pbuf + 4u * 192u);  // a packed block body never exceeds 162 words
+  return L;
 }
 
-__device__ inline EncSmem enc_smem_carve(uint32_t* base, uint32_t W) {
-  uint32_t nw = ceil_div_u32(W, 32), nbmax = ceil_div_u32(W, kBlockN);
-  EncSmem S;
-  S.e = base; base += W;
-  S.z = base; base += W;
-  S.coded = base; base += nw;
-  S.aux = base; base += nw;
-  S.bhdr = base; base += nbmax;
-  S.boff = base; base += nbmax;
-  S.xhigh = base; base += kWarps * 128;
-  S.xpos = reinterpret_cast<uint8_t*>(base); base += kWarps * 32;
-  S.stage = base;
-  return S;
+__device__ __forceinline__ uint32_t mask_class(uint32_t c, uint32_t valid) {
+  return c == 0u ? 0u : (c == valid ? 1u : 2u);
 }
 
-// Warp-wide funnel packing of nbits-wide values src[0..n) into dst words
-// (bit stream, least significant bit first).
-__device__ __forceinline__ void pack_bits(const uint32_t* src, uint32_t n, uint32_t nbits, uint32_t mask,
-                                          uint32_t* dst) {
-  const uint32_t nwords = (n * nbits + 31u) >> 5;
-  for (uint32_t wi = lane_id(); wi < nwords; wi += 32) {
-    const uint32_t bit0 = wi * 32u;
-    const uint32_t i0 = bit0 / nbits;
-    const uint32_t i1 = min(n - 1u, (bit0 + 31u) / nbits);
-    uint32_t word = 0;
-    for (uint32_t i = i0; i <= i1; i++) {
-      const uint32_t v = src[i] & mask;
-      const int32_t sh = (int32_t)(i * nbits) - (int32_t)bit0;
-      word |= sh >= 0 ? (v << sh) : (v >> (uint32_t)(-sh));
-    }
-    dst[wi] = word;
-  }
-}
+struct EncWarp {
+  uint32_t* zbuf;
+  uint32_t* coded;
+  uint8_t* coded_b;
+  uint2* meta;
+  uint32_t* hist;
+  uint32_t* pbuf;
+};
 
-__global__ void __launch_bounds__(kThreads) k_encode(EncParams p) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_tmp[kWarps + 1];
-  __shared__ uint32_t s_item, s_carry, s_ok;
-  __shared__ unsigned long long s_off;
-
-  if (threadIdx.x == 0) s_item = atomicAdd(p.ticket, 1u);
-  __syncthreads();
-  const uint32_t k = s_item;
-  const uint32_t H = p.H, W = p.W, A = p.A, nw = p.nw;
+// One row item, samples of S bytes (compile-time, so each warp runs one
+// compact path).
+__device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k, const EncWarp& w) {
+  const uint32_t S = p.attrs[(k / p.H) % p.A].s;
+  const uint32_t lane = lane_id();
+  const uint32_t H = p.H, W = p.W, A = p.A, nw = p.nw, ncls = p.ncls;
+  const uint32_t niter = ceil_div_u32(W, 256u);
+  const uint32_t below = (1u << lane) - 1u;
+  uint32_t* zbuf = w.zbuf;
+  uint32_t* coded = w.coded;
   const uint32_t r = k % H, ta = k / H, a = ta % A, t = ta / A;
   const uint32_t sec_start = ta * H;  // first item of this attribute-scan
   const AttrDev at = p.attrs[a];
   AttrDev pat = at;
-  if (t == 0) { pat.P = 1; pat.qmax = 0xffffffffu; }
+  if (t == 0) { pat.P = 1; pat.qmax = 0xffffffffu; }  // the stored previous scan is already quantized
   const uint32_t mode = p.modes[ta];
-  const size_t rowb = (size_t)W * at.s;
-  EncSmem S = enc_smem_carve(smem, W);
-
-  // 1. quantize, mask, compaction, residual (Sec. III-B, III-C, III-D)
-  RowLoad L{p.cur[ta] + r * rowb, mode ? p.prev[ta] + r * rowb : nullptr, at, pat, W, nw};
+  const size_t rowb = (size_t)W * S;
+  const uint8_t* cur = p.cur[ta] + r * rowb;
+  const uint8_t* prv = mode ? p.prev[ta] + r * rowb : nullptr;
   uint8_t* st_row = (t + 1 == p.T) ? p.state_next[a] + r * rowb : nullptr;
-  const uint32_t n = load_compact_row(L, mode == 0, mode == 1, mode == 1, S.e, S.e, S.coded, st_row, s_tmp);
-  const uint32_t e_last = n ? S.e[n - 1] : 0u;
+  const bool vec_cur = vec_ok(cur, S), vec_prv = prv && vec_ok(prv, S), vec_st = st_row && vec_ok(st_row, S);
 
-  // 2. delta carry: the residual preceding this row in the flat vector of the
-  //    attribute-scan (Sec. III-C), by a "last valid" look-back over rows.
-  if (threadIdx.x < 32) {
-    uint32_t carry = 0;
-    bool ok = true;
-    if (r == 0) {
-      if (threadIdx.x == 0) st_publish(p.st_carry + k, kStInc | (1ull << 32) | e_last);
-    } else {
-      if (threadIdx.x == 0) st_publish(p.st_carry + k, kStAgg | ((unsigned long long)(n ? 1 : 0) << 32) | e_last);
-      ok = lookback_last(p.st_carry, k, sec_start, carry);
-      if (threadIdx.x == 0)
-        st_publish(p.st_carry + k, ok ? (kStInc | (1ull << 32) | (n ? e_last : carry)) : kStErr);
+  for (uint32_t j = lane; j < nw; j += 32) coded[j] = 0u;
+  __syncwarp();
+
+  // ---- pass A: quantize (Sec. III-B), zero mask (Sec. III-C), mask XOR
+  //      (Sec. III-D), compaction, residual, delta, ZigZag (Eq. 1)
+  uint32_t n = 0;          // nonzero samples so far (uniform)
+  uint32_t last_e = 0;     // last residual so far (uniform, valid when n > 0)
+  uint32_t e_first = 0;    // the row's first residual (uniform)
+  for (uint32_t it = 0; it < niter; it++) {
+    const uint32_t x0 = 256u * it + 8u * lane;
+    const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
+    uint32_t v[8], pv[8];
+    load8<false>(cur, S, x0, nv, vec_cur, v);
+    if (prv) load8<false>(prv, S, x0, nv, vec_prv, pv);
+    uint32_t e[8];
+    uint32_t mb = 0, pm = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const uint32_t q = quantize(v[i], at);
+      v[i] = q;
+      const uint32_t pq = prv ? quantize(pv[i], pat) : 0u;
+      mb |= (uint32_t)((uint32_t)i < nv && q == 0u) << i;
+      pm |= (uint32_t)((uint32_t)i < nv && pq == 0u) << i;
+      e[i] = q - pq;  // I: q (pq = 0); P: q - pq, modulo 2^32
     }
-    if (threadIdx.x == 0) { s_carry = carry; s_ok = ok; }
+    if (st_row && nv) store8(st_row, S, x0, nv, vec_st, v);
+    if (nv) w.coded_b[x0 >> 3] = (uint8_t)(mode ? (mb ^ pm) : mb);
+    const uint32_t nz = ~mb & ((1u << nv) - 1u);
+    const uint32_t c = __popc(nz);
+    uint32_t tot;
+    const uint32_t k0 = n + warp_excl_scan(c, tot);
+    // the residual before this lane's first nonzero: the last one of the
+    // nearest lower lane that has any, else the last one so far
+    uint32_t my_last = 0, my_first = 0;
+#pragma unroll
+    for (int i = 7; i >= 0; i--)
+      if ((nz >> i) & 1u) my_first = e[i];
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+      if ((nz >> i) & 1u) my_last = e[i];
+    const uint32_t has = __ballot_sync(0xffffffffu, c != 0u);
+    const uint32_t lower = has & below;
+    const uint32_t src = lower ? 31u - __clz(lower) : 0u;
+    const uint32_t from_lane = __shfl_sync(0xffffffffu, my_last, src);
+    uint32_t pe = lower ? from_lane : last_e;  // (n == 0: placeholder, fixed after the carry)
+    uint32_t kk = k0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      if ((nz >> i) & 1u) {
+        zbuf[kk++] = zigzag(e[i] - pe);
+        pe = e[i];
+      }
+    }
+    if (has) {
+      const uint32_t hi = 31u - __clz(has), lo = __ffs(has) - 1u;
+      const uint32_t lastv = __shfl_sync(0xffffffffu, my_last, hi);
+      const uint32_t firstv = __shfl_sync(0xffffffffu, my_first, lo);
+      if (n == 0) e_first = firstv;
+      last_e = lastv;
+    }
+    n += tot;
   }
-  __syncthreads();
-  if (!s_ok) {
-    if (threadIdx.x == 0) {
+  // ---- delta carry: the residual preceding this row in the attribute-scan's
+  //      flat vector (Sec. III-C), by a "last valid" look-back over rows
+  uint32_t carry = 0;
+  bool ok = true;
+  if (r == 0) {
+    if (lane == 0) st_publish(p.st_carry + k, kStInc | (1ull << 32) | (n ? last_e : 0u));
+  } else {
+    if (lane == 0) st_publish(p.st_carry + k, kStAgg | ((unsigned long long)(n ? 1 : 0) << 32) | last_e);
+    ok = lookback_last(p.st_carry, k, sec_start, carry);
+    if (lane == 0) st_publish(p.st_carry + k, ok ? (kStInc | (1ull << 32) | (n ? last_e : carry)) : kStErr);
+  }
+  if (!ok) {
+    if (lane == 0) {
       atomicOr(p.err, kErrTimeout);
       st_publish(p.st_bytes + k, kStErr);
     }
     return;
   }
-  const uint32_t carry = s_carry;
+  if (n && lane == 0) zbuf[0] = zigzag(e_first - carry);
+  __syncwarp();
 
-  // 3. delta over the flat vector + ZigZag (Eq. 1)
-  for (uint32_t i = threadIdx.x; i < n; i += kThreads) S.z[i] = zigzag(S.e[i] - (i ? S.e[i - 1] : carry));
-
-  // 4. mask part: 2-bit class per word, literals in order
-  const uint32_t ncls = p.ncls;
-  for (uint32_t j = threadIdx.x; j < nw; j += kThreads) {
-    const uint32_t c = S.coded[j];
+  // ---- mask part size: literal words
+  uint32_t nlit = 0;
+  for (uint32_t jb = 0; jb < nw; jb += 32) {
+    const uint32_t j = jb + lane;
     const uint32_t valid = (j + 1 < nw || (W & 31u) == 0) ? 0xffffffffu : ((1u << (W & 31u)) - 1u);
-    S.aux[j] = (c != 0u && c != valid) ? 1u : 0u;
-  }
-  __syncthreads();
-  const uint32_t nlit = block_excl_scan(S.aux, nw, s_tmp);
-  for (uint32_t i = threadIdx.x; i < ncls; i += kThreads) {
-    uint32_t word = 0;
-    for (uint32_t j = 16u * i; j < min(nw, 16u * i + 16u); j++) {
-      const uint32_t c = S.coded[j];
-      const uint32_t valid = (j + 1 < nw || (W & 31u) == 0) ? 0xffffffffu : ((1u << (W & 31u)) - 1u);
-      const uint32_t cls = c == 0u ? 0u : (c == valid ? 1u : 2u);
-      word |= cls << (2u * (j - 16u * i));
-    }
-    S.stage[i] = word;
-  }
-  for (uint32_t j = threadIdx.x; j < nw; j += kThreads) {
-    const uint32_t c = S.coded[j];
-    const uint32_t valid = (j + 1 < nw || (W & 31u) == 0) ? 0xffffffffu : ((1u << (W & 31u)) - 1u);
-    if (c != 0u && c != valid) S.stage[ncls + S.aux[j]] = c;
+    const bool lit = j < nw && mask_class(coded[j], valid) == 2u;
+    nlit += __popc(__ballot_sync(0xffffffffu, lit));
   }
 
-  // 5. block widths (Sec. II): warp per block
+  // ---- block widths (Sec. II), body offsets
   const uint32_t nb = ceil_div_u32(n, kBlockN);
-  for (uint32_t blk = warp_id(); blk < nb; blk += kWarps) {
+  uint32_t body = 0;
+  for (uint32_t blk = 0; blk < nb; blk++) {
     const uint32_t base = blk * kBlockN, m = min(kBlockN, n - base);
     uint32_t z[4];
-    load_block(S.z + base, m, z);
-    BlockChoice c = choose_block(z, m);
-    if (lane_id() == 0) {
-      S.bhdr[blk] = c.b | (c.e << 8) | (c.hb << 16);
-      S.boff[blk] = c.bytes;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const uint32_t i = lane + 32u * q;
+      z[q] = i < m ? zbuf[base + i] : 0u;
     }
+    const BlockChoice bc = choose_block(z, m, w.hist);
+    if (lane == 0) w.meta[blk] = make_uint2(bc.b | (bc.e << 8) | (bc.hb << 16), body);
+    body += bc.bytes;
   }
-  __syncthreads();
-  const uint32_t body_total = block_excl_scan(S.boff, nb, s_tmp);
+  __syncwarp();
   const uint32_t head_words = ncls + nlit + nb;
-  const uint32_t chunk = 4u * head_words + body_total;
+  const uint32_t chunk = 4u * head_words + body;
 
-  // 6. publish this row's byte aggregate, then pack while predecessors finish
-  if (threadIdx.x == 0) {
-    if (k == sec_start && ta == 0) st_publish(p.st_bytes + k, kStInc | chunk);
-    else st_publish(p.st_bytes + k, kStAgg | chunk);
+  // ---- byte offset by decoupled look-back over all rows of the call
+  unsigned long long excl = 0;
+  if (k == 0) {
+    if (lane == 0) st_publish(p.st_bytes + k, kStInc | chunk);
+  } else {
+    if (lane == 0) st_publish(p.st_bytes + k, kStAgg | chunk);
+    ok = lookback_sum(p.st_bytes, k, 0, excl);
+    if (lane == 0) st_publish(p.st_bytes + k, ok ? (kStInc | (excl + chunk)) : kStErr);
   }
-  for (uint32_t blk = warp_id(); blk < nb; blk += kWarps) {
-    const uint32_t base = blk * kBlockN, m = min(kBlockN, n - base);
-    const uint32_t h = S.bhdr[blk];
-    const uint32_t b = h & 0xffu, ex = (h >> 8) & 0xffu, hb = (h >> 16) & 0xffu;
-    if (lane_id() == 0) S.stage[ncls + nlit + blk] = h;
-    uint32_t* body = S.stage + head_words + S.boff[blk] / 4u;
-    const uint32_t* zb = S.z + base;
-    pack_bits(zb, m, b, b >= 32u ? 0xffffffffu : ((1u << b) - 1u), body);
-    if (ex) {
-      uint32_t* xh = S.xhigh + warp_id() * 128u;
-      uint8_t* xp = S.xpos + warp_id() * 128u;
-      uint32_t xi = 0;
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        const uint32_t i = lane_id() + 32u * q;
-        const uint32_t v = i < m ? zb[i] : 0u;
-        const bool isx = i < m && bit_width(v) > b;
-        const uint32_t bal = __ballot_sync(0xffffffffu, isx);
-        if (isx) {
-          const uint32_t slot = xi + __popc(bal & ((1u << lane_id()) - 1u));
-          xp[slot] = (uint8_t)i;
-          xh[slot] = v >> b;
-        }
-        xi += __popc(bal);
-      }
-      __syncwarp();
-      const uint32_t low_words = (m * b + 31u) >> 5;
-      const uint32_t pos_words = (ex + 3u) >> 2;
-      for (uint32_t wi = lane_id(); wi < pos_words; wi += 32) {
-        uint32_t word = 0;
-#pragma unroll
-        for (uint32_t q = 0; q < 4; q++) {
-          const uint32_t idx = 4u * wi + q;
-          if (idx < ex) word |= (uint32_t)xp[idx] << (8u * q);
-        }
-        body[low_words + wi] = word;
-      }
-      pack_bits(xh, ex, hb, hb >= 32u ? 0xffffffffu : ((1u << hb) - 1u), body + low_words + pos_words);
-      __syncwarp();
-    }
-  }
-
-  // 7. byte offset by decoupled look-back over all rows of the call
-  if (threadIdx.x < 32) {
-    unsigned long long excl = 0;
-    bool ok = true;
-    if (!(k == 0)) {
-      ok = lookback_sum(p.st_bytes, k, 0, excl);
-      if (threadIdx.x == 0) st_publish(p.st_bytes + k, ok ? (kStInc | (excl + chunk)) : kStErr);
-    }
-    if (threadIdx.x == 0) { s_off = excl; s_ok = ok; }
-  }
-  __syncthreads();
-  if (!s_ok) {
-    if (threadIdx.x == 0) atomicOr(p.err, kErrTimeout);
+  if (!ok) {
+    if (lane == 0) atomicOr(p.err, kErrTimeout);
     return;
   }
-  const unsigned long long off = p.shdr + (unsigned long long)(t + 1) * p.fhdr +
-                                 (unsigned long long)(ta + 1) * 8ull * H + s_off;
-  if (threadIdx.x == 0) {
+  if (lane == 0) {
     p.row_bytes[k] = chunk;
     p.row_nnz[k] = n;
     p.row_carry[k] = carry;
   }
-  // 8. copy the staged chunk out (4-byte aligned)
-  if (off + chunk <= p.cap) {
-    uint32_t* dst = reinterpret_cast<uint32_t*>(p.out + off);
-    for (uint32_t i = threadIdx.x; i < chunk / 4u; i += kThreads) dst[i] = S.stage[i];
-  } else if (threadIdx.x == 0) {
-    atomicOr(p.err, kErrCapacity);
+  const unsigned long long off = p.shdr + (unsigned long long)(t + 1) * p.fhdr +
+                                 (unsigned long long)(ta + 1) * 8ull * H + excl;
+  if (off + chunk > p.cap) {
+    if (lane == 0) atomicOr(p.err, kErrCapacity);
+    return;
+  }
+  uint32_t* dst = reinterpret_cast<uint32_t*>(p.out + off);
+
+  // ---- mask part: 2-bit class per word (16 per class word), literals
+  uint32_t litbase = 0;
+  for (uint32_t jb = 0; jb < nw; jb += 32) {
+    const uint32_t j = jb + lane;
+    const uint32_t valid = (j + 1 < nw || (W & 31u) == 0) ? 0xffffffffu : ((1u << (W & 31u)) - 1u);
+    const uint32_t c = j < nw ? coded[j] : 0u;
+    const uint32_t cls = j < nw ? mask_class(c, valid) : 0u;
+    uint32_t cw = cls << (2u * (lane & 15u));
+#pragma unroll
+    for (int o = 1; o < 16; o <<= 1) cw |= __shfl_xor_sync(0xffffffffu, cw, o);
+    const uint32_t ci = (jb >> 4) + (lane >> 4);
+    if ((lane & 15u) == 0 && ci < ncls) dst[ci] = cw;
+    const uint32_t litm = __ballot_sync(0xffffffffu, cls == 2u);
+    if (cls == 2u) dst[ncls + litbase + __popc(litm & below)] = c;
+    litbase += __popc(litm);
+  }
+  // ---- block headers and bodies
+  for (uint32_t blk = lane; blk < nb; blk += 32) dst[ncls + nlit + blk] = w.meta[blk].x;
+  for (uint32_t blk = 0; blk < nb; blk++) {
+    const uint32_t base = blk * kBlockN, m = min(kBlockN, n - base);
+    const uint2 md = w.meta[blk];
+    const uint32_t b = md.x & 0xffu, ex = (md.x >> 8) & 0xffu, hb = (md.x >> 16) & 0xffu;
+    const uint32_t low_words = (m * b + 31u) >> 5;
+    const uint32_t high0 = low_words + ((ex + 3u) >> 2);  // first word of the high parts
+    const uint32_t body_words = block_body_bytes(m, b, ex, b + hb) / 4u;
+    uint32_t* pb = w.pbuf;
+    for (uint32_t i = lane; i < body_words; i += 32) pb[i] = 0u;
+    __syncwarp();
+    // value-centric packing into shared memory: low b bits of every value at
+    // bit i*b; exceptions: position byte and high part (hb bits) by rank
+    const uint32_t bmask = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
+    const uint32_t* zb = zbuf + base;
+    uint32_t xi = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const uint32_t i = lane + 32u * q;
+      const bool valid = i < m;
+      const uint32_t vz = valid ? zb[i] : 0u;
+      if (valid && b) {
+        const uint32_t bit = i * b, wi = bit >> 5, sh = bit & 31u, lo = vz & bmask;
+        atomicOr(pb + wi, lo << sh);
+        if (sh + b > 32u) atomicOr(pb + wi + 1u, lo >> (32u - sh));
+      }
+      if (ex) {
+        const bool isx = valid && bit_width(vz) > b;
+        const uint32_t bal = __ballot_sync(0xffffffffu, isx);
+        if (isx) {
+          const uint32_t slot = xi + __popc(bal & below);
+          atomicOr(pb + low_words + (slot >> 2), i << (8u * (slot & 3u)));
+          const uint32_t hv = vz >> b, hbit = slot * hb, hw = high0 + (hbit >> 5), hs = hbit & 31u;
+          atomicOr(pb + hw, hv << hs);
+          if (hs + hb > 32u) atomicOr(pb + hw + 1u, hv >> (32u - hs));
+        }
+        xi += __popc(bal);
+      }
+    }
+    __syncwarp();
+    uint32_t* bd = dst + head_words + md.y / 4u;
+    for (uint32_t i = lane; i < body_words; i += 32) bd[i] = pb[i];
+    __syncwarp();
+  }
+  __syncwarp();
+}
+
+template <int WPC>
+__global__ void __launch_bounds__(WPC * 32) k_encode(EncParams p) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t lane = lane_id();
+  const EncWarpLayout lay = enc_warp_layout(p.W);
+  uint8_t* wb = reinterpret_cast<uint8_t*>(smem) + warp_id() * lay.bytes;
+  EncWarp w;
+  w.zbuf = reinterpret_cast<uint32_t*>(wb + lay.z);
+  w.coded = reinterpret_cast<uint32_t*>(wb + lay.coded);
+  w.coded_b = wb + lay.coded;
+  w.meta = reinterpret_cast<uint2*>(wb + lay.meta);
+  w.hist = reinterpret_cast<uint32_t*>(wb + lay.hist);
+  w.pbuf = reinterpret_cast<uint32_t*>(wb + lay.pbuf);
+  while (true) {
+    uint32_t k = 0;
+    if (lane == 0) k = atomicAdd(p.ticket, 1u);
+    k = __shfl_sync(0xffffffffu, k, 0);
+    if (k >= p.n_items) break;
+    encode_item(p, k, w);
   }
 }
 
@@ -483,15 +539,33 @@ __global__ void __launch_bounds__(kThreads) k_finalize(EncParams p) {
   }
 }
 
-size_t enc_smem_bytes_host(uint32_t W) { return enc_smem_bytes(W); }
+size_t enc_smem_bytes_host(uint32_t W) { return enc_warp_layout(W).bytes; }
 size_t trial_smem_bytes_host(uint32_t W) { return 8ull * W; }
+
+template <int WPC>
+static cudaError_t launch_encode_rows(const EncParams& p, cudaStream_t st) {
+  const EncWarpLayout L = enc_warp_layout(p.W);
+  if ((L.coded | L.meta | L.hist | L.pbuf | L.bytes) & 15u)
+    return cudaErrorInvalidValue;  // every per-warp region starts 16-byte aligned
+  const size_t smem = (size_t)WPC * L.bytes;
+  cudaError_t e = cudaFuncSetAttribute(k_encode<WPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_encode<WPC>, WPC * 32, smem)) != cudaSuccess)
+    return e;
+  // enough warps to fill the GPU; warps beyond the work find the ticket spent
+  const uint32_t want = ceil_div_u32(p.n_items, WPC);
+  const uint32_t grid = max(1u, min(want, (uint32_t)(max(per_sm, 1) * sms)));
+  k_encode<WPC><<<grid, WPC * 32, smem, st>>>(p);
+  return cudaGetLastError();
+}
 
 int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const size_t s_enc = enc_smem_bytes(p.W), s_trial = 8ull * p.W, s_fin = 4ull * p.H;
-  cudaError_t e = cudaFuncSetAttribute(k_encode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_enc);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_trial);
+  const size_t s_trial = 8ull * p.W, s_fin = 4ull * p.H;
+  cudaError_t e = cudaFuncSetAttribute(k_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_trial);
   if (e != cudaSuccess) return (int)e;
   auto mark = [&](int i) {
     if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[i]), st);
@@ -499,7 +573,12 @@ int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   mark(0);
   k_trial<<<p.T * p.A, kThreads, s_trial, st>>>(p);
   mark(1);
-  k_encode<<<p.n_items, kThreads, s_enc, st>>>(p);
+  // warps per CTA from the per-warp shared memory (row-sized ZigZag buffer)
+  const size_t per_warp = enc_warp_layout(p.W).bytes;
+  if (4 * per_warp <= 100 * 1024) e = launch_encode_rows<4>(p, st);
+  else if (2 * per_warp <= 100 * 1024) e = launch_encode_rows<2>(p, st);
+  else e = launch_encode_rows<1>(p, st);
+  if (e != cudaSuccess) return (int)e;
   mark(2);
   k_finalize<<<p.T, kThreads, s_fin, st>>>(p);
   mark(3);
