@@ -254,10 +254,13 @@ jiffy_status jiffy_encode_seq(jiffy_stream* s, uint32_t n_scans, const void* con
   const size_t o_cur = c.take(8ull * T * A), o_prev = c.take(8ull * T * A), o_next = c.take(8ull * A);
   const size_t o_modes = c.take(4ull * T * A);
   const size_t o_rb = c.take(4ull * items), o_rn = c.take(4ull * items), o_rc = c.take(4ull * items);
+  const size_t o_secb = c.take(8ull * T * A), o_secn = c.take(4ull * T * A);
   const size_t o_zero = c.take(0);
-  const size_t o_stc = c.take(8ull * items), o_stb = c.take(8ull * items), o_tick = c.take(8);
+  const size_t o_stc = c.take(8ull * items), o_tick = c.take(8);
   const size_t zero_bytes = c.off - o_zero;
   const size_t o_foff = c.take(8ull * (T + 1));
+  const uint32_t slot_bytes = (jiffy::row_bound_bytes(W) + 15u) & ~15u;
+  const size_t o_slots = c.take((size_t)slot_bytes * items);
   const size_t dev_bytes = c.off;
   // pinned host layout: pointer arrays (upload), then results (download)
   const size_t h_ptrs = 8ull * (2ull * T * A + A);
@@ -306,7 +309,10 @@ jiffy_status jiffy_encode_seq(jiffy_stream* s, uint32_t n_scans, const void* con
   p.row_nnz = reinterpret_cast<uint32_t*>(d + o_rn);
   p.row_carry = reinterpret_cast<uint32_t*>(d + o_rc);
   p.st_carry = reinterpret_cast<unsigned long long*>(d + o_stc);
-  p.st_bytes = reinterpret_cast<unsigned long long*>(d + o_stb);
+  p.slots = d + o_slots;
+  p.slot_bytes = slot_bytes;
+  p.sec_bytes = reinterpret_cast<unsigned long long*>(d + o_secb);
+  p.sec_nnz = reinterpret_cast<uint32_t*>(d + o_secn);
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
   p.err = reinterpret_cast<uint32_t*>(d + o_tick + 4);
   p.frame_off = reinterpret_cast<unsigned long long*>(d + o_foff);

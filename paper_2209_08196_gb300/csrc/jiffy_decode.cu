@@ -16,13 +16,15 @@
 //   pass 1   own mask byte from its class code / literal, XOR with the
 //            previous scan's bits for P (Sec. III-D); nonzero counts
 //   lanes    block headers validated and sized (Sec. II, PFOR blocks)
-//   unpack   block by block, lane per value: funnel bit extract, exception
-//            high parts patched in shared memory, inverse ZigZag (Eq. 1),
-//            warp scans from the row's carry -> residuals (inverse delta)
+//   then, per 256-pixel step, interleaved:
+//   unpack   the blocks the step needs, lane l owning the 4 consecutive
+//            values 4l..4l+3: funnel bit extract, exception high parts via a
+//            patch buffer, inverse ZigZag (Eq. 1), one warp scan per block
+//            from the row's carry (inverse delta) into a ring of residuals
 //   scatter  warp scan of counts -> compacted index of each own pixel; +
 //            previous pixel for P; x precision (Sec. III-A); vector stores
-// The chunk is read through L1 (__ldg); the row's residuals (compacted order)
-// and mask bytes live in per-warp shared memory.
+// The row chunk is staged in per-warp shared memory with one round of
+// independent loads; residuals pass through a small ring buffer.
 #include "jiffy_device.cuh"
 #include "jiffy_kernels.h"
 
@@ -44,23 +46,29 @@ __device__ __forceinline__ uint32_t literal_bits(uint32_t cwd) { return (cwd >> 
 
 }  // namespace
 
-// Per-warp shared memory (byte offsets): the row's residuals in compacted
-// order (one u32 per pixel at most), then its mask bytes.
+// Per-warp shared memory (byte offsets): the staged row chunk, a ring of
+// 512 residuals (unpacked ahead of the scatter), a 128-word exception patch
+// buffer and the row's mask bytes.
+constexpr uint32_t kRing = 512;
+
 struct DecWarpLayout {
-  uint32_t ebuf, mbytes, bytes;
+  uint32_t stage, ring, patch, mbytes, bytes;
 };
 
 __host__ __device__ inline DecWarpLayout dec_warp_layout(uint32_t W) {
   DecWarpLayout L;
-  L.ebuf = 0;
-  L.mbytes = 4u * W;
+  L.stage = 0;
+  L.ring = (row_bound_bytes(W) + 15u) & ~15u;
+  L.patch = L.ring + 4u * kRing;
+  L.mbytes = L.patch + 4u * kBlockN;
   L.bytes = (L.mbytes + ceil_div_u32(W, 8u) + 15u) & ~15u;
   return L;
 }
 
 // One row item, samples of S bytes (compile-time, so each warp runs one
 // compact path).
-__device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k, uint32_t* ebuf, uint8_t* mbytes) {
+__device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k, uint32_t* stage, uint32_t* ring,
+                                            uint32_t* patch, uint8_t* mbytes) {
   const uint32_t S = p.attrs[(k / p.H) % p.A].s;
   const uint32_t lane = lane_id();
   const uint32_t H = p.H, W = p.W, A = p.A, nw = p.nw, ncls = p.ncls;
@@ -145,13 +153,26 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   chunk_off = __shfl_sync(0xffffffffu, chunk_off, 0);
   if (mode == 1u) __threadfence();  // every lane orders its reads of the previous row after the flag
 
-  const uint32_t* chunk = reinterpret_cast<const uint32_t*>(p.in + chunk_off);
   bool bad = status != 0;
-  if (!bad) prefetch_l1(chunk, clen);
+  // ---- stage the chunk in shared memory: one round of independent loads
+  if (!bad) {
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(p.in + chunk_off);
+    const uint32_t cw = clen / 4u;
+    for (uint32_t i = lane; i < cw; i += 128u) {
+      uint32_t v[4];
+#pragma unroll
+      for (uint32_t q = 0; q < 4; q++) v[q] = i + 32u * q < cw ? __ldg(src + i + 32u * q) : 0u;
+#pragma unroll
+      for (uint32_t q = 0; q < 4; q++)
+        if (i + 32u * q < cw) stage[i + 32u * q] = v[q];
+    }
+  }
+  __syncwarp();
+  const uint32_t* chunk = stage;
   // ---- class words: class 3 and bits past nw are invalid; literal prefix
   uint32_t cw = 0, lit = 0;
   if (!bad && lane < ncls) {
-    cw = __ldg(chunk + lane);
+    cw = chunk[lane];
     uint32_t used = 0xffffffffu;
     const uint32_t nslots = min(16u, nw - 16u * lane);
     if (nslots < 16u) used = (1u << (2u * nslots)) - 1u;
@@ -168,7 +189,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
     const uint32_t lpj = __shfl_sync(0xffffffffu, litpre, (j >> 4) & 31u);
     if (!bad && (W & 31u) && ((cwj >> (2u * (j & 15u))) & 3u) == 2u) {
       const uint32_t li = lpj + __popc(literal_bits(cwj) & ((1u << (2u * (j & 15u))) - 1u));
-      if (__ldg(chunk + ncls + li) & ~valid_word_bits(W, nw, j)) bad = true;
+      if (chunk[ncls + li] & ~valid_word_bits(W, nw, j)) bad = true;
     }
   }
 
@@ -190,7 +211,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
         const uint32_t sl = 2u * (j & 15u), cls = (cwj >> sl) & 3u;
         uint32_t X = 0;
         if (cls == 1u) X = valid_word_bits(W, nw, j);
-        else if (cls == 2u) X = __ldg(chunk + ncls + lpj + __popc(literal_bits(cwj) & ((1u << sl) - 1u)));
+        else if (cls == 2u) X = chunk[ncls + lpj + __popc(literal_bits(cwj) & ((1u << sl) - 1u))];
         const uint32_t nv = min(8u, W - x0), vm = (1u << nv) - 1u;
         uint32_t mb = (X >> (x0 & 31u)) & 0xffu;
         if (mode == 1u) {
@@ -221,7 +242,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
     for (uint32_t q = 0; q < 4; q++) {
       const uint32_t blk = 4u * lane + q;
       if (!bad && blk < nb) {
-        const uint32_t h = __ldg(chunk + hdr0 + blk);
+        const uint32_t h = chunk[hdr0 + blk];
         const uint32_t b = h & 0xffu, e = (h >> 8) & 0xffu, hb = (h >> 16) & 0xffu;
         const uint32_t m = min(kBlockN, n - blk * kBlockN);
         if ((h >> 24) || b > 32u || hb > 32u || b + hb > 32u || e > m || ((e == 0u) != (hb == 0u))) lbad = true;
@@ -231,83 +252,81 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
     bad = __any_sync(0xffffffffu, bad || lbad);
     if (!bad && 4u * (hdr0 + nb + warp_sum(mysum)) != clen) bad = true;
   }
+  __syncwarp();
 
-  // ---- unpack block by block (lane l: values l, l+32, l+64, l+96):
-  //      funnel bit extract, exceptions patched in shared memory, inverse
-  //      ZigZag (Eq. 1) and the inverse delta from the row's carry
-  if (!bad) {
-    uint32_t bodyw = hdr0 + nb;  // word offset of the current block's body
-    uint32_t erun = carry;
-    bool xbad = false;
-    const uint32_t last_word = clen / 4u - 1u;
-    for (uint32_t blk = 0; blk < nb; blk++) {
-      const uint32_t h = __ldg(chunk + hdr0 + blk);
-      const uint32_t b = h & 0xffu, e = (h >> 8) & 0xffu, hb = (h >> 16) & 0xffu;
-      const uint32_t base = blk * kBlockN, m = min(kBlockN, n - base);
-      const uint32_t bmask = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
-      const uint32_t low_words = (m * b + 31u) >> 5;
-      if (b) {
-#pragma unroll
-        for (uint32_t q = 0; q < 4; q++) {
-          const uint32_t i = lane + 32u * q;
-          if (i < m) {
-            const uint32_t bit = i * b, wi = bodyw + (bit >> 5);
-            const uint32_t lo = __ldg(chunk + wi), hi = __ldg(chunk + min(wi + 1u, last_word));
-            ebuf[base + i] = __funnelshift_r(lo, hi, bit & 31u) & bmask;
-          }
-        }
-      } else {
-        for (uint32_t i = lane; i < m; i += 32) ebuf[base + i] = 0u;
-      }
-      if (e) {
-        __syncwarp();
-        const uint8_t* pos = reinterpret_cast<const uint8_t*>(chunk + bodyw + low_words);
-        const uint32_t hw = bodyw + low_words + ((e + 3u) >> 2);
-        const uint32_t hmask = hb >= 32u ? 0xffffffffu : ((1u << hb) - 1u);
-        for (uint32_t jx = lane; jx < e; jx += 32) {
-          const uint32_t ps = __ldg(pos + jx);
-          if (ps >= m || (jx > 0 && ps <= __ldg(pos + jx - 1))) {
-            xbad = true;
-          } else {
-            const uint32_t bit = jx * hb, wi = hw + (bit >> 5);
-            const uint32_t lo = __ldg(chunk + wi), hi = __ldg(chunk + min(wi + 1u, last_word));
-            ebuf[base + ps] |= (__funnelshift_r(lo, hi, bit & 31u) & hmask) << b;
-          }
-        }
-      }
-      __syncwarp();
-#pragma unroll
-      for (uint32_t q = 0; q < 4; q++) {
-        const uint32_t i = lane + 32u * q;
-        const uint32_t d = i < m ? unzigzag(ebuf[base + i]) : 0u;
-        uint32_t tot;
-        const uint32_t ex = warp_excl_scan(d, tot);
-        if (i < m) ebuf[base + i] = erun + ex + d;
-        erun += tot;
-      }
-      bodyw += block_body_bytes(m, b, e, b + hb) / 4u;
-    }
-    bad = __any_sync(0xffffffffu, xbad);
-    __syncwarp();
-  }
-
-  // ---- scatter by position: + previous pixel (P), x precision (Sec. III-A)
+  // ---- unpack (block by block, lane l: the 4 consecutive values 4l..4l+3;
+  //      funnel bit extract, exception high parts through the patch buffer,
+  //      inverse ZigZag (Eq. 1), prefix sum from the row's carry = inverse
+  //      delta) interleaved with the scatter by position (+ previous pixel for
+  //      P, x precision, Sec. III-A) through a ring of residuals
   if (!bad) {
     const uint32_t Pq = at.P;
-    uint32_t kbase = 0;
-    for (uint32_t it = 0; it < niter; it++) {
+    const uint32_t last_word = clen / 4u - 1u;
+    uint32_t bodyw = hdr0 + nb;  // word offset of the next block's body
+    uint32_t erun = carry, blk = 0, unpacked = 0, kbase = 0;
+    bool xbad = false;
+    for (uint32_t it = 0; it < niter && !xbad; it++) {
       const uint32_t x0 = 256u * it + 8u * lane;
       const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
       const uint32_t mb = nv ? mbytes[x0 >> 3] : 0xffu;
       uint32_t segn;
       uint32_t kk = kbase + warp_excl_scan(__popc(~mb & 0xffu), segn);
+      while (unpacked < kbase + segn) {
+        const uint32_t h = chunk[hdr0 + blk];
+        const uint32_t b = h & 0xffu, e = (h >> 8) & 0xffu, hb = (h >> 16) & 0xffu;
+        const uint32_t base = blk * kBlockN, m = min(kBlockN, n - base);
+        const uint32_t bmask = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
+        const uint32_t low_words = (m * b + 31u) >> 5;
+        const uint32_t i0 = 4u * lane;
+        uint32_t z[4] = {0u, 0u, 0u, 0u};
+        if (b) {
+#pragma unroll
+          for (uint32_t q = 0; q < 4; q++) {
+            const uint32_t bit = (i0 + q) * b, wi = min(bodyw + (bit >> 5), last_word);
+            const uint32_t lo = chunk[wi], hi = chunk[min(wi + 1u, last_word)];
+            z[q] = i0 + q < m ? (__funnelshift_r(lo, hi, bit & 31u) & bmask) : 0u;
+          }
+        }
+        if (e) {
+          reinterpret_cast<uint4*>(patch)[lane] = make_uint4(0u, 0u, 0u, 0u);
+          __syncwarp();
+          const uint8_t* pos = reinterpret_cast<const uint8_t*>(chunk + bodyw + low_words);
+          const uint32_t hw = bodyw + low_words + ((e + 3u) >> 2);
+          const uint32_t hmask = hb >= 32u ? 0xffffffffu : ((1u << hb) - 1u);
+          for (uint32_t jx = lane; jx < e; jx += 32) {
+            const uint32_t ps = pos[jx];
+            if (ps >= m || (jx > 0 && ps <= pos[jx - 1])) {
+              xbad = true;
+            } else {
+              const uint32_t bit = jx * hb, wi = hw + (bit >> 5);
+              const uint32_t lo = chunk[wi], hi = chunk[min(wi + 1u, last_word)];
+              patch[ps] = (__funnelshift_r(lo, hi, bit & 31u) & hmask) << b;
+            }
+          }
+          __syncwarp();
+          const uint4 pt = reinterpret_cast<const uint4*>(patch)[lane];
+          z[0] |= pt.x; z[1] |= pt.y; z[2] |= pt.z; z[3] |= pt.w;
+        }
+        const uint32_t s0 = unzigzag(z[0]), s1 = s0 + unzigzag(z[1]), s2 = s1 + unzigzag(z[2]),
+                       s3 = s2 + unzigzag(z[3]);
+        uint32_t tot;
+        const uint32_t e0 = erun + warp_excl_scan(s3, tot);
+        reinterpret_cast<uint4*>(ring)[((base + i0) & (kRing - 1u)) >> 2] = make_uint4(e0 + s0, e0 + s1, e0 + s2, e0 + s3);
+        erun += tot;
+        bodyw += block_body_bytes(m, b, e, b + hb) / 4u;
+        unpacked += m;
+        blk++;
+      }
+      xbad = __any_sync(0xffffffffu, xbad);
+      __syncwarp();
+      if (xbad) break;
       uint32_t pv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       if (mode == 1u && nv) load8<true>(prow, S, x0, nv, vec_prev, pv);
       uint32_t out[8];
 #pragma unroll
       for (int i = 0; i < 8; i++) {
         const bool nzb = !((mb >> i) & 1u);
-        const uint32_t e = nzb ? ebuf[kk] : 0u;
+        const uint32_t e = nzb ? ring[kk & (kRing - 1u)] : 0u;
         out[i] = nzb ? e * Pq + pv[i] : 0u;
         kk += nzb ? 1u : 0u;
       }
@@ -316,7 +335,9 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
         if (srow) store8(srow, S, x0, nv, vec_out, out);
       }
       kbase += segn;
+      __syncwarp();
     }
+    bad = xbad;
   }
   if (lane == 0 && bad && status != 2u) atomicOr(p.err, kErrCorrupt);
   __threadfence();
@@ -330,7 +351,9 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
   const uint32_t lane = lane_id();
   const DecWarpLayout lay = dec_warp_layout(p.W);
   uint8_t* wb = reinterpret_cast<uint8_t*>(smem) + warp_id() * lay.bytes;
-  uint32_t* ebuf = reinterpret_cast<uint32_t*>(wb + lay.ebuf);
+  uint32_t* stage = reinterpret_cast<uint32_t*>(wb + lay.stage);
+  uint32_t* ring = reinterpret_cast<uint32_t*>(wb + lay.ring);
+  uint32_t* patch = reinterpret_cast<uint32_t*>(wb + lay.patch);
   uint8_t* mbytes = wb + lay.mbytes;
   while (true) {
     uint32_t kb = 0;
@@ -339,7 +362,7 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
     if (kb >= p.n_items) break;
     const uint32_t kend = min(kb + kDecBatch, p.n_items);
     for (uint32_t k = kb; k < kend; k++) {
-      decode_item(p, k, ebuf, mbytes);
+      decode_item(p, k, stage, ring, patch, mbytes);
     }
   }
 }
@@ -371,9 +394,8 @@ int launch_decode(const DecParams& p, void* stream, void* const* ev) {
   // warps per CTA from the per-warp shared memory (row-sized residual buffer)
   const size_t per_warp = dec_warp_layout(p.W).bytes;
   int rc;
-  if (8 * per_warp <= 100 * 1024) rc = launch_decode_t<8>(p, st);
-  else if (4 * per_warp <= 100 * 1024) rc = launch_decode_t<4>(p, st);
-  else if (2 * per_warp <= 100 * 1024) rc = launch_decode_t<2>(p, st);
+  if (4 * per_warp <= 48 * 1024) rc = launch_decode_t<4>(p, st);
+  else if (2 * per_warp <= 48 * 1024) rc = launch_decode_t<2>(p, st);
   else rc = launch_decode_t<1>(p, st);
   if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[1]), st);
   return rc;

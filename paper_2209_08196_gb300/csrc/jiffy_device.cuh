@@ -60,6 +60,33 @@ __device__ __forceinline__ void prefetch_l1(const void* p, uint32_t bytes) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
 }
 
+// Warp-wide copy of `bytes` bytes from global to shared memory: one round of
+// independent loads (16-byte vectors when both sides allow, else words, else
+// bytes).
+__device__ __forceinline__ void stage_bytes(uint8_t* dst, const uint8_t* src, uint32_t bytes) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uintptr_t al = reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src) | bytes;
+  if ((al & 15u) == 0) {
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    const uint32_t n = bytes / 16u;
+    for (uint32_t i = lane; i < n; i += 128u) {
+      uint4 v[4];
+#pragma unroll
+      for (uint32_t q = 0; q < 4; q++) v[q] = i + 32u * q < n ? s4[i + 32u * q] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (uint32_t q = 0; q < 4; q++)
+        if (i + 32u * q < n) d4[i + 32u * q] = v[q];
+    }
+  } else if ((al & 3u) == 0) {
+    const uint32_t* s1 = reinterpret_cast<const uint32_t*>(src);
+    uint32_t* d1 = reinterpret_cast<uint32_t*>(dst);
+    for (uint32_t i = lane; i < bytes / 4u; i += 32u) d1[i] = s1[i];
+  } else {
+    for (uint32_t i = lane; i < bytes; i += 32u) dst[i] = src[i];
+  }
+}
+
 // Groups of 8 consecutive samples move as one vector when the group is
 // aligned: 32 bytes (u32), 16 bytes (u16) or 8 bytes (u8). Group starts are
 // multiples of 8 samples, so a vector-aligned row base suffices.
@@ -337,75 +364,99 @@ __device__ __forceinline__ void st_publish(unsigned long long* p, unsigned long 
   atomicExch(p, v);
 }
 
-// Spins (bounded) until status word idx is non-empty.
-__device__ __forceinline__ unsigned long long st_wait(const unsigned long long* st, uint32_t idx, bool& timeout) {
-  unsigned long long s = st_load(st + idx);
-  if (s >> 62) return s;
-  unsigned long long t0 = global_timer_ns();
-  uint32_t ns = 32;
-  while (!((s = st_load(st + idx)) >> 62)) {
-    __nanosleep(ns);
-    if (ns < 1024) ns <<= 1;
-    if (global_timer_ns() - t0 > kSpinLimitNs) {
-      timeout = true;
-      return kStErr;
+// Warp-wide window read for the look-backs: kLookQ x 32 status words per
+// round, entry (q, lane) = word j - 32q - lane (nearest first), `beyond` past
+// the segment start. Finds the nearest entry that decides the look-back,
+// re-reading while an entry nearer than it is still empty; gives up after
+// kSpinLimitNs. stop = kLookQ * 32: no decision in this window. A wide window
+// keeps the walk short when thousands of rows are in flight and the nearest
+// published prefix lies hundreds of entries back.
+constexpr uint32_t kLookQ = 4;
+
+template <typename Decides>
+__device__ __forceinline__ bool lookback_window(const unsigned long long* st, int64_t j, uint32_t seg_start,
+                                                unsigned long long beyond, Decides decides,
+                                                unsigned long long (&s)[kLookQ], uint32_t& stop) {
+  const uint32_t lane = lane_id();
+  unsigned long long t0 = 0;
+  while (true) {
+#pragma unroll
+    for (uint32_t q = 0; q < kLookQ; q++) {
+      const int64_t idx = j - (int64_t)(32u * q + lane);
+      s[q] = idx >= (int64_t)seg_start ? st_load(st + idx) : beyond;
     }
+    bool err = false, waiting = false;
+    stop = kLookQ * 32u;
+#pragma unroll
+    for (uint32_t q = 0; q < kLookQ; q++) {
+      const uint32_t flag = (uint32_t)(s[q] >> 62);
+      err |= flag == 3u;
+      const uint32_t dec = __ballot_sync(0xffffffffu, flag != 0u && decides(s[q]));
+      const uint32_t empty = __ballot_sync(0xffffffffu, flag == 0u);
+      if (stop == kLookQ * 32u) {
+        const uint32_t first = dec ? (uint32_t)(__ffs(dec) - 1) : 32u;
+        if (empty & (first == 32u ? 0xffffffffu : ((1u << first) - 1u))) waiting = true;
+        if (first < 32u) stop = 32u * q + first;
+      }
+    }
+    if (__any_sync(0xffffffffu, err)) return false;  // an upstream error
+    if (!waiting) return true;
+    if (t0 == 0) t0 = global_timer_ns();
+    else if (global_timer_ns() - t0 > kSpinLimitNs) return false;
+    __nanosleep(64);
   }
-  return s;
 }
 
-// Warp 0 only. Exclusive prefix of item k over items [seg_start, k), summing
-// aggregates until an inclusive prefix is found. Returns false on an error
-// or timeout upstream.
+// Warp-wide. Exclusive prefix of item k over items [seg_start, k): sums
+// aggregates back to the nearest inclusive prefix. Returns false on an
+// upstream error or a timeout.
 __device__ inline bool lookback_sum(const unsigned long long* st, uint32_t k, uint32_t seg_start,
                                     unsigned long long& excl) {
   const uint32_t lane = lane_id();
   unsigned long long acc = 0;
   int64_t j = (int64_t)k - 1;
   while (j >= (int64_t)seg_start) {
-    int64_t idx = j - (int64_t)lane;
-    bool timeout = false;
-    unsigned long long s = idx >= (int64_t)seg_start ? st_wait(st, (uint32_t)idx, timeout) : kStInc;
-    bool bad = (s >> 62) == 3ull;
-    if (__any_sync(0xffffffffu, bad)) return false;
-    uint32_t inc = __ballot_sync(0xffffffffu, (s >> 62) == 2ull);
-    unsigned long long v = s & kStValMask;
-    if (inc) {
-      uint32_t first = __ffs(inc) - 1;
-      if (lane > first) v = 0;
-    }
-    // 64-bit warp sum
+    unsigned long long s[kLookQ];
+    uint32_t stop;
+    if (!lookback_window(st, j, seg_start, kStInc, [](unsigned long long x) { return (x >> 62) == 2ull; }, s, stop))
+      return false;
+    unsigned long long v = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kLookQ; q++)
+      if (32u * q + lane <= stop) v += s[q] & kStValMask;  // stop == window: every entry
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     acc += v;
-    if (inc) break;
-    j -= 32;
+    if (stop < kLookQ * 32u) break;
+    j -= kLookQ * 32;
   }
   excl = acc;
   return true;
 }
 
-// Warp 0 only. "Last valid" look-back used for the delta carry: value bit 32
-// = has-a-residual, bits 0..31 = the last residual. Walks back to the nearest
-// predecessor that has a residual or holds an inclusive value; the segment
-// start counts as a residual of 0 (e[-1] = 0).
+// Warp-wide. "Last valid" look-back for the delta carry: value bit 32 =
+// has-a-residual, bits 0..31 = the last residual. The nearest predecessor
+// that has a residual or holds an inclusive value decides; the segment start
+// counts as a residual of 0 (e[-1] = 0).
 __device__ inline bool lookback_last(const unsigned long long* st, uint32_t k, uint32_t seg_start,
                                      uint32_t& carry) {
-  const uint32_t lane = lane_id();
   int64_t j = (int64_t)k - 1;
   while (true) {
-    int64_t idx = j - (int64_t)lane;
-    bool timeout = false;
-    unsigned long long s = idx >= (int64_t)seg_start ? st_wait(st, (uint32_t)idx, timeout)
-                                                     : (kStInc | (1ull << 32));
-    bool bad = (s >> 62) == 3ull;
-    if (__any_sync(0xffffffffu, bad)) return false;
-    uint32_t stop = __ballot_sync(0xffffffffu, ((s >> 62) == 2ull) || ((s >> 32) & 1ull));
-    if (stop) {
-      uint32_t first = __ffs(stop) - 1;
-      carry = __shfl_sync(0xffffffffu, (uint32_t)s, first);
+    unsigned long long s[kLookQ];
+    uint32_t stop;
+    if (!lookback_window(st, j, seg_start, kStInc | (1ull << 32),
+                         [](unsigned long long x) { return ((x >> 62) == 2ull) || ((x >> 32) & 1ull); }, s, stop))
+      return false;
+    if (stop < kLookQ * 32u) {
+      uint32_t c = 0;
+#pragma unroll
+      for (uint32_t q = 0; q < kLookQ; q++) {
+        const uint32_t v = __shfl_sync(0xffffffffu, (uint32_t)s[q], stop & 31u);
+        if (q == stop / 32u) c = v;
+      }
+      carry = c;
       return true;
     }
-    j -= 32;
+    j -= kLookQ * 32;
   }
 }
 

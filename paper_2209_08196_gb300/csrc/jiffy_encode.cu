@@ -245,11 +245,51 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   const uint8_t* cur = p.cur[ta] + r * rowb;
   const uint8_t* prv = mode ? p.prev[ta] + r * rowb : nullptr;
   uint8_t* st_row = (t + 1 == p.T) ? p.state_next[a] + r * rowb : nullptr;
-  const bool vec_cur = vec_ok(cur, S), vec_prv = prv && vec_ok(prv, S), vec_st = st_row && vec_ok(st_row, S);
+  const bool vec_prv = prv && vec_ok(prv, S), vec_st = st_row && vec_ok(st_row, S);
 
   for (uint32_t j = lane; j < nw; j += 32) coded[j] = 0u;
+  // stage the row in one round of loads, at the top of the ZigZag buffer:
+  // ZigZag values fill it from the bottom and, with every lane reading its
+  // pixels of a step before any value of that step is written, never reach
+  // a pixel that is still to be read (raw row at byte (4 - S) * W)
+  uint8_t* raw = reinterpret_cast<uint8_t*>(zbuf) + (4u - S) * W;
+  stage_bytes(raw, cur, W * S);
+  if (prv) prefetch_l1(prv, (uint32_t)rowb);
+  const bool vec_cur = vec_ok(raw, S);
+  // the previous row's last 256 pixels, for the delta carry (read now, used
+  // after pass A)
+  const uint32_t px0 = W > 256u ? W - 256u : 0u;
+  const uint32_t pnv = px0 + 8u * lane < W ? min(8u, W - (px0 + 8u * lane)) : 0u;
+  uint32_t tv[8], tpv[8];
+  if (r > 0) {
+    const bool tvec = (px0 & 7u) == 0;
+    load8<false>(cur - rowb, S, px0 + 8u * lane, pnv, tvec && vec_ok(cur - rowb, S), tv);
+    if (prv) load8<false>(prv - rowb, S, px0 + 8u * lane, pnv, tvec && vec_ok(prv - rowb, S), tpv);
+  }
   __syncwarp();
 
+  // ---- delta carry: the residual preceding this row in the attribute-scan's
+  //      flat vector (Sec. III-C). The previous row's tail usually holds it;
+  //      otherwise a "last valid" look-back over the earlier rows decides.
+  uint32_t carry = 0;
+  bool known = r == 0;  // e[-1] = 0 at the start of the attribute-scan
+  if (r > 0) {
+    uint32_t tnz = 0, tlast = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const uint32_t q = quantize(tv[i], at);
+      const uint32_t pq = prv ? quantize(tpv[i], pat) : 0u;
+      if ((uint32_t)i < pnv && q != 0u) {
+        tnz = 1u;
+        tlast = q - pq;
+      }
+    }
+    const uint32_t has = __ballot_sync(0xffffffffu, tnz != 0u);
+    if (has) {
+      carry = __shfl_sync(0xffffffffu, tlast, 31u - __clz(has));
+      known = true;
+    }
+  }
   // ---- pass A: quantize (Sec. III-B), zero mask (Sec. III-C), mask XOR
   //      (Sec. III-D), compaction, residual, delta, ZigZag (Eq. 1)
   uint32_t n = 0;          // nonzero samples so far (uniform)
@@ -259,8 +299,9 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
     const uint32_t x0 = 256u * it + 8u * lane;
     const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
     uint32_t v[8], pv[8];
-    load8<false>(cur, S, x0, nv, vec_cur, v);
+    load8<false>(raw, S, x0, nv, vec_cur, v);
     if (prv) load8<false>(prv, S, x0, nv, vec_prv, pv);
+    __syncwarp();  // every lane has its pixels of this step before values are written
     uint32_t e[8];
     uint32_t mb = 0, pm = 0;
 #pragma unroll
@@ -309,26 +350,60 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
     }
     n += tot;
   }
-  // ---- delta carry: the residual preceding this row in the attribute-scan's
-  //      flat vector (Sec. III-C), by a "last valid" look-back over rows
-  uint32_t carry = 0;
-  bool ok = true;
-  if (r == 0) {
-    if (lane == 0) st_publish(p.st_carry + k, kStInc | (1ull << 32) | (n ? last_e : 0u));
-  } else {
-    if (lane == 0) st_publish(p.st_carry + k, kStAgg | ((unsigned long long)(n ? 1 : 0) << 32) | last_e);
-    ok = lookback_last(p.st_carry, k, sec_start, carry);
-    if (lane == 0) st_publish(p.st_carry + k, ok ? (kStInc | (1ull << 32) | (n ? last_e : carry)) : kStErr);
+  if (lane == 0) {
+    const unsigned long long lastv = n ? last_e : carry;
+    if (known) st_publish(p.st_carry + k, kStInc | (1ull << 32) | lastv);
+    else st_publish(p.st_carry + k, kStAgg | ((unsigned long long)(n ? 1 : 0) << 32) | last_e);
   }
-  if (!ok) {
-    if (lane == 0) {
-      atomicOr(p.err, kErrTimeout);
-      st_publish(p.st_bytes + k, kStErr);
+
+  // ---- block widths (Sec. II) of blocks 1.. first: only block 0 depends on
+  //      the carry, so a fallback wait overlaps this work
+  const uint32_t nb = ceil_div_u32(n, kBlockN);
+  auto width_of = [&](uint32_t blk) {
+    const uint32_t base = blk * kBlockN, m = min(kBlockN, n - base);
+    uint32_t z[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const uint32_t i = lane + 32u * q;
+      z[q] = i < m ? zbuf[base + i] : 0u;
     }
-    return;
+    const BlockChoice bc = choose_block(z, m, w.hist);
+    if (lane == 0) w.meta[blk] = make_uint2(bc.b | (bc.e << 8) | (bc.hb << 16), bc.bytes);
+  };
+  for (uint32_t blk = 1; blk < nb; blk++) width_of(blk);
+  if (!known) {
+    const bool ok = lookback_last(p.st_carry, k, sec_start, carry);
+    if (lane == 0) st_publish(p.st_carry + k, ok ? (kStInc | (1ull << 32) | (n ? last_e : carry)) : kStErr);
+    if (!ok) {
+      if (lane == 0) atomicOr(p.err, kErrTimeout);
+      return;
+    }
   }
-  if (n && lane == 0) zbuf[0] = zigzag(e_first - carry);
+  if (n) {
+    if (lane == 0) zbuf[0] = zigzag(e_first - carry);
+    __syncwarp();
+    width_of(0);
+  }
   __syncwarp();
+
+  // ---- body offsets: exclusive prefix of the block bytes (lane l: 4l..4l+3)
+  uint32_t body = 0;
+  {
+    uint32_t bsz[4], mysum = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < 4; q++) {
+      const uint32_t blk = 4u * lane + q;
+      bsz[q] = blk < nb ? w.meta[blk].y : 0u;
+      mysum += bsz[q];
+    }
+    uint32_t off = warp_excl_scan(mysum, body);
+#pragma unroll
+    for (uint32_t q = 0; q < 4; q++) {
+      const uint32_t blk = 4u * lane + q;
+      if (blk < nb) w.meta[blk].y = off;
+      off += bsz[q];
+    }
+  }
 
   // ---- mask part size: literal words
   uint32_t nlit = 0;
@@ -338,51 +413,16 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
     const bool lit = j < nw && mask_class(coded[j], valid) == 2u;
     nlit += __popc(__ballot_sync(0xffffffffu, lit));
   }
-
-  // ---- block widths (Sec. II), body offsets
-  const uint32_t nb = ceil_div_u32(n, kBlockN);
-  uint32_t body = 0;
-  for (uint32_t blk = 0; blk < nb; blk++) {
-    const uint32_t base = blk * kBlockN, m = min(kBlockN, n - base);
-    uint32_t z[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const uint32_t i = lane + 32u * q;
-      z[q] = i < m ? zbuf[base + i] : 0u;
-    }
-    const BlockChoice bc = choose_block(z, m, w.hist);
-    if (lane == 0) w.meta[blk] = make_uint2(bc.b | (bc.e << 8) | (bc.hb << 16), body);
-    body += bc.bytes;
-  }
   __syncwarp();
   const uint32_t head_words = ncls + nlit + nb;
   const uint32_t chunk = 4u * head_words + body;
-
-  // ---- byte offset by decoupled look-back over all rows of the call
-  unsigned long long excl = 0;
-  if (k == 0) {
-    if (lane == 0) st_publish(p.st_bytes + k, kStInc | chunk);
-  } else {
-    if (lane == 0) st_publish(p.st_bytes + k, kStAgg | chunk);
-    ok = lookback_sum(p.st_bytes, k, 0, excl);
-    if (lane == 0) st_publish(p.st_bytes + k, ok ? (kStInc | (excl + chunk)) : kStErr);
-  }
-  if (!ok) {
-    if (lane == 0) atomicOr(p.err, kErrTimeout);
-    return;
-  }
   if (lane == 0) {
     p.row_bytes[k] = chunk;
     p.row_nnz[k] = n;
     p.row_carry[k] = carry;
   }
-  const unsigned long long off = p.shdr + (unsigned long long)(t + 1) * p.fhdr +
-                                 (unsigned long long)(ta + 1) * 8ull * H + excl;
-  if (off + chunk > p.cap) {
-    if (lane == 0) atomicOr(p.err, kErrCapacity);
-    return;
-  }
-  uint32_t* dst = reinterpret_cast<uint32_t*>(p.out + off);
+  // the chunk goes to this row's slot; k_place moves it to its offset
+  uint32_t* dst = reinterpret_cast<uint32_t*>(p.slots + (size_t)k * p.slot_bytes);
 
   // ---- mask part: 2-bit class per word (16 per class word), literals
   uint32_t litbase = 0;
@@ -471,8 +511,13 @@ __global__ void __launch_bounds__(WPC * 32) k_encode(EncParams p) {
 }
 
 // ----------------------------------------------------------------------------
-// k_finalize: one CTA per frame: row tables (end offsets + carries), frame
-// header, stream header, frame offsets and the total length.
+// k_sec_sizes: one CTA per section (scan t, attribute a): its bytes (row
+// table + row chunks) and nonzero count.
+// k_place: one CTA per section: the section's offset in the stream (prefix
+// over the earlier sections), its row table (end offsets + carries), the copy
+// of each row chunk from its slot, and, for attribute 0, the frame header and
+// frame offset; section 0 also writes the stream header. Every write is
+// checked against the output capacity.
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ void put_u32_guarded(uint8_t* out, unsigned long long cap, unsigned long long at,
                                                 uint32_t v, uint32_t* err) {
@@ -480,60 +525,91 @@ __device__ __forceinline__ void put_u32_guarded(uint8_t* out, unsigned long long
   else atomicOr(err, kErrCapacity);
 }
 
-__global__ void __launch_bounds__(kThreads) k_finalize(EncParams p) {
-  extern __shared__ __align__(16) uint32_t smem[];  // [H] row ends
-  __shared__ uint32_t s_tmp[kWarps + 1];
-  __shared__ uint32_t s_sec[kMaxAttr], s_nnz[kMaxAttr];
-  const uint32_t t = blockIdx.x, H = p.H, A = p.A;
-  // every status word is an inclusive prefix now
-  const uint32_t first = t * A * H;
-  const unsigned long long before = first ? (p.st_bytes[first - 1] & kStValMask) : 0ull;
-  const unsigned long long fstart = p.shdr + (unsigned long long)t * (p.fhdr + 8ull * A * H) + before;
-  unsigned long long sec_at = fstart + p.fhdr;
-  for (uint32_t a = 0; a < A; a++) {
-    const uint32_t ta = t * A + a;
-    for (uint32_t r = threadIdx.x; r < H; r += kThreads) smem[r] = p.row_bytes[ta * H + r];
-    __syncthreads();
-    const uint32_t data = block_excl_scan(smem, H, s_tmp);  // smem = row starts
-    uint32_t nnz = 0;
-    for (uint32_t r = threadIdx.x; r < H; r += kThreads) {
-      const uint32_t end = (r + 1 < H) ? smem[r + 1] : data;
-      put_u32_guarded(p.out, p.cap, sec_at + 8ull * r, end, p.err);
-      put_u32_guarded(p.out, p.cap, sec_at + 8ull * r + 4, p.row_carry[ta * H + r], p.err);
-      nnz += p.row_nnz[ta * H + r];
-    }
-    nnz = warp_sum(nnz);
-    if (lane_id() == 0) s_tmp[warp_id()] = nnz;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t tot = 0;
-      for (int w = 0; w < kWarps; w++) tot += s_tmp[w];
-      s_nnz[a] = tot;
-      s_sec[a] = 8u * H + data;
-    }
-    __syncthreads();
-    sec_at += s_sec[a];
+__device__ __forceinline__ unsigned long long cta_sum_u64(unsigned long long v, unsigned long long* s_red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane_id() == 0) s_red[warp_id()] = v;
+  __syncthreads();
+  unsigned long long tot = 0;
+  for (uint32_t w2 = 0; w2 < blockDim.x / 32u; w2++) tot += s_red[w2];
+  __syncthreads();
+  return tot;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sec_sizes(EncParams p) {
+  __shared__ unsigned long long s_red[kWarps];
+  const uint32_t ta = blockIdx.x, H = p.H;
+  unsigned long long bytes = 0, nnz = 0;
+  for (uint32_t r = threadIdx.x; r < H; r += kThreads) {
+    bytes += p.row_bytes[ta * H + r];
+    nnz += p.row_nnz[ta * H + r];
   }
+  bytes = cta_sum_u64(bytes, s_red);
+  nnz = cta_sum_u64(nnz, s_red);
   if (threadIdx.x == 0) {
-    const uint32_t frame_bytes = (uint32_t)(sec_at - fstart);
-    put_u32_guarded(p.out, p.cap, fstart, frame_bytes, p.err);
-    put_u32_guarded(p.out, p.cap, fstart + 4, p.frame0 + t, p.err);
-    for (uint32_t a = 0; a < A; a++) {
-      const unsigned long long h = fstart + 8ull + 12ull * a;
-      put_u32_guarded(p.out, p.cap, h, p.modes[t * A + a], p.err);
-      put_u32_guarded(p.out, p.cap, h + 4, s_sec[a], p.err);
-      put_u32_guarded(p.out, p.cap, h + 8, s_nnz[a], p.err);
+    p.sec_bytes[ta] = 8ull * H + bytes;
+    p.sec_nnz[ta] = (uint32_t)nnz;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
+  extern __shared__ __align__(16) uint32_t smem[];  // [H] row chunk starts
+  __shared__ unsigned long long s_red[kWarps];
+  __shared__ uint32_t s_tmp[kWarps + 1];
+  const uint32_t ta = blockIdx.x, H = p.H, A = p.A, t = ta / A, a = ta % A;
+  // bytes of the earlier sections: of earlier frames (frame_before) and of
+  // this frame's earlier attributes
+  unsigned long long frame_before = 0, attr_before = 0;
+  for (uint32_t i = threadIdx.x; i < ta; i += kThreads) {
+    if (i < t * A) frame_before += p.sec_bytes[i];
+    else attr_before += p.sec_bytes[i];
+  }
+  frame_before = cta_sum_u64(frame_before, s_red);
+  attr_before = cta_sum_u64(attr_before, s_red);
+  const unsigned long long frame_at = p.shdr + (unsigned long long)t * p.fhdr + frame_before;
+  const unsigned long long sec_at = frame_at + p.fhdr + attr_before;
+  // row table: end offsets (prefix of chunk sizes) and carries
+  for (uint32_t r = threadIdx.x; r < H; r += kThreads) smem[r] = p.row_bytes[ta * H + r];
+  __syncthreads();
+  const uint32_t data = block_excl_scan(smem, H, s_tmp);  // smem = row starts
+  for (uint32_t r = threadIdx.x; r < H; r += kThreads) {
+    const uint32_t end = (r + 1 < H) ? smem[r + 1] : data;
+    put_u32_guarded(p.out, p.cap, sec_at + 8ull * r, end, p.err);
+    put_u32_guarded(p.out, p.cap, sec_at + 8ull * r + 4, p.row_carry[ta * H + r], p.err);
+  }
+  // row chunks: warp per row, slot -> stream (4-byte aligned words)
+  const unsigned long long data_at = sec_at + 8ull * H;
+  for (uint32_t r = warp_id(); r < H; r += kWarps) {
+    const uint32_t words = p.row_bytes[ta * H + r] / 4u;
+    const unsigned long long at = data_at + smem[r];
+    if (at + 4ull * words > p.cap) {
+      if (lane_id() == 0) atomicOr(p.err, kErrCapacity);
+      continue;
     }
-    p.frame_off[t] = fstart;
-    if (t + 1 == p.T) p.frame_off[p.T] = sec_at;
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(p.slots + (size_t)(ta * H + r) * p.slot_bytes);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(p.out + at);
+    for (uint32_t i = lane_id(); i < words; i += 32u) dst[i] = src[i];
+  }
+  if (a == 0 && threadIdx.x == 0) {
+    unsigned long long fbytes = p.fhdr;
+    for (uint32_t aa = 0; aa < A; aa++) fbytes += p.sec_bytes[t * A + aa];
+    put_u32_guarded(p.out, p.cap, frame_at, (uint32_t)fbytes, p.err);
+    put_u32_guarded(p.out, p.cap, frame_at + 4, p.frame0 + t, p.err);
+    for (uint32_t aa = 0; aa < A; aa++) {
+      const unsigned long long h = frame_at + 8ull + 12ull * aa;
+      put_u32_guarded(p.out, p.cap, h, p.modes[t * A + aa], p.err);
+      put_u32_guarded(p.out, p.cap, h + 4, (uint32_t)p.sec_bytes[t * A + aa], p.err);
+      put_u32_guarded(p.out, p.cap, h + 8, p.sec_nnz[t * A + aa], p.err);
+    }
+    p.frame_off[t] = frame_at;
+    if (t + 1 == p.T) p.frame_off[p.T] = frame_at + fbytes;
     if (t == 0 && p.shdr) {
       put_u32_guarded(p.out, p.cap, 0, 0x3159464Au, p.err);  // "JFY1"
       put_u32_guarded(p.out, p.cap, 4, 1u | (A << 16), p.err);
       put_u32_guarded(p.out, p.cap, 8, H, p.err);
       put_u32_guarded(p.out, p.cap, 12, p.W, p.err);
-      for (uint32_t a = 0; a < A; a++) {
-        put_u32_guarded(p.out, p.cap, 16 + 8ull * a, p.attrs[a].s | (1u << 8), p.err);
-        put_u32_guarded(p.out, p.cap, 20 + 8ull * a, p.attrs[a].P, p.err);
+      for (uint32_t aa = 0; aa < A; aa++) {
+        put_u32_guarded(p.out, p.cap, 16 + 8ull * aa, p.attrs[aa].s | (1u << 8), p.err);
+        put_u32_guarded(p.out, p.cap, 20 + 8ull * aa, p.attrs[aa].P, p.err);
       }
     }
   }
@@ -564,7 +640,7 @@ static cudaError_t launch_encode_rows(const EncParams& p, cudaStream_t st) {
 
 int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const size_t s_trial = 8ull * p.W, s_fin = 4ull * p.H;
+  const size_t s_trial = 8ull * p.W, s_place = 4ull * p.H;
   cudaError_t e = cudaFuncSetAttribute(k_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_trial);
   if (e != cudaSuccess) return (int)e;
   auto mark = [&](int i) {
@@ -580,7 +656,8 @@ int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   else e = launch_encode_rows<1>(p, st);
   if (e != cudaSuccess) return (int)e;
   mark(2);
-  k_finalize<<<p.T, kThreads, s_fin, st>>>(p);
+  k_sec_sizes<<<p.T * p.A, kThreads, 0, st>>>(p);
+  k_place<<<p.T * p.A, kThreads, s_place, st>>>(p);
   mark(3);
   return (int)cudaGetLastError();
 }

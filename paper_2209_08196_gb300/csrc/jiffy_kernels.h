@@ -27,8 +27,11 @@ struct EncParams {
   uint32_t* row_bytes;           // [n_items]
   uint32_t* row_nnz;             // [n_items]
   uint32_t* row_carry;           // [n_items]
-  unsigned long long* st_carry;  // [n_items] look-back status (delta carry)
-  unsigned long long* st_bytes;  // [n_items] look-back status (byte offsets)
+  unsigned long long* st_carry;  // [n_items] look-back status (delta carry, fallback)
+  uint8_t* slots;                // [n_items * slot_bytes] each row's packed chunk
+  uint32_t slot_bytes;           // row_bound(W) rounded up to 16
+  unsigned long long* sec_bytes; // [T*A] section bytes (row table + chunks)
+  uint32_t* sec_nnz;             // [T*A]
   uint32_t* ticket;
   uint32_t* err;
   unsigned long long* frame_off; // [T+1]
