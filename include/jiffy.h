@@ -141,13 +141,52 @@ jiffy_status jiffy_decode(jiffy_stream* s, const void* in, size_t in_len, void* 
 jiffy_status jiffy_decode_seq(jiffy_stream* s, uint32_t n_scans, const void* in, size_t in_len,
                               const uint64_t* frame_offsets, void* const* planes_out, void* cuda_stream);
 
+/* ---- Many streams in one pass (serving many sensors). A batch context owns
+ * the scratch of batched calls on one device. In one call every stream
+ * codes its own consecutive scans; all rows of all streams run in the same
+ * kernel launches, each stream keeping its own state, shape and attributes.
+ * A stream may appear at most once per call and must live on the batch's
+ * device. */
+typedef struct jiffy_batch jiffy_batch;
+
+jiffy_status jiffy_batch_create(jiffy_batch** out, int device);
+void jiffy_batch_destroy(jiffy_batch* b);
+
+/* Encodes, for i < n, n_scans[i] consecutive scans of encoder streams[i]:
+ * planes[i] is a host array of n_scans[i] * n_attr device pointers
+ * (scan-major), outs[i] a 16-byte aligned device buffer of caps[i] bytes.
+ * frame_offsets (nullable host array of n host pointers, each nullable):
+ * frame_offsets[i] receives n_scans[i] + 1 offsets as in jiffy_encode_seq.
+ * out_lens[i] (host) = bytes written (or required, on JIFFY_ERR_CAPACITY);
+ * statuses[i] (host) = that stream's status; a stream whose status is not
+ * JIFFY_OK keeps its state. Returns JIFFY_OK if every stream succeeded, else
+ * the first failing status. Synchronizes cuda_stream (Sec. III-D prediction
+ * within each stream, as jiffy_encode_seq). */
+jiffy_status jiffy_encode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams, const uint32_t* n_scans,
+                                const void* const* const* planes, void* const* outs, const size_t* caps,
+                                uint64_t* const* frame_offsets, size_t* out_lens, jiffy_status* statuses,
+                                void* cuda_stream);
+
+/* Decodes, for i < n, n_frames[i] frames of decoder streams[i] from ins[i]
+ * (in_lens[i] bytes, 4-byte aligned, device) with frame_offsets[i] (host,
+ * n_frames[i] + 1 entries) into planes_out[i] (host array of
+ * n_frames[i] * n_attr device pointers). statuses[i] as in
+ * jiffy_encode_batch. Synchronizes cuda_stream. */
+jiffy_status jiffy_decode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams, const uint32_t* n_frames,
+                                const void* const* ins, const size_t* in_lens, const uint64_t* const* frame_offsets,
+                                void* const* const* planes_out, jiffy_status* statuses, void* cuda_stream);
+
+/* Per-kernel device timing of the batch's calls, as for streams below. */
+jiffy_status jiffy_batch_set_profiling(jiffy_batch* b, int enable);
+uint32_t jiffy_batch_kernel_times(const jiffy_batch* b, float* ms, uint32_t n);
+
 /* Per-kernel device timing (CUDA events recorded around each kernel launch
  * on the call's cuda_stream). enable != 0 turns it on for later calls. */
 jiffy_status jiffy_stream_set_profiling(jiffy_stream* s, int enable);
 
 /* Device milliseconds of each kernel launched by the stream's last
- * successful call, in launch order (encode: trial, encode, finalize;
- * decode: decode). Writes min(n, count) values to ms (host) and returns the
+ * successful call, in launch order (encode: trial, rows, placement; decode:
+ * rows). Writes min(n, count) values to ms (host) and returns the
  * count (0 if profiling is off or no call completed). */
 uint32_t jiffy_stream_kernel_times(const jiffy_stream* s, float* ms, uint32_t n);
 

@@ -1,7 +1,9 @@
-// Host side of the Jiffy C ABI (include/jiffy.h): stream handles, device
-// state and scratch, argument checks, kernel launches and status mapping.
-// Every step of the codec itself runs in the kernels of jiffy_encode.cu and
-// jiffy_decode.cu; this file only marshals pointers and sizes.
+// Host side of the Jiffy C ABI (include/jiffy.h): stream and batch handles,
+// device state and scratch, argument checks, kernel launches and status
+// mapping. Every step of the codec itself runs in the kernels of
+// jiffy_encode.cu and jiffy_decode.cu; this file only marshals pointers and
+// sizes. A call codes one segment per stream: jiffy_encode(_seq) and
+// jiffy_decode(_seq) are one-segment calls, the batch calls code many.
 #include "jiffy.h"
 
 #include <cuda_runtime.h>
@@ -15,8 +17,25 @@
 
 using jiffy::AttrDev;
 
-struct jiffy_stream {
+namespace {
+
+// Device scratch, pinned host staging and timing events of a handle.
+struct Workspace {
   int device = 0;
+  uint8_t* d_scratch = nullptr;
+  size_t scratch_cap = 0;
+  uint8_t* h_pinned = nullptr;
+  size_t pinned_cap = 0;
+  bool profile = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  float kernel_ms[3] = {0, 0, 0};
+  uint32_t n_kernel_ms = 0;
+};
+
+}  // namespace
+
+struct jiffy_stream {
+  Workspace ws;
   jiffy_role role = JIFFY_ENCODER;
   uint32_t H = 0, W = 0, A = 0;
   jiffy_options opt{4, -1};
@@ -26,14 +45,10 @@ struct jiffy_stream {
   std::vector<size_t> plane_off;              // byte offset of attribute a in a state buffer
   int cur = 0;                                // state buffer holding the previous scan
   uint32_t frame = 0;                         // frames since create/reset
-  uint8_t* d_scratch = nullptr;
-  size_t scratch_cap = 0;
-  uint8_t* h_pinned = nullptr;
-  size_t pinned_cap = 0;
-  bool profile = false;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  float kernel_ms[3] = {0, 0, 0};
-  uint32_t n_kernel_ms = 0;
+};
+
+struct jiffy_batch {
+  Workspace ws;
 };
 
 namespace {
@@ -67,24 +82,56 @@ uint64_t magic_for(uint32_t P) {
   return (~0ull) / P + 1ull;
 }
 
-jiffy_status ensure_scratch(jiffy_stream* s, size_t dev_bytes, size_t host_bytes) {
-  if (dev_bytes > s->scratch_cap) {
-    if (s->d_scratch) cudaFree(s->d_scratch);
-    s->d_scratch = nullptr;
-    s->scratch_cap = 0;
+jiffy_status ensure_scratch(Workspace& w, size_t dev_bytes, size_t host_bytes) {
+  if (dev_bytes > w.scratch_cap) {
+    if (w.d_scratch) cudaFree(w.d_scratch);
+    w.d_scratch = nullptr;
+    w.scratch_cap = 0;
     size_t cap = align_up(dev_bytes + dev_bytes / 4, 1 << 20);
-    if (cudaMalloc(&s->d_scratch, cap) != cudaSuccess) return JIFFY_ERR_NOMEM;
-    s->scratch_cap = cap;
+    if (cudaMalloc(&w.d_scratch, cap) != cudaSuccess) return JIFFY_ERR_NOMEM;
+    w.scratch_cap = cap;
   }
-  if (host_bytes > s->pinned_cap) {
-    if (s->h_pinned) cudaFreeHost(s->h_pinned);
-    s->h_pinned = nullptr;
-    s->pinned_cap = 0;
+  if (host_bytes > w.pinned_cap) {
+    if (w.h_pinned) cudaFreeHost(w.h_pinned);
+    w.h_pinned = nullptr;
+    w.pinned_cap = 0;
     size_t cap = align_up(host_bytes + host_bytes / 4, 1 << 16);
-    if (cudaMallocHost(&s->h_pinned, cap) != cudaSuccess) return JIFFY_ERR_NOMEM;
-    s->pinned_cap = cap;
+    if (cudaMallocHost(&w.h_pinned, cap) != cudaSuccess) return JIFFY_ERR_NOMEM;
+    w.pinned_cap = cap;
   }
   return JIFFY_OK;
+}
+
+void release(Workspace& w) {
+  if (w.d_scratch) cudaFree(w.d_scratch);
+  if (w.h_pinned) cudaFreeHost(w.h_pinned);
+  for (cudaEvent_t e : w.ev)
+    if (e) cudaEventDestroy(e);
+  w = Workspace{};
+}
+
+jiffy_status set_profiling(Workspace& w, int enable) {
+  if (enable && !w.ev[0]) {
+    DeviceGuard g(w.device);
+    if (!g.ok) return JIFFY_ERR_CUDA;
+    for (cudaEvent_t& e : w.ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return JIFFY_ERR_CUDA;
+  }
+  w.profile = enable != 0;
+  w.n_kernel_ms = 0;
+  return JIFFY_OK;
+}
+
+// Reads the event intervals of the last call (after its synchronize).
+void read_kernel_times(Workspace& w, uint32_t n_kernels) {
+  w.n_kernel_ms = 0;
+  if (!w.profile) return;
+  for (uint32_t i = 0; i < n_kernels; i++) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, w.ev[i], w.ev[i + 1]) != cudaSuccess) return;
+    w.kernel_ms[i] = ms;
+  }
+  w.n_kernel_ms = n_kernels;
 }
 
 jiffy_status map_device_error(uint32_t err) {
@@ -94,20 +141,331 @@ jiffy_status map_device_error(uint32_t err) {
   return JIFFY_OK;
 }
 
-// Reads the event intervals of the last call (after its synchronize).
-void read_kernel_times(jiffy_stream* s, uint32_t n_kernels) {
-  s->n_kernel_ms = 0;
-  if (!s->profile) return;
-  for (uint32_t i = 0; i < n_kernels; i++) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, s->ev[i], s->ev[i + 1]) != cudaSuccess) return;
-    s->kernel_ms[i] = ms;
-  }
-  s->n_kernel_ms = n_kernels;
-}
-
 uint32_t stream_header_bytes(uint32_t A) { return 16u + 8u * A; }
 uint32_t frame_header_bytes(uint32_t A) { return 8u + 12u * A; }
+uint32_t slot_bytes_for(uint32_t W) { return (jiffy::row_bound_bytes(W) + 15u) & ~15u; }
+
+// ---------------------------------------------------------------- encode
+struct EncJob {
+  jiffy_stream* s;
+  uint32_t T;
+  const void* const* planes;  // T*A device pointers
+  void* out;
+  size_t cap;
+  uint64_t* frame_offsets;    // host, T+1, nullable
+  size_t* out_len;            // host
+  jiffy_status* status;       // host
+};
+
+jiffy_status check_distinct(const std::vector<jiffy_stream*>& ss) {
+  for (size_t i = 0; i < ss.size(); i++)
+    for (size_t k = i + 1; k < ss.size(); k++)
+      if (ss[i] == ss[k]) return JIFFY_ERR_INVALID_ARG;  // a stream at most once per call
+  return JIFFY_OK;
+}
+
+jiffy_status run_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream_t st) {
+  const uint32_t n = (uint32_t)jobs.size();
+  // ---- argument checks and totals
+  unsigned long long items = 0, secs = 0;
+  uint32_t max_W = 1;
+  std::vector<jiffy_stream*> ss(n);
+  for (uint32_t i = 0; i < n; i++) {
+    EncJob& j = jobs[i];
+    *j.status = JIFFY_OK;
+    jiffy_stream* s = j.s;
+    ss[i] = s;
+    if (!s || !j.planes || !j.out || !j.out_len || j.T == 0) return JIFFY_ERR_INVALID_ARG;
+    if (s->role != JIFFY_ENCODER || s->ws.device != ws.device) return JIFFY_ERR_STATE;
+    if (reinterpret_cast<uintptr_t>(j.out) & 15u) return JIFFY_ERR_INVALID_ARG;
+    for (size_t q = 0; q < (size_t)j.T * s->A; q++)
+      if (!j.planes[q]) return JIFFY_ERR_INVALID_ARG;
+    items += (unsigned long long)j.T * s->A * s->H;
+    secs += (unsigned long long)j.T * s->A;
+    if (s->W > max_W) max_W = s->W;
+  }
+  if (check_distinct(ss) != JIFFY_OK) return JIFFY_ERR_INVALID_ARG;
+  if (items > 0x7fffffffull) return JIFFY_ERR_INVALID_ARG;
+
+  // ---- upload image: segments, search keys, per-segment pointer arrays
+  Carver up;
+  const size_t u_seg = up.take(sizeof(jiffy::EncSeg) * n);
+  const size_t u_ib = up.take(4ull * n), u_sb = up.take(4ull * n);
+  std::vector<size_t> u_ptrs(n);
+  for (uint32_t i = 0; i < n; i++) u_ptrs[i] = up.take(8ull * (2ull * jobs[i].T + 1) * jobs[i].s->A);
+  // ---- results image: per-segment error word and frame offsets
+  Carver rs;
+  std::vector<size_t> r_err(n), r_off(n);
+  for (uint32_t i = 0; i < n; i++) {
+    r_err[i] = rs.take(8);
+    r_off[i] = rs.take(8ull * (jobs[i].T + 1));
+  }
+  // ---- device scratch: upload, zeroed region (look-back words, ticket,
+  //      results), work arrays, row slots
+  Carver c;
+  const size_t o_up = c.take(up.off);
+  const size_t o_zero = c.take(0);
+  const size_t o_stc = c.take(8ull * items), o_tick = c.take(8);
+  const size_t o_res = c.take(rs.off);
+  const size_t zero_bytes = c.off - o_zero;
+  const size_t o_modes = c.take(4ull * secs);
+  const size_t o_rb = c.take(4ull * items), o_rn = c.take(4ull * items), o_rc = c.take(4ull * items);
+  const size_t o_secb = c.take(8ull * secs), o_secn = c.take(4ull * secs);
+  std::vector<unsigned long long> slot_base(n);
+  unsigned long long slots_total = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    const jiffy_stream* s = jobs[i].s;
+    slot_base[i] = slots_total;
+    slots_total += (unsigned long long)slot_bytes_for(s->W) * jobs[i].T * s->A * s->H;
+  }
+  const size_t o_slots = c.take(slots_total);
+  const size_t h_res = align_up(up.off, 256);
+  jiffy_status r = ensure_scratch(ws, c.off, h_res + rs.off);
+  if (r != JIFFY_OK) return r;
+  uint8_t* d = ws.d_scratch;
+  uint8_t* h = ws.h_pinned;
+
+  jiffy::EncSeg* segs = reinterpret_cast<jiffy::EncSeg*>(h + u_seg);
+  uint32_t* ib = reinterpret_cast<uint32_t*>(h + u_ib);
+  uint32_t* sb = reinterpret_cast<uint32_t*>(h + u_sb);
+  uint32_t item_base = 0, sec_base = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    EncJob& j = jobs[i];
+    jiffy_stream* s = j.s;
+    const uint32_t T = j.T, A = s->A;
+    uint64_t* hp = reinterpret_cast<uint64_t*>(h + u_ptrs[i]);
+    for (uint32_t t = 0; t < T; t++) {
+      for (uint32_t a = 0; a < A; a++) {
+        hp[t * A + a] = reinterpret_cast<uint64_t>(j.planes[t * A + a]);
+        uint64_t prev = 0;
+        if (t > 0) prev = reinterpret_cast<uint64_t>(j.planes[(t - 1) * A + a]);
+        else if (s->frame > 0) prev = reinterpret_cast<uint64_t>(s->d_state[s->cur] + s->plane_off[a]);
+        hp[(size_t)T * A + t * A + a] = prev;
+      }
+    }
+    for (uint32_t a = 0; a < A; a++)
+      hp[2ull * T * A + a] = reinterpret_cast<uint64_t>(s->d_state[1 - s->cur] + s->plane_off[a]);
+    const uint8_t* dp = d + o_up + u_ptrs[i];
+    jiffy::EncSeg g{};
+    g.H = s->H;
+    g.W = s->W;
+    g.A = A;
+    g.T = T;
+    g.nw = (s->W + 31) / 32;
+    g.ncls = (g.nw + 15) / 16;
+    g.frame0 = s->frame;
+    g.shdr = s->frame == 0 ? stream_header_bytes(A) : 0u;
+    g.fhdr = frame_header_bytes(A);
+    g.test_lines = s->opt.test_lines;
+    g.force_mode = s->opt.force_mode;
+    g.item_base = item_base;
+    g.sec_base = sec_base;
+    g.slot_bytes = slot_bytes_for(s->W);
+    g.slot_base = slot_base[i];
+    g.attrs = s->d_attrs;
+    g.cur = reinterpret_cast<const uint8_t* const*>(dp);
+    g.prev = reinterpret_cast<const uint8_t* const*>(dp + 8ull * T * A);
+    g.state_next = reinterpret_cast<uint8_t* const*>(dp + 16ull * T * A);
+    g.out = static_cast<uint8_t*>(j.out);
+    g.cap = j.cap;
+    g.frame_off = reinterpret_cast<unsigned long long*>(d + o_res + r_off[i]);
+    g.err = reinterpret_cast<uint32_t*>(d + o_res + r_err[i]);
+    segs[i] = g;
+    ib[i] = item_base;
+    sb[i] = sec_base;
+    item_base += T * A * s->H;
+    sec_base += T * A;
+  }
+  cudaError_t ce = cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, st);
+  if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
+
+  jiffy::EncParams p{};
+  p.n_seg = n;
+  p.n_items = (uint32_t)items;
+  p.n_sec = (uint32_t)secs;
+  p.max_W = max_W;
+  p.seg = reinterpret_cast<const jiffy::EncSeg*>(d + o_up + u_seg);
+  p.seg_item_base = reinterpret_cast<const uint32_t*>(d + o_up + u_ib);
+  p.seg_sec_base = reinterpret_cast<const uint32_t*>(d + o_up + u_sb);
+  p.modes = reinterpret_cast<uint32_t*>(d + o_modes);
+  p.row_bytes = reinterpret_cast<uint32_t*>(d + o_rb);
+  p.row_nnz = reinterpret_cast<uint32_t*>(d + o_rn);
+  p.row_carry = reinterpret_cast<uint32_t*>(d + o_rc);
+  p.st_carry = reinterpret_cast<unsigned long long*>(d + o_stc);
+  p.slots = d + o_slots;
+  p.sec_bytes = reinterpret_cast<unsigned long long*>(d + o_secb);
+  p.sec_nnz = reinterpret_cast<uint32_t*>(d + o_secn);
+  p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
+  void* evs[4] = {ws.ev[0], ws.ev[1], ws.ev[2], ws.ev[3]};
+  if (jiffy::launch_encode(p, st, ws.profile ? evs : nullptr) != 0) return JIFFY_ERR_CUDA;
+
+  uint8_t* hres = h + h_res;
+  ce = cudaMemcpyAsync(hres, d + o_res, rs.off, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
+  jiffy_status first = JIFFY_OK;
+  for (uint32_t i = 0; i < n; i++) {
+    EncJob& j = jobs[i];
+    uint32_t err = 0;
+    std::memcpy(&err, hres + r_err[i], 4);
+    const uint64_t* foff = reinterpret_cast<const uint64_t*>(hres + r_off[i]);
+    const jiffy_status res = map_device_error(err);
+    *j.out_len = foff[j.T];
+    *j.status = res;
+    if (res != JIFFY_OK) {
+      if (first == JIFFY_OK) first = res;
+      continue;
+    }
+    if (j.frame_offsets) std::memcpy(j.frame_offsets, foff, 8ull * (j.T + 1));
+    j.s->cur = 1 - j.s->cur;
+    j.s->frame += j.T;
+  }
+  read_kernel_times(ws, 3);
+  return first;
+}
+
+// ---------------------------------------------------------------- decode
+struct DecJob {
+  jiffy_stream* s;
+  uint32_t T;
+  const void* in;
+  size_t in_len;
+  const uint64_t* frame_offsets;  // host, T+1
+  void* const* planes_out;        // T*A device pointers
+  jiffy_status* status;           // host
+};
+
+jiffy_status run_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream_t st) {
+  const uint32_t n = (uint32_t)jobs.size();
+  unsigned long long items = 0;
+  uint32_t max_W = 1;
+  std::vector<jiffy_stream*> ss(n);
+  for (uint32_t i = 0; i < n; i++) {
+    DecJob& j = jobs[i];
+    *j.status = JIFFY_OK;
+    jiffy_stream* s = j.s;
+    ss[i] = s;
+    if (!s || !j.in || !j.frame_offsets || !j.planes_out || j.T == 0) return JIFFY_ERR_INVALID_ARG;
+    if (s->role != JIFFY_DECODER || s->ws.device != ws.device) return JIFFY_ERR_STATE;
+    if (reinterpret_cast<uintptr_t>(j.in) & 3u) return JIFFY_ERR_INVALID_ARG;
+    for (size_t q = 0; q < (size_t)j.T * s->A; q++)
+      if (!j.planes_out[q]) return JIFFY_ERR_INVALID_ARG;
+    // frame offsets: aligned, increasing by at least a frame header, inside `in`
+    const uint64_t* fo = j.frame_offsets;
+    const uint32_t fh = frame_header_bytes(s->A);
+    const uint64_t first = s->frame == 0 ? stream_header_bytes(s->A) : 0u;
+    jiffy_status bad = JIFFY_OK;
+    if (fo[0] < first) bad = JIFFY_ERR_CORRUPT;
+    for (uint32_t t = 0; t < j.T && bad == JIFFY_OK; t++) {
+      if ((fo[t] & 3u) || fo[t + 1] < fo[t] + fh) bad = JIFFY_ERR_CORRUPT;
+      else if (fo[t + 1] - fo[t] > 0xffffffffull) bad = JIFFY_ERR_CORRUPT;
+    }
+    if (fo[j.T] > j.in_len || (fo[j.T] & 3u)) bad = JIFFY_ERR_CORRUPT;
+    if (bad != JIFFY_OK) {
+      *j.status = bad;
+      return bad;
+    }
+    items += (unsigned long long)j.T * s->A * s->H;
+    if (s->W > max_W) max_W = s->W;
+  }
+  if (check_distinct(ss) != JIFFY_OK) return JIFFY_ERR_INVALID_ARG;
+  if (items > 0x7fffffffull) return JIFFY_ERR_INVALID_ARG;
+
+  Carver up;
+  const size_t u_seg = up.take(sizeof(jiffy::DecSeg) * n), u_ib = up.take(4ull * n);
+  std::vector<size_t> u_ptrs(n);
+  for (uint32_t i = 0; i < n; i++)
+    u_ptrs[i] = up.take(8ull * ((size_t)(jobs[i].T + 2) * jobs[i].s->A + jobs[i].T + 1));
+  Carver rs;
+  std::vector<size_t> r_err(n);
+  for (uint32_t i = 0; i < n; i++) r_err[i] = rs.take(8);
+  Carver c;
+  const size_t o_up = c.take(up.off);
+  const size_t o_zero = c.take(0);
+  const size_t o_done = c.take(4ull * items), o_tick = c.take(8);
+  const size_t o_res = c.take(rs.off);
+  const size_t zero_bytes = c.off - o_zero;
+  const size_t h_res = align_up(up.off, 256);
+  jiffy_status r = ensure_scratch(ws, c.off, h_res + rs.off);
+  if (r != JIFFY_OK) return r;
+  uint8_t* d = ws.d_scratch;
+  uint8_t* h = ws.h_pinned;
+
+  jiffy::DecSeg* segs = reinterpret_cast<jiffy::DecSeg*>(h + u_seg);
+  uint32_t* ib = reinterpret_cast<uint32_t*>(h + u_ib);
+  uint32_t item_base = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    DecJob& j = jobs[i];
+    jiffy_stream* s = j.s;
+    const uint32_t T = j.T, A = s->A;
+    uint64_t* hp = reinterpret_cast<uint64_t*>(h + u_ptrs[i]);
+    for (size_t q = 0; q < (size_t)T * A; q++) hp[q] = reinterpret_cast<uint64_t>(j.planes_out[q]);
+    for (uint32_t a = 0; a < A; a++) {
+      hp[(size_t)T * A + a] = reinterpret_cast<uint64_t>(s->d_state[s->cur] + s->plane_off[a]);
+      hp[(size_t)T * A + A + a] = reinterpret_cast<uint64_t>(s->d_state[1 - s->cur] + s->plane_off[a]);
+    }
+    std::memcpy(hp + (size_t)(T + 2) * A, j.frame_offsets, 8ull * (T + 1));
+    const uint8_t* dp = d + o_up + u_ptrs[i];
+    jiffy::DecSeg g{};
+    g.H = s->H;
+    g.W = s->W;
+    g.A = A;
+    g.T = T;
+    g.nw = (s->W + 31) / 32;
+    g.ncls = (g.nw + 15) / 16;
+    g.frame0 = s->frame;
+    g.fhdr = frame_header_bytes(A);
+    g.check_shdr = s->frame == 0;
+    g.item_base = item_base;
+    g.attrs = s->d_attrs;
+    g.in = static_cast<const uint8_t*>(j.in);
+    g.in_len = j.in_len;
+    g.outp = reinterpret_cast<uint8_t* const*>(dp);
+    g.state = reinterpret_cast<const uint8_t* const*>(dp + 8ull * T * A);
+    g.state_next = reinterpret_cast<uint8_t* const*>(dp + 8ull * (T + 1) * A);
+    g.off = reinterpret_cast<const unsigned long long*>(dp + 8ull * (T + 2) * A);
+    g.err = reinterpret_cast<uint32_t*>(d + o_res + r_err[i]);
+    segs[i] = g;
+    ib[i] = item_base;
+    item_base += T * A * s->H;
+  }
+  cudaError_t ce = cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, st);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, st);
+  if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
+
+  jiffy::DecParams p{};
+  p.n_seg = n;
+  p.n_items = (uint32_t)items;
+  p.max_W = max_W;
+  p.seg = reinterpret_cast<const jiffy::DecSeg*>(d + o_up + u_seg);
+  p.seg_item_base = reinterpret_cast<const uint32_t*>(d + o_up + u_ib);
+  p.done = reinterpret_cast<uint32_t*>(d + o_done);
+  p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
+  void* evs[2] = {ws.ev[0], ws.ev[1]};
+  if (jiffy::launch_decode(p, st, ws.profile ? evs : nullptr) != 0) return JIFFY_ERR_CUDA;
+
+  uint8_t* hres = h + h_res;
+  ce = cudaMemcpyAsync(hres, d + o_res, rs.off, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
+  jiffy_status first = JIFFY_OK;
+  for (uint32_t i = 0; i < n; i++) {
+    DecJob& j = jobs[i];
+    uint32_t err = 0;
+    std::memcpy(&err, hres + r_err[i], 4);
+    const jiffy_status res = map_device_error(err);
+    *j.status = res;
+    if (res != JIFFY_OK) {
+      if (first == JIFFY_OK) first = res;
+      continue;
+    }
+    j.s->cur = 1 - j.s->cur;
+    j.s->frame += j.T;
+  }
+  read_kernel_times(ws, 1);
+  return first;
+}
 
 }  // namespace
 
@@ -157,7 +515,7 @@ jiffy_status jiffy_stream_create(jiffy_stream** out, jiffy_role role, uint32_t H
   if (!g.ok) return JIFFY_ERR_CUDA;
   jiffy_stream* s = new (std::nothrow) jiffy_stream();
   if (!s) return JIFFY_ERR_NOMEM;
-  s->device = device;
+  s->ws.device = device;
   s->role = role;
   s->H = H;
   s->W = W;
@@ -196,15 +554,12 @@ jiffy_status jiffy_stream_create(jiffy_stream** out, jiffy_role role, uint32_t H
 
 void jiffy_stream_destroy(jiffy_stream* s) {
   if (!s) return;
-  DeviceGuard g(s->device);
+  DeviceGuard g(s->ws.device);
   cudaDeviceSynchronize();
   if (s->d_attrs) cudaFree(s->d_attrs);
   if (s->d_state[0]) cudaFree(s->d_state[0]);
   if (s->d_state[1]) cudaFree(s->d_state[1]);
-  if (s->d_scratch) cudaFree(s->d_scratch);
-  if (s->h_pinned) cudaFreeHost(s->h_pinned);
-  for (cudaEvent_t e : s->ev)
-    if (e) cudaEventDestroy(e);
+  release(s->ws);
   delete s;
 }
 
@@ -218,123 +573,23 @@ uint32_t jiffy_stream_frame_index(const jiffy_stream* s) { return s ? s->frame :
 
 jiffy_status jiffy_stream_set_profiling(jiffy_stream* s, int enable) {
   if (!s) return JIFFY_ERR_INVALID_ARG;
-  if (enable && !s->ev[0]) {
-    DeviceGuard g(s->device);
-    if (!g.ok) return JIFFY_ERR_CUDA;
-    for (cudaEvent_t& e : s->ev)
-      if (cudaEventCreate(&e) != cudaSuccess) return JIFFY_ERR_CUDA;
-  }
-  s->profile = enable != 0;
-  s->n_kernel_ms = 0;
-  return JIFFY_OK;
+  return set_profiling(s->ws, enable);
 }
 
 uint32_t jiffy_stream_kernel_times(const jiffy_stream* s, float* ms, uint32_t n) {
   if (!s) return 0;
-  for (uint32_t i = 0; i < n && i < s->n_kernel_ms; i++) ms[i] = s->kernel_ms[i];
-  return s->n_kernel_ms;
+  for (uint32_t i = 0; i < n && i < s->ws.n_kernel_ms; i++) ms[i] = s->ws.kernel_ms[i];
+  return s->ws.n_kernel_ms;
 }
 
 jiffy_status jiffy_encode_seq(jiffy_stream* s, uint32_t n_scans, const void* const* planes, void* out,
                               size_t out_capacity, uint64_t* frame_offsets, size_t* out_len, void* cuda_stream) {
-  if (!s || !planes || !out || !out_len || n_scans == 0) return JIFFY_ERR_INVALID_ARG;
-  if (s->role != JIFFY_ENCODER) return JIFFY_ERR_STATE;
-  if (reinterpret_cast<uintptr_t>(out) & 15u) return JIFFY_ERR_INVALID_ARG;
-  const uint32_t T = n_scans, A = s->A, H = s->H, W = s->W;
-  for (size_t i = 0; i < (size_t)T * A; i++)
-    if (!planes[i]) return JIFFY_ERR_INVALID_ARG;
-  const unsigned long long items = (unsigned long long)T * A * H;
-  if (items > 0x7fffffffull) return JIFFY_ERR_INVALID_ARG;
-  DeviceGuard g(s->device);
+  if (!s) return JIFFY_ERR_INVALID_ARG;
+  DeviceGuard g(s->ws.device);
   if (!g.ok) return JIFFY_ERR_CUDA;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-
-  // device scratch layout
-  Carver c;
-  const size_t o_cur = c.take(8ull * T * A), o_prev = c.take(8ull * T * A), o_next = c.take(8ull * A);
-  const size_t o_modes = c.take(4ull * T * A);
-  const size_t o_rb = c.take(4ull * items), o_rn = c.take(4ull * items), o_rc = c.take(4ull * items);
-  const size_t o_secb = c.take(8ull * T * A), o_secn = c.take(4ull * T * A);
-  const size_t o_zero = c.take(0);
-  const size_t o_stc = c.take(8ull * items), o_tick = c.take(8);
-  const size_t zero_bytes = c.off - o_zero;
-  const size_t o_foff = c.take(8ull * (T + 1));
-  const uint32_t slot_bytes = (jiffy::row_bound_bytes(W) + 15u) & ~15u;
-  const size_t o_slots = c.take((size_t)slot_bytes * items);
-  const size_t dev_bytes = c.off;
-  // pinned host layout: pointer arrays (upload), then results (download)
-  const size_t h_ptrs = 8ull * (2ull * T * A + A);
-  const size_t h_res = align_up(h_ptrs, 64);
-  const size_t host_bytes = h_res + 16 + 8ull * (T + 1);
-  jiffy_status rs = ensure_scratch(s, dev_bytes, host_bytes);
-  if (rs != JIFFY_OK) return rs;
-  uint8_t* d = s->d_scratch;
-  uint64_t* hp = reinterpret_cast<uint64_t*>(s->h_pinned);
-  for (uint32_t t = 0; t < T; t++) {
-    for (uint32_t a = 0; a < A; a++) {
-      hp[t * A + a] = reinterpret_cast<uint64_t>(planes[t * A + a]);
-      uint64_t prev = 0;
-      if (t > 0) prev = reinterpret_cast<uint64_t>(planes[(t - 1) * A + a]);
-      else if (s->frame > 0) prev = reinterpret_cast<uint64_t>(s->d_state[s->cur] + s->plane_off[a]);
-      hp[(size_t)T * A + t * A + a] = prev;
-    }
-  }
-  for (uint32_t a = 0; a < A; a++)
-    hp[2ull * T * A + a] = reinterpret_cast<uint64_t>(s->d_state[1 - s->cur] + s->plane_off[a]);
-
-  cudaError_t ce = cudaMemcpyAsync(d + o_cur, hp, 8ull * T * A, cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(d + o_prev, hp + (size_t)T * A, 8ull * T * A, cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(d + o_next, hp + 2ull * T * A, 8ull * A, cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, st);
-  if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
-
-  jiffy::EncParams p{};
-  p.H = H; p.W = W; p.A = A; p.T = T;
-  p.nw = (W + 31) / 32;
-  p.ncls = (p.nw + 15) / 16;
-  p.frame0 = s->frame;
-  p.shdr = s->frame == 0 ? stream_header_bytes(A) : 0u;
-  p.fhdr = frame_header_bytes(A);
-  p.test_lines = s->opt.test_lines;
-  p.force_mode = s->opt.force_mode;
-  p.n_items = (uint32_t)items;
-  p.attrs = s->d_attrs;
-  p.cur = reinterpret_cast<const uint8_t* const*>(d + o_cur);
-  p.prev = reinterpret_cast<const uint8_t* const*>(d + o_prev);
-  p.state_next = reinterpret_cast<uint8_t* const*>(d + o_next);
-  p.out = static_cast<uint8_t*>(out);
-  p.cap = out_capacity;
-  p.modes = reinterpret_cast<uint32_t*>(d + o_modes);
-  p.row_bytes = reinterpret_cast<uint32_t*>(d + o_rb);
-  p.row_nnz = reinterpret_cast<uint32_t*>(d + o_rn);
-  p.row_carry = reinterpret_cast<uint32_t*>(d + o_rc);
-  p.st_carry = reinterpret_cast<unsigned long long*>(d + o_stc);
-  p.slots = d + o_slots;
-  p.slot_bytes = slot_bytes;
-  p.sec_bytes = reinterpret_cast<unsigned long long*>(d + o_secb);
-  p.sec_nnz = reinterpret_cast<uint32_t*>(d + o_secn);
-  p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
-  p.err = reinterpret_cast<uint32_t*>(d + o_tick + 4);
-  p.frame_off = reinterpret_cast<unsigned long long*>(d + o_foff);
-  void* evs[4] = {s->ev[0], s->ev[1], s->ev[2], s->ev[3]};
-  if (jiffy::launch_encode(p, cuda_stream, s->profile ? evs : nullptr) != 0) return JIFFY_ERR_CUDA;
-
-  uint8_t* hr = s->h_pinned + h_res;
-  ce = cudaMemcpyAsync(hr, d + o_tick, 8, cudaMemcpyDeviceToHost, st);
-  if (ce == cudaSuccess) ce = cudaMemcpyAsync(hr + 16, d + o_foff, 8ull * (T + 1), cudaMemcpyDeviceToHost, st);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-  if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
-  uint32_t err = 0;
-  std::memcpy(&err, hr + 4, 4);
-  const uint64_t* foff = reinterpret_cast<const uint64_t*>(hr + 16);
-  jiffy_status res = map_device_error(err);
-  *out_len = foff[T];
-  if (res != JIFFY_OK) return res;
-  read_kernel_times(s, 3);
-  if (frame_offsets) std::memcpy(frame_offsets, foff, 8ull * (T + 1));
-  s->cur = 1 - s->cur;
-  s->frame += T;
-  return JIFFY_OK;
+  jiffy_status st = JIFFY_OK;
+  std::vector<EncJob> jobs{EncJob{s, n_scans, planes, out, out_capacity, frame_offsets, out_len, &st}};
+  return run_encode(s->ws, jobs, reinterpret_cast<cudaStream_t>(cuda_stream));
 }
 
 jiffy_status jiffy_encode(jiffy_stream* s, const void* const* planes, void* out, size_t out_capacity,
@@ -344,88 +599,12 @@ jiffy_status jiffy_encode(jiffy_stream* s, const void* const* planes, void* out,
 
 jiffy_status jiffy_decode_seq(jiffy_stream* s, uint32_t n_scans, const void* in, size_t in_len,
                               const uint64_t* frame_offsets, void* const* planes_out, void* cuda_stream) {
-  if (!s || !in || !frame_offsets || !planes_out || n_scans == 0) return JIFFY_ERR_INVALID_ARG;
-  if (s->role != JIFFY_DECODER) return JIFFY_ERR_STATE;
-  if (reinterpret_cast<uintptr_t>(in) & 3u) return JIFFY_ERR_INVALID_ARG;
-  const uint32_t T = n_scans, A = s->A, H = s->H, W = s->W;
-  for (size_t i = 0; i < (size_t)T * A; i++)
-    if (!planes_out[i]) return JIFFY_ERR_INVALID_ARG;
-  const unsigned long long items = (unsigned long long)T * A * H;
-  if (items > 0x7fffffffull) return JIFFY_ERR_INVALID_ARG;
-  // frame offsets: aligned, increasing by at least a frame header, inside `in`
-  const uint32_t fh = frame_header_bytes(A);
-  const uint64_t first = s->frame == 0 ? stream_header_bytes(A) : 0u;
-  if (frame_offsets[0] < first) return JIFFY_ERR_CORRUPT;
-  for (uint32_t t = 0; t < T; t++) {
-    if ((frame_offsets[t] & 3u) || frame_offsets[t + 1] < frame_offsets[t] + fh) return JIFFY_ERR_CORRUPT;
-    if (frame_offsets[t + 1] - frame_offsets[t] > 0xffffffffull) return JIFFY_ERR_CORRUPT;
-  }
-  if (frame_offsets[T] > in_len || (frame_offsets[T] & 3u)) return JIFFY_ERR_CORRUPT;
-  DeviceGuard g(s->device);
+  if (!s) return JIFFY_ERR_INVALID_ARG;
+  DeviceGuard g(s->ws.device);
   if (!g.ok) return JIFFY_ERR_CUDA;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-
-  Carver c;
-  const size_t o_out = c.take(8ull * T * A), o_state = c.take(8ull * A), o_next = c.take(8ull * A);
-  const size_t o_off = c.take(8ull * (T + 1));
-  const size_t o_zero = c.take(0);
-  const size_t o_done = c.take(4ull * items), o_tick = c.take(8);
-  const size_t zero_bytes = c.off - o_zero;
-  const size_t dev_bytes = c.off;
-  const size_t n_up = (size_t)T * A + 2ull * A + (T + 1);
-  const size_t h_res = align_up(8ull * n_up, 64);
-  jiffy_status rs = ensure_scratch(s, dev_bytes, h_res + 16);
-  if (rs != JIFFY_OK) return rs;
-  uint8_t* d = s->d_scratch;
-  uint64_t* hp = reinterpret_cast<uint64_t*>(s->h_pinned);
-  for (size_t i = 0; i < (size_t)T * A; i++) hp[i] = reinterpret_cast<uint64_t>(planes_out[i]);
-  for (uint32_t a = 0; a < A; a++) {
-    hp[(size_t)T * A + a] = reinterpret_cast<uint64_t>(s->d_state[s->cur] + s->plane_off[a]);
-    hp[(size_t)T * A + A + a] = reinterpret_cast<uint64_t>(s->d_state[1 - s->cur] + s->plane_off[a]);
-  }
-  std::memcpy(hp + (size_t)T * A + 2ull * A, frame_offsets, 8ull * (T + 1));
-  cudaError_t ce = cudaMemcpyAsync(d + o_out, hp, 8ull * T * A, cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(d + o_state, hp + (size_t)T * A, 8ull * A, cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(d + o_next, hp + (size_t)T * A + A, 8ull * A, cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(d + o_off, hp + (size_t)T * A + 2ull * A, 8ull * (T + 1), cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, st);
-  if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
-
-  jiffy::DecParams p{};
-  p.H = H; p.W = W; p.A = A; p.T = T;
-  p.nw = (W + 31) / 32;
-  p.ncls = (p.nw + 15) / 16;
-  p.frame0 = s->frame;
-  p.fhdr = fh;
-  p.check_shdr = s->frame == 0;
-  p.n_items = (uint32_t)items;
-  p.attrs = s->d_attrs;
-  p.in = static_cast<const uint8_t*>(in);
-  p.in_len = in_len;
-  p.off = reinterpret_cast<const unsigned long long*>(d + o_off);
-  p.outp = reinterpret_cast<uint8_t* const*>(d + o_out);
-  p.state = reinterpret_cast<const uint8_t* const*>(d + o_state);
-  p.state_next = reinterpret_cast<uint8_t* const*>(d + o_next);
-  p.done = reinterpret_cast<uint32_t*>(d + o_done);
-  p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
-  p.err = reinterpret_cast<uint32_t*>(d + o_tick + 4);
-  void* evs[2] = {s->ev[0], s->ev[1]};
-  if (jiffy::launch_decode(p, cuda_stream, s->profile ? evs : nullptr) != 0) return JIFFY_ERR_CUDA;
-  uint8_t* hr = s->h_pinned + h_res;
-  ce = cudaMemcpyAsync(hr, d + o_tick, 8, cudaMemcpyDeviceToHost, st);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-  if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
-  uint32_t err = 0;
-  std::memcpy(&err, hr + 4, 4);
-  jiffy_status res = map_device_error(err);
-  if (res != JIFFY_OK) return res;
-  read_kernel_times(s, 1);
-  s->cur = 1 - s->cur;
-  s->frame += T;
-  return JIFFY_OK;
+  jiffy_status st = JIFFY_OK;
+  std::vector<DecJob> jobs{DecJob{s, n_scans, in, in_len, frame_offsets, planes_out, &st}};
+  return run_decode(s->ws, jobs, reinterpret_cast<cudaStream_t>(cuda_stream));
 }
 
 jiffy_status jiffy_decode(jiffy_stream* s, const void* in, size_t in_len, void* const* planes_out,
@@ -433,6 +612,65 @@ jiffy_status jiffy_decode(jiffy_stream* s, const void* in, size_t in_len, void* 
   if (!s) return JIFFY_ERR_INVALID_ARG;
   const uint64_t off[2] = {s->frame == 0 ? stream_header_bytes(s->A) : 0u, in_len};
   return jiffy_decode_seq(s, 1, in, in_len, off, planes_out, cuda_stream);
+}
+
+jiffy_status jiffy_batch_create(jiffy_batch** out, int device) {
+  if (!out) return JIFFY_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return JIFFY_ERR_CUDA;
+  jiffy_batch* b = new (std::nothrow) jiffy_batch();
+  if (!b) return JIFFY_ERR_NOMEM;
+  b->ws.device = device;
+  *out = b;
+  return JIFFY_OK;
+}
+
+void jiffy_batch_destroy(jiffy_batch* b) {
+  if (!b) return;
+  DeviceGuard g(b->ws.device);
+  cudaDeviceSynchronize();
+  release(b->ws);
+  delete b;
+}
+
+jiffy_status jiffy_batch_set_profiling(jiffy_batch* b, int enable) {
+  if (!b) return JIFFY_ERR_INVALID_ARG;
+  return set_profiling(b->ws, enable);
+}
+
+uint32_t jiffy_batch_kernel_times(const jiffy_batch* b, float* ms, uint32_t n) {
+  if (!b) return 0;
+  for (uint32_t i = 0; i < n && i < b->ws.n_kernel_ms; i++) ms[i] = b->ws.kernel_ms[i];
+  return b->ws.n_kernel_ms;
+}
+
+jiffy_status jiffy_encode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams, const uint32_t* n_scans,
+                                const void* const* const* planes, void* const* outs, const size_t* caps,
+                                uint64_t* const* frame_offsets, size_t* out_lens, jiffy_status* statuses,
+                                void* cuda_stream) {
+  if (!b || n == 0 || !streams || !n_scans || !planes || !outs || !caps || !out_lens || !statuses)
+    return JIFFY_ERR_INVALID_ARG;
+  DeviceGuard g(b->ws.device);
+  if (!g.ok) return JIFFY_ERR_CUDA;
+  std::vector<EncJob> jobs(n);
+  for (uint32_t i = 0; i < n; i++)
+    jobs[i] = EncJob{streams[i], n_scans[i], planes[i], outs[i], caps[i],
+                     frame_offsets ? frame_offsets[i] : nullptr, &out_lens[i], &statuses[i]};
+  return run_encode(b->ws, jobs, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+jiffy_status jiffy_decode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams, const uint32_t* n_frames,
+                                const void* const* ins, const size_t* in_lens, const uint64_t* const* frame_offsets,
+                                void* const* const* planes_out, jiffy_status* statuses, void* cuda_stream) {
+  if (!b || n == 0 || !streams || !n_frames || !ins || !in_lens || !frame_offsets || !planes_out || !statuses)
+    return JIFFY_ERR_INVALID_ARG;
+  DeviceGuard g(b->ws.device);
+  if (!g.ok) return JIFFY_ERR_CUDA;
+  std::vector<DecJob> jobs(n);
+  for (uint32_t i = 0; i < n; i++)
+    jobs[i] = DecJob{streams[i], n_frames[i], ins[i], in_lens[i], frame_offsets[i], planes_out[i], &statuses[i]};
+  return run_decode(b->ws, jobs, reinterpret_cast<cudaStream_t>(cuda_stream));
 }
 
 }  // extern "C"

@@ -44,6 +44,17 @@ __device__ __forceinline__ uint32_t valid_word_bits(uint32_t W, uint32_t nw, uin
 
 __device__ __forceinline__ uint32_t literal_bits(uint32_t cwd) { return (cwd >> 1) & ~cwd & 0x55555555u; }
 
+// Index of the segment holding global row item key: the last i with base[i] <= key.
+__device__ __forceinline__ uint32_t find_seg(const uint32_t* base, uint32_t n, uint32_t key) {
+  uint32_t lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(base + mid) <= key) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 }  // namespace
 
 // Per-warp shared memory (byte offsets): the staged row chunk, a ring of
@@ -69,22 +80,24 @@ __host__ __device__ inline DecWarpLayout dec_warp_layout(uint32_t W) {
 // compact path).
 __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k, uint32_t* stage, uint32_t* ring,
                                             uint32_t* patch, uint8_t* mbytes) {
-  const uint32_t S = p.attrs[(k / p.H) % p.A].s;
+  const DecSeg& sg = p.seg[find_seg(p.seg_item_base, p.n_seg, k)];
   const uint32_t lane = lane_id();
-  const uint32_t H = p.H, W = p.W, A = p.A, nw = p.nw, ncls = p.ncls;
+  const uint32_t H = sg.H, W = sg.W, A = sg.A, nw = sg.nw, ncls = sg.ncls;
   const uint32_t niter = ceil_div_u32(W, 256u);
-  const uint32_t r = k % H, ta = k / H, a = ta % A, t = ta / A;
-  const AttrDev at = p.attrs[a];
+  const uint32_t kl = k - sg.item_base;  // item within the segment
+  const uint32_t r = kl % H, ta = kl / H, a = ta % A, t = ta / A;
+  const AttrDev at = sg.attrs[a];
+  const uint32_t S = at.s;
     const size_t rowb = (size_t)W * S;
 
   // ---- frame header and row-table entry; status 1 = malformed, 2 = timed out
-  const unsigned long long f0 = p.off[t], f1 = p.off[t + 1];
+  const unsigned long long f0 = sg.off[t], f1 = sg.off[t + 1];
   bool hbad = false;
   unsigned long long sb_before = 0, sb_total = 0;
   uint32_t my_mode = 0, my_sb = 0;
   for (uint32_t aa = lane; aa < A; aa += 32) {
-    const uint32_t m = ld_in_u32(p.in, f0 + 8ull + 12ull * aa);
-    const uint32_t sb = ld_in_u32(p.in, f0 + 12ull + 12ull * aa);
+    const uint32_t m = ld_in_u32(sg.in, f0 + 8ull + 12ull * aa);
+    const uint32_t sb = ld_in_u32(sg.in, f0 + 12ull + 12ull * aa);
     if ((m & 0xffffff00u) || (m & 0xffu) > 1u || sb < 8u * H || (sb & 3u)) hbad = true;
     sb_total += sb;
     if (aa < a) sb_before += sb;
@@ -101,29 +114,29 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   unsigned long long chunk_off = 0;
   if (lane == 0) {
     bool bad = hbad;
-    const uint32_t frame_bytes = ld_in_u32(p.in, f0);
-    const uint32_t scan = ld_in_u32(p.in, f0 + 4);
-    if (frame_bytes != f1 - f0 || scan != p.frame0 + t || sb_total + p.fhdr != frame_bytes) bad = true;
-    if (mode == 1u && p.frame0 + t == 0) bad = true;
+    const uint32_t frame_bytes = ld_in_u32(sg.in, f0);
+    const uint32_t scan = ld_in_u32(sg.in, f0 + 4);
+    if (frame_bytes != f1 - f0 || scan != sg.frame0 + t || sb_total + sg.fhdr != frame_bytes) bad = true;
+    if (mode == 1u && sg.frame0 + t == 0) bad = true;
     if (!bad) {
-      const unsigned long long sec = f0 + p.fhdr + sb_before;
+      const unsigned long long sec = f0 + sg.fhdr + sb_before;
       const uint32_t data_len = my_sb - 8u * H;
-      const uint32_t end = ld_in_u32(p.in, sec + 8ull * r);
-      carry = ld_in_u32(p.in, sec + 8ull * r + 4);
-      const uint32_t start = r ? ld_in_u32(p.in, sec + 8ull * (r - 1)) : 0u;
+      const uint32_t end = ld_in_u32(sg.in, sec + 8ull * r);
+      carry = ld_in_u32(sg.in, sec + 8ull * r + 4);
+      const uint32_t start = r ? ld_in_u32(sg.in, sec + 8ull * (r - 1)) : 0u;
       if (start > end || end > data_len || (r + 1 == H && end != data_len) || ((start | end) & 3u) ||
           end - start > row_bound_bytes(W) || end - start < 4u * ncls)
         bad = true;
       clen = end - start;
       chunk_off = sec + 8ull * H + start;
     }
-    if (k == 0 && p.check_shdr && !bad) {  // stream header: shape, dtypes, precisions
-      if (ld_in_u32(p.in, 0) != 0x3159464Au || ld_in_u32(p.in, 4) != (1u | (A << 16)) ||
-          ld_in_u32(p.in, 8) != H || ld_in_u32(p.in, 12) != W)
+    if (kl == 0 && sg.check_shdr && !bad) {  // stream header: shape, dtypes, precisions
+      if (ld_in_u32(sg.in, 0) != 0x3159464Au || ld_in_u32(sg.in, 4) != (1u | (A << 16)) ||
+          ld_in_u32(sg.in, 8) != H || ld_in_u32(sg.in, 12) != W)
         bad = true;
       for (uint32_t aa = 0; aa < A && !bad; aa++) {
-        if (ld_in_u32(p.in, 16 + 8ull * aa) != (p.attrs[aa].s | (1u << 8)) ||
-            ld_in_u32(p.in, 20 + 8ull * aa) != p.attrs[aa].P)
+        if (ld_in_u32(sg.in, 16 + 8ull * aa) != (sg.attrs[aa].s | (1u << 8)) ||
+            ld_in_u32(sg.in, 20 + 8ull * aa) != sg.attrs[aa].P)
           bad = true;
       }
     }
@@ -138,7 +151,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
           __nanosleep(ns);
           if (ns < 1024) ns <<= 1;
           if (global_timer_ns() - t0 > kSpinLimitNs) {
-            atomicOr(p.err, kErrTimeout);
+            atomicOr(sg.err, kErrTimeout);
             status = 2u;
             break;
           }
@@ -156,7 +169,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   bool bad = status != 0;
   // ---- stage the chunk in shared memory: one round of independent loads
   if (!bad) {
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(p.in + chunk_off);
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(sg.in + chunk_off);
     const uint32_t cw = clen / 4u;
     for (uint32_t i = lane; i < cw; i += 128u) {
       uint32_t v[4];
@@ -193,9 +206,9 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
     }
   }
 
-  uint8_t* orow = p.outp[ta] + r * rowb;
-  uint8_t* srow = (t + 1 == p.T) ? p.state_next[a] + r * rowb : nullptr;
-  const uint8_t* prow = mode == 1u ? (t > 0 ? p.outp[(t - 1) * A + a] : p.state[a]) + r * rowb : nullptr;
+  uint8_t* orow = sg.outp[ta] + r * rowb;
+  uint8_t* srow = (t + 1 == sg.T) ? sg.state_next[a] + r * rowb : nullptr;
+  const uint8_t* prow = mode == 1u ? (t > 0 ? sg.outp[(t - 1) * A + a] : sg.state[a]) + r * rowb : nullptr;
   const bool vec_prev = prow && vec_ok(prow, S);
   const bool vec_out = vec_ok(orow, S) && (!srow || vec_ok(srow, S));
 
@@ -339,7 +352,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
     }
     bad = xbad;
   }
-  if (lane == 0 && bad && status != 2u) atomicOr(p.err, kErrCorrupt);
+  if (lane == 0 && bad && status != 2u) atomicOr(sg.err, kErrCorrupt);
   __threadfence();
   __syncwarp();
   if (lane == 0) atomicExch(p.done + k, 1u);
@@ -349,7 +362,7 @@ template <int WPC>
 __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t lane = lane_id();
-  const DecWarpLayout lay = dec_warp_layout(p.W);
+  const DecWarpLayout lay = dec_warp_layout(p.max_W);
   uint8_t* wb = reinterpret_cast<uint8_t*>(smem) + warp_id() * lay.bytes;
   uint32_t* stage = reinterpret_cast<uint32_t*>(wb + lay.stage);
   uint32_t* ring = reinterpret_cast<uint32_t*>(wb + lay.ring);
@@ -371,7 +384,7 @@ size_t dec_smem_bytes_host(uint32_t W) { return dec_warp_layout(W).bytes; }
 
 template <int WPC>
 static int launch_decode_t(const DecParams& p, cudaStream_t st) {
-  const DecWarpLayout L = dec_warp_layout(p.W);
+  const DecWarpLayout L = dec_warp_layout(p.max_W);
   if (L.bytes & 15u) return (int)cudaErrorInvalidValue;  // per-warp regions must stay 16-byte aligned
   const size_t smem = (size_t)WPC * L.bytes;
   cudaError_t e = cudaFuncSetAttribute(k_decode<WPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -392,7 +405,7 @@ int launch_decode(const DecParams& p, void* stream, void* const* ev) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[0]), st);
   // warps per CTA from the per-warp shared memory (row-sized residual buffer)
-  const size_t per_warp = dec_warp_layout(p.W).bytes;
+  const size_t per_warp = dec_warp_layout(p.max_W).bytes;
   int rc;
   if (4 * per_warp <= 48 * 1024) rc = launch_decode_t<4>(p, st);
   else if (2 * per_warp <= 48 * 1024) rc = launch_decode_t<2>(p, st);

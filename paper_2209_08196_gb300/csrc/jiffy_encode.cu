@@ -1,20 +1,22 @@
 // Jiffy encoder kernels (sm_103a).
 //
-// One call codes T consecutive scans of one stream, all in parallel: the P
-// prediction of scan t uses the *input* of scan t-1 (Sec. III-D), so no scan
-// waits for another's output. Three launches:
-//   k_trial     one CTA per (scan, attribute): I/P choice by trial compression
-//               of a few scanlines, mask excluded (Sec. III-E, Sec. IV-E).
-//   k_encode    one CTA per (scan, attribute, row), taken in ticket order:
-//               quantize (Sec. III-B) -> zero bitmask by __ballot_sync
-//               (Sec. III-C) -> mask XOR with the previous scan for P
-//               (Sec. III-D) -> mask class code -> compaction -> residual ->
-//               delta carried across rows by a look-back -> ZigZag (Eq. 1) ->
-//               block width choice and funnel packing of 128-value blocks
-//               (Sec. II) in shared memory -> byte offset by decoupled
-//               look-back -> coalesced copy to the output.
-//   k_finalize  one CTA per frame: row tables, frame headers, stream header,
-//               frame offsets.
+// One call codes T consecutive scans of each of one or more streams (the
+// segments of the call), all in parallel: the P prediction of scan t uses the
+// *input* of scan t-1 (Sec. III-D), so no scan waits for another's output.
+// Four launches:
+//   k_trial      one CTA per section (scan, attribute): I/P choice by trial
+//                compression of a few scanlines, mask excluded (Sec. III-E,
+//                Sec. IV-E).
+//   k_encode     one warp per row item (scan, attribute, row), ticket order:
+//                stage the row -> quantize (Sec. III-B) -> zero bitmask
+//                (Sec. III-C) -> mask XOR with the previous scan for P
+//                (Sec. III-D) -> compaction -> residual -> delta (the carry
+//                from the previous row's tail, else a look-back) -> ZigZag
+//                (Eq. 1) -> block widths and packing of 128-value blocks
+//                (Sec. II) into the row's slot.
+//   k_sec_sizes  one CTA per section: its bytes and nonzero count.
+//   k_place      one CTA per section: offsets, row table, chunk copies, frame
+//                and stream headers.
 #include "jiffy_device.cuh"
 #include "jiffy_kernels.h"
 
@@ -110,6 +112,17 @@ __device__ __forceinline__ void load_block(const uint32_t* z, uint32_t n, uint32
   }
 }
 
+// Index of the segment holding global index key: the last i with base[i] <= key.
+__device__ __forceinline__ uint32_t find_seg(const uint32_t* base, uint32_t n, uint32_t key) {
+  uint32_t lo = 0, hi = n;  // base[lo] <= key < base[hi] (base[n] = infinity)
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(base + mid) <= key) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
 // ----------------------------------------------------------------------------
 // k_trial: Sec. III-E. For scans with a predecessor and no forced mode, codes
 // the test rows floor((2k+1)H/(2L)) (de-duplicated) both ways, the residuals
@@ -118,43 +131,45 @@ __device__ __forceinline__ void load_block(const uint32_t* z, uint32_t n, uint32
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) k_trial(EncParams p) {
   extern __shared__ __align__(16) uint32_t smem[];
-  uint32_t* eI = smem;
-  uint32_t* eP = smem + p.W;
   __shared__ uint32_t s_cnt[kWarps + 1];
   __shared__ unsigned long long s_cost[2];
   __shared__ uint32_t s_rows[kMaxTestLines];
   __shared__ uint32_t s_nrows;
   __shared__ uint32_t s_hist[kWarps][33];
 
-  const uint32_t ta = blockIdx.x;
-  const uint32_t t = ta / p.A, a = ta % p.A;
-  if (p.frame0 + t == 0 || p.force_mode == 0) {
-    if (threadIdx.x == 0) p.modes[ta] = 0;
+  const uint32_t gs = blockIdx.x;
+  const EncSeg& sg = p.seg[find_seg(p.seg_sec_base, p.n_seg, gs)];
+  const uint32_t ta = gs - sg.sec_base;
+  const uint32_t t = ta / sg.A, a = ta % sg.A;
+  uint32_t* eI = smem;
+  uint32_t* eP = smem + sg.W;
+  if (sg.frame0 + t == 0 || sg.force_mode == 0) {
+    if (threadIdx.x == 0) p.modes[gs] = 0;
     return;
   }
-  if (p.force_mode == 1) {
-    if (threadIdx.x == 0) p.modes[ta] = 1;
+  if (sg.force_mode == 1) {
+    if (threadIdx.x == 0) p.modes[gs] = 1;
     return;
   }
-  const AttrDev at = p.attrs[a];
+  const AttrDev at = sg.attrs[a];
   AttrDev pat = at;
   if (t == 0) { pat.P = 1; pat.qmax = 0xffffffffu; }  // previous scan stored quantized
   if (threadIdx.x == 0) {
     uint32_t n = 0;
-    for (uint32_t k = 0; k < p.test_lines; k++) {
-      uint32_t r = (uint32_t)(((unsigned long long)(2 * k + 1) * p.H) / (2ull * p.test_lines));
+    for (uint32_t k = 0; k < sg.test_lines; k++) {
+      uint32_t r = (uint32_t)(((unsigned long long)(2 * k + 1) * sg.H) / (2ull * sg.test_lines));
       if (n == 0 || s_rows[n - 1] != r) s_rows[n++] = r;
     }
     s_nrows = n;
     s_cost[0] = s_cost[1] = 0;
   }
   __syncthreads();
-  const size_t rowb = (size_t)p.W * at.s;
+  const size_t rowb = (size_t)sg.W * at.s;
   uint32_t carry_i = 0, carry_p = 0;  // flat vector starts from 0
   unsigned long long cost_i = 0, cost_p = 0;  // per-warp partial sums (lane 0)
   for (uint32_t ri = 0; ri < s_nrows; ri++) {
     const uint32_t r = s_rows[ri];
-    RowLoad L{p.cur[ta] + r * rowb, p.prev[ta] + r * rowb, at, pat, p.W, p.nw};
+    RowLoad L{sg.cur[ta] + r * rowb, sg.prev[ta] + r * rowb, at, pat, sg.W, sg.nw};
     uint32_t n = load_compact_row(L, true, true, false, eI, eP, nullptr, nullptr, s_cnt);
     // residuals -> delta -> ZigZag -> block costs, both modes
     const uint32_t nb = ceil_div_u32(n, kBlockN);
@@ -183,7 +198,7 @@ __global__ void __launch_bounds__(kThreads) k_trial(EncParams p) {
     atomicAdd(&s_cost[1], cost_p);
   }
   __syncthreads();
-  if (threadIdx.x == 0) p.modes[ta] = s_cost[1] < s_cost[0] ? 1u : 0u;
+  if (threadIdx.x == 0) p.modes[gs] = s_cost[1] < s_cost[0] ? 1u : 0u;
 }
 
 // ----------------------------------------------------------------------------
@@ -228,23 +243,25 @@ struct EncWarp {
 // One row item, samples of S bytes (compile-time, so each warp runs one
 // compact path).
 __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k, const EncWarp& w) {
-  const uint32_t S = p.attrs[(k / p.H) % p.A].s;
+  const EncSeg& sg = p.seg[find_seg(p.seg_item_base, p.n_seg, k)];
   const uint32_t lane = lane_id();
-  const uint32_t H = p.H, W = p.W, A = p.A, nw = p.nw, ncls = p.ncls;
+  const uint32_t H = sg.H, W = sg.W, A = sg.A, nw = sg.nw, ncls = sg.ncls;
   const uint32_t niter = ceil_div_u32(W, 256u);
   const uint32_t below = (1u << lane) - 1u;
   uint32_t* zbuf = w.zbuf;
   uint32_t* coded = w.coded;
-  const uint32_t r = k % H, ta = k / H, a = ta % A, t = ta / A;
-  const uint32_t sec_start = ta * H;  // first item of this attribute-scan
-  const AttrDev at = p.attrs[a];
+  const uint32_t kl = k - sg.item_base;  // item within the segment
+  const uint32_t r = kl % H, ta = kl / H, a = ta % A, t = ta / A;
+  const uint32_t sec_start = k - r;  // global item of row 0 of this attribute-scan
+  const AttrDev at = sg.attrs[a];
+  const uint32_t S = at.s;
   AttrDev pat = at;
   if (t == 0) { pat.P = 1; pat.qmax = 0xffffffffu; }  // the stored previous scan is already quantized
-  const uint32_t mode = p.modes[ta];
+  const uint32_t mode = p.modes[sg.sec_base + ta];
   const size_t rowb = (size_t)W * S;
-  const uint8_t* cur = p.cur[ta] + r * rowb;
-  const uint8_t* prv = mode ? p.prev[ta] + r * rowb : nullptr;
-  uint8_t* st_row = (t + 1 == p.T) ? p.state_next[a] + r * rowb : nullptr;
+  const uint8_t* cur = sg.cur[ta] + r * rowb;
+  const uint8_t* prv = mode ? sg.prev[ta] + r * rowb : nullptr;
+  uint8_t* st_row = (t + 1 == sg.T) ? sg.state_next[a] + r * rowb : nullptr;
   const bool vec_prv = prv && vec_ok(prv, S), vec_st = st_row && vec_ok(st_row, S);
 
   for (uint32_t j = lane; j < nw; j += 32) coded[j] = 0u;
@@ -375,7 +392,7 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
     const bool ok = lookback_last(p.st_carry, k, sec_start, carry);
     if (lane == 0) st_publish(p.st_carry + k, ok ? (kStInc | (1ull << 32) | (n ? last_e : carry)) : kStErr);
     if (!ok) {
-      if (lane == 0) atomicOr(p.err, kErrTimeout);
+      if (lane == 0) atomicOr(sg.err, kErrTimeout);
       return;
     }
   }
@@ -422,7 +439,7 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
     p.row_carry[k] = carry;
   }
   // the chunk goes to this row's slot; k_place moves it to its offset
-  uint32_t* dst = reinterpret_cast<uint32_t*>(p.slots + (size_t)k * p.slot_bytes);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(p.slots + sg.slot_base + (size_t)kl * sg.slot_bytes);
 
   // ---- mask part: 2-bit class per word (16 per class word), literals
   uint32_t litbase = 0;
@@ -492,7 +509,7 @@ template <int WPC>
 __global__ void __launch_bounds__(WPC * 32) k_encode(EncParams p) {
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t lane = lane_id();
-  const EncWarpLayout lay = enc_warp_layout(p.W);
+  const EncWarpLayout lay = enc_warp_layout(p.max_W);
   uint8_t* wb = reinterpret_cast<uint8_t*>(smem) + warp_id() * lay.bytes;
   EncWarp w;
   w.zbuf = reinterpret_cast<uint32_t*>(wb + lay.z);
@@ -537,17 +554,20 @@ __device__ __forceinline__ unsigned long long cta_sum_u64(unsigned long long v, 
 
 __global__ void __launch_bounds__(kThreads) k_sec_sizes(EncParams p) {
   __shared__ unsigned long long s_red[kWarps];
-  const uint32_t ta = blockIdx.x, H = p.H;
+  const uint32_t gs = blockIdx.x;
+  const EncSeg& sg = p.seg[find_seg(p.seg_sec_base, p.n_seg, gs)];
+  const uint32_t H = sg.H;
+  const uint32_t item0 = sg.item_base + (gs - sg.sec_base) * H;
   unsigned long long bytes = 0, nnz = 0;
   for (uint32_t r = threadIdx.x; r < H; r += kThreads) {
-    bytes += p.row_bytes[ta * H + r];
-    nnz += p.row_nnz[ta * H + r];
+    bytes += p.row_bytes[item0 + r];
+    nnz += p.row_nnz[item0 + r];
   }
   bytes = cta_sum_u64(bytes, s_red);
   nnz = cta_sum_u64(nnz, s_red);
   if (threadIdx.x == 0) {
-    p.sec_bytes[ta] = 8ull * H + bytes;
-    p.sec_nnz[ta] = (uint32_t)nnz;
+    p.sec_bytes[gs] = 8ull * H + bytes;
+    p.sec_nnz[gs] = (uint32_t)nnz;
   }
 }
 
@@ -555,72 +575,79 @@ __global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
   extern __shared__ __align__(16) uint32_t smem[];  // [H] row chunk starts
   __shared__ unsigned long long s_red[kWarps];
   __shared__ uint32_t s_tmp[kWarps + 1];
-  const uint32_t ta = blockIdx.x, H = p.H, A = p.A, t = ta / A, a = ta % A;
-  // bytes of the earlier sections: of earlier frames (frame_before) and of
-  // this frame's earlier attributes
+  const uint32_t gs = blockIdx.x;
+  const EncSeg& sg = p.seg[find_seg(p.seg_sec_base, p.n_seg, gs)];
+  const uint32_t H = sg.H, A = sg.A;
+  const uint32_t ta = gs - sg.sec_base, t = ta / A, a = ta % A;
+  const uint32_t item0 = sg.item_base + ta * H;
+  uint8_t* out = sg.out;
+  const unsigned long long cap = sg.cap;
+  // bytes of the segment's earlier sections: of earlier frames (frame_before)
+  // and of this frame's earlier attributes
   unsigned long long frame_before = 0, attr_before = 0;
   for (uint32_t i = threadIdx.x; i < ta; i += kThreads) {
-    if (i < t * A) frame_before += p.sec_bytes[i];
-    else attr_before += p.sec_bytes[i];
+    if (i < t * A) frame_before += p.sec_bytes[sg.sec_base + i];
+    else attr_before += p.sec_bytes[sg.sec_base + i];
   }
   frame_before = cta_sum_u64(frame_before, s_red);
   attr_before = cta_sum_u64(attr_before, s_red);
-  const unsigned long long frame_at = p.shdr + (unsigned long long)t * p.fhdr + frame_before;
-  const unsigned long long sec_at = frame_at + p.fhdr + attr_before;
+  const unsigned long long frame_at = sg.shdr + (unsigned long long)t * sg.fhdr + frame_before;
+  const unsigned long long sec_at = frame_at + sg.fhdr + attr_before;
   // row table: end offsets (prefix of chunk sizes) and carries
-  for (uint32_t r = threadIdx.x; r < H; r += kThreads) smem[r] = p.row_bytes[ta * H + r];
+  for (uint32_t r = threadIdx.x; r < H; r += kThreads) smem[r] = p.row_bytes[item0 + r];
   __syncthreads();
   const uint32_t data = block_excl_scan(smem, H, s_tmp);  // smem = row starts
   for (uint32_t r = threadIdx.x; r < H; r += kThreads) {
     const uint32_t end = (r + 1 < H) ? smem[r + 1] : data;
-    put_u32_guarded(p.out, p.cap, sec_at + 8ull * r, end, p.err);
-    put_u32_guarded(p.out, p.cap, sec_at + 8ull * r + 4, p.row_carry[ta * H + r], p.err);
+    put_u32_guarded(out, cap, sec_at + 8ull * r, end, sg.err);
+    put_u32_guarded(out, cap, sec_at + 8ull * r + 4, p.row_carry[item0 + r], sg.err);
   }
   // row chunks: warp per row, slot -> stream (4-byte aligned words)
   const unsigned long long data_at = sec_at + 8ull * H;
   for (uint32_t r = warp_id(); r < H; r += kWarps) {
-    const uint32_t words = p.row_bytes[ta * H + r] / 4u;
+    const uint32_t words = p.row_bytes[item0 + r] / 4u;
     const unsigned long long at = data_at + smem[r];
-    if (at + 4ull * words > p.cap) {
-      if (lane_id() == 0) atomicOr(p.err, kErrCapacity);
+    if (at + 4ull * words > cap) {
+      if (lane_id() == 0) atomicOr(sg.err, kErrCapacity);
       continue;
     }
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(p.slots + (size_t)(ta * H + r) * p.slot_bytes);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(p.out + at);
+    const uint32_t* src =
+        reinterpret_cast<const uint32_t*>(p.slots + sg.slot_base + (size_t)(ta * H + r) * sg.slot_bytes);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(out + at);
     for (uint32_t i = lane_id(); i < words; i += 32u) dst[i] = src[i];
   }
   if (a == 0 && threadIdx.x == 0) {
-    unsigned long long fbytes = p.fhdr;
-    for (uint32_t aa = 0; aa < A; aa++) fbytes += p.sec_bytes[t * A + aa];
-    put_u32_guarded(p.out, p.cap, frame_at, (uint32_t)fbytes, p.err);
-    put_u32_guarded(p.out, p.cap, frame_at + 4, p.frame0 + t, p.err);
+    const uint32_t f0 = sg.sec_base + t * A;
+    unsigned long long fbytes = sg.fhdr;
+    for (uint32_t aa = 0; aa < A; aa++) fbytes += p.sec_bytes[f0 + aa];
+    put_u32_guarded(out, cap, frame_at, (uint32_t)fbytes, sg.err);
+    put_u32_guarded(out, cap, frame_at + 4, sg.frame0 + t, sg.err);
     for (uint32_t aa = 0; aa < A; aa++) {
       const unsigned long long h = frame_at + 8ull + 12ull * aa;
-      put_u32_guarded(p.out, p.cap, h, p.modes[t * A + aa], p.err);
-      put_u32_guarded(p.out, p.cap, h + 4, (uint32_t)p.sec_bytes[t * A + aa], p.err);
-      put_u32_guarded(p.out, p.cap, h + 8, p.sec_nnz[t * A + aa], p.err);
+      put_u32_guarded(out, cap, h, p.modes[f0 + aa], sg.err);
+      put_u32_guarded(out, cap, h + 4, (uint32_t)p.sec_bytes[f0 + aa], sg.err);
+      put_u32_guarded(out, cap, h + 8, p.sec_nnz[f0 + aa], sg.err);
     }
-    p.frame_off[t] = frame_at;
-    if (t + 1 == p.T) p.frame_off[p.T] = frame_at + fbytes;
-    if (t == 0 && p.shdr) {
-      put_u32_guarded(p.out, p.cap, 0, 0x3159464Au, p.err);  // "JFY1"
-      put_u32_guarded(p.out, p.cap, 4, 1u | (A << 16), p.err);
-      put_u32_guarded(p.out, p.cap, 8, H, p.err);
-      put_u32_guarded(p.out, p.cap, 12, p.W, p.err);
+    sg.frame_off[t] = frame_at;
+    if (t + 1 == sg.T) sg.frame_off[sg.T] = frame_at + fbytes;
+    if (t == 0 && sg.shdr) {
+      put_u32_guarded(out, cap, 0, 0x3159464Au, sg.err);  // "JFY1"
+      put_u32_guarded(out, cap, 4, 1u | (A << 16), sg.err);
+      put_u32_guarded(out, cap, 8, H, sg.err);
+      put_u32_guarded(out, cap, 12, sg.W, sg.err);
       for (uint32_t aa = 0; aa < A; aa++) {
-        put_u32_guarded(p.out, p.cap, 16 + 8ull * aa, p.attrs[aa].s | (1u << 8), p.err);
-        put_u32_guarded(p.out, p.cap, 20 + 8ull * aa, p.attrs[aa].P, p.err);
+        put_u32_guarded(out, cap, 16 + 8ull * aa, sg.attrs[aa].s | (1u << 8), sg.err);
+        put_u32_guarded(out, cap, 20 + 8ull * aa, sg.attrs[aa].P, sg.err);
       }
     }
   }
 }
 
 size_t enc_smem_bytes_host(uint32_t W) { return enc_warp_layout(W).bytes; }
-size_t trial_smem_bytes_host(uint32_t W) { return 8ull * W; }
 
 template <int WPC>
 static cudaError_t launch_encode_rows(const EncParams& p, cudaStream_t st) {
-  const EncWarpLayout L = enc_warp_layout(p.W);
+  const EncWarpLayout L = enc_warp_layout(p.max_W);
   if ((L.coded | L.meta | L.hist | L.pbuf | L.bytes) & 15u)
     return cudaErrorInvalidValue;  // every per-warp region starts 16-byte aligned
   const size_t smem = (size_t)WPC * L.bytes;
@@ -640,24 +667,26 @@ static cudaError_t launch_encode_rows(const EncParams& p, cudaStream_t st) {
 
 int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const size_t s_trial = 8ull * p.W, s_place = 4ull * p.H;
+  const size_t s_trial = 8ull * p.max_W, s_place = 4ull * kMaxH;
   cudaError_t e = cudaFuncSetAttribute(k_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_trial);
   if (e != cudaSuccess) return (int)e;
   auto mark = [&](int i) {
     if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[i]), st);
   };
   mark(0);
-  k_trial<<<p.T * p.A, kThreads, s_trial, st>>>(p);
+  k_trial<<<p.n_sec, kThreads, s_trial, st>>>(p);
   mark(1);
   // warps per CTA from the per-warp shared memory (row-sized ZigZag buffer)
-  const size_t per_warp = enc_warp_layout(p.W).bytes;
+  const size_t per_warp = enc_warp_layout(p.max_W).bytes;
   if (4 * per_warp <= 100 * 1024) e = launch_encode_rows<4>(p, st);
   else if (2 * per_warp <= 100 * 1024) e = launch_encode_rows<2>(p, st);
   else e = launch_encode_rows<1>(p, st);
   if (e != cudaSuccess) return (int)e;
   mark(2);
-  k_sec_sizes<<<p.T * p.A, kThreads, 0, st>>>(p);
-  k_place<<<p.T * p.A, kThreads, s_place, st>>>(p);
+  e = cudaFuncSetAttribute(k_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_place);
+  if (e != cudaSuccess) return (int)e;
+  k_sec_sizes<<<p.n_sec, kThreads, 0, st>>>(p);
+  k_place<<<p.n_sec, kThreads, s_place, st>>>(p);
   mark(3);
   return (int)cudaGetLastError();
 }

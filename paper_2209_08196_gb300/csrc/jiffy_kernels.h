@@ -1,5 +1,11 @@
 // Launch parameters of the Jiffy kernels, shared by the kernels and the
 // host-side API in this directory.
+//
+// A call codes one or more segments: a segment is one stream's part of the
+// call (T consecutive scans of one stream). Row items (scan t, attribute a,
+// row r) and sections (scan t, attribute a) are numbered globally across the
+// segments of a call, segment after segment; each segment's items are
+// ordered (t, a, r).
 #pragma once
 
 #include <cstdint>
@@ -8,56 +14,75 @@
 
 namespace jiffy {
 
-struct EncParams {
+struct EncSeg {
   uint32_t H, W, A, T;
   uint32_t nw, ncls;             // mask words per row, class words per row
-  uint32_t frame0;               // scan index of the call's first frame
+  uint32_t frame0;               // scan index of the segment's first frame
   uint32_t shdr;                 // stream header bytes at the start of out (0 or 16 + 8A)
   uint32_t fhdr;                 // frame header bytes (8 + 12A)
   uint32_t test_lines;
   int32_t force_mode;
-  uint32_t n_items;              // T * A * H row items
+  uint32_t item_base;            // first global row item of the segment
+  uint32_t sec_base;             // first global section of the segment
+  uint32_t slot_bytes;           // per-row slot size (row_bound(W) rounded to 16)
+  unsigned long long slot_base;  // byte offset of the segment's first slot
   const AttrDev* attrs;          // [A]
   const uint8_t* const* cur;     // [T*A] current planes
   const uint8_t* const* prev;    // [T*A] previous planes: t = 0 -> stored q (or null), else raw t-1
   uint8_t* const* state_next;    // [A] receives q of the last scan
   uint8_t* out;
   unsigned long long cap;
-  uint32_t* modes;               // [T*A]
+  unsigned long long* frame_off; // [T+1]
+  uint32_t* err;                 // the segment's error word
+};
+
+struct EncParams {
+  uint32_t n_seg;
+  uint32_t n_items;              // row items of all segments
+  uint32_t n_sec;                // sections of all segments
+  uint32_t max_W;                // widest row (per-warp shared memory)
+  const EncSeg* seg;             // [n_seg]
+  const uint32_t* seg_item_base; // [n_seg] (search key for row items)
+  const uint32_t* seg_sec_base;  // [n_seg] (search key for sections)
+  uint32_t* modes;               // [n_sec]
   uint32_t* row_bytes;           // [n_items]
   uint32_t* row_nnz;             // [n_items]
   uint32_t* row_carry;           // [n_items]
   unsigned long long* st_carry;  // [n_items] look-back status (delta carry, fallback)
-  uint8_t* slots;                // [n_items * slot_bytes] each row's packed chunk
-  uint32_t slot_bytes;           // row_bound(W) rounded up to 16
-  unsigned long long* sec_bytes; // [T*A] section bytes (row table + chunks)
-  uint32_t* sec_nnz;             // [T*A]
+  uint8_t* slots;                // packed row chunks, slot_base + local item * slot_bytes
+  unsigned long long* sec_bytes; // [n_sec] section bytes (row table + chunks)
+  uint32_t* sec_nnz;             // [n_sec]
   uint32_t* ticket;
-  uint32_t* err;
-  unsigned long long* frame_off; // [T+1]
 };
 
-struct DecParams {
+struct DecSeg {
   uint32_t H, W, A, T;
   uint32_t nw, ncls;
   uint32_t frame0;
   uint32_t fhdr;
   uint32_t check_shdr;           // validate the stream header at in[0]
-  uint32_t n_items;
+  uint32_t item_base;
   const AttrDev* attrs;
   const uint8_t* in;
   unsigned long long in_len;
   const unsigned long long* off; // [T+1] frame offsets in `in`
   uint8_t* const* outp;          // [T*A] output planes
-  const uint8_t* const* state;   // [A] previous decoded planes (for the call's first frame)
+  const uint8_t* const* state;   // [A] previous decoded planes (for the segment's first frame)
   uint8_t* const* state_next;    // [A] receives the last frame's planes
+  uint32_t* err;                 // the segment's error word
+};
+
+struct DecParams {
+  uint32_t n_seg;
+  uint32_t n_items;
+  uint32_t max_W;
+  const DecSeg* seg;             // [n_seg]
+  const uint32_t* seg_item_base; // [n_seg]
   uint32_t* done;                // [n_items] row-done flags
   uint32_t* ticket;
-  uint32_t* err;
 };
 
 size_t enc_smem_bytes_host(uint32_t W);
-size_t trial_smem_bytes_host(uint32_t W);
 size_t dec_smem_bytes_host(uint32_t W);
 
 // Launchers (return a cudaError_t as int). ev: null, or events (cudaEvent_t

@@ -41,12 +41,15 @@ constexpr uint32_t kMaxDevices = 64;
 constexpr size_t kOffAttrs = 0;                                          // AttrDev[kNoAllocMaxAttr]
 constexpr size_t kOffPtrs = 1024;                                        // 3 x kNoAllocMaxAttr pointers
 constexpr size_t kOffFrameOff = kOffPtrs + 3 * kNoAllocMaxAttr * 8;      // 2 x u64 frame offsets
-constexpr size_t kOffZero = kOffFrameOff + 256;                          // cleared every call:
+constexpr size_t kOffSeg = kOffFrameOff + 256;                           // the call's one DecSeg
+constexpr size_t kOffSegKey = kOffSeg + 256;                             // its first item (0)
+constexpr size_t kOffZero = kOffSegKey + 256;                            // cleared every call:
 constexpr size_t kOffTicket = kOffZero;                                  //   ticket, error word
 constexpr size_t kOffDone = kOffZero + 256;                              //   row-done flags
 constexpr size_t kNoAllocScratchBytes = kOffDone + 4ull * kNoAllocMaxRows;
 
 static_assert(sizeof(AttrDev) * kNoAllocMaxAttr <= kOffPtrs, "attribute table overlaps");
+static_assert(sizeof(DecSeg) <= 256, "segment record overlaps");
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
@@ -127,24 +130,35 @@ extern "C" jiffy_status jiffy_decode_frame_noalloc(const void* in, size_t in_len
   if (ce == cudaSuccess) ce = cudaMemsetAsync(scratch + kOffZero, 0, kOffDone - kOffZero + 4ull * n_attr * H, st);
   if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
 
+  DecSeg g{};
+  g.H = H; g.W = W; g.A = n_attr; g.T = 1;
+  g.nw = (W + 31) / 32;
+  g.ncls = (g.nw + 15) / 16;
+  g.frame0 = scan_index;
+  g.fhdr = fhdr;
+  g.check_shdr = scan_index == 0;
+  g.item_base = 0;
+  g.attrs = reinterpret_cast<const AttrDev*>(scratch + kOffAttrs);
+  g.in = static_cast<const uint8_t*>(in);
+  g.in_len = in_len;
+  g.off = reinterpret_cast<const unsigned long long*>(scratch + kOffFrameOff);
+  g.outp = reinterpret_cast<uint8_t* const*>(scratch + kOffPtrs);
+  g.state = reinterpret_cast<const uint8_t* const*>(scratch + kOffPtrs + 8 * kNoAllocMaxAttr);
+  g.state_next = reinterpret_cast<uint8_t* const*>(scratch + kOffPtrs + 16 * kNoAllocMaxAttr);
+  g.err = reinterpret_cast<uint32_t*>(scratch + kOffTicket + 4);
+  const uint32_t key = 0;
+  cudaError_t ce2 = cudaMemcpyAsync(scratch + kOffSeg, &g, sizeof(g), cudaMemcpyHostToDevice, st);
+  if (ce2 == cudaSuccess) ce2 = cudaMemcpyAsync(scratch + kOffSegKey, &key, 4, cudaMemcpyHostToDevice, st);
+  if (ce2 != cudaSuccess) return JIFFY_ERR_CUDA;
+
   DecParams p{};
-  p.H = H; p.W = W; p.A = n_attr; p.T = 1;
-  p.nw = (W + 31) / 32;
-  p.ncls = (p.nw + 15) / 16;
-  p.frame0 = scan_index;
-  p.fhdr = fhdr;
-  p.check_shdr = scan_index == 0;
+  p.n_seg = 1;
   p.n_items = n_attr * H;
-  p.attrs = reinterpret_cast<const AttrDev*>(scratch + kOffAttrs);
-  p.in = static_cast<const uint8_t*>(in);
-  p.in_len = in_len;
-  p.off = reinterpret_cast<const unsigned long long*>(scratch + kOffFrameOff);
-  p.outp = reinterpret_cast<uint8_t* const*>(scratch + kOffPtrs);
-  p.state = reinterpret_cast<const uint8_t* const*>(scratch + kOffPtrs + 8 * kNoAllocMaxAttr);
-  p.state_next = reinterpret_cast<uint8_t* const*>(scratch + kOffPtrs + 16 * kNoAllocMaxAttr);
+  p.max_W = W;
+  p.seg = reinterpret_cast<const DecSeg*>(scratch + kOffSeg);
+  p.seg_item_base = reinterpret_cast<const uint32_t*>(scratch + kOffSegKey);
   p.done = reinterpret_cast<uint32_t*>(scratch + kOffDone);
   p.ticket = reinterpret_cast<uint32_t*>(scratch + kOffTicket);
-  p.err = reinterpret_cast<uint32_t*>(scratch + kOffTicket + 4);
   if (launch_decode(p, cuda_stream, nullptr) != 0) return JIFFY_ERR_CUDA;
 
   uint32_t res[2] = {0, 0};

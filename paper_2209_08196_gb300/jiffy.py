@@ -78,6 +78,21 @@ def _lib() -> ctypes.CDLL:
         L.jiffy_decode_frame_noalloc.restype = ctypes.c_int
         L.jiffy_decode_frame_noalloc.argtypes = [vp, sz, u32, u32, u32, ctypes.POINTER(_AttrDesc), u32,
                                                  ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+        L.jiffy_batch_create.restype = ctypes.c_int
+        L.jiffy_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+        L.jiffy_batch_destroy.restype = None
+        L.jiffy_batch_destroy.argtypes = [vp]
+        L.jiffy_batch_set_profiling.restype = ctypes.c_int
+        L.jiffy_batch_set_profiling.argtypes = [vp, ctypes.c_int]
+        L.jiffy_batch_kernel_times.restype = u32
+        L.jiffy_batch_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), u32]
+        pp = ctypes.POINTER(vp)
+        L.jiffy_encode_batch.restype = ctypes.c_int
+        L.jiffy_encode_batch.argtypes = [vp, u32, pp, ctypes.POINTER(u32), pp, pp, ctypes.POINTER(sz), pp,
+                                         ctypes.POINTER(sz), ctypes.POINTER(ctypes.c_int), vp]
+        L.jiffy_decode_batch.restype = ctypes.c_int
+        L.jiffy_decode_batch.argtypes = [vp, u32, pp, ctypes.POINTER(u32), pp, ctypes.POINTER(sz), pp, pp,
+                                         ctypes.POINTER(ctypes.c_int), vp]
         _L = L
     return _L
 
@@ -252,6 +267,110 @@ def jiffy_decode_frame_noalloc(buf: torch.Tensor, length: int, H: int, W: int, a
                                            prev, _ptr_array(planes_out), _stream_ptr(stream))
     if st != 0:
         raise JiffyError(st, "jiffy_decode_frame_noalloc")
+
+
+class Batch:
+    """An opaque jiffy_batch*: scratch of many-stream calls on one device."""
+
+    def __init__(self, ptr, device):
+        self.ptr, self.device = ptr, device
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _L is not None:
+            _L.jiffy_batch_destroy(self.ptr)
+            self.ptr = None
+
+
+def jiffy_batch_create(device: int = 0) -> Batch:
+    h = ctypes.c_void_p()
+    st = _lib().jiffy_batch_create(ctypes.byref(h), device)
+    if st != 0:
+        raise JiffyError(st, "jiffy_batch_create")
+    return Batch(h.value, device)
+
+
+def jiffy_batch_destroy(b: Batch):
+    if b.ptr:
+        _lib().jiffy_batch_destroy(b.ptr)
+        b.ptr = None
+
+
+def jiffy_batch_set_profiling(b: Batch, enable: bool = True):
+    st = _lib().jiffy_batch_set_profiling(b.ptr, int(bool(enable)))
+    if st != 0:
+        raise JiffyError(st, "jiffy_batch_set_profiling")
+
+
+def jiffy_batch_kernel_times(b: Batch):
+    buf = (ctypes.c_float * 8)()
+    n = _lib().jiffy_batch_kernel_times(b.ptr, buf, 8)
+    return [float(buf[i]) for i in range(min(n, 8))]
+
+
+class BatchError(JiffyError):
+    """A batched call failed for some streams; .statuses has one code per
+    stream (0 = that stream succeeded and advanced)."""
+
+    def __init__(self, status, what, statuses, required=None):
+        super().__init__(status, what)
+        self.statuses = list(statuses)
+        self.required = required
+
+
+def jiffy_encode_batch(b: Batch, handles, planes, outs, stream=None):
+    """Encodes, per stream i, the scans planes[i] (as for jiffy_encode_seq)
+    into outs[i], all streams in one pass. Returns a list of (bytes, frame
+    offsets) per stream."""
+    n = len(handles)
+    flats, keep = [], []
+    for h, pl in zip(handles, planes):
+        T, flat = _seq_planes(h, pl)
+        for i, p in enumerate(flat):
+            _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "plane %d" % i)
+        flats.append((T, flat))
+    streams = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
+    n_scans = (ctypes.c_uint32 * n)(*[T for T, _ in flats])
+    parr = [_ptr_array(flat) for _, flat in flats]
+    keep.append(parr)
+    planes_pp = (ctypes.c_void_p * n)(*[ctypes.cast(a, ctypes.c_void_p).value for a in parr])
+    outs_p = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    caps = (ctypes.c_size_t * n)(*[o.numel() * o.element_size() for o in outs])
+    offs = [(ctypes.c_uint64 * (T + 1))() for T, _ in flats]
+    offs_pp = (ctypes.c_void_p * n)(*[ctypes.cast(a, ctypes.c_void_p).value for a in offs])
+    lens = (ctypes.c_size_t * n)()
+    sts = (ctypes.c_int * n)()
+    st = _lib().jiffy_encode_batch(b.ptr, n, streams, n_scans, planes_pp, outs_p, caps, offs_pp, lens, sts,
+                                   _stream_ptr(stream))
+    if st != 0:
+        raise BatchError(st, "jiffy_encode_batch", list(sts), required=list(lens))
+    return [(lens[i], list(offs[i])) for i in range(n)]
+
+
+def jiffy_decode_batch(b: Batch, handles, bufs, lengths, offsets, planes_out, stream=None):
+    """Decodes, per stream i, the frames of bufs[i] (lengths[i] bytes, frame
+    offsets offsets[i]) into planes_out[i], all streams in one pass."""
+    n = len(handles)
+    flats = []
+    for h, pl, o in zip(handles, planes_out, offsets):
+        T, flat = _seq_planes(h, pl)
+        if len(o) != T + 1:
+            raise ValueError("need T + 1 frame offsets")
+        for i, p in enumerate(flat):
+            _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "output plane %d" % i)
+        flats.append((T, flat))
+    streams = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
+    n_frames = (ctypes.c_uint32 * n)(*[T for T, _ in flats])
+    ins = (ctypes.c_void_p * n)(*[x.data_ptr() for x in bufs])
+    lens = (ctypes.c_size_t * n)(*[int(x) for x in lengths])
+    offs = [(ctypes.c_uint64 * len(o))(*[int(v) for v in o]) for o in offsets]
+    offs_pp = (ctypes.c_void_p * n)(*[ctypes.cast(a, ctypes.c_void_p).value for a in offs])
+    parr = [_ptr_array(flat) for _, flat in flats]
+    planes_pp = (ctypes.c_void_p * n)(*[ctypes.cast(a, ctypes.c_void_p).value for a in parr])
+    sts = (ctypes.c_int * n)()
+    st = _lib().jiffy_decode_batch(b.ptr, n, streams, n_frames, ins, lens, offs_pp, planes_pp, sts,
+                                   _stream_ptr(stream))
+    if st != 0:
+        raise BatchError(st, "jiffy_decode_batch", list(sts))
 
 
 TORCH_DTYPE = {1: torch.uint8, 2: torch.int16, 4: torch.int32}
