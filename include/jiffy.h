@@ -176,6 +176,56 @@ jiffy_status jiffy_decode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const*
                                 const void* const* ins, const size_t* in_lens, const uint64_t* const* frame_offsets,
                                 void* const* const* planes_out, jiffy_status* statuses, void* cuda_stream);
 
+/* Enqueue-only forms of the two calls above: they return once the work is
+ * on cuda_stream, without waiting. The host arrays out_lens, frame_offsets
+ * and statuses must stay valid until jiffy_batch_wait(b) fills them; the
+ * streams count as advanced until then (jiffy_batch_wait rolls back those
+ * that failed) and may not take part in another call before it. A batch has
+ * at most one unfinished call (JIFFY_ERR_STATE otherwise). With two batch
+ * contexts the host can prepare and enqueue one call while the other runs. */
+jiffy_status jiffy_encode_batch_async(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams,
+                                      const uint32_t* n_scans, const void* const* const* planes,
+                                      void* const* outs, const size_t* caps, uint64_t* const* frame_offsets,
+                                      size_t* out_lens, jiffy_status* statuses, void* cuda_stream);
+jiffy_status jiffy_decode_batch_async(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams,
+                                      const uint32_t* n_frames, const void* const* ins, const size_t* in_lens,
+                                      const uint64_t* const* frame_offsets, void* const* const* planes_out,
+                                      jiffy_status* statuses, void* cuda_stream);
+
+/* Waits for the batch's unfinished call (if any) and reports its results as
+ * the synchronous call would: JIFFY_OK, or the first failing status. */
+jiffy_status jiffy_batch_wait(jiffy_batch* b);
+
+/* enable != 0: the batch captures its call's launch sequence (table upload,
+ * counter clearing, kernels, result download) in a CUDA graph and replays it
+ * while the calls keep the same shape (streams' H, W, attribute counts and
+ * scan counts, in order); the segment table, which holds the buffers and
+ * frame indices, is re-uploaded by the graph each time. Off by default;
+ * not used while profiling is on. */
+jiffy_status jiffy_batch_set_graphs(jiffy_batch* b, int enable);
+
+/* enable != 0: on the first call of each shape class (role, widest row,
+ * log2 of the row count) the batch times the rows kernel under each
+ * candidate launch configuration (warps per CTA, resident CTAs per SM, row
+ * items per ticket), repeating the call's kernels on the same inputs, and
+ * keeps the fastest for later calls of that class. Off by default. */
+jiffy_status jiffy_batch_set_autotune(jiffy_batch* b, int enable);
+
+/* Fixes the launch configuration of the role's rows kernel for the batch's
+ * later calls, over the tuner's choice: warps per CTA (encode 1, 2, 4;
+ * decode 1, 2, 4, 8), resident CTAs per SM, row items per ticket (decode
+ * only, <= 64). 0 leaves a field automatic; a request that does not fit the
+ * device falls back to the automatic choice. Every configuration codes the
+ * same bytes. */
+jiffy_status jiffy_batch_set_launch(jiffy_batch* b, jiffy_role role, uint32_t warps_per_cta,
+                                    uint32_t ctas_per_sm, uint32_t items_per_ticket);
+
+/* Counters and the last launch configuration, in this order: calls, graph
+ * captures, graph replays, tuning runs, tuned shape classes, last rows
+ * kernel's warps per CTA, CTAs per SM, items per ticket, grid. Writes
+ * min(n, 9) values to info (host). */
+jiffy_status jiffy_batch_info(const jiffy_batch* b, uint64_t* info, uint32_t n);
+
 /* Per-kernel device timing of the batch's calls, as for streams below. */
 jiffy_status jiffy_batch_set_profiling(jiffy_batch* b, int enable);
 uint32_t jiffy_batch_kernel_times(const jiffy_batch* b, float* ms, uint32_t n);
@@ -208,6 +258,18 @@ jiffy_status jiffy_decode_frame_noalloc(const void* in, size_t in_len, uint32_t 
                                         const jiffy_attr_desc* attrs, uint32_t scan_index,
                                         const void* const* prev_planes, void* const* planes_out,
                                         void* cuda_stream);
+
+/* Copies src's previous scan and frame counter into dst (same H, W and
+ * attributes, same device, any roles), so that dst continues src's stream.
+ * Encoders and decoders hold the same state, the previous scan as decoded
+ * (q * P, Sec. III-D), so a decoder can take over from an encoder (e.g. to
+ * decode the frame the encoder codes next) and the other way round.
+ * Neither stream may be in an unfinished call (JIFFY_ERR_STATE).
+ * Stream-ordered on cuda_stream; does not wait. */
+jiffy_status jiffy_stream_copy_state(jiffy_stream* dst, const jiffy_stream* src, void* cuda_stream);
+
+/* Device bytes the stream holds now (state, tables and its own scratch). */
+size_t jiffy_stream_device_bytes(const jiffy_stream* s);
 
 /* Frames coded since create/reset (the next frame's scan_index). */
 uint32_t jiffy_stream_frame_index(const jiffy_stream* s);

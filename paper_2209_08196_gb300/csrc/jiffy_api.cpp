@@ -2,24 +2,71 @@
 // device state and scratch, argument checks, kernel launches and status
 // mapping. Every step of the codec itself runs in the kernels of
 // jiffy_encode.cu and jiffy_decode.cu; this file only marshals pointers and
-// sizes. A call codes one segment per stream: jiffy_encode(_seq) and
-// jiffy_decode(_seq) are one-segment calls, the batch calls code many.
+// sizes, and schedules the launches.
+//
+// A call codes one segment per stream: jiffy_encode(_seq) and
+// jiffy_decode(_seq) are one-segment calls, the batch calls code many. A call
+// is enqueued (upload of the segment table, clearing of the counters, the
+// kernels, download of the per-segment results) and then finished (wait,
+// statuses, state roll-back of failed streams). Batch contexts can replay the
+// enqueued sequence from a captured CUDA graph and pick the rows kernels'
+// launch configuration by timing the candidates on the first call of a shape.
 #include "jiffy.h"
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <new>
 #include <vector>
 
 #include "jiffy_kernels.h"
 
 using jiffy::AttrDev;
+using jiffy::RowsLaunch;
 
 namespace {
 
-// Device scratch, pinned host staging and timing events of a handle.
+struct EncJob {
+  jiffy_stream* s;
+  uint32_t T;
+  const void* const* planes;  // T*A device pointers
+  void* out;
+  size_t cap;
+  uint64_t* frame_offsets;    // host, T+1, nullable
+  size_t* out_len;            // host
+  jiffy_status* status;       // host
+};
+
+struct DecJob {
+  jiffy_stream* s;
+  uint32_t T;
+  const void* in;
+  size_t in_len;
+  const uint64_t* frame_offsets;  // host, T+1
+  void* const* planes_out;        // T*A device pointers
+  jiffy_status* status;           // host
+};
+
+// A call enqueued on the device whose results are not read yet.
+struct Pending {
+  int kind = 0;  // 0 none, 1 encode, 2 decode
+  std::vector<EncJob> enc;
+  std::vector<DecJob> dec;
+  std::vector<size_t> r_err, r_off;  // offsets in the results image
+  uint8_t* hres = nullptr;           // results image (pinned)
+  uint32_t n_kernels = 0;            // timed kernels (0: none)
+};
+
+struct GraphCache {
+  std::vector<uint64_t> key;
+  cudaGraphExec_t exec = nullptr;
+};
+
+// Device scratch, pinned host staging, timing events, graph cache and tuned
+// launch configurations of a handle.
 struct Workspace {
   int device = 0;
   uint8_t* d_scratch = nullptr;
@@ -27,9 +74,19 @@ struct Workspace {
   uint8_t* h_pinned = nullptr;
   size_t pinned_cap = 0;
   bool profile = false;
+  bool graphs = false;
+  bool autotune = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t done = nullptr;
+  cudaStream_t capture = nullptr;
   float kernel_ms[3] = {0, 0, 0};
   uint32_t n_kernel_ms = 0;
+  GraphCache g_enc, g_dec;
+  std::map<std::vector<uint32_t>, RowsLaunch> tuned;
+  RowsLaunch last{};
+  RowsLaunch fixed[2] = {};  // launch requests set by the caller (encode, decode); 0 = automatic
+  uint64_t calls = 0, captures = 0, replays = 0, tunings = 0;
+  Pending pend;
 };
 
 }  // namespace
@@ -41,10 +98,12 @@ struct jiffy_stream {
   jiffy_options opt{4, -1};
   std::vector<AttrDev> attrs;
   AttrDev* d_attrs = nullptr;
-  uint8_t* d_state[2] = {nullptr, nullptr};  // previous scan, ping-pong
+  uint8_t* d_state[2] = {nullptr, nullptr};  // previous scan (as decoded, q * P), ping-pong
   std::vector<size_t> plane_off;              // byte offset of attribute a in a state buffer
+  size_t state_bytes = 0;
   int cur = 0;                                // state buffer holding the previous scan
   uint32_t frame = 0;                         // frames since create/reset
+  bool in_flight = false;                     // part of an enqueued, unfinished call
 };
 
 struct jiffy_batch {
@@ -82,8 +141,16 @@ uint64_t magic_for(uint32_t P) {
   return (~0ull) / P + 1ull;
 }
 
+void drop_graph(GraphCache& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  g.key.clear();
+}
+
 jiffy_status ensure_scratch(Workspace& w, size_t dev_bytes, size_t host_bytes) {
   if (dev_bytes > w.scratch_cap) {
+    drop_graph(w.g_enc);  // the captured sequences point into the old buffers
+    drop_graph(w.g_dec);
     if (w.d_scratch) cudaFree(w.d_scratch);
     w.d_scratch = nullptr;
     w.scratch_cap = 0;
@@ -92,6 +159,8 @@ jiffy_status ensure_scratch(Workspace& w, size_t dev_bytes, size_t host_bytes) {
     w.scratch_cap = cap;
   }
   if (host_bytes > w.pinned_cap) {
+    drop_graph(w.g_enc);
+    drop_graph(w.g_dec);
     if (w.h_pinned) cudaFreeHost(w.h_pinned);
     w.h_pinned = nullptr;
     w.pinned_cap = 0;
@@ -99,39 +168,37 @@ jiffy_status ensure_scratch(Workspace& w, size_t dev_bytes, size_t host_bytes) {
     if (cudaMallocHost(&w.h_pinned, cap) != cudaSuccess) return JIFFY_ERR_NOMEM;
     w.pinned_cap = cap;
   }
+  if (!w.done && cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming) != cudaSuccess) return JIFFY_ERR_CUDA;
   return JIFFY_OK;
 }
 
 void release(Workspace& w) {
+  drop_graph(w.g_enc);
+  drop_graph(w.g_dec);
   if (w.d_scratch) cudaFree(w.d_scratch);
   if (w.h_pinned) cudaFreeHost(w.h_pinned);
   for (cudaEvent_t e : w.ev)
     if (e) cudaEventDestroy(e);
+  if (w.done) cudaEventDestroy(w.done);
+  if (w.capture) cudaStreamDestroy(w.capture);
   w = Workspace{};
 }
 
+jiffy_status ensure_events(Workspace& w) {
+  if (w.ev[0]) return JIFFY_OK;
+  for (cudaEvent_t& e : w.ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return JIFFY_ERR_CUDA;
+  return JIFFY_OK;
+}
+
 jiffy_status set_profiling(Workspace& w, int enable) {
-  if (enable && !w.ev[0]) {
+  if (enable) {
     DeviceGuard g(w.device);
-    if (!g.ok) return JIFFY_ERR_CUDA;
-    for (cudaEvent_t& e : w.ev)
-      if (cudaEventCreate(&e) != cudaSuccess) return JIFFY_ERR_CUDA;
+    if (!g.ok || ensure_events(w) != JIFFY_OK) return JIFFY_ERR_CUDA;
   }
   w.profile = enable != 0;
   w.n_kernel_ms = 0;
   return JIFFY_OK;
-}
-
-// Reads the event intervals of the last call (after its synchronize).
-void read_kernel_times(Workspace& w, uint32_t n_kernels) {
-  w.n_kernel_ms = 0;
-  if (!w.profile) return;
-  for (uint32_t i = 0; i < n_kernels; i++) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, w.ev[i], w.ev[i + 1]) != cudaSuccess) return;
-    w.kernel_ms[i] = ms;
-  }
-  w.n_kernel_ms = n_kernels;
 }
 
 jiffy_status map_device_error(uint32_t err) {
@@ -145,18 +212,6 @@ uint32_t stream_header_bytes(uint32_t A) { return 16u + 8u * A; }
 uint32_t frame_header_bytes(uint32_t A) { return 8u + 12u * A; }
 uint32_t slot_bytes_for(uint32_t W) { return (jiffy::row_bound_bytes(W) + 15u) & ~15u; }
 
-// ---------------------------------------------------------------- encode
-struct EncJob {
-  jiffy_stream* s;
-  uint32_t T;
-  const void* const* planes;  // T*A device pointers
-  void* out;
-  size_t cap;
-  uint64_t* frame_offsets;    // host, T+1, nullable
-  size_t* out_len;            // host
-  jiffy_status* status;       // host
-};
-
 jiffy_status check_distinct(const std::vector<jiffy_stream*>& ss) {
   for (size_t i = 0; i < ss.size(); i++)
     for (size_t k = i + 1; k < ss.size(); k++)
@@ -164,8 +219,115 @@ jiffy_status check_distinct(const std::vector<jiffy_stream*>& ss) {
   return JIFFY_OK;
 }
 
-jiffy_status run_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream_t st) {
+uint32_t log2_ceil(uint64_t x) {
+  uint32_t l = 0;
+  while ((1ull << l) < x) l++;
+  return l;
+}
+
+// Candidate launch configurations of the rows kernels, tried by the tuner.
+std::vector<RowsLaunch> candidates(bool encode) {
+  std::vector<RowsLaunch> c;
+  const uint32_t wpcs_e[] = {4, 2, 1}, wpcs_d[] = {8, 4, 2, 1};
+  const uint32_t ctas[] = {0, 2, 1};
+  const uint32_t ipts[] = {1, 4, 16};
+  if (encode) {
+    for (uint32_t w : wpcs_e)
+      for (uint32_t k : ctas) c.push_back(RowsLaunch{w, k, 1, 0});
+  } else {
+    for (uint32_t w : wpcs_d)
+      for (uint32_t k : ctas)
+        for (uint32_t i : ipts) c.push_back(RowsLaunch{w, k, i, 0});
+  }
+  return c;
+}
+
+void apply_ticket(jiffy::EncParams&, uint32_t) {}
+void apply_ticket(jiffy::DecParams& p, uint32_t ipt) { p.items_per_ticket = ipt; }
+
+bool same_launch(const RowsLaunch& a, const RowsLaunch& b) {
+  return a.wpc == b.wpc && a.ctas_per_sm == b.ctas_per_sm && a.items_per_ticket == b.items_per_ticket &&
+         a.grid == b.grid;
+}
+
+// Runs `enqueue` (the whole call on stream st) for every distinct candidate
+// configuration, timing the rows kernel with the workspace's events between
+// ev[e0] and ev[e1]; returns the fastest candidate. The call's kernels are
+// idempotent: repeating them with the same inputs writes the same outputs.
+template <class Params, class Resolve, class Enqueue>
+jiffy_status tune(Workspace& ws, bool encode, const Params& p0, cudaStream_t st, Resolve resolve, Enqueue enqueue,
+                  RowsLaunch* best_cand) {
+  if (ensure_events(ws) != JIFFY_OK) return JIFFY_ERR_CUDA;
+  std::vector<RowsLaunch> seen;
+  float best = 1e30f;
+  *best_cand = RowsLaunch{0, 0, 0, 0};
+  const int e0 = encode ? 1 : 0, e1 = encode ? 2 : 1;
+  for (const RowsLaunch& c : candidates(encode)) {
+    Params p = p0;
+    p.wpc = c.wpc;
+    p.ctas_per_sm = c.ctas_per_sm;
+    apply_ticket(p, c.items_per_ticket);
+    RowsLaunch r{};
+    if (resolve(p, &r) != 0) continue;
+    bool dup = false;
+    for (const RowsLaunch& s : seen) dup |= same_launch(s, r);
+    if (dup) continue;
+    seen.push_back(r);
+    float t_min = 1e30f;
+    for (int rep = 0; rep < 2; rep++) {
+      void* evs[4] = {ws.ev[0], ws.ev[1], ws.ev[2], ws.ev[3]};
+      if (enqueue(st, p, evs) != 0) return JIFFY_ERR_CUDA;
+      if (cudaStreamSynchronize(st) != cudaSuccess) return JIFFY_ERR_CUDA;
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, ws.ev[e0], ws.ev[e1]) != cudaSuccess) return JIFFY_ERR_CUDA;
+      t_min = std::min(t_min, ms);
+    }
+    if (t_min < best) {
+      best = t_min;
+      *best_cand = c;
+    }
+  }
+  ws.tunings++;
+  return JIFFY_OK;
+}
+
+// Enqueues the call through the graph cache when graphs are on: replays the
+// captured sequence if the call's shape and buffers match the last capture,
+// else captures it anew on the workspace's capture stream.
+template <class Enqueue>
+jiffy_status run_sequence(Workspace& ws, GraphCache& gc, const std::vector<uint64_t>& key, cudaStream_t st,
+                          bool use_graph, Enqueue enqueue) {
+  if (!use_graph) return enqueue(st) == 0 ? JIFFY_OK : JIFFY_ERR_CUDA;
+  if (!(gc.exec && gc.key == key)) {
+    drop_graph(gc);
+    if (!ws.capture && cudaStreamCreateWithFlags(&ws.capture, cudaStreamNonBlocking) != cudaSuccess)
+      return JIFFY_ERR_CUDA;
+    if (cudaStreamBeginCapture(ws.capture, cudaStreamCaptureModeRelaxed) != cudaSuccess) return JIFFY_ERR_CUDA;
+    const int rc = enqueue(ws.capture);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(ws.capture, &graph);
+    if (rc != 0 || ce != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return JIFFY_ERR_CUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&gc.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      gc.exec = nullptr;
+      return JIFFY_ERR_CUDA;
+    }
+    gc.key = key;
+    ws.captures++;
+  } else {
+    ws.replays++;
+  }
+  return cudaGraphLaunch(gc.exec, st) == cudaSuccess ? JIFFY_OK : JIFFY_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- encode
+jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream_t st) {
   const uint32_t n = (uint32_t)jobs.size();
+  if (ws.pend.kind) return JIFFY_ERR_STATE;  // the previous call is not finished
   // ---- argument checks and totals
   unsigned long long items = 0, secs = 0;
   uint32_t max_W = 1;
@@ -176,7 +338,7 @@ jiffy_status run_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream_t s
     jiffy_stream* s = j.s;
     ss[i] = s;
     if (!s || !j.planes || !j.out || !j.out_len || j.T == 0) return JIFFY_ERR_INVALID_ARG;
-    if (s->role != JIFFY_ENCODER || s->ws.device != ws.device) return JIFFY_ERR_STATE;
+    if (s->role != JIFFY_ENCODER || s->ws.device != ws.device || s->in_flight) return JIFFY_ERR_STATE;
     if (reinterpret_cast<uintptr_t>(j.out) & 15u) return JIFFY_ERR_INVALID_ARG;
     for (size_t q = 0; q < (size_t)j.T * s->A; q++)
       if (!j.planes[q]) return JIFFY_ERR_INVALID_ARG;
@@ -228,6 +390,8 @@ jiffy_status run_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream_t s
   jiffy::EncSeg* segs = reinterpret_cast<jiffy::EncSeg*>(h + u_seg);
   uint32_t* ib = reinterpret_cast<uint32_t*>(h + u_ib);
   uint32_t* sb = reinterpret_cast<uint32_t*>(h + u_sb);
+  std::vector<uint64_t> key{1, n, (uint64_t)(uintptr_t)d, (uint64_t)(uintptr_t)h};
+  std::vector<uint32_t> sig{1, max_W, log2_ceil(items)};
   uint32_t item_base = 0, sec_base = 0;
   for (uint32_t i = 0; i < n; i++) {
     EncJob& j = jobs[i];
@@ -275,10 +439,9 @@ jiffy_status run_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream_t s
     sb[i] = sec_base;
     item_base += T * A * s->H;
     sec_base += T * A;
+    key.push_back(((uint64_t)s->H << 32) | s->W);
+    key.push_back(((uint64_t)A << 32) | T);
   }
-  cudaError_t ce = cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, st);
-  if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
 
   jiffy::EncParams p{};
   p.n_seg = n;
@@ -297,47 +460,59 @@ jiffy_status run_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream_t s
   p.sec_bytes = reinterpret_cast<unsigned long long*>(d + o_secb);
   p.sec_nnz = reinterpret_cast<uint32_t*>(d + o_secn);
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
-  void* evs[4] = {ws.ev[0], ws.ev[1], ws.ev[2], ws.ev[3]};
-  if (jiffy::launch_encode(p, st, ws.profile ? evs : nullptr) != 0) return JIFFY_ERR_CUDA;
-
   uint8_t* hres = h + h_res;
-  ce = cudaMemcpyAsync(hres, d + o_res, rs.off, cudaMemcpyDeviceToHost, st);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-  if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
-  jiffy_status first = JIFFY_OK;
-  for (uint32_t i = 0; i < n; i++) {
-    EncJob& j = jobs[i];
-    uint32_t err = 0;
-    std::memcpy(&err, hres + r_err[i], 4);
-    const uint64_t* foff = reinterpret_cast<const uint64_t*>(hres + r_off[i]);
-    const jiffy_status res = map_device_error(err);
-    *j.out_len = foff[j.T];
-    *j.status = res;
-    if (res != JIFFY_OK) {
-      if (first == JIFFY_OK) first = res;
-      continue;
+
+  // the whole call on one stream: upload, clear, kernels, results
+  auto enqueue = [&](cudaStream_t s, const jiffy::EncParams& pp, void* const* evs) -> int {
+    cudaError_t ce = cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, s);
+    if (ce != cudaSuccess) return (int)ce;
+    const int rc = jiffy::launch_encode(pp, s, evs);
+    if (rc != 0) return rc;
+    return (int)cudaMemcpyAsync(hres, d + o_res, rs.off, cudaMemcpyDeviceToHost, s);
+  };
+  if (ws.autotune) {
+    auto it = ws.tuned.find(sig);
+    if (it == ws.tuned.end()) {
+      RowsLaunch best{};
+      r = tune(ws, true, p, st, [](const jiffy::EncParams& pp, RowsLaunch* o) { return jiffy::encode_rows_launch(pp, o); },
+               enqueue, &best);
+      if (r != JIFFY_OK) return r;
+      it = ws.tuned.emplace(sig, best).first;
     }
-    if (j.frame_offsets) std::memcpy(j.frame_offsets, foff, 8ull * (j.T + 1));
+    p.wpc = it->second.wpc;
+    p.ctas_per_sm = it->second.ctas_per_sm;
+  }
+  if (ws.fixed[0].wpc) p.wpc = ws.fixed[0].wpc;
+  if (ws.fixed[0].ctas_per_sm) p.ctas_per_sm = ws.fixed[0].ctas_per_sm;
+  if (jiffy::encode_rows_launch(p, &ws.last) != 0) return JIFFY_ERR_CUDA;
+  key.push_back(((uint64_t)p.wpc << 32) | p.ctas_per_sm);
+  const bool timed = ws.profile;
+  void* evs[4] = {ws.ev[0], ws.ev[1], ws.ev[2], ws.ev[3]};
+  r = run_sequence(ws, ws.g_enc, key, st, ws.graphs && !timed,
+                   [&](cudaStream_t s) { return enqueue(s, p, timed ? evs : nullptr); });
+  if (r != JIFFY_OK) return r;
+  if (cudaEventRecord(ws.done, st) != cudaSuccess) return JIFFY_ERR_CUDA;
+  ws.calls++;
+  // the streams advance now; finish() rolls back those that failed
+  for (EncJob& j : jobs) {
     j.s->cur = 1 - j.s->cur;
     j.s->frame += j.T;
+    j.s->in_flight = true;
   }
-  read_kernel_times(ws, 3);
-  return first;
+  ws.pend.kind = 1;
+  ws.pend.enc = jobs;
+  ws.pend.r_err = r_err;
+  ws.pend.r_off = r_off;
+  ws.pend.hres = hres;
+  ws.pend.n_kernels = timed ? 3 : 0;
+  return JIFFY_OK;
 }
 
 // ---------------------------------------------------------------- decode
-struct DecJob {
-  jiffy_stream* s;
-  uint32_t T;
-  const void* in;
-  size_t in_len;
-  const uint64_t* frame_offsets;  // host, T+1
-  void* const* planes_out;        // T*A device pointers
-  jiffy_status* status;           // host
-};
-
-jiffy_status run_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream_t st) {
+jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream_t st) {
   const uint32_t n = (uint32_t)jobs.size();
+  if (ws.pend.kind) return JIFFY_ERR_STATE;
   unsigned long long items = 0;
   uint32_t max_W = 1;
   std::vector<jiffy_stream*> ss(n);
@@ -347,7 +522,7 @@ jiffy_status run_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream_t s
     jiffy_stream* s = j.s;
     ss[i] = s;
     if (!s || !j.in || !j.frame_offsets || !j.planes_out || j.T == 0) return JIFFY_ERR_INVALID_ARG;
-    if (s->role != JIFFY_DECODER || s->ws.device != ws.device) return JIFFY_ERR_STATE;
+    if (s->role != JIFFY_DECODER || s->ws.device != ws.device || s->in_flight) return JIFFY_ERR_STATE;
     if (reinterpret_cast<uintptr_t>(j.in) & 3u) return JIFFY_ERR_INVALID_ARG;
     for (size_t q = 0; q < (size_t)j.T * s->A; q++)
       if (!j.planes_out[q]) return JIFFY_ERR_INVALID_ARG;
@@ -394,6 +569,8 @@ jiffy_status run_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream_t s
 
   jiffy::DecSeg* segs = reinterpret_cast<jiffy::DecSeg*>(h + u_seg);
   uint32_t* ib = reinterpret_cast<uint32_t*>(h + u_ib);
+  std::vector<uint64_t> key{2, n, (uint64_t)(uintptr_t)d, (uint64_t)(uintptr_t)h};
+  std::vector<uint32_t> sig{2, max_W, log2_ceil(items)};
   uint32_t item_base = 0;
   for (uint32_t i = 0; i < n; i++) {
     DecJob& j = jobs[i];
@@ -429,10 +606,9 @@ jiffy_status run_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream_t s
     segs[i] = g;
     ib[i] = item_base;
     item_base += T * A * s->H;
+    key.push_back(((uint64_t)s->H << 32) | s->W);
+    key.push_back(((uint64_t)A << 32) | T);
   }
-  cudaError_t ce = cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, st);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, st);
-  if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
 
   jiffy::DecParams p{};
   p.n_seg = n;
@@ -442,29 +618,121 @@ jiffy_status run_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream_t s
   p.seg_item_base = reinterpret_cast<const uint32_t*>(d + o_up + u_ib);
   p.done = reinterpret_cast<uint32_t*>(d + o_done);
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
-  void* evs[2] = {ws.ev[0], ws.ev[1]};
-  if (jiffy::launch_decode(p, st, ws.profile ? evs : nullptr) != 0) return JIFFY_ERR_CUDA;
-
   uint8_t* hres = h + h_res;
-  ce = cudaMemcpyAsync(hres, d + o_res, rs.off, cudaMemcpyDeviceToHost, st);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-  if (ce != cudaSuccess) return JIFFY_ERR_CUDA;
-  jiffy_status first = JIFFY_OK;
-  for (uint32_t i = 0; i < n; i++) {
-    DecJob& j = jobs[i];
-    uint32_t err = 0;
-    std::memcpy(&err, hres + r_err[i], 4);
-    const jiffy_status res = map_device_error(err);
-    *j.status = res;
-    if (res != JIFFY_OK) {
-      if (first == JIFFY_OK) first = res;
-      continue;
+
+  auto enqueue = [&](cudaStream_t s, const jiffy::DecParams& pp, void* const* evs) -> int {
+    cudaError_t ce = cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, s);
+    if (ce != cudaSuccess) return (int)ce;
+    const int rc = jiffy::launch_decode(pp, s, evs);
+    if (rc != 0) return rc;
+    return (int)cudaMemcpyAsync(hres, d + o_res, rs.off, cudaMemcpyDeviceToHost, s);
+  };
+  if (ws.autotune) {
+    auto it = ws.tuned.find(sig);
+    if (it == ws.tuned.end()) {
+      RowsLaunch best{};
+      r = tune(ws, false, p, st, [](const jiffy::DecParams& pp, RowsLaunch* o) { return jiffy::decode_rows_launch(pp, o); },
+               enqueue, &best);
+      if (r != JIFFY_OK) return r;
+      it = ws.tuned.emplace(sig, best).first;
     }
+    p.wpc = it->second.wpc;
+    p.ctas_per_sm = it->second.ctas_per_sm;
+    p.items_per_ticket = it->second.items_per_ticket;
+  }
+  if (ws.fixed[1].wpc) p.wpc = ws.fixed[1].wpc;
+  if (ws.fixed[1].ctas_per_sm) p.ctas_per_sm = ws.fixed[1].ctas_per_sm;
+  if (ws.fixed[1].items_per_ticket) p.items_per_ticket = ws.fixed[1].items_per_ticket;
+  if (jiffy::decode_rows_launch(p, &ws.last) != 0) return JIFFY_ERR_CUDA;
+  key.push_back(((uint64_t)p.wpc << 32) | p.ctas_per_sm);
+  key.push_back(p.items_per_ticket);
+  const bool timed = ws.profile;
+  void* evs[2] = {ws.ev[0], ws.ev[1]};
+  r = run_sequence(ws, ws.g_dec, key, st, ws.graphs && !timed,
+                   [&](cudaStream_t s) { return enqueue(s, p, timed ? evs : nullptr); });
+  if (r != JIFFY_OK) return r;
+  if (cudaEventRecord(ws.done, st) != cudaSuccess) return JIFFY_ERR_CUDA;
+  ws.calls++;
+  for (DecJob& j : jobs) {
     j.s->cur = 1 - j.s->cur;
     j.s->frame += j.T;
+    j.s->in_flight = true;
   }
-  read_kernel_times(ws, 1);
+  ws.pend.kind = 2;
+  ws.pend.dec = jobs;
+  ws.pend.r_err = r_err;
+  ws.pend.hres = hres;
+  ws.pend.n_kernels = timed ? 1 : 0;
+  return JIFFY_OK;
+}
+
+// Waits for the pending call, reports per-stream results and rolls back the
+// streams that failed. Returns the first failing status.
+jiffy_status finish(Workspace& ws) {
+  Pending& pd = ws.pend;
+  if (!pd.kind) return JIFFY_OK;
+  const cudaError_t ce = cudaEventSynchronize(ws.done);
+  jiffy_status first = JIFFY_OK;
+  auto settle = [&](jiffy_stream* s, uint32_t T, jiffy_status res) {
+    s->in_flight = false;
+    if (res != JIFFY_OK) {
+      s->cur = 1 - s->cur;
+      s->frame -= T;
+      if (first == JIFFY_OK) first = res;
+    }
+  };
+  if (pd.kind == 1) {
+    for (size_t i = 0; i < pd.enc.size(); i++) {
+      EncJob& j = pd.enc[i];
+      uint32_t err = 0;
+      std::memcpy(&err, pd.hres + pd.r_err[i], 4);
+      const uint64_t* foff = reinterpret_cast<const uint64_t*>(pd.hres + pd.r_off[i]);
+      const jiffy_status res = ce != cudaSuccess ? JIFFY_ERR_CUDA : map_device_error(err);
+      *j.status = res;
+      if (ce == cudaSuccess) *j.out_len = foff[j.T];
+      if (res == JIFFY_OK && j.frame_offsets) std::memcpy(j.frame_offsets, foff, 8ull * (j.T + 1));
+      settle(j.s, j.T, res);
+    }
+  } else {
+    for (size_t i = 0; i < pd.dec.size(); i++) {
+      DecJob& j = pd.dec[i];
+      uint32_t err = 0;
+      std::memcpy(&err, pd.hres + pd.r_err[i], 4);
+      const jiffy_status res = ce != cudaSuccess ? JIFFY_ERR_CUDA : map_device_error(err);
+      *j.status = res;
+      settle(j.s, j.T, res);
+    }
+  }
+  ws.n_kernel_ms = 0;
+  if (pd.n_kernels && ce == cudaSuccess) {
+    uint32_t k = 0;
+    for (; k < pd.n_kernels; k++) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, ws.ev[k], ws.ev[k + 1]) != cudaSuccess) break;
+      ws.kernel_ms[k] = ms;
+    }
+    if (k == pd.n_kernels) ws.n_kernel_ms = k;
+  }
+  pd = Pending{};
   return first;
+}
+
+jiffy_status run_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream_t st) {
+  const jiffy_status r = enqueue_encode(ws, jobs, st);
+  return r != JIFFY_OK ? r : finish(ws);
+}
+
+jiffy_status run_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream_t st) {
+  const jiffy_status r = enqueue_decode(ws, jobs, st);
+  return r != JIFFY_OK ? r : finish(ws);
+}
+
+bool same_config(const jiffy_stream* a, const jiffy_stream* b) {
+  if (a->H != b->H || a->W != b->W || a->A != b->A) return false;
+  for (uint32_t i = 0; i < a->A; i++)
+    if (a->attrs[i].s != b->attrs[i].s || a->attrs[i].P != b->attrs[i].P) return false;
+  return true;
 }
 
 }  // namespace
@@ -533,6 +801,7 @@ jiffy_status jiffy_stream_create(jiffy_stream** out, jiffy_role role, uint32_t H
     s->plane_off.push_back(state_bytes);
     state_bytes = align_up(state_bytes + (size_t)H * W * d.s, 256);
   }
+  s->state_bytes = state_bytes;
   jiffy_status st = JIFFY_OK;
   if (cudaMalloc(&s->d_attrs, sizeof(AttrDev) * n_attr) != cudaSuccess ||
       cudaMalloc(&s->d_state[0], state_bytes) != cudaSuccess ||
@@ -565,11 +834,31 @@ void jiffy_stream_destroy(jiffy_stream* s) {
 
 jiffy_status jiffy_stream_reset(jiffy_stream* s) {
   if (!s) return JIFFY_ERR_INVALID_ARG;
+  if (s->in_flight) return JIFFY_ERR_STATE;
   s->frame = 0;
   return JIFFY_OK;
 }
 
 uint32_t jiffy_stream_frame_index(const jiffy_stream* s) { return s ? s->frame : 0u; }
+
+size_t jiffy_stream_device_bytes(const jiffy_stream* s) {
+  if (!s) return 0;
+  return 2 * s->state_bytes + sizeof(AttrDev) * s->A + s->ws.scratch_cap;
+}
+
+jiffy_status jiffy_stream_copy_state(jiffy_stream* dst, const jiffy_stream* src, void* cuda_stream) {
+  if (!dst || !src) return JIFFY_ERR_INVALID_ARG;
+  if (dst == src) return JIFFY_OK;
+  if (!same_config(dst, src) || dst->ws.device != src->ws.device) return JIFFY_ERR_INVALID_ARG;
+  if (dst->in_flight || src->in_flight) return JIFFY_ERR_STATE;
+  DeviceGuard g(dst->ws.device);
+  if (!g.ok) return JIFFY_ERR_CUDA;
+  if (cudaMemcpyAsync(dst->d_state[dst->cur], src->d_state[src->cur], src->state_bytes, cudaMemcpyDeviceToDevice,
+                      reinterpret_cast<cudaStream_t>(cuda_stream)) != cudaSuccess)
+    return JIFFY_ERR_CUDA;
+  dst->frame = src->frame;
+  return JIFFY_OK;
+}
 
 jiffy_status jiffy_stream_set_profiling(jiffy_stream* s, int enable) {
   if (!s) return JIFFY_ERR_INVALID_ARG;
@@ -629,6 +918,7 @@ jiffy_status jiffy_batch_create(jiffy_batch** out, int device) {
 void jiffy_batch_destroy(jiffy_batch* b) {
   if (!b) return;
   DeviceGuard g(b->ws.device);
+  finish(b->ws);
   cudaDeviceSynchronize();
   release(b->ws);
   delete b;
@@ -645,10 +935,46 @@ uint32_t jiffy_batch_kernel_times(const jiffy_batch* b, float* ms, uint32_t n) {
   return b->ws.n_kernel_ms;
 }
 
-jiffy_status jiffy_encode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams, const uint32_t* n_scans,
-                                const void* const* const* planes, void* const* outs, const size_t* caps,
-                                uint64_t* const* frame_offsets, size_t* out_lens, jiffy_status* statuses,
-                                void* cuda_stream) {
+jiffy_status jiffy_batch_set_graphs(jiffy_batch* b, int enable) {
+  if (!b) return JIFFY_ERR_INVALID_ARG;
+  if (b->ws.pend.kind) return JIFFY_ERR_STATE;
+  b->ws.graphs = enable != 0;
+  if (!b->ws.graphs) {
+    DeviceGuard g(b->ws.device);
+    drop_graph(b->ws.g_enc);
+    drop_graph(b->ws.g_dec);
+  }
+  return JIFFY_OK;
+}
+
+jiffy_status jiffy_batch_set_autotune(jiffy_batch* b, int enable) {
+  if (!b) return JIFFY_ERR_INVALID_ARG;
+  b->ws.autotune = enable != 0;
+  return JIFFY_OK;
+}
+
+jiffy_status jiffy_batch_set_launch(jiffy_batch* b, jiffy_role role, uint32_t warps_per_cta,
+                                    uint32_t ctas_per_sm, uint32_t items_per_ticket) {
+  if (!b || (role != JIFFY_ENCODER && role != JIFFY_DECODER)) return JIFFY_ERR_INVALID_ARG;
+  if (warps_per_cta > 8 || ctas_per_sm > 64 || items_per_ticket > 64) return JIFFY_ERR_INVALID_ARG;
+  if (b->ws.pend.kind) return JIFFY_ERR_STATE;
+  b->ws.fixed[role == JIFFY_ENCODER ? 0 : 1] = RowsLaunch{warps_per_cta, ctas_per_sm, items_per_ticket, 0};
+  return JIFFY_OK;
+}
+
+jiffy_status jiffy_batch_info(const jiffy_batch* b, uint64_t* info, uint32_t n) {
+  if (!b || (!info && n)) return JIFFY_ERR_INVALID_ARG;
+  const Workspace& w = b->ws;
+  const uint64_t v[9] = {w.calls, w.captures, w.replays, w.tunings, (uint64_t)w.tuned.size(),
+                         w.last.wpc, w.last.ctas_per_sm, w.last.items_per_ticket, w.last.grid};
+  for (uint32_t i = 0; i < n && i < 9; i++) info[i] = v[i];
+  return JIFFY_OK;
+}
+
+jiffy_status jiffy_encode_batch_async(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams,
+                                      const uint32_t* n_scans, const void* const* const* planes, void* const* outs,
+                                      const size_t* caps, uint64_t* const* frame_offsets, size_t* out_lens,
+                                      jiffy_status* statuses, void* cuda_stream) {
   if (!b || n == 0 || !streams || !n_scans || !planes || !outs || !caps || !out_lens || !statuses)
     return JIFFY_ERR_INVALID_ARG;
   DeviceGuard g(b->ws.device);
@@ -657,12 +983,13 @@ jiffy_status jiffy_encode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const*
   for (uint32_t i = 0; i < n; i++)
     jobs[i] = EncJob{streams[i], n_scans[i], planes[i], outs[i], caps[i],
                      frame_offsets ? frame_offsets[i] : nullptr, &out_lens[i], &statuses[i]};
-  return run_encode(b->ws, jobs, reinterpret_cast<cudaStream_t>(cuda_stream));
+  return enqueue_encode(b->ws, jobs, reinterpret_cast<cudaStream_t>(cuda_stream));
 }
 
-jiffy_status jiffy_decode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams, const uint32_t* n_frames,
-                                const void* const* ins, const size_t* in_lens, const uint64_t* const* frame_offsets,
-                                void* const* const* planes_out, jiffy_status* statuses, void* cuda_stream) {
+jiffy_status jiffy_decode_batch_async(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams,
+                                      const uint32_t* n_frames, const void* const* ins, const size_t* in_lens,
+                                      const uint64_t* const* frame_offsets, void* const* const* planes_out,
+                                      jiffy_status* statuses, void* cuda_stream) {
   if (!b || n == 0 || !streams || !n_frames || !ins || !in_lens || !frame_offsets || !planes_out || !statuses)
     return JIFFY_ERR_INVALID_ARG;
   DeviceGuard g(b->ws.device);
@@ -670,7 +997,31 @@ jiffy_status jiffy_decode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const*
   std::vector<DecJob> jobs(n);
   for (uint32_t i = 0; i < n; i++)
     jobs[i] = DecJob{streams[i], n_frames[i], ins[i], in_lens[i], frame_offsets[i], planes_out[i], &statuses[i]};
-  return run_decode(b->ws, jobs, reinterpret_cast<cudaStream_t>(cuda_stream));
+  return enqueue_decode(b->ws, jobs, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+jiffy_status jiffy_batch_wait(jiffy_batch* b) {
+  if (!b) return JIFFY_ERR_INVALID_ARG;
+  DeviceGuard g(b->ws.device);
+  if (!g.ok) return JIFFY_ERR_CUDA;
+  return finish(b->ws);
+}
+
+jiffy_status jiffy_encode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams, const uint32_t* n_scans,
+                                const void* const* const* planes, void* const* outs, const size_t* caps,
+                                uint64_t* const* frame_offsets, size_t* out_lens, jiffy_status* statuses,
+                                void* cuda_stream) {
+  const jiffy_status r = jiffy_encode_batch_async(b, n, streams, n_scans, planes, outs, caps, frame_offsets,
+                                                  out_lens, statuses, cuda_stream);
+  return r != JIFFY_OK ? r : jiffy_batch_wait(b);
+}
+
+jiffy_status jiffy_decode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams, const uint32_t* n_frames,
+                                const void* const* ins, const size_t* in_lens, const uint64_t* const* frame_offsets,
+                                void* const* const* planes_out, jiffy_status* statuses, void* cuda_stream) {
+  const jiffy_status r = jiffy_decode_batch_async(b, n, streams, n_frames, ins, in_lens, frame_offsets, planes_out,
+                                                  statuses, cuda_stream);
+  return r != JIFFY_OK ? r : jiffy_batch_wait(b);
 }
 
 }  // extern "C"

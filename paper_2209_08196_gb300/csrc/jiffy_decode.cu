@@ -32,7 +32,7 @@ namespace jiffy {
 
 namespace {
 
-constexpr uint32_t kDecBatch = 4;  // row items per ticket
+constexpr uint32_t kDecBatch = 4;  // row items per ticket unless the launch asks otherwise
 
 __device__ __forceinline__ uint32_t ld_in_u32(const uint8_t* in, unsigned long long at) {
   return __ldg(reinterpret_cast<const unsigned int*>(in + at));
@@ -370,10 +370,10 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
   uint8_t* mbytes = wb + lay.mbytes;
   while (true) {
     uint32_t kb = 0;
-    if (lane == 0) kb = atomicAdd(p.ticket, kDecBatch);
+    if (lane == 0) kb = atomicAdd(p.ticket, p.items_per_ticket);
     kb = __shfl_sync(0xffffffffu, kb, 0);
     if (kb >= p.n_items) break;
-    const uint32_t kend = min(kb + kDecBatch, p.n_items);
+    const uint32_t kend = min(kb + p.items_per_ticket, p.n_items);
     for (uint32_t k = kb; k < kend; k++) {
       decode_item(p, k, stage, ring, patch, mbytes);
     }
@@ -382,36 +382,60 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
 
 size_t dec_smem_bytes_host(uint32_t W) { return dec_warp_layout(W).bytes; }
 
+constexpr size_t kDecSmemAuto = 48 * 1024;  // per CTA when picking warps per CTA by itself
+constexpr size_t kDecSmemMax = 227 * 1024;
+
 template <int WPC>
-static int launch_decode_t(const DecParams& p, cudaStream_t st) {
-  const DecWarpLayout L = dec_warp_layout(p.max_W);
-  if (L.bytes & 15u) return (int)cudaErrorInvalidValue;  // per-warp regions must stay 16-byte aligned
-  const size_t smem = (size_t)WPC * L.bytes;
+static cudaError_t dec_occupancy(size_t smem, int* per_sm) {
   cudaError_t e = cudaFuncSetAttribute(k_decode<WPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return (int)e;
-  int dev = 0, sms = 0, per_sm = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_decode<WPC>, WPC * 32, smem)) != cudaSuccess)
-    return (int)e;
-  // enough warps to fill the GPU; warps beyond the work find the ticket spent
-  const uint32_t want = ceil_div_u32(p.n_items, kDecBatch * WPC);
-  const uint32_t grid = max(1u, min(want, (uint32_t)(max(per_sm, 1) * sms)));
-  k_decode<WPC><<<grid, WPC * 32, smem, st>>>(p);
-  return (int)cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_decode<WPC>, WPC * 32, smem);
 }
 
-int launch_decode(const DecParams& p, void* stream, void* const* ev) {
+int decode_rows_launch(const DecParams& p, RowsLaunch* out) {
+  const DecWarpLayout L = dec_warp_layout(p.max_W);
+  if (L.bytes & 15u) return (int)cudaErrorInvalidValue;  // per-warp regions must stay 16-byte aligned
+  uint32_t wpc = p.wpc;
+  if ((wpc != 1 && wpc != 2 && wpc != 4 && wpc != 8) || wpc * L.bytes > kDecSmemMax) wpc = 0;
+  if (!wpc) wpc = 4 * L.bytes <= kDecSmemAuto ? 4u : (2 * L.bytes <= kDecSmemAuto ? 2u : 1u);
+  const size_t smem = (size_t)wpc * L.bytes;
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    if (wpc == 8) e = dec_occupancy<8>(smem, &per_sm);
+    else if (wpc == 4) e = dec_occupancy<4>(smem, &per_sm);
+    else if (wpc == 2) e = dec_occupancy<2>(smem, &per_sm);
+    else e = dec_occupancy<1>(smem, &per_sm);
+  }
+  if (e != cudaSuccess) return (int)e;
+  uint32_t ctas = (uint32_t)max(per_sm, 1);
+  if (p.ctas_per_sm) ctas = min(ctas, p.ctas_per_sm);
+  const uint32_t ipt = p.items_per_ticket ? min(p.items_per_ticket, 64u) : kDecBatch;
+  // enough warps to fill the GPU; warps beyond the work find the ticket spent
+  const uint32_t want = ceil_div_u32(p.n_items, ipt * wpc);
+  out->wpc = wpc;
+  out->ctas_per_sm = ctas;
+  out->items_per_ticket = ipt;
+  out->grid = max(1u, min(want, ctas * (uint32_t)sms));
+  return 0;
+}
+
+int launch_decode(const DecParams& p0, void* stream, void* const* ev) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  RowsLaunch rl{};
+  int rc = decode_rows_launch(p0, &rl);
+  if (rc != 0) return rc;
+  DecParams p = p0;
+  p.items_per_ticket = rl.items_per_ticket;
+  const size_t smem = (size_t)rl.wpc * dec_warp_layout(p.max_W).bytes;
   if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[0]), st);
-  // warps per CTA from the per-warp shared memory (row-sized residual buffer)
-  const size_t per_warp = dec_warp_layout(p.max_W).bytes;
-  int rc;
-  if (4 * per_warp <= 48 * 1024) rc = launch_decode_t<4>(p, st);
-  else if (2 * per_warp <= 48 * 1024) rc = launch_decode_t<2>(p, st);
-  else rc = launch_decode_t<1>(p, st);
+  if (rl.wpc == 8) k_decode<8><<<rl.grid, 8 * 32, smem, st>>>(p);
+  else if (rl.wpc == 4) k_decode<4><<<rl.grid, 4 * 32, smem, st>>>(p);
+  else if (rl.wpc == 2) k_decode<2><<<rl.grid, 2 * 32, smem, st>>>(p);
+  else k_decode<1><<<rl.grid, 32, smem, st>>>(p);
   if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[1]), st);
-  return rc;
+  return (int)cudaGetLastError();
 }
 
 }  // namespace jiffy

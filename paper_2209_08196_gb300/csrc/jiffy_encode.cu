@@ -28,20 +28,19 @@ namespace jiffy {
 // samples into shared memory in row-major order.
 //   want_i / want_p: write I residuals (q) to eI and/or P residuals (q - pq)
 //   to eP. coded (nullable): receives per word M (mode I) or M ^ Mprev (P).
-//   st_row (nullable): receives q (state of the next call).
+//   Both rows hold raw samples (the stored previous scan is dequantized, and
+//   quantizing q * P gives q back), so one quantizer serves both.
 // Returns the row's nonzero count. Every thread calls it.
 // ----------------------------------------------------------------------------
 struct RowLoad {
   const uint8_t* cur;   // row of the current scan (raw samples)
   const uint8_t* prev;  // row of the previous scan, or null
-  AttrDev at;           // quantizer of cur
-  AttrDev pat;          // quantizer of prev (identity when prev is stored q)
+  AttrDev at;           // quantizer
   uint32_t W, nw;
 };
 
 __device__ uint32_t load_compact_row(const RowLoad& L, bool want_i, bool want_p, bool xor_prev,
-                                     uint32_t* eI, uint32_t* eP, uint32_t* coded, uint8_t* st_row,
-                                     uint32_t* s_cnt) {
+                                     uint32_t* eI, uint32_t* eP, uint32_t* coded, uint32_t* s_cnt) {
   const uint32_t lane = lane_id(), warp = warp_id();
   const uint32_t s = L.at.s;
   uint32_t total = 0;
@@ -63,8 +62,7 @@ __device__ uint32_t load_compact_row(const RowLoad& L, bool want_i, bool want_p,
       uint32_t x = j * 32u + lane;
       bool in = j < L.nw && x < L.W;
       uint32_t q = quantize(v[i], L.at);
-      uint32_t pq = L.prev ? quantize(pv[i], L.pat) : 0u;
-      if (st_row && in) store_sample(st_row, s, x, q);
+      uint32_t pq = L.prev ? quantize(pv[i], L.at) : 0u;
       uint32_t nz = __ballot_sync(0xffffffffu, in && q != 0u);
       if (coded) {
         uint32_t m = __ballot_sync(0xffffffffu, in && q == 0u);  // Sec. III-C: 1 = zero sample
@@ -152,8 +150,6 @@ __global__ void __launch_bounds__(kThreads) k_trial(EncParams p) {
     return;
   }
   const AttrDev at = sg.attrs[a];
-  AttrDev pat = at;
-  if (t == 0) { pat.P = 1; pat.qmax = 0xffffffffu; }  // previous scan stored quantized
   if (threadIdx.x == 0) {
     uint32_t n = 0;
     for (uint32_t k = 0; k < sg.test_lines; k++) {
@@ -169,8 +165,8 @@ __global__ void __launch_bounds__(kThreads) k_trial(EncParams p) {
   unsigned long long cost_i = 0, cost_p = 0;  // per-warp partial sums (lane 0)
   for (uint32_t ri = 0; ri < s_nrows; ri++) {
     const uint32_t r = s_rows[ri];
-    RowLoad L{sg.cur[ta] + r * rowb, sg.prev[ta] + r * rowb, at, pat, sg.W, sg.nw};
-    uint32_t n = load_compact_row(L, true, true, false, eI, eP, nullptr, nullptr, s_cnt);
+    RowLoad L{sg.cur[ta] + r * rowb, sg.prev[ta] + r * rowb, at, sg.W, sg.nw};
+    uint32_t n = load_compact_row(L, true, true, false, eI, eP, nullptr, s_cnt);
     // residuals -> delta -> ZigZag -> block costs, both modes
     const uint32_t nb = ceil_div_u32(n, kBlockN);
     for (uint32_t blk = warp_id(); blk < 2 * nb; blk += kWarps) {
@@ -255,8 +251,6 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   const uint32_t sec_start = k - r;  // global item of row 0 of this attribute-scan
   const AttrDev at = sg.attrs[a];
   const uint32_t S = at.s;
-  AttrDev pat = at;
-  if (t == 0) { pat.P = 1; pat.qmax = 0xffffffffu; }  // the stored previous scan is already quantized
   const uint32_t mode = p.modes[sg.sec_base + ta];
   const size_t rowb = (size_t)W * S;
   const uint8_t* cur = sg.cur[ta] + r * rowb;
@@ -295,7 +289,7 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
 #pragma unroll
     for (int i = 0; i < 8; i++) {
       const uint32_t q = quantize(tv[i], at);
-      const uint32_t pq = prv ? quantize(tpv[i], pat) : 0u;
+      const uint32_t pq = prv ? quantize(tpv[i], at) : 0u;
       if ((uint32_t)i < pnv && q != 0u) {
         tnz = 1u;
         tlast = q - pq;
@@ -325,12 +319,17 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
     for (int i = 0; i < 8; i++) {
       const uint32_t q = quantize(v[i], at);
       v[i] = q;
-      const uint32_t pq = prv ? quantize(pv[i], pat) : 0u;
+      const uint32_t pq = prv ? quantize(pv[i], at) : 0u;
       mb |= (uint32_t)((uint32_t)i < nv && q == 0u) << i;
       pm |= (uint32_t)((uint32_t)i < nv && pq == 0u) << i;
       e[i] = q - pq;  // I: q (pq = 0); P: q - pq, modulo 2^32
     }
-    if (st_row && nv) store8(st_row, S, x0, nv, vec_st, v);
+    if (st_row && nv) {  // the next call's previous scan, dequantized as the decoder holds it
+      uint32_t sv[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) sv[i] = v[i] * at.P;
+      store8(st_row, S, x0, nv, vec_st, sv);
+    }
     if (nv) w.coded_b[x0 >> 3] = (uint8_t)(mode ? (mb ^ pm) : mb);
     const uint32_t nz = ~mb & ((1u << nv) - 1u);
     const uint32_t c = __popc(nz);
@@ -645,30 +644,52 @@ __global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
 
 size_t enc_smem_bytes_host(uint32_t W) { return enc_warp_layout(W).bytes; }
 
+constexpr size_t kRowsSmemAuto = 100 * 1024;  // per CTA when picking warps per CTA by itself
+constexpr size_t kRowsSmemMax = 227 * 1024;
+
 template <int WPC>
-static cudaError_t launch_encode_rows(const EncParams& p, cudaStream_t st) {
-  const EncWarpLayout L = enc_warp_layout(p.max_W);
-  if ((L.coded | L.meta | L.hist | L.pbuf | L.bytes) & 15u)
-    return cudaErrorInvalidValue;  // every per-warp region starts 16-byte aligned
-  const size_t smem = (size_t)WPC * L.bytes;
+static cudaError_t rows_occupancy(size_t smem, int* per_sm) {
   cudaError_t e = cudaFuncSetAttribute(k_encode<WPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_encode<WPC>, WPC * 32, smem);
+}
+
+int encode_rows_launch(const EncParams& p, RowsLaunch* out) {
+  const EncWarpLayout L = enc_warp_layout(p.max_W);
+  if ((L.coded | L.meta | L.hist | L.pbuf | L.bytes) & 15u)
+    return (int)cudaErrorInvalidValue;  // every per-warp region starts 16-byte aligned
+  uint32_t wpc = p.wpc;
+  if ((wpc != 1 && wpc != 2 && wpc != 4) || wpc * L.bytes > kRowsSmemMax) wpc = 0;
+  if (!wpc) wpc = 4 * L.bytes <= kRowsSmemAuto ? 4u : (2 * L.bytes <= kRowsSmemAuto ? 2u : 1u);
+  const size_t smem = (size_t)wpc * L.bytes;
   int dev = 0, sms = 0, per_sm = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_encode<WPC>, WPC * 32, smem)) != cudaSuccess)
-    return e;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) {
+    if (wpc == 4) e = rows_occupancy<4>(smem, &per_sm);
+    else if (wpc == 2) e = rows_occupancy<2>(smem, &per_sm);
+    else e = rows_occupancy<1>(smem, &per_sm);
+  }
+  if (e != cudaSuccess) return (int)e;
+  uint32_t ctas = (uint32_t)max(per_sm, 1);
+  if (p.ctas_per_sm) ctas = min(ctas, p.ctas_per_sm);
   // enough warps to fill the GPU; warps beyond the work find the ticket spent
-  const uint32_t want = ceil_div_u32(p.n_items, WPC);
-  const uint32_t grid = max(1u, min(want, (uint32_t)(max(per_sm, 1) * sms)));
-  k_encode<WPC><<<grid, WPC * 32, smem, st>>>(p);
-  return cudaGetLastError();
+  const uint32_t want = ceil_div_u32(p.n_items, wpc);
+  out->wpc = wpc;
+  out->ctas_per_sm = ctas;
+  out->items_per_ticket = 1;
+  out->grid = max(1u, min(want, ctas * (uint32_t)sms));
+  return 0;
 }
 
 int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const size_t s_trial = 8ull * p.max_W, s_place = 4ull * kMaxH;
+  RowsLaunch rl{};
+  int rc = encode_rows_launch(p, &rl);
+  if (rc != 0) return rc;
   cudaError_t e = cudaFuncSetAttribute(k_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_trial);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_place);
   if (e != cudaSuccess) return (int)e;
   auto mark = [&](int i) {
     if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[i]), st);
@@ -676,15 +697,11 @@ int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   mark(0);
   k_trial<<<p.n_sec, kThreads, s_trial, st>>>(p);
   mark(1);
-  // warps per CTA from the per-warp shared memory (row-sized ZigZag buffer)
-  const size_t per_warp = enc_warp_layout(p.max_W).bytes;
-  if (4 * per_warp <= 100 * 1024) e = launch_encode_rows<4>(p, st);
-  else if (2 * per_warp <= 100 * 1024) e = launch_encode_rows<2>(p, st);
-  else e = launch_encode_rows<1>(p, st);
-  if (e != cudaSuccess) return (int)e;
+  const size_t smem = (size_t)rl.wpc * enc_warp_layout(p.max_W).bytes;
+  if (rl.wpc == 4) k_encode<4><<<rl.grid, 4 * 32, smem, st>>>(p);
+  else if (rl.wpc == 2) k_encode<2><<<rl.grid, 2 * 32, smem, st>>>(p);
+  else k_encode<1><<<rl.grid, 32, smem, st>>>(p);
   mark(2);
-  e = cudaFuncSetAttribute(k_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_place);
-  if (e != cudaSuccess) return (int)e;
   k_sec_sizes<<<p.n_sec, kThreads, 0, st>>>(p);
   k_place<<<p.n_sec, kThreads, s_place, st>>>(p);
   mark(3);

@@ -28,8 +28,8 @@ struct EncSeg {
   unsigned long long slot_base;  // byte offset of the segment's first slot
   const AttrDev* attrs;          // [A]
   const uint8_t* const* cur;     // [T*A] current planes
-  const uint8_t* const* prev;    // [T*A] previous planes: t = 0 -> stored q (or null), else raw t-1
-  uint8_t* const* state_next;    // [A] receives q of the last scan
+  const uint8_t* const* prev;    // [T*A] previous planes: t = 0 -> stored scan (or null), else raw t-1
+  uint8_t* const* state_next;    // [A] receives the last scan as decoded (q * P)
   uint8_t* out;
   unsigned long long cap;
   unsigned long long* frame_off; // [T+1]
@@ -53,6 +53,8 @@ struct EncParams {
   unsigned long long* sec_bytes; // [n_sec] section bytes (row table + chunks)
   uint32_t* sec_nnz;             // [n_sec]
   uint32_t* ticket;
+  uint32_t wpc;                  // rows kernel: warps per CTA (1, 2, 4; 0 = by shared memory)
+  uint32_t ctas_per_sm;          // rows kernel: resident CTAs per SM (0 = occupancy limit)
 };
 
 struct DecSeg {
@@ -80,10 +82,22 @@ struct DecParams {
   const uint32_t* seg_item_base; // [n_seg]
   uint32_t* done;                // [n_items] row-done flags
   uint32_t* ticket;
+  uint32_t wpc;                  // warps per CTA (1, 2, 4, 8; 0 = by shared memory)
+  uint32_t ctas_per_sm;          // resident CTAs per SM (0 = occupancy limit)
+  uint32_t items_per_ticket;     // row items a warp takes per ticket (0 = 4)
+};
+
+// Launch configuration of a rows kernel as resolved for given parameters
+// (requests clamped to what fits the device).
+struct RowsLaunch {
+  uint32_t wpc, ctas_per_sm, items_per_ticket, grid;
 };
 
 size_t enc_smem_bytes_host(uint32_t W);
 size_t dec_smem_bytes_host(uint32_t W);
+// Return a cudaError_t as int; *out receives the configuration.
+int encode_rows_launch(const EncParams& p, RowsLaunch* out);
+int decode_rows_launch(const DecParams& p, RowsLaunch* out);
 
 // Launchers (return a cudaError_t as int). ev: null, or events (cudaEvent_t
 // as void*) recorded before each kernel and after the last one (encode: 4,

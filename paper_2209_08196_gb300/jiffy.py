@@ -93,6 +93,24 @@ def _lib() -> ctypes.CDLL:
         L.jiffy_decode_batch.restype = ctypes.c_int
         L.jiffy_decode_batch.argtypes = [vp, u32, pp, ctypes.POINTER(u32), pp, ctypes.POINTER(sz), pp, pp,
                                          ctypes.POINTER(ctypes.c_int), vp]
+        L.jiffy_encode_batch_async.restype = ctypes.c_int
+        L.jiffy_encode_batch_async.argtypes = L.jiffy_encode_batch.argtypes
+        L.jiffy_decode_batch_async.restype = ctypes.c_int
+        L.jiffy_decode_batch_async.argtypes = L.jiffy_decode_batch.argtypes
+        L.jiffy_batch_wait.restype = ctypes.c_int
+        L.jiffy_batch_wait.argtypes = [vp]
+        L.jiffy_batch_set_graphs.restype = ctypes.c_int
+        L.jiffy_batch_set_graphs.argtypes = [vp, ctypes.c_int]
+        L.jiffy_batch_set_autotune.restype = ctypes.c_int
+        L.jiffy_batch_set_autotune.argtypes = [vp, ctypes.c_int]
+        L.jiffy_batch_set_launch.restype = ctypes.c_int
+        L.jiffy_batch_set_launch.argtypes = [vp, ctypes.c_int, u32, u32, u32]
+        L.jiffy_batch_info.restype = ctypes.c_int
+        L.jiffy_batch_info.argtypes = [vp, u64p, u32]
+        L.jiffy_stream_copy_state.restype = ctypes.c_int
+        L.jiffy_stream_copy_state.argtypes = [vp, vp, vp]
+        L.jiffy_stream_device_bytes.restype = sz
+        L.jiffy_stream_device_bytes.argtypes = [vp]
         _L = L
     return _L
 
@@ -317,60 +335,157 @@ class BatchError(JiffyError):
         self.required = required
 
 
+def jiffy_batch_set_graphs(b: Batch, enable: bool = True):
+    st = _lib().jiffy_batch_set_graphs(b.ptr, int(bool(enable)))
+    if st != 0:
+        raise JiffyError(st, "jiffy_batch_set_graphs")
+
+
+def jiffy_batch_set_autotune(b: Batch, enable: bool = True):
+    st = _lib().jiffy_batch_set_autotune(b.ptr, int(bool(enable)))
+    if st != 0:
+        raise JiffyError(st, "jiffy_batch_set_autotune")
+
+
+def jiffy_batch_set_launch(b: Batch, role: int, warps_per_cta: int = 0, ctas_per_sm: int = 0,
+                           items_per_ticket: int = 0):
+    st = _lib().jiffy_batch_set_launch(b.ptr, role, warps_per_cta, ctas_per_sm, items_per_ticket)
+    if st != 0:
+        raise JiffyError(st, "jiffy_batch_set_launch")
+
+
+BATCH_INFO = ("calls", "graph_captures", "graph_replays", "tunings", "tuned_classes",
+              "warps_per_cta", "ctas_per_sm", "items_per_ticket", "grid")
+
+
+def jiffy_batch_info(b: Batch) -> dict:
+    buf = (ctypes.c_uint64 * len(BATCH_INFO))()
+    st = _lib().jiffy_batch_info(b.ptr, buf, len(BATCH_INFO))
+    if st != 0:
+        raise JiffyError(st, "jiffy_batch_info")
+    return {k: int(v) for k, v in zip(BATCH_INFO, buf)}
+
+
+def jiffy_stream_copy_state(dst: Handle, src: Handle, stream=None):
+    st = _lib().jiffy_stream_copy_state(dst.ptr, src.ptr, _stream_ptr(stream))
+    if st != 0:
+        raise JiffyError(st, "jiffy_stream_copy_state")
+
+
+def jiffy_stream_device_bytes(h: Handle) -> int:
+    return _lib().jiffy_stream_device_bytes(h.ptr)
+
+
+def _addr(a) -> int:
+    return ctypes.cast(a, ctypes.c_void_p).value
+
+
+class _EncCall:
+    """Marshalled arguments of one batched encode (kept alive until it ends)."""
+
+    def __init__(self, handles, planes, outs):
+        n = len(handles)
+        flats = []
+        for h, pl in zip(handles, planes):
+            T, flat = _seq_planes(h, pl)
+            for i, p in enumerate(flat):
+                _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "plane %d" % i)
+            flats.append((T, flat))
+        self.n = n
+        self.streams = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
+        self.n_scans = (ctypes.c_uint32 * n)(*[T for T, _ in flats])
+        self.parr = [_ptr_array(flat) for _, flat in flats]
+        self.planes = (ctypes.c_void_p * n)(*[_addr(a) for a in self.parr])
+        self.outs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        self.caps = (ctypes.c_size_t * n)(*[o.numel() * o.element_size() for o in outs])
+        self.offs = [(ctypes.c_uint64 * (T + 1))() for T, _ in flats]
+        self.offs_pp = (ctypes.c_void_p * n)(*[_addr(a) for a in self.offs])
+        self.lens = (ctypes.c_size_t * n)()
+        self.sts = (ctypes.c_int * n)()
+
+    def args(self, b, stream):
+        return (b.ptr, self.n, self.streams, self.n_scans, self.planes, self.outs, self.caps, self.offs_pp,
+                self.lens, self.sts, _stream_ptr(stream))
+
+    def result(self):
+        return [(self.lens[i], list(self.offs[i])) for i in range(self.n)]
+
+
+class _DecCall:
+    def __init__(self, handles, bufs, lengths, offsets, planes_out):
+        n = len(handles)
+        flats = []
+        for h, pl, o in zip(handles, planes_out, offsets):
+            T, flat = _seq_planes(h, pl)
+            if len(o) != T + 1:
+                raise ValueError("need T + 1 frame offsets")
+            for i, p in enumerate(flat):
+                _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "output plane %d" % i)
+            flats.append((T, flat))
+        self.n = n
+        self.streams = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
+        self.n_frames = (ctypes.c_uint32 * n)(*[T for T, _ in flats])
+        self.ins = (ctypes.c_void_p * n)(*[x.data_ptr() for x in bufs])
+        self.lens = (ctypes.c_size_t * n)(*[int(x) for x in lengths])
+        self.offs = [(ctypes.c_uint64 * len(o))(*[int(v) for v in o]) for o in offsets]
+        self.offs_pp = (ctypes.c_void_p * n)(*[_addr(a) for a in self.offs])
+        self.parr = [_ptr_array(flat) for _, flat in flats]
+        self.planes = (ctypes.c_void_p * n)(*[_addr(a) for a in self.parr])
+        self.sts = (ctypes.c_int * n)()
+
+    def args(self, b, stream):
+        return (b.ptr, self.n, self.streams, self.n_frames, self.ins, self.lens, self.offs_pp, self.planes,
+                self.sts, _stream_ptr(stream))
+
+
 def jiffy_encode_batch(b: Batch, handles, planes, outs, stream=None):
     """Encodes, per stream i, the scans planes[i] (as for jiffy_encode_seq)
     into outs[i], all streams in one pass. Returns a list of (bytes, frame
     offsets) per stream."""
-    n = len(handles)
-    flats, keep = [], []
-    for h, pl in zip(handles, planes):
-        T, flat = _seq_planes(h, pl)
-        for i, p in enumerate(flat):
-            _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "plane %d" % i)
-        flats.append((T, flat))
-    streams = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
-    n_scans = (ctypes.c_uint32 * n)(*[T for T, _ in flats])
-    parr = [_ptr_array(flat) for _, flat in flats]
-    keep.append(parr)
-    planes_pp = (ctypes.c_void_p * n)(*[ctypes.cast(a, ctypes.c_void_p).value for a in parr])
-    outs_p = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
-    caps = (ctypes.c_size_t * n)(*[o.numel() * o.element_size() for o in outs])
-    offs = [(ctypes.c_uint64 * (T + 1))() for T, _ in flats]
-    offs_pp = (ctypes.c_void_p * n)(*[ctypes.cast(a, ctypes.c_void_p).value for a in offs])
-    lens = (ctypes.c_size_t * n)()
-    sts = (ctypes.c_int * n)()
-    st = _lib().jiffy_encode_batch(b.ptr, n, streams, n_scans, planes_pp, outs_p, caps, offs_pp, lens, sts,
-                                   _stream_ptr(stream))
+    c = _EncCall(handles, planes, outs)
+    st = _lib().jiffy_encode_batch(*c.args(b, stream))
     if st != 0:
-        raise BatchError(st, "jiffy_encode_batch", list(sts), required=list(lens))
-    return [(lens[i], list(offs[i])) for i in range(n)]
+        raise BatchError(st, "jiffy_encode_batch", list(c.sts), required=list(c.lens))
+    return c.result()
 
 
 def jiffy_decode_batch(b: Batch, handles, bufs, lengths, offsets, planes_out, stream=None):
     """Decodes, per stream i, the frames of bufs[i] (lengths[i] bytes, frame
     offsets offsets[i]) into planes_out[i], all streams in one pass."""
-    n = len(handles)
-    flats = []
-    for h, pl, o in zip(handles, planes_out, offsets):
-        T, flat = _seq_planes(h, pl)
-        if len(o) != T + 1:
-            raise ValueError("need T + 1 frame offsets")
-        for i, p in enumerate(flat):
-            _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "output plane %d" % i)
-        flats.append((T, flat))
-    streams = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
-    n_frames = (ctypes.c_uint32 * n)(*[T for T, _ in flats])
-    ins = (ctypes.c_void_p * n)(*[x.data_ptr() for x in bufs])
-    lens = (ctypes.c_size_t * n)(*[int(x) for x in lengths])
-    offs = [(ctypes.c_uint64 * len(o))(*[int(v) for v in o]) for o in offsets]
-    offs_pp = (ctypes.c_void_p * n)(*[ctypes.cast(a, ctypes.c_void_p).value for a in offs])
-    parr = [_ptr_array(flat) for _, flat in flats]
-    planes_pp = (ctypes.c_void_p * n)(*[ctypes.cast(a, ctypes.c_void_p).value for a in parr])
-    sts = (ctypes.c_int * n)()
-    st = _lib().jiffy_decode_batch(b.ptr, n, streams, n_frames, ins, lens, offs_pp, planes_pp, sts,
-                                   _stream_ptr(stream))
+    c = _DecCall(handles, bufs, lengths, offsets, planes_out)
+    st = _lib().jiffy_decode_batch(*c.args(b, stream))
     if st != 0:
-        raise BatchError(st, "jiffy_decode_batch", list(sts))
+        raise BatchError(st, "jiffy_decode_batch", list(c.sts))
+
+
+def jiffy_encode_batch_async(b: Batch, handles, planes, outs, stream=None):
+    """Enqueues a batched encode and returns at once; jiffy_batch_wait(b)
+    returns its result (as jiffy_encode_batch does)."""
+    c = _EncCall(handles, planes, outs)
+    st = _lib().jiffy_encode_batch_async(*c.args(b, stream))
+    if st != 0:
+        raise BatchError(st, "jiffy_encode_batch_async", list(c.sts))
+    b.pending = ("encode", c)
+
+
+def jiffy_decode_batch_async(b: Batch, handles, bufs, lengths, offsets, planes_out, stream=None):
+    c = _DecCall(handles, bufs, lengths, offsets, planes_out)
+    st = _lib().jiffy_decode_batch_async(*c.args(b, stream))
+    if st != 0:
+        raise BatchError(st, "jiffy_decode_batch_async", list(c.sts))
+    b.pending = ("decode", c)
+
+
+def jiffy_batch_wait(b: Batch):
+    """Waits for the batch's enqueued call; returns the encode result (list of
+    (bytes, frame offsets)) or None for a decode."""
+    kind, c = getattr(b, "pending", None) or (None, None)
+    st = _lib().jiffy_batch_wait(b.ptr)
+    b.pending = None
+    if st != 0:
+        raise BatchError(st, "jiffy_batch_wait", list(c.sts) if c else [],
+                         required=list(c.lens) if kind == "encode" else None)
+    return c.result() if kind == "encode" else None
 
 
 TORCH_DTYPE = {1: torch.uint8, 2: torch.int16, 4: torch.int32}

@@ -153,3 +153,140 @@ def test_batch_rejects_repeated_stream_and_wrong_role():
         J.jiffy_encode_batch(b, [enc, dec], [[sc], [sc]], out)
     assert ei.value.status == 4
     assert J.jiffy_stream_frame_index(enc) == 0
+
+
+def _oracle_bytes(fleet, i, scans):
+    return b"".join(fleet.ref[i].encode(s) for s in scans)
+
+
+def test_graph_replay_matches_oracle():
+    rng = np.random.default_rng(14)
+    fleet = Fleet(SENSORS)
+    J.jiffy_batch_set_graphs(fleet.b, True)
+    for call in range(3):
+        scans = [make_scans(rng, H, W, a, 2) for H, W, a in SENSORS]
+        got = fleet.encode(scans)
+        for i in range(len(SENSORS)):
+            assert got[i][0] == _oracle_bytes(fleet, i, scans[i]), (call, i)
+    info = J.jiffy_batch_info(fleet.b)
+    assert info["graph_captures"] == 1 and info["graph_replays"] == 2, info
+    # a different shape captures again
+    scans = [make_scans(rng, H, W, a, 1) for H, W, a in SENSORS]
+    got = fleet.encode(scans)
+    for i in range(len(SENSORS)):
+        assert got[i][0] == _oracle_bytes(fleet, i, scans[i])
+    assert J.jiffy_batch_info(fleet.b)["graph_captures"] == 2
+
+
+@pytest.mark.parametrize("wpc,ctas", [(1, 1), (2, 0), (4, 1), (4, 2)])
+def test_every_encode_launch_configuration_codes_the_same_bytes(wpc, ctas):
+    rng = np.random.default_rng(15)
+    fleet = Fleet(SENSORS)
+    J.jiffy_batch_set_launch(fleet.b, J.JIFFY_ENCODER, wpc, ctas, 0)
+    scans = [make_scans(rng, H, W, a, 3) for H, W, a in SENSORS]
+    got = fleet.encode(scans)
+    info = J.jiffy_batch_info(fleet.b)
+    assert info["warps_per_cta"] == wpc and (ctas == 0 or info["ctas_per_sm"] <= ctas)
+    for i in range(len(SENSORS)):
+        assert got[i][0] == _oracle_bytes(fleet, i, scans[i])
+
+
+@pytest.mark.parametrize("wpc,ctas,ipt", [(1, 1, 1), (8, 0, 16), (2, 2, 64), (4, 0, 3)])
+def test_every_decode_launch_configuration_decodes_the_same(wpc, ctas, ipt):
+    rng = np.random.default_rng(16)
+    fleet = Fleet(SENSORS)
+    scans = [make_scans(rng, H, W, a, 4) for H, W, a in SENSORS]
+    got = fleet.encode(scans)
+    J.jiffy_batch_set_launch(fleet.b, J.JIFFY_DECODER, wpc, ctas, ipt)
+    bufs = [torch.from_numpy(np.frombuffer(x, dtype=np.uint8).copy()).cuda() for x, _ in got]
+    outs = [[torch.empty((4, H, W), dtype=TORCH_DT[s], device="cuda") for s, _ in a] for H, W, a in SENSORS]
+    J.jiffy_decode_batch(fleet.b, fleet.dec, bufs, [len(x) for x, _ in got], [o for _, o in got], outs)
+    info = J.jiffy_batch_info(fleet.b)
+    assert info["warps_per_cta"] == wpc and info["items_per_ticket"] == ipt, info
+    for i, (H, W, a) in enumerate(SENSORS):
+        want, _ = oracle.decode_sequence(H, W, a, got[i][0], 4)
+        for t in range(4):
+            for k, (s, _) in enumerate(a):
+                assert np.array_equal(to_np(outs[i][k][t], s), want[t][k]), (i, t, k)
+
+
+def test_autotune_keeps_bytes_and_records_a_choice():
+    rng = np.random.default_rng(17)
+    fleet = Fleet(SENSORS)
+    J.jiffy_batch_set_autotune(fleet.b, True)
+    for call in range(2):
+        scans = [make_scans(rng, H, W, a, 2) for H, W, a in SENSORS]
+        got = fleet.encode(scans)
+        for i in range(len(SENSORS)):
+            assert got[i][0] == _oracle_bytes(fleet, i, scans[i]), (call, i)
+    info = J.jiffy_batch_info(fleet.b)
+    assert info["tunings"] == 1 and info["tuned_classes"] == 1, info
+
+
+def test_async_calls_on_two_batches_overlap_and_match():
+    rng = np.random.default_rng(18)
+    half = [SENSORS[:2], SENSORS[2:]]
+    fleets = [Fleet(h) for h in half]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for call in range(3):
+        scans = [[make_scans(rng, H, W, a, 2) for H, W, a in h] for h in half]
+        outs, keep = [], []
+        for f, sc, cs in zip(fleets, scans, streams):
+            planes = [[[to_dev(p) for p in s] for s in x] for x in sc]
+            o = [torch.zeros(J.jiffy_max_encoded_size(H, W, a, 2), dtype=torch.uint8, device="cuda")
+                 for H, W, a in f.sensors]
+            torch.cuda.synchronize()
+            J.jiffy_encode_batch_async(f.b, f.enc, planes, o, stream=cs)
+            outs.append(o)
+            keep.append(planes)
+        for f, o, sc in zip(fleets, outs, scans):
+            res = J.jiffy_batch_wait(f.b)
+            for i, (n, _) in enumerate(res):
+                assert o[i][:n].cpu().numpy().tobytes() == _oracle_bytes(f, i, sc[i]), (call, i)
+
+
+def test_async_call_blocks_its_streams_until_waited():
+    H, W, a = SENSORS[1]
+    enc = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, a)
+    b1, b2 = J.jiffy_batch_create(), J.jiffy_batch_create()
+    sc = [[to_dev(p) for p in make_scans(np.random.default_rng(2), H, W, a, 1)[0]]]
+    o = [torch.zeros(J.jiffy_max_encoded_size(H, W, a, 1), dtype=torch.uint8, device="cuda")]
+    J.jiffy_encode_batch_async(b1, [enc], [sc], o)
+    with pytest.raises(J.JiffyError) as ei:  # the stream is in flight in b1
+        J.jiffy_encode_batch(b2, [enc], [sc], o)
+    assert ei.value.status == 4
+    with pytest.raises(J.JiffyError) as ei:  # b1 has an unfinished call
+        J.jiffy_encode_batch_async(b1, [enc], [sc], o)
+    assert ei.value.status == 4
+    J.jiffy_batch_wait(b1)
+    assert J.jiffy_stream_frame_index(enc) == 1
+
+
+def test_decoder_takes_over_from_encoder_state():
+    """A decode request for the frame an encoder codes next: copy the
+    encoder's state into a decoder first (both hold the previous scan as
+    decoded), then decode the new frame alone."""
+    rng = np.random.default_rng(19)
+    H, W, a = SENSORS[0]
+    scans = make_scans(rng, H, W, a, 5)
+    enc = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, a)
+    dec = J.jiffy_stream_create(J.JIFFY_DECODER, H, W, a)
+    ref = oracle.Codec(H, W, a)
+    refd = oracle.Codec(H, W, a)
+    cap = J.jiffy_max_encoded_size(H, W, a, 1)
+    for t, sc in enumerate(scans):
+        want_bytes = ref.encode(sc)
+        want_planes, _ = refd.decode(want_bytes)
+        out = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+        if t in (0, 3, 4):
+            J.jiffy_stream_copy_state(dec, enc)
+        n = J.jiffy_encode(enc, [to_dev(p) for p in sc], out)
+        assert out[:n].cpu().numpy().tobytes() == want_bytes
+        if t in (0, 3, 4):
+            got = J.empty_planes(dec)
+            J.jiffy_decode(dec, out, n, got)
+            for k, (s, _) in enumerate(a):
+                assert np.array_equal(to_np(got[k], s), want_planes[k]), (t, k)
+    other = J.jiffy_stream_create(J.JIFFY_DECODER, H, W + 1, a)
+    with pytest.raises(J.JiffyError):
+        J.jiffy_stream_copy_state(other, enc)
