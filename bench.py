@@ -49,54 +49,103 @@ def peaks():
 
 
 class Clocks:
-    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """Samples the SM clock and the clock event (throttle) reasons during a
+    region: NVML read through ctypes from a background thread every 5 ms
+    (reads only; nothing is set), else nvidia-smi every 200 ms."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
 
     def __init__(self, device_index: int):
         self.dev = device_index
+        self.samples = []
+        self.smax = None
+        self.mode = None
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device_index)
 
+    def _nvml(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.dev), ctypes.byref(h)) != 0:
+            raise OSError("no NVML handle")
+        fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+            self.smax = float(mx.value)
+        return lib, h, fn
+
     def start(self):
+        import threading
+        try:
+            lib, h, fn = self._nvml()
+            import ctypes
+            self.stop_flag = threading.Event()
+
+            def loop():
+                mhz, rs = ctypes.c_uint(), ctypes.c_ulonglong()
+                while not self.stop_flag.is_set():
+                    if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0 and \
+                            fn(h, ctypes.byref(rs)) == 0:
+                        self.samples.append((float(mhz.value), int(rs.value)))
+                    time.sleep(0.005)
+            self.thread = threading.Thread(target=loop, daemon=True)
+            self.thread.start()
+            self.mode = "nvml"
+            return
+        except Exception:
+            pass
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.Q,
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + q,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
+            self.mode = "nvidia-smi"
         except Exception:
             self.proc = None
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.f.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
-                continue
+        if self.mode == "nvml":
+            self.stop_flag.set()
+            self.thread.join()
+            sm = [m for m, _ in self.samples]
+            reasons = sorted({n for _, r in self.samples for bit, n in self.REASONS.items() if r & bit})
+            smax = self.smax
+        elif self.proc is not None:
+            self.proc.terminate()
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for n, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(n)
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+            sm, mx, rset = [], [], set()
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        rset.add(n)
+            reasons, smax = sorted(rset), (max(mx) if mx else None)
+        else:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock reader"]}
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": ["no samples"]}
         loaded = [x for x in sm if x >= 0.5 * max(sm)] or sm
-        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(sm), "source": self.mode}
 
 
 def make_workload(device: str, seed: int, n_scans: int = 100):
@@ -171,15 +220,160 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def batched_leg(J, torch, dev, local, steps, warmup, n_streams=256, n_scans=8, base_seed=1000):
+    """Many streams in one pass: n_streams sensors of uneven shapes and
+    attribute sets, n_scans scans each, encoded by one batched call and
+    decoded by another (CUDA-graph replay, autotuned launches), against the
+    same scans coded one scan per launch (jiffy_encode / jiffy_decode)."""
+    from paper_2209_08196_gb300 import synth
+    t_gen = time.perf_counter()
+    cfgs = [synth.batch_stream_config(i, base_seed=base_seed, n_scans=n_scans) for i in range(n_streams)]
+    scans, encs, decs, outs, planes, attrs_l = [], [], [], [], [], []
+    for c in cfgs:
+        seq = synth.ScanSequence(c, device=dev)
+        sc = [seq.scan(t, as_numpy=False) for t in range(n_scans)]
+        at = synth.attr_descs(c)
+        scans.append(sc)
+        attrs_l.append(at)
+        encs.append(J.jiffy_stream_create(J.JIFFY_ENCODER, c.H, c.W, at, device=local))
+        decs.append(J.jiffy_stream_create(J.JIFFY_DECODER, c.H, c.W, at, device=local))
+        outs.append(torch.empty(J.jiffy_max_encoded_size(c.H, c.W, at, n_scans), dtype=torch.uint8, device=dev))
+        planes.append(J.empty_planes(decs[-1], n_scans))
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    px = sum(c.H * c.W * n_scans for c in cfgs)
+    raw = sum(p.numel() * p.element_size() for sc in scans for s in sc for p in s)
+    b = J.jiffy_batch_create(local)
+    J.jiffy_batch_set_graphs(b, True)
+    J.jiffy_batch_set_autotune(b, True)
+    stream = torch.cuda.current_stream()
+    res = {}
+
+    def step():
+        for h in encs + decs:
+            J.jiffy_stream_reset(h)
+        r = J.jiffy_encode_batch(b, encs, scans, outs, stream)
+        J.jiffy_decode_batch(b, decs, outs, [n for n, _ in r], [o for _, o in r], planes, stream)
+        res["r"] = r
+
+    for _ in range(warmup):
+        step()
+    # round trip of every stream (outside the timed region)
+    for c, sc, pl, at in zip(cfgs, scans, planes, attrs_l):
+        for a, (sz, P) in enumerate(at):
+            m = (1 << (8 * sz)) - 1
+            v = torch.stack([sc[t][a] for t in range(n_scans)]).to(torch.int64) & m
+            q = torch.clamp((v + P // 2) // P, max=m // P)
+            if not torch.equal(pl[a].to(torch.int64) & m, q * P):
+                raise SystemExit("batched round trip mismatch")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    info = J.jiffy_batch_info(b)
+    stream_bytes = sum(n for n, _ in res["r"])
+    # kernel split of one batched step (graphs off while profiling)
+    J.jiffy_batch_set_profiling(b, True)
+    for h in encs + decs:
+        J.jiffy_stream_reset(h)
+    r = J.jiffy_encode_batch(b, encs, scans, outs, stream)
+    ke = J.jiffy_batch_kernel_times(b)
+    J.jiffy_decode_batch(b, decs, outs, [n for n, _ in r], [o for _, o in r], planes, stream)
+    kd = J.jiffy_batch_kernel_times(b)
+    J.jiffy_batch_set_profiling(b, False)
+
+    # the same scans, one scan per launch
+    def per_launch():
+        frames = []
+        for h in encs + decs:
+            J.jiffy_stream_reset(h)
+        for i, (c, sc) in enumerate(zip(cfgs, scans)):
+            pos = 0
+            for t in range(n_scans):
+                n = J.jiffy_encode(encs[i], sc[t], outs[i][pos:], stream)
+                frames.append((i, pos, n))
+                pos += (n + 15) // 16 * 16
+        for i, pos, n in frames:
+            J.jiffy_decode(decs[i], outs[i][pos:], n, [p[0] for p in planes[i]], stream)
+    per_launch()
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    per_launch()
+    p1.record(stream)
+    torch.cuda.synchronize()
+    ms_pl = p0.elapsed_time(p1)
+    return {"workload": "%d streams x %d scans, shapes from %s, attribute sets from %s" % (
+                n_streams, n_scans, list(synth.BATCH_SHAPES), [list(a) for a in synth.BATCH_ATTR_SETS]),
+            "gpoints_s": px / (ms / 1e3) / 1e9, "ms_per_step": ms, "points_per_step": px, "raw_bytes": raw,
+            "stream_bytes": stream_bytes, "ratio": raw / stream_bytes,
+            "one_scan_per_launch_gpoints_s": px / (ms_pl / 1e3) / 1e9, "speedup_vs_one_scan_per_launch": ms_pl / ms,
+            "kernels_ms": {"trial": ke[0], "encode_rows": ke[1], "placement": ke[2], "decode_rows": kd[0]}
+            if len(ke) == 3 and kd else None,
+            "launch": {k: info[k] for k in ("warps_per_cta", "ctas_per_sm", "items_per_ticket", "grid")},
+            "graph_replays": info["graph_replays"], "tunings": info["tunings"], "gen_s": t_gen,
+            "launches_per_step": 5}
+
+
+def serve_leg(J, torch, dev, local, seconds, sat_seconds, n_sensors=512, base_seed=5000):
+    """Serving loop: n_sensors sensors (shapes and attribute sets of the
+    many-stream set) with Poisson arrivals at 10-20 Hz, replayed in real time
+    for `seconds`, 10 % decode requests, 40 GB HBM budget; then the same
+    sensors with every scan available at once (saturation) for capacity."""
+    import numpy as np
+    from paper_2209_08196_gb300 import serve, synth
+    rng = np.random.default_rng(base_seed)
+    classes = [(sh, at) for sh in synth.BATCH_SHAPES for at in synth.BATCH_ATTR_SETS]
+    t_gen = time.perf_counter()
+    pools, descs = [], []
+    for k, ((H, W), at) in enumerate(classes):
+        prec = tuple(10 if a in (synth.RANGE, synth.RANGE2) else 1 for a in at)
+        c = synth.SensorConfig(H=H, W=W, attrs=at, precisions=prec, n_scans=8, dropout=0.0,
+                               target_zero_frac=0.12, wall=True, seed=base_seed + k)
+        seq = synth.ScanSequence(c, device=dev)
+        pools.append([seq.scan(t, as_numpy=False) for t in range(8)])
+        descs.append(synth.attr_descs(c))
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    sensors = []
+    for i in range(n_sensors):
+        ci = int(rng.integers(len(classes)))
+        (H, W), _ = classes[ci]
+        sensors.append(serve.Sensor(i, H, W, descs[ci], float(rng.uniform(10, 20)), pool=ci,
+                                    pool_offset=int(rng.integers(8))))
+    max_px = sum(s.H * s.W for s in sensors)
+    be = serve.GpuBackend(pools, device=local, graphs=False, autotune=True, max_batch_px=max_px)
+    # warm-up: tune and build the handles' scratch on a short saturated run
+    serve.Server(be, sensors, budget_bytes=40e9).run(
+        serve.poisson_arrivals(sensors, 0.5, 0.1, seed=base_seed + 1), realtime=False)
+    rt = serve.Server(be, sensors, budget_bytes=40e9).run(
+        serve.poisson_arrivals(sensors, seconds, 0.1, seed=base_seed + 2), realtime=True).summary()
+    sat = serve.Server(be, sensors, budget_bytes=40e9).run(
+        serve.poisson_arrivals(sensors, sat_seconds, 0.1, seed=base_seed + 3), realtime=False).summary()
+    return {"workload": "%d sensors, Poisson 10-20 Hz, %g s real time, 10%% decode requests, 40 GB budget"
+                        % (n_sensors, seconds),
+            "p50_ms": rt["p50_ms"], "p99_ms": rt["p99_ms"], "decode_p50_ms": rt["decode_p50_ms"],
+            "decode_p99_ms": rt["decode_p99_ms"], "gpoints_s": rt["gpoints_s"], "realtime": rt,
+            "saturated": sat, "gen_s": t_gen}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer leg (profiling runs)")
     ap.add_argument("--scans", type=int, default=100, help="scans per step (100 = the benchmark workload)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the many-stream leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
+    ap.add_argument("--serve-seconds", type=float, default=60.0)
+    ap.add_argument("--serve-sat-seconds", type=float, default=5.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -317,6 +511,12 @@ def main():
                    "frac_of_peak": (algo[k] / (avg[k] / 1e3) / 1e9 / peak) if k in algo else None}
                for k in avg}
 
+    batched = served = None
+    if not args.no_batched:
+        batched = batched_leg(J, torch, dev, local, args.steps, args.warmup)
+    if not args.no_serve:
+        served = serve_leg(J, torch, dev, local, args.serve_seconds, args.serve_sat_seconds)
+
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and world == 1:
@@ -329,7 +529,8 @@ def main():
                            "raw_bytes_per_step": raw_bytes, "l2": "inputs larger than L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-                "gpu_launches": 4 * args.steps * (2 if e2e else 1),
+                "gpu_launches": 5 * args.steps * (2 if e2e else 1),
+                "batched": batched, "served": served,
                 "detail": {"kernels": kernels, "compression": modes, "stream_bytes": n,
                            "encode_gpoints_s": px_step / (avg["k_trial"] + avg["k_encode"] + avg["k_finalize"]) / 1e6,
                            "decode_gpoints_s": px_step / avg["k_decode"] / 1e6,

@@ -269,7 +269,8 @@ class GpuBackend:
     pools of device planes; n_contexts batch contexts on their own CUDA
     streams."""
 
-    def __init__(self, pools, n_contexts=2, device=0, graphs=False, autotune=False, max_batch_px=None):
+    def __init__(self, pools, n_contexts=2, device=0, graphs=False, autotune=False, max_batch_px=None,
+                 keep=False):
         import torch
 
         from paper_2209_08196_gb300 import jiffy as J
@@ -288,6 +289,10 @@ class GpuBackend:
         self.max_batch_px = max_batch_px or 0
         self.s = {}                 # sensor id -> dict of handles and buffers
         self.n_decode = [0] * n_contexts
+        self.items = [None] * n_contexts
+        self.keep = keep            # copy every frame and decoded scan to the host (tests)
+        self.frames = {}            # (sensor, seq) -> bytes
+        self.decoded = {}           # (sensor, seq) -> [numpy planes]
 
     @staticmethod
     def sensor_bytes(sensor):
@@ -335,6 +340,7 @@ class GpuBackend:
             ev = self.torch.cuda.Event()
             ev.record(st)
         self.events[ctx] = ev
+        self.items[ctx] = batch
 
     def ready(self, ctx):
         return self.events[ctx] is None or self.events[ctx].query()
@@ -347,6 +353,10 @@ class GpuBackend:
         except J.BatchError as e:
             out = [((e.required or [0] * len(e.statuses))[i], st) for i, st in enumerate(e.statuses)]
         self.events[ctx] = None
+        if self.keep:
+            for (sid, r), (n, st) in zip(self.items[ctx], out):
+                if st == 0:
+                    self.frames[(sid, r.seq)] = self.s[sid]["out"][:n].cpu().numpy().tobytes()
         return out
 
     def submit_decode(self, ctx, items):
@@ -355,7 +365,8 @@ class GpuBackend:
         handles, bufs, lens, offs, planes = [], [], [], [], []
         for sid, r in items:
             d = self.s[sid]
-            first = 16 + 8 * len(d["sensor"].attrs) if r.seq == 0 else 0  # stream header before frame 0
+            # the stream header precedes frame 0
+            first = 16 + 8 * len(d["sensor"].attrs) if J.jiffy_stream_frame_index(d["dec"]) == 0 else 0
             handles.append(d["dec"])
             bufs.append(d["out"])
             lens.append(r.nbytes)
@@ -367,12 +378,18 @@ class GpuBackend:
             ev.record(st)
         self.events[ctx] = ev
         self.n_decode[ctx] = len(items)
+        self.items[ctx] = items
 
     def finish_decode(self, ctx):
         J = self.J
         self.events[ctx] = None
         try:
             J.jiffy_batch_wait(self.batches[ctx])
-            return [0] * self.n_decode[ctx]
+            res = [0] * self.n_decode[ctx]
         except J.BatchError as e:
-            return list(e.statuses)
+            res = list(e.statuses)
+        if self.keep:
+            for (sid, r), st in zip(self.items[ctx], res):
+                if st == 0:
+                    self.decoded[(sid, r.seq)] = [p.cpu().clone() for p in self.s[sid]["planes"]]
+        return res
