@@ -135,12 +135,6 @@ struct Carver {
   }
 };
 
-uint64_t magic_for(uint32_t P) {
-  if (P < 2 || P > 0x80000000u) return 0;
-  // ceil(2^64 / P) = floor((2^64 - 1) / P) + 1
-  return (~0ull) / P + 1ull;
-}
-
 void drop_graph(GraphCache& g) {
   if (g.exec) cudaGraphExecDestroy(g.exec);
   g.exec = nullptr;
@@ -210,7 +204,16 @@ jiffy_status map_device_error(uint32_t err) {
 
 uint32_t stream_header_bytes(uint32_t A) { return 16u + 8u * A; }
 uint32_t frame_header_bytes(uint32_t A) { return 8u + 12u * A; }
-uint32_t slot_bytes_for(uint32_t W) { return (jiffy::row_bound_bytes(W) + 15u) & ~15u; }
+// Number of distinct test rows floor((2k+1)H/(2L)), k < L (Sec. III-E).
+uint32_t distinct_test_rows(uint32_t H, uint32_t L) {
+  uint32_t n = 0, last = 0;
+  for (uint32_t k = 0; k < L; k++) {
+    const uint32_t r = (uint32_t)(((uint64_t)(2 * k + 1) * H) / (2ull * L));
+    if (n == 0 || r != last) n++;
+    last = r;
+  }
+  return n;
+}
 
 jiffy_status check_distinct(const std::vector<jiffy_stream*>& ss) {
   for (size_t i = 0; i < ss.size(); i++)
@@ -348,6 +351,15 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   }
   if (check_distinct(ss) != JIFFY_OK) return JIFFY_ERR_INVALID_ARG;
   if (items > 0x7fffffffull) return JIFFY_ERR_INVALID_ARG;
+  // most distinct test rows of a stream that may run the trial (the kernel
+  // skips first frames itself, so the launch shape does not depend on the
+  // streams' frame counters and captured graphs stay valid)
+  uint32_t trial_rows = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    const jiffy_stream* s = jobs[i].s;
+    if (s->opt.force_mode >= 0) continue;
+    trial_rows = std::max(trial_rows, distinct_test_rows(s->H, s->opt.test_lines));
+  }
 
   // ---- upload image: segments, search keys, per-segment pointer arrays
   Carver up;
@@ -362,25 +374,18 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     r_err[i] = rs.take(8);
     r_off[i] = rs.take(8ull * (jobs[i].T + 1));
   }
-  // ---- device scratch: upload, zeroed region (look-back words, ticket,
-  //      results), work arrays, row slots
+  // ---- device scratch: upload, zeroed region (look-back words, trial
+  //      costs, ticket, results), work arrays
   Carver c;
   const size_t o_up = c.take(up.off);
   const size_t o_zero = c.take(0);
-  const size_t o_stc = c.take(8ull * items), o_tick = c.take(8);
+  const size_t o_stc = c.take(8ull * items), o_stb = c.take(8ull * items);
+  const size_t o_cost = c.take(8ull * secs), o_tick = c.take(8);
   const size_t o_res = c.take(rs.off);
   const size_t zero_bytes = c.off - o_zero;
   const size_t o_modes = c.take(4ull * secs);
   const size_t o_rb = c.take(4ull * items), o_rn = c.take(4ull * items), o_rc = c.take(4ull * items);
-  const size_t o_secb = c.take(8ull * secs), o_secn = c.take(4ull * secs);
-  std::vector<unsigned long long> slot_base(n);
-  unsigned long long slots_total = 0;
-  for (uint32_t i = 0; i < n; i++) {
-    const jiffy_stream* s = jobs[i].s;
-    slot_base[i] = slots_total;
-    slots_total += (unsigned long long)slot_bytes_for(s->W) * jobs[i].T * s->A * s->H;
-  }
-  const size_t o_slots = c.take(slots_total);
+  const size_t o_roff = c.take(8ull * items);
   const size_t h_res = align_up(up.off, 256);
   jiffy_status r = ensure_scratch(ws, c.off, h_res + rs.off);
   if (r != JIFFY_OK) return r;
@@ -424,8 +429,6 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     g.force_mode = s->opt.force_mode;
     g.item_base = item_base;
     g.sec_base = sec_base;
-    g.slot_bytes = slot_bytes_for(s->W);
-    g.slot_base = slot_base[i];
     g.attrs = s->d_attrs;
     g.cur = reinterpret_cast<const uint8_t* const*>(dp);
     g.prev = reinterpret_cast<const uint8_t* const*>(dp + 8ull * T * A);
@@ -451,14 +454,15 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   p.seg = reinterpret_cast<const jiffy::EncSeg*>(d + o_up + u_seg);
   p.seg_item_base = reinterpret_cast<const uint32_t*>(d + o_up + u_ib);
   p.seg_sec_base = reinterpret_cast<const uint32_t*>(d + o_up + u_sb);
+  p.trial_rows = trial_rows;
+  p.cost = reinterpret_cast<uint32_t*>(d + o_cost);
   p.modes = reinterpret_cast<uint32_t*>(d + o_modes);
   p.row_bytes = reinterpret_cast<uint32_t*>(d + o_rb);
   p.row_nnz = reinterpret_cast<uint32_t*>(d + o_rn);
   p.row_carry = reinterpret_cast<uint32_t*>(d + o_rc);
+  p.row_off = reinterpret_cast<unsigned long long*>(d + o_roff);
   p.st_carry = reinterpret_cast<unsigned long long*>(d + o_stc);
-  p.slots = d + o_slots;
-  p.sec_bytes = reinterpret_cast<unsigned long long*>(d + o_secb);
-  p.sec_nnz = reinterpret_cast<uint32_t*>(d + o_secn);
+  p.st_bytes = reinterpret_cast<unsigned long long*>(d + o_stb);
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
   uint8_t* hres = h + h_res;
 
@@ -487,6 +491,7 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   if (ws.fixed[0].ctas_per_sm) p.ctas_per_sm = ws.fixed[0].ctas_per_sm;
   if (jiffy::encode_rows_launch(p, &ws.last) != 0) return JIFFY_ERR_CUDA;
   key.push_back(((uint64_t)p.wpc << 32) | p.ctas_per_sm);
+  key.push_back(trial_rows);
   const bool timed = ws.profile;
   void* evs[4] = {ws.ev[0], ws.ev[1], ws.ev[2], ws.ev[3]};
   r = run_sequence(ws, ws.g_enc, key, st, ws.graphs && !timed,
@@ -791,12 +796,7 @@ jiffy_status jiffy_stream_create(jiffy_stream** out, jiffy_role role, uint32_t H
   s->opt = o;
   size_t state_bytes = 0;
   for (uint32_t a = 0; a < n_attr; a++) {
-    AttrDev d{};
-    d.s = attrs[a].dtype_bytes;
-    d.P = attrs[a].precision;
-    const uint32_t maxv = d.s == 4 ? 0xffffffffu : ((1u << (8 * d.s)) - 1u);
-    d.qmax = maxv / d.P;
-    d.magic = magic_for(d.P);
+    const AttrDev d = jiffy::make_attr(attrs[a].dtype_bytes, attrs[a].precision);
     s->attrs.push_back(d);
     s->plane_off.push_back(state_bytes);
     state_bytes = align_up(state_bytes + (size_t)H * W * d.s, 256);

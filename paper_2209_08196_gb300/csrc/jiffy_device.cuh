@@ -220,7 +220,7 @@ __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, uint32_t& total) 
 }
 
 // Quantization, Sec. III-B: q = min(floor((v + floor(P/2)) / P), floor(max/P)).
-// The division uses the round-up reciprocal m = ceil(2^64/P) (Granlund and
+// qkind 2 divides with the round-up reciprocal m = ceil(2^64/P) (Granlund and
 // Montgomery, "Division by invariant integers using multiplication", 1994):
 // for a dividend n < 2^33 the product n*m/2^64 exceeds n/P by less than
 // 2^-31 <= 1/P, which never crosses the next integer, so the high word of
@@ -232,6 +232,25 @@ __device__ __forceinline__ uint32_t quantize(uint32_t v, const AttrDev& a) {
   if (a.P <= 0x80000000u) q = (uint32_t)__umul64hi(n, a.magic);
   else q = (uint32_t)(n >= a.P) + (uint32_t)(n >= 2ull * a.P);
   return q < a.qmax ? q : a.qmax;
+}
+
+// Compile-time quantizer kind (AttrDev::qkind): 0 identity, 1 32-bit
+// reciprocal with a two-step correction (P < 2^30), 2 the 64-bit form above.
+// Kind 1: q0 = floor(v m32 / 2^32) with m32 = floor(2^32/P) is floor(v/P) or
+// one less, so r = v - q0 P is in [0, 2P) and floor((v + h)/P) = q0 +
+// floor((r + h)/P) with r + h < 3P < 2^32.
+template <int QU>
+__device__ __forceinline__ uint32_t quant(uint32_t v, const AttrDev& a) {
+  if constexpr (QU == 0) {
+    return v;
+  } else if constexpr (QU == 1) {
+    const uint32_t q0 = __umulhi(v, a.m32);
+    const uint32_t t = v - q0 * a.P + a.half;
+    const uint32_t q = q0 + (t >= a.P ? 1u : 0u) + (t >= 2u * a.P ? 1u : 0u);
+    return q < a.qmax ? q : a.qmax;
+  } else {
+    return quantize(v, a);
+  }
 }
 
 // ZigZag, Eq. 1: 2|x| + [x < 0] with x the residual read as a signed 32-bit
@@ -258,53 +277,6 @@ __device__ __forceinline__ uint32_t block_body_bytes(uint32_t n, uint32_t b, uin
   uint32_t bytes = 4u * ((n * b + 31u) >> 5);
   if (e) bytes += 4u * ((e + 3u) >> 2) + 4u * ((e * (wmax - b) + 31u) >> 5);
   return bytes;
-}
-
-struct BlockChoice {
-  uint32_t b, e, hb, bytes;
-};
-
-// Warp-wide choice of the block width. Lane l holds values l, l+32, l+64,
-// l+96 of a block of n <= 128 values (zero past n); hist is a per-warp shared
-// scratch of 33 words. Builds the histogram of value widths (one shared write
-// per distinct width per pass, grouped with __match_any_sync), turns it into
-// e_b = #values wider than b with a suffix sum across lanes (lane l <-> width
-// l + 1), prices every candidate b in [0, wmax] in parallel (lane b) and takes
-// the cheapest, the smallest b on ties: the same choice as an exhaustive
-// search over b.
-__device__ __forceinline__ BlockChoice choose_block(const uint32_t (&z)[4], uint32_t n, uint32_t* hist) {
-  const uint32_t lane = lane_id();
-  hist[lane] = 0;
-  if (lane == 0) hist[32] = 0;
-  __syncwarp();
-#pragma unroll
-  for (int m = 0; m < 4; m++) {
-    const uint32_t w = (lane + 32u * m < n) ? bit_width(z[m]) : 0u;
-    const uint32_t grp = __match_any_sync(0xffffffffu, w);
-    if (lane == (uint32_t)(__ffs(grp) - 1)) hist[w] += __popc(grp);
-    __syncwarp();
-  }
-  const uint32_t c = hist[lane + 1];  // values of width lane + 1
-  const uint32_t present = __ballot_sync(0xffffffffu, c != 0u);
-  const uint32_t wmax = present ? 32u - __clz(present) : 0u;
-  uint32_t e = c;  // -> number of values wider than lane
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_down_sync(0xffffffffu, e, o);
-    if (lane + o < 32u) e += t;
-  }
-  uint32_t key = 0xffffffffu;
-  if (lane <= wmax) key = (block_body_bytes(n, lane, e, wmax) << 6) | lane;
-  key = __reduce_min_sync(0xffffffffu, key);
-  if (wmax == 32u) key = min(key, ((4u * n) << 6) | 32u);  // b = 32: no exceptions
-  const uint32_t b = key & 63u;
-  const uint32_t eb = __shfl_sync(0xffffffffu, e, b & 31u);
-  BlockChoice r;
-  r.b = b;
-  r.e = b < 32u ? eb : 0u;
-  r.hb = r.e ? wmax - b : 0u;
-  r.bytes = key >> 6;
-  return r;
 }
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
@@ -458,6 +430,24 @@ __device__ inline bool lookback_last(const unsigned long long* st, uint32_t k, u
     }
     j -= kLookQ * 32;
   }
+}
+
+// ---- bit-sliced counting (carry-save adders, as in the Harley-Seal
+// population count: Warren, "Hacker's Delight", 2nd ed., Sec. 5-1).
+// csa: per bit position, a + b + c = 2 * hi + lo.
+__device__ __forceinline__ void csa(uint32_t& hi, uint32_t& lo, uint32_t a, uint32_t b, uint32_t c) {
+  const uint32_t u = a ^ b;
+  hi = (a & b) | (u & c);
+  lo = u ^ c;
+}
+
+// Unary code of a value's bit width: bits 0 .. W(z)-1 set, W(z) = bits
+// needed to write z (0 for z = 0). Bit b is set exactly when z needs more
+// than b bits. (PTX shr clamps the shift amount at 32, giving 0 for z = 0.)
+__device__ __forceinline__ uint32_t width_unary(uint32_t z) {
+  uint32_t u;
+  asm("shr.b32 %0, %1, %2;" : "=r"(u) : "r"(0xffffffffu), "r"((uint32_t)__clz(z)));
+  return u;
 }
 
 }  // namespace jiffy

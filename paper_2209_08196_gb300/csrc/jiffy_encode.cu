@@ -3,114 +3,49 @@
 // One call codes T consecutive scans of each of one or more streams (the
 // segments of the call), all in parallel: the P prediction of scan t uses the
 // *input* of scan t-1 (Sec. III-D), so no scan waits for another's output.
-// Four launches:
-//   k_trial      one CTA per section (scan, attribute): I/P choice by trial
-//                compression of a few scanlines, mask excluded (Sec. III-E,
-//                Sec. IV-E).
-//   k_encode     one warp per row item (scan, attribute, row), ticket order:
-//                stage the row -> quantize (Sec. III-B) -> zero bitmask
-//                (Sec. III-C) -> mask XOR with the previous scan for P
-//                (Sec. III-D) -> compaction -> residual -> delta (the carry
-//                from the previous row's tail, else a look-back) -> ZigZag
-//                (Eq. 1) -> block widths and packing of 128-value blocks
-//                (Sec. II) into the row's slot.
-//   k_sec_sizes  one CTA per section: its bytes and nonzero count.
-//   k_place      one CTA per section: offsets, row table, chunk copies, frame
-//                and stream headers.
+// Three launches:
+//   k_trial     one warp per (section, test row): I and P residuals of the
+//               scanline, delta chained across the test rows, priced with
+//               the block-width pass below; the bytes add up per section and
+//               mode (trial compression, mask excluded, Sec. III-E, IV-E).
+//   k_encode    one warp per row item (scan, attribute, row), items taken in
+//               ticket order. Per row:
+//     pass A    8 consecutive pixels per lane per 256-pixel step: quantize
+//               (Sec. III-B), zero bitmask (Sec. III-C), mask XOR with the
+//               previous scan for P (Sec. III-D), residual (I: q, P: q - q'),
+//               compaction of the nonzero samples (warp scan of counts) into
+//               a swizzled shared buffer.
+//     pass B1   32 consecutive values per lane (8 blocks of 128 per warp
+//               step): delta (Sec. III-C) from the previous row's last
+//               residual, ZigZag (Eq. 1), then per block the count of values
+//               wider than b for every b at once -- carry-save adders over
+//               the values' unary width codes, bit-sliced across the 4 lanes
+//               of a block -- and the byte-minimal width (Sec. II, PFOR).
+//     place     the row's chunk size goes into a decoupled look-back over
+//               all rows of the segment (Merrill & Garland, 2016), giving
+//               the chunk's final byte offset in the stream.
+//     pass B2   one block at a time, 4 consecutive values per lane: low bits
+//               assembled in registers with funnel shifts and merged into
+//               the block body in shared memory, exceptions apart; then the
+//               mask code, block headers and bodies go straight to the
+//               stream.
+//   k_finalize  one CTA per section: row table, frame and stream headers.
 #include "jiffy_device.cuh"
 #include "jiffy_kernels.h"
 
 namespace jiffy {
 
-// ----------------------------------------------------------------------------
-// Row load: quantize the samples of one row (and of the previous scan's row),
-// build the zero bitmask words, and compact the residuals of the nonzero
-// samples into shared memory in row-major order.
-//   want_i / want_p: write I residuals (q) to eI and/or P residuals (q - pq)
-//   to eP. coded (nullable): receives per word M (mode I) or M ^ Mprev (P).
-//   Both rows hold raw samples (the stored previous scan is dequantized, and
-//   quantizing q * P gives q back), so one quantizer serves both.
-// Returns the row's nonzero count. Every thread calls it.
-// ----------------------------------------------------------------------------
-struct RowLoad {
-  const uint8_t* cur;   // row of the current scan (raw samples)
-  const uint8_t* prev;  // row of the previous scan, or null
-  AttrDev at;           // quantizer
-  uint32_t W, nw;
-};
+namespace {
 
-__device__ uint32_t load_compact_row(const RowLoad& L, bool want_i, bool want_p, bool xor_prev,
-                                     uint32_t* eI, uint32_t* eP, uint32_t* coded, uint32_t* s_cnt) {
-  const uint32_t lane = lane_id(), warp = warp_id();
-  const uint32_t s = L.at.s;
-  uint32_t total = 0;
-  for (uint32_t wbase = 0; wbase < L.nw; wbase += kWarps * kSegWords) {
-    uint32_t v[kSegWords], pv[kSegWords];
-#pragma unroll
-    for (uint32_t i = 0; i < kSegWords; i++) {
-      uint32_t j = wbase + warp * kSegWords + i;
-      uint32_t x = j * 32u + lane;
-      bool in = j < L.nw && x < L.W;
-      v[i] = in ? load_sample(L.cur, s, x) : 0u;
-      pv[i] = (in && L.prev) ? load_sample(L.prev, s, x) : 0u;
-    }
-    uint32_t ei[kSegWords], ep[kSegWords], nzm[kSegWords];
-    uint32_t cnt = 0;
-#pragma unroll
-    for (uint32_t i = 0; i < kSegWords; i++) {
-      uint32_t j = wbase + warp * kSegWords + i;
-      uint32_t x = j * 32u + lane;
-      bool in = j < L.nw && x < L.W;
-      uint32_t q = quantize(v[i], L.at);
-      uint32_t pq = L.prev ? quantize(pv[i], L.at) : 0u;
-      uint32_t nz = __ballot_sync(0xffffffffu, in && q != 0u);
-      if (coded) {
-        uint32_t m = __ballot_sync(0xffffffffu, in && q == 0u);  // Sec. III-C: 1 = zero sample
-        if (xor_prev) m ^= __ballot_sync(0xffffffffu, in && pq == 0u);  // Sec. III-D
-        if (lane == 0 && j < L.nw) coded[j] = m;
-      }
-      ei[i] = q;
-      ep[i] = q - pq;  // modulo 2^32
-      nzm[i] = nz;
-      cnt += __popc(nz);
-    }
-    if (lane == 0) s_cnt[warp] = cnt;
-    __syncthreads();
-    uint32_t base = total, seg = 0;
-#pragma unroll
-    for (int w2 = 0; w2 < kWarps; w2++) {
-      uint32_t c = s_cnt[w2];
-      if ((uint32_t)w2 < warp) base += c;
-      seg += c;
-    }
-    const uint32_t below = (1u << lane) - 1u;
-#pragma unroll
-    for (uint32_t i = 0; i < kSegWords; i++) {
-      uint32_t nz = nzm[i];
-      if ((nz >> lane) & 1u) {
-        uint32_t k = base + __popc(nz & below);
-        if (want_i) eI[k] = ei[i];
-        if (want_p) eP[k] = ep[i];
-      }
-      base += __popc(nz);
-    }
-    total += seg;
-    __syncthreads();
-  }
-  return total;
-}
+constexpr uint32_t kStepPx = 256;    // pixels per warp step of pass A (8 per lane)
+constexpr uint32_t kStepVal = 1024;  // values per warp step of pass B1 (32 per lane)
 
-// Warp-wide: loads block blk of z (n values) into lanes (4 per lane).
-__device__ __forceinline__ void load_block(const uint32_t* z, uint32_t n, uint32_t (&r)[4]) {
-  const uint32_t lane = lane_id();
-#pragma unroll
-  for (int m = 0; m < 4; m++) {
-    uint32_t i = lane + 32u * m;
-    r[m] = i < n ? z[i] : 0u;
-  }
-}
+// Residual buffer layout: value k lives in 32-value segment k >> 5; the
+// segment's 16-byte chunks are XOR-swizzled by the segment index so that a
+// lane reading a whole segment and a lane reading 4 consecutive values both
+// hit distinct banks.
+__device__ __forceinline__ uint32_t swz(uint32_t k) { return k ^ (((k >> 5) & 7u) << 2); }
 
-// Index of the segment holding global index key: the last i with base[i] <= key.
 __device__ __forceinline__ uint32_t find_seg(const uint32_t* base, uint32_t n, uint32_t key) {
   uint32_t lo = 0, hi = n;  // base[lo] <= key < base[hi] (base[n] = infinity)
   while (hi - lo > 1) {
@@ -121,80 +56,421 @@ __device__ __forceinline__ uint32_t find_seg(const uint32_t* base, uint32_t n, u
   return lo;
 }
 
-// ----------------------------------------------------------------------------
-// k_trial: Sec. III-E. For scans with a predecessor and no forced mode, codes
-// the test rows floor((2k+1)H/(2L)) (de-duplicated) both ways, the residuals
-// of the test rows delta-coded as one flat vector from 0 and packed per row,
-// and picks P iff its packed bytes are strictly fewer.
-// ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_trial(EncParams p) {
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint32_t s_cnt[kWarps + 1];
-  __shared__ unsigned long long s_cost[2];
-  __shared__ uint32_t s_rows[kMaxTestLines];
-  __shared__ uint32_t s_nrows;
-  __shared__ uint32_t s_hist[kWarps][33];
+__device__ __forceinline__ uint32_t mask_class(uint32_t c, uint32_t valid) {
+  return c == 0u ? 0u : (c == valid ? 1u : 2u);
+}
 
-  const uint32_t gs = blockIdx.x;
+__device__ __forceinline__ uint32_t valid_bits(uint32_t W, uint32_t nw, uint32_t j) {
+  return (j + 1 < nw || (W & 31u) == 0) ? 0xffffffffu : ((1u << (W & 31u)) - 1u);
+}
+
+// Mode of section (scan t, attribute a): the first frame after create/reset
+// is I; forced modes; else P iff the trial priced P strictly cheaper.
+__device__ __forceinline__ uint32_t section_mode(const EncParams& p, const EncSeg& sg, uint32_t sec, uint32_t t) {
+  if (sg.frame0 + t == 0 || sg.force_mode == 0) return 0u;
+  if (sg.force_mode == 1) return 1u;
+  return p.cost[2 * sec + 1] < p.cost[2 * sec] ? 1u : 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Pass A (one row): returns the number n of nonzero samples; their residuals
+// go to zb in row-major order (swizzled), the coded mask bytes (M, or M xor
+// M_prev for P) to mb, and, for the call's last scan, q * P to st_row.
+// ---------------------------------------------------------------------------
+template <bool PM, int QU>
+__device__ __forceinline__ uint32_t pass_a(const uint8_t* cur, const uint8_t* prv, uint8_t* st_row, const AttrDev at,
+                                        uint32_t W, uint32_t* zb, uint8_t* mb) {
+  const uint32_t lane = lane_id(), S = at.s;
+  const bool vc = vec_ok(cur, S), vp = PM && vec_ok(prv, S), vs = st_row && vec_ok(st_row, S);
+  const uint32_t Wm = (W + 31u) & ~31u;
+  uint32_t n = 0;
+  for (uint32_t base = 0; base < W; base += kStepPx) {
+    const uint32_t x0 = base + 8u * lane;
+    const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
+    uint32_t v[8], pv[8];
+    load8<false>(cur, S, x0, nv, vc, v);
+    if (PM) load8<false>(prv, S, x0, nv, vp, pv);
+    uint32_t e[8], zm = 0, pm = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const uint32_t q = quant<QU>(v[i], at);
+      v[i] = q;
+      zm |= (q == 0u ? 1u : 0u) << i;  // Sec. III-C: 1 = zero sample
+      if (PM) {
+        const uint32_t pq = quant<QU>(pv[i], at);
+        pm |= (pq == 0u ? 1u : 0u) << i;
+        e[i] = q - pq;  // Sec. III-D, modulo 2^32
+      } else {
+        e[i] = q;
+      }
+    }
+    const uint32_t vm = (1u << nv) - 1u;
+    const uint32_t nz = ~zm & vm;
+    if (x0 < Wm) mb[x0 >> 3] = (uint8_t)((PM ? (zm ^ pm) : zm) & vm);
+    if (st_row && nv) {  // the next call's previous scan, dequantized as the decoder holds it
+      uint32_t sv[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) sv[i] = v[i] * at.P;
+      store8(st_row, S, x0, nv, vs, sv);
+    }
+    uint32_t tot;
+    uint32_t kk = n + warp_excl_scan(__popc(nz), tot);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      if ((nz >> i) & 1u) {
+        zb[swz(kk)] = e[i];
+        kk++;
+      }
+    }
+    n += tot;
+  }
+  return n;
+}
+
+// Pass A of the trial: the residuals of the row's nonzero samples both ways
+// (I to zi, P to zp).
+template <int QU>
+__device__ __forceinline__ uint32_t pass_a_trial(const uint8_t* cur, const uint8_t* prv, const AttrDev at, uint32_t W,
+                                              uint32_t* zi, uint32_t* zp) {
+  const uint32_t lane = lane_id(), S = at.s;
+  const bool vc = vec_ok(cur, S), vp = vec_ok(prv, S);
+  uint32_t n = 0;
+  for (uint32_t base = 0; base < W; base += kStepPx) {
+    const uint32_t x0 = base + 8u * lane;
+    const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
+    uint32_t v[8], pv[8];
+    load8<false>(cur, S, x0, nv, vc, v);
+    load8<false>(prv, S, x0, nv, vp, pv);
+    uint32_t zm = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      v[i] = quant<QU>(v[i], at);
+      pv[i] = v[i] - quant<QU>(pv[i], at);
+      zm |= (v[i] == 0u ? 1u : 0u) << i;
+    }
+    const uint32_t nz = ~zm & ((1u << nv) - 1u);
+    uint32_t tot;
+    uint32_t kk = n + warp_excl_scan(__popc(nz), tot);
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      if ((nz >> i) & 1u) {
+        zi[swz(kk)] = v[i];
+        zp[swz(kk)] = pv[i];
+        kk++;
+      }
+    }
+    n += tot;
+  }
+  return n;
+}
+
+// The residuals (I and, with prv, P) of the last nonzero sample among the
+// row's last max_steps 256-pixel steps. Returns false if there is none.
+template <int QU>
+__device__ __noinline__ bool row_last(const uint8_t* cur, const uint8_t* prv, const AttrDev at, uint32_t W,
+                                      uint32_t max_steps, uint32_t* e_i, uint32_t* e_p) {
+  const uint32_t lane = lane_id(), S = at.s;
+  const uint32_t nsteps = ceil_div_u32(W, kStepPx);
+  const bool vc = vec_ok(cur, S), vp = prv && vec_ok(prv, S);
+  for (uint32_t si = 0; si < min(nsteps, max_steps); si++) {
+    const uint32_t x0 = kStepPx * (nsteps - 1u - si) + 8u * lane;
+    const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
+    uint32_t v[8], pv[8];
+    load8<false>(cur, S, x0, nv, vc, v);
+    if (prv) load8<false>(prv, S, x0, nv, vp, pv);
+    bool has = false;
+    uint32_t li = 0, lp = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+      const uint32_t q = quant<QU>(v[i], at);
+      if ((uint32_t)i < nv && q != 0u) {
+        has = true;
+        li = q;
+        lp = prv ? q - quant<QU>(pv[i], at) : q;
+      }
+    }
+    const uint32_t hm = __ballot_sync(0xffffffffu, has);
+    if (hm) {
+      const uint32_t src = 31u - __clz(hm);
+      *e_i = __shfl_sync(0xffffffffu, li, src);
+      *e_p = __shfl_sync(0xffffffffu, lp, src);
+      return true;
+    }
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Pass B1: delta + ZigZag in place and the width of every block (Sec. II:
+// b in [0, wmax] minimising the block's body bytes, ties to the smallest b).
+// Lane l of a warp step holds values 32l .. 32l+31 of the step: the 4 lanes
+// 4g'..4g'+3 hold block g' of the step. For each value, its unary width code
+// has bit b set iff the value needs more than b bits, so the column sums of
+// a block's unary codes are e_b = #values wider than b, for all b at once:
+// carry-save adders give each lane its 6 bit planes (counts <= 32), two
+// bit-sliced additions across the block's 4 lanes give 8 planes (counts <=
+// 128). Each lane then prices the candidates b = j, j+4, ... (j = lane & 3).
+// meta[g] = {b | e << 8 | hb << 16, body bytes}. Returns the sum over blocks
+// of header + body bytes.
+// ---------------------------------------------------------------------------
+template <bool WRITE>
+__device__ __forceinline__ uint32_t pass_b1(uint32_t* zb, uint32_t n, uint32_t carry, uint2* meta) {
+  const uint32_t lane = lane_id(), j = lane & 3u;
+  uint32_t pred_step = carry;  // the residual before the step's first value
+  uint32_t total = 0;
+  for (uint32_t s0 = 0; s0 < n; s0 += kStepVal) {
+    const uint32_t seg = (s0 >> 5) + lane;
+    uint4* sp = reinterpret_cast<uint4*>(zb + 32u * seg);
+    uint32_t z[32];
+#pragma unroll
+    for (uint32_t c = 0; c < 8; c++) {
+      const uint4 v = sp[c ^ (seg & 7u)];
+      z[4 * c] = v.x; z[4 * c + 1] = v.y; z[4 * c + 2] = v.z; z[4 * c + 3] = v.w;
+    }
+    uint32_t pred = __shfl_up_sync(0xffffffffu, z[31], 1);
+    if (lane == 0) pred = pred_step;
+    pred_step = __shfl_sync(0xffffffffu, z[31], 31);
+    const uint32_t kb = s0 + 32u * lane;
+    // delta (Sec. III-C) and ZigZag (Eq. 1); values past n become 0
+#pragma unroll
+    for (int i = 31; i >= 0; i--) {
+      const uint32_t d = z[i] - (i ? z[i - 1] : pred);
+      z[i] = kb + (uint32_t)i < n ? zigzag(d) : 0u;
+    }
+    if (WRITE) {
+#pragma unroll
+      for (uint32_t c = 0; c < 8; c++) sp[c ^ (seg & 7u)] = make_uint4(z[4 * c], z[4 * c + 1], z[4 * c + 2], z[4 * c + 3]);
+    }
+    // per-lane column counts of the unary width codes: 6 bit planes
+    uint32_t p1, p2, p4, p8, p16, p32;
+    {
+      uint32_t ones = 0, twos = 0, fours = 0, eights = 0, sixteens[2];
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        uint32_t ta, tb, fa, fb, ea, eb;
+        const int o = 16 * h;
+        csa(ta, ones, ones, width_unary(z[o + 0]), width_unary(z[o + 1]));
+        csa(tb, ones, ones, width_unary(z[o + 2]), width_unary(z[o + 3]));
+        csa(fa, twos, twos, ta, tb);
+        csa(ta, ones, ones, width_unary(z[o + 4]), width_unary(z[o + 5]));
+        csa(tb, ones, ones, width_unary(z[o + 6]), width_unary(z[o + 7]));
+        csa(fb, twos, twos, ta, tb);
+        csa(ea, fours, fours, fa, fb);
+        csa(ta, ones, ones, width_unary(z[o + 8]), width_unary(z[o + 9]));
+        csa(tb, ones, ones, width_unary(z[o + 10]), width_unary(z[o + 11]));
+        csa(fa, twos, twos, ta, tb);
+        csa(ta, ones, ones, width_unary(z[o + 12]), width_unary(z[o + 13]));
+        csa(tb, ones, ones, width_unary(z[o + 14]), width_unary(z[o + 15]));
+        csa(fb, twos, twos, ta, tb);
+        csa(eb, fours, fours, fa, fb);
+        csa(sixteens[h], eights, eights, ea, eb);
+      }
+      p1 = ones; p2 = twos; p4 = fours; p8 = eights;
+      p16 = sixteens[0] ^ sixteens[1];
+      p32 = sixteens[0] & sixteens[1];
+    }
+    // bit-sliced sums across the block's 4 lanes: 8 planes E[0..7]
+    uint32_t E[8];
+    {
+      uint32_t A[6] = {p1, p2, p4, p8, p16, p32}, B[7];
+#pragma unroll
+      for (int k = 0; k < 6; k++) B[k] = __shfl_xor_sync(0xffffffffu, A[k], 1);
+      uint32_t C[7], c = 0;
+#pragma unroll
+      for (int k = 0; k < 6; k++) {
+        const uint32_t u = A[k] ^ B[k];
+        C[k] = u ^ c;
+        c = (A[k] & B[k]) | (u & c);
+      }
+      C[6] = c;
+#pragma unroll
+      for (int k = 0; k < 7; k++) B[k] = __shfl_xor_sync(0xffffffffu, C[k], 2);
+      c = 0;
+#pragma unroll
+      for (int k = 0; k < 7; k++) {
+        const uint32_t u = C[k] ^ B[k];
+        E[k] = u ^ c;
+        c = (C[k] & B[k]) | (u & c);
+      }
+      E[7] = c;
+    }
+    const uint32_t anyb = E[0] | E[1] | E[2] | E[3] | E[4] | E[5] | E[6] | E[7];
+    const uint32_t wmax = 32u - __clz(anyb);  // e_b > 0 exactly for b < wmax
+    const uint32_t g = (s0 >> 7) + (lane >> 2);
+    const uint32_t m = n > 128u * g ? min(128u, n - 128u * g) : 0u;
+    // e_b for b = j + 4i: nibble i of lo (low 4 bits) and hi (high 4 bits)
+    uint32_t lo4, hi4;
+    {
+      uint32_t F[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) F[k] = (E[k] >> j) & 0x11111111u;
+      lo4 = F[0] + 2u * F[1] + 4u * F[2] + 8u * F[3];
+      hi4 = F[4] + 2u * F[5] + 4u * F[6] + 8u * F[7];
+    }
+    const uint32_t wtop = __reduce_max_sync(0xffffffffu, m ? wmax : 0u);
+    uint32_t key = 0xffffffffu;
+#pragma unroll
+    for (uint32_t i = 0; i < 9; i++) {
+      if (4u * i > wtop) break;
+      const uint32_t b = j + 4u * i;
+      const uint32_t e = i < 8 ? ((lo4 >> (4 * i)) & 15u) | (((hi4 >> (4 * i)) & 15u) << 4) : 0u;
+      const uint32_t f = 4u * ((m * b + 31u) >> 5) + ((e + 3u) & ~3u) + 4u * ((e * (wmax - b) + 31u) >> 5);
+      if (b <= wmax) key = min(key, (f << 14) | (b << 8) | e);
+    }
+    key = min(key, __shfl_xor_sync(0xffffffffu, key, 1));
+    key = min(key, __shfl_xor_sync(0xffffffffu, key, 2));
+    if (m && j == 0) {
+      const uint32_t b = (key >> 8) & 63u, e = key & 255u, f = key >> 14;
+      if (WRITE) meta[g] = make_uint2(b | (e << 8) | ((e ? wmax - b : 0u) << 16), f);
+      total += 4u + f;
+    }
+  }
+  return __reduce_add_sync(0xffffffffu, total);
+}
+
+// ---------------------------------------------------------------------------
+// Pass B2: packs every block's body into zb, in place and unswizzled (block
+// g's body lands in words [off_g, off_g + size_g) with off_g + size_g <=
+// 128 (g + 1), so it never reaches a value still to be read). Lane l holds
+// values 4l .. 4l+3 of the block: their low b bits are joined in registers
+// (4b bits) and OR-ed into the body at bit 4lb (Sec. II: low parts of all
+// values, then the exceptions' positions and high parts).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pass_b2(uint32_t* zb, uint32_t n, uint32_t nb, const uint2* meta) {
+  const uint32_t lane = lane_id(), below = (1u << lane) - 1u;
+  for (uint32_t g = 0; g < nb; g++) {
+    const uint2 md = meta[g];  // .x header, .y body byte offset
+    const uint32_t b = md.x & 0xffu, e = (md.x >> 8) & 0xffu, hb = (md.x >> 16) & 0xffu;
+    const uint32_t m = min(128u, n - 128u * g);
+    const uint32_t off = md.y >> 2;
+    const uint32_t low_words = (m * b + 31u) >> 5;
+    const uint32_t size_words = block_body_bytes(m, b, e, b + hb) >> 2;
+    const uint32_t sgi = 4u * g + (lane >> 3);
+    const uint4 zz = reinterpret_cast<const uint4*>(zb + 32u * sgi)[(lane & 7u) ^ (sgi & 7u)];
+    const uint32_t z[4] = {zz.x, zz.y, zz.z, zz.w};
+    __syncwarp();
+    for (uint32_t i = lane; i < size_words; i += 32u) zb[off + i] = 0u;
+    __syncwarp();
+    if (b) {
+      const uint32_t bm = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
+      const uint32_t l0 = z[0] & bm, l1 = z[1] & bm, l2 = z[2] & bm, l3 = z[3] & bm;
+      const uint32_t bit = 4u * lane * b, sh = bit & 31u;
+      uint32_t* dst = zb + off + (bit >> 5);
+      if (b <= 8u) {
+        const uint32_t x = l0 | (l1 << b) | (l2 << (2u * b)) | (l3 << (3u * b));
+        const uint32_t y0 = x << sh, y1 = __funnelshift_l(x, 0u, sh);
+        if (y0) atomicOr(dst, y0);
+        if (y1) atomicOr(dst + 1, y1);
+      } else if (b <= 16u) {
+        const unsigned long long x = (unsigned long long)l0 | ((unsigned long long)l1 << b) |
+                                     ((unsigned long long)l2 << (2u * b)) | ((unsigned long long)l3 << (3u * b));
+        const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
+        const uint32_t y0 = x0 << sh, y1 = __funnelshift_l(x0, x1, sh), y2 = __funnelshift_l(x1, 0u, sh);
+        if (y0) atomicOr(dst, y0);
+        if (y1) atomicOr(dst + 1, y1);
+        if (y2) atomicOr(dst + 2, y2);
+      } else {
+        // 4b in (64, 128]: lo = l0 | l1 << b (2b bits), hi = l2 | l3 << b,
+        // x = lo | hi << 2b with 2b - 32 = s in (0, 32]
+        const unsigned long long lo = (unsigned long long)l0 | ((unsigned long long)l1 << b);
+        const unsigned long long hi = (unsigned long long)l2 | ((unsigned long long)l3 << b);
+        const uint32_t s = 2u * b - 32u;
+        const uint32_t h0 = (uint32_t)hi, h1 = (uint32_t)(hi >> 32);
+        const uint32_t x0 = (uint32_t)lo;
+        const uint32_t x1 = (uint32_t)(lo >> 32) | __funnelshift_lc(0u, h0, s);
+        const uint32_t x2 = __funnelshift_lc(h0, h1, s);
+        const uint32_t x3 = __funnelshift_lc(h1, 0u, s);
+        const uint32_t y0 = x0 << sh, y1 = __funnelshift_l(x0, x1, sh), y2 = __funnelshift_l(x1, x2, sh),
+                       y3 = __funnelshift_l(x2, x3, sh), y4 = __funnelshift_l(x3, 0u, sh);
+        if (y0) atomicOr(dst, y0);
+        if (y1) atomicOr(dst + 1, y1);
+        if (y2) atomicOr(dst + 2, y2);
+        if (y3) atomicOr(dst + 3, y3);
+        if (y4) atomicOr(dst + 4, y4);
+      }
+    }
+    if (e) {  // exceptions: position bytes (ascending), then high parts of hb bits
+      bool isx[4];
+      uint32_t rank = 0;
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        isx[q] = b < 32u && (z[q] >> b) != 0u;
+        rank += __popc(__ballot_sync(0xffffffffu, isx[q]) & below);
+      }
+      uint8_t* pos = reinterpret_cast<uint8_t*>(zb + off + low_words);
+      const uint32_t hw0 = off + low_words + ((e + 3u) >> 2);
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        if (isx[q]) {
+          pos[rank] = (uint8_t)(4u * lane + q);
+          const uint32_t hv = z[q] >> b, hbit = rank * hb, hs = hbit & 31u;
+          uint32_t* hp = zb + hw0 + (hbit >> 5);
+          atomicOr(hp, hv << hs);
+          if (hs + hb > 32u) atomicOr(hp + 1, hv >> (32u - hs));
+          rank++;
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------
+// k_trial: Sec. III-E. For sections with a predecessor and no forced mode,
+// one warp per test row floor((2k+1)H/(2L)) (de-duplicated): the I and P
+// residuals of the row, delta-chained from the last residual of the earlier
+// test rows (the test rows' residuals form one flat vector starting from 0),
+// priced per block. cost[2 sec + mode] += the row's block bytes.
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(32) k_trial(EncParams p) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  const uint32_t gs = blockIdx.x / p.trial_rows, ti = blockIdx.x % p.trial_rows;
   const EncSeg& sg = p.seg[find_seg(p.seg_sec_base, p.n_seg, gs)];
   const uint32_t ta = gs - sg.sec_base;
   const uint32_t t = ta / sg.A, a = ta % sg.A;
-  uint32_t* eI = smem;
-  uint32_t* eP = smem + sg.W;
-  if (sg.frame0 + t == 0 || sg.force_mode == 0) {
-    if (threadIdx.x == 0) p.modes[gs] = 0;
-    return;
+  if (sg.frame0 + t == 0 || sg.force_mode >= 0) return;
+  // the distinct test rows, ascending
+  const uint32_t L = sg.test_lines, H = sg.H;
+  uint32_t rows[kMaxTestLines];
+  uint32_t nr = 0;
+  for (uint32_t k = 0; k < L; k++) {
+    const uint32_t r = (uint32_t)(((unsigned long long)(2 * k + 1) * H) / (2ull * L));
+    if (nr == 0 || rows[nr - 1] != r) rows[nr++] = r;
   }
-  if (sg.force_mode == 1) {
-    if (threadIdx.x == 0) p.modes[gs] = 1;
-    return;
-  }
+  if (ti >= nr) return;
   const AttrDev at = sg.attrs[a];
-  if (threadIdx.x == 0) {
-    uint32_t n = 0;
-    for (uint32_t k = 0; k < sg.test_lines; k++) {
-      uint32_t r = (uint32_t)(((unsigned long long)(2 * k + 1) * sg.H) / (2ull * sg.test_lines));
-      if (n == 0 || s_rows[n - 1] != r) s_rows[n++] = r;
-    }
-    s_nrows = n;
-    s_cost[0] = s_cost[1] = 0;
+  const uint32_t W = sg.W;
+  const size_t rowb = (size_t)W * at.s;
+  const uint8_t* cur = sg.cur[ta];
+  const uint8_t* prv = sg.prev[ta];
+  uint32_t* zi = smem;
+  uint32_t* zp = smem + ((W + kStepVal - 1) / kStepVal) * kStepVal;
+  // carry: the last residual of the nearest earlier test row that has one
+  uint32_t ci = 0, cp = 0;
+  for (int k = (int)ti - 1; k >= 0; k--) {
+    const uint8_t* c0 = cur + rows[k] * rowb;
+    const uint8_t* p0 = prv + rows[k] * rowb;
+    bool f;
+    if (at.qkind == 0) f = row_last<0>(c0, p0, at, W, 0xffffffffu, &ci, &cp);
+    else if (at.qkind == 1) f = row_last<1>(c0, p0, at, W, 0xffffffffu, &ci, &cp);
+    else f = row_last<2>(c0, p0, at, W, 0xffffffffu, &ci, &cp);
+    if (f) break;
   }
-  __syncthreads();
-  const size_t rowb = (size_t)sg.W * at.s;
-  uint32_t carry_i = 0, carry_p = 0;  // flat vector starts from 0
-  unsigned long long cost_i = 0, cost_p = 0;  // per-warp partial sums (lane 0)
-  for (uint32_t ri = 0; ri < s_nrows; ri++) {
-    const uint32_t r = s_rows[ri];
-    RowLoad L{sg.cur[ta] + r * rowb, sg.prev[ta] + r * rowb, at, sg.W, sg.nw};
-    uint32_t n = load_compact_row(L, true, true, false, eI, eP, nullptr, s_cnt);
-    // residuals -> delta -> ZigZag -> block costs, both modes
-    const uint32_t nb = ceil_div_u32(n, kBlockN);
-    for (uint32_t blk = warp_id(); blk < 2 * nb; blk += kWarps) {
-      const uint32_t mode = blk / nb, bi = blk % nb;
-      const uint32_t* e = mode ? eP : eI;
-      const uint32_t carry = mode ? carry_p : carry_i;
-      const uint32_t base = bi * kBlockN, m = min(kBlockN, n - base);
-      uint32_t z[4];
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        uint32_t i = base + lane_id() + 32u * q;
-        z[q] = (i - base) < m ? zigzag(e[i] - (i ? e[i - 1] : carry)) : 0u;
-      }
-      BlockChoice c = choose_block(z, m, s_hist[warp_id()]);
-      if (lane_id() == 0) {
-        if (mode) cost_p += 4u + c.bytes;
-        else cost_i += 4u + c.bytes;
-      }
-    }
-    if (n > 0) { carry_i = eI[n - 1]; carry_p = eP[n - 1]; }
-    __syncthreads();  // e arrays are rewritten by the next row
-  }
+  const uint8_t* c1 = cur + rows[ti] * rowb;
+  const uint8_t* p1 = prv + rows[ti] * rowb;
+  uint32_t n;
+  if (at.qkind == 0) n = pass_a_trial<0>(c1, p1, at, W, zi, zp);
+  else if (at.qkind == 1) n = pass_a_trial<1>(c1, p1, at, W, zi, zp);
+  else n = pass_a_trial<2>(c1, p1, at, W, zi, zp);
+  __syncwarp();
+  const uint32_t cost_i = pass_b1<false>(zi, n, ci, nullptr);
+  const uint32_t cost_p = pass_b1<false>(zp, n, cp, nullptr);
   if (lane_id() == 0) {
-    atomicAdd(&s_cost[0], cost_i);
-    atomicAdd(&s_cost[1], cost_p);
+    atomicAdd(p.cost + 2 * gs, cost_i);
+    atomicAdd(p.cost + 2 * gs + 1, cost_p);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) p.modes[gs] = s_cost[1] < s_cost[0] ? 1u : 0u;
 }
 
 // ----------------------------------------------------------------------------
@@ -203,206 +479,104 @@ __global__ void __launch_bounds__(kThreads) k_trial(EncParams p) {
 // earlier items) was handed out earlier. No CTA-wide barrier.
 // ----------------------------------------------------------------------------
 
-// Per-warp shared memory (byte offsets): ZigZag values of the row, coded mask
-// words, per-block {header, body byte offset}, width histogram, and the body
-// of the block being packed.
+// Per-warp shared memory (byte offsets): residual / ZigZag / packed-body
+// buffer (values rounded up to whole pass-B1 steps), coded mask bytes, block
+// metadata.
 struct EncWarpLayout {
-  uint32_t z, coded, meta, hist, pbuf, bytes;
+  uint32_t zb, mb, meta, bytes;
 };
 
 __host__ __device__ inline EncWarpLayout enc_warp_layout(uint32_t W) {
-  const uint32_t nbmax = ceil_div_u32(W, kBlockN), nw = ceil_div_u32(W, 32);
+  const uint32_t nbmax = ceil_div_u32(W, kBlockN);
   auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
   EncWarpLayout L;
-  L.z = 0;
-  L.coded = a16(4u * W);
-  L.meta = a16(L.coded + 4u * nw);
-  L.hist = a16(L.meta + 8u * nbmax);
-  L.pbuf = a16(L.hist + 4u * 36u);
-  L.bytes = a16(L.pbuf + 4u * 192u);  // a packed block body never exceeds 162 words
+  L.zb = 0;
+  L.mb = 4u * ceil_div_u32(W, kStepVal) * kStepVal;
+  L.meta = a16(L.mb + ceil_div_u32(W, 32) * 4u);
+  L.bytes = a16(L.meta + 8u * nbmax);
   return L;
 }
 
-__device__ __forceinline__ uint32_t mask_class(uint32_t c, uint32_t valid) {
-  return c == 0u ? 0u : (c == valid ? 1u : 2u);
-}
-
 struct EncWarp {
-  uint32_t* zbuf;
-  uint32_t* coded;
-  uint8_t* coded_b;
+  uint32_t* zb;
+  uint8_t* mb;
   uint2* meta;
-  uint32_t* hist;
-  uint32_t* pbuf;
 };
 
-// One row item, samples of S bytes (compile-time, so each warp runs one
-// compact path).
 __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k, const EncWarp& w) {
   const EncSeg& sg = p.seg[find_seg(p.seg_item_base, p.n_seg, k)];
   const uint32_t lane = lane_id();
   const uint32_t H = sg.H, W = sg.W, A = sg.A, nw = sg.nw, ncls = sg.ncls;
-  const uint32_t niter = ceil_div_u32(W, 256u);
-  const uint32_t below = (1u << lane) - 1u;
-  uint32_t* zbuf = w.zbuf;
-  uint32_t* coded = w.coded;
   const uint32_t kl = k - sg.item_base;  // item within the segment
   const uint32_t r = kl % H, ta = kl / H, a = ta % A, t = ta / A;
+  const uint32_t sec = sg.sec_base + ta;
   const uint32_t sec_start = k - r;  // global item of row 0 of this attribute-scan
   const AttrDev at = sg.attrs[a];
-  const uint32_t S = at.s;
-  const uint32_t mode = p.modes[sg.sec_base + ta];
-  const size_t rowb = (size_t)W * S;
+  const uint32_t mode = section_mode(p, sg, sec, t);
+  if (r == 0 && lane == 0) p.modes[sec] = mode;
+  const size_t rowb = (size_t)W * at.s;
   const uint8_t* cur = sg.cur[ta] + r * rowb;
   const uint8_t* prv = mode ? sg.prev[ta] + r * rowb : nullptr;
   uint8_t* st_row = (t + 1 == sg.T) ? sg.state_next[a] + r * rowb : nullptr;
-  const bool vec_prv = prv && vec_ok(prv, S), vec_st = st_row && vec_ok(st_row, S);
-
-  for (uint32_t j = lane; j < nw; j += 32) coded[j] = 0u;
-  // stage the row in one round of loads, at the top of the ZigZag buffer:
-  // ZigZag values fill it from the bottom and, with every lane reading its
-  // pixels of a step before any value of that step is written, never reach
-  // a pixel that is still to be read (raw row at byte (4 - S) * W)
-  uint8_t* raw = reinterpret_cast<uint8_t*>(zbuf) + (4u - S) * W;
-  stage_bytes(raw, cur, W * S);
-  if (prv) prefetch_l1(prv, (uint32_t)rowb);
-  const bool vec_cur = vec_ok(raw, S);
-  // the previous row's last 256 pixels, for the delta carry (read now, used
-  // after pass A)
-  const uint32_t px0 = W > 256u ? W - 256u : 0u;
-  const uint32_t pnv = px0 + 8u * lane < W ? min(8u, W - (px0 + 8u * lane)) : 0u;
-  uint32_t tv[8], tpv[8];
-  if (r > 0) {
-    const bool tvec = (px0 & 7u) == 0;
-    load8<false>(cur - rowb, S, px0 + 8u * lane, pnv, tvec && vec_ok(cur - rowb, S), tv);
-    if (prv) load8<false>(prv - rowb, S, px0 + 8u * lane, pnv, tvec && vec_ok(prv - rowb, S), tpv);
-  }
-  __syncwarp();
+  const int qk = (int)at.qkind;
 
   // ---- delta carry: the residual preceding this row in the attribute-scan's
   //      flat vector (Sec. III-C). The previous row's tail usually holds it;
   //      otherwise a "last valid" look-back over the earlier rows decides.
-  uint32_t carry = 0;
+  uint32_t carry = 0, unused;
   bool known = r == 0;  // e[-1] = 0 at the start of the attribute-scan
   if (r > 0) {
-    uint32_t tnz = 0, tlast = 0;
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-      const uint32_t q = quantize(tv[i], at);
-      const uint32_t pq = prv ? quantize(tpv[i], at) : 0u;
-      if ((uint32_t)i < pnv && q != 0u) {
-        tnz = 1u;
-        tlast = q - pq;
-      }
-    }
-    const uint32_t has = __ballot_sync(0xffffffffu, tnz != 0u);
-    if (has) {
-      carry = __shfl_sync(0xffffffffu, tlast, 31u - __clz(has));
-      known = true;
-    }
+    const uint8_t* pc = cur - rowb;
+    const uint8_t* pp = prv ? prv - rowb : nullptr;
+    if (qk == 0) known = row_last<0>(pc, pp, at, W, 1, &unused, &carry);
+    else if (qk == 1) known = row_last<1>(pc, pp, at, W, 1, &unused, &carry);
+    else known = row_last<2>(pc, pp, at, W, 1, &unused, &carry);
   }
-  // ---- pass A: quantize (Sec. III-B), zero mask (Sec. III-C), mask XOR
-  //      (Sec. III-D), compaction, residual, delta, ZigZag (Eq. 1)
-  uint32_t n = 0;          // nonzero samples so far (uniform)
-  uint32_t last_e = 0;     // last residual so far (uniform, valid when n > 0)
-  uint32_t e_first = 0;    // the row's first residual (uniform)
-  for (uint32_t it = 0; it < niter; it++) {
-    const uint32_t x0 = 256u * it + 8u * lane;
-    const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
-    uint32_t v[8], pv[8];
-    load8<false>(raw, S, x0, nv, vec_cur, v);
-    if (prv) load8<false>(prv, S, x0, nv, vec_prv, pv);
-    __syncwarp();  // every lane has its pixels of this step before values are written
-    uint32_t e[8];
-    uint32_t mb = 0, pm = 0;
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-      const uint32_t q = quantize(v[i], at);
-      v[i] = q;
-      const uint32_t pq = prv ? quantize(pv[i], at) : 0u;
-      mb |= (uint32_t)((uint32_t)i < nv && q == 0u) << i;
-      pm |= (uint32_t)((uint32_t)i < nv && pq == 0u) << i;
-      e[i] = q - pq;  // I: q (pq = 0); P: q - pq, modulo 2^32
-    }
-    if (st_row && nv) {  // the next call's previous scan, dequantized as the decoder holds it
-      uint32_t sv[8];
-#pragma unroll
-      for (int i = 0; i < 8; i++) sv[i] = v[i] * at.P;
-      store8(st_row, S, x0, nv, vec_st, sv);
-    }
-    if (nv) w.coded_b[x0 >> 3] = (uint8_t)(mode ? (mb ^ pm) : mb);
-    const uint32_t nz = ~mb & ((1u << nv) - 1u);
-    const uint32_t c = __popc(nz);
-    uint32_t tot;
-    const uint32_t k0 = n + warp_excl_scan(c, tot);
-    // the residual before this lane's first nonzero: the last one of the
-    // nearest lower lane that has any, else the last one so far
-    uint32_t my_last = 0, my_first = 0;
-#pragma unroll
-    for (int i = 7; i >= 0; i--)
-      if ((nz >> i) & 1u) my_first = e[i];
-#pragma unroll
-    for (int i = 0; i < 8; i++)
-      if ((nz >> i) & 1u) my_last = e[i];
-    const uint32_t has = __ballot_sync(0xffffffffu, c != 0u);
-    const uint32_t lower = has & below;
-    const uint32_t src = lower ? 31u - __clz(lower) : 0u;
-    const uint32_t from_lane = __shfl_sync(0xffffffffu, my_last, src);
-    uint32_t pe = lower ? from_lane : last_e;  // (n == 0: placeholder, fixed after the carry)
-    uint32_t kk = k0;
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-      if ((nz >> i) & 1u) {
-        zbuf[kk++] = zigzag(e[i] - pe);
-        pe = e[i];
-      }
-    }
-    if (has) {
-      const uint32_t hi = 31u - __clz(has), lo = __ffs(has) - 1u;
-      const uint32_t lastv = __shfl_sync(0xffffffffu, my_last, hi);
-      const uint32_t firstv = __shfl_sync(0xffffffffu, my_first, lo);
-      if (n == 0) e_first = firstv;
-      last_e = lastv;
-    }
-    n += tot;
+
+  // ---- pass A
+  uint32_t n;
+  if (mode) {
+    if (qk == 0) n = pass_a<true, 0>(cur, prv, st_row, at, W, w.zb, w.mb);
+    else if (qk == 1) n = pass_a<true, 1>(cur, prv, st_row, at, W, w.zb, w.mb);
+    else n = pass_a<true, 2>(cur, prv, st_row, at, W, w.zb, w.mb);
+  } else {
+    if (qk == 0) n = pass_a<false, 0>(cur, nullptr, st_row, at, W, w.zb, w.mb);
+    else if (qk == 1) n = pass_a<false, 1>(cur, nullptr, st_row, at, W, w.zb, w.mb);
+    else n = pass_a<false, 2>(cur, nullptr, st_row, at, W, w.zb, w.mb);
   }
+  __syncwarp();
+  const uint32_t last_e = n ? w.zb[swz(n - 1)] : 0u;
   if (lane == 0) {
-    const unsigned long long lastv = n ? last_e : carry;
-    if (known) st_publish(p.st_carry + k, kStInc | (1ull << 32) | lastv);
+    if (known) st_publish(p.st_carry + k, kStInc | (1ull << 32) | (n ? last_e : carry));
     else st_publish(p.st_carry + k, kStAgg | ((unsigned long long)(n ? 1 : 0) << 32) | last_e);
   }
 
-  // ---- block widths (Sec. II) of blocks 1.. first: only block 0 depends on
-  //      the carry, so a fallback wait overlaps this work
-  const uint32_t nb = ceil_div_u32(n, kBlockN);
-  auto width_of = [&](uint32_t blk) {
-    const uint32_t base = blk * kBlockN, m = min(kBlockN, n - base);
-    uint32_t z[4];
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const uint32_t i = lane + 32u * q;
-      z[q] = i < m ? zbuf[base + i] : 0u;
-    }
-    const BlockChoice bc = choose_block(z, m, w.hist);
-    if (lane == 0) w.meta[blk] = make_uint2(bc.b | (bc.e << 8) | (bc.hb << 16), bc.bytes);
-  };
-  for (uint32_t blk = 1; blk < nb; blk++) width_of(blk);
+  // ---- mask part size: literal words
+  const uint32_t* mbw = reinterpret_cast<const uint32_t*>(w.mb);
+  uint32_t nlit = 0;
+  for (uint32_t jb = 0; jb < nw; jb += 32) {
+    const uint32_t jw = jb + lane;
+    const bool lit = jw < nw && mask_class(mbw[jw], valid_bits(W, nw, jw)) == 2u;
+    nlit += __popc(__ballot_sync(0xffffffffu, lit));
+  }
+
   if (!known) {
     const bool ok = lookback_last(p.st_carry, k, sec_start, carry);
     if (lane == 0) st_publish(p.st_carry + k, ok ? (kStInc | (1ull << 32) | (n ? last_e : carry)) : kStErr);
     if (!ok) {
-      if (lane == 0) atomicOr(sg.err, kErrTimeout);
+      if (lane == 0) {
+        atomicOr(sg.err, kErrTimeout);
+        st_publish(p.st_bytes + k, kStErr);
+      }
       return;
     }
   }
-  if (n) {
-    if (lane == 0) zbuf[0] = zigzag(e_first - carry);
-    __syncwarp();
-    width_of(0);
-  }
-  __syncwarp();
 
-  // ---- body offsets: exclusive prefix of the block bytes (lane l: 4l..4l+3)
+  // ---- pass B1: delta, ZigZag, block widths
+  const uint32_t nb = ceil_div_u32(n, kBlockN);
+  pass_b1<true>(w.zb, n, carry, w.meta);
+  __syncwarp();
+  // body offsets: exclusive prefix of the block bytes (lane l: 4l..4l+3)
   uint32_t body = 0;
   {
     uint32_t bsz[4], mysum = 0;
@@ -412,41 +586,54 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
       bsz[q] = blk < nb ? w.meta[blk].y : 0u;
       mysum += bsz[q];
     }
-    uint32_t off = warp_excl_scan(mysum, body);
+    uint32_t o = warp_excl_scan(mysum, body);
 #pragma unroll
     for (uint32_t q = 0; q < 4; q++) {
       const uint32_t blk = 4u * lane + q;
-      if (blk < nb) w.meta[blk].y = off;
-      off += bsz[q];
+      if (blk < nb) w.meta[blk].y = o;
+      o += bsz[q];
     }
-  }
-
-  // ---- mask part size: literal words
-  uint32_t nlit = 0;
-  for (uint32_t jb = 0; jb < nw; jb += 32) {
-    const uint32_t j = jb + lane;
-    const uint32_t valid = (j + 1 < nw || (W & 31u) == 0) ? 0xffffffffu : ((1u << (W & 31u)) - 1u);
-    const bool lit = j < nw && mask_class(coded[j], valid) == 2u;
-    nlit += __popc(__ballot_sync(0xffffffffu, lit));
   }
   __syncwarp();
   const uint32_t head_words = ncls + nlit + nb;
   const uint32_t chunk = 4u * head_words + body;
+
+  // ---- placement: decoupled look-back over the segment's rows
+  unsigned long long excl = 0;
+  if (kl == 0) {
+    if (lane == 0) st_publish(p.st_bytes + k, kStInc | chunk);
+  } else {
+    if (lane == 0) st_publish(p.st_bytes + k, kStAgg | chunk);
+    const bool ok = lookback_sum(p.st_bytes, k, sg.item_base, excl);
+    if (lane == 0) st_publish(p.st_bytes + k, ok ? (kStInc | (excl + chunk)) : kStErr);
+    if (!ok) {
+      if (lane == 0) atomicOr(sg.err, kErrTimeout);
+      return;
+    }
+  }
   if (lane == 0) {
     p.row_bytes[k] = chunk;
     p.row_nnz[k] = n;
     p.row_carry[k] = carry;
+    p.row_off[k] = excl;
   }
-  // the chunk goes to this row's slot; k_place moves it to its offset
-  uint32_t* dst = reinterpret_cast<uint32_t*>(p.slots + sg.slot_base + (size_t)kl * sg.slot_bytes);
+  const unsigned long long at_b =
+      sg.shdr + (unsigned long long)(t + 1) * sg.fhdr + 8ull * H * (ta + 1) + excl;
+  const bool fits = at_b + chunk <= sg.cap;
+  if (!fits && lane == 0) atomicOr(sg.err, kErrCapacity);
+
+  // ---- pass B2: block bodies (in shared memory)
+  pass_b2(w.zb, n, nb, w.meta);
+  if (!fits) return;
+  uint32_t* dst = reinterpret_cast<uint32_t*>(sg.out + at_b);
 
   // ---- mask part: 2-bit class per word (16 per class word), literals
+  const uint32_t below = (1u << lane) - 1u;
   uint32_t litbase = 0;
   for (uint32_t jb = 0; jb < nw; jb += 32) {
-    const uint32_t j = jb + lane;
-    const uint32_t valid = (j + 1 < nw || (W & 31u) == 0) ? 0xffffffffu : ((1u << (W & 31u)) - 1u);
-    const uint32_t c = j < nw ? coded[j] : 0u;
-    const uint32_t cls = j < nw ? mask_class(c, valid) : 0u;
+    const uint32_t jw = jb + lane;
+    const uint32_t c = jw < nw ? mbw[jw] : 0u;
+    const uint32_t cls = jw < nw ? mask_class(c, valid_bits(W, nw, jw)) : 0u;
     uint32_t cw = cls << (2u * (lane & 15u));
 #pragma unroll
     for (int o = 1; o < 16; o <<= 1) cw |= __shfl_xor_sync(0xffffffffu, cw, o);
@@ -458,65 +645,21 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   }
   // ---- block headers and bodies
   for (uint32_t blk = lane; blk < nb; blk += 32) dst[ncls + nlit + blk] = w.meta[blk].x;
-  for (uint32_t blk = 0; blk < nb; blk++) {
-    const uint32_t base = blk * kBlockN, m = min(kBlockN, n - base);
-    const uint2 md = w.meta[blk];
-    const uint32_t b = md.x & 0xffu, ex = (md.x >> 8) & 0xffu, hb = (md.x >> 16) & 0xffu;
-    const uint32_t low_words = (m * b + 31u) >> 5;
-    const uint32_t high0 = low_words + ((ex + 3u) >> 2);  // first word of the high parts
-    const uint32_t body_words = block_body_bytes(m, b, ex, b + hb) / 4u;
-    uint32_t* pb = w.pbuf;
-    for (uint32_t i = lane; i < body_words; i += 32) pb[i] = 0u;
-    __syncwarp();
-    // value-centric packing into shared memory: low b bits of every value at
-    // bit i*b; exceptions: position byte and high part (hb bits) by rank
-    const uint32_t bmask = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
-    const uint32_t* zb = zbuf + base;
-    uint32_t xi = 0;
-#pragma unroll
-    for (int q = 0; q < 4; q++) {
-      const uint32_t i = lane + 32u * q;
-      const bool valid = i < m;
-      const uint32_t vz = valid ? zb[i] : 0u;
-      if (valid && b) {
-        const uint32_t bit = i * b, wi = bit >> 5, sh = bit & 31u, lo = vz & bmask;
-        atomicOr(pb + wi, lo << sh);
-        if (sh + b > 32u) atomicOr(pb + wi + 1u, lo >> (32u - sh));
-      }
-      if (ex) {
-        const bool isx = valid && bit_width(vz) > b;
-        const uint32_t bal = __ballot_sync(0xffffffffu, isx);
-        if (isx) {
-          const uint32_t slot = xi + __popc(bal & below);
-          atomicOr(pb + low_words + (slot >> 2), i << (8u * (slot & 3u)));
-          const uint32_t hv = vz >> b, hbit = slot * hb, hw = high0 + (hbit >> 5), hs = hbit & 31u;
-          atomicOr(pb + hw, hv << hs);
-          if (hs + hb > 32u) atomicOr(pb + hw + 1u, hv >> (32u - hs));
-        }
-        xi += __popc(bal);
-      }
-    }
-    __syncwarp();
-    uint32_t* bd = dst + head_words + md.y / 4u;
-    for (uint32_t i = lane; i < body_words; i += 32) bd[i] = pb[i];
-    __syncwarp();
-  }
+  uint32_t* bd = dst + head_words;
+  for (uint32_t i = lane; i < body / 4u; i += 32u) bd[i] = w.zb[i];
   __syncwarp();
 }
 
 template <int WPC>
-__global__ void __launch_bounds__(WPC * 32) k_encode(EncParams p) {
+__global__ void __launch_bounds__(WPC * 32, 24 / WPC) k_encode(EncParams p) {
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t lane = lane_id();
   const EncWarpLayout lay = enc_warp_layout(p.max_W);
   uint8_t* wb = reinterpret_cast<uint8_t*>(smem) + warp_id() * lay.bytes;
   EncWarp w;
-  w.zbuf = reinterpret_cast<uint32_t*>(wb + lay.z);
-  w.coded = reinterpret_cast<uint32_t*>(wb + lay.coded);
-  w.coded_b = wb + lay.coded;
+  w.zb = reinterpret_cast<uint32_t*>(wb + lay.zb);
+  w.mb = wb + lay.mb;
   w.meta = reinterpret_cast<uint2*>(wb + lay.meta);
-  w.hist = reinterpret_cast<uint32_t*>(wb + lay.hist);
-  w.pbuf = reinterpret_cast<uint32_t*>(wb + lay.pbuf);
   while (true) {
     uint32_t k = 0;
     if (lane == 0) k = atomicAdd(p.ticket, 1u);
@@ -527,13 +670,11 @@ __global__ void __launch_bounds__(WPC * 32) k_encode(EncParams p) {
 }
 
 // ----------------------------------------------------------------------------
-// k_sec_sizes: one CTA per section (scan t, attribute a): its bytes (row
-// table + row chunks) and nonzero count.
-// k_place: one CTA per section: the section's offset in the stream (prefix
-// over the earlier sections), its row table (end offsets + carries), the copy
-// of each row chunk from its slot, and, for attribute 0, the frame header and
-// frame offset; section 0 also writes the stream header. Every write is
-// checked against the output capacity.
+// k_finalize: one CTA per section (scan t, attribute a): the row table (end
+// offsets within the section's chunk data + carries), the section's entry in
+// the frame header and, for attribute 0, the frame's size, scan index and
+// offset; section 0 of a segment with a stream header also writes it. Every
+// write is checked against the output capacity.
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ void put_u32_guarded(uint8_t* out, unsigned long long cap, unsigned long long at,
                                                 uint32_t v, uint32_t* err) {
@@ -541,39 +682,8 @@ __device__ __forceinline__ void put_u32_guarded(uint8_t* out, unsigned long long
   else atomicOr(err, kErrCapacity);
 }
 
-__device__ __forceinline__ unsigned long long cta_sum_u64(unsigned long long v, unsigned long long* s_red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if (lane_id() == 0) s_red[warp_id()] = v;
-  __syncthreads();
-  unsigned long long tot = 0;
-  for (uint32_t w2 = 0; w2 < blockDim.x / 32u; w2++) tot += s_red[w2];
-  __syncthreads();
-  return tot;
-}
-
-__global__ void __launch_bounds__(kThreads) k_sec_sizes(EncParams p) {
+__global__ void __launch_bounds__(kThreads) k_finalize(EncParams p) {
   __shared__ unsigned long long s_red[kWarps];
-  const uint32_t gs = blockIdx.x;
-  const EncSeg& sg = p.seg[find_seg(p.seg_sec_base, p.n_seg, gs)];
-  const uint32_t H = sg.H;
-  const uint32_t item0 = sg.item_base + (gs - sg.sec_base) * H;
-  unsigned long long bytes = 0, nnz = 0;
-  for (uint32_t r = threadIdx.x; r < H; r += kThreads) {
-    bytes += p.row_bytes[item0 + r];
-    nnz += p.row_nnz[item0 + r];
-  }
-  bytes = cta_sum_u64(bytes, s_red);
-  nnz = cta_sum_u64(nnz, s_red);
-  if (threadIdx.x == 0) {
-    p.sec_bytes[gs] = 8ull * H + bytes;
-    p.sec_nnz[gs] = (uint32_t)nnz;
-  }
-}
-
-__global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
-  extern __shared__ __align__(16) uint32_t smem[];  // [H] row chunk starts
-  __shared__ unsigned long long s_red[kWarps];
-  __shared__ uint32_t s_tmp[kWarps + 1];
   const uint32_t gs = blockIdx.x;
   const EncSeg& sg = p.seg[find_seg(p.seg_sec_base, p.n_seg, gs)];
   const uint32_t H = sg.H, A = sg.A;
@@ -581,52 +691,36 @@ __global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
   const uint32_t item0 = sg.item_base + ta * H;
   uint8_t* out = sg.out;
   const unsigned long long cap = sg.cap;
-  // bytes of the segment's earlier sections: of earlier frames (frame_before)
-  // and of this frame's earlier attributes
-  unsigned long long frame_before = 0, attr_before = 0;
-  for (uint32_t i = threadIdx.x; i < ta; i += kThreads) {
-    if (i < t * A) frame_before += p.sec_bytes[sg.sec_base + i];
-    else attr_before += p.sec_bytes[sg.sec_base + i];
-  }
-  frame_before = cta_sum_u64(frame_before, s_red);
-  attr_before = cta_sum_u64(attr_before, s_red);
-  const unsigned long long frame_at = sg.shdr + (unsigned long long)t * sg.fhdr + frame_before;
-  const unsigned long long sec_at = frame_at + sg.fhdr + attr_before;
-  // row table: end offsets (prefix of chunk sizes) and carries
-  for (uint32_t r = threadIdx.x; r < H; r += kThreads) smem[r] = p.row_bytes[item0 + r];
-  __syncthreads();
-  const uint32_t data = block_excl_scan(smem, H, s_tmp);  // smem = row starts
+  const unsigned long long off0 = p.row_off[item0];
+  const unsigned long long sec_at = sg.shdr + (unsigned long long)(t + 1) * sg.fhdr + 8ull * H * ta + off0;
+  unsigned long long nnz = 0;
   for (uint32_t r = threadIdx.x; r < H; r += kThreads) {
-    const uint32_t end = (r + 1 < H) ? smem[r + 1] : data;
+    const uint32_t end = (uint32_t)(p.row_off[item0 + r] + p.row_bytes[item0 + r] - off0);
     put_u32_guarded(out, cap, sec_at + 8ull * r, end, sg.err);
     put_u32_guarded(out, cap, sec_at + 8ull * r + 4, p.row_carry[item0 + r], sg.err);
+    nnz += p.row_nnz[item0 + r];
   }
-  // row chunks: warp per row, slot -> stream (4-byte aligned words)
-  const unsigned long long data_at = sec_at + 8ull * H;
-  for (uint32_t r = warp_id(); r < H; r += kWarps) {
-    const uint32_t words = p.row_bytes[item0 + r] / 4u;
-    const unsigned long long at = data_at + smem[r];
-    if (at + 4ull * words > cap) {
-      if (lane_id() == 0) atomicOr(sg.err, kErrCapacity);
-      continue;
-    }
-    const uint32_t* src =
-        reinterpret_cast<const uint32_t*>(p.slots + sg.slot_base + (size_t)(ta * H + r) * sg.slot_bytes);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(out + at);
-    for (uint32_t i = lane_id(); i < words; i += 32u) dst[i] = src[i];
-  }
-  if (a == 0 && threadIdx.x == 0) {
-    const uint32_t f0 = sg.sec_base + t * A;
-    unsigned long long fbytes = sg.fhdr;
-    for (uint32_t aa = 0; aa < A; aa++) fbytes += p.sec_bytes[f0 + aa];
+  for (int o = 16; o > 0; o >>= 1) nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
+  if (lane_id() == 0) s_red[warp_id()] = nnz;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  nnz = 0;
+  for (uint32_t w2 = 0; w2 < kWarps; w2++) nnz += s_red[w2];
+  const uint32_t last = item0 + H - 1;
+  const unsigned long long sec_bytes = 8ull * H + (p.row_off[last] + p.row_bytes[last] - off0);
+  const unsigned long long frame_at = sg.shdr + (unsigned long long)t * sg.fhdr + 8ull * H * (t * A) +
+                                      p.row_off[sg.item_base + t * A * H];
+  const unsigned long long h = frame_at + 8ull + 12ull * a;
+  put_u32_guarded(out, cap, h, p.modes[gs], sg.err);
+  put_u32_guarded(out, cap, h + 4, (uint32_t)sec_bytes, sg.err);
+  put_u32_guarded(out, cap, h + 8, (uint32_t)nnz, sg.err);
+  if (a == 0) {
+    // frame bytes: header + row tables + all chunks of the frame's rows
+    const uint32_t fl = sg.item_base + (t * A + A) * H - 1;  // the frame's last row
+    const unsigned long long chunks = p.row_off[fl] + p.row_bytes[fl] - p.row_off[sg.item_base + t * A * H];
+    const unsigned long long fbytes = sg.fhdr + 8ull * H * A + chunks;
     put_u32_guarded(out, cap, frame_at, (uint32_t)fbytes, sg.err);
     put_u32_guarded(out, cap, frame_at + 4, sg.frame0 + t, sg.err);
-    for (uint32_t aa = 0; aa < A; aa++) {
-      const unsigned long long h = frame_at + 8ull + 12ull * aa;
-      put_u32_guarded(out, cap, h, p.modes[f0 + aa], sg.err);
-      put_u32_guarded(out, cap, h + 4, (uint32_t)p.sec_bytes[f0 + aa], sg.err);
-      put_u32_guarded(out, cap, h + 8, p.sec_nnz[f0 + aa], sg.err);
-    }
     sg.frame_off[t] = frame_at;
     if (t + 1 == sg.T) sg.frame_off[sg.T] = frame_at + fbytes;
     if (t == 0 && sg.shdr) {
@@ -656,8 +750,7 @@ static cudaError_t rows_occupancy(size_t smem, int* per_sm) {
 
 int encode_rows_launch(const EncParams& p, RowsLaunch* out) {
   const EncWarpLayout L = enc_warp_layout(p.max_W);
-  if ((L.coded | L.meta | L.hist | L.pbuf | L.bytes) & 15u)
-    return (int)cudaErrorInvalidValue;  // every per-warp region starts 16-byte aligned
+  if ((L.mb | L.meta | L.bytes) & 15u) return (int)cudaErrorInvalidValue;  // 16-byte aligned regions
   uint32_t wpc = p.wpc;
   if ((wpc != 1 && wpc != 2 && wpc != 4) || wpc * L.bytes > kRowsSmemMax) wpc = 0;
   if (!wpc) wpc = 4 * L.bytes <= kRowsSmemAuto ? 4u : (2 * L.bytes <= kRowsSmemAuto ? 2u : 1u);
@@ -682,28 +775,28 @@ int encode_rows_launch(const EncParams& p, RowsLaunch* out) {
   return 0;
 }
 
+size_t trial_smem_bytes_host(uint32_t W) { return 2ull * 4u * ceil_div_u32(W, kStepVal) * kStepVal; }
+
 int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const size_t s_trial = 8ull * p.max_W, s_place = 4ull * kMaxH;
+  const size_t s_trial = trial_smem_bytes_host(p.max_W);
   RowsLaunch rl{};
   int rc = encode_rows_launch(p, &rl);
   if (rc != 0) return rc;
   cudaError_t e = cudaFuncSetAttribute(k_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_trial);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_place);
   if (e != cudaSuccess) return (int)e;
   auto mark = [&](int i) {
     if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[i]), st);
   };
   mark(0);
-  k_trial<<<p.n_sec, kThreads, s_trial, st>>>(p);
+  if (p.trial_rows) k_trial<<<p.n_sec * p.trial_rows, 32, s_trial, st>>>(p);
   mark(1);
   const size_t smem = (size_t)rl.wpc * enc_warp_layout(p.max_W).bytes;
   if (rl.wpc == 4) k_encode<4><<<rl.grid, 4 * 32, smem, st>>>(p);
   else if (rl.wpc == 2) k_encode<2><<<rl.grid, 2 * 32, smem, st>>>(p);
   else k_encode<1><<<rl.grid, 32, smem, st>>>(p);
   mark(2);
-  k_sec_sizes<<<p.n_sec, kThreads, 0, st>>>(p);
-  k_place<<<p.n_sec, kThreads, s_place, st>>>(p);
+  k_finalize<<<p.n_sec, kThreads, 0, st>>>(p);
   mark(3);
   return (int)cudaGetLastError();
 }

@@ -24,8 +24,6 @@ struct EncSeg {
   int32_t force_mode;
   uint32_t item_base;            // first global row item of the segment
   uint32_t sec_base;             // first global section of the segment
-  uint32_t slot_bytes;           // per-row slot size (row_bound(W) rounded to 16)
-  unsigned long long slot_base;  // byte offset of the segment's first slot
   const AttrDev* attrs;          // [A]
   const uint8_t* const* cur;     // [T*A] current planes
   const uint8_t* const* prev;    // [T*A] previous planes: t = 0 -> stored scan (or null), else raw t-1
@@ -41,17 +39,18 @@ struct EncParams {
   uint32_t n_items;              // row items of all segments
   uint32_t n_sec;                // sections of all segments
   uint32_t max_W;                // widest row (per-warp shared memory)
+  uint32_t trial_rows;           // most distinct test rows of a segment (0: no trial)
   const EncSeg* seg;             // [n_seg]
   const uint32_t* seg_item_base; // [n_seg] (search key for row items)
   const uint32_t* seg_sec_base;  // [n_seg] (search key for sections)
+  uint32_t* cost;                // [2 n_sec] trial bytes of I and P (zeroed)
   uint32_t* modes;               // [n_sec]
-  uint32_t* row_bytes;           // [n_items]
+  uint32_t* row_bytes;           // [n_items] chunk bytes
   uint32_t* row_nnz;             // [n_items]
   uint32_t* row_carry;           // [n_items]
-  unsigned long long* st_carry;  // [n_items] look-back status (delta carry, fallback)
-  uint8_t* slots;                // packed row chunks, slot_base + local item * slot_bytes
-  unsigned long long* sec_bytes; // [n_sec] section bytes (row table + chunks)
-  uint32_t* sec_nnz;             // [n_sec]
+  unsigned long long* row_off;   // [n_items] exclusive prefix of chunk bytes in the segment
+  unsigned long long* st_carry;  // [n_items] look-back status, delta carry (zeroed)
+  unsigned long long* st_bytes;  // [n_items] look-back status, chunk bytes (zeroed)
   uint32_t* ticket;
   uint32_t wpc;                  // rows kernel: warps per CTA (1, 2, 4; 0 = by shared memory)
   uint32_t ctas_per_sm;          // rows kernel: resident CTAs per SM (0 = occupancy limit)
@@ -94,6 +93,7 @@ struct RowsLaunch {
 };
 
 size_t enc_smem_bytes_host(uint32_t W);
+size_t trial_smem_bytes_host(uint32_t W);
 size_t dec_smem_bytes_host(uint32_t W);
 // Return a cudaError_t as int; *out receives the configuration.
 int encode_rows_launch(const EncParams& p, RowsLaunch* out);

@@ -12,14 +12,13 @@
 
 namespace jiffy {
 
-constexpr int kThreads = 256;          // threads per CTA of every row kernel
+constexpr int kThreads = 256;          // threads per CTA of the per-section kernels
 constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kMaxW = 16384;      // columns
 constexpr uint32_t kMaxH = 4096;       // rows
 constexpr uint32_t kMaxAttr = 64;
 constexpr uint32_t kMaxTestLines = 64;
 constexpr uint32_t kBlockN = 128;      // values per packing block (Sec. II frames of 128)
-constexpr uint32_t kSegWords = 8;      // mask words per warp per pass over a row
 
 // bits of the device error word
 enum : uint32_t { kErrCorrupt = 1u, kErrCapacity = 2u, kErrTimeout = 4u };
@@ -28,13 +27,40 @@ enum : uint32_t { kErrCorrupt = 1u, kErrCapacity = 2u, kErrTimeout = 4u };
 // kErrTimeout and the kernel returns instead of hanging.
 constexpr unsigned long long kSpinLimitNs = 2000000000ull;
 
+// Quantizer of one attribute (Sec. III-B): q = min(floor((v + half) / P), qmax).
+//   qkind 0: P = 1, q = v.
+//   qkind 1: 2 <= P < 2^30: q0 = umulhi(v, m32) with m32 = floor(2^32 / P) is
+//            floor(v / P) or one less, so r = v - q0 P lies in [0, 2P) and
+//            q = q0 + [r + half >= P] + [r + half >= 2P] (no overflow: 3P < 2^32).
+//   qkind 2: larger P: 64-bit reciprocal `magic` = ceil(2^64 / P).
 struct AttrDev {
   uint32_t s;                 // bytes per sample: 1, 2 or 4
   uint32_t P;                 // precision
   uint32_t qmax;              // floor(max_sample / P)
-  uint32_t pad;
+  uint32_t qkind;
   unsigned long long magic;   // ceil(2^64 / P), for 2 <= P <= 2^31
+  uint32_t m32;               // floor(2^32 / P) for qkind 1
+  uint32_t half;              // floor(P / 2)
 };
+
+inline AttrDev make_attr(uint32_t s, uint32_t P) {
+  AttrDev d{};
+  d.s = s;
+  d.P = P;
+  const uint32_t maxv = s == 4 ? 0xffffffffu : ((1u << (8 * s)) - 1u);
+  d.qmax = maxv / P;
+  d.half = P >> 1;
+  d.magic = (P >= 2 && P <= 0x80000000u) ? (~0ull) / P + 1ull : 0ull;
+  if (P == 1) {
+    d.qkind = 0;
+  } else if (P < (1u << 30)) {
+    d.qkind = 1;
+    d.m32 = (uint32_t)((1ull << 32) / P);
+  } else {
+    d.qkind = 2;
+  }
+  return d;
+}
 
 JIFFY_HD inline uint32_t ceil_div_u32(uint32_t a, uint32_t b) { return (a + b - 1) / b; }
 
