@@ -235,19 +235,13 @@ __device__ __forceinline__ uint32_t quantize(uint32_t v, const AttrDev& a) {
 }
 
 // Compile-time quantizer kind (AttrDev::qkind): 0 identity, 1 32-bit
-// reciprocal with a two-step correction (P < 2^30), 2 the 64-bit form above.
-// Kind 1: q0 = floor(v m32 / 2^32) with m32 = floor(2^32/P) is floor(v/P) or
-// one less, so r = v - q0 P is in [0, 2P) and floor((v + h)/P) = q0 +
-// floor((r + h)/P) with r + h < 3P < 2^32.
+// multiply-high and shift on the clamped input, 2 the 64-bit form above.
 template <int QU>
 __device__ __forceinline__ uint32_t quant(uint32_t v, const AttrDev& a) {
   if constexpr (QU == 0) {
     return v;
   } else if constexpr (QU == 1) {
-    const uint32_t q0 = __umulhi(v, a.m32);
-    const uint32_t t = v - q0 * a.P + a.half;
-    const uint32_t q = q0 + (t >= a.P ? 1u : 0u) + (t >= 2u * a.P ? 1u : 0u);
-    return q < a.qmax ? q : a.qmax;
+    return __umulhi(min(v, a.lim) + a.half, a.m32) >> a.sh;
   } else {
     return quantize(v, a);
   }

@@ -72,24 +72,39 @@ __device__ __forceinline__ uint32_t section_mode(const EncParams& p, const EncSe
   return p.cost[2 * sec + 1] < p.cost[2 * sec] ? 1u : 0u;
 }
 
+// Loads / stores 8 samples with the width fixed at compile time (S = 1, 2,
+// 4) or read at run time (S = 0).
+template <uint32_t S>
+__device__ __forceinline__ void ld8(const uint8_t* row, uint32_t s, uint32_t x0, uint32_t nv, bool vec,
+                                    uint32_t (&v)[8]) {
+  if constexpr (S == 0) load8<false>(row, s, x0, nv, vec, v);
+  else load8s<S, false>(row, x0, nv, vec, v);
+}
+template <uint32_t S>
+__device__ __forceinline__ void st8(uint8_t* row, uint32_t s, uint32_t x0, uint32_t nv, bool vec,
+                                    const uint32_t (&v)[8]) {
+  if constexpr (S == 0) store8(row, s, x0, nv, vec, v);
+  else store8s<S>(row, x0, nv, vec, v);
+}
+
 // ---------------------------------------------------------------------------
 // Pass A (one row): returns the number n of nonzero samples; their residuals
 // go to zb in row-major order (swizzled), the coded mask bytes (M, or M xor
 // M_prev for P) to mb, and, for the call's last scan, q * P to st_row.
 // ---------------------------------------------------------------------------
-template <bool PM, int QU>
-__device__ __forceinline__ uint32_t pass_a(const uint8_t* cur, const uint8_t* prv, uint8_t* st_row, const AttrDev at,
-                                        uint32_t W, uint32_t* zb, uint8_t* mb) {
-  const uint32_t lane = lane_id(), S = at.s;
-  const bool vc = vec_ok(cur, S), vp = PM && vec_ok(prv, S), vs = st_row && vec_ok(st_row, S);
+template <bool PM, int QU, uint32_t S>
+__device__ __forceinline__ uint32_t pass_a(const uint8_t* cur, const uint8_t* prv, uint8_t* st_row, const AttrDev& at,
+                                           uint32_t W, uint32_t* zb, uint8_t* mb) {
+  const uint32_t lane = lane_id(), s = at.s;
+  const bool vc = vec_ok(cur, s), vp = PM && vec_ok(prv, s), vs = st_row && vec_ok(st_row, s);
   const uint32_t Wm = (W + 31u) & ~31u;
   uint32_t n = 0;
   for (uint32_t base = 0; base < W; base += kStepPx) {
     const uint32_t x0 = base + 8u * lane;
     const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
     uint32_t v[8], pv[8];
-    load8<false>(cur, S, x0, nv, vc, v);
-    if (PM) load8<false>(prv, S, x0, nv, vp, pv);
+    ld8<S>(cur, s, x0, nv, vc, v);
+    if (PM) ld8<S>(prv, s, x0, nv, vp, pv);
     uint32_t e[8], zm = 0, pm = 0;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
@@ -111,7 +126,7 @@ __device__ __forceinline__ uint32_t pass_a(const uint8_t* cur, const uint8_t* pr
       uint32_t sv[8];
 #pragma unroll
       for (int i = 0; i < 8; i++) sv[i] = v[i] * at.P;
-      store8(st_row, S, x0, nv, vs, sv);
+      st8<S>(st_row, s, x0, nv, vs, sv);
     }
     uint32_t tot;
     uint32_t kk = n + warp_excl_scan(__popc(nz), tot);
@@ -200,6 +215,16 @@ __device__ __noinline__ bool row_last(const uint8_t* cur, const uint8_t* prv, co
   return false;
 }
 
+// Repeats the last residual from n up to the end of pass B1's last step, so
+// that those slots delta-code to 0 (and count as zero-width values).
+__device__ __forceinline__ void fill_tail(uint32_t* zb, uint32_t n) {
+  if (n == 0) return;
+  const uint32_t last = zb[swz(n - 1)];
+  const uint32_t end = (n + kStepVal - 1) / kStepVal * kStepVal;
+  for (uint32_t k = n + lane_id(); k < end; k += 32u) zb[swz(k)] = last;
+  __syncwarp();
+}
+
 // ---------------------------------------------------------------------------
 // Pass B1: delta + ZigZag in place and the width of every block (Sec. II:
 // b in [0, wmax] minimising the block's body bytes, ties to the smallest b).
@@ -230,13 +255,10 @@ __device__ __forceinline__ uint32_t pass_b1(uint32_t* zb, uint32_t n, uint32_t c
     uint32_t pred = __shfl_up_sync(0xffffffffu, z[31], 1);
     if (lane == 0) pred = pred_step;
     pred_step = __shfl_sync(0xffffffffu, z[31], 31);
-    const uint32_t kb = s0 + 32u * lane;
-    // delta (Sec. III-C) and ZigZag (Eq. 1); values past n become 0
+    // delta (Sec. III-C) and ZigZag (Eq. 1); values past n repeat the last
+    // residual (fill_tail), so their ZigZag values are 0
 #pragma unroll
-    for (int i = 31; i >= 0; i--) {
-      const uint32_t d = z[i] - (i ? z[i - 1] : pred);
-      z[i] = kb + (uint32_t)i < n ? zigzag(d) : 0u;
-    }
+    for (int i = 31; i >= 0; i--) z[i] = zigzag(z[i] - (i ? z[i - 1] : pred));
     if (WRITE) {
 #pragma unroll
       for (uint32_t c = 0; c < 8; c++) sp[c ^ (seg & 7u)] = make_uint4(z[4 * c], z[4 * c + 1], z[4 * c + 2], z[4 * c + 3]);
@@ -332,9 +354,12 @@ __device__ __forceinline__ uint32_t pass_b1(uint32_t* zb, uint32_t n, uint32_t c
 // Pass B2: packs every block's body into zb, in place and unswizzled (block
 // g's body lands in words [off_g, off_g + size_g) with off_g + size_g <=
 // 128 (g + 1), so it never reaches a value still to be read). Lane l holds
-// values 4l .. 4l+3 of the block: their low b bits are joined in registers
-// (4b bits) and OR-ed into the body at bit 4lb (Sec. II: low parts of all
-// values, then the exceptions' positions and high parts).
+// values 4l .. 4l+3 of the block, i.e. bits [4lb, 4lb + 4b) of the low-bit
+// stream (Sec. II: low parts of all values, then the exceptions' positions
+// and high parts). Each stream word is written once, by the lane holding its
+// first bit: the lane joins its values with funnel shifts and completes the
+// word with the following lanes' bits (one shuffle for b > 8; for b <= 8,
+// where a word spans several lanes, log-step shuffles double the run).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void pass_b2(uint32_t* zb, uint32_t n, uint32_t nb, const uint2* meta) {
   const uint32_t lane = lane_id(), below = (1u << lane) - 1u;
@@ -342,77 +367,85 @@ __device__ __forceinline__ void pass_b2(uint32_t* zb, uint32_t n, uint32_t nb, c
     const uint2 md = meta[g];  // .x header, .y body byte offset
     const uint32_t b = md.x & 0xffu, e = (md.x >> 8) & 0xffu, hb = (md.x >> 16) & 0xffu;
     const uint32_t m = min(128u, n - 128u * g);
-    const uint32_t off = md.y >> 2;
+    uint32_t* body = zb + (md.y >> 2);
     const uint32_t low_words = (m * b + 31u) >> 5;
-    const uint32_t size_words = block_body_bytes(m, b, e, b + hb) >> 2;
     const uint32_t sgi = 4u * g + (lane >> 3);
     const uint4 zz = reinterpret_cast<const uint4*>(zb + 32u * sgi)[(lane & 7u) ^ (sgi & 7u)];
-    const uint32_t z[4] = {zz.x, zz.y, zz.z, zz.w};
+    const uint32_t z0 = zz.x, z1 = zz.y, z2 = zz.z, z3 = zz.w;  // 0 past m
     __syncwarp();
-    for (uint32_t i = lane; i < size_words; i += 32u) zb[off + i] = 0u;
-    __syncwarp();
-    if (b) {
-      const uint32_t bm = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
-      const uint32_t l0 = z[0] & bm, l1 = z[1] & bm, l2 = z[2] & bm, l3 = z[3] & bm;
-      const uint32_t bit = 4u * lane * b, sh = bit & 31u;
-      uint32_t* dst = zb + off + (bit >> 5);
-      if (b <= 8u) {
-        const uint32_t x = l0 | (l1 << b) | (l2 << (2u * b)) | (l3 << (3u * b));
-        const uint32_t y0 = x << sh, y1 = __funnelshift_l(x, 0u, sh);
-        if (y0) atomicOr(dst, y0);
-        if (y1) atomicOr(dst + 1, y1);
-      } else if (b <= 16u) {
-        const unsigned long long x = (unsigned long long)l0 | ((unsigned long long)l1 << b) |
-                                     ((unsigned long long)l2 << (2u * b)) | ((unsigned long long)l3 << (3u * b));
-        const uint32_t x0 = (uint32_t)x, x1 = (uint32_t)(x >> 32);
-        const uint32_t y0 = x0 << sh, y1 = __funnelshift_l(x0, x1, sh), y2 = __funnelshift_l(x1, 0u, sh);
-        if (y0) atomicOr(dst, y0);
-        if (y1) atomicOr(dst + 1, y1);
-        if (y2) atomicOr(dst + 2, y2);
-      } else {
-        // 4b in (64, 128]: lo = l0 | l1 << b (2b bits), hi = l2 | l3 << b,
-        // x = lo | hi << 2b with 2b - 32 = s in (0, 32]
-        const unsigned long long lo = (unsigned long long)l0 | ((unsigned long long)l1 << b);
-        const unsigned long long hi = (unsigned long long)l2 | ((unsigned long long)l3 << b);
-        const uint32_t s = 2u * b - 32u;
-        const uint32_t h0 = (uint32_t)hi, h1 = (uint32_t)(hi >> 32);
-        const uint32_t x0 = (uint32_t)lo;
-        const uint32_t x1 = (uint32_t)(lo >> 32) | __funnelshift_lc(0u, h0, s);
-        const uint32_t x2 = __funnelshift_lc(h0, h1, s);
-        const uint32_t x3 = __funnelshift_lc(h1, 0u, s);
-        const uint32_t y0 = x0 << sh, y1 = __funnelshift_l(x0, x1, sh), y2 = __funnelshift_l(x1, x2, sh),
-                       y3 = __funnelshift_l(x2, x3, sh), y4 = __funnelshift_l(x3, 0u, sh);
-        if (y0) atomicOr(dst, y0);
-        if (y1) atomicOr(dst + 1, y1);
-        if (y2) atomicOr(dst + 2, y2);
-        if (y3) atomicOr(dst + 3, y3);
-        if (y4) atomicOr(dst + 4, y4);
+    const uint32_t S = 4u * lane * b;           // the lane's first bit
+    const uint32_t o = (32u - (S & 31u)) & 31u;  // its first word start, relative to S
+    const uint32_t w = (S + o) >> 5;            // that word
+    if (b == 0) {
+    } else if (b <= 8u) {
+      const uint32_t bm = (1u << b) - 1u;
+      unsigned long long y = (z0 & bm) | ((z1 & bm) << b) | ((z2 & bm) << (2u * b)) | ((z3 & bm) << (3u * b));
+      for (uint32_t d = 1, len = 4u * b; len < 64u; d <<= 1, len <<= 1) {
+        unsigned long long t = __shfl_down_sync(0xffffffffu, y, d);
+        if (lane + d > 31u) t = 0ull;
+        y |= t << len;
       }
+      if (o < 4u * b && w < low_words) body[w] = (uint32_t)(y >> o);
+    } else if (b <= 16u) {
+      const uint32_t bm = (1u << b) - 1u;
+      const unsigned long long x = (unsigned long long)(z0 & bm) | ((unsigned long long)(z1 & bm) << b) |
+                                   ((unsigned long long)(z2 & bm) << (2u * b)) |
+                                   ((unsigned long long)(z3 & bm) << (3u * b));
+      uint32_t N = __shfl_down_sync(0xffffffffu, (uint32_t)x, 1);
+      if (lane == 31u) N = 0u;
+      const uint32_t sN = 4u * b - 32u;  // the next lane's bits start at word 1, bit sN (4..32)
+      const uint32_t Z0 = (uint32_t)x, Z1 = (uint32_t)(x >> 32) | __funnelshift_lc(0u, N, sN),
+                     Z2 = __funnelshift_lc(N, 0u, sN);
+      if (w < low_words) body[w] = __funnelshift_r(Z0, Z1, o);
+      if (o + 32u < 4u * b && w + 1u < low_words) body[w + 1] = __funnelshift_r(Z1, Z2, o);
+    } else {
+      const uint32_t bm = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
+      const unsigned long long lo = (unsigned long long)(z0 & bm) | ((unsigned long long)(z1 & bm) << b);
+      const unsigned long long hi = (unsigned long long)(z2 & bm) | ((unsigned long long)(z3 & bm) << b);
+      const uint32_t s2 = 2u * b - 32u;  // hi starts at word 1, bit s2 (2..32)
+      const uint32_t h0 = (uint32_t)hi, h1 = (uint32_t)(hi >> 32);
+      uint32_t X0 = (uint32_t)lo, X1 = (uint32_t)(lo >> 32) | __funnelshift_lc(0u, h0, s2),
+               X2 = __funnelshift_lc(h0, h1, s2), X3 = __funnelshift_lc(h1, 0u, s2), X4 = 0u;
+      uint32_t N = __shfl_down_sync(0xffffffffu, X0, 1);
+      if (lane == 31u) N = 0u;
+      if (4u * b <= 96u) {  // the next lane's bits start at word 2, bit 4b - 64 (4..32)
+        const uint32_t sN = 4u * b - 64u;
+        X2 |= __funnelshift_lc(0u, N, sN);
+        X3 |= __funnelshift_lc(N, 0u, sN);
+      } else {  // word 3, bit 4b - 96 (4..32)
+        const uint32_t sN = 4u * b - 96u;
+        X3 |= __funnelshift_lc(0u, N, sN);
+        X4 = __funnelshift_lc(N, 0u, sN);
+      }
+      if (w < low_words) body[w] = __funnelshift_r(X0, X1, o);
+      if (o + 32u < 4u * b && w + 1u < low_words) body[w + 1] = __funnelshift_r(X1, X2, o);
+      if (o + 64u < 4u * b && w + 2u < low_words) body[w + 2] = __funnelshift_r(X2, X3, o);
+      if (o + 96u < 4u * b && w + 3u < low_words) body[w + 3] = __funnelshift_r(X3, X4, o);
     }
     if (e) {  // exceptions: position bytes (ascending), then high parts of hb bits
-      bool isx[4];
+      const uint32_t pw = (e + 3u) >> 2, hw = (e * hb + 31u) >> 5;
+      for (uint32_t i = lane; i < pw + hw; i += 32u) body[low_words + i] = 0u;
+      __syncwarp();
+      uint32_t xm = ((z0 >> b) != 0u ? 1u : 0u) | ((z1 >> b) != 0u ? 2u : 0u) | ((z2 >> b) != 0u ? 4u : 0u) |
+                    ((z3 >> b) != 0u ? 8u : 0u);  // e > 0 implies b < 32
       uint32_t rank = 0;
 #pragma unroll
-      for (int q = 0; q < 4; q++) {
-        isx[q] = b < 32u && (z[q] >> b) != 0u;
-        rank += __popc(__ballot_sync(0xffffffffu, isx[q]) & below);
-      }
-      uint8_t* pos = reinterpret_cast<uint8_t*>(zb + off + low_words);
-      const uint32_t hw0 = off + low_words + ((e + 3u) >> 2);
-#pragma unroll
-      for (int q = 0; q < 4; q++) {
-        if (isx[q]) {
-          pos[rank] = (uint8_t)(4u * lane + q);
-          const uint32_t hv = z[q] >> b, hbit = rank * hb, hs = hbit & 31u;
-          uint32_t* hp = zb + hw0 + (hbit >> 5);
-          atomicOr(hp, hv << hs);
-          if (hs + hb > 32u) atomicOr(hp + 1, hv >> (32u - hs));
-          rank++;
-        }
+      for (uint32_t q = 0; q < 4; q++) rank += __popc(__ballot_sync(0xffffffffu, (xm >> q) & 1u) & below);
+      uint8_t* pos = reinterpret_cast<uint8_t*>(body + low_words);
+      uint32_t* hp = body + low_words + pw;
+      while (xm) {
+        const uint32_t q = __ffs(xm) - 1u;
+        xm &= xm - 1u;
+        const uint32_t v = q == 0 ? z0 : (q == 1 ? z1 : (q == 2 ? z2 : z3));
+        pos[rank] = (uint8_t)(4u * lane + q);
+        const uint32_t hv = v >> b, hbit = rank * hb, hs = hbit & 31u;
+        atomicOr(hp + (hbit >> 5), hv << hs);
+        if (hs + hb > 32u) atomicOr(hp + (hbit >> 5) + 1u, hv >> (32u - hs));
+        rank++;
       }
     }
+    __syncwarp();
   }
-  __syncwarp();
 }
 
 }  // namespace
@@ -465,6 +498,8 @@ __global__ void __launch_bounds__(32) k_trial(EncParams p) {
   else if (at.qkind == 1) n = pass_a_trial<1>(c1, p1, at, W, zi, zp);
   else n = pass_a_trial<2>(c1, p1, at, W, zi, zp);
   __syncwarp();
+  fill_tail(zi, n);
+  fill_tail(zp, n);
   const uint32_t cost_i = pass_b1<false>(zi, n, ci, nullptr);
   const uint32_t cost_p = pass_b1<false>(zp, n, cp, nullptr);
   if (lane_id() == 0) {
@@ -503,6 +538,39 @@ struct EncWarp {
   uint2* meta;
 };
 
+// The last nonzero sample among the 8 (nv valid) in v / pv, across the warp:
+// its residual (P: q - q', I: q). Returns false if there is none.
+template <int QU>
+__device__ __forceinline__ bool tail_residual(const uint32_t (&v)[8], const uint32_t (&pv)[8], uint32_t nv, bool pm,
+                                              const AttrDev& at, uint32_t& e_last) {
+  bool has = false;
+  uint32_t last = 0;
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    const uint32_t q = quant<QU>(v[i], at);
+    if ((uint32_t)i < nv && q != 0u) {
+      has = true;
+      last = pm ? q - quant<QU>(pv[i], at) : q;
+    }
+  }
+  const uint32_t hm = __ballot_sync(0xffffffffu, has);
+  if (!hm) return false;
+  e_last = __shfl_sync(0xffffffffu, last, 31u - __clz(hm));
+  return true;
+}
+
+template <bool PM, int QU>
+__device__ __forceinline__ uint32_t pass_a_any(const uint8_t* cur, const uint8_t* prv, uint8_t* st_row,
+                                               const AttrDev& at, uint32_t W, uint32_t* zb, uint8_t* mb) {
+  if constexpr (QU == 2) {
+    return pass_a<PM, QU, 0>(cur, prv, st_row, at, W, zb, mb);
+  } else {
+    if (at.s == 4) return pass_a<PM, QU, 4>(cur, prv, st_row, at, W, zb, mb);
+    if (at.s == 2) return pass_a<PM, QU, 2>(cur, prv, st_row, at, W, zb, mb);
+    return pass_a<PM, QU, 1>(cur, prv, st_row, at, W, zb, mb);
+  }
+}
+
 __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k, const EncWarp& w) {
   const EncSeg& sg = p.seg[find_seg(p.seg_item_base, p.n_seg, k)];
   const uint32_t lane = lane_id();
@@ -519,37 +587,65 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   const uint8_t* prv = mode ? sg.prev[ta] + r * rowb : nullptr;
   uint8_t* st_row = (t + 1 == sg.T) ? sg.state_next[a] + r * rowb : nullptr;
   const int qk = (int)at.qkind;
-
-  // ---- delta carry: the residual preceding this row in the attribute-scan's
-  //      flat vector (Sec. III-C). The previous row's tail usually holds it;
-  //      otherwise a "last valid" look-back over the earlier rows decides.
-  uint32_t carry = 0, unused;
-  bool known = r == 0;  // e[-1] = 0 at the start of the attribute-scan
+  if (lane == 0) {  // fetch the row(s) into L2 ahead of the 256-pixel steps
+    const uintptr_t c0 = reinterpret_cast<uintptr_t>(cur), c1 = c0 + rowb;
+    const uintptr_t a0 = (c0 + 15u) & ~uintptr_t(15), a1 = c1 & ~uintptr_t(15);
+    if (a1 > a0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0)) : "memory");
+    if (prv) {
+      const uintptr_t p0 = reinterpret_cast<uintptr_t>(prv), p1 = p0 + rowb;
+      const uintptr_t b0 = (p0 + 15u) & ~uintptr_t(15), b1 = p1 & ~uintptr_t(15);
+      if (b1 > b0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b0), "r"((uint32_t)(b1 - b0)) : "memory");
+    }
+  }
+  // the previous row's last 256-pixel step, loaded now and read after pass A:
+  // its last nonzero residual is this row's delta carry (Sec. III-C)
+  const uint32_t nsteps = ceil_div_u32(W, kStepPx);
+  const uint32_t tx0 = kStepPx * (nsteps - 1u) + 8u * lane;
+  const uint32_t tnv = tx0 < W ? min(8u, W - tx0) : 0u;
+  uint32_t tv[8], tpv[8];
   if (r > 0) {
-    const uint8_t* pc = cur - rowb;
-    const uint8_t* pp = prv ? prv - rowb : nullptr;
-    if (qk == 0) known = row_last<0>(pc, pp, at, W, 1, &unused, &carry);
-    else if (qk == 1) known = row_last<1>(pc, pp, at, W, 1, &unused, &carry);
-    else known = row_last<2>(pc, pp, at, W, 1, &unused, &carry);
+    load8<false>(cur - rowb, at.s, tx0, tnv, vec_ok(cur - rowb, at.s), tv);
+    if (prv) load8<false>(prv - rowb, at.s, tx0, tnv, vec_ok(prv - rowb, at.s), tpv);
   }
 
   // ---- pass A
   uint32_t n;
   if (mode) {
-    if (qk == 0) n = pass_a<true, 0>(cur, prv, st_row, at, W, w.zb, w.mb);
-    else if (qk == 1) n = pass_a<true, 1>(cur, prv, st_row, at, W, w.zb, w.mb);
-    else n = pass_a<true, 2>(cur, prv, st_row, at, W, w.zb, w.mb);
+    if (qk == 0) n = pass_a_any<true, 0>(cur, prv, st_row, at, W, w.zb, w.mb);
+    else if (qk == 1) n = pass_a_any<true, 1>(cur, prv, st_row, at, W, w.zb, w.mb);
+    else n = pass_a_any<true, 2>(cur, prv, st_row, at, W, w.zb, w.mb);
   } else {
-    if (qk == 0) n = pass_a<false, 0>(cur, nullptr, st_row, at, W, w.zb, w.mb);
-    else if (qk == 1) n = pass_a<false, 1>(cur, nullptr, st_row, at, W, w.zb, w.mb);
-    else n = pass_a<false, 2>(cur, nullptr, st_row, at, W, w.zb, w.mb);
+    if (qk == 0) n = pass_a_any<false, 0>(cur, nullptr, st_row, at, W, w.zb, w.mb);
+    else if (qk == 1) n = pass_a_any<false, 1>(cur, nullptr, st_row, at, W, w.zb, w.mb);
+    else n = pass_a_any<false, 2>(cur, nullptr, st_row, at, W, w.zb, w.mb);
   }
   __syncwarp();
   const uint32_t last_e = n ? w.zb[swz(n - 1)] : 0u;
-  if (lane == 0) {
-    if (known) st_publish(p.st_carry + k, kStInc | (1ull << 32) | (n ? last_e : carry));
-    else st_publish(p.st_carry + k, kStAgg | ((unsigned long long)(n ? 1 : 0) << 32) | last_e);
+  if (lane == 0) {  // this row's last residual, for the rows after it
+    st_publish(p.st_carry + k, kStAgg | ((unsigned long long)(n ? 1 : 0) << 32) | last_e);
   }
+  fill_tail(w.zb, n);
+
+  // ---- delta carry
+  uint32_t carry = 0;
+  bool known = r == 0;  // e[-1] = 0 at the start of the attribute-scan
+  if (r > 0) {
+    if (qk == 0) known = tail_residual<0>(tv, tpv, tnv, prv != nullptr, at, carry);
+    else if (qk == 1) known = tail_residual<1>(tv, tpv, tnv, prv != nullptr, at, carry);
+    else known = tail_residual<2>(tv, tpv, tnv, prv != nullptr, at, carry);
+  }
+  if (!known) {  // the previous rows' "last residual" words decide
+    const bool ok = lookback_last(p.st_carry, k, sec_start, carry);
+    if (!ok) {
+      if (lane == 0) {
+        atomicOr(sg.err, kErrTimeout);
+        st_publish(p.st_carry + k, kStErr);
+        st_publish(p.st_bytes + k, kStErr);
+      }
+      return;
+    }
+  }
+  if (lane == 0) st_publish(p.st_carry + k, kStInc | (1ull << 32) | (n ? last_e : carry));
 
   // ---- mask part size: literal words
   const uint32_t* mbw = reinterpret_cast<const uint32_t*>(w.mb);
@@ -558,18 +654,6 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
     const uint32_t jw = jb + lane;
     const bool lit = jw < nw && mask_class(mbw[jw], valid_bits(W, nw, jw)) == 2u;
     nlit += __popc(__ballot_sync(0xffffffffu, lit));
-  }
-
-  if (!known) {
-    const bool ok = lookback_last(p.st_carry, k, sec_start, carry);
-    if (lane == 0) st_publish(p.st_carry + k, ok ? (kStInc | (1ull << 32) | (n ? last_e : carry)) : kStErr);
-    if (!ok) {
-      if (lane == 0) {
-        atomicOr(sg.err, kErrTimeout);
-        st_publish(p.st_bytes + k, kStErr);
-      }
-      return;
-    }
   }
 
   // ---- pass B1: delta, ZigZag, block widths
@@ -597,13 +681,14 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   __syncwarp();
   const uint32_t head_words = ncls + nlit + nb;
   const uint32_t chunk = 4u * head_words + body;
+  if (lane == 0) st_publish(p.st_bytes + k, (kl == 0 ? kStInc : kStAgg) | chunk);
+
+  // ---- pass B2: block bodies, packed in shared memory
+  pass_b2(w.zb, n, nb, w.meta);
 
   // ---- placement: decoupled look-back over the segment's rows
   unsigned long long excl = 0;
-  if (kl == 0) {
-    if (lane == 0) st_publish(p.st_bytes + k, kStInc | chunk);
-  } else {
-    if (lane == 0) st_publish(p.st_bytes + k, kStAgg | chunk);
+  if (kl > 0) {
     const bool ok = lookback_sum(p.st_bytes, k, sg.item_base, excl);
     if (lane == 0) st_publish(p.st_bytes + k, ok ? (kStInc | (excl + chunk)) : kStErr);
     if (!ok) {
@@ -619,12 +704,10 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   }
   const unsigned long long at_b =
       sg.shdr + (unsigned long long)(t + 1) * sg.fhdr + 8ull * H * (ta + 1) + excl;
-  const bool fits = at_b + chunk <= sg.cap;
-  if (!fits && lane == 0) atomicOr(sg.err, kErrCapacity);
-
-  // ---- pass B2: block bodies (in shared memory)
-  pass_b2(w.zb, n, nb, w.meta);
-  if (!fits) return;
+  if (at_b + chunk > sg.cap) {
+    if (lane == 0) atomicOr(sg.err, kErrCapacity);
+    return;
+  }
   uint32_t* dst = reinterpret_cast<uint32_t*>(sg.out + at_b);
 
   // ---- mask part: 2-bit class per word (16 per class word), literals

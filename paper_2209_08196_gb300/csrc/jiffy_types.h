@@ -29,18 +29,23 @@ constexpr unsigned long long kSpinLimitNs = 2000000000ull;
 
 // Quantizer of one attribute (Sec. III-B): q = min(floor((v + half) / P), qmax).
 //   qkind 0: P = 1, q = v.
-//   qkind 1: 2 <= P < 2^30: q0 = umulhi(v, m32) with m32 = floor(2^32 / P) is
-//            floor(v / P) or one less, so r = v - q0 P lies in [0, 2P) and
-//            q = q0 + [r + half >= P] + [r + half >= 2P] (no overflow: 3P < 2^32).
-//   qkind 2: larger P: 64-bit reciprocal `magic` = ceil(2^64 / P).
+//   qkind 1: q = umulhi(min(v, lim) + half, m32) >> sh. lim = the largest v
+//            whose q is not clamped (capped so that lim + half < 2^32); any
+//            larger v gives q = qmax, and so does lim. (m32, sh) divides
+//            every 32-bit dividend exactly: m32 = ceil(2^(32+sh) / P) with
+//            m32 P - 2^(32+sh) <= 2^sh (Granlund and Montgomery, "Division by
+//            invariant integers using multiplication", 1994, Thm. 4.2).
+//   qkind 2: no 32-bit multiplier exists: 64-bit reciprocal `magic` =
+//            ceil(2^64 / P).
 struct AttrDev {
   uint32_t s;                 // bytes per sample: 1, 2 or 4
   uint32_t P;                 // precision
   uint32_t qmax;              // floor(max_sample / P)
   uint32_t qkind;
   unsigned long long magic;   // ceil(2^64 / P), for 2 <= P <= 2^31
-  uint32_t m32;               // floor(2^32 / P) for qkind 1
+  uint32_t m32, sh;           // qkind 1 multiplier and shift
   uint32_t half;              // floor(P / 2)
+  uint32_t lim;               // qkind 1 input clamp
 };
 
 inline AttrDev make_attr(uint32_t s, uint32_t P) {
@@ -51,13 +56,24 @@ inline AttrDev make_attr(uint32_t s, uint32_t P) {
   d.qmax = maxv / P;
   d.half = P >> 1;
   d.magic = (P >= 2 && P <= 0x80000000u) ? (~0ull) / P + 1ull : 0ull;
+  d.qkind = 2;
   if (P == 1) {
     d.qkind = 0;
-  } else if (P < (1u << 30)) {
-    d.qkind = 1;
-    d.m32 = (uint32_t)((1ull << 32) / P);
-  } else {
-    d.qkind = 2;
+    return d;
+  }
+  for (uint32_t l = 0; l < 32; l++) {
+    const unsigned __int128 two = (unsigned __int128)1 << (32 + l);
+    const unsigned __int128 m = (two + P - 1) / P;
+    if (m >> 32) break;  // multipliers only grow with l
+    if (m * P - two <= ((unsigned __int128)1 << l)) {
+      d.qkind = 1;
+      d.m32 = (uint32_t)m;
+      d.sh = l;
+      const unsigned long long top = (unsigned long long)d.qmax * P + (P - 1) - d.half;
+      const unsigned long long cap = 0xffffffffull - d.half;
+      d.lim = (uint32_t)(top < cap ? top : cap);
+      break;
+    }
   }
   return d;
 }

@@ -231,15 +231,36 @@ def _seq_planes(h: Handle, planes):
     return T, [p for scan in planes for p in scan]
 
 
+def _seq_ptrs(h: Handle, planes, what: str):
+    """(T, ctypes array of the T * A plane pointers, scan-major). A list over
+    attributes of contiguous T x H x W tensors is checked once per attribute
+    and addressed by arithmetic; any other form is checked plane by plane."""
+    if isinstance(planes[0], torch.Tensor) and len(planes) == h.A and planes[0].dim() == 3:
+        T = planes[0].shape[0]
+        bases, steps = [], []
+        for a, (p, (s, _)) in enumerate(zip(planes, h.attrs)):
+            if p.shape[0] != T or not p.is_cuda or p.element_size() != s or not p.is_contiguous() or \
+                    p.shape[1] * p.shape[2] != h.H * h.W:
+                raise ValueError("%s %d: expected a contiguous CUDA tensor of %d x %d x %d %d-byte samples, got %s %s"
+                                 % (what, a, T, h.H, h.W, s, tuple(p.shape), p.dtype))
+            bases.append(p.data_ptr())
+            steps.append(h.H * h.W * s)
+        A = h.A
+        ptrs = [bases[a] + t * steps[a] for t in range(T) for a in range(A)]
+        return T, (ctypes.c_void_p * len(ptrs))(*ptrs)
+    T, flat = _seq_planes(h, planes)
+    for i, p in enumerate(flat):
+        _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "%s %d" % (what, i))
+    return T, _ptr_array(flat)
+
+
 def jiffy_encode_seq(h: Handle, planes, out: torch.Tensor, stream=None):
     """Encodes T consecutive scans in one pass; returns (total bytes, list of
     T + 1 frame offsets)."""
-    T, flat = _seq_planes(h, planes)
-    for i, p in enumerate(flat):
-        _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "plane %d" % i)
+    T, arr = _seq_ptrs(h, planes, "plane")
     offs = (ctypes.c_uint64 * (T + 1))()
     n = ctypes.c_size_t(0)
-    st = _lib().jiffy_encode_seq(h.ptr, T, _ptr_array(flat), out.data_ptr(), out.numel() * out.element_size(),
+    st = _lib().jiffy_encode_seq(h.ptr, T, arr, out.data_ptr(), out.numel() * out.element_size(),
                                  offs, ctypes.byref(n), _stream_ptr(stream))
     if st != 0:
         raise JiffyError(st, "jiffy_encode_seq", required=n.value if st == 2 else None)
@@ -257,13 +278,11 @@ def jiffy_decode(h: Handle, buf: torch.Tensor, length: int, planes_out, stream=N
 
 def jiffy_decode_seq(h: Handle, buf: torch.Tensor, length: int, offsets, planes_out, stream=None):
     """Decodes T frames whose byte offsets (T + 1 entries) are `offsets`."""
-    T, flat = _seq_planes(h, planes_out)
+    T, arr = _seq_ptrs(h, planes_out, "output plane")
     if len(offsets) != T + 1:
         raise ValueError("need T + 1 frame offsets")
-    for i, p in enumerate(flat):
-        _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "output plane %d" % i)
     offs = (ctypes.c_uint64 * (T + 1))(*[int(o) for o in offsets])
-    st = _lib().jiffy_decode_seq(h.ptr, T, buf.data_ptr(), length, offs, _ptr_array(flat), _stream_ptr(stream))
+    st = _lib().jiffy_decode_seq(h.ptr, T, buf.data_ptr(), length, offs, arr, _stream_ptr(stream))
     if st != 0:
         raise JiffyError(st, "jiffy_decode_seq")
 
