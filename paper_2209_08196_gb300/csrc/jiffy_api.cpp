@@ -204,6 +204,8 @@ jiffy_status map_device_error(uint32_t err) {
 
 uint32_t stream_header_bytes(uint32_t A) { return 16u + 8u * A; }
 uint32_t frame_header_bytes(uint32_t A) { return 8u + 12u * A; }
+uint32_t slot_bytes_for(uint32_t W) { return (jiffy::row_bound_bytes(W) + 15u) & ~15u; }
+
 // Number of distinct test rows floor((2k+1)H/(2L)), k < L (Sec. III-E).
 uint32_t distinct_test_rows(uint32_t H, uint32_t L) {
   uint32_t n = 0, last = 0;
@@ -375,17 +377,25 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     r_off[i] = rs.take(8ull * (jobs[i].T + 1));
   }
   // ---- device scratch: upload, zeroed region (look-back words, trial
-  //      costs, ticket, results), work arrays
+  //      costs, ticket, results), work arrays, row slots
   Carver c;
   const size_t o_up = c.take(up.off);
   const size_t o_zero = c.take(0);
-  const size_t o_stc = c.take(8ull * items), o_stb = c.take(8ull * items);
+  const size_t o_stc = c.take(8ull * items);
   const size_t o_cost = c.take(8ull * secs), o_tick = c.take(8);
   const size_t o_res = c.take(rs.off);
   const size_t zero_bytes = c.off - o_zero;
   const size_t o_modes = c.take(4ull * secs);
   const size_t o_rb = c.take(4ull * items), o_rn = c.take(4ull * items), o_rc = c.take(4ull * items);
-  const size_t o_roff = c.take(8ull * items);
+  const size_t o_secb = c.take(8ull * secs), o_secn = c.take(4ull * secs);
+  std::vector<unsigned long long> slot_base(n);
+  unsigned long long slots_total = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    const jiffy_stream* s = jobs[i].s;
+    slot_base[i] = slots_total;
+    slots_total += (unsigned long long)slot_bytes_for(s->W) * jobs[i].T * s->A * s->H;
+  }
+  const size_t o_slots = c.take(slots_total);
   const size_t h_res = align_up(up.off, 256);
   jiffy_status r = ensure_scratch(ws, c.off, h_res + rs.off);
   if (r != JIFFY_OK) return r;
@@ -429,6 +439,8 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     g.force_mode = s->opt.force_mode;
     g.item_base = item_base;
     g.sec_base = sec_base;
+    g.slot_bytes = slot_bytes_for(s->W);
+    g.slot_base = slot_base[i];
     g.attrs = s->d_attrs;
     g.cur = reinterpret_cast<const uint8_t* const*>(dp);
     g.prev = reinterpret_cast<const uint8_t* const*>(dp + 8ull * T * A);
@@ -460,9 +472,10 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   p.row_bytes = reinterpret_cast<uint32_t*>(d + o_rb);
   p.row_nnz = reinterpret_cast<uint32_t*>(d + o_rn);
   p.row_carry = reinterpret_cast<uint32_t*>(d + o_rc);
-  p.row_off = reinterpret_cast<unsigned long long*>(d + o_roff);
   p.st_carry = reinterpret_cast<unsigned long long*>(d + o_stc);
-  p.st_bytes = reinterpret_cast<unsigned long long*>(d + o_stb);
+  p.slots = d + o_slots;
+  p.sec_bytes = reinterpret_cast<unsigned long long*>(d + o_secb);
+  p.sec_nnz = reinterpret_cast<uint32_t*>(d + o_secn);
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
   uint8_t* hres = h + h_res;
 

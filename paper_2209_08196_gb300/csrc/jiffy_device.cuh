@@ -330,21 +330,24 @@ __device__ __forceinline__ void st_publish(unsigned long long* p, unsigned long 
   atomicExch(p, v);
 }
 
+// Outcome of a look-back step.
+enum : int { kLbFail = 0, kLbOk = 1, kLbPending = 2 };
+
 // Warp-wide window read for the look-backs: kLookQ x 32 status words per
 // round, entry (q, lane) = word j - 32q - lane (nearest first), `beyond` past
 // the segment start. Finds the nearest entry that decides the look-back,
-// re-reading while an entry nearer than it is still empty; gives up after
-// kSpinLimitNs. stop = kLookQ * 32: no decision in this window. A wide window
-// keeps the walk short when thousands of rows are in flight and the nearest
-// published prefix lies hundreds of entries back.
+// re-reading while an entry nearer than it is still empty (or, with wait =
+// false, returning kLbPending at once); gives up after kSpinLimitNs. stop =
+// kLookQ * 32: no decision in this window.
 constexpr uint32_t kLookQ = 4;
 
 template <typename Decides>
-__device__ __forceinline__ bool lookback_window(const unsigned long long* st, int64_t j, uint32_t seg_start,
-                                                unsigned long long beyond, Decides decides,
-                                                unsigned long long (&s)[kLookQ], uint32_t& stop) {
+__device__ __forceinline__ int lookback_window(const unsigned long long* st, int64_t j, uint32_t seg_start,
+                                               unsigned long long beyond, Decides decides,
+                                               unsigned long long (&s)[kLookQ], uint32_t& stop, bool wait) {
   const uint32_t lane = lane_id();
   unsigned long long t0 = 0;
+  uint32_t ns = 32;
   while (true) {
 #pragma unroll
     for (uint32_t q = 0; q < kLookQ; q++) {
@@ -365,27 +368,31 @@ __device__ __forceinline__ bool lookback_window(const unsigned long long* st, in
         if (first < 32u) stop = 32u * q + first;
       }
     }
-    if (__any_sync(0xffffffffu, err)) return false;  // an upstream error
-    if (!waiting) return true;
+    if (__any_sync(0xffffffffu, err)) return kLbFail;  // an upstream error
+    if (!waiting) return kLbOk;
+    if (!wait) return kLbPending;
     if (t0 == 0) t0 = global_timer_ns();
-    else if (global_timer_ns() - t0 > kSpinLimitNs) return false;
-    __nanosleep(64);
+    else if (global_timer_ns() - t0 > kSpinLimitNs) return kLbFail;
+    __nanosleep(ns);
+    if (ns < 512) ns <<= 1;
   }
 }
 
 // Warp-wide. Exclusive prefix of item k over items [seg_start, k): sums
-// aggregates back to the nearest inclusive prefix. Returns false on an
-// upstream error or a timeout.
-__device__ inline bool lookback_sum(const unsigned long long* st, uint32_t k, uint32_t seg_start,
-                                    unsigned long long& excl) {
+// aggregates back to the nearest inclusive prefix. Returns kLbOk, kLbFail
+// (an upstream error or a timeout) or, with wait = false, kLbPending when a
+// predecessor has not published yet.
+__device__ inline int lookback_sum(const unsigned long long* st, uint32_t k, uint32_t seg_start,
+                                   unsigned long long& excl, bool wait = true) {
   const uint32_t lane = lane_id();
   unsigned long long acc = 0;
   int64_t j = (int64_t)k - 1;
   while (j >= (int64_t)seg_start) {
     unsigned long long s[kLookQ];
     uint32_t stop;
-    if (!lookback_window(st, j, seg_start, kStInc, [](unsigned long long x) { return (x >> 62) == 2ull; }, s, stop))
-      return false;
+    const int rc = lookback_window(st, j, seg_start, kStInc, [](unsigned long long x) { return (x >> 62) == 2ull; },
+                                   s, stop, wait);
+    if (rc != kLbOk) return rc;
     unsigned long long v = 0;
 #pragma unroll
     for (uint32_t q = 0; q < kLookQ; q++)
@@ -396,7 +403,7 @@ __device__ inline bool lookback_sum(const unsigned long long* st, uint32_t k, ui
     j -= kLookQ * 32;
   }
   excl = acc;
-  return true;
+  return kLbOk;
 }
 
 // Warp-wide. "Last valid" look-back for the delta carry: value bit 32 =
@@ -409,8 +416,9 @@ __device__ inline bool lookback_last(const unsigned long long* st, uint32_t k, u
   while (true) {
     unsigned long long s[kLookQ];
     uint32_t stop;
-    if (!lookback_window(st, j, seg_start, kStInc | (1ull << 32),
-                         [](unsigned long long x) { return ((x >> 62) == 2ull) || ((x >> 32) & 1ull); }, s, stop))
+    if (lookback_window(st, j, seg_start, kStInc | (1ull << 32),
+                        [](unsigned long long x) { return ((x >> 62) == 2ull) || ((x >> 32) & 1ull); }, s, stop,
+                        true) != kLbOk)
       return false;
     if (stop < kLookQ * 32u) {
       uint32_t c = 0;

@@ -21,15 +21,17 @@
 //               wider than b for every b at once -- carry-save adders over
 //               the values' unary width codes, bit-sliced across the 4 lanes
 //               of a block -- and the byte-minimal width (Sec. II, PFOR).
-//     place     the row's chunk size goes into a decoupled look-back over
-//               all rows of the segment (Merrill & Garland, 2016), giving
-//               the chunk's final byte offset in the stream.
 //     pass B2   one block at a time, 4 consecutive values per lane: low bits
-//               assembled in registers with funnel shifts and merged into
-//               the block body in shared memory, exceptions apart; then the
-//               mask code, block headers and bodies go straight to the
-//               stream.
-//   k_finalize  one CTA per section: row table, frame and stream headers.
+//               joined with funnel shifts, each body word written once by
+//               the lane holding its first bit, exceptions listed and packed
+//               the same way; then the mask code, block headers and bodies
+//               go to the row's slot. Rows never wait for one another's
+//               sizes (sections differ a lot in cost, and an in-order prefix
+//               over rows would queue fast rows behind slow ones).
+//   k_sec_sizes one CTA per section: its bytes and nonzero count.
+//   k_place     one CTA per section: offset (sum over the earlier sections),
+//               row table, frame and stream headers, and the copy of every
+//               row chunk from its slot to its place in the stream.
 #include "jiffy_device.cuh"
 #include "jiffy_kernels.h"
 
@@ -351,17 +353,79 @@ __device__ __forceinline__ uint32_t pass_b1(uint32_t* zb, uint32_t n, uint32_t c
 }
 
 // ---------------------------------------------------------------------------
+// Packs 128 values of b bits, value i at bit i b (Sec. II, a block's low-bit
+// stream), into words [0, nwords) of dst. Lane l holds values 4l .. 4l+3,
+// bits [4lb, 4lb + 4b) of the stream; each word is written once, by the lane
+// holding its first bit: the lane joins its values with funnel shifts and
+// completes the word with the following lanes' bits (one shuffle for b > 8;
+// for b <= 8, where a word spans several lanes, log-step shuffles double the
+// joined run). Bits of the values above b are dropped.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pack4(uint32_t* dst, uint32_t b, uint32_t nwords, uint32_t z0, uint32_t z1,
+                                      uint32_t z2, uint32_t z3) {
+  const uint32_t lane = lane_id();
+  const uint32_t S = 4u * lane * b;           // the lane's first bit
+  const uint32_t o = (32u - (S & 31u)) & 31u;  // its first word start, relative to S
+  const uint32_t w = (S + o) >> 5;            // that word
+  if (b == 0) return;
+  if (b <= 8u) {
+    const uint32_t bm = (1u << b) - 1u;
+    unsigned long long y = (z0 & bm) | ((z1 & bm) << b) | ((z2 & bm) << (2u * b)) | ((z3 & bm) << (3u * b));
+    for (uint32_t d = 1, len = 4u * b; len < 64u; d <<= 1, len <<= 1) {
+      unsigned long long t = __shfl_down_sync(0xffffffffu, y, d);
+      if (lane + d > 31u) t = 0ull;
+      y |= t << len;
+    }
+    if (o < 4u * b && w < nwords) dst[w] = (uint32_t)(y >> o);
+  } else if (b <= 16u) {
+    const uint32_t bm = (1u << b) - 1u;
+    const unsigned long long x = (unsigned long long)(z0 & bm) | ((unsigned long long)(z1 & bm) << b) |
+                                 ((unsigned long long)(z2 & bm) << (2u * b)) |
+                                 ((unsigned long long)(z3 & bm) << (3u * b));
+    uint32_t N = __shfl_down_sync(0xffffffffu, (uint32_t)x, 1);
+    if (lane == 31u) N = 0u;
+    const uint32_t sN = 4u * b - 32u;  // the next lane's bits start at word 1, bit sN (4..32)
+    const uint32_t Z0 = (uint32_t)x, Z1 = (uint32_t)(x >> 32) | __funnelshift_lc(0u, N, sN),
+                   Z2 = __funnelshift_lc(N, 0u, sN);
+    if (w < nwords) dst[w] = __funnelshift_r(Z0, Z1, o);
+    if (o + 32u < 4u * b && w + 1u < nwords) dst[w + 1] = __funnelshift_r(Z1, Z2, o);
+  } else {
+    const uint32_t bm = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
+    const unsigned long long lo = (unsigned long long)(z0 & bm) | ((unsigned long long)(z1 & bm) << b);
+    const unsigned long long hi = (unsigned long long)(z2 & bm) | ((unsigned long long)(z3 & bm) << b);
+    const uint32_t s2 = 2u * b - 32u;  // hi starts at word 1, bit s2 (2..32)
+    const uint32_t h0 = (uint32_t)hi, h1 = (uint32_t)(hi >> 32);
+    uint32_t X0 = (uint32_t)lo, X1 = (uint32_t)(lo >> 32) | __funnelshift_lc(0u, h0, s2),
+             X2 = __funnelshift_lc(h0, h1, s2), X3 = __funnelshift_lc(h1, 0u, s2), X4 = 0u;
+    uint32_t N = __shfl_down_sync(0xffffffffu, X0, 1);
+    if (lane == 31u) N = 0u;
+    if (4u * b <= 96u) {  // the next lane's bits start at word 2, bit 4b - 64 (4..32)
+      const uint32_t sN = 4u * b - 64u;
+      X2 |= __funnelshift_lc(0u, N, sN);
+      X3 |= __funnelshift_lc(N, 0u, sN);
+    } else {  // word 3, bit 4b - 96 (4..32)
+      const uint32_t sN = 4u * b - 96u;
+      X3 |= __funnelshift_lc(0u, N, sN);
+      X4 = __funnelshift_lc(N, 0u, sN);
+    }
+    if (w < nwords) dst[w] = __funnelshift_r(X0, X1, o);
+    if (o + 32u < 4u * b && w + 1u < nwords) dst[w + 1] = __funnelshift_r(X1, X2, o);
+    if (o + 64u < 4u * b && w + 2u < nwords) dst[w + 2] = __funnelshift_r(X2, X3, o);
+    if (o + 96u < 4u * b && w + 3u < nwords) dst[w + 3] = __funnelshift_r(X3, X4, o);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Pass B2: packs every block's body into zb, in place and unswizzled (block
 // g's body lands in words [off_g, off_g + size_g) with off_g + size_g <=
-// 128 (g + 1), so it never reaches a value still to be read). Lane l holds
-// values 4l .. 4l+3 of the block, i.e. bits [4lb, 4lb + 4b) of the low-bit
-// stream (Sec. II: low parts of all values, then the exceptions' positions
-// and high parts). Each stream word is written once, by the lane holding its
-// first bit: the lane joins its values with funnel shifts and completes the
-// word with the following lanes' bits (one shuffle for b > 8; for b <= 8,
-// where a word spans several lanes, log-step shuffles double the run).
+// 128 (g + 1), so it never reaches a value still to be read): the low b
+// bits of all values, then the exceptions (values wider than b) as e
+// position bytes in ascending order and their high parts of hb bits (Sec. II,
+// PFOR). The exceptions are first listed in order in xpos / xhv (128
+// entries), then packed like the low bits.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void pass_b2(uint32_t* zb, uint32_t n, uint32_t nb, const uint2* meta) {
+__device__ __forceinline__ void pass_b2(uint32_t* zb, uint32_t n, uint32_t nb, const uint2* meta, uint8_t* xpos,
+                                        uint32_t* xhv) {
   const uint32_t lane = lane_id(), below = (1u << lane) - 1u;
   for (uint32_t g = 0; g < nb; g++) {
     const uint2 md = meta[g];  // .x header, .y body byte offset
@@ -373,76 +437,26 @@ __device__ __forceinline__ void pass_b2(uint32_t* zb, uint32_t n, uint32_t nb, c
     const uint4 zz = reinterpret_cast<const uint4*>(zb + 32u * sgi)[(lane & 7u) ^ (sgi & 7u)];
     const uint32_t z0 = zz.x, z1 = zz.y, z2 = zz.z, z3 = zz.w;  // 0 past m
     __syncwarp();
-    const uint32_t S = 4u * lane * b;           // the lane's first bit
-    const uint32_t o = (32u - (S & 31u)) & 31u;  // its first word start, relative to S
-    const uint32_t w = (S + o) >> 5;            // that word
-    if (b == 0) {
-    } else if (b <= 8u) {
-      const uint32_t bm = (1u << b) - 1u;
-      unsigned long long y = (z0 & bm) | ((z1 & bm) << b) | ((z2 & bm) << (2u * b)) | ((z3 & bm) << (3u * b));
-      for (uint32_t d = 1, len = 4u * b; len < 64u; d <<= 1, len <<= 1) {
-        unsigned long long t = __shfl_down_sync(0xffffffffu, y, d);
-        if (lane + d > 31u) t = 0ull;
-        y |= t << len;
-      }
-      if (o < 4u * b && w < low_words) body[w] = (uint32_t)(y >> o);
-    } else if (b <= 16u) {
-      const uint32_t bm = (1u << b) - 1u;
-      const unsigned long long x = (unsigned long long)(z0 & bm) | ((unsigned long long)(z1 & bm) << b) |
-                                   ((unsigned long long)(z2 & bm) << (2u * b)) |
-                                   ((unsigned long long)(z3 & bm) << (3u * b));
-      uint32_t N = __shfl_down_sync(0xffffffffu, (uint32_t)x, 1);
-      if (lane == 31u) N = 0u;
-      const uint32_t sN = 4u * b - 32u;  // the next lane's bits start at word 1, bit sN (4..32)
-      const uint32_t Z0 = (uint32_t)x, Z1 = (uint32_t)(x >> 32) | __funnelshift_lc(0u, N, sN),
-                     Z2 = __funnelshift_lc(N, 0u, sN);
-      if (w < low_words) body[w] = __funnelshift_r(Z0, Z1, o);
-      if (o + 32u < 4u * b && w + 1u < low_words) body[w + 1] = __funnelshift_r(Z1, Z2, o);
-    } else {
-      const uint32_t bm = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
-      const unsigned long long lo = (unsigned long long)(z0 & bm) | ((unsigned long long)(z1 & bm) << b);
-      const unsigned long long hi = (unsigned long long)(z2 & bm) | ((unsigned long long)(z3 & bm) << b);
-      const uint32_t s2 = 2u * b - 32u;  // hi starts at word 1, bit s2 (2..32)
-      const uint32_t h0 = (uint32_t)hi, h1 = (uint32_t)(hi >> 32);
-      uint32_t X0 = (uint32_t)lo, X1 = (uint32_t)(lo >> 32) | __funnelshift_lc(0u, h0, s2),
-               X2 = __funnelshift_lc(h0, h1, s2), X3 = __funnelshift_lc(h1, 0u, s2), X4 = 0u;
-      uint32_t N = __shfl_down_sync(0xffffffffu, X0, 1);
-      if (lane == 31u) N = 0u;
-      if (4u * b <= 96u) {  // the next lane's bits start at word 2, bit 4b - 64 (4..32)
-        const uint32_t sN = 4u * b - 64u;
-        X2 |= __funnelshift_lc(0u, N, sN);
-        X3 |= __funnelshift_lc(N, 0u, sN);
-      } else {  // word 3, bit 4b - 96 (4..32)
-        const uint32_t sN = 4u * b - 96u;
-        X3 |= __funnelshift_lc(0u, N, sN);
-        X4 = __funnelshift_lc(N, 0u, sN);
-      }
-      if (w < low_words) body[w] = __funnelshift_r(X0, X1, o);
-      if (o + 32u < 4u * b && w + 1u < low_words) body[w + 1] = __funnelshift_r(X1, X2, o);
-      if (o + 64u < 4u * b && w + 2u < low_words) body[w + 2] = __funnelshift_r(X2, X3, o);
-      if (o + 96u < 4u * b && w + 3u < low_words) body[w + 3] = __funnelshift_r(X3, X4, o);
-    }
-    if (e) {  // exceptions: position bytes (ascending), then high parts of hb bits
-      const uint32_t pw = (e + 3u) >> 2, hw = (e * hb + 31u) >> 5;
-      for (uint32_t i = lane; i < pw + hw; i += 32u) body[low_words + i] = 0u;
-      __syncwarp();
-      uint32_t xm = ((z0 >> b) != 0u ? 1u : 0u) | ((z1 >> b) != 0u ? 2u : 0u) | ((z2 >> b) != 0u ? 4u : 0u) |
-                    ((z3 >> b) != 0u ? 8u : 0u);  // e > 0 implies b < 32
+    pack4(body, b, low_words, z0, z1, z2, z3);
+    if (e) {  // e > 0 implies b < 32
+      const uint32_t xm = ((z0 >> b) != 0u ? 1u : 0u) | ((z1 >> b) != 0u ? 2u : 0u) |
+                          ((z2 >> b) != 0u ? 4u : 0u) | ((z3 >> b) != 0u ? 8u : 0u);
       uint32_t rank = 0;
 #pragma unroll
       for (uint32_t q = 0; q < 4; q++) rank += __popc(__ballot_sync(0xffffffffu, (xm >> q) & 1u) & below);
-      uint8_t* pos = reinterpret_cast<uint8_t*>(body + low_words);
-      uint32_t* hp = body + low_words + pw;
-      while (xm) {
-        const uint32_t q = __ffs(xm) - 1u;
-        xm &= xm - 1u;
-        const uint32_t v = q == 0 ? z0 : (q == 1 ? z1 : (q == 2 ? z2 : z3));
-        pos[rank] = (uint8_t)(4u * lane + q);
-        const uint32_t hv = v >> b, hbit = rank * hb, hs = hbit & 31u;
-        atomicOr(hp + (hbit >> 5), hv << hs);
-        if (hs + hb > 32u) atomicOr(hp + (hbit >> 5) + 1u, hv >> (32u - hs));
-        rank++;
-      }
+      if (xm & 1u) { xpos[rank] = (uint8_t)(4u * lane); xhv[rank] = z0 >> b; rank++; }
+      if (xm & 2u) { xpos[rank] = (uint8_t)(4u * lane + 1u); xhv[rank] = z1 >> b; rank++; }
+      if (xm & 4u) { xpos[rank] = (uint8_t)(4u * lane + 2u); xhv[rank] = z2 >> b; rank++; }
+      if (xm & 8u) { xpos[rank] = (uint8_t)(4u * lane + 3u); xhv[rank] = z3 >> b; }
+      __syncwarp();
+      const uint32_t pw = (e + 3u) >> 2;
+      uint32_t pword = reinterpret_cast<const uint32_t*>(xpos)[lane];
+      if (4u * lane + 4u > e) pword &= 4u * lane >= e ? 0u : ((1u << (8u * (e - 4u * lane))) - 1u);
+      if (lane < pw) body[low_words + lane] = pword;
+      const uint4 hv = reinterpret_cast<const uint4*>(xhv)[lane];
+      const uint32_t i0 = 4u * lane;
+      pack4(body + low_words + pw, hb, (e * hb + 31u) >> 5, i0 < e ? hv.x : 0u, i0 + 1u < e ? hv.y : 0u,
+            i0 + 2u < e ? hv.z : 0u, i0 + 3u < e ? hv.w : 0u);
     }
     __syncwarp();
   }
@@ -518,7 +532,7 @@ __global__ void __launch_bounds__(32) k_trial(EncParams p) {
 // buffer (values rounded up to whole pass-B1 steps), coded mask bytes, block
 // metadata.
 struct EncWarpLayout {
-  uint32_t zb, mb, meta, bytes;
+  uint32_t zb, mb, meta, xpos, xhv, bytes;
 };
 
 __host__ __device__ inline EncWarpLayout enc_warp_layout(uint32_t W) {
@@ -528,7 +542,9 @@ __host__ __device__ inline EncWarpLayout enc_warp_layout(uint32_t W) {
   L.zb = 0;
   L.mb = 4u * ceil_div_u32(W, kStepVal) * kStepVal;
   L.meta = a16(L.mb + ceil_div_u32(W, 32) * 4u);
-  L.bytes = a16(L.meta + 8u * nbmax);
+  L.xpos = a16(L.meta + 8u * nbmax);
+  L.xhv = L.xpos + kBlockN;
+  L.bytes = a16(L.xhv + 4u * kBlockN);
   return L;
 }
 
@@ -536,6 +552,8 @@ struct EncWarp {
   uint32_t* zb;
   uint8_t* mb;
   uint2* meta;
+  uint8_t* xpos;
+  uint32_t* xhv;
 };
 
 // The last nonzero sample among the 8 (nv valid) in v / pv, across the warp:
@@ -640,7 +658,6 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
       if (lane == 0) {
         atomicOr(sg.err, kErrTimeout);
         st_publish(p.st_carry + k, kStErr);
-        st_publish(p.st_bytes + k, kStErr);
       }
       return;
     }
@@ -681,34 +698,17 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   __syncwarp();
   const uint32_t head_words = ncls + nlit + nb;
   const uint32_t chunk = 4u * head_words + body;
-  if (lane == 0) st_publish(p.st_bytes + k, (kl == 0 ? kStInc : kStAgg) | chunk);
-
-  // ---- pass B2: block bodies, packed in shared memory
-  pass_b2(w.zb, n, nb, w.meta);
-
-  // ---- placement: decoupled look-back over the segment's rows
-  unsigned long long excl = 0;
-  if (kl > 0) {
-    const bool ok = lookback_sum(p.st_bytes, k, sg.item_base, excl);
-    if (lane == 0) st_publish(p.st_bytes + k, ok ? (kStInc | (excl + chunk)) : kStErr);
-    if (!ok) {
-      if (lane == 0) atomicOr(sg.err, kErrTimeout);
-      return;
-    }
-  }
   if (lane == 0) {
     p.row_bytes[k] = chunk;
     p.row_nnz[k] = n;
     p.row_carry[k] = carry;
-    p.row_off[k] = excl;
   }
-  const unsigned long long at_b =
-      sg.shdr + (unsigned long long)(t + 1) * sg.fhdr + 8ull * H * (ta + 1) + excl;
-  if (at_b + chunk > sg.cap) {
-    if (lane == 0) atomicOr(sg.err, kErrCapacity);
-    return;
-  }
-  uint32_t* dst = reinterpret_cast<uint32_t*>(sg.out + at_b);
+
+  // ---- pass B2: block bodies, packed in shared memory
+  pass_b2(w.zb, n, nb, w.meta, w.xpos, w.xhv);
+
+  // ---- the chunk goes to this row's slot; k_place moves it to its offset
+  uint32_t* dst = reinterpret_cast<uint32_t*>(p.slots + sg.slot_base + (size_t)kl * sg.slot_bytes);
 
   // ---- mask part: 2-bit class per word (16 per class word), literals
   const uint32_t below = (1u << lane) - 1u;
@@ -743,6 +743,8 @@ __global__ void __launch_bounds__(WPC * 32, 24 / WPC) k_encode(EncParams p) {
   w.zb = reinterpret_cast<uint32_t*>(wb + lay.zb);
   w.mb = wb + lay.mb;
   w.meta = reinterpret_cast<uint2*>(wb + lay.meta);
+  w.xpos = wb + lay.xpos;
+  w.xhv = reinterpret_cast<uint32_t*>(wb + lay.xhv);
   while (true) {
     uint32_t k = 0;
     if (lane == 0) k = atomicAdd(p.ticket, 1u);
@@ -753,10 +755,12 @@ __global__ void __launch_bounds__(WPC * 32, 24 / WPC) k_encode(EncParams p) {
 }
 
 // ----------------------------------------------------------------------------
-// k_finalize: one CTA per section (scan t, attribute a): the row table (end
-// offsets within the section's chunk data + carries), the section's entry in
-// the frame header and, for attribute 0, the frame's size, scan index and
-// offset; section 0 of a segment with a stream header also writes it. Every
+// k_sec_sizes: one CTA per section (scan t, attribute a): its bytes (row
+// table + row chunks) and nonzero count.
+// k_place: one CTA per section: the section's offset in the stream (sum over
+// the segment's earlier sections), its row table (end offsets + carries),
+// the copy of each row chunk from its slot and, for attribute 0, the frame
+// header and frame offset; section 0 also writes the stream header. Every
 // write is checked against the output capacity.
 // ----------------------------------------------------------------------------
 __device__ __forceinline__ void put_u32_guarded(uint8_t* out, unsigned long long cap, unsigned long long at,
@@ -765,8 +769,39 @@ __device__ __forceinline__ void put_u32_guarded(uint8_t* out, unsigned long long
   else atomicOr(err, kErrCapacity);
 }
 
-__global__ void __launch_bounds__(kThreads) k_finalize(EncParams p) {
+__device__ __forceinline__ unsigned long long cta_sum_u64(unsigned long long v, unsigned long long* s_red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane_id() == 0) s_red[warp_id()] = v;
+  __syncthreads();
+  unsigned long long tot = 0;
+  for (uint32_t w2 = 0; w2 < blockDim.x / 32u; w2++) tot += s_red[w2];
+  __syncthreads();
+  return tot;
+}
+
+__global__ void __launch_bounds__(kThreads) k_sec_sizes(EncParams p) {
   __shared__ unsigned long long s_red[kWarps];
+  const uint32_t gs = blockIdx.x;
+  const EncSeg& sg = p.seg[find_seg(p.seg_sec_base, p.n_seg, gs)];
+  const uint32_t H = sg.H;
+  const uint32_t item0 = sg.item_base + (gs - sg.sec_base) * H;
+  unsigned long long bytes = 0, nnz = 0;
+  for (uint32_t r = threadIdx.x; r < H; r += kThreads) {
+    bytes += p.row_bytes[item0 + r];
+    nnz += p.row_nnz[item0 + r];
+  }
+  bytes = cta_sum_u64(bytes, s_red);
+  nnz = cta_sum_u64(nnz, s_red);
+  if (threadIdx.x == 0) {
+    p.sec_bytes[gs] = 8ull * H + bytes;
+    p.sec_nnz[gs] = (uint32_t)nnz;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
+  extern __shared__ __align__(16) uint32_t smem[];  // [H] row chunk starts
+  __shared__ unsigned long long s_red[kWarps];
+  __shared__ uint32_t s_tmp[kWarps + 1];
   const uint32_t gs = blockIdx.x;
   const EncSeg& sg = p.seg[find_seg(p.seg_sec_base, p.n_seg, gs)];
   const uint32_t H = sg.H, A = sg.A;
@@ -774,36 +809,60 @@ __global__ void __launch_bounds__(kThreads) k_finalize(EncParams p) {
   const uint32_t item0 = sg.item_base + ta * H;
   uint8_t* out = sg.out;
   const unsigned long long cap = sg.cap;
-  const unsigned long long off0 = p.row_off[item0];
-  const unsigned long long sec_at = sg.shdr + (unsigned long long)(t + 1) * sg.fhdr + 8ull * H * ta + off0;
-  unsigned long long nnz = 0;
+  // bytes of the segment's earlier sections: of earlier frames (frame_before)
+  // and of this frame's earlier attributes
+  unsigned long long frame_before = 0, attr_before = 0;
+  for (uint32_t i = threadIdx.x; i < ta; i += kThreads) {
+    if (i < t * A) frame_before += p.sec_bytes[sg.sec_base + i];
+    else attr_before += p.sec_bytes[sg.sec_base + i];
+  }
+  frame_before = cta_sum_u64(frame_before, s_red);
+  attr_before = cta_sum_u64(attr_before, s_red);
+  const unsigned long long frame_at = sg.shdr + (unsigned long long)t * sg.fhdr + frame_before;
+  const unsigned long long sec_at = frame_at + sg.fhdr + attr_before;
+  // row table: end offsets (prefix of chunk sizes) and carries
+  for (uint32_t r = threadIdx.x; r < H; r += kThreads) smem[r] = p.row_bytes[item0 + r];
+  __syncthreads();
+  const uint32_t data = block_excl_scan(smem, H, s_tmp);  // smem = row starts
   for (uint32_t r = threadIdx.x; r < H; r += kThreads) {
-    const uint32_t end = (uint32_t)(p.row_off[item0 + r] + p.row_bytes[item0 + r] - off0);
+    const uint32_t end = (r + 1 < H) ? smem[r + 1] : data;
     put_u32_guarded(out, cap, sec_at + 8ull * r, end, sg.err);
     put_u32_guarded(out, cap, sec_at + 8ull * r + 4, p.row_carry[item0 + r], sg.err);
-    nnz += p.row_nnz[item0 + r];
   }
-  for (int o = 16; o > 0; o >>= 1) nnz += __shfl_xor_sync(0xffffffffu, nnz, o);
-  if (lane_id() == 0) s_red[warp_id()] = nnz;
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  nnz = 0;
-  for (uint32_t w2 = 0; w2 < kWarps; w2++) nnz += s_red[w2];
-  const uint32_t last = item0 + H - 1;
-  const unsigned long long sec_bytes = 8ull * H + (p.row_off[last] + p.row_bytes[last] - off0);
-  const unsigned long long frame_at = sg.shdr + (unsigned long long)t * sg.fhdr + 8ull * H * (t * A) +
-                                      p.row_off[sg.item_base + t * A * H];
-  const unsigned long long h = frame_at + 8ull + 12ull * a;
-  put_u32_guarded(out, cap, h, p.modes[gs], sg.err);
-  put_u32_guarded(out, cap, h + 4, (uint32_t)sec_bytes, sg.err);
-  put_u32_guarded(out, cap, h + 8, (uint32_t)nnz, sg.err);
-  if (a == 0) {
-    // frame bytes: header + row tables + all chunks of the frame's rows
-    const uint32_t fl = sg.item_base + (t * A + A) * H - 1;  // the frame's last row
-    const unsigned long long chunks = p.row_off[fl] + p.row_bytes[fl] - p.row_off[sg.item_base + t * A * H];
-    const unsigned long long fbytes = sg.fhdr + 8ull * H * A + chunks;
+  // row chunks: a warp per row, slot -> stream, 4 words in flight per lane
+  const unsigned long long data_at = sec_at + 8ull * H;
+  const uint32_t lane = lane_id();
+  for (uint32_t r = warp_id(); r < H; r += kWarps) {
+    const uint32_t words = p.row_bytes[item0 + r] / 4u;
+    const unsigned long long at = data_at + smem[r];
+    if (at + 4ull * words > cap) {
+      if (lane == 0) atomicOr(sg.err, kErrCapacity);
+      continue;
+    }
+    const uint32_t* src =
+        reinterpret_cast<const uint32_t*>(p.slots + sg.slot_base + (size_t)(ta * H + r) * sg.slot_bytes);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(out + at);
+    for (uint32_t i = lane; i < words; i += 128u) {
+      uint32_t v[4];
+#pragma unroll
+      for (uint32_t q = 0; q < 4; q++) v[q] = i + 32u * q < words ? __ldcs(src + i + 32u * q) : 0u;
+#pragma unroll
+      for (uint32_t q = 0; q < 4; q++)
+        if (i + 32u * q < words) dst[i + 32u * q] = v[q];
+    }
+  }
+  if (a == 0 && threadIdx.x == 0) {
+    const uint32_t f0 = sg.sec_base + t * A;
+    unsigned long long fbytes = sg.fhdr;
+    for (uint32_t aa = 0; aa < A; aa++) fbytes += p.sec_bytes[f0 + aa];
     put_u32_guarded(out, cap, frame_at, (uint32_t)fbytes, sg.err);
     put_u32_guarded(out, cap, frame_at + 4, sg.frame0 + t, sg.err);
+    for (uint32_t aa = 0; aa < A; aa++) {
+      const unsigned long long h = frame_at + 8ull + 12ull * aa;
+      put_u32_guarded(out, cap, h, p.modes[f0 + aa], sg.err);
+      put_u32_guarded(out, cap, h + 4, (uint32_t)p.sec_bytes[f0 + aa], sg.err);
+      put_u32_guarded(out, cap, h + 8, p.sec_nnz[f0 + aa], sg.err);
+    }
     sg.frame_off[t] = frame_at;
     if (t + 1 == sg.T) sg.frame_off[sg.T] = frame_at + fbytes;
     if (t == 0 && sg.shdr) {
@@ -833,7 +892,7 @@ static cudaError_t rows_occupancy(size_t smem, int* per_sm) {
 
 int encode_rows_launch(const EncParams& p, RowsLaunch* out) {
   const EncWarpLayout L = enc_warp_layout(p.max_W);
-  if ((L.mb | L.meta | L.bytes) & 15u) return (int)cudaErrorInvalidValue;  // 16-byte aligned regions
+  if ((L.mb | L.meta | L.xpos | L.xhv | L.bytes) & 15u) return (int)cudaErrorInvalidValue;  // 16-byte aligned regions
   uint32_t wpc = p.wpc;
   if ((wpc != 1 && wpc != 2 && wpc != 4) || wpc * L.bytes > kRowsSmemMax) wpc = 0;
   if (!wpc) wpc = 4 * L.bytes <= kRowsSmemAuto ? 4u : (2 * L.bytes <= kRowsSmemAuto ? 2u : 1u);
@@ -866,7 +925,9 @@ int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   RowsLaunch rl{};
   int rc = encode_rows_launch(p, &rl);
   if (rc != 0) return rc;
+  const size_t s_place = 4ull * kMaxH;
   cudaError_t e = cudaFuncSetAttribute(k_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_trial);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_place);
   if (e != cudaSuccess) return (int)e;
   auto mark = [&](int i) {
     if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[i]), st);
@@ -879,7 +940,8 @@ int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   else if (rl.wpc == 2) k_encode<2><<<rl.grid, 2 * 32, smem, st>>>(p);
   else k_encode<1><<<rl.grid, 32, smem, st>>>(p);
   mark(2);
-  k_finalize<<<p.n_sec, kThreads, 0, st>>>(p);
+  k_sec_sizes<<<p.n_sec, kThreads, 0, st>>>(p);
+  k_place<<<p.n_sec, kThreads, s_place, st>>>(p);
   mark(3);
   return (int)cudaGetLastError();
 }

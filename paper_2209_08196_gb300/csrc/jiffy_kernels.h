@@ -24,6 +24,8 @@ struct EncSeg {
   int32_t force_mode;
   uint32_t item_base;            // first global row item of the segment
   uint32_t sec_base;             // first global section of the segment
+  uint32_t slot_bytes;           // per-row slot size (row_bound(W) rounded to 16)
+  unsigned long long slot_base;  // byte offset of the segment's first slot
   const AttrDev* attrs;          // [A]
   const uint8_t* const* cur;     // [T*A] current planes
   const uint8_t* const* prev;    // [T*A] previous planes: t = 0 -> stored scan (or null), else raw t-1
@@ -48,9 +50,10 @@ struct EncParams {
   uint32_t* row_bytes;           // [n_items] chunk bytes
   uint32_t* row_nnz;             // [n_items]
   uint32_t* row_carry;           // [n_items]
-  unsigned long long* row_off;   // [n_items] exclusive prefix of chunk bytes in the segment
   unsigned long long* st_carry;  // [n_items] look-back status, delta carry (zeroed)
-  unsigned long long* st_bytes;  // [n_items] look-back status, chunk bytes (zeroed)
+  uint8_t* slots;                // packed row chunks, slot_base + local item * slot_bytes
+  unsigned long long* sec_bytes; // [n_sec] section bytes (row table + chunks)
+  uint32_t* sec_nnz;             // [n_sec]
   uint32_t* ticket;
   uint32_t wpc;                  // rows kernel: warps per CTA (1, 2, 4; 0 = by shared memory)
   uint32_t ctas_per_sm;          // rows kernel: resident CTAs per SM (0 = occupancy limit)
