@@ -18,13 +18,15 @@
 //   lanes    block headers validated and sized (Sec. II, PFOR blocks)
 //   then, per 256-pixel step, interleaved:
 //   unpack   the blocks the step needs, lane l owning the 4 consecutive
-//            values 4l..4l+3: funnel bit extract, exception high parts via a
-//            patch buffer, inverse ZigZag (Eq. 1), one warp scan per block
-//            from the row's carry (inverse delta) into a ring of residuals
-//   scatter  warp scan of counts -> compacted index of each own pixel; +
+//            values 4l..4l+3: a window of the body words they occupy,
+//            funnel-shift extraction, exception high parts via a patch
+//            buffer, inverse ZigZag (Eq. 1), into a ring of deltas
+//   scatter  warp scan of counts -> compacted index of each own pixel; the
+//            lane's running sum of its deltas + a warp scan of the lanes'
+//            sums from the row's carry = the residuals (inverse delta); +
 //            previous pixel for P; x precision (Sec. III-A); vector stores
-// The row chunk is staged in per-warp shared memory with one round of
-// independent loads; residuals pass through a small ring buffer.
+// The row chunk is read through L1 (bulk-prefetched into L2 at the start of
+// the row); deltas pass through a small ring buffer in shared memory.
 #include "jiffy_device.cuh"
 #include "jiffy_kernels.h"
 
@@ -57,29 +59,29 @@ __device__ __forceinline__ uint32_t find_seg(const uint32_t* base, uint32_t n, u
 
 }  // namespace
 
-// Per-warp shared memory (byte offsets): the staged row chunk, a ring of
-// 512 residuals (unpacked ahead of the scatter), a 128-word exception patch
-// buffer and the row's mask bytes.
+// Per-warp shared memory (byte offsets): a ring of 512 deltas (unpacked
+// ahead of the scatter), a 128-word exception patch buffer, the row's block
+// descriptors and mask bytes.
 constexpr uint32_t kRing = 512;
 
 struct DecWarpLayout {
-  uint32_t stage, ring, patch, mbytes, bytes;
+  uint32_t ring, patch, desc, mbytes, bytes;
 };
 
 __host__ __device__ inline DecWarpLayout dec_warp_layout(uint32_t W) {
   DecWarpLayout L;
-  L.stage = 0;
-  L.ring = (row_bound_bytes(W) + 15u) & ~15u;
+  L.ring = 0;
   L.patch = L.ring + 4u * kRing;
-  L.mbytes = L.patch + 4u * kBlockN;
+  L.desc = L.patch + 4u * kBlockN;
+  L.mbytes = L.desc + ((8u * ceil_div_u32(W, kBlockN) + 15u) & ~15u);
   L.bytes = (L.mbytes + ceil_div_u32(W, 8u) + 15u) & ~15u;
   return L;
 }
 
 // One row item, samples of S bytes (compile-time, so each warp runs one
 // compact path).
-__device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k, uint32_t* stage, uint32_t* ring,
-                                            uint32_t* patch, uint8_t* mbytes) {
+__device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k, uint32_t* ring,
+                                            uint32_t* patch, uint2* desc, uint8_t* mbytes) {
   const DecSeg& sg = p.seg[find_seg(p.seg_item_base, p.n_seg, k)];
   const uint32_t lane = lane_id();
   const uint32_t H = sg.H, W = sg.W, A = sg.A, nw = sg.nw, ncls = sg.ncls;
@@ -167,21 +169,18 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   if (mode == 1u) __threadfence();  // every lane orders its reads of the previous row after the flag
 
   bool bad = status != 0;
-  // ---- stage the chunk in shared memory: one round of independent loads
+  // ---- the chunk is read through L1: fetched into L2 in one bulk request,
+  //      its lines requested for L1 by the lanes (one round)
+  const uint32_t* chunk = reinterpret_cast<const uint32_t*>(sg.in + chunk_off);
   if (!bad) {
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(sg.in + chunk_off);
-    const uint32_t cw = clen / 4u;
-    for (uint32_t i = lane; i < cw; i += 128u) {
-      uint32_t v[4];
-#pragma unroll
-      for (uint32_t q = 0; q < 4; q++) v[q] = i + 32u * q < cw ? __ldg(src + i + 32u * q) : 0u;
-#pragma unroll
-      for (uint32_t q = 0; q < 4; q++)
-        if (i + 32u * q < cw) stage[i + 32u * q] = v[q];
+    if (lane == 0) {
+      const uintptr_t c0 = reinterpret_cast<uintptr_t>(chunk), c1 = c0 + clen;
+      const uintptr_t a0 = (c0 + 15u) & ~uintptr_t(15), a1 = c1 & ~uintptr_t(15);
+      if (a1 > a0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0)) : "memory");
     }
+    prefetch_l1(chunk, clen);
   }
-  __syncwarp();
-  const uint32_t* chunk = stage;
   // ---- class words: class 3 and bits past nw are invalid; literal prefix
   uint32_t cw = 0, lit = 0;
   if (!bad && lane < ncls) {
@@ -245,66 +244,92 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   const uint32_t nb = ceil_div_u32(n, kBlockN);
 
   // ---- block headers (lane l: blocks 4l .. 4l+3): validate, size the
-  //      bodies, check they fill the chunk exactly
+  //      bodies, check they fill the chunk exactly; descriptors {body word,
+  //      b | e << 8 | hb << 16 | m << 24} for the unpack
   const uint32_t hdr0 = ncls + nlit;
   if (!bad && 4u * (hdr0 + nb) > clen) bad = true;
   {
-    uint32_t mysum = 0;
+    uint32_t sz[4], hv[4], mysum = 0;
     bool lbad = false;
 #pragma unroll
     for (uint32_t q = 0; q < 4; q++) {
       const uint32_t blk = 4u * lane + q;
+      sz[q] = 0;
+      hv[q] = 0;
       if (!bad && blk < nb) {
         const uint32_t h = chunk[hdr0 + blk];
         const uint32_t b = h & 0xffu, e = (h >> 8) & 0xffu, hb = (h >> 16) & 0xffu;
         const uint32_t m = min(kBlockN, n - blk * kBlockN);
         if ((h >> 24) || b > 32u || hb > 32u || b + hb > 32u || e > m || ((e == 0u) != (hb == 0u))) lbad = true;
-        mysum += block_body_bytes(m, min(b, 32u), min(e, m), min(b + hb, 32u)) / 4u;
+        sz[q] = block_body_bytes(m, min(b, 32u), min(e, m), min(b + hb, 32u)) / 4u;
+        hv[q] = (h & 0x00ffffffu) | (m << 24);
+        mysum += sz[q];
       }
     }
     bad = __any_sync(0xffffffffu, bad || lbad);
-    if (!bad && 4u * (hdr0 + nb + warp_sum(mysum)) != clen) bad = true;
+    uint32_t total;
+    uint32_t o = hdr0 + nb + warp_excl_scan(mysum, total);
+    if (!bad && 4u * (hdr0 + nb + total) != clen) bad = true;
+#pragma unroll
+    for (uint32_t q = 0; q < 4; q++) {
+      const uint32_t blk = 4u * lane + q;
+      if (blk < nb) desc[blk] = make_uint2(o, hv[q]);
+      o += sz[q];
+    }
   }
   __syncwarp();
 
-  // ---- unpack (block by block, lane l: the 4 consecutive values 4l..4l+3;
-  //      funnel bit extract, exception high parts through the patch buffer,
-  //      inverse ZigZag (Eq. 1), prefix sum from the row's carry = inverse
-  //      delta) interleaved with the scatter by position (+ previous pixel for
-  //      P, x precision, Sec. III-A) through a ring of residuals
+  // ---- unpack, block by block (lane l: the 4 consecutive values 4l..4l+3,
+  //      a register window of the body words they occupy, funnel-shift
+  //      extraction; exceptions' high parts through the patch buffer;
+  //      inverse ZigZag, Eq. 1) into a ring of deltas, interleaved with the
+  //      scatter by position: per 256-pixel step a warp scan of the lanes'
+  //      delta sums from the running residual is the inverse delta; + the
+  //      previous pixel for P, x precision (Sec. III-A)
   if (!bad) {
     const uint32_t Pq = at.P;
     const uint32_t last_word = clen / 4u - 1u;
-    uint32_t bodyw = hdr0 + nb;  // word offset of the next block's body
     uint32_t erun = carry, blk = 0, unpacked = 0, kbase = 0;
     bool xbad = false;
     for (uint32_t it = 0; it < niter && !xbad; it++) {
       const uint32_t x0 = 256u * it + 8u * lane;
       const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
       const uint32_t mb = nv ? mbytes[x0 >> 3] : 0xffu;
+      const uint32_t nzm = ~mb & 0xffu;
       uint32_t segn;
-      uint32_t kk = kbase + warp_excl_scan(__popc(~mb & 0xffu), segn);
+      uint32_t kk = kbase + warp_excl_scan(__popc(nzm), segn);
       while (unpacked < kbase + segn) {
-        const uint32_t h = chunk[hdr0 + blk];
-        const uint32_t b = h & 0xffu, e = (h >> 8) & 0xffu, hb = (h >> 16) & 0xffu;
-        const uint32_t base = blk * kBlockN, m = min(kBlockN, n - base);
-        const uint32_t bmask = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
-        const uint32_t low_words = (m * b + 31u) >> 5;
-        const uint32_t i0 = 4u * lane;
-        uint32_t z[4] = {0u, 0u, 0u, 0u};
+        const uint2 dsc = desc[blk];
+        const uint32_t b = dsc.y & 0xffu, e = (dsc.y >> 8) & 0xffu, hb = (dsc.y >> 16) & 0xffu;
+        const uint32_t bm = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
+        const uint32_t bit0 = 4u * lane * b, sh = bit0 & 31u;
+        const uint32_t w0 = dsc.x + (bit0 >> 5);
+        uint32_t v0 = 0, v1 = 0, v2 = 0, v3 = 0;
         if (b) {
-#pragma unroll
-          for (uint32_t q = 0; q < 4; q++) {
-            const uint32_t bit = (i0 + q) * b, wi = min(bodyw + (bit >> 5), last_word);
-            const uint32_t lo = chunk[wi], hi = chunk[min(wi + 1u, last_word)];
-            z[q] = i0 + q < m ? (__funnelshift_r(lo, hi, bit & 31u) & bmask) : 0u;
+          const uint32_t W0 = chunk[min(w0, last_word)], W1 = chunk[min(w0 + 1u, last_word)],
+                         W2 = chunk[min(w0 + 2u, last_word)];
+          const uint32_t A = __funnelshift_r(W0, W1, sh), B = __funnelshift_r(W1, W2, sh);
+          if (b <= 8u) {
+            v0 = A; v1 = A >> b; v2 = A >> (2u * b); v3 = A >> (3u * b);
+          } else if (b <= 16u) {
+            const unsigned long long Y = ((unsigned long long)B << 32) | A;
+            v0 = A; v1 = __funnelshift_r(A, B, b); v2 = __funnelshift_rc(A, B, 2u * b);
+            v3 = (uint32_t)(Y >> (3u * b));
+          } else {
+            const uint32_t W3 = chunk[min(w0 + 3u, last_word)], W4 = chunk[min(w0 + 4u, last_word)];
+            const uint32_t C = __funnelshift_r(W2, W3, sh), D = __funnelshift_r(W3, W4, sh);
+            v0 = A; v1 = __funnelshift_rc(A, B, b); v2 = __funnelshift_rc(B, C, 2u * b - 32u);
+            v3 = 3u * b <= 64u ? __funnelshift_rc(B, C, 3u * b - 32u) : __funnelshift_rc(C, D, 3u * b - 64u);
           }
+          v0 &= bm; v1 &= bm; v2 &= bm; v3 &= bm;
         }
-        if (e) {
+        if (e) {  // exceptions: positions (ascending, < m), high parts of hb bits
+          const uint32_t m = dsc.y >> 24;
           reinterpret_cast<uint4*>(patch)[lane] = make_uint4(0u, 0u, 0u, 0u);
           __syncwarp();
-          const uint8_t* pos = reinterpret_cast<const uint8_t*>(chunk + bodyw + low_words);
-          const uint32_t hw = bodyw + low_words + ((e + 3u) >> 2);
+          const uint32_t lw = dsc.x + ((m * b + 31u) >> 5);
+          const uint8_t* pos = reinterpret_cast<const uint8_t*>(chunk + lw);
+          const uint32_t hw = lw + ((e + 3u) >> 2);
           const uint32_t hmask = hb >= 32u ? 0xffffffffu : ((1u << hb) - 1u);
           for (uint32_t jx = lane; jx < e; jx += 32) {
             const uint32_t ps = pos[jx];
@@ -312,22 +337,17 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
               xbad = true;
             } else {
               const uint32_t bit = jx * hb, wi = hw + (bit >> 5);
-              const uint32_t lo = chunk[wi], hi = chunk[min(wi + 1u, last_word)];
+              const uint32_t lo = chunk[min(wi, last_word)], hi = chunk[min(wi + 1u, last_word)];
               patch[ps] = (__funnelshift_r(lo, hi, bit & 31u) & hmask) << b;
             }
           }
           __syncwarp();
           const uint4 pt = reinterpret_cast<const uint4*>(patch)[lane];
-          z[0] |= pt.x; z[1] |= pt.y; z[2] |= pt.z; z[3] |= pt.w;
+          v0 |= pt.x; v1 |= pt.y; v2 |= pt.z; v3 |= pt.w;
         }
-        const uint32_t s0 = unzigzag(z[0]), s1 = s0 + unzigzag(z[1]), s2 = s1 + unzigzag(z[2]),
-                       s3 = s2 + unzigzag(z[3]);
-        uint32_t tot;
-        const uint32_t e0 = erun + warp_excl_scan(s3, tot);
-        reinterpret_cast<uint4*>(ring)[((base + i0) & (kRing - 1u)) >> 2] = make_uint4(e0 + s0, e0 + s1, e0 + s2, e0 + s3);
-        erun += tot;
-        bodyw += block_body_bytes(m, b, e, b + hb) / 4u;
-        unpacked += m;
+        reinterpret_cast<uint4*>(ring)[((128u * blk + 4u * lane) & (kRing - 1u)) >> 2] =
+            make_uint4(unzigzag(v0), unzigzag(v1), unzigzag(v2), unzigzag(v3));
+        unpacked += min(kBlockN, n - 128u * blk);
         blk++;
       }
       xbad = __any_sync(0xffffffffu, xbad);
@@ -335,14 +355,22 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
       if (xbad) break;
       uint32_t pv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       if (mode == 1u && nv) load8<true>(prow, S, x0, nv, vec_prev, pv);
-      uint32_t out[8];
+      // residuals: running sum of the deltas from the step's start
+      uint32_t d[8], lsum = 0;
 #pragma unroll
       for (int i = 0; i < 8; i++) {
-        const bool nzb = !((mb >> i) & 1u);
-        const uint32_t e = nzb ? ring[kk & (kRing - 1u)] : 0u;
-        out[i] = nzb ? e * Pq + pv[i] : 0u;
+        const bool nzb = (nzm >> i) & 1u;
+        d[i] = nzb ? ring[kk & (kRing - 1u)] : 0u;
         kk += nzb ? 1u : 0u;
+        lsum += d[i];
+        d[i] = lsum;
       }
+      uint32_t stot;
+      const uint32_t ebase = erun + warp_excl_scan(lsum, stot);
+      erun += stot;
+      uint32_t out[8];
+#pragma unroll
+      for (int i = 0; i < 8; i++) out[i] = ((nzm >> i) & 1u) ? (ebase + d[i]) * Pq + pv[i] : 0u;
       if (nv) {
         store8(orow, S, x0, nv, vec_out, out);
         if (srow) store8(srow, S, x0, nv, vec_out, out);
@@ -364,9 +392,9 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
   const uint32_t lane = lane_id();
   const DecWarpLayout lay = dec_warp_layout(p.max_W);
   uint8_t* wb = reinterpret_cast<uint8_t*>(smem) + warp_id() * lay.bytes;
-  uint32_t* stage = reinterpret_cast<uint32_t*>(wb + lay.stage);
   uint32_t* ring = reinterpret_cast<uint32_t*>(wb + lay.ring);
   uint32_t* patch = reinterpret_cast<uint32_t*>(wb + lay.patch);
+  uint2* desc = reinterpret_cast<uint2*>(wb + lay.desc);
   uint8_t* mbytes = wb + lay.mbytes;
   while (true) {
     uint32_t kb = 0;
@@ -375,7 +403,7 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
     if (kb >= p.n_items) break;
     const uint32_t kend = min(kb + p.items_per_ticket, p.n_items);
     for (uint32_t k = kb; k < kend; k++) {
-      decode_item(p, k, stage, ring, patch, mbytes);
+      decode_item(p, k, ring, patch, desc, mbytes);
     }
   }
 }
@@ -394,7 +422,7 @@ static cudaError_t dec_occupancy(size_t smem, int* per_sm) {
 
 int decode_rows_launch(const DecParams& p, RowsLaunch* out) {
   const DecWarpLayout L = dec_warp_layout(p.max_W);
-  if (L.bytes & 15u) return (int)cudaErrorInvalidValue;  // per-warp regions must stay 16-byte aligned
+  if ((L.ring | L.patch | L.desc | L.mbytes | L.bytes) & 15u) return (int)cudaErrorInvalidValue;  // 16-byte aligned regions
   uint32_t wpc = p.wpc;
   if ((wpc != 1 && wpc != 2 && wpc != 4 && wpc != 8) || wpc * L.bytes > kDecSmemMax) wpc = 0;
   if (!wpc) wpc = 4 * L.bytes <= kDecSmemAuto ? 4u : (2 * L.bytes <= kDecSmemAuto ? 2u : 1u);
