@@ -579,6 +579,14 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   const size_t o_done = c.take(4ull * items), o_tick = c.take(8);
   const size_t o_res = c.take(rs.off);
   const size_t zero_bytes = c.off - o_zero;
+  std::vector<unsigned long long> mask_base(n);
+  unsigned long long mask_words = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    const jiffy_stream* s = jobs[i].s;
+    mask_base[i] = mask_words;
+    mask_words += (unsigned long long)jobs[i].T * s->A * s->H * ((s->W + 31) / 32);
+  }
+  const size_t o_masks = c.take(4ull * mask_words);
   const size_t h_res = align_up(up.off, 256);
   jiffy_status r = ensure_scratch(ws, c.off, h_res + rs.off);
   if (r != JIFFY_OK) return r;
@@ -621,6 +629,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
     g.state_next = reinterpret_cast<uint8_t* const*>(dp + 8ull * (T + 1) * A);
     g.off = reinterpret_cast<const unsigned long long*>(dp + 8ull * (T + 2) * A);
     g.err = reinterpret_cast<uint32_t*>(d + o_res + r_err[i]);
+    g.mask_base = mask_base[i];
     segs[i] = g;
     ib[i] = item_base;
     item_base += T * A * s->H;
@@ -635,6 +644,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   p.seg = reinterpret_cast<const jiffy::DecSeg*>(d + o_up + u_seg);
   p.seg_item_base = reinterpret_cast<const uint32_t*>(d + o_up + u_ib);
   p.done = reinterpret_cast<uint32_t*>(d + o_done);
+  p.masks = reinterpret_cast<uint32_t*>(d + o_masks);
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
   uint8_t* hres = h + h_res;
 

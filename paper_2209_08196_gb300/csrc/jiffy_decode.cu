@@ -80,9 +80,19 @@ __host__ __device__ inline DecWarpLayout dec_warp_layout(uint32_t W) {
 
 // One row item, samples of S bytes (compile-time, so each warp runs one
 // compact path).
+// The frame- and section-level part of a row's parse, shared by the rows of
+// one section (a warp's consecutive items are mostly of one section).
+struct SecCache {
+  unsigned long long key;       // (1 + segment) << 32 | section in the segment; 0 = empty
+  uint32_t mode, bad;           // the section's mode; 1 = malformed frame header
+  uint32_t data_len;            // bytes of the section's row chunks
+  unsigned long long sec;       // byte offset of the section (its row table)
+};
+
 __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k, uint32_t* ring,
-                                            uint32_t* patch, uint2* desc, uint8_t* mbytes) {
-  const DecSeg& sg = p.seg[find_seg(p.seg_item_base, p.n_seg, k)];
+                                            uint32_t* patch, uint2* desc, uint8_t* mbytes, SecCache& sc) {
+  const uint32_t si = find_seg(p.seg_item_base, p.n_seg, k);
+  const DecSeg& sg = p.seg[si];
   const uint32_t lane = lane_id();
   const uint32_t H = sg.H, W = sg.W, A = sg.A, nw = sg.nw, ncls = sg.ncls;
   const uint32_t niter = ceil_div_u32(W, 256u);
@@ -90,39 +100,47 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   const uint32_t r = kl % H, ta = kl / H, a = ta % A, t = ta / A;
   const AttrDev at = sg.attrs[a];
   const uint32_t S = at.s;
-    const size_t rowb = (size_t)W * S;
+  const size_t rowb = (size_t)W * S;
 
-  // ---- frame header and row-table entry; status 1 = malformed, 2 = timed out
-  const unsigned long long f0 = sg.off[t], f1 = sg.off[t + 1];
-  bool hbad = false;
-  unsigned long long sb_before = 0, sb_total = 0;
-  uint32_t my_mode = 0, my_sb = 0;
-  for (uint32_t aa = lane; aa < A; aa += 32) {
-    const uint32_t m = ld_in_u32(sg.in, f0 + 8ull + 12ull * aa);
-    const uint32_t sb = ld_in_u32(sg.in, f0 + 12ull + 12ull * aa);
-    if ((m & 0xffffff00u) || (m & 0xffu) > 1u || sb < 8u * H || (sb & 3u)) hbad = true;
-    sb_total += sb;
-    if (aa < a) sb_before += sb;
-    if (aa == a) { my_mode = m & 0xffu; my_sb = sb; }
+  // ---- frame header (once per section); status 1 = malformed, 2 = timed out
+  const unsigned long long key = ((unsigned long long)(si + 1u) << 32) | ta;
+  if (sc.key != key) {
+    const unsigned long long f0 = sg.off[t], f1 = sg.off[t + 1];
+    bool hbad = false;
+    unsigned long long sb_before = 0, sb_total = 0;
+    uint32_t my_mode = 0, my_sb = 0;
+    for (uint32_t aa = lane; aa < A; aa += 32) {
+      const uint32_t m = ld_in_u32(sg.in, f0 + 8ull + 12ull * aa);
+      const uint32_t sb = ld_in_u32(sg.in, f0 + 12ull + 12ull * aa);
+      if ((m & 0xffffff00u) || (m & 0xffu) > 1u || sb < 8u * H || (sb & 3u)) hbad = true;
+      sb_total += sb;
+      if (aa < a) sb_before += sb;
+      if (aa == a) { my_mode = m & 0xffu; my_sb = sb; }
+    }
+    hbad = __any_sync(0xffffffffu, hbad);
+    for (int o = 16; o > 0; o >>= 1) {
+      sb_total += __shfl_xor_sync(0xffffffffu, sb_total, o);
+      sb_before += __shfl_xor_sync(0xffffffffu, sb_before, o);
+    }
+    sc.mode = __shfl_sync(0xffffffffu, my_mode, a & 31u);
+    my_sb = __shfl_sync(0xffffffffu, my_sb, a & 31u);
+    const uint32_t frame_bytes = ld_in_u32(sg.in, f0);
+    const uint32_t scan = ld_in_u32(sg.in, f0 + 4);
+    if (frame_bytes != f1 - f0 || scan != sg.frame0 + t || sb_total + sg.fhdr != frame_bytes) hbad = true;
+    if (sc.mode == 1u && sg.frame0 + t == 0) hbad = true;
+    sc.bad = hbad ? 1u : 0u;
+    sc.sec = f0 + sg.fhdr + sb_before;
+    sc.data_len = my_sb - 8u * H;
+    sc.key = key;
   }
-  hbad = __any_sync(0xffffffffu, hbad);
-  for (int o = 16; o > 0; o >>= 1) {
-    sb_total += __shfl_xor_sync(0xffffffffu, sb_total, o);
-    sb_before += __shfl_xor_sync(0xffffffffu, sb_before, o);
-  }
-  const uint32_t mode = __shfl_sync(0xffffffffu, my_mode, a & 31u);
-  my_sb = __shfl_sync(0xffffffffu, my_sb, a & 31u);
+  const uint32_t mode = sc.mode;
   uint32_t status = 0, clen = 0, carry = 0;
   unsigned long long chunk_off = 0;
   if (lane == 0) {
-    bool bad = hbad;
-    const uint32_t frame_bytes = ld_in_u32(sg.in, f0);
-    const uint32_t scan = ld_in_u32(sg.in, f0 + 4);
-    if (frame_bytes != f1 - f0 || scan != sg.frame0 + t || sb_total + sg.fhdr != frame_bytes) bad = true;
-    if (mode == 1u && sg.frame0 + t == 0) bad = true;
-    if (!bad) {
-      const unsigned long long sec = f0 + sg.fhdr + sb_before;
-      const uint32_t data_len = my_sb - 8u * H;
+    bool bad = sc.bad != 0;
+    if (!bad) {  // the row-table entry
+      const unsigned long long sec = sc.sec;
+      const uint32_t data_len = sc.data_len;
       const uint32_t end = ld_in_u32(sg.in, sec + 8ull * r);
       carry = ld_in_u32(sg.in, sec + 8ull * r + 4);
       const uint32_t start = r ? ld_in_u32(sg.in, sec + 8ull * (r - 1)) : 0u;
@@ -209,11 +227,23 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   uint8_t* srow = (t + 1 == sg.T) ? sg.state_next[a] + r * rowb : nullptr;
   const uint8_t* prow = mode == 1u ? (t > 0 ? sg.outp[(t - 1) * A + a] : sg.state[a]) + r * rowb : nullptr;
   const bool vec_prev = prow && vec_ok(prow, S);
+  if (!bad && prow && lane == 0) {  // the previous scan's row, for the P sums of the scatter
+    const uintptr_t c0 = reinterpret_cast<uintptr_t>(prow), c1 = c0 + rowb;
+    const uintptr_t a0 = (c0 + 15u) & ~uintptr_t(15), a1 = c1 & ~uintptr_t(15);
+    if (a1 > a0)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0)) : "memory");
+  }
   const bool vec_out = vec_ok(orow, S) && (!srow || vec_ok(srow, S));
 
-  // ---- pass 1: own mask bytes (1 = zero sample) and nonzero counts
+  // ---- pass 1: own mask bytes (1 = zero sample) and nonzero counts. For P
+  //      (Sec. III-D) the previous scan's mask comes from the mask words the
+  //      previous frame's row wrote in this call, else from its samples.
   uint32_t cnt = 0;
   if (!bad) {
+    const uint8_t* pmask = (mode == 1u && t > 0)
+                               ? reinterpret_cast<const uint8_t*>(p.masks + sg.mask_base + (size_t)(kl - A * H) * nw)
+                               : nullptr;
+    uint8_t* omask = t + 1 < sg.T ? reinterpret_cast<uint8_t*>(p.masks + sg.mask_base + (size_t)kl * nw) : nullptr;
     for (uint32_t it = 0; it < niter; it++) {
       const uint32_t x0 = 256u * it + 8u * lane;
       const uint32_t j = x0 >> 5;
@@ -226,15 +256,19 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
         else if (cls == 2u) X = chunk[ncls + lpj + __popc(literal_bits(cwj) & ((1u << sl) - 1u))];
         const uint32_t nv = min(8u, W - x0), vm = (1u << nv) - 1u;
         uint32_t mb = (X >> (x0 & 31u)) & 0xffu;
-        if (mode == 1u) {
+        if (pmask) {
+          mb ^= __ldcg(pmask + (x0 >> 3));  // Sec. III-D: undo the XOR with the previous scan's mask
+        } else if (mode == 1u) {
           uint32_t pv[8];
           load8<true>(prow, S, x0, nv, vec_prev, pv);
           uint32_t pm = 0;
 #pragma unroll
           for (int i = 0; i < 8; i++) pm |= (uint32_t)(pv[i] == 0u) << i;
-          mb ^= pm;  // Sec. III-D: undo the XOR with the previous scan's mask
+          mb ^= pm;
         }
-        mb = (mb & vm) | (0xffu & ~vm);  // pixels past W count as zero samples
+        mb &= vm;
+        if (omask) omask[x0 >> 3] = (uint8_t)mb;
+        mb |= 0xffu & ~vm;  // pixels past W count as zero samples
         mbytes[x0 >> 3] = (uint8_t)mb;
         cnt += __popc(~mb & 0xffu);
       }
@@ -396,6 +430,7 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
   uint32_t* patch = reinterpret_cast<uint32_t*>(wb + lay.patch);
   uint2* desc = reinterpret_cast<uint2*>(wb + lay.desc);
   uint8_t* mbytes = wb + lay.mbytes;
+  SecCache sc{0ull, 0u, 0u, 0u, 0ull};
   while (true) {
     uint32_t kb = 0;
     if (lane == 0) kb = atomicAdd(p.ticket, p.items_per_ticket);
@@ -403,7 +438,7 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
     if (kb >= p.n_items) break;
     const uint32_t kend = min(kb + p.items_per_ticket, p.n_items);
     for (uint32_t k = kb; k < kend; k++) {
-      decode_item(p, k, ring, patch, desc, mbytes);
+      decode_item(p, k, ring, patch, desc, mbytes, sc);
     }
   }
 }

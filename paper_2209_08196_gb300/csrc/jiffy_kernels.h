@@ -74,6 +74,7 @@ struct DecSeg {
   const uint8_t* const* state;   // [A] previous decoded planes (for the segment's first frame)
   uint8_t* const* state_next;    // [A] receives the last frame's planes
   uint32_t* err;                 // the segment's error word
+  unsigned long long mask_base;  // word offset of the segment's first row in DecParams::masks
 };
 
 struct DecParams {
@@ -83,6 +84,7 @@ struct DecParams {
   const DecSeg* seg;             // [n_seg]
   const uint32_t* seg_item_base; // [n_seg]
   uint32_t* done;                // [n_items] row-done flags
+  uint32_t* masks;               // decoded zero masks, nw words per row item (read by the next frame's P rows)
   uint32_t* ticket;
   uint32_t wpc;                  // warps per CTA (1, 2, 4, 8; 0 = by shared memory)
   uint32_t ctas_per_sm;          // resident CTAs per SM (0 = occupancy limit)
