@@ -58,6 +58,14 @@ __device__ __forceinline__ uint32_t find_seg(const uint32_t* base, uint32_t n, u
   return lo;
 }
 
+// Row items of a segment are numbered attribute-major, (a, t, r): the rows a
+// warp takes next are of the attribute it just coded, so resident warps run
+// the same code (the kernel is large; mixing attributes thrashes instruction
+// fetch), and a section's rows stay consecutive for the carry look-back.
+__device__ __forceinline__ uint32_t enc_item(const EncSeg& sg, uint32_t t, uint32_t a, uint32_t r) {
+  return (a * sg.T + t) * sg.H + r;
+}
+
 __device__ __forceinline__ uint32_t mask_class(uint32_t c, uint32_t valid) {
   return c == 0u ? 0u : (c == valid ? 1u : 2u);
 }
@@ -593,8 +601,9 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   const EncSeg& sg = p.seg[find_seg(p.seg_item_base, p.n_seg, k)];
   const uint32_t lane = lane_id();
   const uint32_t H = sg.H, W = sg.W, A = sg.A, nw = sg.nw, ncls = sg.ncls;
-  const uint32_t kl = k - sg.item_base;  // item within the segment
-  const uint32_t r = kl % H, ta = kl / H, a = ta % A, t = ta / A;
+  const uint32_t kl = k - sg.item_base;  // item within the segment, attribute-major (enc_item)
+  const uint32_t r = kl % H, at_idx = kl / H, a = at_idx / sg.T, t = at_idx % sg.T;
+  const uint32_t ta = t * A + a;     // section (scan t, attribute a)
   const uint32_t sec = sg.sec_base + ta;
   const uint32_t sec_start = k - r;  // global item of row 0 of this attribute-scan
   const AttrDev at = sg.attrs[a];
@@ -783,8 +792,8 @@ __global__ void __launch_bounds__(kThreads) k_sec_sizes(EncParams p) {
   __shared__ unsigned long long s_red[kWarps];
   const uint32_t gs = blockIdx.x;
   const EncSeg& sg = p.seg[find_seg(p.seg_sec_base, p.n_seg, gs)];
-  const uint32_t H = sg.H;
-  const uint32_t item0 = sg.item_base + (gs - sg.sec_base) * H;
+  const uint32_t H = sg.H, ta = gs - sg.sec_base;
+  const uint32_t item0 = sg.item_base + enc_item(sg, ta / sg.A, ta % sg.A, 0);
   unsigned long long bytes = 0, nnz = 0;
   for (uint32_t r = threadIdx.x; r < H; r += kThreads) {
     bytes += p.row_bytes[item0 + r];
@@ -806,7 +815,8 @@ __global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
   const EncSeg& sg = p.seg[find_seg(p.seg_sec_base, p.n_seg, gs)];
   const uint32_t H = sg.H, A = sg.A;
   const uint32_t ta = gs - sg.sec_base, t = ta / A, a = ta % A;
-  const uint32_t item0 = sg.item_base + ta * H;
+  const uint32_t local0 = enc_item(sg, t, a, 0);
+  const uint32_t item0 = sg.item_base + local0;
   uint8_t* out = sg.out;
   const unsigned long long cap = sg.cap;
   // bytes of the segment's earlier sections: of earlier frames (frame_before)
@@ -840,7 +850,7 @@ __global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
       continue;
     }
     const uint32_t* src =
-        reinterpret_cast<const uint32_t*>(p.slots + sg.slot_base + (size_t)(ta * H + r) * sg.slot_bytes);
+        reinterpret_cast<const uint32_t*>(p.slots + sg.slot_base + (size_t)(local0 + r) * sg.slot_bytes);
     uint32_t* dst = reinterpret_cast<uint32_t*>(out + at);
     for (uint32_t i = lane; i < words; i += 128u) {
       uint32_t v[4];

@@ -4,8 +4,9 @@
 // A call codes one or more segments: a segment is one stream's part of the
 // call (T consecutive scans of one stream). Row items (scan t, attribute a,
 // row r) and sections (scan t, attribute a) are numbered globally across the
-// segments of a call, segment after segment; each segment's items are
-// ordered (t, a, r).
+// segments of a call, segment after segment. Within a segment, sections are
+// ordered (t, a); the encoder's row items are ordered (a, t, r) (attribute-
+// major) and the decoder's (t, a, r).
 #pragma once
 
 #include <cstdint>

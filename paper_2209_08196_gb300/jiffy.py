@@ -145,6 +145,7 @@ class Handle:
 
     def __init__(self, ptr, role, H, W, attrs, device):
         self.ptr, self.role, self.H, self.W, self.attrs, self.device = ptr, role, H, W, list(attrs), device
+        self._ptr_cache = {}  # (T, attribute base addresses) -> ctypes pointer array
 
     @property
     def A(self):
@@ -245,9 +246,16 @@ def _seq_ptrs(h: Handle, planes, what: str):
                                  % (what, a, T, h.H, h.W, s, tuple(p.shape), p.dtype))
             bases.append(p.data_ptr())
             steps.append(h.H * h.W * s)
-        A = h.A
-        ptrs = [bases[a] + t * steps[a] for t in range(T) for a in range(A)]
-        return T, (ctypes.c_void_p * len(ptrs))(*ptrs)
+        key = (T, tuple(bases))
+        arr = h._ptr_cache.get(key)
+        if arr is None:
+            A = h.A
+            ptrs = [bases[a] + t * steps[a] for t in range(T) for a in range(A)]
+            arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+            if len(h._ptr_cache) >= 8:
+                h._ptr_cache.clear()
+            h._ptr_cache[key] = arr
+        return T, arr
     T, flat = _seq_planes(h, planes)
     for i, p in enumerate(flat):
         _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "%s %d" % (what, i))
