@@ -362,30 +362,30 @@ __device__ __forceinline__ uint32_t pass_b1(uint32_t* zb, uint32_t n, uint32_t c
 
 // ---------------------------------------------------------------------------
 // Packs 128 values of b bits, value i at bit i b (Sec. II, a block's low-bit
-// stream), into words [0, nwords) of dst. Lane l holds values 4l .. 4l+3,
-// bits [4lb, 4lb + 4b) of the stream; each word is written once, by the lane
-// holding its first bit: the lane joins its values with funnel shifts and
-// completes the word with the following lanes' bits (one shuffle for b > 8;
-// for b <= 8, where a word spans several lanes, log-step shuffles double the
-// joined run). Bits of the values above b are dropped.
+// stream), into words [0, nwords) of dst, which must be zero. Lane l holds
+// values 4l .. 4l+3, bits [4lb, 4lb + 4b) of the stream, joined in registers
+// with funnel shifts. For b <= 8 (a word spans up to 8 lanes) the lanes OR
+// their 4b bits into the (at most 2) words they touch; for b > 8 each word is
+// written once, by the lane holding its first bit, completed with the next
+// lane's bits (one shuffle). Bits of the values above b are dropped.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void pack4(uint32_t* dst, uint32_t b, uint32_t nwords, uint32_t z0, uint32_t z1,
                                       uint32_t z2, uint32_t z3) {
   const uint32_t lane = lane_id();
   const uint32_t S = 4u * lane * b;           // the lane's first bit
-  const uint32_t o = (32u - (S & 31u)) & 31u;  // its first word start, relative to S
-  const uint32_t w = (S + o) >> 5;            // that word
   if (b == 0) return;
   if (b <= 8u) {
     const uint32_t bm = (1u << b) - 1u;
-    unsigned long long y = (z0 & bm) | ((z1 & bm) << b) | ((z2 & bm) << (2u * b)) | ((z3 & bm) << (3u * b));
-    for (uint32_t d = 1, len = 4u * b; len < 64u; d <<= 1, len <<= 1) {
-      unsigned long long t = __shfl_down_sync(0xffffffffu, y, d);
-      if (lane + d > 31u) t = 0ull;
-      y |= t << len;
-    }
-    if (o < 4u * b && w < nwords) dst[w] = (uint32_t)(y >> o);
-  } else if (b <= 16u) {
+    const uint32_t x = (z0 & bm) | ((z1 & bm) << b) | ((z2 & bm) << (2u * b)) | ((z3 & bm) << (3u * b));
+    const uint32_t sh = S & 31u, w = S >> 5;
+    const uint32_t y0 = x << sh, y1 = __funnelshift_l(x, 0u, sh);
+    if (y0) atomicOr(dst + w, y0);
+    if (y1) atomicOr(dst + w + 1u, y1);
+    return;
+  }
+  const uint32_t o = (32u - (S & 31u)) & 31u;  // the lane's first word start, relative to S
+  const uint32_t w = (S + o) >> 5;            // that word
+  if (b <= 16u) {
     const uint32_t bm = (1u << b) - 1u;
     const unsigned long long x = (unsigned long long)(z0 & bm) | ((unsigned long long)(z1 & bm) << b) |
                                  ((unsigned long long)(z2 & bm) << (2u * b)) |
@@ -429,42 +429,47 @@ __device__ __forceinline__ void pack4(uint32_t* dst, uint32_t b, uint32_t nwords
 // 128 (g + 1), so it never reaches a value still to be read): the low b
 // bits of all values, then the exceptions (values wider than b) as e
 // position bytes in ascending order and their high parts of hb bits (Sec. II,
-// PFOR). The exceptions are first listed in order in xpos / xhv (128
-// entries), then packed like the low bits.
+// PFOR). The body is zeroed first. The exceptions are listed in order in
+// xpos / xhv (a warp scan of the lanes' counts gives the ranks); lane x then
+// ORs the high part of exception x into place and lane l writes position
+// bytes 4l .. 4l+3 as one word.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void pass_b2(uint32_t* zb, uint32_t n, uint32_t nb, const uint2* meta, uint8_t* xpos,
                                         uint32_t* xhv) {
-  const uint32_t lane = lane_id(), below = (1u << lane) - 1u;
+  const uint32_t lane = lane_id();
   for (uint32_t g = 0; g < nb; g++) {
     const uint2 md = meta[g];  // .x header, .y body byte offset
     const uint32_t b = md.x & 0xffu, e = (md.x >> 8) & 0xffu, hb = (md.x >> 16) & 0xffu;
     const uint32_t m = min(128u, n - 128u * g);
     uint32_t* body = zb + (md.y >> 2);
     const uint32_t low_words = (m * b + 31u) >> 5;
+    const uint32_t pw = (e + 3u) >> 2, size_words = low_words + (e ? pw + ((e * hb + 31u) >> 5) : 0u);
     const uint32_t sgi = 4u * g + (lane >> 3);
     const uint4 zz = reinterpret_cast<const uint4*>(zb + 32u * sgi)[(lane & 7u) ^ (sgi & 7u)];
     const uint32_t z0 = zz.x, z1 = zz.y, z2 = zz.z, z3 = zz.w;  // 0 past m
+    __syncwarp();
+    for (uint32_t i = lane; i < size_words; i += 32u) body[i] = 0u;
     __syncwarp();
     pack4(body, b, low_words, z0, z1, z2, z3);
     if (e) {  // e > 0 implies b < 32
       const uint32_t xm = ((z0 >> b) != 0u ? 1u : 0u) | ((z1 >> b) != 0u ? 2u : 0u) |
                           ((z2 >> b) != 0u ? 4u : 0u) | ((z3 >> b) != 0u ? 8u : 0u);
-      uint32_t rank = 0;
-#pragma unroll
-      for (uint32_t q = 0; q < 4; q++) rank += __popc(__ballot_sync(0xffffffffu, (xm >> q) & 1u) & below);
+      uint32_t unused;
+      uint32_t rank = warp_excl_scan(__popc(xm), unused);
       if (xm & 1u) { xpos[rank] = (uint8_t)(4u * lane); xhv[rank] = z0 >> b; rank++; }
       if (xm & 2u) { xpos[rank] = (uint8_t)(4u * lane + 1u); xhv[rank] = z1 >> b; rank++; }
       if (xm & 4u) { xpos[rank] = (uint8_t)(4u * lane + 2u); xhv[rank] = z2 >> b; rank++; }
       if (xm & 8u) { xpos[rank] = (uint8_t)(4u * lane + 3u); xhv[rank] = z3 >> b; }
       __syncwarp();
-      const uint32_t pw = (e + 3u) >> 2;
       uint32_t pword = reinterpret_cast<const uint32_t*>(xpos)[lane];
       if (4u * lane + 4u > e) pword &= 4u * lane >= e ? 0u : ((1u << (8u * (e - 4u * lane))) - 1u);
       if (lane < pw) body[low_words + lane] = pword;
-      const uint4 hv = reinterpret_cast<const uint4*>(xhv)[lane];
-      const uint32_t i0 = 4u * lane;
-      pack4(body + low_words + pw, hb, (e * hb + 31u) >> 5, i0 < e ? hv.x : 0u, i0 + 1u < e ? hv.y : 0u,
-            i0 + 2u < e ? hv.z : 0u, i0 + 3u < e ? hv.w : 0u);
+      uint32_t* hp = body + low_words + pw;
+      for (uint32_t x = lane; x < e; x += 32u) {
+        const uint32_t hv = xhv[x], hbit = x * hb, hs = hbit & 31u;
+        atomicOr(hp + (hbit >> 5), hv << hs);
+        if (hs + hb > 32u) atomicOr(hp + (hbit >> 5) + 1u, hv >> (32u - hs));
+      }
     }
     __syncwarp();
   }
