@@ -233,7 +233,9 @@ def batched_leg(J, torch, dev, local, steps, warmup, n_streams=256, n_scans=8, b
         seq = synth.ScanSequence(c, device=dev)
         sc = [seq.scan(t, as_numpy=False) for t in range(n_scans)]
         at = synth.attr_descs(c)
-        scans.append(sc)
+        # one T x H x W tensor per attribute (the binding addresses planes by arithmetic)
+        stk = [torch.stack([sc[t][a] for t in range(n_scans)]) for a in range(len(at))]
+        scans.append(stk)
         attrs_l.append(at)
         encs.append(J.jiffy_stream_create(J.JIFFY_ENCODER, c.H, c.W, at, device=local))
         decs.append(J.jiffy_stream_create(J.JIFFY_DECODER, c.H, c.W, at, device=local))
@@ -242,7 +244,7 @@ def batched_leg(J, torch, dev, local, steps, warmup, n_streams=256, n_scans=8, b
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     px = sum(c.H * c.W * n_scans for c in cfgs)
-    raw = sum(p.numel() * p.element_size() for sc in scans for s in sc for p in s)
+    raw = sum(p.numel() * p.element_size() for stk in scans for p in stk)
     b = J.jiffy_batch_create(local)
     J.jiffy_batch_set_graphs(b, True)
     J.jiffy_batch_set_autotune(b, True)
@@ -262,7 +264,7 @@ def batched_leg(J, torch, dev, local, steps, warmup, n_streams=256, n_scans=8, b
     for c, sc, pl, at in zip(cfgs, scans, planes, attrs_l):
         for a, (sz, P) in enumerate(at):
             m = (1 << (8 * sz)) - 1
-            v = torch.stack([sc[t][a] for t in range(n_scans)]).to(torch.int64) & m
+            v = sc[a].to(torch.int64) & m
             q = torch.clamp((v + P // 2) // P, max=m // P)
             if not torch.equal(pl[a].to(torch.int64) & m, q * P):
                 raise SystemExit("batched round trip mismatch")
@@ -294,7 +296,7 @@ def batched_leg(J, torch, dev, local, steps, warmup, n_streams=256, n_scans=8, b
         for i, (c, sc) in enumerate(zip(cfgs, scans)):
             pos = 0
             for t in range(n_scans):
-                n = J.jiffy_encode(encs[i], sc[t], outs[i][pos:], stream)
+                n = J.jiffy_encode(encs[i], [p[t] for p in sc], outs[i][pos:], stream)
                 frames.append((i, pos, n))
                 pos += (n + 15) // 16 * 16
         for i, pos, n in frames:

@@ -412,16 +412,11 @@ class _EncCall:
 
     def __init__(self, handles, planes, outs):
         n = len(handles)
-        flats = []
-        for h, pl in zip(handles, planes):
-            T, flat = _seq_planes(h, pl)
-            for i, p in enumerate(flat):
-                _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "plane %d" % i)
-            flats.append((T, flat))
+        flats = [_seq_ptrs(h, pl, "plane") for h, pl in zip(handles, planes)]
         self.n = n
         self.streams = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
         self.n_scans = (ctypes.c_uint32 * n)(*[T for T, _ in flats])
-        self.parr = [_ptr_array(flat) for _, flat in flats]
+        self.parr = [arr for _, arr in flats]
         self.planes = (ctypes.c_void_p * n)(*[_addr(a) for a in self.parr])
         self.outs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
         self.caps = (ctypes.c_size_t * n)(*[o.numel() * o.element_size() for o in outs])
@@ -441,14 +436,10 @@ class _EncCall:
 class _DecCall:
     def __init__(self, handles, bufs, lengths, offsets, planes_out):
         n = len(handles)
-        flats = []
-        for h, pl, o in zip(handles, planes_out, offsets):
-            T, flat = _seq_planes(h, pl)
+        flats = [_seq_ptrs(h, pl, "output plane") for h, pl in zip(handles, planes_out)]
+        for (T, _), o in zip(flats, offsets):
             if len(o) != T + 1:
                 raise ValueError("need T + 1 frame offsets")
-            for i, p in enumerate(flat):
-                _check_plane(p, h.H, h.W, h.attrs[i % h.A][0], "output plane %d" % i)
-            flats.append((T, flat))
         self.n = n
         self.streams = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
         self.n_frames = (ctypes.c_uint32 * n)(*[T for T, _ in flats])
@@ -456,7 +447,7 @@ class _DecCall:
         self.lens = (ctypes.c_size_t * n)(*[int(x) for x in lengths])
         self.offs = [(ctypes.c_uint64 * len(o))(*[int(v) for v in o]) for o in offsets]
         self.offs_pp = (ctypes.c_void_p * n)(*[_addr(a) for a in self.offs])
-        self.parr = [_ptr_array(flat) for _, flat in flats]
+        self.parr = [arr for _, arr in flats]
         self.planes = (ctypes.c_void_p * n)(*[_addr(a) for a in self.parr])
         self.sts = (ctypes.c_int * n)()
 
