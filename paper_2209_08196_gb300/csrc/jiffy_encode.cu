@@ -339,15 +339,21 @@ __device__ __forceinline__ uint32_t pass_b1(uint32_t* zb, uint32_t n, uint32_t c
       lo4 = F[0] + 2u * F[1] + 4u * F[2] + 8u * F[3];
       hi4 = F[4] + 2u * F[5] + 4u * F[6] + 8u * F[7];
     }
-    const uint32_t wtop = __reduce_max_sync(0xffffffffu, m ? wmax : 0u);
+    // candidates in increasing b; the low-bit words alone, 4 ceil(mb/32),
+    // bound a candidate's bytes from below, so once that bound reaches the
+    // lane's best so far no larger b can win (ties go to the smaller b)
     uint32_t key = 0xffffffffu;
 #pragma unroll
     for (uint32_t i = 0; i < 9; i++) {
-      if (4u * i > wtop) break;
       const uint32_t b = j + 4u * i;
-      const uint32_t e = i < 8 ? ((lo4 >> (4 * i)) & 15u) | (((hi4 >> (4 * i)) & 15u) << 4) : 0u;
-      const uint32_t f = 4u * ((m * b + 31u) >> 5) + ((e + 3u) & ~3u) + 4u * ((e * (wmax - b) + 31u) >> 5);
-      if (b <= wmax) key = min(key, (f << 14) | (b << 8) | e);
+      const uint32_t low = 4u * ((m * b + 31u) >> 5);
+      const bool live = m != 0u && b <= wmax && low < (key >> 14);
+      if (!__any_sync(0xffffffffu, live)) break;
+      if (live) {
+        const uint32_t e = i < 8 ? ((lo4 >> (4 * i)) & 15u) | (((hi4 >> (4 * i)) & 15u) << 4) : 0u;
+        const uint32_t f = low + ((e + 3u) & ~3u) + 4u * ((e * (wmax - b) + 31u) >> 5);
+        key = min(key, (f << 14) | (b << 8) | e);
+      }
     }
     key = min(key, __shfl_xor_sync(0xffffffffu, key, 1));
     key = min(key, __shfl_xor_sync(0xffffffffu, key, 2));
@@ -812,11 +818,13 @@ __global__ void __launch_bounds__(kThreads) k_sec_sizes(EncParams p) {
   }
 }
 
+constexpr uint32_t kPlaceSplit = 4;  // CTAs per section in k_place (rows dealt round robin)
+
 __global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
   extern __shared__ __align__(16) uint32_t smem[];  // [H] row chunk starts
   __shared__ unsigned long long s_red[kWarps];
   __shared__ uint32_t s_tmp[kWarps + 1];
-  const uint32_t gs = blockIdx.x;
+  const uint32_t gs = blockIdx.x / kPlaceSplit, part = blockIdx.x % kPlaceSplit;
   const EncSeg& sg = p.seg[find_seg(p.seg_sec_base, p.n_seg, gs)];
   const uint32_t H = sg.H, A = sg.A;
   const uint32_t ta = gs - sg.sec_base, t = ta / A, a = ta % A;
@@ -839,15 +847,17 @@ __global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
   for (uint32_t r = threadIdx.x; r < H; r += kThreads) smem[r] = p.row_bytes[item0 + r];
   __syncthreads();
   const uint32_t data = block_excl_scan(smem, H, s_tmp);  // smem = row starts
-  for (uint32_t r = threadIdx.x; r < H; r += kThreads) {
-    const uint32_t end = (r + 1 < H) ? smem[r + 1] : data;
-    put_u32_guarded(out, cap, sec_at + 8ull * r, end, sg.err);
-    put_u32_guarded(out, cap, sec_at + 8ull * r + 4, p.row_carry[item0 + r], sg.err);
+  if (part == 0) {
+    for (uint32_t r = threadIdx.x; r < H; r += kThreads) {
+      const uint32_t end = (r + 1 < H) ? smem[r + 1] : data;
+      put_u32_guarded(out, cap, sec_at + 8ull * r, end, sg.err);
+      put_u32_guarded(out, cap, sec_at + 8ull * r + 4, p.row_carry[item0 + r], sg.err);
+    }
   }
   // row chunks: a warp per row, slot -> stream, 4 words in flight per lane
   const unsigned long long data_at = sec_at + 8ull * H;
   const uint32_t lane = lane_id();
-  for (uint32_t r = warp_id(); r < H; r += kWarps) {
+  for (uint32_t r = part * kWarps + warp_id(); r < H; r += kWarps * kPlaceSplit) {
     const uint32_t words = p.row_bytes[item0 + r] / 4u;
     const unsigned long long at = data_at + smem[r];
     if (at + 4ull * words > cap) {
@@ -866,7 +876,7 @@ __global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
         if (i + 32u * q < words) dst[i + 32u * q] = v[q];
     }
   }
-  if (a == 0 && threadIdx.x == 0) {
+  if (part == 0 && a == 0 && threadIdx.x == 0) {
     const uint32_t f0 = sg.sec_base + t * A;
     unsigned long long fbytes = sg.fhdr;
     for (uint32_t aa = 0; aa < A; aa++) fbytes += p.sec_bytes[f0 + aa];
@@ -956,7 +966,7 @@ int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   else k_encode<1><<<rl.grid, 32, smem, st>>>(p);
   mark(2);
   k_sec_sizes<<<p.n_sec, kThreads, 0, st>>>(p);
-  k_place<<<p.n_sec, kThreads, s_place, st>>>(p);
+  k_place<<<p.n_sec * kPlaceSplit, kThreads, s_place, st>>>(p);
   mark(3);
   return (int)cudaGetLastError();
 }
