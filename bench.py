@@ -363,6 +363,23 @@ def serve_leg(J, torch, dev, local, seconds, sat_seconds, n_sensors=512, base_se
             "saturated": sat, "gen_s": t_gen}
 
 
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The slowest rank's time: replicas run independently (no collective on
+    the data path); only this reduction joins them."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gpoints(px_per_rank: int, world: int, ms: float) -> float:
+    """All ranks' pixels over the slowest rank's time, in Gpoints/s."""
+    return px_per_rank * world / (ms / 1e3) / 1e9
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -453,14 +470,10 @@ def main():
     ev1.record(stream)
     barrier()
     clocks = clk.stop()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     ms_step = ms / args.steps
     px_step = T * H * W
-    value = px_step * world / (ms_step / 1e3) / 1e9
+    value = whole_job_gpoints(px_step, world, ms_step)
     n = state["n"]
 
     # e2e through host buffers, every step: H2D of the scans, encode, D2H of
@@ -531,11 +544,7 @@ def main():
         nn = e2e_run(args.steps)
         e1.record(stream)
         barrier()
-        e2e_ms = e0.elapsed_time(e1) / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
         # the pipelined run decoded every step: check the last one bit-exactly
         for a, (s_, P) in enumerate(attrs):
             m = (1 << (8 * s_)) - 1
@@ -543,7 +552,7 @@ def main():
             if not torch.equal(dev_out[(args.steps - 1) % 2][a].to(torch.int64) & m, q * P):
                 raise SystemExit("e2e round trip mismatch on attribute %d" % a)
             del q
-        e2e = {"value": px_step * world / (e2e_ms / 1e3) / 1e9, "unit": UNIT,
+        e2e = {"value": whole_job_gpoints(px_step, world, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": raw_bytes + nn, "d2h_bytes_per_step": nn + raw_bytes,
                "pipelined": "upload of step i+1 and download of step i-1 overlap the calls of step i"}
 
