@@ -75,9 +75,12 @@ typedef struct {
 } jiffy_attr_desc;
 
 /* test_lines: number of scanlines of the trial compression (Sec. III-E;
- * Sec. IV-E uses 4); rows floor((2k+1)H/(2L)), k < L. force_mode: -1 picks I
- * or P per attribute and scan by trial, 0 forces I, 1 forces P (the first
- * frame after create/reset is always I). */
+ * Sec. IV-E uses 4); rows floor((2k+1)H/(2L)), k < L, >= 1. test_lines >= H
+ * makes every row a test row: the brute-force choice between I and P over
+ * the data sections (mask excluded), at about the cost of coding each scan
+ * a second time. force_mode: -1 picks I or P per attribute and scan by
+ * trial, 0 forces I, 1 forces P (the first frame after create/reset is
+ * always I). */
 typedef struct {
   uint32_t test_lines;
   int32_t force_mode;

@@ -206,16 +206,9 @@ uint32_t stream_header_bytes(uint32_t A) { return 16u + 8u * A; }
 uint32_t frame_header_bytes(uint32_t A) { return 8u + 12u * A; }
 uint32_t slot_bytes_for(uint32_t W) { return (jiffy::row_bound_bytes(W) + 15u) & ~15u; }
 
-// Number of distinct test rows floor((2k+1)H/(2L)), k < L (Sec. III-E).
-uint32_t distinct_test_rows(uint32_t H, uint32_t L) {
-  uint32_t n = 0, last = 0;
-  for (uint32_t k = 0; k < L; k++) {
-    const uint32_t r = (uint32_t)(((uint64_t)(2 * k + 1) * H) / (2ull * L));
-    if (n == 0 || r != last) n++;
-    last = r;
-  }
-  return n;
-}
+// Number of distinct test rows floor((2k+1)H/(2L)), k < L (Sec. III-E): the
+// rows are distinct while L <= H, and cover every row once L >= H.
+uint32_t distinct_test_rows(uint32_t H, uint32_t L) { return L < H ? L : H; }
 
 jiffy_status check_distinct(const std::vector<jiffy_stream*>& ss) {
   for (size_t i = 0; i < ss.size(); i++)
@@ -799,7 +792,7 @@ jiffy_status jiffy_stream_create(jiffy_stream** out, jiffy_role role, uint32_t H
     return JIFFY_ERR_INVALID_ARG;
   jiffy_options o{4, -1};
   if (opt) o = *opt;
-  if (o.test_lines == 0 || o.test_lines > jiffy::kMaxTestLines || o.force_mode < -1 || o.force_mode > 1)
+  if (o.test_lines == 0 || o.force_mode < -1 || o.force_mode > 1)
     return JIFFY_ERR_INVALID_ARG;
   for (uint32_t a = 0; a < n_attr; a++) {
     const uint32_t sz = attrs[a].dtype_bytes;

@@ -497,15 +497,14 @@ __global__ void __launch_bounds__(32) k_trial(EncParams p) {
   const uint32_t ta = gs - sg.sec_base;
   const uint32_t t = ta / sg.A, a = ta % sg.A;
   if (sg.frame0 + t == 0 || sg.force_mode >= 0) return;
-  // the distinct test rows, ascending
+  // the distinct test rows, ascending: floor((2k+1)H/(2L)) are distinct for
+  // L <= H, and for L >= H they are every row (brute force over the data)
   const uint32_t L = sg.test_lines, H = sg.H;
-  uint32_t rows[kMaxTestLines];
-  uint32_t nr = 0;
-  for (uint32_t k = 0; k < L; k++) {
-    const uint32_t r = (uint32_t)(((unsigned long long)(2 * k + 1) * H) / (2ull * L));
-    if (nr == 0 || rows[nr - 1] != r) rows[nr++] = r;
-  }
+  const uint32_t nr = min(L, H);
   if (ti >= nr) return;
+  auto test_row = [&](uint32_t k) -> uint32_t {
+    return L >= H ? k : (uint32_t)(((unsigned long long)(2 * k + 1) * H) / (2ull * L));
+  };
   const AttrDev at = sg.attrs[a];
   const uint32_t W = sg.W;
   const size_t rowb = (size_t)W * at.s;
@@ -516,16 +515,16 @@ __global__ void __launch_bounds__(32) k_trial(EncParams p) {
   // carry: the last residual of the nearest earlier test row that has one
   uint32_t ci = 0, cp = 0;
   for (int k = (int)ti - 1; k >= 0; k--) {
-    const uint8_t* c0 = cur + rows[k] * rowb;
-    const uint8_t* p0 = prv + rows[k] * rowb;
+    const uint8_t* c0 = cur + test_row(k) * rowb;
+    const uint8_t* p0 = prv + test_row(k) * rowb;
     bool f;
     if (at.qkind == 0) f = row_last<0>(c0, p0, at, W, 0xffffffffu, &ci, &cp);
     else if (at.qkind == 1) f = row_last<1>(c0, p0, at, W, 0xffffffffu, &ci, &cp);
     else f = row_last<2>(c0, p0, at, W, 0xffffffffu, &ci, &cp);
     if (f) break;
   }
-  const uint8_t* c1 = cur + rows[ti] * rowb;
-  const uint8_t* p1 = prv + rows[ti] * rowb;
+  const uint8_t* c1 = cur + test_row(ti) * rowb;
+  const uint8_t* p1 = prv + test_row(ti) * rowb;
   uint32_t n;
   if (at.qkind == 0) n = pass_a_trial<0>(c1, p1, at, W, zi, zp);
   else if (at.qkind == 1) n = pass_a_trial<1>(c1, p1, at, W, zi, zp);

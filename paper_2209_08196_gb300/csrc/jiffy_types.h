@@ -17,7 +17,6 @@ constexpr int kWarps = kThreads / 32;
 constexpr uint32_t kMaxW = 16384;      // columns
 constexpr uint32_t kMaxH = 4096;       // rows
 constexpr uint32_t kMaxAttr = 64;
-constexpr uint32_t kMaxTestLines = 64;
 constexpr uint32_t kBlockN = 128;      // values per packing block (Sec. II frames of 128)
 
 // bits of the device error word

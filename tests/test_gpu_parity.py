@@ -152,6 +152,15 @@ def test_synthetic_multi_attr_and_low_coherence(maker):
     check_stream(cfg.H, cfg.W, synth.attr_descs(cfg), scans, seq=True)
 
 
+@pytest.mark.parametrize("lines", ["H", "10H"])
+def test_brute_force_choice_over_every_row(lines):
+    # test_lines >= H: every scanline is a test row, the brute-force I/P choice
+    cfg = synth.config_multi_attr(n_scans=3)
+    scans = synth.ScanSequence(cfg).scans()
+    L = cfg.H if lines == "H" else 10 * cfg.H
+    check_stream(cfg.H, cfg.W, synth.attr_descs(cfg), scans, test_lines=L, seq=True)
+
+
 def test_sequence_equals_single_calls_and_state_carries_across_calls():
     rng = np.random.default_rng(13)
     H, W, attrs = 8, 700, [(4, 10), (2, 1)]
