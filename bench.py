@@ -601,6 +601,23 @@ def main():
             "paper": "96 % agreement on 22,877 range scans (0.5 % sub-optimal I, 3.5 % sub-optimal P)"}
         del out_bf
 
+    # precision sweep on the range plane (Fig. 4, Sec. IV-G): bits per sample as
+    # the quantization precision doubles (the paper: about one bit saved per
+    # doubling once the precision exceeds the sensor noise)
+    precision = None
+    if not args.no_heuristic:
+        n_t = min(T, 20)
+        rng_planes = [planes_in[0][:n_t]]
+        rows = []
+        for P in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024):
+            pe = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, [(4, P)], device=local)
+            pbuf = torch.empty(J.jiffy_max_encoded_size(H, W, [(4, P)], n_t), dtype=torch.uint8, device=dev)
+            nb_p, _ = J.jiffy_encode_seq(pe, rng_planes, pbuf, stream)
+            rows.append({"precision_mm": P, "bits_per_sample": 8.0 * nb_p / (n_t * H * W)})
+            del pe, pbuf
+        precision = {"scans": n_t, "attribute": "range (uint32 mm)", "sweep": rows,
+                     "bits_saved_per_doubling_above_16mm": (rows[4]["bits_per_sample"] - rows[-1]["bits_per_sample"]) / 6.0}
+
     batched = served = None
     if not args.no_batched:
         batched = batched_leg(J, torch, dev, local, args.steps, args.warmup)
@@ -620,7 +637,7 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": 5 * args.steps * (2 if e2e else 1),
-                "batched": batched, "served": served, "heuristic": heuristic,
+                "batched": batched, "served": served, "heuristic": heuristic, "precision": precision,
                 "detail": {"kernels": kernels, "compression": modes, "stream_bytes": n,
                            "encode_gpoints_s": px_step / (avg["k_trial"] + avg["k_encode"] + avg["k_finalize"]) / 1e6,
                            "decode_gpoints_s": px_step / avg["k_decode"] / 1e6,

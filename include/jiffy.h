@@ -203,8 +203,10 @@ jiffy_status jiffy_batch_wait(jiffy_batch* b);
  * counter clearing, kernels, result download) in a CUDA graph and replays it
  * while the calls keep the same shape (streams' H, W, attribute counts and
  * scan counts, in order); the segment table, which holds the buffers and
- * frame indices, is re-uploaded by the graph each time. Off by default;
- * not used while profiling is on. */
+ * frame indices, is re-uploaded by the graph each time. Off by default for
+ * batches; single-stream calls (jiffy_encode(_seq), jiffy_decode(_seq))
+ * always replay their sequence this way while their shape repeats. Kernel
+ * timing (profiling) works with replays. */
 jiffy_status jiffy_batch_set_graphs(jiffy_batch* b, int enable);
 
 /* enable != 0: on the first call of each shape class (role, widest row,

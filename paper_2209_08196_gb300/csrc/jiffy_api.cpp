@@ -499,8 +499,9 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   key.push_back(((uint64_t)p.wpc << 32) | p.ctas_per_sm);
   key.push_back(trial_rows);
   const bool timed = ws.profile;
+  key.push_back(timed ? 1u : 0u);
   void* evs[4] = {ws.ev[0], ws.ev[1], ws.ev[2], ws.ev[3]};
-  r = run_sequence(ws, ws.g_enc, key, st, ws.graphs && !timed,
+  r = run_sequence(ws, ws.g_enc, key, st, ws.graphs,
                    [&](cudaStream_t s) { return enqueue(s, p, timed ? evs : nullptr); });
   if (r != JIFFY_OK) return r;
   if (cudaEventRecord(ws.done, st) != cudaSuccess) return JIFFY_ERR_CUDA;
@@ -669,8 +670,9 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   key.push_back(((uint64_t)p.wpc << 32) | p.ctas_per_sm);
   key.push_back(p.items_per_ticket);
   const bool timed = ws.profile;
+  key.push_back(timed ? 1u : 0u);
   void* evs[2] = {ws.ev[0], ws.ev[1]};
-  r = run_sequence(ws, ws.g_dec, key, st, ws.graphs && !timed,
+  r = run_sequence(ws, ws.g_dec, key, st, ws.graphs,
                    [&](cudaStream_t s) { return enqueue(s, p, timed ? evs : nullptr); });
   if (r != JIFFY_OK) return r;
   if (cudaEventRecord(ws.done, st) != cudaSuccess) return JIFFY_ERR_CUDA;
@@ -805,6 +807,7 @@ jiffy_status jiffy_stream_create(jiffy_stream** out, jiffy_role role, uint32_t H
   jiffy_stream* s = new (std::nothrow) jiffy_stream();
   if (!s) return JIFFY_ERR_NOMEM;
   s->ws.device = device;
+  s->ws.graphs = true;  // a stream replays its call sequence while the call's shape repeats
   s->role = role;
   s->H = H;
   s->W = W;

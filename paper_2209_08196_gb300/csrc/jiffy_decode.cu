@@ -492,12 +492,12 @@ int launch_decode(const DecParams& p0, void* stream, void* const* ev) {
   DecParams p = p0;
   p.items_per_ticket = rl.items_per_ticket;
   const size_t smem = (size_t)rl.wpc * dec_warp_layout(p.max_W).bytes;
-  if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[0]), st);
+  if (ev) record_event(ev[0], st);
   if (rl.wpc == 8) k_decode<8><<<rl.grid, 8 * 32, smem, st>>>(p);
   else if (rl.wpc == 4) k_decode<4><<<rl.grid, 4 * 32, smem, st>>>(p);
   else if (rl.wpc == 2) k_decode<2><<<rl.grid, 2 * 32, smem, st>>>(p);
   else k_decode<1><<<rl.grid, 32, smem, st>>>(p);
-  if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[1]), st);
+  if (ev) record_event(ev[1], st);
   return (int)cudaGetLastError();
 }
 

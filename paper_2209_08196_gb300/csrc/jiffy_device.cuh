@@ -18,6 +18,15 @@ __device__ __forceinline__ unsigned long long global_timer_ns() {
   return t;
 }
 
+// Host: records a timing event on st; inside a stream capture it becomes an
+// event-record node of the graph, so replays time their kernels too.
+inline cudaError_t record_event(void* ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    return cudaEventRecordWithFlags(reinterpret_cast<cudaEvent_t>(ev), st, cudaEventRecordExternal);
+  return cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev), st);
+}
+
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 __device__ __forceinline__ uint32_t warp_id() { return threadIdx.x >> 5; }
 

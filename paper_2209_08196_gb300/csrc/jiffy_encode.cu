@@ -954,7 +954,7 @@ int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_place);
   if (e != cudaSuccess) return (int)e;
   auto mark = [&](int i) {
-    if (ev) cudaEventRecord(reinterpret_cast<cudaEvent_t>(ev[i]), st);
+    if (ev) record_event(ev[i], st);
   };
   mark(0);
   if (p.trial_rows) k_trial<<<p.n_sec * p.trial_rows, 32, s_trial, st>>>(p);
