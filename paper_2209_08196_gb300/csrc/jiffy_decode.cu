@@ -97,7 +97,11 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   const uint32_t H = sg.H, W = sg.W, A = sg.A, nw = sg.nw, ncls = sg.ncls;
   const uint32_t niter = ceil_div_u32(W, 256u);
   const uint32_t kl = k - sg.item_base;  // item within the segment
-  const uint32_t r = kl % H, ta = kl / H, a = ta % A, t = ta / A;
+  // items of a segment are numbered attribute-major, (a, t, r): resident warps
+  // decode one attribute's rows at a time, and a P row's dependency, the same
+  // row of the previous scan, is the item H before it
+  const uint32_t r = kl % H, at_idx = kl / H, a = at_idx / sg.T, t = at_idx % sg.T;
+  const uint32_t ta = t * A + a;
   const AttrDev at = sg.attrs[a];
   const uint32_t S = at.s;
   const size_t rowb = (size_t)W * S;
@@ -163,7 +167,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
     status = bad ? 1u : 0u;
     // a P row waits for the same row of the previous frame (bounded)
     if (!bad && mode == 1u && t > 0) {
-      const volatile uint32_t* flag = p.done + (k - A * H);
+      const volatile uint32_t* flag = p.done + (k - H);
       if (!*flag) {
         const unsigned long long t0 = global_timer_ns();
         uint32_t ns = 32;
@@ -241,7 +245,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   uint32_t cnt = 0;
   if (!bad) {
     const uint8_t* pmask = (mode == 1u && t > 0)
-                               ? reinterpret_cast<const uint8_t*>(p.masks + sg.mask_base + (size_t)(kl - A * H) * nw)
+                               ? reinterpret_cast<const uint8_t*>(p.masks + sg.mask_base + (size_t)(kl - H) * nw)
                                : nullptr;
     uint8_t* omask = t + 1 < sg.T ? reinterpret_cast<uint8_t*>(p.masks + sg.mask_base + (size_t)kl * nw) : nullptr;
     for (uint32_t it = 0; it < niter; it++) {

@@ -6,7 +6,7 @@
 // row r) and sections (scan t, attribute a) are numbered globally across the
 // segments of a call, segment after segment. Within a segment, sections are
 // ordered (t, a); the encoder's row items are ordered (a, t, r) (attribute-
-// major) and the decoder's (t, a, r).
+// major), and so are the decoder's.
 #pragma once
 
 #include <cstdint>
