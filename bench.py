@@ -479,23 +479,28 @@ def main():
 
     # e2e through host buffers, every step: H2D of the scans, encode, D2H of
     # the stream, H2D of the stream, decode, D2H of the decoded scans. The
-    # steps are pipelined the way a streaming user would run them: the next
-    # step's upload and the previous step's download run on copy streams while
-    # the (synchronous) encode and decode calls run on the compute stream;
-    # device buffers are double-buffered. All K steps' copies fall inside the
-    # timed region.
+    # steps are software-pipelined the way a streaming user would run them:
+    # while the (synchronous) encode of step i+1 and decode of step i run on
+    # the compute stream, copy streams upload step i+2's scans, move step
+    # i+1's stream to the host and back, and download step i-1's planes; all
+    # device and host buffers are double-buffered and ordered by events. All
+    # K steps' copies fall inside the timed region.
+    scap = (n + (1 << 20)) // 256 * 256 + 256  # the stream of these scans, with room to spare
     host_in = [p.cpu().pin_memory() for p in planes_in]
-    host_stream = torch.empty(cap, dtype=torch.uint8).pin_memory()
+    host_stream = [torch.empty(scap, dtype=torch.uint8).pin_memory() for _ in range(2)]
     host_out = [[torch.empty_like(o, device="cpu").pin_memory() for o in outs] for _ in range(2)]
     dev_in = [[torch.empty_like(p) for p in planes_in] for _ in range(2)]
+    enc_out = [torch.empty(scap, dtype=torch.uint8, device=dev) for _ in range(2)]
+    dec_in = [torch.empty(scap, dtype=torch.uint8, device=dev) for _ in range(2)]
     dev_out = [outs, J.empty_planes(dec, T)]
-    dev_stream = torch.empty(cap, dtype=torch.uint8, device=dev)
     up, down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
-    ev_dec = [torch.cuda.Event(), torch.cuda.Event()]
-    ev_out = [torch.cuda.Event(), torch.cuda.Event()]
-    for ev in ev_out:
+
+    def evs():
+        return [torch.cuda.Event(), torch.cuda.Event()]
+    ev_in, ev_d2h, ev_h2d, ev_dec, ev_out = evs(), evs(), evs(), evs(), evs()
+    for ev in ev_d2h + ev_h2d + ev_out:
         ev.record(stream)
+    meta = {}
 
     def upload(i):
         s = i % 2
@@ -504,18 +509,31 @@ def main():
                 d.copy_(h, non_blocking=True)
             ev_in[s].record(up)
 
-    def e2e_step(i, last):
+    def encode(i):
         s = i % 2
-        if not last:
-            upload(i + 1)
         stream.wait_event(ev_in[s])
+        stream.wait_event(ev_d2h[s])  # step i-2's stream has left enc_out[s]
         J.jiffy_stream_reset(enc)
+        meta[i] = J.jiffy_encode_seq(enc, dev_in[s], enc_out[s], stream)
+
+    def round_trip(i):
+        s, nn = i % 2, meta[i][0]
+        with torch.cuda.stream(down):
+            down.wait_event(ev_h2d[s])  # step i-2's stream has left host_stream[s]
+            host_stream[s][:nn].copy_(enc_out[s][:nn], non_blocking=True)
+            ev_d2h[s].record(down)
+        with torch.cuda.stream(up):
+            up.wait_event(ev_d2h[s])
+            dec_in[s][:nn].copy_(host_stream[s][:nn], non_blocking=True)
+            ev_h2d[s].record(up)
+
+    def decode(i):
+        s = i % 2
+        nn, offs = meta.pop(i)
+        stream.wait_event(ev_h2d[s])
+        stream.wait_event(ev_out[s])  # step i-2's planes have left dev_out[s]
         J.jiffy_stream_reset(dec)
-        nn, offs = J.jiffy_encode_seq(enc, dev_in[s], out, stream)
-        host_stream[:nn].copy_(out[:nn], non_blocking=True)
-        dev_stream[:nn].copy_(host_stream[:nn], non_blocking=True)
-        stream.wait_event(ev_out[s])  # the download of step i - 2 has left dev_out[s]
-        J.jiffy_decode_seq(dec, dev_stream, nn, offs, dev_out[s], stream)
+        J.jiffy_decode_seq(dec, dec_in[s], nn, offs, dev_out[s], stream)
         ev_dec[s].record(stream)
         with torch.cuda.stream(down):
             down.wait_event(ev_dec[s])
@@ -526,16 +544,25 @@ def main():
 
     def e2e_run(k):
         upload(0)
+        if k > 1:
+            upload(1)
+        encode(0)
+        round_trip(0)
         nn = 0
         for i in range(k):
-            nn = e2e_step(i, i + 1 == k)
-        stream.wait_event(ev_out[(k - 1) % 2])
-        stream.wait_event(ev_out[k % 2])
+            if i + 1 < k:
+                encode(i + 1)
+                if i + 2 < k:
+                    upload(i + 2)
+                round_trip(i + 1)
+            nn = decode(i)
+        for ev in ev_out:
+            stream.wait_event(ev)
         return nn
 
     e2e = None
     if not args.no_e2e:
-        e2e_run(2)
+        e2e_run(3)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -555,7 +582,9 @@ def main():
             del q
         e2e = {"value": whole_job_gpoints(px_step, world, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": raw_bytes + nn, "d2h_bytes_per_step": nn + raw_bytes,
-               "pipelined": "upload of step i+1 and download of step i-1 overlap the calls of step i"}
+               "pipelined": "encode of step i+1 and decode of step i overlap the uploads of step i+2, "
+                            "the stream round trip of step i+1 and the download of step i-1"}
+        del host_stream, host_out, dev_in, enc_out, dec_in
 
     # roofline of the dominant kernel: algorithmic bytes / CUDA-event duration
     avg = {k: statistics.mean(v) for k, v in ktimes.items()}
