@@ -130,6 +130,19 @@ def test_degenerate_scans(case):
     check_stream(H, W, attrs, scans, seq=True)
 
 
+@pytest.mark.parametrize("shape", ["max_w", "max_h"])
+def test_maximum_shapes(shape):
+    # the largest row (W = 16384: 128 blocks per row, one warp per CTA) and the
+    # most rows (H = 4096) the library accepts, both modes, several attributes
+    rng = np.random.default_rng(21)
+    H, W = (2, 16384) if shape == "max_w" else (4096, 40)
+    attrs = [(4, 10), (2, 1), (1, 3)]
+    base = [rand_scan(rng, H, W, s, 0.1) for s, _ in attrs]
+    scans = [[drift(rng, b, s, t, 0.05) for b, (s, _) in zip(base, attrs)] for t in range(3)]
+    check_stream(H, W, attrs, scans, seq=True)
+    check_stream(H, W, attrs, scans, force_mode=1)
+
+
 def test_test_lines_option():
     rng = np.random.default_rng(12)
     H, W, attrs = 40, 512, [(4, 10)]
