@@ -290,3 +290,37 @@ def test_decoder_takes_over_from_encoder_state():
     other = J.jiffy_stream_create(J.JIFFY_DECODER, H, W + 1, a)
     with pytest.raises(J.JiffyError):
         J.jiffy_stream_copy_state(other, enc)
+
+
+def test_many_stream_workload_sampled_against_oracle():
+    # the many-stream configuration (uneven shapes from 16x1024 to 128x4096,
+    # attribute sets {range}, {range, signal}, all five; 8 scans each) in one
+    # batched call each way; sampled streams, the widest among them, checked
+    # byte for byte and plane for plane against the oracle
+    from paper_2209_08196_gb300 import synth
+    cfgs = [synth.batch_stream_config(i, base_seed=77, n_scans=8) for i in range(24)]
+    encs, decs, planes, outs, attrs_l = [], [], [], [], []
+    for c in cfgs:
+        at = synth.attr_descs(c)
+        attrs_l.append(at)
+        seq = synth.ScanSequence(c, device="cuda")
+        sc = [seq.scan(t, as_numpy=False) for t in range(c.n_scans)]
+        planes.append([torch.stack([sc[t][a] for t in range(c.n_scans)]) for a in range(len(at))])
+        encs.append(J.jiffy_stream_create(J.JIFFY_ENCODER, c.H, c.W, at))
+        decs.append(J.jiffy_stream_create(J.JIFFY_DECODER, c.H, c.W, at))
+        outs.append(torch.empty(J.jiffy_max_encoded_size(c.H, c.W, at, c.n_scans), dtype=torch.uint8, device="cuda"))
+    b = J.jiffy_batch_create()
+    res = J.jiffy_encode_batch(b, encs, planes, outs)
+    dec_planes = [J.empty_planes(d, c.n_scans) for d, c in zip(decs, cfgs)]
+    J.jiffy_decode_batch(b, decs, outs, [n for n, _ in res], [o for _, o in res], dec_planes)
+    widest = max(range(len(cfgs)), key=lambda i: cfgs[i].H * cfgs[i].W * len(attrs_l[i]))
+    for i in sorted({0, 5, 11, 17, widest}):
+        c, at = cfgs[i], attrs_l[i]
+        host = [[to_np(planes[i][a][t], s) for a, (s, _) in enumerate(at)] for t in range(c.n_scans)]
+        want, _, _ = oracle.encode_sequence(c.H, c.W, at, host)
+        n, offs = res[i]
+        assert outs[i][:n].cpu().numpy().tobytes() == want, i
+        ref_planes, _ = oracle.decode_sequence(c.H, c.W, at, want, c.n_scans)
+        for t in range(c.n_scans):
+            for a, (s, _) in enumerate(at):
+                assert np.array_equal(to_np(dec_planes[i][a][t], s), ref_planes[t][a]), (i, t, a)
