@@ -69,33 +69,6 @@ __device__ __forceinline__ void prefetch_l1(const void* p, uint32_t bytes) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
 }
 
-// Warp-wide copy of `bytes` bytes from global to shared memory: one round of
-// independent loads (16-byte vectors when both sides allow, else words, else
-// bytes).
-__device__ __forceinline__ void stage_bytes(uint8_t* dst, const uint8_t* src, uint32_t bytes) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uintptr_t al = reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src) | bytes;
-  if ((al & 15u) == 0) {
-    const uint4* s4 = reinterpret_cast<const uint4*>(src);
-    uint4* d4 = reinterpret_cast<uint4*>(dst);
-    const uint32_t n = bytes / 16u;
-    for (uint32_t i = lane; i < n; i += 128u) {
-      uint4 v[4];
-#pragma unroll
-      for (uint32_t q = 0; q < 4; q++) v[q] = i + 32u * q < n ? s4[i + 32u * q] : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-      for (uint32_t q = 0; q < 4; q++)
-        if (i + 32u * q < n) d4[i + 32u * q] = v[q];
-    }
-  } else if ((al & 3u) == 0) {
-    const uint32_t* s1 = reinterpret_cast<const uint32_t*>(src);
-    uint32_t* d1 = reinterpret_cast<uint32_t*>(dst);
-    for (uint32_t i = lane; i < bytes / 4u; i += 32u) d1[i] = s1[i];
-  } else {
-    for (uint32_t i = lane; i < bytes; i += 32u) dst[i] = src[i];
-  }
-}
-
 // Groups of 8 consecutive samples move as one vector when the group is
 // aligned: 32 bytes (u32), 16 bytes (u16) or 8 bytes (u8). Group starts are
 // multiples of 8 samples, so a vector-aligned row base suffices.
@@ -342,7 +315,7 @@ __device__ __forceinline__ void st_publish(unsigned long long* p, unsigned long 
 // Outcome of a look-back step.
 enum : int { kLbFail = 0, kLbOk = 1, kLbPending = 2 };
 
-// Warp-wide window read for the look-backs: kLookQ x 32 status words per
+// Warp-wide window read for the look-back: kLookQ x 32 status words per
 // round, entry (q, lane) = word j - 32q - lane (nearest first), `beyond` past
 // the segment start. Finds the nearest entry that decides the look-back,
 // re-reading while an entry nearer than it is still empty (or, with wait =
@@ -385,34 +358,6 @@ __device__ __forceinline__ int lookback_window(const unsigned long long* st, int
     __nanosleep(ns);
     if (ns < 512) ns <<= 1;
   }
-}
-
-// Warp-wide. Exclusive prefix of item k over items [seg_start, k): sums
-// aggregates back to the nearest inclusive prefix. Returns kLbOk, kLbFail
-// (an upstream error or a timeout) or, with wait = false, kLbPending when a
-// predecessor has not published yet.
-__device__ inline int lookback_sum(const unsigned long long* st, uint32_t k, uint32_t seg_start,
-                                   unsigned long long& excl, bool wait = true) {
-  const uint32_t lane = lane_id();
-  unsigned long long acc = 0;
-  int64_t j = (int64_t)k - 1;
-  while (j >= (int64_t)seg_start) {
-    unsigned long long s[kLookQ];
-    uint32_t stop;
-    const int rc = lookback_window(st, j, seg_start, kStInc, [](unsigned long long x) { return (x >> 62) == 2ull; },
-                                   s, stop, wait);
-    if (rc != kLbOk) return rc;
-    unsigned long long v = 0;
-#pragma unroll
-    for (uint32_t q = 0; q < kLookQ; q++)
-      if (32u * q + lane <= stop) v += s[q] & kStValMask;  // stop == window: every entry
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    acc += v;
-    if (stop < kLookQ * 32u) break;
-    j -= kLookQ * 32;
-  }
-  excl = acc;
-  return kLbOk;
 }
 
 // Warp-wide. "Last valid" look-back for the delta carry: value bit 32 =
