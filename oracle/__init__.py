@@ -8,7 +8,8 @@ the CUDA path: the C file is compiled on its own with gcc.
 The oracle follows the paper (Ford & Ford, arXiv 2209.08196) step by step:
 quantization (Sec. III-A/B), zero bitmask (Sec. III-C), trial I/P selection
 (Sec. III-E), mask XOR (Sec. III-D), compaction, residual, delta, ZigZag
-(Eq. 1) and PFOR-style packing (Sec. II).
+(Eq. 1) and PFOR-style packing (Sec. II). A stream may drop the mask, delta or
+ZigZag stage (the ablated codecs of Sec. IV-H, Table IV).
 """
 from __future__ import annotations
 
@@ -24,6 +25,11 @@ _LIB = os.path.join(_HERE, "libjiffy_oracle.so")
 
 ERR_CAPACITY = 2
 ERR_CORRUPT = 3
+
+# stage switches of a stream (Table IV ablations)
+NO_MASK = 1
+NO_DELTA = 2
+NO_ZIGZAG = 4
 
 _DT = {1: np.uint8, 2: np.uint16, 4: np.uint32}
 
@@ -59,7 +65,7 @@ def lib() -> ctypes.CDLL:
         L.jo_pack_block.restype = u32
         L.jo_pack_block.argtypes = [vp, u32, u32, vp]
         L.jo_create.restype = vp
-        L.jo_create.argtypes = [u32, u32, u32, vp, vp, u32, i32]
+        L.jo_create.argtypes = [u32, u32, u32, vp, vp, u32, i32, u32]
         L.jo_destroy.restype = None
         L.jo_destroy.argtypes = [vp]
         L.jo_reset.restype = None
@@ -138,13 +144,13 @@ class Codec:
     """One stateful oracle stream (encoder or decoder role; the state is the
     previous scan's quantized values, Sec. III-D)."""
 
-    def __init__(self, H: int, W: int, attrs, test_lines: int = 4, force_mode: int = -1):
+    def __init__(self, H: int, W: int, attrs, test_lines: int = 4, force_mode: int = -1, stages: int = 0):
         self.H, self.W = H, W
         self.attrs = [(int(s), int(p)) for s, p in attrs]
         self.A = len(self.attrs)
         dt = np.array([s for s, _ in self.attrs], dtype=np.uint8)
         pr = np.array([p for _, p in self.attrs], dtype=np.uint32)
-        self._h = lib().jo_create(H, W, self.A, _ptr(dt), _ptr(pr), test_lines, force_mode)
+        self._h = lib().jo_create(H, W, self.A, _ptr(dt), _ptr(pr), test_lines, force_mode, stages)
         if not self._h:
             raise ValueError("invalid oracle configuration")
 
@@ -193,10 +199,10 @@ class Codec:
         return outs, int(n)
 
 
-def encode_sequence(H, W, attrs, scans, test_lines=4, force_mode=-1):
+def encode_sequence(H, W, attrs, scans, test_lines=4, force_mode=-1, stages=0):
     """Encodes scans (a list of per-scan plane lists) as one stream; returns
     (bytes of the whole stream, per-frame byte lengths, per-frame modes)."""
-    c = Codec(H, W, attrs, test_lines, force_mode)
+    c = Codec(H, W, attrs, test_lines, force_mode, stages)
     parts, lens, modes = [], [], []
     for planes in scans:
         b, m = c.encode(planes, return_modes=True)
@@ -207,8 +213,8 @@ def encode_sequence(H, W, attrs, scans, test_lines=4, force_mode=-1):
     return b"".join(parts), lens, modes
 
 
-def decode_sequence(H, W, attrs, buf: bytes, n_scans: int):
-    c = Codec(H, W, attrs)
+def decode_sequence(H, W, attrs, buf: bytes, n_scans: int, stages: int = 0):
+    c = Codec(H, W, attrs, stages=stages)
     out, pos = [], 0
     for _ in range(n_scans):
         planes, n = c.decode(buf[pos:])

@@ -25,6 +25,13 @@
  * The decoder runs the same steps backwards (Sec. III-C, "straightforward
  * reversal").
  *
+ * Ablation switches (Sec. IV-H, Table IV): a stream may drop the zero mask
+ * (every sample is coded, zeros included), the horizontal delta (residuals
+ * packed as they are) or ZigZag (deltas packed as 32-bit two's complement
+ * words); with I forced as well, the four ablated codecs of Table IV are
+ * SIMD-PFOR alone, Delta -> PFOR, Delta -> ZigZag -> PFOR and
+ * Mask -> Delta -> ZigZag -> PFOR.
+ *
  * The paper does not fix a byte layout; the layout written here (stream
  * header, frame header, per-attribute section with a row table, per-row
  * chunks, mask class words, block headers and bodies) is this project's and
@@ -42,6 +49,9 @@
 #define JO_MAX_ATTR 64
 
 enum { JO_OK = 0, JO_ERR_INVALID_ARG = 1, JO_ERR_CAPACITY = 2, JO_ERR_CORRUPT = 3 };
+
+/* Stage switches of a stream (Table IV ablations); 0 = the full codec. */
+enum { JO_NO_MASK = 1, JO_NO_DELTA = 2, JO_NO_ZIGZAG = 4 };
 
 /* ------------------------------------------------------------------ */
 /* small helpers                                                       */
@@ -232,9 +242,10 @@ static uint32_t unpack_block(const uint8_t* hdr, const uint8_t* body, size_t ava
 /* Compacts the nonzero samples of the listed rows in row-major order and
  * forms residuals: e = q (I) or e = q - pq (P), modulo 2^32, with pq the
  * previous scan's quantized value at the same pixel (Sec. III-D: both scans
- * are masked with the current scan's mask). row_start[k] receives the index
- * of the first residual of listed row k; row_start[nrows] the total. */
-static uint32_t residuals(uint32_t W, const uint32_t* q, const uint32_t* pq, int mode,
+ * are masked with the current scan's mask). Without the mask stage every
+ * sample is kept. row_start[k] receives the index of the first residual of
+ * listed row k; row_start[nrows] the total. */
+static uint32_t residuals(uint32_t W, const uint32_t* q, const uint32_t* pq, int mode, uint32_t stages,
                           const uint32_t* rows, uint32_t nrows, uint32_t* e, uint32_t* row_start) {
   uint32_t k = 0;
   for (uint32_t ri = 0; ri < nrows; ri++) {
@@ -242,7 +253,7 @@ static uint32_t residuals(uint32_t W, const uint32_t* q, const uint32_t* pq, int
     uint32_t r = rows[ri];
     for (uint32_t x = 0; x < W; x++) {
       size_t i = (size_t)r * W + x;
-      if (q[i] == 0) continue; /* masked out (Sec. III-C) */
+      if (q[i] == 0 && !(stages & JO_NO_MASK)) continue; /* masked out (Sec. III-C) */
       e[k++] = mode == 0 ? q[i] : q[i] - pq[i];
     }
   }
@@ -251,12 +262,12 @@ static uint32_t residuals(uint32_t W, const uint32_t* q, const uint32_t* pq, int
 }
 
 /* Horizontal delta over the flat vector (Sec. III-C), e[-1] = 0, then ZigZag
- * (Eq. 1). */
-static void delta_zigzag(const uint32_t* e, uint32_t n, uint32_t* z) {
+ * (Eq. 1); each step only if the stream keeps it. */
+static void delta_zigzag(const uint32_t* e, uint32_t n, uint32_t stages, uint32_t* z) {
   uint32_t prev = 0;
   for (uint32_t k = 0; k < n; k++) {
-    uint32_t d = e[k] - prev; /* modulo 2^32 */
-    z[k] = jo_zigzag((int32_t)d);
+    uint32_t d = (stages & JO_NO_DELTA) ? e[k] : e[k] - prev; /* modulo 2^32 */
+    z[k] = (stages & JO_NO_ZIGZAG) ? d : jo_zigzag((int32_t)d);
     prev = e[k];
   }
 }
@@ -290,14 +301,14 @@ static uint32_t test_rows(uint32_t H, uint32_t L, uint32_t* rows) {
 }
 
 static uint64_t trial_cost(uint32_t H, uint32_t W, const uint32_t* q, const uint32_t* pq, int mode,
-                           uint32_t L) {
+                           uint32_t L, uint32_t stages) {
   uint32_t* rows = (uint32_t*)calloc(L ? L : 1, sizeof(uint32_t));
   uint32_t nrows = test_rows(H, L, rows);
   uint32_t* e = (uint32_t*)malloc(sizeof(uint32_t) * ((size_t)nrows * W + 1));
   uint32_t* z = (uint32_t*)malloc(sizeof(uint32_t) * ((size_t)nrows * W + 1));
   uint32_t* start = (uint32_t*)malloc(sizeof(uint32_t) * (nrows + 1));
-  uint32_t n = residuals(W, q, pq, mode, rows, nrows, e, start);
-  delta_zigzag(e, n, z);
+  uint32_t n = residuals(W, q, pq, mode, stages, rows, nrows, e, start);
+  delta_zigzag(e, n, stages, z);
   uint64_t cost = 0;
   for (uint32_t k = 0; k < nrows; k++) cost += row_block_bytes(z + start[k], start[k + 1] - start[k]);
   free(rows); free(e); free(z); free(start);
@@ -312,6 +323,7 @@ static uint64_t trial_cost(uint32_t H, uint32_t W, const uint32_t* q, const uint
 /*             flat vector (0 if none): the value row r's first delta   */
 /*             subtracts. Redundant, it lets rows decode independently. */
 /*   row chunks, r = 0..H-1:                                            */
+/*     (mask part, absent without the mask stage:)                      */
 /*     mask class words: ceil(nw/16) u32, nw = ceil(W/32); word j's     */
 /*       2-bit class sits at bits 2*(j%16) of class word j/16:           */
 /*       0: coded word is 0, 1: coded word has every valid bit set,     */
@@ -343,8 +355,9 @@ static size_t section_bound(uint32_t H, uint32_t W) {
  * section_bound bytes). Returns its size; mask_bytes / data_bytes receive
  * the mask-part and block (header + body) byte counts. */
 static size_t encode_section(uint32_t H, uint32_t W, const uint32_t* q, const uint32_t* pq, int mode,
-                             uint8_t* out, uint32_t* nnz_out, uint64_t* mask_bytes, uint64_t* data_bytes) {
-  uint32_t nw = ceil_div(W, 32u);
+                             uint32_t stages, uint8_t* out, uint32_t* nnz_out, uint64_t* mask_bytes,
+                             uint64_t* data_bytes) {
+  uint32_t nw = (stages & JO_NO_MASK) ? 0u : ceil_div(W, 32u); /* mask words per row */
   size_t HW = (size_t)H * W;
   /* zero bitmask, one entry per sample (Sec. III-C): 1 = zero sample */
   uint8_t* M = (uint8_t*)malloc(HW ? HW : 1);
@@ -355,9 +368,9 @@ static size_t encode_section(uint32_t H, uint32_t W, const uint32_t* q, const ui
   uint32_t* e = (uint32_t*)malloc(sizeof(uint32_t) * (HW + 1));
   uint32_t* z = (uint32_t*)malloc(sizeof(uint32_t) * (HW + 1));
   uint32_t* start = (uint32_t*)malloc(sizeof(uint32_t) * (H + 1));
-  uint32_t nnz = residuals(W, q, pq, mode, rows, H, e, start);
+  uint32_t nnz = residuals(W, q, pq, mode, stages, rows, H, e, start);
   /* delta over the flat vector, then ZigZag (Sec. III-C, Eq. 1) */
-  delta_zigzag(e, nnz, z);
+  delta_zigzag(e, nnz, stages, z);
 
   uint8_t* table = out;
   uint8_t* data = out + (size_t)H * 8u;
@@ -414,9 +427,10 @@ static size_t encode_section(uint32_t H, uint32_t W, const uint32_t* q, const ui
 }
 
 /* Decodes one section into q_out. Returns 0 or JO_ERR_CORRUPT. */
-static int decode_section(uint32_t H, uint32_t W, const uint8_t* sec, size_t len, int mode,
+static int decode_section(uint32_t H, uint32_t W, const uint8_t* sec, size_t len, int mode, uint32_t stages,
                           const uint32_t* pq, uint32_t* q_out, uint32_t expect_nnz) {
   uint32_t nw = ceil_div(W, 32u);
+  uint32_t nmw = (stages & JO_NO_MASK) ? 0u : nw; /* coded mask words per row */
   if (len < (size_t)H * 8u) return JO_ERR_CORRUPT;
   const uint8_t* table = sec;
   const uint8_t* data = sec + (size_t)H * 8u;
@@ -433,11 +447,15 @@ static int decode_section(uint32_t H, uint32_t W, const uint8_t* sec, size_t len
     const uint8_t* chunk = data + begin;
     size_t clen = end - begin, p = 0;
     /* mask part */
-    uint32_t ncls = ceil_div(nw, 16u);
+    uint32_t ncls = ceil_div(nmw, 16u);
     if (4u * ncls > clen) { rc = JO_ERR_CORRUPT; break; }
     p = 4u * ncls;
     uint32_t n = 0;
-    for (uint32_t j = 0; j < nw && rc == JO_OK; j++) {
+    if (nmw == 0) { /* no mask stage: every sample was coded */
+      for (uint32_t j = 0; j < nw; j++) word[j] = 0;
+      n = W;
+    }
+    for (uint32_t j = 0; j < nmw && rc == JO_OK; j++) {
       uint32_t c = (get_u32(chunk + 4u * (j / 16u)) >> (2u * (j % 16u))) & 3u;
       uint32_t w;
       if (c == 0) w = 0;
@@ -476,7 +494,8 @@ static int decode_section(uint32_t H, uint32_t W, const uint8_t* sec, size_t len
     for (uint32_t x = 0; x < W; x++) {
       size_t i = (size_t)r * W + x;
       if ((word[x / 32u] >> (x % 32u)) & 1u) { q_out[i] = 0; continue; }
-      uint32_t e = prev + (uint32_t)jo_unzigzag(z[k++]); /* modulo 2^32 */
+      uint32_t d = (stages & JO_NO_ZIGZAG) ? z[k++] : (uint32_t)jo_unzigzag(z[k++]);
+      uint32_t e = (stages & JO_NO_DELTA) ? d : prev + d; /* modulo 2^32 */
       prev = e;
       q_out[i] = mode == 0 ? e : e + pq[i];
     }
@@ -493,8 +512,9 @@ static int decode_section(uint32_t H, uint32_t W, const uint8_t* sec, size_t len
 /* Stream codec                                                         */
 /*   stream header (first frame after create/reset), 16 + 8A bytes:     */
 /*     "JFY1", u16 version = 1, u16 A, u32 H, u32 W,                     */
-/*     per attribute: u8 dtype_bytes, u8 zigzag variant (1 = Eq. 1),     */
-/*     u16 0, u32 precision (Sec. III-A: the precision is stored)        */
+/*     per attribute: u8 dtype_bytes, u8 zigzag variant (1 = Eq. 1,      */
+/*     0 = none), u8 stage flags (bit 0: no zero mask, bit 1: no delta), */
+/*     u8 0, u32 precision (Sec. III-A: the precision is stored)         */
 /*   frame, header 8 + 12A bytes:                                       */
 /*     u32 frame_bytes (header included), u32 scan_index,               */
 /*     per attribute: u8 mode (0 = I, 1 = P), 3 bytes 0,                 */
@@ -505,6 +525,7 @@ static int decode_section(uint32_t H, uint32_t W, const uint8_t* sec, size_t len
 typedef struct {
   uint32_t H, W, A, L;
   int32_t force_mode;
+  uint32_t stages; /* JO_NO_* switches */
   uint8_t dtype[JO_MAX_ATTR];
   uint32_t prec[JO_MAX_ATTR];
   uint32_t frame;
@@ -512,13 +533,13 @@ typedef struct {
 } jo_codec;
 
 jo_codec* jo_create(uint32_t H, uint32_t W, uint32_t A, const uint8_t* dtypes, const uint32_t* precs,
-                    uint32_t test_lines, int32_t force_mode) {
-  if (H == 0 || W == 0 || A == 0 || A > JO_MAX_ATTR || test_lines == 0) return NULL;
+                    uint32_t test_lines, int32_t force_mode, uint32_t stages) {
+  if (H == 0 || W == 0 || A == 0 || A > JO_MAX_ATTR || test_lines == 0 || stages > 7u) return NULL;
   for (uint32_t a = 0; a < A; a++) {
     if (!(dtypes[a] == 1 || dtypes[a] == 2 || dtypes[a] == 4) || precs[a] == 0) return NULL;
   }
   jo_codec* c = (jo_codec*)calloc(1, sizeof(jo_codec));
-  c->H = H; c->W = W; c->A = A; c->L = test_lines; c->force_mode = force_mode;
+  c->H = H; c->W = W; c->A = A; c->L = test_lines; c->force_mode = force_mode; c->stages = stages;
   for (uint32_t a = 0; a < A; a++) {
     c->dtype[a] = dtypes[a]; c->prec[a] = precs[a];
     c->prev_q[a] = (uint32_t*)calloc((size_t)H * W, sizeof(uint32_t));
@@ -551,7 +572,11 @@ int64_t jo_encode(jo_codec* c, const void* const* planes, uint8_t* out, size_t c
     put_u16(buf + 4, 1); put_u16(buf + 6, c->A); put_u32(buf + 8, c->H); put_u32(buf + 12, c->W);
     for (uint32_t a = 0; a < c->A; a++) {
       uint8_t* p = buf + 16 + 8 * a;
-      p[0] = c->dtype[a]; p[1] = 1; p[2] = 0; p[3] = 0; put_u32(p + 4, c->prec[a]);
+      p[0] = c->dtype[a];
+      p[1] = (c->stages & JO_NO_ZIGZAG) ? 0 : 1;
+      p[2] = (uint8_t)(c->stages & (JO_NO_MASK | JO_NO_DELTA));
+      p[3] = 0;
+      put_u32(p + 4, c->prec[a]);
     }
     pos = stream_header_bytes(c->A);
   }
@@ -564,12 +589,12 @@ int64_t jo_encode(jo_codec* c, const void* const* planes, uint8_t* out, size_t c
     if (c->frame == 0) mode = 0;
     else if (c->force_mode == 0 || c->force_mode == 1) mode = c->force_mode;
     else {
-      uint64_t ci = trial_cost(c->H, c->W, q[a], c->prev_q[a], 0, c->L);
-      uint64_t cp = trial_cost(c->H, c->W, q[a], c->prev_q[a], 1, c->L);
+      uint64_t ci = trial_cost(c->H, c->W, q[a], c->prev_q[a], 0, c->L, c->stages);
+      uint64_t cp = trial_cost(c->H, c->W, q[a], c->prev_q[a], 1, c->L, c->stages);
       mode = cp < ci ? 1 : 0;
     }
     uint32_t nnz = 0;
-    size_t sec = encode_section(c->H, c->W, q[a], c->prev_q[a], mode, buf + pos, &nnz, NULL, NULL);
+    size_t sec = encode_section(c->H, c->W, q[a], c->prev_q[a], mode, c->stages, buf + pos, &nnz, NULL, NULL);
     uint8_t* h = buf + frame_start + 8 + 12 * a;
     h[0] = (uint8_t)mode; put_u32(h + 4, (uint32_t)sec); put_u32(h + 8, nnz);
     if (modes_out) modes_out[a] = (uint8_t)mode;
@@ -603,7 +628,8 @@ int64_t jo_decode(jo_codec* c, const uint8_t* in, size_t len, void* const* plane
       return -JO_ERR_CORRUPT;
     for (uint32_t a = 0; a < c->A; a++) {
       const uint8_t* p = in + 16 + 8 * a;
-      if (p[0] != c->dtype[a] || p[1] != 1 || p[2] != 0 || p[3] != 0 || get_u32(p + 4) != c->prec[a])
+      if (p[0] != c->dtype[a] || p[1] != ((c->stages & JO_NO_ZIGZAG) ? 0 : 1) ||
+          p[2] != (c->stages & (JO_NO_MASK | JO_NO_DELTA)) || p[3] != 0 || get_u32(p + 4) != c->prec[a])
         return -JO_ERR_CORRUPT;
     }
     pos = stream_header_bytes(c->A);
@@ -624,7 +650,7 @@ int64_t jo_decode(jo_codec* c, const uint8_t* in, size_t len, void* const* plane
       rc = JO_ERR_CORRUPT; break;
     }
     q[a] = (uint32_t*)malloc(sizeof(uint32_t) * (HW ? HW : 1));
-    rc = decode_section(c->H, c->W, in + sp, sec, mode, c->prev_q[a], q[a], nnz);
+    rc = decode_section(c->H, c->W, in + sp, sec, mode, c->stages, c->prev_q[a], q[a], nnz);
     if (rc == JO_OK) {
       uint32_t qmax = dtype_max(c->dtype[a]) / c->prec[a];
       for (size_t i = 0; i < HW; i++) if (q[a][i] > qmax) { rc = JO_ERR_CORRUPT; break; }
@@ -660,7 +686,7 @@ uint64_t jo_trial_cost(uint32_t H, uint32_t W, uint32_t s, uint32_t P, uint32_t 
   size_t HW = (size_t)H * W;
   uint32_t* q = quantize_plane(cur, s, P, HW);
   uint32_t* pq = quantize_plane(prev, s, P, HW);
-  uint64_t c = trial_cost(H, W, q, pq, mode, L);
+  uint64_t c = trial_cost(H, W, q, pq, mode, L, 0u);
   free(q); free(pq);
   return c;
 }
@@ -674,7 +700,7 @@ uint64_t jo_section_split(uint32_t H, uint32_t W, uint32_t s, uint32_t P, const 
   uint32_t* pq = quantize_plane(prev, s, P, HW);
   uint8_t* buf = (uint8_t*)calloc(section_bound(H, W), 1);
   uint32_t nnz = 0;
-  size_t sec = encode_section(H, W, q, pq, mode, buf, &nnz, mask_bytes, data_bytes);
+  size_t sec = encode_section(H, W, q, pq, mode, 0u, buf, &nnz, mask_bytes, data_bytes);
   free(q); free(pq); free(buf);
   return sec;
 }

@@ -37,5 +37,20 @@ def load(name):
     return H, W, attrs, frames
 
 
+def options(name):
+    """Stream options of a fixture: 'force <mode>' (default -1, trial) and
+    'stages <bits>' (default 0; 1 = no zero mask, 2 = no delta, 4 = no
+    ZigZag, the ablations of Sec. IV-H)."""
+    opt = {"force_mode": -1, "stages": 0}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line.startswith("force "):
+                opt["force_mode"] = int(line.split()[1])
+            elif line.startswith("stages "):
+                opt["stages"] = int(line.split()[1])
+    return opt
+
+
 def names():
     return sorted(n for n in os.listdir(GOLDEN) if n.startswith("stream_") and n.endswith(".txt"))

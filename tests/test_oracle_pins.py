@@ -20,8 +20,9 @@ def quantize_plane(v, P, s):
 @pytest.mark.parametrize("name", golden_io.names())
 def test_golden_stream(name):
     H, W, attrs, frames = golden_io.load(name)
-    enc = oracle.Codec(H, W, attrs)
-    dec = oracle.Codec(H, W, attrs)
+    opt = golden_io.options(name)
+    enc = oracle.Codec(H, W, attrs, 4, opt["force_mode"], opt["stages"])
+    dec = oracle.Codec(H, W, attrs, stages=opt["stages"])
     for f in frames:
         b, modes = enc.encode(f["in"], return_modes=True)
         assert modes == f["mode"]
@@ -283,3 +284,141 @@ def test_corrupt_streams_are_rejected():
         oracle.Codec(3, 100, [(4, 10)]).decode(bytes(bad))
     with pytest.raises(oracle.OracleError):  # precision differs from the stream's
         oracle.Codec(3, 100, [(4, 11)]).decode(buf)
+
+
+# ---------------------------------------------------------------- ablations (Sec. IV-H, Table IV)
+def _read_bits(words, pos, n):
+    """n bits of a little-endian bit stream held in u32 words, from bit pos."""
+    v = 0
+    for k in range(n):
+        p = pos + k
+        v |= ((int(words[p // 32]) >> (p % 32)) & 1) << k
+    return v
+
+
+def _unmasked_row_values(buf, H, W, A, a, frame_start):
+    """Reads the packed values of every row of attribute a of the frame at
+    frame_start in a stream without the mask stage, straight from the bytes:
+    row table, block headers {b, e, hb, 0}, low bits, exception positions
+    and high parts."""
+    u32 = lambda o: int.from_bytes(buf[o:o + 4], "little")
+    sec = frame_start + 8 + 12 * A
+    for aa in range(a):
+        sec += u32(frame_start + 12 + 12 * aa)
+    data = sec + 8 * H
+    rows, begin = [], 0
+    for r in range(H):
+        end = u32(sec + 8 * r)
+        chunk = np.frombuffer(buf[data + begin:data + end], dtype="<u4")
+        nb = (W + 127) // 128
+        pos = nb
+        z = []
+        for g in range(nb):
+            h = int(chunk[g])
+            b, e, hb = h & 255, (h >> 8) & 255, (h >> 16) & 255
+            m = min(128, W - 128 * g)
+            body = chunk[pos:]
+            vals = [_read_bits(body, i * b, b) for i in range(m)]
+            low = (m * b + 31) // 32
+            if e:
+                pbytes = body[low:].tobytes()
+                highs = body[low + (e + 3) // 4:]
+                for j in range(e):
+                    vals[pbytes[j]] |= _read_bits(highs, j * hb, hb) << b
+            pos += low + ((e + 3) // 4 + (e * hb + 31) // 32 if e else 0)
+            z += vals
+        assert pos == len(chunk)
+        rows.append(z)
+        begin = end
+    return rows
+
+
+def _zz(x):
+    x = int(np.int64(np.int32(np.uint32(x & 0xFFFFFFFF))))  # two's complement value
+    return (2 * abs(x) + (1 if x < 0 else 0)) & 0xFFFFFFFF   # Eq. 1, modulo 2^32
+
+
+@pytest.mark.parametrize("stages", [1, 3, 5, 7])
+def test_unmasked_streams_pack_the_definition_of_each_stage(stages):
+    # without the mask every sample is coded (zeros too); the packed values
+    # are the residuals (I: q), deltaed over the flat vector unless the delta
+    # is off, ZigZag coded (Eq. 1) unless ZigZag is off
+    rng = np.random.default_rng(20 + stages)
+    H, W, P = 3, 300, 3
+    v = random_scan(rng, H, W, 2, 0.25, 60000)
+    buf = oracle.Codec(H, W, [(2, P)], force_mode=0, stages=stages).encode([v])
+    assert buf[16 + 1] == (0 if stages & 4 else 1) and buf[16 + 2] == stages & 3
+    rows = _unmasked_row_values(buf, H, W, 1, 0, 24)
+    e = [int(x) for x in quantize_plane(v, P, 2).ravel()]
+    want, prev = [], 0
+    for x in e:
+        d = x if stages & 2 else (x - prev) & 0xFFFFFFFF
+        want.append(d if stages & 4 else _zz(d))
+        prev = x
+    assert sum(rows, []) == want
+
+
+def test_unmasked_p_frame_packs_every_temporal_difference():
+    rng = np.random.default_rng(31)
+    H, W = 2, 200
+    v0 = random_scan(rng, H, W, 4, 0.3, 10**6)
+    v1 = v0.copy()
+    v1[rng.random(v1.shape) < 0.2] = 0  # new dropouts stay in the residual stream
+    c = oracle.Codec(H, W, [(4, 1)], force_mode=1, stages=7)
+    c.encode([v0])
+    buf = c.encode([v1])
+    rows = _unmasked_row_values(buf, H, W, 1, 0, 0)
+    assert sum(rows, []) == [(int(a) - int(b)) & 0xFFFFFFFF for a, b in zip(v1.ravel(), v0.ravel())]
+
+
+def test_mask_stage_off_on_a_scan_without_zeros_only_drops_the_class_words():
+    # no zero sample: the masked stream's rows carry all-zero class words
+    # (ceil(nw/16) per row) before the same blocks
+    rng = np.random.default_rng(32)
+    H, W = 4, 700
+    v = rng.integers(1, 50000, size=(H, W)).astype(np.uint16)
+    a = oracle.Codec(H, W, [(2, 1)], force_mode=0).encode([v])
+    b = oracle.Codec(H, W, [(2, 1)], force_mode=0, stages=1).encode([v])
+    ncls = ((W + 31) // 32 + 15) // 16
+    assert len(a) - len(b) == 4 * ncls * H
+    u32 = lambda buf, o: int.from_bytes(buf[o:o + 4], "little")
+    sa, sb = 24 + 20 + 8 * H, 24 + 20 + 8 * H
+    ba = bb = 0
+    for r in range(H):
+        ea, eb = u32(a, 24 + 20 + 8 * r), u32(b, 24 + 20 + 8 * r)
+        assert a[sa + ba:sa + ba + 4 * ncls] == bytes(4 * ncls)
+        assert a[sa + ba + 4 * ncls:sa + ea] == b[sb + bb:sb + eb]
+        assert u32(a, 24 + 20 + 8 * r + 4) == u32(b, 24 + 20 + 8 * r + 4)  # same carries
+        ba, bb = ea, eb
+
+
+@pytest.mark.parametrize("stages", range(8))
+@pytest.mark.parametrize("force", [-1, 0, 1])
+def test_round_trip_every_stage_set(stages, force):
+    rng = np.random.default_rng(40 + 3 * stages + force)
+    H, W = 5, 77
+    attrs = [(4, 3), (2, 1), (1, 2)]
+    enc = oracle.Codec(H, W, attrs, force_mode=force, stages=stages)
+    dec = oracle.Codec(H, W, attrs, stages=stages)
+    base = [random_scan(rng, H, W, s, 0.3, 1 << (8 * s)) for s, _ in attrs]
+    for t in range(4):
+        planes = []
+        for s, b in zip((4, 2, 1), base):
+            x = np.clip(b.astype(np.int64) + rng.integers(-3, 4, size=b.shape), 0, (1 << (8 * s)) - 1).astype(DT[s])
+            x[rng.random(x.shape) < 0.1] = 0
+            planes.append(x)
+        buf = enc.encode(planes)
+        out, n = dec.decode(buf)
+        assert n == len(buf)
+        for (s, P), x, o in zip(attrs, planes, out):
+            assert np.array_equal(o.astype(np.uint64), quantize_plane(x, P, s) * P)
+
+
+def test_stage_set_is_part_of_the_stream_header():
+    rng = np.random.default_rng(41)
+    v = random_scan(rng, 2, 64, 2, 0.2, 60000)
+    buf = oracle.Codec(2, 64, [(2, 1)], stages=3).encode([v])
+    with pytest.raises(oracle.OracleError):  # a decoder of the full codec refuses it
+        oracle.Codec(2, 64, [(2, 1)]).decode(buf)
+    with pytest.raises(ValueError):
+        oracle.Codec(2, 64, [(2, 1)], stages=8)
