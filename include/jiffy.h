@@ -22,8 +22,10 @@
  * little-endian, every section 4-byte aligned):
  *   stream header (before the first frame after create/reset), 16 + 8A bytes:
  *     "JFY1", u16 version = 1, u16 A, u32 H, u32 W,
- *     per attribute { u8 dtype_bytes, u8 zigzag variant = 1 (Eq. 1), u16 0,
- *                     u32 precision }   (Sec. III-A: precision is stored)
+ *     per attribute { u8 dtype_bytes, u8 zigzag variant (1 = Eq. 1, 0 =
+ *                     none), u8 stage flags (bit 0: no zero mask, bit 1:
+ *                     no delta), u8 0, u32 precision }
+ *                     (Sec. III-A: precision is stored)
  *   frame, one per scan: header 8 + 12A bytes
  *     u32 frame_bytes, u32 scan_index (frames since create/reset),
  *     per attribute { u8 mode (0 = I, 1 = P), 3 x u8 0, u32 section_bytes,
@@ -36,6 +38,11 @@
  *     1 = all valid bits set, 2 = literal follows), literal mask words,
  *     block headers {u8 b, u8 exceptions, u8 high bits, u8 0}, block bodies
  *     (low bits, exception positions, exception high bits).
+ *   A stream created with stage switches (jiffy_options.stages) leaves out
+ *   steps: without the mask stage row chunks have no mask part and every
+ *   sample is coded (frame nnz = H * W), without the delta the residuals are
+ *   packed directly (row carries are still recorded), without ZigZag the
+ *   32-bit two's complement words are packed.
  *
  * Errors: every function returns a jiffy_status; nothing aborts. A failed
  * call leaves the stream's state (previous scan, frame counter) unchanged.
@@ -74,16 +81,27 @@ typedef struct {
   uint32_t precision;
 } jiffy_attr_desc;
 
+/* Stage switches (jiffy_options.stages): each removes one step of the codec,
+ * for the ablated codecs of Sec. IV-H (Table IV). With force_mode = 0 as
+ * well, NO_MASK | NO_DELTA | NO_ZIGZAG is "SIMD-PFOR" alone, NO_MASK |
+ * NO_ZIGZAG is "Delta -> SIMD-PFOR", NO_MASK is "Delta -> ZigZag ->
+ * SIMD-PFOR" and 0 is "Mask -> Delta -> ZigZag -> SIMD-PFOR". */
+#define JIFFY_STAGE_NO_MASK 1u   /* no zero mask: every sample is coded, zeros too */
+#define JIFFY_STAGE_NO_DELTA 2u  /* residuals packed without the horizontal delta */
+#define JIFFY_STAGE_NO_ZIGZAG 4u /* deltas packed as 32-bit two's complement words */
+
 /* test_lines: number of scanlines of the trial compression (Sec. III-E;
  * Sec. IV-E uses 4); rows floor((2k+1)H/(2L)), k < L, >= 1. test_lines >= H
  * makes every row a test row: the brute-force choice between I and P over
  * the data sections (mask excluded), at about the cost of coding each scan
  * a second time. force_mode: -1 picks I or P per attribute and scan by
  * trial, 0 forces I, 1 forces P (the first frame after create/reset is
- * always I). */
+ * always I). stages: JIFFY_STAGE_* bits, 0 = the full codec; recorded in the
+ * stream header, and a decoder must be created with the same bits. */
 typedef struct {
   uint32_t test_lines;
   int32_t force_mode;
+  uint32_t stages;
 } jiffy_options;
 
 typedef struct jiffy_stream jiffy_stream;
@@ -91,7 +109,7 @@ typedef struct jiffy_stream jiffy_stream;
 /* Creates a codec stream on CUDA device `device`: the encoder or decoder of
  * one sensor's scan sequence with H x W planes and n_attr attributes.
  * 1 <= H <= 4096, 1 <= W <= 16384, 1 <= n_attr <= 64. opt may be NULL
- * (test_lines = 4, force_mode = -1). The stream owns its device state (the
+ * (test_lines = 4, force_mode = -1, stages = 0). The stream owns its device state (the
  * previous scan of every attribute, Sec. III-D) and scratch; *out receives
  * the handle. Errors: INVALID_ARG, NOMEM, CUDA. */
 jiffy_status jiffy_stream_create(jiffy_stream** out, jiffy_role role, uint32_t H, uint32_t W,
@@ -258,14 +276,16 @@ uint32_t jiffy_stream_kernel_times(const jiffy_stream* s, float* ms, uint32_t n)
  * library, shared by every call (calls that overlap on the GPU race on it).
  * The first call on each device looks up that array's address; make it before
  * any stream capture. Limits: n_attr <= 16, n_attr * H <= 16384, W <= 16384;
- * beyond them JIFFY_ERR_INVALID_ARG. Synchronizes cuda_stream. */
+ * beyond them JIFFY_ERR_INVALID_ARG. Frames of the full codec only (streams
+ * without stage switches; a stream header with stage flags is CORRUPT).
+ * Synchronizes cuda_stream. */
 jiffy_status jiffy_decode_frame_noalloc(const void* in, size_t in_len, uint32_t H, uint32_t W, uint32_t n_attr,
                                         const jiffy_attr_desc* attrs, uint32_t scan_index,
                                         const void* const* prev_planes, void* const* planes_out,
                                         void* cuda_stream);
 
-/* Copies src's previous scan and frame counter into dst (same H, W and
- * attributes, same device, any roles), so that dst continues src's stream.
+/* Copies src's previous scan and frame counter into dst (same H, W,
+ * attributes and stage switches, same device, any roles), so that dst continues src's stream.
  * Encoders and decoders hold the same state, the previous scan as decoded
  * (q * P, Sec. III-D), so a decoder can take over from an encoder (e.g. to
  * decode the frame the encoder codes next) and the other way round.

@@ -95,7 +95,7 @@ struct jiffy_stream {
   Workspace ws;
   jiffy_role role = JIFFY_ENCODER;
   uint32_t H = 0, W = 0, A = 0;
-  jiffy_options opt{4, -1};
+  jiffy_options opt{4, -1, 0};
   std::vector<AttrDev> attrs;
   AttrDev* d_attrs = nullptr;
   uint8_t* d_state[2] = {nullptr, nullptr};  // previous scan (as decoded, q * P), ping-pong
@@ -400,6 +400,7 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   uint32_t* sb = reinterpret_cast<uint32_t*>(h + u_sb);
   std::vector<uint64_t> key{1, n, (uint64_t)(uintptr_t)d, (uint64_t)(uintptr_t)h};
   std::vector<uint32_t> sig{1, max_W, log2_ceil(items)};
+  uint32_t staged = 0;
   uint32_t item_base = 0, sec_base = 0;
   for (uint32_t i = 0; i < n; i++) {
     EncJob& j = jobs[i];
@@ -424,7 +425,8 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     g.A = A;
     g.T = T;
     g.nw = (s->W + 31) / 32;
-    g.ncls = (g.nw + 15) / 16;
+    g.ncls = (s->opt.stages & jiffy::kStageNoMask) ? 0u : (g.nw + 15) / 16;
+    g.stages = s->opt.stages;
     g.frame0 = s->frame;
     g.shdr = s->frame == 0 ? stream_header_bytes(A) : 0u;
     g.fhdr = frame_header_bytes(A);
@@ -447,9 +449,12 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     sb[i] = sec_base;
     item_base += T * A * s->H;
     sec_base += T * A;
+    staged |= s->opt.stages ? 1u : 0u;
     key.push_back(((uint64_t)s->H << 32) | s->W);
     key.push_back(((uint64_t)A << 32) | T);
   }
+  key.push_back(staged);
+  sig.push_back(staged);
 
   jiffy::EncParams p{};
   p.n_seg = n;
@@ -470,6 +475,7 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   p.sec_bytes = reinterpret_cast<unsigned long long*>(d + o_secb);
   p.sec_nnz = reinterpret_cast<uint32_t*>(d + o_secn);
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
+  p.staged = staged;
   uint8_t* hres = h + h_res;
 
   // the whole call on one stream: upload, clear, kernels, results
@@ -591,6 +597,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   uint32_t* ib = reinterpret_cast<uint32_t*>(h + u_ib);
   std::vector<uint64_t> key{2, n, (uint64_t)(uintptr_t)d, (uint64_t)(uintptr_t)h};
   std::vector<uint32_t> sig{2, max_W, log2_ceil(items)};
+  uint32_t staged = 0;
   uint32_t item_base = 0;
   for (uint32_t i = 0; i < n; i++) {
     DecJob& j = jobs[i];
@@ -610,7 +617,8 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
     g.A = A;
     g.T = T;
     g.nw = (s->W + 31) / 32;
-    g.ncls = (g.nw + 15) / 16;
+    g.ncls = (s->opt.stages & jiffy::kStageNoMask) ? 0u : (g.nw + 15) / 16;
+    g.stages = s->opt.stages;
     g.frame0 = s->frame;
     g.fhdr = frame_header_bytes(A);
     g.check_shdr = s->frame == 0;
@@ -627,9 +635,12 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
     segs[i] = g;
     ib[i] = item_base;
     item_base += T * A * s->H;
+    staged |= s->opt.stages ? 1u : 0u;
     key.push_back(((uint64_t)s->H << 32) | s->W);
     key.push_back(((uint64_t)A << 32) | T);
   }
+  key.push_back(staged);
+  sig.push_back(staged);
 
   jiffy::DecParams p{};
   p.n_seg = n;
@@ -640,6 +651,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   p.done = reinterpret_cast<uint32_t*>(d + o_done);
   p.masks = reinterpret_cast<uint32_t*>(d + o_masks);
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
+  p.staged = staged;
   uint8_t* hres = h + h_res;
 
   auto enqueue = [&](cudaStream_t s, const jiffy::DecParams& pp, void* const* evs) -> int {
@@ -752,7 +764,7 @@ jiffy_status run_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream_t s
 }
 
 bool same_config(const jiffy_stream* a, const jiffy_stream* b) {
-  if (a->H != b->H || a->W != b->W || a->A != b->A) return false;
+  if (a->H != b->H || a->W != b->W || a->A != b->A || a->opt.stages != b->opt.stages) return false;
   for (uint32_t i = 0; i < a->A; i++)
     if (a->attrs[i].s != b->attrs[i].s || a->attrs[i].P != b->attrs[i].P) return false;
   return true;
@@ -792,9 +804,9 @@ jiffy_status jiffy_stream_create(jiffy_stream** out, jiffy_role role, uint32_t H
   if (role != JIFFY_ENCODER && role != JIFFY_DECODER) return JIFFY_ERR_INVALID_ARG;
   if (H == 0 || H > jiffy::kMaxH || W == 0 || W > jiffy::kMaxW || n_attr == 0 || n_attr > jiffy::kMaxAttr)
     return JIFFY_ERR_INVALID_ARG;
-  jiffy_options o{4, -1};
+  jiffy_options o{4, -1, 0};
   if (opt) o = *opt;
-  if (o.test_lines == 0 || o.force_mode < -1 || o.force_mode > 1)
+  if (o.test_lines == 0 || o.force_mode < -1 || o.force_mode > 1 || (o.stages & ~jiffy::kStageAll))
     return JIFFY_ERR_INVALID_ARG;
   for (uint32_t a = 0; a < n_attr; a++) {
     const uint32_t sz = attrs[a].dtype_bytes;

@@ -89,12 +89,15 @@ struct SecCache {
   unsigned long long sec;       // byte offset of the section (its row table)
 };
 
+// STAGED: the segments may have stage switches (else they are read as 0).
+template <bool STAGED>
 __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k, uint32_t* ring,
                                             uint32_t* patch, uint2* desc, uint8_t* mbytes, SecCache& sc) {
   const uint32_t si = find_seg(p.seg_item_base, p.n_seg, k);
   const DecSeg& sg = p.seg[si];
   const uint32_t lane = lane_id();
   const uint32_t H = sg.H, W = sg.W, A = sg.A, nw = sg.nw, ncls = sg.ncls;
+  const uint32_t stages = STAGED ? sg.stages : 0u;
   const uint32_t niter = ceil_div_u32(W, 256u);
   const uint32_t kl = k - sg.item_base;  // item within the segment
   // items of a segment are numbered attribute-major, (a, t, r): resident warps
@@ -159,7 +162,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
           ld_in_u32(sg.in, 8) != H || ld_in_u32(sg.in, 12) != W)
         bad = true;
       for (uint32_t aa = 0; aa < A && !bad; aa++) {
-        if (ld_in_u32(sg.in, 16 + 8ull * aa) != (sg.attrs[aa].s | (1u << 8)) ||
+        if (ld_in_u32(sg.in, 16 + 8ull * aa) != attr_header_word(sg.attrs[aa].s, stages) ||
             ld_in_u32(sg.in, 20 + 8ull * aa) != sg.attrs[aa].P)
           bad = true;
       }
@@ -242,12 +245,16 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   // ---- pass 1: own mask bytes (1 = zero sample) and nonzero counts. For P
   //      (Sec. III-D) the previous scan's mask comes from the mask words the
   //      previous frame's row wrote in this call, else from its samples.
+  //      Without the mask stage (no class words) every sample is coded.
   uint32_t cnt = 0;
   if (!bad) {
-    const uint8_t* pmask = (mode == 1u && t > 0)
+    const bool xor_prev = mode == 1u && !(stages & kStageNoMask);
+    const uint8_t* pmask = (xor_prev && t > 0)
                                ? reinterpret_cast<const uint8_t*>(p.masks + sg.mask_base + (size_t)(kl - H) * nw)
                                : nullptr;
-    uint8_t* omask = t + 1 < sg.T ? reinterpret_cast<uint8_t*>(p.masks + sg.mask_base + (size_t)kl * nw) : nullptr;
+    uint8_t* omask = (t + 1 < sg.T && !(stages & kStageNoMask))
+                         ? reinterpret_cast<uint8_t*>(p.masks + sg.mask_base + (size_t)kl * nw)
+                         : nullptr;
     for (uint32_t it = 0; it < niter; it++) {
       const uint32_t x0 = 256u * it + 8u * lane;
       const uint32_t j = x0 >> 5;
@@ -262,7 +269,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
         uint32_t mb = (X >> (x0 & 31u)) & 0xffu;
         if (pmask) {
           mb ^= __ldcg(pmask + (x0 >> 3));  // Sec. III-D: undo the XOR with the previous scan's mask
-        } else if (mode == 1u) {
+        } else if (xor_prev) {
           uint32_t pv[8];
           load8<true>(prow, S, x0, nv, vec_prev, pv);
           uint32_t pm = 0;
@@ -326,6 +333,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   //      previous pixel for P, x precision (Sec. III-A)
   if (!bad) {
     const uint32_t Pq = at.P;
+    const bool no_delta = (stages & kStageNoDelta) != 0u, no_zz = (stages & kStageNoZigzag) != 0u;
     const uint32_t last_word = clen / 4u - 1u;
     uint32_t erun = carry, blk = 0, unpacked = 0, kbase = 0;
     bool xbad = false;
@@ -383,8 +391,10 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
           const uint4 pt = reinterpret_cast<const uint4*>(patch)[lane];
           v0 |= pt.x; v1 |= pt.y; v2 |= pt.z; v3 |= pt.w;
         }
-        reinterpret_cast<uint4*>(ring)[((128u * blk + 4u * lane) & (kRing - 1u)) >> 2] =
-            make_uint4(unzigzag(v0), unzigzag(v1), unzigzag(v2), unzigzag(v3));
+        if (!no_zz) {
+          v0 = unzigzag(v0); v1 = unzigzag(v1); v2 = unzigzag(v2); v3 = unzigzag(v3);
+        }
+        reinterpret_cast<uint4*>(ring)[((128u * blk + 4u * lane) & (kRing - 1u)) >> 2] = make_uint4(v0, v1, v2, v3);
         unpacked += min(kBlockN, n - 128u * blk);
         blk++;
       }
@@ -393,19 +403,30 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
       if (xbad) break;
       uint32_t pv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
       if (mode == 1u && nv) load8<true>(prow, S, x0, nv, vec_prev, pv);
-      // residuals: running sum of the deltas from the step's start
-      uint32_t d[8], lsum = 0;
+      // residuals: running sum of the deltas from the step's start (without
+      // the delta stage the values are the residuals)
+      uint32_t d[8], ebase = 0;
+      if (!no_delta) {
+        uint32_t lsum = 0;
 #pragma unroll
-      for (int i = 0; i < 8; i++) {
-        const bool nzb = (nzm >> i) & 1u;
-        d[i] = nzb ? ring[kk & (kRing - 1u)] : 0u;
-        kk += nzb ? 1u : 0u;
-        lsum += d[i];
-        d[i] = lsum;
+        for (int i = 0; i < 8; i++) {
+          const bool nzb = (nzm >> i) & 1u;
+          d[i] = nzb ? ring[kk & (kRing - 1u)] : 0u;
+          kk += nzb ? 1u : 0u;
+          lsum += d[i];
+          d[i] = lsum;
+        }
+        uint32_t stot;
+        ebase = erun + warp_excl_scan(lsum, stot);
+        erun += stot;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+          const bool nzb = (nzm >> i) & 1u;
+          d[i] = nzb ? ring[kk & (kRing - 1u)] : 0u;
+          kk += nzb ? 1u : 0u;
+        }
       }
-      uint32_t stot;
-      const uint32_t ebase = erun + warp_excl_scan(lsum, stot);
-      erun += stot;
       uint32_t out[8];
 #pragma unroll
       for (int i = 0; i < 8; i++) out[i] = ((nzm >> i) & 1u) ? (ebase + d[i]) * Pq + pv[i] : 0u;
@@ -424,7 +445,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   if (lane == 0) atomicExch(p.done + k, 1u);
 }
 
-template <int WPC>
+template <int WPC, bool STAGED>
 __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t lane = lane_id();
@@ -442,7 +463,7 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
     if (kb >= p.n_items) break;
     const uint32_t kend = min(kb + p.items_per_ticket, p.n_items);
     for (uint32_t k = kb; k < kend; k++) {
-      decode_item(p, k, ring, patch, desc, mbytes, sc);
+      decode_item<STAGED>(p, k, ring, patch, desc, mbytes, sc);
     }
   }
 }
@@ -453,10 +474,11 @@ constexpr size_t kDecSmemAuto = 48 * 1024;  // per CTA when picking warps per CT
 constexpr size_t kDecSmemMax = 227 * 1024;
 
 template <int WPC>
-static cudaError_t dec_occupancy(size_t smem, int* per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_decode<WPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static cudaError_t dec_occupancy(size_t smem, bool staged, int* per_sm) {
+  auto f = staged ? k_decode<WPC, true> : k_decode<WPC, false>;
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_decode<WPC>, WPC * 32, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, f, WPC * 32, smem);
 }
 
 int decode_rows_launch(const DecParams& p, RowsLaunch* out) {
@@ -470,10 +492,11 @@ int decode_rows_launch(const DecParams& p, RowsLaunch* out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) {
-    if (wpc == 8) e = dec_occupancy<8>(smem, &per_sm);
-    else if (wpc == 4) e = dec_occupancy<4>(smem, &per_sm);
-    else if (wpc == 2) e = dec_occupancy<2>(smem, &per_sm);
-    else e = dec_occupancy<1>(smem, &per_sm);
+    const bool sd = p.staged != 0;
+    if (wpc == 8) e = dec_occupancy<8>(smem, sd, &per_sm);
+    else if (wpc == 4) e = dec_occupancy<4>(smem, sd, &per_sm);
+    else if (wpc == 2) e = dec_occupancy<2>(smem, sd, &per_sm);
+    else e = dec_occupancy<1>(smem, sd, &per_sm);
   }
   if (e != cudaSuccess) return (int)e;
   uint32_t ctas = (uint32_t)max(per_sm, 1);
@@ -497,10 +520,17 @@ int launch_decode(const DecParams& p0, void* stream, void* const* ev) {
   p.items_per_ticket = rl.items_per_ticket;
   const size_t smem = (size_t)rl.wpc * dec_warp_layout(p.max_W).bytes;
   if (ev) record_event(ev[0], st);
-  if (rl.wpc == 8) k_decode<8><<<rl.grid, 8 * 32, smem, st>>>(p);
-  else if (rl.wpc == 4) k_decode<4><<<rl.grid, 4 * 32, smem, st>>>(p);
-  else if (rl.wpc == 2) k_decode<2><<<rl.grid, 2 * 32, smem, st>>>(p);
-  else k_decode<1><<<rl.grid, 32, smem, st>>>(p);
+  if (p.staged) {
+    if (rl.wpc == 8) k_decode<8, true><<<rl.grid, 8 * 32, smem, st>>>(p);
+    else if (rl.wpc == 4) k_decode<4, true><<<rl.grid, 4 * 32, smem, st>>>(p);
+    else if (rl.wpc == 2) k_decode<2, true><<<rl.grid, 2 * 32, smem, st>>>(p);
+    else k_decode<1, true><<<rl.grid, 32, smem, st>>>(p);
+  } else {
+    if (rl.wpc == 8) k_decode<8, false><<<rl.grid, 8 * 32, smem, st>>>(p);
+    else if (rl.wpc == 4) k_decode<4, false><<<rl.grid, 4 * 32, smem, st>>>(p);
+    else if (rl.wpc == 2) k_decode<2, false><<<rl.grid, 2 * 32, smem, st>>>(p);
+    else k_decode<1, false><<<rl.grid, 32, smem, st>>>(p);
+  }
   if (ev) record_event(ev[1], st);
   return (int)cudaGetLastError();
 }

@@ -100,11 +100,12 @@ __device__ __forceinline__ void st8(uint8_t* row, uint32_t s, uint32_t x0, uint3
 // ---------------------------------------------------------------------------
 // Pass A (one row): returns the number n of nonzero samples; their residuals
 // go to zb in row-major order (swizzled), the coded mask bytes (M, or M xor
-// M_prev for P) to mb, and, for the call's last scan, q * P to st_row.
+// M_prev for P) to mb, and, for the call's last scan, q * P to st_row. kz =
+// 0xff, or 0 without the mask stage (every sample kept, mask bytes 0).
 // ---------------------------------------------------------------------------
 template <bool PM, int QU, uint32_t S>
 __device__ __forceinline__ uint32_t pass_a(const uint8_t* cur, const uint8_t* prv, uint8_t* st_row, const AttrDev& at,
-                                           uint32_t W, uint32_t* zb, uint8_t* mb) {
+                                           uint32_t W, uint32_t kz, uint32_t* zb, uint8_t* mb) {
   const uint32_t lane = lane_id(), s = at.s;
   const bool vc = vec_ok(cur, s), vp = PM && vec_ok(prv, s), vs = st_row && vec_ok(st_row, s);
   const uint32_t Wm = (W + 31u) & ~31u;
@@ -129,9 +130,10 @@ __device__ __forceinline__ uint32_t pass_a(const uint8_t* cur, const uint8_t* pr
         e[i] = q;
       }
     }
+    zm &= kz;
     const uint32_t vm = (1u << nv) - 1u;
     const uint32_t nz = ~zm & vm;
-    if (x0 < Wm) mb[x0 >> 3] = (uint8_t)((PM ? (zm ^ pm) : zm) & vm);
+    if (x0 < Wm) mb[x0 >> 3] = (uint8_t)((PM ? (zm ^ (pm & kz)) : zm) & vm);
     if (st_row && nv) {  // the next call's previous scan, dequantized as the decoder holds it
       uint32_t sv[8];
 #pragma unroll
@@ -152,11 +154,11 @@ __device__ __forceinline__ uint32_t pass_a(const uint8_t* cur, const uint8_t* pr
   return n;
 }
 
-// Pass A of the trial: the residuals of the row's nonzero samples both ways
-// (I to zi, P to zp).
+// Pass A of the trial: the residuals of the row's nonzero samples (all
+// samples with kz = 0) both ways (I to zi, P to zp).
 template <int QU>
 __device__ __forceinline__ uint32_t pass_a_trial(const uint8_t* cur, const uint8_t* prv, const AttrDev at, uint32_t W,
-                                              uint32_t* zi, uint32_t* zp) {
+                                              uint32_t kz, uint32_t* zi, uint32_t* zp) {
   const uint32_t lane = lane_id(), S = at.s;
   const bool vc = vec_ok(cur, S), vp = vec_ok(prv, S);
   uint32_t n = 0;
@@ -173,7 +175,7 @@ __device__ __forceinline__ uint32_t pass_a_trial(const uint8_t* cur, const uint8
       pv[i] = v[i] - quant<QU>(pv[i], at);
       zm |= (v[i] == 0u ? 1u : 0u) << i;
     }
-    const uint32_t nz = ~zm & ((1u << nv) - 1u);
+    const uint32_t nz = ~(zm & kz) & ((1u << nv) - 1u);
     uint32_t tot;
     uint32_t kk = n + warp_excl_scan(__popc(nz), tot);
 #pragma unroll
@@ -189,11 +191,12 @@ __device__ __forceinline__ uint32_t pass_a_trial(const uint8_t* cur, const uint8
   return n;
 }
 
-// The residuals (I and, with prv, P) of the last nonzero sample among the
-// row's last max_steps 256-pixel steps. Returns false if there is none.
+// The residuals (I and, with prv, P) of the last nonzero sample (with all,
+// the last sample) among the row's last max_steps 256-pixel steps. Returns
+// false if there is none.
 template <int QU>
 __device__ __noinline__ bool row_last(const uint8_t* cur, const uint8_t* prv, const AttrDev at, uint32_t W,
-                                      uint32_t max_steps, uint32_t* e_i, uint32_t* e_p) {
+                                      uint32_t max_steps, bool all, uint32_t* e_i, uint32_t* e_p) {
   const uint32_t lane = lane_id(), S = at.s;
   const uint32_t nsteps = ceil_div_u32(W, kStepPx);
   const bool vc = vec_ok(cur, S), vp = prv && vec_ok(prv, S);
@@ -208,7 +211,7 @@ __device__ __noinline__ bool row_last(const uint8_t* cur, const uint8_t* prv, co
 #pragma unroll
     for (int i = 0; i < 8; i++) {
       const uint32_t q = quant<QU>(v[i], at);
-      if ((uint32_t)i < nv && q != 0u) {
+      if ((uint32_t)i < nv && (q != 0u || all)) {
         has = true;
         li = q;
         lp = prv ? q - quant<QU>(pv[i], at) : q;
@@ -225,11 +228,12 @@ __device__ __noinline__ bool row_last(const uint8_t* cur, const uint8_t* prv, co
   return false;
 }
 
-// Repeats the last residual from n up to the end of pass B1's last step, so
-// that those slots delta-code to 0 (and count as zero-width values).
-__device__ __forceinline__ void fill_tail(uint32_t* zb, uint32_t n) {
+// Repeats the last residual (0 without the delta stage) from n up to the end
+// of pass B1's last step, so that those slots code to 0 (and count as
+// zero-width values).
+__device__ __forceinline__ void fill_tail(uint32_t* zb, uint32_t n, bool no_delta) {
   if (n == 0) return;
-  const uint32_t last = zb[swz(n - 1)];
+  const uint32_t last = no_delta ? 0u : zb[swz(n - 1)];
   const uint32_t end = (n + kStepVal - 1) / kStepVal * kStepVal;
   for (uint32_t k = n + lane_id(); k < end; k += 32u) zb[swz(k)] = last;
   __syncwarp();
@@ -246,10 +250,11 @@ __device__ __forceinline__ void fill_tail(uint32_t* zb, uint32_t n) {
 // bit-sliced additions across the block's 4 lanes give 8 planes (counts <=
 // 128). Each lane then prices the candidates b = j, j+4, ... (j = lane & 3).
 // meta[g] = {b | e << 8 | hb << 16, body bytes}. Returns the sum over blocks
-// of header + body bytes.
+// of header + body bytes. st: the stream's stage switches (delta and ZigZag
+// may be off).
 // ---------------------------------------------------------------------------
 template <bool WRITE>
-__device__ __forceinline__ uint32_t pass_b1(uint32_t* zb, uint32_t n, uint32_t carry, uint2* meta) {
+__device__ __forceinline__ uint32_t pass_b1(uint32_t* zb, uint32_t n, uint32_t carry, uint2* meta, uint32_t st) {
   const uint32_t lane = lane_id(), j = lane & 3u;
   uint32_t pred_step = carry;  // the residual before the step's first value
   uint32_t total = 0;
@@ -267,8 +272,16 @@ __device__ __forceinline__ uint32_t pass_b1(uint32_t* zb, uint32_t n, uint32_t c
     pred_step = __shfl_sync(0xffffffffu, z[31], 31);
     // delta (Sec. III-C) and ZigZag (Eq. 1); values past n repeat the last
     // residual (fill_tail), so their ZigZag values are 0
+    if (!(st & (kStageNoDelta | kStageNoZigzag))) {
 #pragma unroll
-    for (int i = 31; i >= 0; i--) z[i] = zigzag(z[i] - (i ? z[i - 1] : pred));
+      for (int i = 31; i >= 0; i--) z[i] = zigzag(z[i] - (i ? z[i - 1] : pred));
+    } else {  // ablated codecs (Sec. IV-H); values past n are 0 without the delta
+#pragma unroll
+      for (int i = 31; i >= 0; i--) {
+        const uint32_t d = (st & kStageNoDelta) ? z[i] : z[i] - (i ? z[i - 1] : pred);
+        z[i] = (st & kStageNoZigzag) ? d : zigzag(d);
+      }
+    }
     if (WRITE) {
 #pragma unroll
       for (uint32_t c = 0; c < 8; c++) sp[c ^ (seg & 7u)] = make_uint4(z[4 * c], z[4 * c + 1], z[4 * c + 2], z[4 * c + 3]);
@@ -510,6 +523,8 @@ __global__ void __launch_bounds__(32) k_trial(EncParams p) {
   const size_t rowb = (size_t)W * at.s;
   const uint8_t* cur = sg.cur[ta];
   const uint8_t* prv = sg.prev[ta];
+  const uint32_t st = sg.stages;
+  const bool all = (st & kStageNoMask) != 0u;
   uint32_t* zi = smem;
   uint32_t* zp = smem + ((W + kStepVal - 1) / kStepVal) * kStepVal;
   // carry: the last residual of the nearest earlier test row that has one
@@ -518,22 +533,23 @@ __global__ void __launch_bounds__(32) k_trial(EncParams p) {
     const uint8_t* c0 = cur + test_row(k) * rowb;
     const uint8_t* p0 = prv + test_row(k) * rowb;
     bool f;
-    if (at.qkind == 0) f = row_last<0>(c0, p0, at, W, 0xffffffffu, &ci, &cp);
-    else if (at.qkind == 1) f = row_last<1>(c0, p0, at, W, 0xffffffffu, &ci, &cp);
-    else f = row_last<2>(c0, p0, at, W, 0xffffffffu, &ci, &cp);
+    if (at.qkind == 0) f = row_last<0>(c0, p0, at, W, 0xffffffffu, all, &ci, &cp);
+    else if (at.qkind == 1) f = row_last<1>(c0, p0, at, W, 0xffffffffu, all, &ci, &cp);
+    else f = row_last<2>(c0, p0, at, W, 0xffffffffu, all, &ci, &cp);
     if (f) break;
   }
   const uint8_t* c1 = cur + test_row(ti) * rowb;
   const uint8_t* p1 = prv + test_row(ti) * rowb;
   uint32_t n;
-  if (at.qkind == 0) n = pass_a_trial<0>(c1, p1, at, W, zi, zp);
-  else if (at.qkind == 1) n = pass_a_trial<1>(c1, p1, at, W, zi, zp);
-  else n = pass_a_trial<2>(c1, p1, at, W, zi, zp);
+  const uint32_t kz = all ? 0u : 0xffu;
+  if (at.qkind == 0) n = pass_a_trial<0>(c1, p1, at, W, kz, zi, zp);
+  else if (at.qkind == 1) n = pass_a_trial<1>(c1, p1, at, W, kz, zi, zp);
+  else n = pass_a_trial<2>(c1, p1, at, W, kz, zi, zp);
   __syncwarp();
-  fill_tail(zi, n);
-  fill_tail(zp, n);
-  const uint32_t cost_i = pass_b1<false>(zi, n, ci, nullptr);
-  const uint32_t cost_p = pass_b1<false>(zp, n, cp, nullptr);
+  fill_tail(zi, n, st & kStageNoDelta);
+  fill_tail(zp, n, st & kStageNoDelta);
+  const uint32_t cost_i = pass_b1<false>(zi, n, ci, nullptr, st);
+  const uint32_t cost_p = pass_b1<false>(zp, n, cp, nullptr, st);
   if (lane_id() == 0) {
     atomicAdd(p.cost + 2 * gs, cost_i);
     atomicAdd(p.cost + 2 * gs + 1, cost_p);
@@ -574,17 +590,18 @@ struct EncWarp {
   uint32_t* xhv;
 };
 
-// The last nonzero sample among the 8 (nv valid) in v / pv, across the warp:
-// its residual (P: q - q', I: q). Returns false if there is none.
+// The last nonzero sample (with all, the last sample) among the 8 (nv valid)
+// in v / pv, across the warp: its residual (P: q - q', I: q). Returns false
+// if there is none.
 template <int QU>
 __device__ __forceinline__ bool tail_residual(const uint32_t (&v)[8], const uint32_t (&pv)[8], uint32_t nv, bool pm,
-                                              const AttrDev& at, uint32_t& e_last) {
+                                              bool all, const AttrDev& at, uint32_t& e_last) {
   bool has = false;
   uint32_t last = 0;
 #pragma unroll
   for (int i = 0; i < 8; i++) {
     const uint32_t q = quant<QU>(v[i], at);
-    if ((uint32_t)i < nv && q != 0u) {
+    if ((uint32_t)i < nv && (q != 0u || all)) {
       has = true;
       last = pm ? q - quant<QU>(pv[i], at) : q;
     }
@@ -597,20 +614,26 @@ __device__ __forceinline__ bool tail_residual(const uint32_t (&v)[8], const uint
 
 template <bool PM, int QU>
 __device__ __forceinline__ uint32_t pass_a_any(const uint8_t* cur, const uint8_t* prv, uint8_t* st_row,
-                                               const AttrDev& at, uint32_t W, uint32_t* zb, uint8_t* mb) {
+                                               const AttrDev& at, uint32_t W, uint32_t kz, uint32_t* zb,
+                                               uint8_t* mb) {
   if constexpr (QU == 2) {
-    return pass_a<PM, QU, 0>(cur, prv, st_row, at, W, zb, mb);
+    return pass_a<PM, QU, 0>(cur, prv, st_row, at, W, kz, zb, mb);
   } else {
-    if (at.s == 4) return pass_a<PM, QU, 4>(cur, prv, st_row, at, W, zb, mb);
-    if (at.s == 2) return pass_a<PM, QU, 2>(cur, prv, st_row, at, W, zb, mb);
-    return pass_a<PM, QU, 1>(cur, prv, st_row, at, W, zb, mb);
+    if (at.s == 4) return pass_a<PM, QU, 4>(cur, prv, st_row, at, W, kz, zb, mb);
+    if (at.s == 2) return pass_a<PM, QU, 2>(cur, prv, st_row, at, W, kz, zb, mb);
+    return pass_a<PM, QU, 1>(cur, prv, st_row, at, W, kz, zb, mb);
   }
 }
 
+// STAGED: the segments may have stage switches (else they are read as 0 and
+// the full codec's code is all that is compiled in).
+template <bool STAGED>
 __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k, const EncWarp& w) {
   const EncSeg& sg = p.seg[find_seg(p.seg_item_base, p.n_seg, k)];
   const uint32_t lane = lane_id();
-  const uint32_t H = sg.H, W = sg.W, A = sg.A, nw = sg.nw, ncls = sg.ncls;
+  const uint32_t H = sg.H, W = sg.W, A = sg.A, ncls = sg.ncls;
+  const uint32_t nw = (!STAGED || ncls) ? sg.nw : 0u;  // coded mask words (none without the mask stage)
+  const uint32_t st = STAGED ? sg.stages : 0u, kz = (st & kStageNoMask) ? 0u : 0xffu;
   const uint32_t kl = k - sg.item_base;  // item within the segment, attribute-major (enc_item)
   const uint32_t r = kl % H, at_idx = kl / H, a = at_idx / sg.T, t = at_idx % sg.T;
   const uint32_t ta = t * A + a;     // section (scan t, attribute a)
@@ -648,28 +671,28 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   // ---- pass A
   uint32_t n;
   if (mode) {
-    if (qk == 0) n = pass_a_any<true, 0>(cur, prv, st_row, at, W, w.zb, w.mb);
-    else if (qk == 1) n = pass_a_any<true, 1>(cur, prv, st_row, at, W, w.zb, w.mb);
-    else n = pass_a_any<true, 2>(cur, prv, st_row, at, W, w.zb, w.mb);
+    if (qk == 0) n = pass_a_any<true, 0>(cur, prv, st_row, at, W, kz, w.zb, w.mb);
+    else if (qk == 1) n = pass_a_any<true, 1>(cur, prv, st_row, at, W, kz, w.zb, w.mb);
+    else n = pass_a_any<true, 2>(cur, prv, st_row, at, W, kz, w.zb, w.mb);
   } else {
-    if (qk == 0) n = pass_a_any<false, 0>(cur, nullptr, st_row, at, W, w.zb, w.mb);
-    else if (qk == 1) n = pass_a_any<false, 1>(cur, nullptr, st_row, at, W, w.zb, w.mb);
-    else n = pass_a_any<false, 2>(cur, nullptr, st_row, at, W, w.zb, w.mb);
+    if (qk == 0) n = pass_a_any<false, 0>(cur, nullptr, st_row, at, W, kz, w.zb, w.mb);
+    else if (qk == 1) n = pass_a_any<false, 1>(cur, nullptr, st_row, at, W, kz, w.zb, w.mb);
+    else n = pass_a_any<false, 2>(cur, nullptr, st_row, at, W, kz, w.zb, w.mb);
   }
   __syncwarp();
   const uint32_t last_e = n ? w.zb[swz(n - 1)] : 0u;
   if (lane == 0) {  // this row's last residual, for the rows after it
     st_publish(p.st_carry + k, kStAgg | ((unsigned long long)(n ? 1 : 0) << 32) | last_e);
   }
-  fill_tail(w.zb, n);
+  fill_tail(w.zb, n, st & kStageNoDelta);
 
   // ---- delta carry
   uint32_t carry = 0;
   bool known = r == 0;  // e[-1] = 0 at the start of the attribute-scan
   if (r > 0) {
-    if (qk == 0) known = tail_residual<0>(tv, tpv, tnv, prv != nullptr, at, carry);
-    else if (qk == 1) known = tail_residual<1>(tv, tpv, tnv, prv != nullptr, at, carry);
-    else known = tail_residual<2>(tv, tpv, tnv, prv != nullptr, at, carry);
+    if (qk == 0) known = tail_residual<0>(tv, tpv, tnv, prv != nullptr, kz == 0u, at, carry);
+    else if (qk == 1) known = tail_residual<1>(tv, tpv, tnv, prv != nullptr, kz == 0u, at, carry);
+    else known = tail_residual<2>(tv, tpv, tnv, prv != nullptr, kz == 0u, at, carry);
   }
   if (!known) {  // the previous rows' "last residual" words decide
     const bool ok = lookback_last(p.st_carry, k, sec_start, carry);
@@ -694,7 +717,7 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
 
   // ---- pass B1: delta, ZigZag, block widths
   const uint32_t nb = ceil_div_u32(n, kBlockN);
-  pass_b1<true>(w.zb, n, carry, w.meta);
+  pass_b1<true>(w.zb, n, carry, w.meta, st);
   __syncwarp();
   // body offsets: exclusive prefix of the block bytes (lane l: 4l..4l+3)
   uint32_t body = 0;
@@ -752,7 +775,7 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   __syncwarp();
 }
 
-template <int WPC>
+template <int WPC, bool STAGED>
 __global__ void __launch_bounds__(WPC * 32, 24 / WPC) k_encode(EncParams p) {
   extern __shared__ __align__(16) uint32_t smem[];
   const uint32_t lane = lane_id();
@@ -769,7 +792,7 @@ __global__ void __launch_bounds__(WPC * 32, 24 / WPC) k_encode(EncParams p) {
     if (lane == 0) k = atomicAdd(p.ticket, 1u);
     k = __shfl_sync(0xffffffffu, k, 0);
     if (k >= p.n_items) break;
-    encode_item(p, k, w);
+    encode_item<STAGED>(p, k, w);
   }
 }
 
@@ -895,7 +918,7 @@ __global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
       put_u32_guarded(out, cap, 8, H, sg.err);
       put_u32_guarded(out, cap, 12, sg.W, sg.err);
       for (uint32_t aa = 0; aa < A; aa++) {
-        put_u32_guarded(out, cap, 16 + 8ull * aa, sg.attrs[aa].s | (1u << 8), sg.err);
+        put_u32_guarded(out, cap, 16 + 8ull * aa, attr_header_word(sg.attrs[aa].s, sg.stages), sg.err);
         put_u32_guarded(out, cap, 20 + 8ull * aa, sg.attrs[aa].P, sg.err);
       }
     }
@@ -908,10 +931,11 @@ constexpr size_t kRowsSmemAuto = 100 * 1024;  // per CTA when picking warps per 
 constexpr size_t kRowsSmemMax = 227 * 1024;
 
 template <int WPC>
-static cudaError_t rows_occupancy(size_t smem, int* per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(k_encode<WPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static cudaError_t rows_occupancy(size_t smem, bool staged, int* per_sm) {
+  auto f = staged ? k_encode<WPC, true> : k_encode<WPC, false>;
+  cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_encode<WPC>, WPC * 32, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, f, WPC * 32, smem);
 }
 
 int encode_rows_launch(const EncParams& p, RowsLaunch* out) {
@@ -925,9 +949,9 @@ int encode_rows_launch(const EncParams& p, RowsLaunch* out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess) {
-    if (wpc == 4) e = rows_occupancy<4>(smem, &per_sm);
-    else if (wpc == 2) e = rows_occupancy<2>(smem, &per_sm);
-    else e = rows_occupancy<1>(smem, &per_sm);
+    if (wpc == 4) e = rows_occupancy<4>(smem, p.staged != 0, &per_sm);
+    else if (wpc == 2) e = rows_occupancy<2>(smem, p.staged != 0, &per_sm);
+    else e = rows_occupancy<1>(smem, p.staged != 0, &per_sm);
   }
   if (e != cudaSuccess) return (int)e;
   uint32_t ctas = (uint32_t)max(per_sm, 1);
@@ -960,9 +984,15 @@ int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   if (p.trial_rows) k_trial<<<p.n_sec * p.trial_rows, 32, s_trial, st>>>(p);
   mark(1);
   const size_t smem = (size_t)rl.wpc * enc_warp_layout(p.max_W).bytes;
-  if (rl.wpc == 4) k_encode<4><<<rl.grid, 4 * 32, smem, st>>>(p);
-  else if (rl.wpc == 2) k_encode<2><<<rl.grid, 2 * 32, smem, st>>>(p);
-  else k_encode<1><<<rl.grid, 32, smem, st>>>(p);
+  if (p.staged) {
+    if (rl.wpc == 4) k_encode<4, true><<<rl.grid, 4 * 32, smem, st>>>(p);
+    else if (rl.wpc == 2) k_encode<2, true><<<rl.grid, 2 * 32, smem, st>>>(p);
+    else k_encode<1, true><<<rl.grid, 32, smem, st>>>(p);
+  } else {
+    if (rl.wpc == 4) k_encode<4, false><<<rl.grid, 4 * 32, smem, st>>>(p);
+    else if (rl.wpc == 2) k_encode<2, false><<<rl.grid, 2 * 32, smem, st>>>(p);
+    else k_encode<1, false><<<rl.grid, 32, smem, st>>>(p);
+  }
   mark(2);
   k_sec_sizes<<<p.n_sec, kThreads, 0, st>>>(p);
   k_place<<<p.n_sec * kPlaceSplit, kThreads, s_place, st>>>(p);

@@ -17,7 +17,8 @@ namespace jiffy {
 
 struct EncSeg {
   uint32_t H, W, A, T;
-  uint32_t nw, ncls;             // mask words per row, class words per row
+  uint32_t nw, ncls;             // mask words per row, class words per row (0 without the mask stage)
+  uint32_t stages;               // kStage* switches of the stream
   uint32_t frame0;               // scan index of the segment's first frame
   uint32_t shdr;                 // stream header bytes at the start of out (0 or 16 + 8A)
   uint32_t fhdr;                 // frame header bytes (8 + 12A)
@@ -58,11 +59,13 @@ struct EncParams {
   uint32_t* ticket;
   uint32_t wpc;                  // rows kernel: warps per CTA (1, 2, 4; 0 = by shared memory)
   uint32_t ctas_per_sm;          // rows kernel: resident CTAs per SM (0 = occupancy limit)
+  uint32_t staged;               // 1 if a segment has stage switches (the rows kernel that reads them)
 };
 
 struct DecSeg {
   uint32_t H, W, A, T;
-  uint32_t nw, ncls;
+  uint32_t nw, ncls;             // as in EncSeg
+  uint32_t stages;
   uint32_t frame0;
   uint32_t fhdr;
   uint32_t check_shdr;           // validate the stream header at in[0]
@@ -90,6 +93,7 @@ struct DecParams {
   uint32_t wpc;                  // warps per CTA (1, 2, 4, 8; 0 = by shared memory)
   uint32_t ctas_per_sm;          // resident CTAs per SM (0 = occupancy limit)
   uint32_t items_per_ticket;     // row items a warp takes per ticket (0 = 4)
+  uint32_t staged;               // as in EncParams
 };
 
 // Launch configuration of a rows kernel as resolved for given parameters

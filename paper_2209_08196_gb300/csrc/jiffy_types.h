@@ -19,6 +19,16 @@ constexpr uint32_t kMaxH = 4096;       // rows
 constexpr uint32_t kMaxAttr = 64;
 constexpr uint32_t kBlockN = 128;      // values per packing block (Sec. II frames of 128)
 
+// Stage switches of a stream: each removes one step of the codec, for the
+// ablated codecs of Sec. IV-H (Table IV). 0 = the full codec.
+enum : uint32_t { kStageNoMask = 1u, kStageNoDelta = 2u, kStageNoZigzag = 4u, kStageAll = 7u };
+
+// First word of an attribute's stream-header entry: dtype bytes, ZigZag
+// variant (1 = Eq. 1, 0 = none), stage flags (no mask | no delta), 0.
+JIFFY_HD inline uint32_t attr_header_word(uint32_t s, uint32_t stages) {
+  return s | (((stages & kStageNoZigzag) ? 0u : 1u) << 8) | ((stages & (kStageNoMask | kStageNoDelta)) << 16);
+}
+
 // bits of the device error word
 enum : uint32_t { kErrCorrupt = 1u, kErrCapacity = 2u, kErrTimeout = 4u };
 

@@ -37,7 +37,13 @@ class _AttrDesc(ctypes.Structure):
 
 
 class _Options(ctypes.Structure):
-    _fields_ = [("test_lines", ctypes.c_uint32), ("force_mode", ctypes.c_int32)]
+    _fields_ = [("test_lines", ctypes.c_uint32), ("force_mode", ctypes.c_int32), ("stages", ctypes.c_uint32)]
+
+
+# stage switches (jiffy_options.stages): the ablated codecs of Sec. IV-H
+STAGE_NO_MASK = 1
+STAGE_NO_DELTA = 2
+STAGE_NO_ZIGZAG = 4
 
 
 _L = None
@@ -158,10 +164,10 @@ class Handle:
 
 
 def jiffy_stream_create(role: int, H: int, W: int, attrs, test_lines: int = 4, force_mode: int = -1,
-                        device: int = 0) -> Handle:
+                        device: int = 0, stages: int = 0) -> Handle:
     L = _lib()
     h = ctypes.c_void_p()
-    opt = _Options(test_lines, force_mode)
+    opt = _Options(test_lines, force_mode, stages)
     st = L.jiffy_stream_create(ctypes.byref(h), role, H, W, len(attrs), _attrs(attrs), ctypes.byref(opt), device)
     if st != 0:
         raise JiffyError(st, "jiffy_stream_create")

@@ -43,6 +43,8 @@ class SensorConfig:
     precisions: tuple = (10,)
     n_scans: int = 16
     dropout: float = 0.08          # i.i.d. dropout probability
+    persistent_dropout: float = 0.0  # share of the dropouts on a fixed pixel set (same every scan)
+    range_noise_mm: float = 0.0    # Gaussian range noise, standard deviation in mm
     target_zero_frac: float | None = None   # tune dropouts so range has this zero fraction
     disc_zero_frac: float = 0.0    # clustered dropouts: discs of radius 5..40 px
     speed_mps: float = 10.0        # forward motion along +x
@@ -141,6 +143,12 @@ class ScanSequence:
         el = np.radians(np.linspace(22.5, -22.5, H)) if H > 1 else np.zeros(1)
         self._el = torch.tensor(el, dtype=torch.float32, device=self.device)
         self._az0 = torch.arange(W, dtype=torch.float32, device=self.device) * (2 * math.pi / W)
+        # pixels that return nothing in every scan (persistent dropouts): a fixed
+        # uniform draw per stream, thresholded by the scan's dropout rate
+        self._persist_u = None
+        if cfg.persistent_dropout > 0:
+            gp = torch.Generator(device="cpu").manual_seed(int(cfg.seed) * 7919 + 17)
+            self._persist_u = torch.rand((H, W), generator=gp)
 
     # -- geometry -----------------------------------------------------------
     def _cast(self, t: int):
@@ -206,12 +214,18 @@ class ScanSequence:
         if cfg.target_zero_frac is not None:
             f0 = 1.0 - float(valid.float().mean())
             p = max(0.0, (cfg.target_zero_frac - f0) / max(1e-9, 1.0 - f0))
-        if p > 0:
+        if p > 0 and self._persist_u is not None:
+            drop |= self._persist_u < p * cfg.persistent_dropout
+            drop |= torch.rand((H, W), generator=g) < p * (1.0 - cfg.persistent_dropout)
+        elif p > 0:
             drop |= torch.rand((H, W), generator=g) < p
         if cfg.disc_zero_frac > 0:
             drop |= self._discs(g, cfg.disc_zero_frac)
         valid = valid & ~drop.to(dev)
-        r_mm = torch.where(valid, torch.round(best * 1000.0), torch.zeros_like(best))
+        r_m = best
+        if cfg.range_noise_mm > 0:
+            r_m = best + torch.randn((H, W), generator=g).to(dev) * (cfg.range_noise_mm / 1000.0)
+        r_mm = torch.where(valid, torch.round(r_m * 1000.0).clamp_min(1.0), torch.zeros_like(best))
         out = []
         for a in cfg.attrs:
             if a == RANGE:

@@ -19,10 +19,10 @@ def to_np(t: torch.Tensor, s: int) -> np.ndarray:
 
 
 class GpuCodec:
-    def __init__(self, H, W, attrs, test_lines=4, force_mode=-1):
+    def __init__(self, H, W, attrs, test_lines=4, force_mode=-1, stages=0):
         self.H, self.W, self.attrs = H, W, attrs
-        self.enc = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, attrs, test_lines, force_mode)
-        self.dec = J.jiffy_stream_create(J.JIFFY_DECODER, H, W, attrs, test_lines, force_mode)
+        self.enc = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, attrs, test_lines, force_mode, stages=stages)
+        self.dec = J.jiffy_stream_create(J.JIFFY_DECODER, H, W, attrs, test_lines, force_mode, stages=stages)
 
     def encode(self, planes):
         dev = [to_dev(p) for p in planes]

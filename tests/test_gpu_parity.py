@@ -40,12 +40,12 @@ def drift(rng, base, s, amount, zero_frac=0.05):
     return x
 
 
-def check_stream(H, W, attrs, scans, test_lines=4, force_mode=-1, seq=False):
+def check_stream(H, W, attrs, scans, test_lines=4, force_mode=-1, seq=False, stages=0):
     """Encodes scans with oracle and GPU, compares bytes frame by frame and
     the decoded planes; seq=True uses the one-pass sequence entry points."""
-    ref = oracle.Codec(H, W, attrs, test_lines, force_mode)
-    refd = oracle.Codec(H, W, attrs, test_lines, force_mode)
-    gpu = GpuCodec(H, W, attrs, test_lines, force_mode)
+    ref = oracle.Codec(H, W, attrs, test_lines, force_mode, stages)
+    refd = oracle.Codec(H, W, attrs, test_lines, force_mode, stages)
+    gpu = GpuCodec(H, W, attrs, test_lines, force_mode, stages)
     ref_frames = [ref.encode(s) for s in scans]
     if seq:
         buf, offs = gpu.encode_seq(scans)
@@ -67,7 +67,8 @@ def check_stream(H, W, attrs, scans, test_lines=4, force_mode=-1, seq=False):
 @pytest.mark.parametrize("name", golden_io.names())
 def test_golden_streams_on_gpu(name):
     H, W, attrs, frames = golden_io.load(name)
-    gpu = GpuCodec(H, W, attrs)
+    opt = golden_io.options(name)
+    gpu = GpuCodec(H, W, attrs, 4, opt["force_mode"], opt["stages"])
     for f in frames:
         b = gpu.encode(f["in"])
         assert b == f["bytes"], (b.hex(" "), f["bytes"].hex(" "))
@@ -286,3 +287,30 @@ def test_full_size_multi_attribute_sequence_sampled_against_oracle():
             assert bytes(got) == want, "frame %d" % t
         else:
             assert host[:offs[1]] == want
+
+
+@pytest.mark.parametrize("stages", range(1, 8))
+@pytest.mark.parametrize("force", [-1, 0, 1])
+def test_ablated_codecs_match_oracle(stages, force):
+    # the stage switches of the Sec. IV-H ablations: bytes and planes equal
+    # the oracle's for every stage set, in both entry points, across several
+    # blocks and a ragged tail, with zeros, maxima and P frames
+    rng = np.random.default_rng(300 + 3 * stages + force)
+    H, W = 9, 1000
+    attrs = [(4, 7), (2, 1), (1, 1)]
+    base = [rand_scan(rng, H, W, s, 0.2) for s, _ in attrs]
+    scans = []
+    for t in range(4):
+        planes = [drift(rng, b, s, 3, 0.1) for b, (s, _) in zip(base, attrs)]
+        if t == 2:
+            planes[1][0, :] = 0xFFFF  # maximal values: wide exceptions without ZigZag
+        scans.append(planes)
+    check_stream(H, W, attrs, scans, force_mode=force, seq=bool(stages % 2), stages=stages)
+
+
+@pytest.mark.parametrize("stages", [1, 5, 7])
+def test_ablated_codecs_on_the_benchmark_shape(stages):
+    cfg = synth.config_multi_attr(n_scans=3, H=128, W=2048)
+    seq = synth.ScanSequence(cfg).scans()
+    check_stream(cfg.H, cfg.W, synth.attr_descs(cfg), seq, force_mode=0 if stages & 4 else -1, seq=True,
+                 stages=stages)
