@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "jiffy_oracle.c")
+_SRC_STD = os.path.join(_HERE, "jiffy_std_oracle.c")
 _LIB = os.path.join(_HERE, "libjiffy_oracle.so")
 
 ERR_CAPACITY = 2
@@ -36,9 +37,11 @@ _DT = {1: np.uint8, 2: np.uint16, 4: np.uint32}
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C99, no target-specific flags)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_STD))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp,
+                               _SRC, _SRC_STD, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -78,6 +81,17 @@ def lib() -> ctypes.CDLL:
         L.jo_trial_cost.argtypes = [u32, u32, u32, u32, u32, vp, vp, ctypes.c_int]
         L.jo_section_split.restype = u64
         L.jo_section_split.argtypes = [u32, u32, u32, u32, vp, vp, ctypes.c_int, vp, vp]
+        L.js_azimuth.restype = i64
+        L.js_azimuth.argtypes = [i64, i64]
+        L.js_elevation.restype = i64
+        L.js_elevation.argtypes = [i64, i64, i64]
+        L.js_isqrt.restype = u64
+        L.js_isqrt.argtypes = [u64, u64]
+        L.js_quantize_attr.restype = u32
+        L.js_quantize_attr.argtypes = [ctypes.c_float, ctypes.c_float, u32]
+        L.js_standardize.restype = ctypes.c_int
+        L.js_standardize.argtypes = [vp, u32, u32, u32, vp, ctypes.c_double, ctypes.c_int, ctypes.c_float, u32, u32,
+                                     u32, vp, u32, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -222,3 +236,50 @@ def decode_sequence(H, W, attrs, buf: bytes, n_scans: int, stages: int = 0):
         pos += n
     c.close()
     return out, pos
+
+
+# ---------------------------------------------------------------- standardization (Sec. III-A)
+ANGLE_UNITS = 1 << 48  # binary angle units per turn
+
+
+def azimuth(X: int, Y: int) -> int:
+    """CORDIC azimuth of the integer vector (X, Y), binary angle in [0, 2^48)."""
+    return lib().js_azimuth(X, Y)
+
+
+def elevation(X: int, Y: int, Z: int) -> int:
+    """CORDIC elevation of (sqrt(X^2 + Y^2), Z), signed binary angle."""
+    return lib().js_elevation(X, Y, Z)
+
+
+def isqrt(n: int) -> int:
+    """floor(sqrt(n)) for n < 2^126."""
+    return lib().js_isqrt(n >> 64, n & ((1 << 64) - 1))
+
+
+def quantize_attr(v: float, scale: float, nbytes: int) -> int:
+    return lib().js_quantize_attr(v, scale, nbytes)
+
+
+def standardize(xyz, H: int, W: int, beam_alt, az0: float = 0.0, clockwise: bool = False, units_per_m: float = 1000.0,
+                range_bytes: int = 4, min_range: int = 0, max_range: int = 0xFFFFFFFF, attrs=()):
+    """Standardizes one scan: xyz (n x 3 float32, metres) -> (range image,
+    [attribute images]). attrs: list of (values (n float32), bytes, scale)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float32).reshape(-1, 3)
+    n = xyz.shape[0]
+    alt = np.ascontiguousarray(beam_alt, dtype=np.float64)
+    assert alt.shape == (H,)
+    rng_out = np.zeros((H, W), dtype=_DT[range_bytes])
+    A = len(attrs)
+    vals = [np.ascontiguousarray(v, dtype=np.float32) for v, _, _ in attrs]
+    outs = [np.zeros((H, W), dtype=_DT[b]) for _, b, _ in attrs]
+    vp = (ctypes.c_void_p * max(A, 1))(*[_ptr(v) for v in vals])
+    op = (ctypes.c_void_p * max(A, 1))(*[_ptr(o) for o in outs])
+    nb = np.array([b for _, b, _ in attrs] or [4], dtype=np.uint32)
+    sc = np.array([s for _, _, s in attrs] or [1.0], dtype=np.float32)
+    src = xyz if n else np.zeros((1, 3), dtype=np.float32)
+    rc = lib().js_standardize(_ptr(src), n, H, W, _ptr(alt), az0, int(clockwise), units_per_m, range_bytes,
+                              min_range, max_range, _ptr(rng_out), A, vp, _ptr(nb), _ptr(sc), op)
+    if rc != 0:
+        raise ValueError("invalid standardization arguments")
+    return rng_out, outs
