@@ -302,6 +302,56 @@ uint32_t jiffy_stream_frame_index(const jiffy_stream* s);
 /* Human-readable name of a status code (static string). */
 const char* jiffy_status_string(jiffy_status st);
 
+/* ---- Input standardization (Sec. III-A): points given as floating-point
+ * Cartesian coordinates become the canonical H x W image the codec takes:
+ * spherical coordinates, rows by altitude (nearest beam), columns by azimuth,
+ * ranges and attributes quantized to unsigned integers, 0 where a pixel has
+ * no valid point. The arithmetic is exact integer arithmetic (the paper fixes
+ * none): coordinates round(x * units_per_m) (float32 product, ties to even),
+ * range = nearest integer to the Euclidean norm, angles by 44-step CORDIC in
+ * binary angles of 2^48 per turn; a pixel hit by several points keeps the
+ * nearest (then the first). */
+typedef struct {
+  uint32_t H, W;                 /* rows (beams) and columns, as jiffy_stream_create */
+  const double* beam_altitude;   /* host, H entries, radians, strictly decreasing (row 0 = top beam);
+                                  * copied at create */
+  double azimuth0;               /* radians: where column 0 starts, counterclockwise from +x */
+  int32_t clockwise;             /* nonzero: columns advance clockwise (y is negated) */
+  float units_per_m;             /* range unit per metre, e.g. 1000 for millimetres (> 0) */
+  uint32_t range_bytes;          /* range sample size: 2 or 4 */
+  uint32_t min_range, max_range; /* valid ranges in range units; others give 0 */
+} jiffy_sensor_desc;
+
+/* One per-point attribute: values (device, n_points floats), quantized as
+ * round(v * scale) clamped to the sample type (v * scale <= 0 or NaN -> 0)
+ * into out (device, H x W samples of dtype_bytes = 1, 2 or 4). */
+typedef struct {
+  const float* values;
+  void* out;
+  float scale;
+  uint32_t dtype_bytes;
+} jiffy_point_attr;
+
+typedef struct jiffy_standardizer jiffy_standardizer;
+
+/* Creates a standardizer for one sensor on `device` (owns an H x W x 8-byte
+ * pixel table and the beam table). Points more than half a beam spacing
+ * above the first or below the last beam are dropped (H > 1). Errors:
+ * INVALID_ARG (shape, unit, range size, non-decreasing or non-finite beams),
+ * NOMEM, CUDA. */
+jiffy_status jiffy_standardizer_create(jiffy_standardizer** out, const jiffy_sensor_desc* sensor, int device);
+
+/* Releases the standardizer (synchronizes its device). */
+void jiffy_standardizer_destroy(jiffy_standardizer* s);
+
+/* Standardizes one scan: xyz (device, 3 * n_points floats, x y z per point,
+ * metres) -> range_out (device, H x W samples of range_bytes, row-major) and
+ * n_attr <= 16 attribute images (attrs: host array). Stream-ordered on
+ * cuda_stream, does not wait; calls on one standardizer must be ordered on
+ * one stream. Errors: INVALID_ARG, CUDA. */
+jiffy_status jiffy_standardize(jiffy_standardizer* s, const float* xyz, uint32_t n_points, void* range_out,
+                               uint32_t n_attr, const jiffy_point_attr* attrs, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

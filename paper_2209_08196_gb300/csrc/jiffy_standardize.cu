@@ -1,0 +1,327 @@
+// Input standardization (Sec. III-A): one scan of floating-point Cartesian
+// points -> an H x W range image (rows by altitude, columns by azimuth) and
+// attribute images, quantized to unsigned integers, 0 where no valid point.
+//
+// The paper leaves the arithmetic open; this library fixes it in integers so
+// that every decision is exact (no floating-point rounding can move a point
+// to another pixel between two implementations):
+//   coordinates  X = round-half-even(x * k), the product rounded to float32
+//                (k = range units per metre); |x * k| >= 2^31 or NaN drops
+//                the point
+//   range        R = nearest integer to sqrt(X^2 + Y^2 + Z^2) (exact integer
+//                square root)
+//   angles       binary angles, 2^48 per turn, by CORDIC vectoring (Volder,
+//                1959) in 64-bit integers: 44 micro-rotations of atan(2^-i)
+//                on the vector scaled by a power of two so that its larger
+//                component has 46 bits. Azimuth of (X, Y) (counterclockwise
+//                from +x, 0 for X = Y = 0); elevation of (rho, Z), rho =
+//                floor(sqrt(X^2 + Y^2) 2^f) with the most fractional bits f
+//                that keep rho and Z 2^f below 2^46
+//   pixel        row = nearest beam (midpoints between the beams' binary
+//                altitudes; beyond half a spacing outside the first or last
+//                beam the point is dropped), column = floor(((az - az0) mod
+//                2^48) W / 2^48)
+//   collisions   the nearest point wins (smallest R, then smallest index)
+//   attributes   round-half-even(v * scale), the product rounded to float32,
+//                clamped to the sample type, NaN and v * scale <= 0 -> 0
+//
+// Two launches per scan: k_std_points (one thread per point: pixel and an
+// atomicMin of the key (R << 32 | index) into a per-pixel word, which stays
+// in L2) and k_std_pixels (one thread per pixel: the winning point's range
+// and attributes, and the key word reset for the next scan).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "jiffy.h"
+#include "jiffy_types.h"
+
+namespace jiffy {
+namespace {
+
+constexpr int kStdIter = 44;         // CORDIC micro-rotations
+constexpr int kAngleBits = 48;       // binary angle units per turn: 2^48
+constexpr int kNormBits = 46;        // CORDIC inputs scaled to this many bits
+constexpr uint32_t kStdMaxAttr = 16;
+constexpr double kPi = 3.14159265358979323846;
+
+struct StdAttr {
+  const float* v;
+  void* out;
+  float scale;
+  uint32_t bytes;
+};
+
+struct StdParams {
+  uint32_t H, W, n, clockwise, range_bytes, rmin, rmax, n_attr;
+  float k;
+  long long az0;         // binary angle in [0, 2^48)
+  long long top, bottom; // elevation limits (H > 1)
+  const long long* mid;  // [H - 1] midpoints between beams, decreasing
+  long long atan_t[kStdIter];
+  const float* xyz;
+  unsigned long long* keys;
+  void* range_out;
+  StdAttr attr[kStdMaxAttr];
+};
+
+__device__ __forceinline__ bool coord(float v, float k, long long& out) {
+  const float p = __fmul_rn(v, k);
+  if (!(fabsf(p) < 2147483648.0f)) return false;  // also NaN
+  out = (long long)rintf(p);                     // round half to even
+  return true;
+}
+
+// (hi, lo) >= (hi2, lo2) as unsigned 128-bit values
+__device__ __forceinline__ bool ge128(unsigned long long h1, unsigned long long l1, unsigned long long h2,
+                                      unsigned long long l2) {
+  return h1 > h2 || (h1 == h2 && l1 >= l2);
+}
+
+// floor(sqrt(n)) for n = hi 2^64 + lo < 2^94: a double estimate, then exact
+// integer corrections.
+__device__ unsigned long long isqrt128(unsigned long long hi, unsigned long long lo) {
+  unsigned long long r = (unsigned long long)sqrt((double)hi * 18446744073709551616.0 + (double)lo);
+  while (!ge128(hi, lo, __umul64hi(r, r), r * r)) r--;  // r^2 > n
+  while (true) {
+    const unsigned long long s = r + 1;
+    if (!ge128(hi, lo, __umul64hi(s, s), s * s)) break;  // (r+1)^2 > n
+    r = s;
+  }
+  return r;
+}
+
+__device__ __forceinline__ long long cordic_vec(long long x, long long y, const long long* t) {
+  long long ang = 0;
+#pragma unroll 4
+  for (int i = 0; i < kStdIter; i++) {
+    const long long xs = x >> i, ys = y >> i;
+    const bool up = y > 0;
+    x += up ? ys : -ys;
+    y += up ? -xs : xs;
+    ang += up ? t[i] : -t[i];
+  }
+  return ang;
+}
+
+__device__ __forceinline__ int bit_length(unsigned long long m) { return 64 - __clzll(m); }
+
+__device__ __forceinline__ long long azimuth(long long X, long long Y, const long long* t) {
+  if (X == 0 && Y == 0) return 0;
+  const unsigned long long m = (unsigned long long)(X < 0 ? -X : X) | (unsigned long long)(Y < 0 ? -Y : Y);
+  const int b = bit_length(m);
+  const long long f = b < kNormBits ? (1ll << (kNormBits - b)) : 1ll;
+  long long x = X * f, y = Y * f, base = 0;
+  if (x < 0) {  // a half turn first
+    x = -x;
+    y = -y;
+    base = 1ll << (kAngleBits - 1);
+  }
+  return (base + cordic_vec(x, y, t)) & ((1ll << kAngleBits) - 1);
+}
+
+__device__ __forceinline__ long long elevation(long long X, long long Y, long long Z, const long long* t) {
+  const unsigned long long h = (unsigned long long)(X * X) + (unsigned long long)(Y * Y);
+  const unsigned long long z2 = (unsigned long long)(Z * Z);
+  const unsigned long long m = h > z2 ? h : z2;
+  if (m == 0) return 0;
+  const int b = bit_length(m);
+  const int f = b < 2 * kNormBits ? (2 * kNormBits - b) / 2 : 0;  // m 4^f < 2^92
+  const int s = 2 * f;                                             // h << s, s <= 90
+  const unsigned long long hi = s == 0 ? 0ull : (s >= 64 ? h << (s - 64) : h >> (64 - s));
+  const unsigned long long lo = s >= 64 ? 0ull : h << s;
+  const long long rho = (long long)isqrt128(hi, lo);
+  return cordic_vec(rho, Z * (1ll << f), t);
+}
+
+__device__ __forceinline__ void store_sample(void* p, uint32_t bytes, size_t i, uint32_t v) {
+  if (bytes == 4) static_cast<uint32_t*>(p)[i] = v;
+  else if (bytes == 2) static_cast<uint16_t*>(p)[i] = (uint16_t)v;
+  else static_cast<uint8_t*>(p)[i] = (uint8_t)v;
+}
+
+__device__ __forceinline__ uint32_t quantize_attr(float v, float scale, uint32_t bytes) {
+  const float p = __fmul_rn(v, scale);
+  const uint32_t mx = bytes == 4 ? 0xffffffffu : ((1u << (8 * bytes)) - 1u);
+  if (!(p > 0.0f)) return 0u;  // also NaN
+  if (p >= (float)mx) return mx;
+  const float r = rintf(p);
+  return r >= (float)mx ? mx : (uint32_t)r;
+}
+
+__global__ void __launch_bounds__(256) k_std_points(const StdParams p) {
+  __shared__ long long t[kStdIter];
+  for (int i = threadIdx.x; i < kStdIter; i += blockDim.x) t[i] = p.atan_t[i];
+  __syncthreads();
+  for (unsigned long long ii = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; ii < p.n;
+       ii += (unsigned long long)gridDim.x * blockDim.x) {
+    const uint32_t i = (uint32_t)ii;
+    long long X, Y, Z;
+    const float* q = p.xyz + 3ull * i;
+    if (!coord(__ldg(q), p.k, X) || !coord(__ldg(q + 1), p.k, Y) || !coord(__ldg(q + 2), p.k, Z)) continue;
+    if (p.clockwise) Y = -Y;
+    const unsigned long long n = (unsigned long long)(X * X) + (unsigned long long)(Y * Y) +
+                                 (unsigned long long)(Z * Z);  // < 3 2^62
+    unsigned long long r = (unsigned long long)sqrt((double)n);
+    while (r * r > n) r--;
+    while ((r + 1) * (r + 1) <= n) r++;
+    const unsigned long long R = r + ((n - r * r) > r ? 1ull : 0ull);
+    if (R < 1 || R < p.rmin || R > p.rmax) continue;
+    uint32_t row = 0;
+    if (p.H > 1) {
+      const long long el = elevation(X, Y, Z, t);
+      if (el > p.top || el < p.bottom) continue;
+      uint32_t lo = 0, hi = p.H - 1;  // row = number of midpoints above el
+      while (lo < hi) {
+        const uint32_t m = (lo + hi) >> 1;
+        if (__ldg(p.mid + m) > el) lo = m + 1;
+        else hi = m;
+      }
+      row = lo;
+    }
+    const unsigned long long a = (unsigned long long)((azimuth(X, Y, t) - p.az0) & ((1ll << kAngleBits) - 1));
+    const uint32_t col = (uint32_t)((a * p.W) >> kAngleBits);
+    atomicMin(p.keys + (size_t)row * p.W + col, (R << 32) | i);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_std_pixels(const StdParams p) {
+  const size_t HW = (size_t)p.H * p.W;
+  for (size_t px = blockIdx.x * (size_t)blockDim.x + threadIdx.x; px < HW; px += (size_t)gridDim.x * blockDim.x) {
+    const unsigned long long key = p.keys[px];
+    const bool hit = key != ~0ull;
+    if (hit) p.keys[px] = ~0ull;  // ready for the next scan
+    const uint32_t idx = (uint32_t)key;
+    store_sample(p.range_out, p.range_bytes, px, hit ? (uint32_t)(key >> 32) : 0u);
+    for (uint32_t a = 0; a < p.n_attr; a++) {
+      const StdAttr& at = p.attr[a];
+      store_sample(at.out, at.bytes, px, hit ? quantize_attr(__ldg(at.v + idx), at.scale, at.bytes) : 0u);
+    }
+  }
+}
+
+long long binary_angle(double rad) {
+  return std::llround(rad / (2.0 * kPi) * 281474976710656.0);  // 2^48 per turn
+}
+
+}  // namespace
+}  // namespace jiffy
+
+struct jiffy_standardizer {
+  int device = 0;
+  uint32_t H = 0, W = 0;
+  jiffy::StdParams base{};
+  long long* d_mid = nullptr;
+  unsigned long long* d_keys = nullptr;
+  int sms = 0;
+};
+
+extern "C" {
+
+jiffy_status jiffy_standardizer_create(jiffy_standardizer** out, const jiffy_sensor_desc* sd, int device) {
+  using namespace jiffy;
+  if (!out || !sd) return JIFFY_ERR_INVALID_ARG;
+  *out = nullptr;
+  const uint32_t H = sd->H, W = sd->W;
+  if (H == 0 || H > kMaxH || W == 0 || W > kMaxW || !sd->beam_altitude || !(sd->units_per_m > 0.0f) ||
+      !(sd->range_bytes == 2 || sd->range_bytes == 4) || !std::isfinite(sd->azimuth0))
+    return JIFFY_ERR_INVALID_ARG;
+  std::vector<long long> alt(H), mid(H > 1 ? H - 1 : 1, 0);
+  for (uint32_t b = 0; b < H; b++) {
+    if (!std::isfinite(sd->beam_altitude[b])) return JIFFY_ERR_INVALID_ARG;
+    alt[b] = binary_angle(sd->beam_altitude[b]);
+    if (b > 0 && alt[b] >= alt[b - 1]) return JIFFY_ERR_INVALID_ARG;
+  }
+  for (uint32_t b = 0; b + 1 < H; b++) mid[b] = alt[b + 1] + (alt[b] - alt[b + 1]) / 2;
+  int prev = 0, ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return JIFFY_ERR_CUDA;
+  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return JIFFY_ERR_CUDA;
+  jiffy_standardizer* s = new (std::nothrow) jiffy_standardizer();
+  jiffy_status st = s ? JIFFY_OK : JIFFY_ERR_NOMEM;
+  if (st == JIFFY_OK) {
+    s->device = device;
+    s->H = H;
+    s->W = W;
+    StdParams& p = s->base;
+    p.H = H;
+    p.W = W;
+    p.clockwise = sd->clockwise ? 1u : 0u;
+    p.range_bytes = sd->range_bytes;
+    p.rmin = sd->min_range;
+    const uint32_t dmax = sd->range_bytes == 4 ? 0xffffffffu : 0xffffu;
+    p.rmax = sd->max_range < dmax ? sd->max_range : dmax;
+    p.k = sd->units_per_m;
+    p.az0 = binary_angle(sd->azimuth0) & ((1ll << kAngleBits) - 1);
+    if (H > 1) {
+      p.top = alt[0] + (alt[0] - alt[1]) / 2;
+      p.bottom = alt[H - 1] - (alt[H - 2] - alt[H - 1]) / 2;
+    }
+    for (int i = 0; i < kStdIter; i++) p.atan_t[i] = std::llround(std::atan(std::ldexp(1.0, -i)) / (2.0 * kPi) * 281474976710656.0);
+    if (cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaMalloc(&s->d_mid, sizeof(long long) * mid.size()) != cudaSuccess ||
+        cudaMalloc(&s->d_keys, sizeof(unsigned long long) * (size_t)H * W) != cudaSuccess ||
+        cudaMemcpy(s->d_mid, mid.data(), sizeof(long long) * mid.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(s->d_keys, 0xff, sizeof(unsigned long long) * (size_t)H * W) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+      st = JIFFY_ERR_CUDA;
+    p.mid = s->d_mid;
+    p.keys = s->d_keys;
+  }
+  if (st != JIFFY_OK && s) {
+    cudaFree(s->d_mid);
+    cudaFree(s->d_keys);
+    delete s;
+    s = nullptr;
+  }
+  cudaSetDevice(prev);
+  *out = s;
+  return st;
+}
+
+void jiffy_standardizer_destroy(jiffy_standardizer* s) {
+  if (!s) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(s->device);
+  cudaDeviceSynchronize();
+  cudaFree(s->d_mid);
+  cudaFree(s->d_keys);
+  cudaSetDevice(prev);
+  delete s;
+}
+
+jiffy_status jiffy_standardize(jiffy_standardizer* s, const float* xyz, uint32_t n_points, void* range_out,
+                               uint32_t n_attr, const jiffy_point_attr* attrs, void* cuda_stream) {
+  using namespace jiffy;
+  if (!s || !range_out || (n_points && !xyz) || n_attr > kStdMaxAttr || (n_attr && !attrs))
+    return JIFFY_ERR_INVALID_ARG;
+  StdParams p = s->base;
+  p.n = n_points;
+  p.xyz = xyz;
+  p.range_out = range_out;
+  p.n_attr = n_attr;
+  for (uint32_t a = 0; a < n_attr; a++) {
+    const uint32_t b = attrs[a].dtype_bytes;
+    if (!(b == 1 || b == 2 || b == 4) || !attrs[a].out || (n_points && !attrs[a].values)) return JIFFY_ERR_INVALID_ARG;
+    p.attr[a] = StdAttr{attrs[a].values, attrs[a].out, attrs[a].scale, b};
+  }
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(s->device) != cudaSuccess) return JIFFY_ERR_CUDA;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  const uint32_t cap = 8u * (uint32_t)s->sms;  // 8 CTAs of 256 per SM, grid-stride beyond
+  if (n_points) {
+    const uint32_t blocks = std::min(cap, (n_points + 255u) / 256u);
+    k_std_points<<<blocks, 256, 0, st>>>(p);
+  }
+  const size_t HW = (size_t)s->H * s->W;
+  k_std_pixels<<<(uint32_t)std::min<size_t>(cap, (HW + 255) / 256), 256, 0, st>>>(p);
+  const cudaError_t e = cudaGetLastError();
+  cudaSetDevice(prev);
+  return e == cudaSuccess ? JIFFY_OK : JIFFY_ERR_CUDA;
+}
+
+}  // extern "C"

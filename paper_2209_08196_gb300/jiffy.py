@@ -40,6 +40,17 @@ class _Options(ctypes.Structure):
     _fields_ = [("test_lines", ctypes.c_uint32), ("force_mode", ctypes.c_int32), ("stages", ctypes.c_uint32)]
 
 
+class _SensorDesc(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_uint32), ("W", ctypes.c_uint32), ("beam_altitude", ctypes.POINTER(ctypes.c_double)),
+                ("azimuth0", ctypes.c_double), ("clockwise", ctypes.c_int32), ("units_per_m", ctypes.c_float),
+                ("range_bytes", ctypes.c_uint32), ("min_range", ctypes.c_uint32), ("max_range", ctypes.c_uint32)]
+
+
+class _PointAttr(ctypes.Structure):
+    _fields_ = [("values", ctypes.c_void_p), ("out", ctypes.c_void_p), ("scale", ctypes.c_float),
+                ("dtype_bytes", ctypes.c_uint32)]
+
+
 # stage switches (jiffy_options.stages): the ablated codecs of Sec. IV-H
 STAGE_NO_MASK = 1
 STAGE_NO_DELTA = 2
@@ -117,6 +128,10 @@ def _lib() -> ctypes.CDLL:
         L.jiffy_stream_copy_state.argtypes = [vp, vp, vp]
         L.jiffy_stream_device_bytes.restype = sz
         L.jiffy_stream_device_bytes.argtypes = [vp]
+        L.jiffy_standardizer_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_SensorDesc), ctypes.c_int]
+        L.jiffy_standardizer_destroy.restype = None
+        L.jiffy_standardizer_destroy.argtypes = [vp]
+        L.jiffy_standardize.argtypes = [vp, vp, u32, vp, u32, ctypes.POINTER(_PointAttr), vp]
         _L = L
     return _L
 
@@ -520,3 +535,56 @@ def empty_planes(h: Handle, T: int | None = None, device=None):
     dev = device if device is not None else torch.device("cuda", h.device)
     shape = (h.H, h.W) if T is None else (T, h.H, h.W)
     return [torch.empty(shape, dtype=TORCH_DTYPE[s], device=dev) for s, _ in h.attrs]
+
+
+# ---- input standardization (Sec. III-A): Cartesian points -> range image
+
+
+class Standardizer:
+    """An opaque jiffy_standardizer* for one sensor."""
+
+    def __init__(self, ptr, H, W, range_bytes, device):
+        self.ptr, self.H, self.W, self.range_bytes, self.device = ptr, H, W, range_bytes, device
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _L is not None:
+            _L.jiffy_standardizer_destroy(self.ptr)
+            self.ptr = None
+
+
+def jiffy_standardizer_create(H: int, W: int, beam_altitude, azimuth0: float = 0.0, clockwise: bool = False,
+                              units_per_m: float = 1000.0, range_bytes: int = 4, min_range: int = 0,
+                              max_range: int = 0xFFFFFFFF, device: int = 0) -> Standardizer:
+    alt = (ctypes.c_double * H)(*[float(a) for a in beam_altitude])
+    d = _SensorDesc(H, W, alt, azimuth0, 1 if clockwise else 0, units_per_m, range_bytes, min_range, max_range)
+    h = ctypes.c_void_p()
+    st = _lib().jiffy_standardizer_create(ctypes.byref(h), ctypes.byref(d), device)
+    if st != 0:
+        raise JiffyError(st, "jiffy_standardizer_create")
+    return Standardizer(h.value, H, W, range_bytes, device)
+
+
+def jiffy_standardizer_destroy(h: Standardizer):
+    if h.ptr:
+        _lib().jiffy_standardizer_destroy(h.ptr)
+        h.ptr = None
+
+
+def jiffy_standardize(h: Standardizer, xyz: torch.Tensor, range_out: torch.Tensor, attrs=(), stream=None):
+    """xyz: n x 3 float32 CUDA tensor (metres); range_out: H x W CUDA tensor of
+    range_bytes samples; attrs: (values (n float32), out (H x W), scale)
+    triples. Stream-ordered, does not wait."""
+    if xyz.dtype != torch.float32 or not xyz.is_cuda or not xyz.is_contiguous() or xyz.numel() % 3:
+        raise ValueError("xyz: expected a contiguous CUDA float32 tensor of n x 3 coordinates")
+    n = xyz.numel() // 3
+    _check_plane(range_out, h.H, h.W, h.range_bytes, "range_out")
+    arr = (_PointAttr * max(len(attrs), 1))()
+    for i, (v, o, scale) in enumerate(attrs):
+        if v.dtype != torch.float32 or not v.is_cuda or not v.is_contiguous() or v.numel() != n:
+            raise ValueError("attribute %d: expected %d contiguous CUDA float32 values" % (i, n))
+        _check_plane(o, h.H, h.W, o.element_size(), "attribute %d out" % i)
+        arr[i] = _PointAttr(v.data_ptr(), o.data_ptr(), float(scale), o.element_size())
+    st = _lib().jiffy_standardize(h.ptr, xyz.data_ptr() if n else None, n, range_out.data_ptr(), len(attrs), arr,
+                                  _stream_ptr(stream))
+    if st != 0:
+        raise JiffyError(st, "jiffy_standardize")
