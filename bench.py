@@ -693,8 +693,8 @@ def main():
 
     # input standardization (Sec. III-A) of the same scans given as points:
     # each scan's valid pixels as float32 x y z (metres) plus three float
-    # attributes, converted back to the range and attribute images, one call
-    # per scan (two kernels: points, then pixels)
+    # attributes, converted back to the range and attribute images, all scans
+    # in one call (two kernels: points, then pixels)
     standardize = None
     if not args.no_standardize:
         n_s = T
@@ -710,18 +710,21 @@ def main():
             vals = [(planes_in[a][t][rows_, cols_].to(torch.int64) & 0xFFFF).to(torch.float32) for a in (2, 3, 4)]
             clouds.append((xyz, vals))
         std = J.jiffy_standardizer_create(H, W, alt.cpu().tolist(), device=local)
-        s_range = torch.empty((H, W), dtype=torch.int32, device=dev)
-        s_attr = [torch.empty((H, W), dtype=torch.int16, device=dev), torch.empty((H, W), dtype=torch.uint8, device=dev),
-                  torch.empty((H, W), dtype=torch.int16, device=dev)]
+        s_offs = [0]
+        for c in clouds:
+            s_offs.append(s_offs[-1] + c[0].shape[0])
+        s_xyz = torch.cat([c[0] for c in clouds])
+        s_vals = [torch.cat([c[1][a] for c in clouds]) for a in range(3)]
+        del clouds
+        s_range = torch.empty((n_s, H, W), dtype=torch.int32, device=dev)
+        s_attr = [torch.empty((n_s, H, W), dtype=d, device=dev) for d in (torch.int16, torch.uint8, torch.int16)]
 
         def std_run():
-            for xyz, vals in clouds:
-                J.jiffy_standardize(std, xyz, s_range, [(vals[0], s_attr[0], 1.0), (vals[1], s_attr[1], 1.0),
-                                                        (vals[2], s_attr[2], 1.0)], stream)
+            J.jiffy_standardize_seq(std, s_xyz, s_offs, s_range, [(s_vals[a], s_attr[a], 1.0) for a in range(3)],
+                                    stream)
         std_run()
         torch.cuda.synchronize()
-        ok = torch.equal(s_range, planes_in[0][n_s - 1]) or \
-            int((s_range.to(torch.int64) - planes_in[0][n_s - 1].to(torch.int64)).abs().max()) <= 1
+        ok = int((s_range.to(torch.int64) - planes_in[0][:n_s].to(torch.int64)).abs().max()) <= 1
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         reps = 3
@@ -731,14 +734,14 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / (reps * n_s)
-        npts = sum(c[0].shape[0] for c in clouds) / n_s
+        npts = s_offs[-1] / n_s
         moved = npts * (12 + 12) + H * W * (4 + 2 + 1 + 2)  # points + attributes in, images out
         peak_s, _ = peaks()
         standardize = {"scans": n_s, "points_per_scan": npts, "attributes": 3, "ms_per_scan": ms,
                        "gpoints_s": npts / ms / 1e6, "algorithmic_bytes_per_scan": moved,
                        "achieved_GBps": moved / ms / 1e6, "frac_of_hbm": moved / ms / 1e6 / peak_s,
-                       "launches_per_scan": 2, "last_scan_within_1_unit": bool(ok)}
-        del clouds, std
+                       "launches_per_call": 2, "scans_per_call": n_s, "all_scans_within_1_unit": bool(ok)}
+        del s_xyz, s_vals, s_range, s_attr, std
 
     batched = served = None
     if not args.no_batched:

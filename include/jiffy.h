@@ -334,8 +334,8 @@ typedef struct {
 
 typedef struct jiffy_standardizer jiffy_standardizer;
 
-/* Creates a standardizer for one sensor on `device` (owns an H x W x 8-byte
- * pixel table and the beam table). Points more than half a beam spacing
+/* Creates a standardizer for one sensor on `device` (owns a pixel table of
+ * H x W x 8 bytes per scan of its largest call, and the beam table). Points more than half a beam spacing
  * above the first or below the last beam are dropped (H > 1). Errors:
  * INVALID_ARG (shape, unit, range size, non-decreasing or non-finite beams),
  * NOMEM, CUDA. */
@@ -351,6 +351,18 @@ void jiffy_standardizer_destroy(jiffy_standardizer* s);
  * one stream. Errors: INVALID_ARG, CUDA. */
 jiffy_status jiffy_standardize(jiffy_standardizer* s, const float* xyz, uint32_t n_points, void* range_out,
                                uint32_t n_attr, const jiffy_point_attr* attrs, void* cuda_stream);
+
+/* Standardizes n_scans <= 256 scans in one pass (two kernel launches for
+ * all of them). Scan t's points are [point_offsets[t], point_offsets[t+1])
+ * of xyz (host array of n_scans + 1 non-decreasing point indices, fewer than
+ * 2^32 points per scan); the attributes' values are indexed the same way.
+ * range_out and every attribute's out hold n_scans consecutive H x W images.
+ * The first call with more scans than any before it reallocates the pixel
+ * table (n_scans x H x W x 8 bytes) after waiting for cuda_stream. Otherwise
+ * as jiffy_standardize; NOMEM if the table cannot grow. */
+jiffy_status jiffy_standardize_seq(jiffy_standardizer* s, uint32_t n_scans, const float* xyz,
+                                   const uint64_t* point_offsets, void* range_out, uint32_t n_attr,
+                                   const jiffy_point_attr* attrs, void* cuda_stream);
 
 #ifdef __cplusplus
 }

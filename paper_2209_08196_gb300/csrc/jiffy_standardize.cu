@@ -25,10 +25,11 @@
 //   attributes   round-half-even(v * scale), the product rounded to float32,
 //                clamped to the sample type, NaN and v * scale <= 0 -> 0
 //
-// Two launches per scan: k_std_points (one thread per point: pixel and an
-// atomicMin of the key (R << 32 | index) into a per-pixel word, which stays
-// in L2) and k_std_pixels (one thread per pixel: the winning point's range
-// and attributes, and the key word reset for the next scan).
+// Two launches per call of up to 256 scans: k_std_points (one thread per
+// point, one grid row per scan: pixel and an atomicMin of the key (R << 32 |
+// index in the scan) into a per-pixel word, L2-resident for a few scans) and
+// k_std_pixels (one thread per pixel of every scan: the winning point's range
+// and attributes, and the key word reset for the next call).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -47,6 +48,7 @@ constexpr int kStdIter = 44;         // CORDIC micro-rotations
 constexpr int kAngleBits = 48;       // binary angle units per turn: 2^48
 constexpr int kNormBits = 46;        // CORDIC inputs scaled to this many bits
 constexpr uint32_t kStdMaxAttr = 16;
+constexpr uint32_t kStdMaxScans = 256;  // scans per call
 constexpr double kPi = 3.14159265358979323846;
 
 struct StdAttr {
@@ -57,16 +59,17 @@ struct StdAttr {
 };
 
 struct StdParams {
-  uint32_t H, W, n, clockwise, range_bytes, rmin, rmax, n_attr;
+  uint32_t H, W, T, clockwise, range_bytes, rmin, rmax, n_attr;
   float k;
   long long az0;         // binary angle in [0, 2^48)
   long long top, bottom; // elevation limits (H > 1)
   const long long* mid;  // [H - 1] midpoints between beams, decreasing
   long long atan_t[kStdIter];
   const float* xyz;
-  unsigned long long* keys;
-  void* range_out;
+  unsigned long long* keys;  // [T][H * W]
+  void* range_out;           // [T][H * W]
   StdAttr attr[kStdMaxAttr];
+  unsigned long long off[kStdMaxScans + 1];  // scan t's points: [off[t], off[t + 1])
 };
 
 __device__ __forceinline__ bool coord(float v, float k, long long& out) {
@@ -153,15 +156,18 @@ __device__ __forceinline__ uint32_t quantize_attr(float v, float scale, uint32_t
   return r >= (float)mx ? mx : (uint32_t)r;
 }
 
-__global__ void __launch_bounds__(256) k_std_points(const StdParams p) {
+__global__ void __launch_bounds__(256) k_std_points(const __grid_constant__ StdParams p) {
   __shared__ long long t[kStdIter];
   for (int i = threadIdx.x; i < kStdIter; i += blockDim.x) t[i] = p.atan_t[i];
   __syncthreads();
-  for (unsigned long long ii = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; ii < p.n;
+  const uint32_t scan = blockIdx.y;
+  const unsigned long long p0 = p.off[scan], n = p.off[scan + 1] - p0;
+  unsigned long long* keys = p.keys + (size_t)scan * p.H * p.W;
+  for (unsigned long long ii = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; ii < n;
        ii += (unsigned long long)gridDim.x * blockDim.x) {
-    const uint32_t i = (uint32_t)ii;
+    const uint32_t i = (uint32_t)ii;  // index within the scan (< 2^32)
     long long X, Y, Z;
-    const float* q = p.xyz + 3ull * i;
+    const float* q = p.xyz + 3ull * (p0 + ii);
     if (!coord(__ldg(q), p.k, X) || !coord(__ldg(q + 1), p.k, Y) || !coord(__ldg(q + 2), p.k, Z)) continue;
     if (p.clockwise) Y = -Y;
     const unsigned long long n = (unsigned long long)(X * X) + (unsigned long long)(Y * Y) +
@@ -185,17 +191,17 @@ __global__ void __launch_bounds__(256) k_std_points(const StdParams p) {
     }
     const unsigned long long a = (unsigned long long)((azimuth(X, Y, t) - p.az0) & ((1ll << kAngleBits) - 1));
     const uint32_t col = (uint32_t)((a * p.W) >> kAngleBits);
-    atomicMin(p.keys + (size_t)row * p.W + col, (R << 32) | i);
+    atomicMin(keys + (size_t)row * p.W + col, (R << 32) | i);
   }
 }
 
-__global__ void __launch_bounds__(256) k_std_pixels(const StdParams p) {
-  const size_t HW = (size_t)p.H * p.W;
-  for (size_t px = blockIdx.x * (size_t)blockDim.x + threadIdx.x; px < HW; px += (size_t)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) k_std_pixels(const __grid_constant__ StdParams p) {
+  const size_t HW = (size_t)p.H * p.W, total = HW * p.T;
+  for (size_t px = blockIdx.x * (size_t)blockDim.x + threadIdx.x; px < total; px += (size_t)gridDim.x * blockDim.x) {
     const unsigned long long key = p.keys[px];
     const bool hit = key != ~0ull;
-    if (hit) p.keys[px] = ~0ull;  // ready for the next scan
-    const uint32_t idx = (uint32_t)key;
+    if (hit) p.keys[px] = ~0ull;  // ready for the next call
+    const unsigned long long idx = p.off[px / HW] + (uint32_t)key;  // the point, across the call
     store_sample(p.range_out, p.range_bytes, px, hit ? (uint32_t)(key >> 32) : 0u);
     for (uint32_t a = 0; a < p.n_attr; a++) {
       const StdAttr& at = p.attr[a];
@@ -216,7 +222,8 @@ struct jiffy_standardizer {
   uint32_t H = 0, W = 0;
   jiffy::StdParams base{};
   long long* d_mid = nullptr;
-  unsigned long long* d_keys = nullptr;
+  unsigned long long* d_keys = nullptr;  // key_scans x H x W, all ~0 between calls
+  uint32_t key_scans = 0;
   int sms = 0;
 };
 
@@ -269,7 +276,7 @@ jiffy_status jiffy_standardizer_create(jiffy_standardizer** out, const jiffy_sen
         cudaDeviceSynchronize() != cudaSuccess)
       st = JIFFY_ERR_CUDA;
     p.mid = s->d_mid;
-    p.keys = s->d_keys;
+    s->key_scans = 1;
   }
   if (st != JIFFY_OK && s) {
     cudaFree(s->d_mid);
@@ -294,34 +301,69 @@ void jiffy_standardizer_destroy(jiffy_standardizer* s) {
   delete s;
 }
 
-jiffy_status jiffy_standardize(jiffy_standardizer* s, const float* xyz, uint32_t n_points, void* range_out,
-                               uint32_t n_attr, const jiffy_point_attr* attrs, void* cuda_stream) {
+jiffy_status jiffy_standardize_seq(jiffy_standardizer* s, uint32_t n_scans, const float* xyz,
+                                   const uint64_t* point_offsets, void* range_out, uint32_t n_attr,
+                                   const jiffy_point_attr* attrs, void* cuda_stream) {
   using namespace jiffy;
-  if (!s || !range_out || (n_points && !xyz) || n_attr > kStdMaxAttr || (n_attr && !attrs))
+  if (!s || n_scans == 0 || n_scans > kStdMaxScans || !point_offsets || !range_out || n_attr > kStdMaxAttr ||
+      (n_attr && !attrs))
     return JIFFY_ERR_INVALID_ARG;
   StdParams p = s->base;
-  p.n = n_points;
+  unsigned long long max_n = 0;
+  for (uint32_t t = 0; t < n_scans; t++) {
+    if (point_offsets[t + 1] < point_offsets[t] || point_offsets[t + 1] - point_offsets[t] > 0xffffffffull)
+      return JIFFY_ERR_INVALID_ARG;
+    max_n = std::max<unsigned long long>(max_n, point_offsets[t + 1] - point_offsets[t]);
+  }
+  for (uint32_t t = 0; t <= n_scans; t++) p.off[t] = point_offsets[t];
+  if (max_n && !xyz) return JIFFY_ERR_INVALID_ARG;
+  p.T = n_scans;
   p.xyz = xyz;
   p.range_out = range_out;
   p.n_attr = n_attr;
   for (uint32_t a = 0; a < n_attr; a++) {
     const uint32_t b = attrs[a].dtype_bytes;
-    if (!(b == 1 || b == 2 || b == 4) || !attrs[a].out || (n_points && !attrs[a].values)) return JIFFY_ERR_INVALID_ARG;
+    if (!(b == 1 || b == 2 || b == 4) || !attrs[a].out || (max_n && !attrs[a].values)) return JIFFY_ERR_INVALID_ARG;
     p.attr[a] = StdAttr{attrs[a].values, attrs[a].out, attrs[a].scale, b};
   }
   int prev = 0;
   if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(s->device) != cudaSuccess) return JIFFY_ERR_CUDA;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-  const uint32_t cap = 8u * (uint32_t)s->sms;  // 8 CTAs of 256 per SM, grid-stride beyond
-  if (n_points) {
-    const uint32_t blocks = std::min(cap, (n_points + 255u) / 256u);
-    k_std_points<<<blocks, 256, 0, st>>>(p);
-  }
   const size_t HW = (size_t)s->H * s->W;
-  k_std_pixels<<<(uint32_t)std::min<size_t>(cap, (HW + 255) / 256), 256, 0, st>>>(p);
-  const cudaError_t e = cudaGetLastError();
+  jiffy_status rc = JIFFY_OK;
+  if (n_scans > s->key_scans || !s->d_keys) {  // a larger pixel table: wait for the calls using the old one
+    if (cudaStreamSynchronize(st) != cudaSuccess) rc = JIFFY_ERR_CUDA;
+    cudaFree(s->d_keys);
+    s->d_keys = nullptr;
+    s->key_scans = 0;
+    if (rc == JIFFY_OK) {
+      const size_t bytes = sizeof(unsigned long long) * HW * n_scans;
+      const cudaError_t me = cudaMalloc(&s->d_keys, bytes);
+      if (me != cudaSuccess) rc = me == cudaErrorMemoryAllocation ? JIFFY_ERR_NOMEM : JIFFY_ERR_CUDA;
+      else if (cudaMemsetAsync(s->d_keys, 0xff, bytes, st) != cudaSuccess) rc = JIFFY_ERR_CUDA;
+      else s->key_scans = n_scans;
+    }
+  }
+  if (rc == JIFFY_OK) {
+    p.keys = s->d_keys;
+    const uint32_t target = 16u * (uint32_t)s->sms;  // CTAs of 256 threads in flight, grid-stride beyond
+    if (max_n) {
+      const unsigned long long need = (max_n + 255u) / 256u;
+      const uint32_t bx = (uint32_t)std::max<unsigned long long>(
+          1ull, std::min<unsigned long long>(need, (target + n_scans - 1) / n_scans));
+      k_std_points<<<dim3(bx, n_scans), 256, 0, st>>>(p);
+    }
+    k_std_pixels<<<(uint32_t)std::min<size_t>(target, (HW * n_scans + 255) / 256), 256, 0, st>>>(p);
+    if (cudaGetLastError() != cudaSuccess) rc = JIFFY_ERR_CUDA;
+  }
   cudaSetDevice(prev);
-  return e == cudaSuccess ? JIFFY_OK : JIFFY_ERR_CUDA;
+  return rc;
+}
+
+jiffy_status jiffy_standardize(jiffy_standardizer* s, const float* xyz, uint32_t n_points, void* range_out,
+                               uint32_t n_attr, const jiffy_point_attr* attrs, void* cuda_stream) {
+  const uint64_t off[2] = {0, n_points};
+  return jiffy_standardize_seq(s, 1, xyz, off, range_out, n_attr, attrs, cuda_stream);
 }
 
 }  // extern "C"

@@ -132,6 +132,7 @@ def _lib() -> ctypes.CDLL:
         L.jiffy_standardizer_destroy.restype = None
         L.jiffy_standardizer_destroy.argtypes = [vp]
         L.jiffy_standardize.argtypes = [vp, vp, u32, vp, u32, ctypes.POINTER(_PointAttr), vp]
+        L.jiffy_standardize_seq.argtypes = [vp, u32, vp, u64p, vp, u32, ctypes.POINTER(_PointAttr), vp]
         _L = L
     return _L
 
@@ -588,3 +589,34 @@ def jiffy_standardize(h: Standardizer, xyz: torch.Tensor, range_out: torch.Tenso
                                   _stream_ptr(stream))
     if st != 0:
         raise JiffyError(st, "jiffy_standardize")
+
+
+def jiffy_standardize_seq(h: Standardizer, xyz: torch.Tensor, offsets, range_out: torch.Tensor, attrs=(),
+                          stream=None):
+    """Several scans in one pass: xyz holds all scans' points (N x 3 float32),
+    scan t = rows offsets[t]:offsets[t+1]; range_out and each attribute out
+    are T x H x W; attrs: (values (N float32), out, scale) triples."""
+    T = len(offsets) - 1
+    if xyz.dtype != torch.float32 or not xyz.is_cuda or not xyz.is_contiguous() or xyz.numel() % 3:
+        raise ValueError("xyz: expected a contiguous CUDA float32 tensor of N x 3 coordinates")
+    n = xyz.numel() // 3
+    if T < 1 or offsets[0] < 0 or offsets[-1] > n:
+        raise ValueError("offsets: expected T + 1 point indices within xyz")
+
+    def check_out(t, what):
+        if not t.is_cuda or not t.is_contiguous() or t.numel() != T * h.H * h.W:
+            raise ValueError("%s: expected a contiguous CUDA tensor of %d x %d x %d samples" % (what, T, h.H, h.W))
+    check_out(range_out, "range_out")
+    if range_out.element_size() != h.range_bytes:
+        raise ValueError("range_out: expected %d-byte samples" % h.range_bytes)
+    arr = (_PointAttr * max(len(attrs), 1))()
+    for i, (v, o, scale) in enumerate(attrs):
+        if v.dtype != torch.float32 or not v.is_cuda or not v.is_contiguous() or v.numel() != n:
+            raise ValueError("attribute %d: expected %d contiguous CUDA float32 values" % (i, n))
+        check_out(o, "attribute %d out" % i)
+        arr[i] = _PointAttr(v.data_ptr(), o.data_ptr(), float(scale), o.element_size())
+    offs = (ctypes.c_uint64 * (T + 1))(*[int(x) for x in offsets])
+    st = _lib().jiffy_standardize_seq(h.ptr, T, xyz.data_ptr() if n else None, offs, range_out.data_ptr(),
+                                      len(attrs), arr, _stream_ptr(stream))
+    if st != 0:
+        raise JiffyError(st, "jiffy_standardize_seq")

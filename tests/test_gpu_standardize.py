@@ -140,6 +140,32 @@ def test_repeated_calls_reuse_the_pixel_table_and_empty_scans():
             assert not got.any()
 
 
+def test_many_scans_in_one_call():
+    # uneven point counts (one scan empty), attributes, and a second call with
+    # more scans than the first (the pixel table grows)
+    rng = np.random.default_rng(6)
+    H, W = 16, 700
+    alt = beams(H)
+    h = J.jiffy_standardizer_create(H, W, alt, range_bytes=2, max_range=65000)
+    for counts in ([3000, 0, 12345, 1, 999], [5000] * 3 + [0] * 2 + [7777] * 6):
+        clouds = [cloud(rng, c, 25.0) for c in counts]
+        vals = [rng.uniform(0, 400, c).astype(np.float32) for c in counts]
+        offs = np.concatenate([[0], np.cumsum(counts)]).tolist()
+        T = len(counts)
+        xyz = torch.from_numpy(np.concatenate(clouds).reshape(-1, 3)).cuda()
+        v = torch.from_numpy(np.concatenate(vals)).cuda()
+        r = torch.full((T, H, W), 3, dtype=torch.int16, device="cuda")
+        o = torch.full((T, H, W), 3, dtype=torch.uint8, device="cuda")
+        J.jiffy_standardize_seq(h, xyz, offs, r, [(v, o, 0.5)])
+        torch.cuda.synchronize()
+        r, o = r.cpu().numpy().view(np.uint16), o.cpu().numpy()
+        for t in range(T):
+            wr, (wa,) = oracle.standardize(clouds[t], H, W, alt, range_bytes=2, max_range=65000,
+                                           attrs=[(vals[t], 1, 0.5)])
+            assert np.array_equal(r[t], wr), (counts, t)
+            assert np.array_equal(o[t], wa), (counts, t)
+
+
 def test_largest_shape():
     rng = np.random.default_rng(5)
     H, W = 64, 16384
