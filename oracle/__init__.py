@@ -81,9 +81,9 @@ def lib() -> ctypes.CDLL:
         L.jo_trial_cost.argtypes = [u32, u32, u32, u32, u32, vp, vp, ctypes.c_int]
         L.jo_section_split.restype = u64
         L.jo_section_split.argtypes = [u32, u32, u32, u32, vp, vp, ctypes.c_int, vp, vp]
-        L.js_azimuth.restype = i64
+        L.js_azimuth.restype = u32
         L.js_azimuth.argtypes = [i64, i64]
-        L.js_elevation.restype = i64
+        L.js_elevation.restype = i32
         L.js_elevation.argtypes = [i64, i64, i64]
         L.js_isqrt.restype = u64
         L.js_isqrt.argtypes = [u64, u64]
@@ -239,11 +239,11 @@ def decode_sequence(H, W, attrs, buf: bytes, n_scans: int, stages: int = 0):
 
 
 # ---------------------------------------------------------------- standardization (Sec. III-A)
-ANGLE_UNITS = 1 << 48  # binary angle units per turn
+ANGLE_UNITS = 1 << 32  # binary angle units per turn
 
 
 def azimuth(X: int, Y: int) -> int:
-    """CORDIC azimuth of the integer vector (X, Y), binary angle in [0, 2^48)."""
+    """CORDIC azimuth of the integer vector (X, Y), binary angle in [0, 2^32)."""
     return lib().js_azimuth(X, Y)
 
 

@@ -18,15 +18,15 @@
  *      with |x * k| >= 2^31 (or NaN) is invalid;
  *   2. range R = X^2 + Y^2 + Z^2 square-rooted and rounded to the nearest
  *      integer (exact integer square root);
- *   3. angles as binary angles, 2^48 units per turn, by CORDIC vectoring
+ *   3. angles as binary angles, 2^32 units per turn, by CORDIC vectoring
  *      (Volder, "The CORDIC trigonometric computing technique", 1959) in
- *      64-bit integers, 44 iterations, on the vector scaled by a power of
- *      two so that its larger component has 46 bits: azimuth of (X, Y) in
- *      [0, 2^48) counterclockwise from +x (clockwise sensors negate Y; 0 for
- *      X = Y = 0), elevation of (rho, Z) with rho = sqrt(X^2 + Y^2) floored
- *      in fixed point, with the most fractional bits f that keep rho and
- *      Z * 2^f below 2^46 (0 for X = Y = Z = 0); the arctangent table
- *      atan(2^-i) is rounded from the C library's atan;
+ *      32-bit integers, 30 iterations, on the vector scaled by a power of
+ *      two (arithmetic shifts) so that its larger component has 29 bits:
+ *      azimuth of (X, Y) in [0, 2^32) counterclockwise from +x (clockwise
+ *      sensors negate Y; 0 for X = Y = 0), elevation of (rho, Z) with rho =
+ *      floor(sqrt(X^2 + Y^2) 2^f) and Z 2^f (floor), f the largest (possibly
+ *      negative) integer that keeps both below 2^29 (0 for X = Y = Z = 0);
+ *      the arctangent table atan(2^-i) is rounded from the C library's atan;
  *   4. row = nearest beam: beam altitudes (radians, strictly decreasing, row
  *      0 on top) as binary angles; row r covers elevations from the midpoint
  *      with the beam below up to the midpoint with the beam above (the top
@@ -43,31 +43,31 @@
 #include <string.h>
 
 #define JS_PI 3.14159265358979323846
-#define JS_ANGLE_BITS 48
-#define JS_ITER 44
-#define JS_NORM_BITS 46
+#define JS_ITER 30
+#define JS_NORM_BITS 29
 
 enum { JS_OK = 0, JS_ERR_INVALID_ARG = 1 };
 
-static int64_t js_atan_table[JS_ITER];
+static int32_t js_atan_table[JS_ITER];
 static int js_table_ready = 0;
 
-/* atan(2^-i) as a binary angle (2^48 per turn), rounded to nearest. */
+/* atan(2^-i) as a binary angle (2^32 per turn), rounded to nearest. */
 static void js_init_table(void) {
   if (js_table_ready) return;
   for (int i = 0; i < JS_ITER; i++) {
     double a = atan(ldexp(1.0, -i)); /* radians */
-    js_atan_table[i] = (int64_t)llround(a / (2.0 * JS_PI) * ldexp(1.0, JS_ANGLE_BITS));
+    js_atan_table[i] = (int32_t)llround(a / (2.0 * JS_PI) * 4294967296.0);
   }
   js_table_ready = 1;
 }
 
-/* Vectoring CORDIC: the angle of (x, y) for x >= 0, as a signed binary
- * angle; y is driven to 0 by micro-rotations of +-atan(2^-i). */
-static int64_t js_cordic_vec(int64_t x, int64_t y) {
-  int64_t ang = 0;
+/* Vectoring CORDIC: the angle of (x, y) for x >= 0, components below 2^29,
+ * as a signed binary angle; y is driven to 0 by micro-rotations of
+ * +-atan(2^-i). |x| stays below 1.65 * sqrt(2) * 2^29 < 2^31. */
+static int32_t js_cordic_vec(int32_t x, int32_t y) {
+  int32_t ang = 0;
   for (int i = 0; i < JS_ITER; i++) {
-    int64_t xs = x >> i, ys = y >> i; /* arithmetic shifts */
+    int32_t xs = x >> i, ys = y >> i; /* arithmetic shifts */
     if (y > 0) {
       x = x + ys; y = y - xs; ang += js_atan_table[i];
     } else {
@@ -77,27 +77,26 @@ static int64_t js_cordic_vec(int64_t x, int64_t y) {
   return ang;
 }
 
-/* Power of two that brings the larger of |a|, |b| to JS_NORM_BITS bits (1
- * if it has that many already). */
-static int64_t js_norm(int64_t a, int64_t b) {
-  uint64_t m = (uint64_t)(a < 0 ? -a : a) | (uint64_t)(b < 0 ? -b : b);
+static int js_bits(uint64_t m) {
   int bits = 0;
-  while (m >> bits) bits++;
-  return bits < JS_NORM_BITS ? (int64_t)1 << (JS_NORM_BITS - bits) : 1;
+  while (bits < 64 && (m >> bits)) bits++;
+  return bits;
 }
 
-int64_t js_azimuth(int64_t X, int64_t Y) {
+/* v * 2^s, with floor division for s < 0 (arithmetic shift). */
+static int64_t js_scale(int64_t v, int s) {
+  return s >= 0 ? v * ((int64_t)1 << s) : (v >> (-s));
+}
+
+uint32_t js_azimuth(int64_t X, int64_t Y) {
   js_init_table();
   if (X == 0 && Y == 0) return 0;
-  int64_t f = js_norm(X, Y);
-  int64_t x = X * f, y = Y * f;
-  int64_t base = 0;
-  if (x < 0) { x = -x; y = -y; base = (int64_t)1 << (JS_ANGLE_BITS - 1); } /* rotate by a half turn */
-  int64_t a = base + js_cordic_vec(x, y);
-  int64_t turn = (int64_t)1 << JS_ANGLE_BITS;
-  a %= turn;
-  if (a < 0) a += turn;
-  return a;
+  uint64_t m = (uint64_t)(X < 0 ? -X : X) | (uint64_t)(Y < 0 ? -Y : Y);
+  int s = JS_NORM_BITS - js_bits(m);
+  int32_t x = (int32_t)js_scale(X, s), y = (int32_t)js_scale(Y, s);
+  uint32_t base = 0;
+  if (x < 0) { x = -x; y = -y; base = 0x80000000u; } /* a half turn first */
+  return base + (uint32_t)js_cordic_vec(x, y);       /* modulo 2^32 */
 }
 
 /* floor(sqrt(n)) for n < 2^126. */
@@ -112,21 +111,22 @@ uint64_t js_isqrt(uint64_t hi, uint64_t lo) {
   return js_isqrt128(((unsigned __int128)hi << 64) | lo);
 }
 
-int64_t js_elevation(int64_t X, int64_t Y, int64_t Z) {
+int32_t js_elevation(int64_t X, int64_t Y, int64_t Z) {
   js_init_table();
   uint64_t h = (uint64_t)(X * X) + (uint64_t)(Y * Y); /* < 2^63 */
   uint64_t z2 = (uint64_t)(Z * Z);
   uint64_t m = h > z2 ? h : z2;
   if (m == 0) return 0;
-  int bits = 0;
-  while (m >> bits) bits++;
-  int f = bits < 2 * JS_NORM_BITS ? (2 * JS_NORM_BITS - bits) / 2 : 0; /* m * 4^f < 2^92 */
-  int64_t rho = (int64_t)js_isqrt128((unsigned __int128)h << (2 * f)); /* floor(sqrt(h) * 2^f) */
-  return js_cordic_vec(rho, Z * ((int64_t)1 << f));
+  int e = js_bits(m);
+  /* largest f with m * 4^f < 2^58 */
+  int f = e <= 2 * JS_NORM_BITS ? (2 * JS_NORM_BITS - e) / 2 : -((e - 2 * JS_NORM_BITS + 1) / 2);
+  uint64_t hs = f >= 0 ? h << (2 * f) : h >> (-2 * f);
+  int32_t rho = (int32_t)js_isqrt128(hs); /* floor(sqrt(h) * 2^f), below 2^29 */
+  return js_cordic_vec(rho, (int32_t)js_scale(Z, f));
 }
 
 static int64_t js_binary_angle(double rad) {
-  return (int64_t)llround(rad / (2.0 * JS_PI) * ldexp(1.0, JS_ANGLE_BITS));
+  return (int64_t)llround(rad / (2.0 * JS_PI) * 4294967296.0);
 }
 
 /* Float -> integer coordinate (step 1); returns 0 if invalid. */
@@ -157,7 +157,7 @@ uint32_t js_quantize_attr(float v, float scale, uint32_t bytes) {
 }
 
 /* Pixel of one point, or -1 if dropped; *range receives R (steps 1-4). */
-int64_t js_pixel(float x, float y, float z, float k, uint32_t H, uint32_t W, const int64_t* alt, int64_t az0,
+int64_t js_pixel(float x, float y, float z, float k, uint32_t H, uint32_t W, const int64_t* alt, uint32_t az0,
                  int clockwise, uint32_t rmin, uint32_t rmax, uint32_t* range) {
   int64_t X, Y, Z;
   if (!js_coord(x, k, &X) || !js_coord(y, k, &Y) || !js_coord(z, k, &Z)) return -1;
@@ -179,11 +179,8 @@ int64_t js_pixel(float x, float y, float z, float k, uint32_t H, uint32_t W, con
     }
   }
   /* column */
-  int64_t turn = (int64_t)1 << JS_ANGLE_BITS;
-  int64_t a = js_azimuth(X, Y) - az0;
-  a %= turn;
-  if (a < 0) a += turn;
-  uint64_t col = (uint64_t)(((unsigned __int128)a * W) >> JS_ANGLE_BITS);
+  uint32_t a = js_azimuth(X, Y) - az0; /* modulo 2^32 */
+  uint64_t col = ((uint64_t)a * W) >> 32;
   return (int64_t)row * W + (int64_t)col;
 }
 
@@ -205,9 +202,7 @@ int js_standardize(const float* xyz, uint32_t n, uint32_t H, uint32_t W, const d
     alt[b] = js_binary_angle(beam_alt[b]);
     if (b > 0 && alt[b] >= alt[b - 1]) { free(alt); return JS_ERR_INVALID_ARG; }
   }
-  int64_t turn = (int64_t)1 << JS_ANGLE_BITS;
-  int64_t a0 = js_binary_angle(az0) % turn;
-  if (a0 < 0) a0 += turn;
+  uint32_t a0 = (uint32_t)(uint64_t)js_binary_angle(az0); /* modulo 2^32 */
   uint32_t rcap = rmax < js_max_of(range_bytes) ? rmax : js_max_of(range_bytes);
   size_t HW = (size_t)H * W;
   uint64_t* best = (uint64_t*)malloc(sizeof(uint64_t) * HW); /* (R << 32) | point index */
