@@ -308,13 +308,14 @@ const char* jiffy_status_string(jiffy_status st);
  * ranges and attributes quantized to unsigned integers, 0 where a pixel has
  * no valid point. The arithmetic is exact integer arithmetic (the paper fixes
  * none): coordinates round(x * units_per_m) (float32 product, ties to even),
- * range = nearest integer to the Euclidean norm, angles by 44-step CORDIC in
- * binary angles of 2^48 per turn; a pixel hit by several points keeps the
- * nearest (then the first). */
+ * range = nearest integer to the Euclidean norm, angles by a 30-step CORDIC
+ * in 32-bit integers (binary angles of 2^32 per turn, within 6e-8 rad of the
+ * exact angle); a pixel hit by several points keeps the nearest (then the
+ * first). */
 typedef struct {
   uint32_t H, W;                 /* rows (beams) and columns, as jiffy_stream_create */
-  const double* beam_altitude;   /* host, H entries, radians, strictly decreasing (row 0 = top beam);
-                                  * copied at create */
+  const double* beam_altitude;   /* host, H entries, radians within +-pi/2, strictly decreasing
+                                  * (row 0 = top beam); copied at create */
   double azimuth0;               /* radians: where column 0 starts, counterclockwise from +x */
   int32_t clockwise;             /* nonzero: columns advance clockwise (y is negated) */
   float units_per_m;             /* range unit per metre, e.g. 1000 for millimetres (> 0) */

@@ -27,8 +27,8 @@
  *      floor(sqrt(X^2 + Y^2) 2^f) and Z 2^f (floor), f the largest (possibly
  *      negative) integer that keeps both below 2^29 (0 for X = Y = Z = 0);
  *      the arctangent table atan(2^-i) is rounded from the C library's atan;
- *   4. row = nearest beam: beam altitudes (radians, strictly decreasing, row
- *      0 on top) as binary angles; row r covers elevations from the midpoint
+ *   4. row = nearest beam: beam altitudes (radians within +-pi/2, strictly
+ *      decreasing, row 0 on top) as binary angles; row r covers elevations from the midpoint
  *      with the beam below up to the midpoint with the beam above (the top
  *      and bottom rows extend half their spacing outwards; points beyond are
  *      dropped); column c = floor(((az - az0) mod 2^48) * W / 2^48);
@@ -200,7 +200,10 @@ int js_standardize(const float* xyz, uint32_t n, uint32_t H, uint32_t W, const d
   int64_t* alt = (int64_t*)malloc(sizeof(int64_t) * H);
   for (uint32_t b = 0; b < H; b++) {
     alt[b] = js_binary_angle(beam_alt[b]);
-    if (b > 0 && alt[b] >= alt[b - 1]) { free(alt); return JS_ERR_INVALID_ARG; }
+    if (alt[b] > (1 << 30) || alt[b] < -(1 << 30) || (b > 0 && alt[b] >= alt[b - 1])) { /* within +-90 deg */
+      free(alt);
+      return JS_ERR_INVALID_ARG;
+    }
   }
   uint32_t a0 = (uint32_t)(uint64_t)js_binary_angle(az0); /* modulo 2^32 */
   uint32_t rcap = rmax < js_max_of(range_bytes) ? rmax : js_max_of(range_bytes);

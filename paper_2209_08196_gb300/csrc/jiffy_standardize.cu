@@ -10,17 +10,17 @@
 //                the point
 //   range        R = nearest integer to sqrt(X^2 + Y^2 + Z^2) (exact integer
 //                square root)
-//   angles       binary angles, 2^48 per turn, by CORDIC vectoring (Volder,
-//                1959) in 64-bit integers: 44 micro-rotations of atan(2^-i)
-//                on the vector scaled by a power of two so that its larger
-//                component has 46 bits. Azimuth of (X, Y) (counterclockwise
-//                from +x, 0 for X = Y = 0); elevation of (rho, Z), rho =
-//                floor(sqrt(X^2 + Y^2) 2^f) with the most fractional bits f
-//                that keep rho and Z 2^f below 2^46
+//   angles       binary angles, 2^32 per turn, by CORDIC vectoring (Volder,
+//                1959) in 32-bit integers: 30 micro-rotations of atan(2^-i)
+//                on the vector scaled by a power of two (arithmetic shifts)
+//                so that its larger component has 29 bits. Azimuth of (X, Y)
+//                (counterclockwise from +x, 0 for X = Y = 0); elevation of
+//                (rho, Z 2^f), rho = floor(sqrt(X^2 + Y^2) 2^f), f the
+//                largest (possibly negative) integer keeping both below 2^29
 //   pixel        row = nearest beam (midpoints between the beams' binary
 //                altitudes; beyond half a spacing outside the first or last
 //                beam the point is dropped), column = floor(((az - az0) mod
-//                2^48) W / 2^48)
+//                2^32) W / 2^32)
 //   collisions   the nearest point wins (smallest R, then smallest index)
 //   attributes   round-half-even(v * scale), the product rounded to float32,
 //                clamped to the sample type, NaN and v * scale <= 0 -> 0
@@ -44,9 +44,8 @@
 namespace jiffy {
 namespace {
 
-constexpr int kStdIter = 44;         // CORDIC micro-rotations
-constexpr int kAngleBits = 48;       // binary angle units per turn: 2^48
-constexpr int kNormBits = 46;        // CORDIC inputs scaled to this many bits
+constexpr int kStdIter = 30;         // CORDIC micro-rotations
+constexpr int kNormBits = 29;        // CORDIC inputs scaled to this many bits
 constexpr uint32_t kStdMaxAttr = 16;
 constexpr uint32_t kStdMaxScans = 256;  // scans per call
 constexpr double kPi = 3.14159265358979323846;
@@ -61,10 +60,10 @@ struct StdAttr {
 struct StdParams {
   uint32_t H, W, T, clockwise, range_bytes, rmin, rmax, n_attr;
   float k;
-  long long az0;         // binary angle in [0, 2^48)
-  long long top, bottom; // elevation limits (H > 1)
-  const long long* mid;  // [H - 1] midpoints between beams, decreasing
-  long long atan_t[kStdIter];
+  uint32_t az0;          // binary angle (2^32 per turn)
+  int top, bottom;       // elevation limits (H > 1)
+  const int* mid;        // [H - 1] midpoints between beams, decreasing
+  int atan_t[kStdIter];
   const float* xyz;
   unsigned long long* keys;  // [T][H * W]
   void* range_out;           // [T][H * W]
@@ -79,30 +78,24 @@ __device__ __forceinline__ bool coord(float v, float k, long long& out) {
   return true;
 }
 
-// (hi, lo) >= (hi2, lo2) as unsigned 128-bit values
-__device__ __forceinline__ bool ge128(unsigned long long h1, unsigned long long l1, unsigned long long h2,
-                                      unsigned long long l2) {
-  return h1 > h2 || (h1 == h2 && l1 >= l2);
-}
-
-// floor(sqrt(n)) for n = hi 2^64 + lo < 2^94: a double estimate, then exact
-// integer corrections.
-__device__ unsigned long long isqrt128(unsigned long long hi, unsigned long long lo) {
-  unsigned long long r = (unsigned long long)sqrt((double)hi * 18446744073709551616.0 + (double)lo);
-  while (!ge128(hi, lo, __umul64hi(r, r), r * r)) r--;  // r^2 > n
-  while (true) {
-    const unsigned long long s = r + 1;
-    if (!ge128(hi, lo, __umul64hi(s, s), s * s)) break;  // (r+1)^2 > n
-    r = s;
-  }
+// floor(sqrt(n)) for n < 2^63.6 (n < 3 2^62): a float32 estimate (the FP64
+// units of this GPU are few), one Newton correction r += (n - r^2) / 2r in
+// float32 (leaves r within one of the root), then exact integer corrections.
+__device__ __forceinline__ unsigned long long isqrt64(unsigned long long n) {
+  if (n == 0ull) return 0ull;
+  unsigned long long r = (unsigned long long)__fsqrt_rn(__ull2float_rn(n));
+  const long long e = (long long)(n - r * r);  // |e| < 2^42
+  r = (unsigned long long)((long long)r + __float2ll_rn(__fdividef((float)e, 2.0f * (float)r)));
+  while (r * r > n) r--;
+  while ((r + 1) * (r + 1) <= n) r++;
   return r;
 }
 
-__device__ __forceinline__ long long cordic_vec(long long x, long long y, const long long* t) {
-  long long ang = 0;
-#pragma unroll 4
+__device__ __forceinline__ int cordic_vec(int x, int y, const int* t) {
+  int ang = 0;
+#pragma unroll
   for (int i = 0; i < kStdIter; i++) {
-    const long long xs = x >> i, ys = y >> i;
+    const int xs = x >> i, ys = y >> i;
     const bool up = y > 0;
     x += up ? ys : -ys;
     y += up ? -xs : xs;
@@ -113,32 +106,32 @@ __device__ __forceinline__ long long cordic_vec(long long x, long long y, const 
 
 __device__ __forceinline__ int bit_length(unsigned long long m) { return 64 - __clzll(m); }
 
-__device__ __forceinline__ long long azimuth(long long X, long long Y, const long long* t) {
-  if (X == 0 && Y == 0) return 0;
+// v 2^s, floor division (arithmetic shift) for s < 0
+__device__ __forceinline__ long long scale2(long long v, int s) { return s >= 0 ? v * (1ll << s) : (v >> (-s)); }
+
+__device__ __forceinline__ uint32_t azimuth(long long X, long long Y, const int* t) {
+  if (X == 0 && Y == 0) return 0u;
   const unsigned long long m = (unsigned long long)(X < 0 ? -X : X) | (unsigned long long)(Y < 0 ? -Y : Y);
-  const int b = bit_length(m);
-  const long long f = b < kNormBits ? (1ll << (kNormBits - b)) : 1ll;
-  long long x = X * f, y = Y * f, base = 0;
+  const int s = kNormBits - bit_length(m);
+  int x = (int)scale2(X, s), y = (int)scale2(Y, s);
+  uint32_t base = 0u;
   if (x < 0) {  // a half turn first
     x = -x;
     y = -y;
-    base = 1ll << (kAngleBits - 1);
+    base = 0x80000000u;
   }
-  return (base + cordic_vec(x, y, t)) & ((1ll << kAngleBits) - 1);
+  return base + (uint32_t)cordic_vec(x, y, t);  // modulo 2^32
 }
 
-__device__ __forceinline__ long long elevation(long long X, long long Y, long long Z, const long long* t) {
+__device__ __forceinline__ int elevation(long long X, long long Y, long long Z, const int* t) {
   const unsigned long long h = (unsigned long long)(X * X) + (unsigned long long)(Y * Y);
   const unsigned long long z2 = (unsigned long long)(Z * Z);
   const unsigned long long m = h > z2 ? h : z2;
   if (m == 0) return 0;
-  const int b = bit_length(m);
-  const int f = b < 2 * kNormBits ? (2 * kNormBits - b) / 2 : 0;  // m 4^f < 2^92
-  const int s = 2 * f;                                             // h << s, s <= 90
-  const unsigned long long hi = s == 0 ? 0ull : (s >= 64 ? h << (s - 64) : h >> (64 - s));
-  const unsigned long long lo = s >= 64 ? 0ull : h << s;
-  const long long rho = (long long)isqrt128(hi, lo);
-  return cordic_vec(rho, Z * (1ll << f), t);
+  const int e = bit_length(m);
+  const int f = e <= 2 * kNormBits ? (2 * kNormBits - e) / 2 : -((e - 2 * kNormBits + 1) / 2);  // m 4^f < 2^58
+  const unsigned long long hs = f >= 0 ? h << (2 * f) : h >> (-2 * f);
+  return cordic_vec((int)isqrt64(hs), (int)scale2(Z, f), t);
 }
 
 __device__ __forceinline__ void store_sample(void* p, uint32_t bytes, size_t i, uint32_t v) {
@@ -157,7 +150,7 @@ __device__ __forceinline__ uint32_t quantize_attr(float v, float scale, uint32_t
 }
 
 __global__ void __launch_bounds__(256) k_std_points(const __grid_constant__ StdParams p) {
-  __shared__ long long t[kStdIter];
+  __shared__ int t[kStdIter];
   for (int i = threadIdx.x; i < kStdIter; i += blockDim.x) t[i] = p.atan_t[i];
   __syncthreads();
   const uint32_t scan = blockIdx.y;
@@ -172,14 +165,12 @@ __global__ void __launch_bounds__(256) k_std_points(const __grid_constant__ StdP
     if (p.clockwise) Y = -Y;
     const unsigned long long n = (unsigned long long)(X * X) + (unsigned long long)(Y * Y) +
                                  (unsigned long long)(Z * Z);  // < 3 2^62
-    unsigned long long r = (unsigned long long)sqrt((double)n);
-    while (r * r > n) r--;
-    while ((r + 1) * (r + 1) <= n) r++;
+    const unsigned long long r = isqrt64(n);
     const unsigned long long R = r + ((n - r * r) > r ? 1ull : 0ull);
     if (R < 1 || R < p.rmin || R > p.rmax) continue;
     uint32_t row = 0;
     if (p.H > 1) {
-      const long long el = elevation(X, Y, Z, t);
+      const int el = elevation(X, Y, Z, t);
       if (el > p.top || el < p.bottom) continue;
       uint32_t lo = 0, hi = p.H - 1;  // row = number of midpoints above el
       while (lo < hi) {
@@ -189,8 +180,8 @@ __global__ void __launch_bounds__(256) k_std_points(const __grid_constant__ StdP
       }
       row = lo;
     }
-    const unsigned long long a = (unsigned long long)((azimuth(X, Y, t) - p.az0) & ((1ll << kAngleBits) - 1));
-    const uint32_t col = (uint32_t)((a * p.W) >> kAngleBits);
+    const uint32_t a = azimuth(X, Y, t) - p.az0;  // modulo 2^32
+    const uint32_t col = (uint32_t)(((unsigned long long)a * p.W) >> 32);
     atomicMin(keys + (size_t)row * p.W + col, (R << 32) | i);
   }
 }
@@ -211,7 +202,7 @@ __global__ void __launch_bounds__(256) k_std_pixels(const __grid_constant__ StdP
 }
 
 long long binary_angle(double rad) {
-  return std::llround(rad / (2.0 * kPi) * 281474976710656.0);  // 2^48 per turn
+  return std::llround(rad / (2.0 * kPi) * 4294967296.0);  // 2^32 per turn
 }
 
 }  // namespace
@@ -221,7 +212,7 @@ struct jiffy_standardizer {
   int device = 0;
   uint32_t H = 0, W = 0;
   jiffy::StdParams base{};
-  long long* d_mid = nullptr;
+  int* d_mid = nullptr;
   unsigned long long* d_keys = nullptr;  // key_scans x H x W, all ~0 between calls
   uint32_t key_scans = 0;
   int sms = 0;
@@ -237,13 +228,15 @@ jiffy_status jiffy_standardizer_create(jiffy_standardizer** out, const jiffy_sen
   if (H == 0 || H > kMaxH || W == 0 || W > kMaxW || !sd->beam_altitude || !(sd->units_per_m > 0.0f) ||
       !(sd->range_bytes == 2 || sd->range_bytes == 4) || !std::isfinite(sd->azimuth0))
     return JIFFY_ERR_INVALID_ARG;
-  std::vector<long long> alt(H), mid(H > 1 ? H - 1 : 1, 0);
+  std::vector<long long> alt(H);
+  std::vector<int> mid(H > 1 ? H - 1 : 1, 0);
   for (uint32_t b = 0; b < H; b++) {
     if (!std::isfinite(sd->beam_altitude[b])) return JIFFY_ERR_INVALID_ARG;
     alt[b] = binary_angle(sd->beam_altitude[b]);
-    if (b > 0 && alt[b] >= alt[b - 1]) return JIFFY_ERR_INVALID_ARG;
+    if (alt[b] > (1ll << 30) || alt[b] < -(1ll << 30) || (b > 0 && alt[b] >= alt[b - 1]))  // within +-90 deg
+      return JIFFY_ERR_INVALID_ARG;
   }
-  for (uint32_t b = 0; b + 1 < H; b++) mid[b] = alt[b + 1] + (alt[b] - alt[b + 1]) / 2;
+  for (uint32_t b = 0; b + 1 < H; b++) mid[b] = (int)(alt[b + 1] + (alt[b] - alt[b + 1]) / 2);
   int prev = 0, ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return JIFFY_ERR_CUDA;
   if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(device) != cudaSuccess) return JIFFY_ERR_CUDA;
@@ -262,16 +255,17 @@ jiffy_status jiffy_standardizer_create(jiffy_standardizer** out, const jiffy_sen
     const uint32_t dmax = sd->range_bytes == 4 ? 0xffffffffu : 0xffffu;
     p.rmax = sd->max_range < dmax ? sd->max_range : dmax;
     p.k = sd->units_per_m;
-    p.az0 = binary_angle(sd->azimuth0) & ((1ll << kAngleBits) - 1);
+    p.az0 = (uint32_t)(unsigned long long)binary_angle(sd->azimuth0);  // modulo 2^32
     if (H > 1) {
-      p.top = alt[0] + (alt[0] - alt[1]) / 2;
-      p.bottom = alt[H - 1] - (alt[H - 2] - alt[H - 1]) / 2;
+      p.top = (int)std::min<long long>(alt[0] + (alt[0] - alt[1]) / 2, 0x7fffffffll);
+      p.bottom = (int)std::max<long long>(alt[H - 1] - (alt[H - 2] - alt[H - 1]) / 2, -0x7fffffffll - 1);
     }
-    for (int i = 0; i < kStdIter; i++) p.atan_t[i] = std::llround(std::atan(std::ldexp(1.0, -i)) / (2.0 * kPi) * 281474976710656.0);
+    for (int i = 0; i < kStdIter; i++)
+      p.atan_t[i] = (int)std::llround(std::atan(std::ldexp(1.0, -i)) / (2.0 * kPi) * 4294967296.0);
     if (cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-        cudaMalloc(&s->d_mid, sizeof(long long) * mid.size()) != cudaSuccess ||
+        cudaMalloc(&s->d_mid, sizeof(int) * mid.size()) != cudaSuccess ||
         cudaMalloc(&s->d_keys, sizeof(unsigned long long) * (size_t)H * W) != cudaSuccess ||
-        cudaMemcpy(s->d_mid, mid.data(), sizeof(long long) * mid.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(s->d_mid, mid.data(), sizeof(int) * mid.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(s->d_keys, 0xff, sizeof(unsigned long long) * (size_t)H * W) != cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess)
       st = JIFFY_ERR_CUDA;

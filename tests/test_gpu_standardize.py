@@ -180,3 +180,5 @@ def test_invalid_sensors_are_rejected():
         J.jiffy_standardizer_create(4, 16, beams(4), range_bytes=1)
     with pytest.raises(J.JiffyError):
         J.jiffy_standardizer_create(4, 16, beams(4), units_per_m=0.0)
+    with pytest.raises(J.JiffyError):  # beyond +-90 degrees
+        J.jiffy_standardizer_create(3, 16, [1.7, 0.0, -0.1])

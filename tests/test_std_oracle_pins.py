@@ -154,3 +154,5 @@ def test_no_points_and_invalid_coordinates():
     assert not img.any()
     with pytest.raises(ValueError):  # beams must be strictly decreasing
         oracle.standardize(bad, H, W, alt[::-1])
+    with pytest.raises(ValueError):  # and within +-90 degrees
+        oracle.standardize(bad, H, W, np.array([1.7, 0.0, -0.1]))
