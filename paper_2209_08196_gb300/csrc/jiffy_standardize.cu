@@ -28,8 +28,8 @@
 // Two launches per call of up to 256 scans: k_std_points (one thread per
 // point, one grid row per scan: pixel and an atomicMin of the key (R << 32 |
 // index in the scan) into a per-pixel word, L2-resident for a few scans) and
-// k_std_pixels (one thread per pixel of every scan: the winning point's range
-// and attributes, and the key word reset for the next call).
+// k_std_pixels (one thread per pixel of every scan, grid-stride: the winning
+// point's range and attributes, and the key word reset for the next call).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -187,16 +187,26 @@ __global__ void __launch_bounds__(256) k_std_points(const __grid_constant__ StdP
 }
 
 __global__ void __launch_bounds__(256) k_std_pixels(const __grid_constant__ StdParams p) {
-  const size_t HW = (size_t)p.H * p.W, total = HW * p.T;
-  for (size_t px = blockIdx.x * (size_t)blockDim.x + threadIdx.x; px < total; px += (size_t)gridDim.x * blockDim.x) {
+  const uint32_t HW = p.H * p.W;  // <= 2^26
+  const size_t total = (size_t)HW * p.T;
+  const uint32_t G = gridDim.x * blockDim.x, g0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t dt = G / HW, dr = G % HW;  // the stride as (scans, pixels)
+  uint32_t t = g0 / HW, r = g0 % HW;        // this thread's scan and pixel
+  for (size_t px = g0; px < total; px += G) {
     const unsigned long long key = p.keys[px];
     const bool hit = key != ~0ull;
     if (hit) p.keys[px] = ~0ull;  // ready for the next call
-    const unsigned long long idx = p.off[px / HW] + (uint32_t)key;  // the point, across the call
+    const unsigned long long idx = p.off[t] + (uint32_t)key;  // the point, across the call
     store_sample(p.range_out, p.range_bytes, px, hit ? (uint32_t)(key >> 32) : 0u);
     for (uint32_t a = 0; a < p.n_attr; a++) {
       const StdAttr& at = p.attr[a];
       store_sample(at.out, at.bytes, px, hit ? quantize_attr(__ldg(at.v + idx), at.scale, at.bytes) : 0u);
+    }
+    t += dt;
+    r += dr;
+    if (r >= HW) {
+      r -= HW;
+      t++;
     }
   }
 }
