@@ -89,7 +89,8 @@ class Clocks:
         self.smax = None
         self.mode = None
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device_index)
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), "jiffy_bench_clocks_%d_rank%d.csv" % (os.getpid(), device_index))
 
     def _nvml(self):
         import ctypes
