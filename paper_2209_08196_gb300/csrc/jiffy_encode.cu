@@ -66,6 +66,13 @@ __device__ __forceinline__ uint32_t enc_item(const EncSeg& sg, uint32_t t, uint3
   return (a * sg.T + t) * sg.H + r;
 }
 
+// Bulk prefetch of [p, p + bytes) into L2 (the 16-byte aligned part of it).
+__device__ __forceinline__ void prefetch_l2(const uint8_t* p, size_t bytes) {
+  const uintptr_t c0 = reinterpret_cast<uintptr_t>(p), c1 = c0 + bytes;
+  const uintptr_t a0 = (c0 + 15u) & ~uintptr_t(15), a1 = c1 & ~uintptr_t(15);
+  if (a1 > a0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0)) : "memory");
+}
+
 __device__ __forceinline__ uint32_t mask_class(uint32_t c, uint32_t valid) {
   return c == 0u ? 0u : (c == valid ? 1u : 2u);
 }
@@ -530,6 +537,15 @@ __global__ void __launch_bounds__(32) k_trial(EncParams p) {
   const bool all = (st & kStageNoMask) != 0u;
   uint32_t* zi = smem;
   uint32_t* zp = smem + ((W + kStepVal - 1) / kStepVal) * kStepVal;
+  if (lane_id() == 0) {  // fetch the test row (both scans) and the earlier test row's tail into L2 at once
+    prefetch_l2(cur + test_row(ti) * rowb, rowb);
+    prefetch_l2(prv + test_row(ti) * rowb, rowb);
+    if (ti > 0) {
+      const size_t tail = min(rowb, (size_t)kStepPx * at.s);
+      prefetch_l2(cur + test_row(ti - 1) * rowb + rowb - tail, tail);
+      prefetch_l2(prv + test_row(ti - 1) * rowb + rowb - tail, tail);
+    }
+  }
   // carry: the last residual of the nearest earlier test row that has one
   uint32_t ci = 0, cp = 0;
   for (int k = (int)ti - 1; k >= 0; k--) {
