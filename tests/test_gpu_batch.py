@@ -51,14 +51,16 @@ def make_scans(rng, H, W, attrs, T):
 
 
 class Fleet:
-    """One encoder, decoder and oracle pair per sensor."""
+    """One encoder, decoder and oracle pair per sensor (stages: optional
+    per-sensor stage switches)."""
 
-    def __init__(self, sensors):
+    def __init__(self, sensors, stages=None):
         self.sensors = sensors
-        self.enc = [J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, a) for H, W, a in sensors]
-        self.dec = [J.jiffy_stream_create(J.JIFFY_DECODER, H, W, a) for H, W, a in sensors]
-        self.ref = [oracle.Codec(H, W, a) for H, W, a in sensors]
-        self.refd = [oracle.Codec(H, W, a) for H, W, a in sensors]
+        st = stages or [0] * len(sensors)
+        self.enc = [J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, a, stages=g) for (H, W, a), g in zip(sensors, st)]
+        self.dec = [J.jiffy_stream_create(J.JIFFY_DECODER, H, W, a, stages=g) for (H, W, a), g in zip(sensors, st)]
+        self.ref = [oracle.Codec(H, W, a, stages=g) for (H, W, a), g in zip(sensors, st)]
+        self.refd = [oracle.Codec(H, W, a, stages=g) for (H, W, a), g in zip(sensors, st)]
         self.b = J.jiffy_batch_create()
 
     def encode(self, scans_per_stream, caps=None):
@@ -71,9 +73,13 @@ class Fleet:
         return [(o[:n].cpu().numpy().tobytes(), offs) for o, (n, offs) in zip(outs, res)]
 
 
-def test_batch_encode_decode_matches_oracle_over_calls():
+@pytest.mark.parametrize("stages", [None, [0, 7, 1, 6]])
+def test_batch_encode_decode_matches_oracle_over_calls(stages):
+    # stages: streams of the full codec and ablated ones (Sec. IV-H) in the
+    # same launches (the kernels that read stage switches then run every
+    # segment, the full-codec ones included)
     rng = np.random.default_rng(11)
-    fleet = Fleet(SENSORS)
+    fleet = Fleet(SENSORS, stages)
     T_calls = [[1, 3, 2, 4], [2, 1, 3, 1], [3, 2, 1, 2]]
     saw_p = False
     for Ts in T_calls:
