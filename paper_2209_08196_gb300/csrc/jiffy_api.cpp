@@ -104,6 +104,7 @@ struct jiffy_stream {
   int cur = 0;                                // state buffer holding the previous scan
   uint32_t frame = 0;                         // frames since create/reset
   bool in_flight = false;                     // part of an enqueued, unfinished call
+  uint32_t withhold = UINT32_MAX;             // test hook: row item of the next decode call left unpublished
 };
 
 struct jiffy_batch {
@@ -597,7 +598,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   uint32_t* ib = reinterpret_cast<uint32_t*>(h + u_ib);
   std::vector<uint64_t> key{2, n, (uint64_t)(uintptr_t)d, (uint64_t)(uintptr_t)h};
   std::vector<uint32_t> sig{2, max_W, log2_ceil(items)};
-  uint32_t staged = 0;
+  uint32_t staged = 0, withhold = 0;
   uint32_t item_base = 0;
   for (uint32_t i = 0; i < n; i++) {
     DecJob& j = jobs[i];
@@ -634,6 +635,8 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
     g.mask_base = mask_base[i];
     segs[i] = g;
     ib[i] = item_base;
+    if (s->withhold < T * A * s->H) withhold = item_base + s->withhold + 1u;
+    s->withhold = UINT32_MAX;  // one call
     item_base += T * A * s->H;
     staged |= s->opt.stages ? 1u : 0u;
     key.push_back(((uint64_t)s->H << 32) | s->W);
@@ -652,6 +655,8 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   p.masks = reinterpret_cast<uint32_t*>(d + o_masks);
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
   p.staged = staged;
+  p.withhold = withhold;
+  key.push_back(withhold);
   uint8_t* hres = h + h_res;
 
   auto enqueue = [&](cudaStream_t s, const jiffy::DecParams& pp, void* const* evs) -> int {
@@ -888,6 +893,12 @@ jiffy_status jiffy_stream_copy_state(jiffy_stream* dst, const jiffy_stream* src,
                       reinterpret_cast<cudaStream_t>(cuda_stream)) != cudaSuccess)
     return JIFFY_ERR_CUDA;
   dst->frame = src->frame;
+  return JIFFY_OK;
+}
+
+jiffy_status jiffy_stream_test_withhold_row(jiffy_stream* s, uint32_t row_item) {
+  if (!s || s->role != JIFFY_DECODER) return JIFFY_ERR_INVALID_ARG;
+  s->withhold = row_item;
   return JIFFY_OK;
 }
 

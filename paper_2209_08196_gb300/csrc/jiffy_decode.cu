@@ -442,7 +442,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   if (lane == 0 && bad && status != 2u) atomicOr(sg.err, kErrCorrupt);
   __threadfence();
   __syncwarp();
-  if (lane == 0) atomicExch(p.done + k, 1u);
+  if (lane == 0 && k + 1u != p.withhold) atomicExch(p.done + k, 1u);
 }
 
 template <int WPC, bool STAGED>

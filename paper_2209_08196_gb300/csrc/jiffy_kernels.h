@@ -94,6 +94,7 @@ struct DecParams {
   uint32_t ctas_per_sm;          // resident CTAs per SM (0 = occupancy limit)
   uint32_t items_per_ticket;     // row items a warp takes per ticket (0 = 4)
   uint32_t staged;               // as in EncParams
+  uint32_t withhold;             // test hook: 1 + the row item that does not publish its done flag (0: none)
 };
 
 // Launch configuration of a rows kernel as resolved for given parameters

@@ -128,6 +128,7 @@ def _lib() -> ctypes.CDLL:
         L.jiffy_stream_copy_state.argtypes = [vp, vp, vp]
         L.jiffy_stream_device_bytes.restype = sz
         L.jiffy_stream_device_bytes.argtypes = [vp]
+        L.jiffy_stream_test_withhold_row.argtypes = [vp, u32]
         L.jiffy_standardizer_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_SensorDesc), ctypes.c_int]
         L.jiffy_standardizer_destroy.restype = None
         L.jiffy_standardizer_destroy.argtypes = [vp]
@@ -419,6 +420,14 @@ def jiffy_stream_copy_state(dst: Handle, src: Handle, stream=None):
     st = _lib().jiffy_stream_copy_state(dst.ptr, src.ptr, _stream_ptr(stream))
     if st != 0:
         raise JiffyError(st, "jiffy_stream_copy_state")
+
+
+def jiffy_stream_test_withhold_row(h: Handle, row_item: int):
+    """Test hook: the next decode call leaves row item `row_item` unpublished
+    (its dependent P row's bounded wait runs out: JIFFY_ERR_TIMEOUT)."""
+    st = _lib().jiffy_stream_test_withhold_row(h.ptr, row_item)
+    if st != 0:
+        raise JiffyError(st, "jiffy_stream_test_withhold_row")
 
 
 def jiffy_stream_device_bytes(h: Handle) -> int:

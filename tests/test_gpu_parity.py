@@ -20,7 +20,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 from paper_2209_08196_gb300 import build as jbuild  # noqa: E402
 from paper_2209_08196_gb300 import jiffy as J  # noqa: E402
 from paper_2209_08196_gb300 import synth  # noqa: E402
-from tests.gpu_util import GpuCodec  # noqa: E402
+from tests.gpu_util import TORCH_DT, GpuCodec  # noqa: E402
 
 jbuild.build()
 DT = {1: np.uint8, 2: np.uint16, 4: np.uint32}
@@ -314,3 +314,29 @@ def test_ablated_codecs_on_the_benchmark_shape(stages):
     seq = synth.ScanSequence(cfg).scans()
     check_stream(cfg.H, cfg.W, synth.attr_descs(cfg), seq, force_mode=0 if stages & 4 else -1, seq=True,
                  stages=stages)
+
+
+def test_bounded_wait_runs_out_and_the_stream_recovers():
+    # failure made on the host: one decoder row withholds its completion flag,
+    # so the same row of the next (P) frame waits until the bounded device
+    # wait gives up; the call reports a timeout, the stream's state is
+    # unchanged and the device stays usable (the same frames decode next)
+    rng = np.random.default_rng(77)
+    H, W, attrs = 8, 512, [(2, 1), (1, 1)]
+    base = [rand_scan(rng, H, W, s, 0.1) for s, _ in attrs]
+    scans = [[drift(rng, b, s, 1, 0.0) for b, (s, _) in zip(base, attrs)] for _ in range(3)]
+    gpu = GpuCodec(H, W, attrs, force_mode=1)  # frames 1 and 2 are P
+    buf, offs = gpu.encode_seq(scans)
+    assert buf == oracle.encode_sequence(H, W, attrs, scans, force_mode=1)[0]
+    src = torch.from_numpy(np.frombuffer(buf, dtype=np.uint8).copy()).cuda()
+    outs = [torch.empty((3, H, W), dtype=TORCH_DT[s], device="cuda") for s, _ in attrs]
+    J.jiffy_stream_test_withhold_row(gpu.dec, 5)  # attribute 0, scan 0, row 5
+    with pytest.raises(J.JiffyError) as ei:
+        J.jiffy_decode_seq(gpu.dec, src, len(buf), offs, outs)
+    assert ei.value.name == "JIFFY_ERR_TIMEOUT"
+    assert J.jiffy_stream_frame_index(gpu.dec) == 0
+    dec = gpu.decode_seq(buf, offs)  # same frames, no hook: decodes and matches the oracle
+    want, _ = oracle.decode_sequence(H, W, attrs, buf, 3)
+    for t in range(3):
+        for a in range(len(attrs)):
+            assert np.array_equal(dec[t][a], want[t][a])
