@@ -294,13 +294,15 @@ jiffy_status jiffy_decode_frame_noalloc(const void* in, size_t in_len, uint32_t 
 jiffy_status jiffy_stream_copy_state(jiffy_stream* dst, const jiffy_stream* src, void* cuda_stream);
 
 /* Failure-detection test hook (the failure is made on the host; nothing
- * faults): in the decoder stream's next decode call, row item `row_item` --
- * numbered (a * n_scans + t) * H + r over the call's scans t, attributes a
- * and rows r -- does not publish its completion. If the same row of the next
- * frame is a P row, its bounded device wait (2 s) runs out; the call then
- * returns JIFFY_ERR_TIMEOUT, the stream's state stays unchanged and the
- * device stays usable. Applies to one call. Errors: INVALID_ARG (not a
- * decoder). */
+ * faults): in the stream's next call, row item `row_item` -- numbered
+ * (a * n_scans + t) * H + r over the call's scans t, attributes a and rows r
+ * -- does not publish its status: a decoder row its completion (waited on by
+ * the same row of the next frame when that is a P row), an encoder row its
+ * last residual (waited on by the next row when that row's previous-row tail
+ * holds no nonzero sample). A row that waits on it gives up after the bounded
+ * device wait (2 s); the call then returns JIFFY_ERR_TIMEOUT, the stream's
+ * state stays unchanged and the device stays usable. Applies to one call.
+ * Errors: INVALID_ARG. */
 jiffy_status jiffy_stream_test_withhold_row(jiffy_stream* s, uint32_t row_item);
 
 /* Device bytes the stream holds now (state, tables and its own scratch). */

@@ -401,7 +401,7 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   uint32_t* sb = reinterpret_cast<uint32_t*>(h + u_sb);
   std::vector<uint64_t> key{1, n, (uint64_t)(uintptr_t)d, (uint64_t)(uintptr_t)h};
   std::vector<uint32_t> sig{1, max_W, log2_ceil(items)};
-  uint32_t staged = 0;
+  uint32_t staged = 0, withhold = 0;
   uint32_t item_base = 0, sec_base = 0;
   for (uint32_t i = 0; i < n; i++) {
     EncJob& j = jobs[i];
@@ -448,6 +448,8 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     segs[i] = g;
     ib[i] = item_base;
     sb[i] = sec_base;
+    if (s->withhold < T * A * s->H) withhold = item_base + s->withhold + 1u;
+    s->withhold = UINT32_MAX;  // one call
     item_base += T * A * s->H;
     sec_base += T * A;
     staged |= s->opt.stages ? 1u : 0u;
@@ -455,6 +457,7 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     key.push_back(((uint64_t)A << 32) | T);
   }
   key.push_back(staged);
+  key.push_back(withhold);
   sig.push_back(staged);
 
   jiffy::EncParams p{};
@@ -476,7 +479,8 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   p.sec_bytes = reinterpret_cast<unsigned long long*>(d + o_secb);
   p.sec_nnz = reinterpret_cast<uint32_t*>(d + o_secn);
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
-  p.staged = staged;
+  p.staged = staged | (withhold ? 1u : 0u);
+  p.withhold = withhold;
   uint8_t* hres = h + h_res;
 
   // the whole call on one stream: upload, clear, kernels, results
@@ -654,7 +658,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   p.done = reinterpret_cast<uint32_t*>(d + o_done);
   p.masks = reinterpret_cast<uint32_t*>(d + o_masks);
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
-  p.staged = staged;
+  p.staged = staged | (withhold ? 1u : 0u);
   p.withhold = withhold;
   key.push_back(withhold);
   uint8_t* hres = h + h_res;
@@ -897,7 +901,7 @@ jiffy_status jiffy_stream_copy_state(jiffy_stream* dst, const jiffy_stream* src,
 }
 
 jiffy_status jiffy_stream_test_withhold_row(jiffy_stream* s, uint32_t row_item) {
-  if (!s || s->role != JIFFY_DECODER) return JIFFY_ERR_INVALID_ARG;
+  if (!s) return JIFFY_ERR_INVALID_ARG;
   s->withhold = row_item;
   return JIFFY_OK;
 }

@@ -89,7 +89,8 @@ struct SecCache {
   unsigned long long sec;       // byte offset of the section (its row table)
 };
 
-// STAGED: the segments may have stage switches (else they are read as 0).
+// STAGED: the segments may have stage switches, or the test hook may be set
+// (else both are read as 0).
 template <bool STAGED>
 __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k, uint32_t* ring,
                                             uint32_t* patch, uint2* desc, uint8_t* mbytes, SecCache& sc) {
@@ -442,7 +443,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   if (lane == 0 && bad && status != 2u) atomicOr(sg.err, kErrCorrupt);
   __threadfence();
   __syncwarp();
-  if (lane == 0 && k + 1u != p.withhold) atomicExch(p.done + k, 1u);
+  if (lane == 0 && (!STAGED || k + 1u != p.withhold)) atomicExch(p.done + k, 1u);
 }
 
 template <int WPC, bool STAGED>

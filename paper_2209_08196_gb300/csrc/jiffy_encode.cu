@@ -644,8 +644,9 @@ __device__ __forceinline__ uint32_t pass_a_any(const uint8_t* cur, const uint8_t
   }
 }
 
-// STAGED: the segments may have stage switches (else they are read as 0 and
-// the full codec's code is all that is compiled in).
+// STAGED: the segments may have stage switches, or the test hook may be set
+// (else both are read as 0 and the full codec's code is all that is compiled
+// in).
 template <bool STAGED>
 __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k, const EncWarp& w) {
   const EncSeg& sg = p.seg[find_seg(p.seg_item_base, p.n_seg, k)];
@@ -700,7 +701,10 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   }
   __syncwarp();
   const uint32_t last_e = n ? w.zb[swz(n - 1)] : 0u;
-  if (lane == 0) {  // this row's last residual, for the rows after it
+  // (the failure-detection test hook, read by the STAGED instance only, may
+  // withhold this row's status)
+  const bool publish = !STAGED || k + 1u != p.withhold;
+  if (lane == 0 && publish) {  // this row's last residual, for the rows after it
     st_publish(p.st_carry + k, kStAgg | ((unsigned long long)(n ? 1 : 0) << 32) | last_e);
   }
   fill_tail(w.zb, n, st & kStageNoDelta);
@@ -723,7 +727,7 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
       return;
     }
   }
-  if (lane == 0) st_publish(p.st_carry + k, kStInc | (1ull << 32) | (n ? last_e : carry));
+  if (lane == 0 && publish) st_publish(p.st_carry + k, kStInc | (1ull << 32) | (n ? last_e : carry));
 
   // ---- mask part size: literal words
   const uint32_t* mbw = reinterpret_cast<const uint32_t*>(w.mb);

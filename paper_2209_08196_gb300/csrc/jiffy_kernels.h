@@ -59,7 +59,8 @@ struct EncParams {
   uint32_t* ticket;
   uint32_t wpc;                  // rows kernel: warps per CTA (1, 2, 4; 0 = by shared memory)
   uint32_t ctas_per_sm;          // rows kernel: resident CTAs per SM (0 = occupancy limit)
-  uint32_t staged;               // 1 if a segment has stage switches (the rows kernel that reads them)
+  uint32_t staged;               // 1: launch the rows kernel that reads stage switches and the test hook
+  uint32_t withhold;             // test hook: 1 + the row item that does not publish its carry status (0: none)
 };
 
 struct DecSeg {

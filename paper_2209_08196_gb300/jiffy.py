@@ -423,8 +423,8 @@ def jiffy_stream_copy_state(dst: Handle, src: Handle, stream=None):
 
 
 def jiffy_stream_test_withhold_row(h: Handle, row_item: int):
-    """Test hook: the next decode call leaves row item `row_item` unpublished
-    (its dependent P row's bounded wait runs out: JIFFY_ERR_TIMEOUT)."""
+    """Test hook: the stream's next call leaves row item `row_item` unpublished
+    (a row that waits on it gives up after the bounded wait: JIFFY_ERR_TIMEOUT)."""
     st = _lib().jiffy_stream_test_withhold_row(h.ptr, row_item)
     if st != 0:
         raise JiffyError(st, "jiffy_stream_test_withhold_row")

@@ -340,3 +340,21 @@ def test_bounded_wait_runs_out_and_the_stream_recovers():
     for t in range(3):
         for a in range(len(attrs)):
             assert np.array_equal(dec[t][a], want[t][a])
+
+
+def test_encoder_carry_wait_runs_out_and_the_stream_recovers():
+    # every row ends in 300 zero samples, so each row's delta carry comes from
+    # the look-back over the earlier rows' last residuals; one row withholds
+    # its status (host-side hook), the next row gives up after the bounded
+    # wait, the call reports a timeout and leaves the stream as it was
+    rng = np.random.default_rng(78)
+    H, W, attrs = 6, 512, [(2, 1)]
+    v = rand_scan(rng, H, W, 2, 0.05)
+    v[:, W - 300:] = 0
+    gpu = GpuCodec(H, W, attrs)
+    J.jiffy_stream_test_withhold_row(gpu.enc, 2)  # scan 0, row 2
+    with pytest.raises(J.JiffyError) as ei:
+        gpu.encode([v])
+    assert ei.value.name == "JIFFY_ERR_TIMEOUT"
+    assert J.jiffy_stream_frame_index(gpu.enc) == 0
+    assert gpu.encode([v]) == oracle.Codec(H, W, attrs).encode([v])
