@@ -245,8 +245,6 @@ __device__ __forceinline__ uint32_t unzigzag(uint32_t z) {
   return m;
 }
 
-__device__ __forceinline__ uint32_t bit_width(uint32_t x) { return 32u - __clz(x); }
-
 // Body bytes of a block of n values coded with width b, e exceptions and
 // widest value wmax bits (Sec. II, PFOR: low bits for all, exceptions apart).
 __device__ __forceinline__ uint32_t block_body_bytes(uint32_t n, uint32_t b, uint32_t e, uint32_t wmax) {
@@ -313,20 +311,19 @@ __device__ __forceinline__ void st_publish(unsigned long long* p, unsigned long 
 }
 
 // Outcome of a look-back step.
-enum : int { kLbFail = 0, kLbOk = 1, kLbPending = 2 };
+enum : int { kLbFail = 0, kLbOk = 1 };
 
 // Warp-wide window read for the look-back: kLookQ x 32 status words per
 // round, entry (q, lane) = word j - 32q - lane (nearest first), `beyond` past
 // the segment start. Finds the nearest entry that decides the look-back,
-// re-reading while an entry nearer than it is still empty (or, with wait =
-// false, returning kLbPending at once); gives up after kSpinLimitNs. stop =
-// kLookQ * 32: no decision in this window.
+// re-reading while an entry nearer than it is still empty; gives up after
+// kSpinLimitNs. stop = kLookQ * 32: no decision in this window.
 constexpr uint32_t kLookQ = 4;
 
 template <typename Decides>
 __device__ __forceinline__ int lookback_window(const unsigned long long* st, int64_t j, uint32_t seg_start,
                                                unsigned long long beyond, Decides decides,
-                                               unsigned long long (&s)[kLookQ], uint32_t& stop, bool wait) {
+                                               unsigned long long (&s)[kLookQ], uint32_t& stop) {
   const uint32_t lane = lane_id();
   unsigned long long t0 = 0;
   uint32_t ns = 32;
@@ -352,7 +349,6 @@ __device__ __forceinline__ int lookback_window(const unsigned long long* st, int
     }
     if (__any_sync(0xffffffffu, err)) return kLbFail;  // an upstream error
     if (!waiting) return kLbOk;
-    if (!wait) return kLbPending;
     if (t0 == 0) t0 = global_timer_ns();
     else if (global_timer_ns() - t0 > kSpinLimitNs) return kLbFail;
     __nanosleep(ns);
@@ -371,8 +367,8 @@ __device__ inline bool lookback_last(const unsigned long long* st, uint32_t k, u
     unsigned long long s[kLookQ];
     uint32_t stop;
     if (lookback_window(st, j, seg_start, kStInc | (1ull << 32),
-                        [](unsigned long long x) { return ((x >> 62) == 2ull) || ((x >> 32) & 1ull); }, s, stop,
-                        true) != kLbOk)
+                        [](unsigned long long x) { return ((x >> 62) == 2ull) || ((x >> 32) & 1ull); }, s,
+                        stop) != kLbOk)
       return false;
     if (stop < kLookQ * 32u) {
       uint32_t c = 0;
