@@ -455,7 +455,7 @@ __device__ __forceinline__ void pack4(uint32_t* dst, uint32_t b, uint32_t nwords
 // 128 (g + 1), so it never reaches a value still to be read): the low b
 // bits of all values, then the exceptions (values wider than b) as e
 // position bytes in ascending order and their high parts of hb bits (Sec. II,
-// PFOR). The words that are OR-ed into are zeroed first. The exceptions are listed in order in
+// PFOR). The body is zeroed first. The exceptions are listed in order in
 // xpos / xhv (a warp scan of the lanes' counts gives the ranks); lane x then
 // ORs the high part of exception x into place and lane l writes position
 // bytes 4l .. 4l+3 as one word.
@@ -474,10 +474,7 @@ __device__ __forceinline__ void pass_b2(uint32_t* zb, uint32_t n, uint32_t nb, c
     const uint4 zz = reinterpret_cast<const uint4*>(zb + 32u * sgi)[(lane & 7u) ^ (sgi & 7u)];
     const uint32_t z0 = zz.x, z1 = zz.y, z2 = zz.z, z3 = zz.w;  // 0 past m
     __syncwarp();
-    // words that are OR-ed into must start at 0: the low bits for b <= 8 and
-    // the exceptions' high parts (for b > 8 every low-bit word is written
-    // whole by its owner lane, and the position words are written whole)
-    for (uint32_t i = (b > 8u ? low_words + (e ? pw : 0u) : 0u) + lane; i < size_words; i += 32u) body[i] = 0u;
+    for (uint32_t i = lane; i < size_words; i += 32u) body[i] = 0u;
     __syncwarp();
     pack4(body, b, low_words, z0, z1, z2, z3);
     if (e) {  // e > 0 implies b < 32
