@@ -166,9 +166,11 @@ def test_many_scans_in_one_call():
             assert np.array_equal(o[t], wa), (counts, t)
 
 
-def test_largest_shape():
-    rng = np.random.default_rng(5)
-    H, W = 64, 16384
+@pytest.mark.parametrize("H,W", [(64, 16384), (4096, 64)])
+def test_largest_shapes(H, W):
+    # the widest rows, and the most beams (4096 rows: the row search over
+    # 4095 midpoints spaced 1.1e-4 rad apart)
+    rng = np.random.default_rng(5 + H)
     xyz = cloud(rng, 1_500_000, 40.0)
     check(xyz, H, W, beams(H), [(rng.uniform(0, 300, len(xyz)).astype(np.float32), 1, 1.0)])
 
