@@ -305,9 +305,10 @@ constexpr unsigned long long kStValMask = (1ull << 62) - 1;
 __device__ __forceinline__ unsigned long long st_load(const unsigned long long* p) {
   return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
-__device__ __forceinline__ void st_publish(unsigned long long* p, unsigned long long v) {
-  __threadfence();
-  atomicExch(p, v);
+// A status word carries its value with its flag, so nothing has to become
+// visible before it: one relaxed 64-bit store, no fence.
+__device__ __forceinline__ void st_store(unsigned long long* p, unsigned long long v) {
+  *reinterpret_cast<volatile unsigned long long*>(p) = v;
 }
 
 // Outcome of a look-back step.

@@ -3,31 +3,34 @@
 // One call codes T consecutive scans of each of one or more streams (the
 // segments of the call), all in parallel: the P prediction of scan t uses the
 // *input* of scan t-1 (Sec. III-D), so no scan waits for another's output.
-// Three launches:
+// Launches:
 //   k_trial     one warp per (section, test row): I and P residuals of the
 //               scanline, delta chained across the test rows, priced with
-//               the block-width pass below; the bytes add up per section and
-//               mode (trial compression, mask excluded, Sec. III-E, IV-E).
+//               the block-width choice below; the bytes add up per section
+//               and mode (trial compression, mask excluded, Sec. III-E, IV-E).
 //   k_encode    one warp per row item (scan, attribute, row), items taken in
 //               ticket order. Per row:
 //     pass A    8 consecutive pixels per lane per 256-pixel step: quantize
 //               (Sec. III-B), zero bitmask (Sec. III-C), mask XOR with the
 //               previous scan for P (Sec. III-D), residual (I: q, P: q - q'),
-//               compaction of the nonzero samples (warp scan of counts) into
-//               a swizzled shared buffer.
-//     pass B1   32 consecutive values per lane (8 blocks of 128 per warp
-//               step): delta (Sec. III-C) from the previous row's last
-//               residual, ZigZag (Eq. 1), then per block the count of values
-//               wider than b for every b at once -- carry-save adders over
-//               the values' unary width codes, bit-sliced across the 4 lanes
-//               of a block -- and the byte-minimal width (Sec. II, PFOR).
-//     pass B2   one block at a time, 4 consecutive values per lane: low bits
-//               joined with funnel shifts, each body word written once by
-//               the lane holding its first bit, exceptions listed and packed
-//               the same way; then the mask code, block headers and bodies
-//               go to the row's slot. Rows never wait for one another's
-//               sizes (sections differ a lot in cost, and an in-order prefix
-//               over rows would queue fast rows behind slow ones).
+//               compaction of the kept samples (warp scan of counts) into a
+//               padded shared buffer.
+//     steps     1024 compacted values at a time, 32 consecutive ones per
+//               lane (a block of 128 = 4 lanes): delta (Sec. III-C) from the
+//               previous row's last residual, ZigZag (Eq. 1), the
+//               byte-minimal width of every block (Sec. II, PFOR: counts of
+//               the values wider than b for all b at once, carry-save adders
+//               over unary width codes, bit-sliced across the block's 4
+//               lanes), then each lane packs its 32 values' low bits -- b
+//               words exactly -- and its exceptions (positions, high parts)
+//               straight into the row's chunk in global memory. No lane
+//               waits for another lane's words: the only words two lanes
+//               share (the ends of their high-part runs) are merged in
+//               registers through shuffles.
+//     The mask code and block headers complete the chunk, which goes to the
+//     row's slot; rows never wait for one another's sizes (sections differ a
+//     lot in cost, and an in-order prefix over rows would queue fast rows
+//     behind slow ones).
 //   k_sec_sizes one CTA per section: its bytes and nonzero count.
 //   k_place     one CTA per section: offset (sum over the earlier sections),
 //               row table, frame and stream headers, and the copy of every
@@ -40,13 +43,18 @@ namespace jiffy {
 namespace {
 
 constexpr uint32_t kStepPx = 256;    // pixels per warp step of pass A (8 per lane)
-constexpr uint32_t kStepVal = 1024;  // values per warp step of pass B1 (32 per lane)
+constexpr uint32_t kStepVal = 1024;  // values per warp step of the packing (32 per lane)
+constexpr uint32_t kFull = 0xffffffffu;
 
-// Residual buffer layout: value k lives in 32-value segment k >> 5; the
-// segment's 16-byte chunks are XOR-swizzled by the segment index so that a
-// lane reading a whole segment and a lane reading 4 consecutive values both
-// hit distinct banks.
-__device__ __forceinline__ uint32_t swz(uint32_t k) { return k ^ (((k >> 5) & 7u) << 2); }
+// Compacted-value buffer: value k at word k + 4 floor(k / 32), i.e. every
+// 32-value segment is followed by 4 pad words (segment stride 144 bytes).
+// A lane reading a whole segment as 8 16-byte vectors and lanes storing
+// consecutive values both spread over all 32 banks.
+constexpr uint32_t kSegWords = 36;
+__device__ __forceinline__ uint32_t zaddr(uint32_t k) { return k + ((k >> 5) << 2); }
+__host__ __device__ inline uint32_t zbuf_words(uint32_t W) {
+  return ceil_div_u32(W, kStepVal) * (kStepVal / 32u) * kSegWords;
+}
 
 __device__ __forceinline__ uint32_t find_seg(const uint32_t* base, uint32_t n, uint32_t key) {
   uint32_t lo = 0, hi = n;  // base[lo] <= key < base[hi] (base[n] = infinity)
@@ -104,65 +112,108 @@ __device__ __forceinline__ void st8(uint8_t* row, uint32_t s, uint32_t x0, uint3
   else store8s<S>(row, x0, nv, vec, v);
 }
 
+// ZigZag of a delta known to satisfy |d| < 2^30: with t = 2d, Eq. 1 gives
+// t for d >= 0 and 1 - t for d < 0, and in that range the wanted one is the
+// smaller as an unsigned number (d >= 0: 1 - t wraps above 2^31 unless d = 0,
+// where 0 < 1; d < 0: t wraps above 2^31, 1 - t = 2|d| + 1 < 2^31 + 1).
+// Three adds and a min, none of them on the logic/shift pipe.
+__device__ __forceinline__ uint32_t zigzag_small(uint32_t d) {
+  const uint32_t t = d + d;
+  return min(t, 1u - t);
+}
+
+__device__ __forceinline__ void quant8(uint32_t (&v)[8], const AttrDev& at) {
+  if (at.qkind == 1) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = quant<1>(v[i], at);
+  } else if (at.qkind == 2) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] = quant<2>(v[i], at);
+  }
+}
+
 // ---------------------------------------------------------------------------
-// Pass A (one row): returns the number n of nonzero samples; their residuals
-// go to zb in row-major order (swizzled), the coded mask bytes (M, or M xor
-// M_prev for P) to mb, and, for the call's last scan, q * P to st_row. kz =
-// 0xff, or 0 without the mask stage (every sample kept, mask bytes 0).
+// Pass A (one row): returns the number n of kept samples (the nonzero ones;
+// all samples with kz = 0, i.e. without the mask stage); their residuals (I:
+// q, P with prv: q - q', Sec. III-D) go to zb in row-major order (padded
+// layout), the coded mask bytes (M, or M xor M_prev for P, Sec. III-C/D) to
+// mb. qhi receives the largest quantized sample of the row (current and
+// previous scan) for 4-byte samples (0 otherwise). One copy of the code
+// serves every sample width, quantizer and mode (warp-uniform branches
+// around small blocks): the kernel is bound by instruction fetch, so its
+// footprint matters more than a few uniform branches per step.
 // ---------------------------------------------------------------------------
-template <bool PM, int QU, uint32_t S>
-__device__ __forceinline__ uint32_t pass_a(const uint8_t* cur, const uint8_t* prv, uint8_t* st_row, const AttrDev& at,
-                                           uint32_t W, uint32_t kz, uint32_t* zb, uint8_t* mb) {
+__device__ __forceinline__ uint32_t pass_a(const uint8_t* cur, const uint8_t* prv, const AttrDev& at, uint32_t W,
+                                           uint32_t kz, uint32_t* zb, uint8_t* mb, uint32_t& qhi) {
   const uint32_t lane = lane_id(), s = at.s;
-  const bool vc = vec_ok(cur, s), vp = PM && vec_ok(prv, s), vs = st_row && vec_ok(st_row, s);
+  const bool vc = vec_ok(cur, s), vp = prv && vec_ok(prv, s);
   const uint32_t Wm = (W + 31u) & ~31u;
-  uint32_t n = 0;
+  uint32_t n = 0, qm = 0;
   for (uint32_t base = 0; base < W; base += kStepPx) {
     const uint32_t x0 = base + 8u * lane;
     const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
-    uint32_t v[8], pv[8];
-    ld8<S>(cur, s, x0, nv, vc, v);
-    if (PM) ld8<S>(prv, s, x0, nv, vp, pv);
-    uint32_t e[8], zm = 0, pm = 0;
+    uint32_t v[8];
+    load8<false>(cur, s, x0, nv, vc, v);
+    quant8(v, at);
+    uint32_t keep = 0;
 #pragma unroll
-    for (int i = 0; i < 8; i++) {
-      const uint32_t q = quant<QU>(v[i], at);
-      v[i] = q;
-      zm |= (q == 0u ? 1u : 0u) << i;  // Sec. III-C: 1 = zero sample
-      if (PM) {
-        const uint32_t pq = quant<QU>(pv[i], at);
-        pm |= (pq == 0u ? 1u : 0u) << i;
-        e[i] = q - pq;  // Sec. III-D, modulo 2^32
-      } else {
-        e[i] = q;
-      }
+    for (int i = 0; i < 8; i++) keep += min(v[i], 1u) << i;  // 1 = nonzero
+    if (s == 4) {
+#pragma unroll
+      for (int i = 0; i < 8; i++) qm = max(qm, v[i]);
     }
-    zm &= kz;
     const uint32_t vm = (1u << nv) - 1u;
-    const uint32_t nz = ~zm & vm;
-    if (x0 < Wm) mb[x0 >> 3] = (uint8_t)((PM ? (zm ^ (pm & kz)) : zm) & vm);
-    if (st_row && nv) {  // the next call's previous scan, dequantized as the decoder holds it
-      uint32_t sv[8];
+    uint32_t code = ~keep & vm & kz;  // 1 = zero sample
+    if (prv) {
+      uint32_t pv[8];
+      load8<false>(prv, s, x0, nv, vp, pv);
+      quant8(pv, at);
+      uint32_t pkeep = 0;
 #pragma unroll
-      for (int i = 0; i < 8; i++) sv[i] = v[i] * at.P;
-      st8<S>(st_row, s, x0, nv, vs, sv);
+      for (int i = 0; i < 8; i++) {
+        pkeep += min(pv[i], 1u) << i;
+        if (s == 4) qm = max(qm, pv[i]);
+        v[i] -= pv[i];  // modulo 2^32
+      }
+      code ^= ~pkeep & vm & kz;
     }
+    keep = kz ? (keep & vm) : vm;
+    if (x0 < Wm) mb[x0 >> 3] = (uint8_t)code;
     uint32_t tot;
-    uint32_t kk = n + warp_excl_scan(__popc(nz), tot);
+    uint32_t kk = n + warp_excl_scan(__popc(keep), tot);
 #pragma unroll
     for (int i = 0; i < 8; i++) {
-      if ((nz >> i) & 1u) {
-        zb[swz(kk)] = e[i];
+      if ((keep >> i) & 1u) {
+        zb[zaddr(kk)] = v[i];
         kk++;
       }
     }
     n += tot;
   }
+  qhi = __reduce_max_sync(kFull, qm);
   return n;
 }
 
-// Pass A of the trial: the residuals of the row's nonzero samples (all
-// samples with kz = 0) both ways (I to zi, P to zp).
+// The call's last scan of a row, dequantized (q * P) as the decoder holds it:
+// the next call's previous scan.
+__device__ __noinline__ void state_row(const uint8_t* cur, uint8_t* st_row, const AttrDev at, uint32_t W) {
+  const uint32_t lane = lane_id(), s = at.s;
+  const bool vc = vec_ok(cur, s), vs = vec_ok(st_row, s);
+  for (uint32_t base = 0; base < W; base += kStepPx) {
+    const uint32_t x0 = base + 8u * lane;
+    const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
+    if (!nv) continue;
+    uint32_t v[8];
+    load8<false>(cur, s, x0, nv, vc, v);
+    quant8(v, at);
+#pragma unroll
+    for (int i = 0; i < 8; i++) v[i] *= at.P;
+    store8(st_row, s, x0, nv, vs, v);
+  }
+}
+
+// Pass A of the trial: the residuals of the row's kept samples both ways (I
+// to zi, P to zp).
 template <int QU>
 __device__ __forceinline__ uint32_t pass_a_trial(const uint8_t* cur, const uint8_t* prv, const AttrDev at, uint32_t W,
                                               uint32_t kz, uint32_t* zi, uint32_t* zp) {
@@ -188,8 +239,8 @@ __device__ __forceinline__ uint32_t pass_a_trial(const uint8_t* cur, const uint8
 #pragma unroll
     for (int i = 0; i < 8; i++) {
       if ((nz >> i) & 1u) {
-        zi[swz(kk)] = v[i];
-        zp[swz(kk)] = pv[i];
+        zi[zaddr(kk)] = v[i];
+        zp[zaddr(kk)] = pv[i];
         kk++;
       }
     }
@@ -224,281 +275,345 @@ __device__ __noinline__ bool row_last(const uint8_t* cur, const uint8_t* prv, co
         lp = prv ? q - quant<QU>(pv[i], at) : q;
       }
     }
-    const uint32_t hm = __ballot_sync(0xffffffffu, has);
+    const uint32_t hm = __ballot_sync(kFull, has);
     if (hm) {
       const uint32_t src = 31u - __clz(hm);
-      *e_i = __shfl_sync(0xffffffffu, li, src);
-      *e_p = __shfl_sync(0xffffffffu, lp, src);
+      *e_i = __shfl_sync(kFull, li, src);
+      *e_p = __shfl_sync(kFull, lp, src);
       return true;
     }
   }
   return false;
 }
 
-// Repeats the last residual (0 without the delta stage) from n up to the end
-// of pass B1's last step, so that those slots code to 0 (and count as
-// zero-width values).
-__device__ __forceinline__ void fill_tail(uint32_t* zb, uint32_t n, bool no_delta) {
-  if (n == 0) return;
-  const uint32_t last = no_delta ? 0u : zb[swz(n - 1)];
+// Values n .. (end of the last 1024-value step) repeat `last` (the last
+// residual, or 0 without the delta stage), so that their deltas are 0 and
+// they count as zero-width values.
+__device__ __forceinline__ void fill_tail(uint32_t* zb, uint32_t n, uint32_t last) {
   const uint32_t end = (n + kStepVal - 1) / kStepVal * kStepVal;
-  for (uint32_t k = n + lane_id(); k < end; k += 32u) zb[swz(k)] = last;
+  for (uint32_t k = n + lane_id(); k < end; k += 32u) zb[zaddr(k)] = last;
   __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
-// Pass B1: delta + ZigZag in place and the width of every block (Sec. II:
-// b in [0, wmax] minimising the block's body bytes, ties to the smallest b).
-// Lane l of a warp step holds values 32l .. 32l+31 of the step: the 4 lanes
-// 4g'..4g'+3 hold block g' of the step. For each value, its unary width code
-// has bit b set iff the value needs more than b bits, so the column sums of
-// a block's unary codes are e_b = #values wider than b, for all b at once:
-// carry-save adders give each lane its 6 bit planes (counts <= 32), two
-// bit-sliced additions across the block's 4 lanes give 8 planes (counts <=
-// 128). Each lane then prices the candidates b = j, j+4, ... (j = lane & 3).
-// meta[g] = {b | e << 8 | hb << 16, body bytes}. Returns the sum over blocks
-// of header + body bytes. st: the stream's stage switches (delta and ZigZag
-// may be off).
+// Block width (Sec. II, PFOR): b in [0, wmax] minimising the block's body
+// bytes, ties to the smallest b. Warp-wide: lane l holds the 32 consecutive
+// values z of its segment, the 4 lanes 4g'..4g'+3 (j = l & 3) hold one block
+// of m values (the values past m are 0). For each value, its unary width
+// code has bit b set iff the value needs more than b bits, so the column
+// sums of a block's unary codes are e_b = #values wider than b, for all b at
+// once: carry-save adders give each lane its 6 bit planes (counts <= 32),
+// two bit-sliced additions across the block's 4 lanes give 8 planes (counts
+// <= 128). Each lane then prices the candidates b = j, j+4, ... Returns
+// f << 14 | b << 8 | e (f = body bytes), the same in the block's 4 lanes
+// (all ones for m = 0); wmax = the bits of the block's widest value.
 // ---------------------------------------------------------------------------
-template <bool WRITE>
-__device__ __forceinline__ uint32_t pass_b1(uint32_t* zb, uint32_t n, uint32_t carry, uint2* meta, uint32_t st) {
+__device__ __forceinline__ uint32_t block_width(const uint32_t (&z)[32], uint32_t j, uint32_t m, uint32_t& wmax) {
+  // per-lane column counts of the unary width codes: 6 bit planes
+  uint32_t p1, p2, p4, p8, p16, p32;
+  {
+    uint32_t ones = 0, twos = 0, fours = 0, eights = 0, sixteens[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      uint32_t ta, tb, fa, fb, ea, eb;
+      const int o = 16 * h;
+      csa(ta, ones, ones, width_unary(z[o + 0]), width_unary(z[o + 1]));
+      csa(tb, ones, ones, width_unary(z[o + 2]), width_unary(z[o + 3]));
+      csa(fa, twos, twos, ta, tb);
+      csa(ta, ones, ones, width_unary(z[o + 4]), width_unary(z[o + 5]));
+      csa(tb, ones, ones, width_unary(z[o + 6]), width_unary(z[o + 7]));
+      csa(fb, twos, twos, ta, tb);
+      csa(ea, fours, fours, fa, fb);
+      csa(ta, ones, ones, width_unary(z[o + 8]), width_unary(z[o + 9]));
+      csa(tb, ones, ones, width_unary(z[o + 10]), width_unary(z[o + 11]));
+      csa(fa, twos, twos, ta, tb);
+      csa(ta, ones, ones, width_unary(z[o + 12]), width_unary(z[o + 13]));
+      csa(tb, ones, ones, width_unary(z[o + 14]), width_unary(z[o + 15]));
+      csa(fb, twos, twos, ta, tb);
+      csa(eb, fours, fours, fa, fb);
+      csa(sixteens[h], eights, eights, ea, eb);
+    }
+    p1 = ones; p2 = twos; p4 = fours; p8 = eights;
+    p16 = sixteens[0] ^ sixteens[1];
+    p32 = sixteens[0] & sixteens[1];
+  }
+  // bit-sliced sums across the block's 4 lanes: 8 planes E[0..7]
+  uint32_t E[8];
+  {
+    uint32_t A[6] = {p1, p2, p4, p8, p16, p32}, B[7];
+#pragma unroll
+    for (int k = 0; k < 6; k++) B[k] = __shfl_xor_sync(kFull, A[k], 1);
+    uint32_t C[7], c = 0;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+      const uint32_t u = A[k] ^ B[k];
+      C[k] = u ^ c;
+      c = (A[k] & B[k]) | (u & c);
+    }
+    C[6] = c;
+#pragma unroll
+    for (int k = 0; k < 7; k++) B[k] = __shfl_xor_sync(kFull, C[k], 2);
+    c = 0;
+#pragma unroll
+    for (int k = 0; k < 7; k++) {
+      const uint32_t u = C[k] ^ B[k];
+      E[k] = u ^ c;
+      c = (C[k] & B[k]) | (u & c);
+    }
+    E[7] = c;
+  }
+  const uint32_t anyb = E[0] | E[1] | E[2] | E[3] | E[4] | E[5] | E[6] | E[7];
+  wmax = 32u - __clz(anyb);  // e_b > 0 exactly for b < wmax
+  // e_b for b = j + 4i: nibble i of lo (low 4 bits) and hi (high 4 bits)
+  uint32_t lo4, hi4;
+  {
+    uint32_t F[8];
+#pragma unroll
+    for (int k = 0; k < 8; k++) F[k] = (E[k] >> j) & 0x11111111u;
+    lo4 = F[0] + 2u * F[1] + 4u * F[2] + 8u * F[3];
+    hi4 = F[4] + 2u * F[5] + 4u * F[6] + 8u * F[7];
+  }
+  // candidates in increasing b; the low-bit words alone, 4 ceil(mb/32),
+  // bound a candidate's bytes from below, so once that bound reaches the
+  // lane's best so far no larger b can win (ties go to the smaller b)
+  uint32_t key = 0xffffffffu;
+#pragma unroll
+  for (uint32_t i = 0; i < 9; i++) {
+    const uint32_t b = j + 4u * i;
+    const uint32_t low = 4u * ((m * b + 31u) >> 5);
+    const bool live = m != 0u && b <= wmax && low < (key >> 14);
+    if (!__any_sync(kFull, live)) break;
+    if (live) {
+      const uint32_t e = i < 8 ? ((lo4 >> (4 * i)) & 15u) | (((hi4 >> (4 * i)) & 15u) << 4) : 0u;
+      const uint32_t f = low + ((e + 3u) & ~3u) + 4u * ((e * (wmax - b) + 31u) >> 5);
+      key = min(key, (f << 14) | (b << 8) | e);
+    }
+  }
+  key = min(key, __shfl_xor_sync(kFull, key, 1));
+  key = min(key, __shfl_xor_sync(kFull, key, 2));
+  return key;
+}
+
+// Delta (Sec. III-C) and ZigZag (Eq. 1) of a lane's 32 consecutive residuals
+// in place; pred = the residual before the first. FAST: every delta is below
+// 2^30 in magnitude (zigzag_small). st: stage switches (delta and ZigZag may
+// be off, Sec. IV-H).
+template <bool STAGED, bool FAST>
+__device__ __forceinline__ void delta_zigzag(uint32_t (&z)[32], uint32_t pred, uint32_t st) {
+  if (!STAGED || !(st & (kStageNoDelta | kStageNoZigzag))) {
+#pragma unroll
+    for (int i = 31; i >= 0; i--) {
+      const uint32_t d = z[i] - (i ? z[i - 1] : pred);
+      z[i] = FAST ? zigzag_small(d) : zigzag(d);
+    }
+  } else {  // ablated codecs (Sec. IV-H); values past n are 0 without the delta
+#pragma unroll
+    for (int i = 31; i >= 0; i--) {
+      const uint32_t d = (st & kStageNoDelta) ? z[i] : z[i] - (i ? z[i - 1] : pred);
+      z[i] = (st & kStageNoZigzag) ? d : zigzag(d);
+    }
+  }
+}
+
+// Loads a lane's segment (32 consecutive values) from the padded buffer.
+__device__ __forceinline__ void load_seg(const uint32_t* zb, uint32_t seg, uint32_t (&z)[32]) {
+  const uint4* sp = reinterpret_cast<const uint4*>(zb + kSegWords * seg);
+#pragma unroll
+  for (uint32_t c = 0; c < 8; c++) {
+    const uint4 v = sp[c];
+    z[4 * c] = v.x; z[4 * c + 1] = v.y; z[4 * c + 2] = v.z; z[4 * c + 3] = v.w;
+  }
+}
+
+// Bytes of the blocks of a row's n residuals (trial pricing, Sec. III-E):
+// header + body bytes summed over the blocks, delta chained from carry.
+__device__ __forceinline__ uint32_t price_row(const uint32_t* zb, uint32_t n, uint32_t carry, uint32_t st) {
   const uint32_t lane = lane_id(), j = lane & 3u;
-  uint32_t pred_step = carry;  // the residual before the step's first value
+  uint32_t pred_step = carry;
   uint32_t total = 0;
   for (uint32_t s0 = 0; s0 < n; s0 += kStepVal) {
     const uint32_t seg = (s0 >> 5) + lane;
-    uint4* sp = reinterpret_cast<uint4*>(zb + 32u * seg);
     uint32_t z[32];
-#pragma unroll
-    for (uint32_t c = 0; c < 8; c++) {
-      const uint4 v = sp[c ^ (seg & 7u)];
-      z[4 * c] = v.x; z[4 * c + 1] = v.y; z[4 * c + 2] = v.z; z[4 * c + 3] = v.w;
-    }
-    uint32_t pred = __shfl_up_sync(0xffffffffu, z[31], 1);
+    load_seg(zb, seg, z);
+    uint32_t pred = __shfl_up_sync(kFull, z[31], 1);
     if (lane == 0) pred = pred_step;
-    pred_step = __shfl_sync(0xffffffffu, z[31], 31);
-    // delta (Sec. III-C) and ZigZag (Eq. 1); values past n repeat the last
-    // residual (fill_tail), so their ZigZag values are 0
-    if (!(st & (kStageNoDelta | kStageNoZigzag))) {
-#pragma unroll
-      for (int i = 31; i >= 0; i--) z[i] = zigzag(z[i] - (i ? z[i - 1] : pred));
-    } else {  // ablated codecs (Sec. IV-H); values past n are 0 without the delta
-#pragma unroll
-      for (int i = 31; i >= 0; i--) {
-        const uint32_t d = (st & kStageNoDelta) ? z[i] : z[i] - (i ? z[i - 1] : pred);
-        z[i] = (st & kStageNoZigzag) ? d : zigzag(d);
-      }
-    }
-    if (WRITE) {
-#pragma unroll
-      for (uint32_t c = 0; c < 8; c++) sp[c ^ (seg & 7u)] = make_uint4(z[4 * c], z[4 * c + 1], z[4 * c + 2], z[4 * c + 3]);
-    }
-    // per-lane column counts of the unary width codes: 6 bit planes
-    uint32_t p1, p2, p4, p8, p16, p32;
-    {
-      uint32_t ones = 0, twos = 0, fours = 0, eights = 0, sixteens[2];
-#pragma unroll
-      for (int h = 0; h < 2; h++) {
-        uint32_t ta, tb, fa, fb, ea, eb;
-        const int o = 16 * h;
-        csa(ta, ones, ones, width_unary(z[o + 0]), width_unary(z[o + 1]));
-        csa(tb, ones, ones, width_unary(z[o + 2]), width_unary(z[o + 3]));
-        csa(fa, twos, twos, ta, tb);
-        csa(ta, ones, ones, width_unary(z[o + 4]), width_unary(z[o + 5]));
-        csa(tb, ones, ones, width_unary(z[o + 6]), width_unary(z[o + 7]));
-        csa(fb, twos, twos, ta, tb);
-        csa(ea, fours, fours, fa, fb);
-        csa(ta, ones, ones, width_unary(z[o + 8]), width_unary(z[o + 9]));
-        csa(tb, ones, ones, width_unary(z[o + 10]), width_unary(z[o + 11]));
-        csa(fa, twos, twos, ta, tb);
-        csa(ta, ones, ones, width_unary(z[o + 12]), width_unary(z[o + 13]));
-        csa(tb, ones, ones, width_unary(z[o + 14]), width_unary(z[o + 15]));
-        csa(fb, twos, twos, ta, tb);
-        csa(eb, fours, fours, fa, fb);
-        csa(sixteens[h], eights, eights, ea, eb);
-      }
-      p1 = ones; p2 = twos; p4 = fours; p8 = eights;
-      p16 = sixteens[0] ^ sixteens[1];
-      p32 = sixteens[0] & sixteens[1];
-    }
-    // bit-sliced sums across the block's 4 lanes: 8 planes E[0..7]
-    uint32_t E[8];
-    {
-      uint32_t A[6] = {p1, p2, p4, p8, p16, p32}, B[7];
-#pragma unroll
-      for (int k = 0; k < 6; k++) B[k] = __shfl_xor_sync(0xffffffffu, A[k], 1);
-      uint32_t C[7], c = 0;
-#pragma unroll
-      for (int k = 0; k < 6; k++) {
-        const uint32_t u = A[k] ^ B[k];
-        C[k] = u ^ c;
-        c = (A[k] & B[k]) | (u & c);
-      }
-      C[6] = c;
-#pragma unroll
-      for (int k = 0; k < 7; k++) B[k] = __shfl_xor_sync(0xffffffffu, C[k], 2);
-      c = 0;
-#pragma unroll
-      for (int k = 0; k < 7; k++) {
-        const uint32_t u = C[k] ^ B[k];
-        E[k] = u ^ c;
-        c = (C[k] & B[k]) | (u & c);
-      }
-      E[7] = c;
-    }
-    const uint32_t anyb = E[0] | E[1] | E[2] | E[3] | E[4] | E[5] | E[6] | E[7];
-    const uint32_t wmax = 32u - __clz(anyb);  // e_b > 0 exactly for b < wmax
-    const uint32_t g = (s0 >> 7) + (lane >> 2);
+    pred_step = __shfl_sync(kFull, z[31], 31);
+    delta_zigzag<true, false>(z, pred, st);
+    const uint32_t g = seg >> 2;
     const uint32_t m = n > 128u * g ? min(128u, n - 128u * g) : 0u;
-    // e_b for b = j + 4i: nibble i of lo (low 4 bits) and hi (high 4 bits)
-    uint32_t lo4, hi4;
-    {
-      uint32_t F[8];
-#pragma unroll
-      for (int k = 0; k < 8; k++) F[k] = (E[k] >> j) & 0x11111111u;
-      lo4 = F[0] + 2u * F[1] + 4u * F[2] + 8u * F[3];
-      hi4 = F[4] + 2u * F[5] + 4u * F[6] + 8u * F[7];
-    }
-    // candidates in increasing b; the low-bit words alone, 4 ceil(mb/32),
-    // bound a candidate's bytes from below, so once that bound reaches the
-    // lane's best so far no larger b can win (ties go to the smaller b)
-    uint32_t key = 0xffffffffu;
-#pragma unroll
-    for (uint32_t i = 0; i < 9; i++) {
-      const uint32_t b = j + 4u * i;
-      const uint32_t low = 4u * ((m * b + 31u) >> 5);
-      const bool live = m != 0u && b <= wmax && low < (key >> 14);
-      if (!__any_sync(0xffffffffu, live)) break;
-      if (live) {
-        const uint32_t e = i < 8 ? ((lo4 >> (4 * i)) & 15u) | (((hi4 >> (4 * i)) & 15u) << 4) : 0u;
-        const uint32_t f = low + ((e + 3u) & ~3u) + 4u * ((e * (wmax - b) + 31u) >> 5);
-        key = min(key, (f << 14) | (b << 8) | e);
-      }
-    }
-    key = min(key, __shfl_xor_sync(0xffffffffu, key, 1));
-    key = min(key, __shfl_xor_sync(0xffffffffu, key, 2));
-    if (m && j == 0) {
-      const uint32_t b = (key >> 8) & 63u, e = key & 255u, f = key >> 14;
-      if (WRITE) meta[g] = make_uint2(b | (e << 8) | ((e ? wmax - b : 0u) << 16), f);
-      total += 4u + f;
-    }
+    uint32_t wmax;
+    const uint32_t key = block_width(z, j, m, wmax);
+    if (m && j == 0) total += 4u + (key >> 14);
   }
-  return __reduce_add_sync(0xffffffffu, total);
+  return __reduce_add_sync(kFull, total);
 }
 
 // ---------------------------------------------------------------------------
-// Packs 128 values of b bits, value i at bit i b (Sec. II, a block's low-bit
-// stream), into words [0, nwords) of dst, which must be zero. Lane l holds
-// values 4l .. 4l+3, bits [4lb, 4lb + 4b) of the stream, joined in registers
-// with funnel shifts. For b <= 8 (a word spans up to 8 lanes) the lanes OR
-// their 4b bits into the (at most 2) words they touch; for b > 8 each word is
-// written once, by the lane holding its first bit, completed with the next
-// lane's bits (one shuffle). Bits of the values above b are dropped.
+// Low bits of a lane's 32 values (Sec. II, PFOR: value i at bit i b of the
+// block's bit stream, LSB first). 32 values of b bits are exactly b words,
+// so a lane owns words [j b, j b + b) of its block. Words k >= lim are not
+// stored (the lane's share past the block's last value). Values wider than
+// b are cut (masked) when the block has exceptions. Each word is assembled
+// in a 64-bit accumulator (multiply-adds place the bits) and stored once.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void pack4(uint32_t* dst, uint32_t b, uint32_t nwords, uint32_t z0, uint32_t z1,
-                                      uint32_t z2, uint32_t z3) {
-  const uint32_t lane = lane_id();
-  const uint32_t S = 4u * lane * b;           // the lane's first bit
-  if (b == 0) return;
-  if (b <= 8u) {
-    const uint32_t bm = (1u << b) - 1u;
-    const uint32_t x = (z0 & bm) | ((z1 & bm) << b) | ((z2 & bm) << (2u * b)) | ((z3 & bm) << (3u * b));
-    const uint32_t sh = S & 31u, w = S >> 5;
-    const uint32_t y0 = x << sh, y1 = __funnelshift_l(x, 0u, sh);
-    if (y0) atomicOr(dst + w, y0);
-    if (y1) atomicOr(dst + w + 1u, y1);
-    return;
-  }
-  const uint32_t o = (32u - (S & 31u)) & 31u;  // the lane's first word start, relative to S
-  const uint32_t w = (S + o) >> 5;            // that word
-  if (b <= 16u) {
-    const uint32_t bm = (1u << b) - 1u;
-    const unsigned long long x = (unsigned long long)(z0 & bm) | ((unsigned long long)(z1 & bm) << b) |
-                                 ((unsigned long long)(z2 & bm) << (2u * b)) |
-                                 ((unsigned long long)(z3 & bm) << (3u * b));
-    uint32_t N = __shfl_down_sync(0xffffffffu, (uint32_t)x, 1);
-    if (lane == 31u) N = 0u;
-    const uint32_t sN = 4u * b - 32u;  // the next lane's bits start at word 1, bit sN (4..32)
-    const uint32_t Z0 = (uint32_t)x, Z1 = (uint32_t)(x >> 32) | __funnelshift_lc(0u, N, sN),
-                   Z2 = __funnelshift_lc(N, 0u, sN);
-    if (w < nwords) dst[w] = __funnelshift_r(Z0, Z1, o);
-    if (o + 32u < 4u * b && w + 1u < nwords) dst[w + 1] = __funnelshift_r(Z1, Z2, o);
-  } else {
+__device__ __forceinline__ void pack_low(const uint32_t (&z)[32], const uint32_t* zseg, uint32_t b, uint32_t lim,
+                                         bool masked, uint32_t* wp) {
+  unsigned long long acc = 0;
+  uint32_t nbit = 0, k = 0;
+  if (__all_sync(kFull, b <= 8u)) {
+    // quads: 4 values = 4b <= 32 bits, at most one word completes per quad
+    const uint32_t bm = (1u << b) - 1u, m1 = 1u << b, u4 = 4u * b;
+    const bool anym = __any_sync(kFull, masked);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+      uint32_t a0 = z[4 * q], a1 = z[4 * q + 1], a2 = z[4 * q + 2], a3 = z[4 * q + 3];
+      if (anym) { a0 &= bm; a1 &= bm; a2 &= bm; a3 &= bm; }
+      const uint32_t x = ((a3 * m1 + a2) * m1 + a1) * m1 + a0;
+      acc += (unsigned long long)x * (1u << nbit);
+      nbit += u4;
+      if (nbit >= 32u) {
+        if (k < lim) wp[k] = (uint32_t)acc;
+        k++;
+        acc >>= 32;
+        nbit -= 32u;
+      }
+    }
+  } else {  // some block of the step is wider than 8 bits (rare): one value at a time, rolled
     const uint32_t bm = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
-    const unsigned long long lo = (unsigned long long)(z0 & bm) | ((unsigned long long)(z1 & bm) << b);
-    const unsigned long long hi = (unsigned long long)(z2 & bm) | ((unsigned long long)(z3 & bm) << b);
-    const uint32_t s2 = 2u * b - 32u;  // hi starts at word 1, bit s2 (2..32)
-    const uint32_t h0 = (uint32_t)hi, h1 = (uint32_t)(hi >> 32);
-    uint32_t X0 = (uint32_t)lo, X1 = (uint32_t)(lo >> 32) | __funnelshift_lc(0u, h0, s2),
-             X2 = __funnelshift_lc(h0, h1, s2), X3 = __funnelshift_lc(h1, 0u, s2), X4 = 0u;
-    uint32_t N = __shfl_down_sync(0xffffffffu, X0, 1);
-    if (lane == 31u) N = 0u;
-    if (4u * b <= 96u) {  // the next lane's bits start at word 2, bit 4b - 64 (4..32)
-      const uint32_t sN = 4u * b - 64u;
-      X2 |= __funnelshift_lc(0u, N, sN);
-      X3 |= __funnelshift_lc(N, 0u, sN);
-    } else {  // word 3, bit 4b - 96 (4..32)
-      const uint32_t sN = 4u * b - 96u;
-      X3 |= __funnelshift_lc(0u, N, sN);
-      X4 = __funnelshift_lc(N, 0u, sN);
+#pragma unroll 1
+    for (uint32_t i = 0; i < 32; i++) {
+      acc += (unsigned long long)(zseg[i] & bm) * (1u << nbit);
+      nbit += b;
+      if (nbit >= 32u) {
+        if (k < lim) wp[k] = (uint32_t)acc;
+        k++;
+        acc >>= 32;
+        nbit -= 32u;
+      }
     }
-    if (w < nwords) dst[w] = __funnelshift_r(X0, X1, o);
-    if (o + 32u < 4u * b && w + 1u < nwords) dst[w + 1] = __funnelshift_r(X1, X2, o);
-    if (o + 64u < 4u * b && w + 2u < nwords) dst[w + 2] = __funnelshift_r(X2, X3, o);
-    if (o + 96u < 4u * b && w + 3u < nwords) dst[w + 3] = __funnelshift_r(X3, X4, o);
   }
 }
 
 // ---------------------------------------------------------------------------
-// Pass B2: packs every block's body into zb, in place and unswizzled (block
-// g's body lands in words [off_g, off_g + size_g) with off_g + size_g <=
-// 128 (g + 1), so it never reaches a value still to be read): the low b
-// bits of all values, then the exceptions (values wider than b) as e
-// position bytes in ascending order and their high parts of hb bits (Sec. II,
-// PFOR). The body is zeroed first. The exceptions are listed in order in
-// xpos / xhv (a warp scan of the lanes' counts gives the ranks); lane x then
-// ORs the high part of exception x into place and lane l writes position
-// bytes 4l .. 4l+3 as one word.
+// Exceptions of a block (Sec. II, PFOR: the values wider than b): e position
+// bytes in ascending order, zero-padded to 4 bytes, then the high parts
+// (value >> b) as a bit stream of hb bits each. Lane j of the block handles
+// its own exceptions: ranks r0 .. r0 + c - 1 (prefix of the counts over the
+// block's lanes), position bytes stored one by one, high parts appended to
+// its run of bits [r0 hb, (r0 + c) hb). Words inside a run are stored by its
+// lane; a word where runs meet belongs to the lane whose run holds its first
+// bit, which ORs in the later lanes' leading bits (shuffles) and stores it.
+// zseg: the lane's 32 ZigZag values in shared memory (dynamic indexing).
+// Warp-wide (shuffles).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void pass_b2(uint32_t* zb, uint32_t n, uint32_t nb, const uint2* meta, uint8_t* xpos,
-                                        uint32_t* xhv) {
-  const uint32_t lane = lane_id();
-  for (uint32_t g = 0; g < nb; g++) {
-    const uint2 md = meta[g];  // .x header, .y body byte offset
-    const uint32_t b = md.x & 0xffu, e = (md.x >> 8) & 0xffu, hb = (md.x >> 16) & 0xffu;
-    const uint32_t m = min(128u, n - 128u * g);
-    uint32_t* body = zb + (md.y >> 2);
-    const uint32_t low_words = (m * b + 31u) >> 5;
-    const uint32_t pw = (e + 3u) >> 2, size_words = low_words + (e ? pw + ((e * hb + 31u) >> 5) : 0u);
-    const uint32_t sgi = 4u * g + (lane >> 3);
-    const uint4 zz = reinterpret_cast<const uint4*>(zb + 32u * sgi)[(lane & 7u) ^ (sgi & 7u)];
-    const uint32_t z0 = zz.x, z1 = zz.y, z2 = zz.z, z3 = zz.w;  // 0 past m
-    __syncwarp();
-    for (uint32_t i = lane; i < size_words; i += 32u) body[i] = 0u;
-    __syncwarp();
-    pack4(body, b, low_words, z0, z1, z2, z3);
-    if (e) {  // e > 0 implies b < 32
-      const uint32_t xm = ((z0 >> b) != 0u ? 1u : 0u) | ((z1 >> b) != 0u ? 2u : 0u) |
-                          ((z2 >> b) != 0u ? 4u : 0u) | ((z3 >> b) != 0u ? 8u : 0u);
-      uint32_t unused;
-      uint32_t rank = warp_excl_scan(__popc(xm), unused);
-      if (xm & 1u) { xpos[rank] = (uint8_t)(4u * lane); xhv[rank] = z0 >> b; rank++; }
-      if (xm & 2u) { xpos[rank] = (uint8_t)(4u * lane + 1u); xhv[rank] = z1 >> b; rank++; }
-      if (xm & 4u) { xpos[rank] = (uint8_t)(4u * lane + 2u); xhv[rank] = z2 >> b; rank++; }
-      if (xm & 8u) { xpos[rank] = (uint8_t)(4u * lane + 3u); xhv[rank] = z3 >> b; }
-      __syncwarp();
-      uint32_t pword = reinterpret_cast<const uint32_t*>(xpos)[lane];
-      if (4u * lane + 4u > e) pword &= 4u * lane >= e ? 0u : ((1u << (8u * (e - 4u * lane))) - 1u);
-      if (lane < pw) body[low_words + lane] = pword;
-      uint32_t* hp = body + low_words + pw;
-      for (uint32_t x = lane; x < e; x += 32u) {
-        const uint32_t hv = xhv[x], hbit = x * hb, hs = hbit & 31u;
-        atomicOr(hp + (hbit >> 5), hv << hs);
-        if (hs + hb > 32u) atomicOr(hp + (hbit >> 5) + 1u, hv >> (32u - hs));
-      }
-    }
-    __syncwarp();
+__device__ __forceinline__ void pack_exceptions(const uint32_t (&z)[32], const uint32_t* zseg, uint32_t j, uint32_t b,
+                                                uint32_t e, uint32_t hb, uint8_t* blk, uint32_t low_words) {
+  uint32_t xm = 0;
+  if (e) {  // e > 0 implies b < 32
+#pragma unroll
+    for (int i = 0; i < 32; i++) xm |= (z[i] >> b ? 1u : 0u) << i;
   }
+  const uint32_t c = __popc(xm);
+  uint32_t incl = c;
+  {
+    const uint32_t t1 = __shfl_up_sync(kFull, incl, 1);
+    if (j >= 1) incl += t1;
+    const uint32_t t2 = __shfl_up_sync(kFull, incl, 2);
+    if (j >= 2) incl += t2;
+  }
+  const uint32_t r0 = incl - c;
+  uint8_t* pb = blk + 4u * low_words;                                              // position bytes
+  uint32_t* hw = reinterpret_cast<uint32_t*>(blk + 4u * low_words + ((e + 3u) & ~3u));  // high parts
+  const uint32_t S0 = r0 * hb;
+  uint32_t q = S0 >> 5, nbit = S0 & 31u;
+  const bool unaligned = nbit != 0u;
+  bool first = true;
+  uint32_t F = 0, Fq = 0xffffffffu;  // a first word that starts in an earlier lane's run
+  unsigned long long acc = 0;
+  uint32_t rank = r0, xs = xm;
+  while (xs) {
+    const uint32_t i = __ffs(xs) - 1u;
+    xs &= xs - 1u;
+    pb[rank++] = (uint8_t)(32u * j + i);
+    const uint32_t h = zseg[i] >> b;
+    acc += (unsigned long long)h * (1u << nbit);
+    nbit += hb;
+    if (nbit >= 32u) {
+      if (first && unaligned) { F = (uint32_t)acc; Fq = q; }
+      else hw[q] = (uint32_t)acc;
+      first = false;
+      q++;
+      acc >>= 32;
+      nbit -= 32u;
+    }
+  }
+  uint32_t Bw = 0, Bq = 0xffffffffu;  // the run's last, partial word
+  if (c && nbit) {
+    if (first && unaligned) { F = (uint32_t)acc; Fq = q; }
+    else { Bw = (uint32_t)acc; Bq = q; }
+  }
+  if (j == 3u && e) {  // zero padding of the position bytes
+    for (uint32_t t = e; t < ((e + 3u) & ~3u); t++) pb[t] = 0;
+  }
+#pragma unroll
+  for (uint32_t d = 1; d <= 3; d++) {
+    const uint32_t oq = __shfl_down_sync(kFull, Fq, d), ov = __shfl_down_sync(kFull, F, d);
+    if (j + d <= 3u && Bq != 0xffffffffu && oq == Bq) Bw |= ov;
+  }
+  if (Bq != 0xffffffffu) hw[Bq] = Bw;
+}
+
+// ---------------------------------------------------------------------------
+// One step of a row: compacted values [s0, s0 + 1024) of n (lane l: segment
+// s0/32 + l, block g = segment/4 of the row, j = l & 3). Delta from
+// pred_step (updated to the step's last residual), ZigZag, widths, block
+// headers to hdr[g], bodies from body + boff (bytes). Returns the step's
+// body bytes.
+// ---------------------------------------------------------------------------
+template <bool STAGED>
+__device__ __forceinline__ uint32_t code_step(uint32_t* zb, uint32_t s0, uint32_t n, uint32_t& pred_step, bool fast,
+                                              uint32_t st, uint32_t* hdr, uint8_t* body, uint32_t boff) {
+  const uint32_t lane = lane_id(), j = lane & 3u;
+  const uint32_t seg = (s0 >> 5) + lane;
+  uint32_t z[32];
+  load_seg(zb, seg, z);
+  uint32_t pred = __shfl_up_sync(kFull, z[31], 1);
+  if (lane == 0) pred = pred_step;
+  pred_step = __shfl_sync(kFull, z[31], 31);
+  uint4* sp = reinterpret_cast<uint4*>(zb + kSegWords * seg);  // ZigZag values back, for the exceptions
+  if (!STAGED && fast) {
+    delta_zigzag<false, true>(z, pred, st);
+#pragma unroll
+    for (uint32_t c = 0; c < 8; c++) sp[c] = make_uint4(z[4 * c], z[4 * c + 1], z[4 * c + 2], z[4 * c + 3]);
+  } else {  // deltas of 2^30 or more, or ablated codecs (Sec. IV-H; rare): rolled, through shared memory
+    uint32_t* zs = zb + kSegWords * seg;
+    uint32_t prev = pred;
+#pragma unroll 1
+    for (uint32_t i = 0; i < 32; i++) {
+      const uint32_t e = zs[i];
+      const uint32_t d = (STAGED && (st & kStageNoDelta)) ? e : e - prev;
+      zs[i] = (STAGED && (st & kStageNoZigzag)) ? d : zigzag(d);
+      prev = e;
+    }
+    load_seg(zb, seg, z);
+  }
+  const uint32_t g = seg >> 2;
+  const uint32_t m = n > 128u * g ? min(128u, n - 128u * g) : 0u;
+  uint32_t wmax;
+  const uint32_t key = block_width(z, j, m, wmax);
+  const uint32_t b = m ? (key >> 8) & 63u : 0u, e = m ? key & 255u : 0u, f = m ? key >> 14 : 0u;
+  const uint32_t hb = e ? wmax - b : 0u;
+  // the block's body offset: prefix of the sizes over the step's blocks
+  uint32_t tot;
+  const uint32_t pre = warp_excl_scan(j == 0u ? f : 0u, tot);
+  const uint32_t off = boff + __shfl_sync(kFull, pre, lane & ~3u);
+  if (j == 0u && m) hdr[g] = b | (e << 8) | (hb << 16);
+  const uint32_t low_words = (m * b + 31u) >> 5;
+  const uint32_t lim = min(b, low_words > j * b ? low_words - j * b : 0u);
+  uint8_t* blk = body + off;
+  pack_low(z, zb + kSegWords * seg, b, lim, e != 0u, reinterpret_cast<uint32_t*>(blk) + j * b);
+  if (__any_sync(kFull, e != 0u)) pack_exceptions(z, zb + kSegWords * seg, j, b, e, hb, blk, low_words);
+  return tot;
 }
 
 }  // namespace
@@ -533,7 +648,7 @@ __global__ void __launch_bounds__(32) k_trial(EncParams p) {
   const uint32_t st = sg.stages;
   const bool all = (st & kStageNoMask) != 0u;
   uint32_t* zi = smem;
-  uint32_t* zp = smem + ((W + kStepVal - 1) / kStepVal) * kStepVal;
+  uint32_t* zp = smem + zbuf_words(W);
   if (lane_id() == 0) {  // fetch the test row (both scans) and the earlier test row's tail into L2 at once
     prefetch_l2(cur + test_row(ti) * rowb, rowb);
     prefetch_l2(prv + test_row(ti) * rowb, rowb);
@@ -562,10 +677,13 @@ __global__ void __launch_bounds__(32) k_trial(EncParams p) {
   else if (at.qkind == 1) n = pass_a_trial<1>(c1, p1, at, W, kz, zi, zp);
   else n = pass_a_trial<2>(c1, p1, at, W, kz, zi, zp);
   __syncwarp();
-  fill_tail(zi, n, st & kStageNoDelta);
-  fill_tail(zp, n, st & kStageNoDelta);
-  const uint32_t cost_i = pass_b1<false>(zi, n, ci, nullptr, st);
-  const uint32_t cost_p = pass_b1<false>(zp, n, cp, nullptr, st);
+  const bool nd = (st & kStageNoDelta) != 0u;
+  if (n) {
+    fill_tail(zi, n, nd ? 0u : zi[zaddr(n - 1)]);
+    fill_tail(zp, n, nd ? 0u : zp[zaddr(n - 1)]);
+  }
+  const uint32_t cost_i = price_row(zi, n, ci, st);
+  const uint32_t cost_p = price_row(zp, n, cp, st);
   if (lane_id() == 0) {
     atomicAdd(p.cost + 2 * gs, cost_i);
     atomicAdd(p.cost + 2 * gs + 1, cost_p);
@@ -578,67 +696,45 @@ __global__ void __launch_bounds__(32) k_trial(EncParams p) {
 // earlier items) was handed out earlier. No CTA-wide barrier.
 // ----------------------------------------------------------------------------
 
-// Per-warp shared memory (byte offsets): residual / ZigZag / packed-body
-// buffer (values rounded up to whole pass-B1 steps), coded mask bytes, block
-// metadata.
+// Per-warp shared memory (byte offsets): compacted residuals / ZigZag values
+// (padded layout, whole 1024-value steps), coded mask bytes.
 struct EncWarpLayout {
-  uint32_t zb, mb, meta, xpos, xhv, bytes;
+  uint32_t zb, mb, bytes;
 };
 
 __host__ __device__ inline EncWarpLayout enc_warp_layout(uint32_t W) {
-  const uint32_t nbmax = ceil_div_u32(W, kBlockN);
   auto a16 = [](uint32_t x) { return (x + 15u) & ~15u; };
   EncWarpLayout L;
   L.zb = 0;
-  L.mb = 4u * ceil_div_u32(W, kStepVal) * kStepVal;
-  L.meta = a16(L.mb + ceil_div_u32(W, 32) * 4u);
-  L.xpos = a16(L.meta + 8u * nbmax);
-  L.xhv = L.xpos + kBlockN;
-  L.bytes = a16(L.xhv + 4u * kBlockN);
+  L.mb = 4u * zbuf_words(W);
+  L.bytes = a16(L.mb + ceil_div_u32(W, 32) * 4u);
   return L;
 }
 
 struct EncWarp {
   uint32_t* zb;
   uint8_t* mb;
-  uint2* meta;
-  uint8_t* xpos;
-  uint32_t* xhv;
 };
 
-// The last nonzero sample (with all, the last sample) among the 8 (nv valid)
-// in v / pv, across the warp: its residual (P: q - q', I: q). Returns false
-// if there is none.
-template <int QU>
-__device__ __forceinline__ bool tail_residual(const uint32_t (&v)[8], const uint32_t (&pv)[8], uint32_t nv, bool pm,
-                                              bool all, const AttrDev& at, uint32_t& e_last) {
+// The last kept sample among the 8 (nv valid) in v / pv, across the warp:
+// its residual (P: q - q', I: q). Returns false if there is none.
+__device__ __forceinline__ bool tail_residual(uint32_t (&v)[8], uint32_t (&pv)[8], uint32_t nv, bool pm, bool all,
+                                              const AttrDev& at, uint32_t& e_last) {
+  quant8(v, at);
+  if (pm) quant8(pv, at);
   bool has = false;
   uint32_t last = 0;
 #pragma unroll
   for (int i = 0; i < 8; i++) {
-    const uint32_t q = quant<QU>(v[i], at);
-    if ((uint32_t)i < nv && (q != 0u || all)) {
+    if ((uint32_t)i < nv && (v[i] != 0u || all)) {
       has = true;
-      last = pm ? q - quant<QU>(pv[i], at) : q;
+      last = pm ? v[i] - pv[i] : v[i];
     }
   }
-  const uint32_t hm = __ballot_sync(0xffffffffu, has);
+  const uint32_t hm = __ballot_sync(kFull, has);
   if (!hm) return false;
-  e_last = __shfl_sync(0xffffffffu, last, 31u - __clz(hm));
+  e_last = __shfl_sync(kFull, last, 31u - __clz(hm));
   return true;
-}
-
-template <bool PM, int QU>
-__device__ __forceinline__ uint32_t pass_a_any(const uint8_t* cur, const uint8_t* prv, uint8_t* st_row,
-                                               const AttrDev& at, uint32_t W, uint32_t kz, uint32_t* zb,
-                                               uint8_t* mb) {
-  if constexpr (QU == 2) {
-    return pass_a<PM, QU, 0>(cur, prv, st_row, at, W, kz, zb, mb);
-  } else {
-    if (at.s == 4) return pass_a<PM, QU, 4>(cur, prv, st_row, at, W, kz, zb, mb);
-    if (at.s == 2) return pass_a<PM, QU, 2>(cur, prv, st_row, at, W, kz, zb, mb);
-    return pass_a<PM, QU, 1>(cur, prv, st_row, at, W, kz, zb, mb);
-  }
 }
 
 // STAGED: the segments may have stage switches, or the test hook may be set
@@ -662,20 +758,12 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   const size_t rowb = (size_t)W * at.s;
   const uint8_t* cur = sg.cur[ta] + r * rowb;
   const uint8_t* prv = mode ? sg.prev[ta] + r * rowb : nullptr;
-  uint8_t* st_row = (t + 1 == sg.T) ? sg.state_next[a] + r * rowb : nullptr;
-  const int qk = (int)at.qkind;
   if (lane == 0) {  // fetch the row(s) into L2 ahead of the 256-pixel steps
-    const uintptr_t c0 = reinterpret_cast<uintptr_t>(cur), c1 = c0 + rowb;
-    const uintptr_t a0 = (c0 + 15u) & ~uintptr_t(15), a1 = c1 & ~uintptr_t(15);
-    if (a1 > a0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0), "r"((uint32_t)(a1 - a0)) : "memory");
-    if (prv) {
-      const uintptr_t p0 = reinterpret_cast<uintptr_t>(prv), p1 = p0 + rowb;
-      const uintptr_t b0 = (p0 + 15u) & ~uintptr_t(15), b1 = p1 & ~uintptr_t(15);
-      if (b1 > b0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(b0), "r"((uint32_t)(b1 - b0)) : "memory");
-    }
+    prefetch_l2(cur, rowb);
+    if (prv) prefetch_l2(prv, rowb);
   }
   // the previous row's last 256-pixel step, loaded now and read after pass A:
-  // its last nonzero residual is this row's delta carry (Sec. III-C)
+  // its last kept residual is this row's delta carry (Sec. III-C)
   const uint32_t nsteps = ceil_div_u32(W, kStepPx);
   const uint32_t tx0 = kStepPx * (nsteps - 1u) + 8u * lane;
   const uint32_t tnv = tx0 < W ? min(8u, W - tx0) : 0u;
@@ -686,94 +774,46 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   }
 
   // ---- pass A
-  uint32_t n;
-  if (mode) {
-    if (qk == 0) n = pass_a_any<true, 0>(cur, prv, st_row, at, W, kz, w.zb, w.mb);
-    else if (qk == 1) n = pass_a_any<true, 1>(cur, prv, st_row, at, W, kz, w.zb, w.mb);
-    else n = pass_a_any<true, 2>(cur, prv, st_row, at, W, kz, w.zb, w.mb);
-  } else {
-    if (qk == 0) n = pass_a_any<false, 0>(cur, nullptr, st_row, at, W, kz, w.zb, w.mb);
-    else if (qk == 1) n = pass_a_any<false, 1>(cur, nullptr, st_row, at, W, kz, w.zb, w.mb);
-    else n = pass_a_any<false, 2>(cur, nullptr, st_row, at, W, kz, w.zb, w.mb);
-  }
+  uint32_t qhi;
+  const uint32_t n = pass_a(cur, prv, at, W, kz, w.zb, w.mb, qhi);
+  if (t + 1 == sg.T) state_row(cur, sg.state_next[a] + r * rowb, at, W);
   __syncwarp();
-  const uint32_t last_e = n ? w.zb[swz(n - 1)] : 0u;
+  const uint32_t last_e = n ? w.zb[zaddr(n - 1)] : 0u;
   // (the failure-detection test hook, read by the STAGED instance only, may
   // withhold this row's status)
   const bool publish = !STAGED || k + 1u != p.withhold;
-  if (lane == 0 && publish) {  // this row's last residual, for the rows after it
-    st_publish(p.st_carry + k, kStAgg | ((unsigned long long)(n ? 1 : 0) << 32) | last_e);
+  if (lane == 0 && publish) {  // this row's last residual, for the rows after it (one word: no fence)
+    st_store(p.st_carry + k, kStAgg | ((unsigned long long)(n ? 1 : 0) << 32) | last_e);
   }
-  fill_tail(w.zb, n, st & kStageNoDelta);
+  if (n) fill_tail(w.zb, n, (st & kStageNoDelta) ? 0u : last_e);
 
   // ---- delta carry
   uint32_t carry = 0;
   bool known = r == 0;  // e[-1] = 0 at the start of the attribute-scan
   if (r > 0) {
-    if (qk == 0) known = tail_residual<0>(tv, tpv, tnv, prv != nullptr, kz == 0u, at, carry);
-    else if (qk == 1) known = tail_residual<1>(tv, tpv, tnv, prv != nullptr, kz == 0u, at, carry);
-    else known = tail_residual<2>(tv, tpv, tnv, prv != nullptr, kz == 0u, at, carry);
+    known = tail_residual(tv, tpv, tnv, prv != nullptr, kz == 0u, at, carry);
   }
   if (!known) {  // the previous rows' "last residual" words decide
     const bool ok = lookback_last(p.st_carry, k, sec_start, carry);
     if (!ok) {
       if (lane == 0) {
         atomicOr(sg.err, kErrTimeout);
-        st_publish(p.st_carry + k, kStErr);
+        st_store(p.st_carry + k, kStErr);
       }
       return;
     }
   }
-  if (lane == 0 && publish) st_publish(p.st_carry + k, kStInc | (1ull << 32) | (n ? last_e : carry));
 
-  // ---- mask part size: literal words
+  // ---- mask part: 2-bit class per word (16 per class word), literals
+  uint32_t* dst = reinterpret_cast<uint32_t*>(p.slots + sg.slot_base + (size_t)kl * sg.slot_bytes);
   const uint32_t* mbw = reinterpret_cast<const uint32_t*>(w.mb);
+  const uint32_t below = (1u << lane) - 1u;
   uint32_t nlit = 0;
   for (uint32_t jb = 0; jb < nw; jb += 32) {
     const uint32_t jw = jb + lane;
     const bool lit = jw < nw && mask_class(mbw[jw], valid_bits(W, nw, jw)) == 2u;
-    nlit += __popc(__ballot_sync(0xffffffffu, lit));
+    nlit += __popc(__ballot_sync(kFull, lit));
   }
-
-  // ---- pass B1: delta, ZigZag, block widths
-  const uint32_t nb = ceil_div_u32(n, kBlockN);
-  pass_b1<true>(w.zb, n, carry, w.meta, st);
-  __syncwarp();
-  // body offsets: exclusive prefix of the block bytes (lane l: 4l..4l+3)
-  uint32_t body = 0;
-  {
-    uint32_t bsz[4], mysum = 0;
-#pragma unroll
-    for (uint32_t q = 0; q < 4; q++) {
-      const uint32_t blk = 4u * lane + q;
-      bsz[q] = blk < nb ? w.meta[blk].y : 0u;
-      mysum += bsz[q];
-    }
-    uint32_t o = warp_excl_scan(mysum, body);
-#pragma unroll
-    for (uint32_t q = 0; q < 4; q++) {
-      const uint32_t blk = 4u * lane + q;
-      if (blk < nb) w.meta[blk].y = o;
-      o += bsz[q];
-    }
-  }
-  __syncwarp();
-  const uint32_t head_words = ncls + nlit + nb;
-  const uint32_t chunk = 4u * head_words + body;
-  if (lane == 0) {
-    p.row_bytes[k] = chunk;
-    p.row_nnz[k] = n;
-    p.row_carry[k] = carry;
-  }
-
-  // ---- pass B2: block bodies, packed in shared memory
-  pass_b2(w.zb, n, nb, w.meta, w.xpos, w.xhv);
-
-  // ---- the chunk goes to this row's slot; k_place moves it to its offset
-  uint32_t* dst = reinterpret_cast<uint32_t*>(p.slots + sg.slot_base + (size_t)kl * sg.slot_bytes);
-
-  // ---- mask part: 2-bit class per word (16 per class word), literals
-  const uint32_t below = (1u << lane) - 1u;
   uint32_t litbase = 0;
   for (uint32_t jb = 0; jb < nw; jb += 32) {
     const uint32_t jw = jb + lane;
@@ -781,17 +821,29 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
     const uint32_t cls = jw < nw ? mask_class(c, valid_bits(W, nw, jw)) : 0u;
     uint32_t cw = cls << (2u * (lane & 15u));
 #pragma unroll
-    for (int o = 1; o < 16; o <<= 1) cw |= __shfl_xor_sync(0xffffffffu, cw, o);
+    for (int o = 1; o < 16; o <<= 1) cw |= __shfl_xor_sync(kFull, cw, o);
     const uint32_t ci = (jb >> 4) + (lane >> 4);
     if ((lane & 15u) == 0 && ci < ncls) dst[ci] = cw;
-    const uint32_t litm = __ballot_sync(0xffffffffu, cls == 2u);
+    const uint32_t litm = __ballot_sync(kFull, cls == 2u);
     if (cls == 2u) dst[ncls + litbase + __popc(litm & below)] = c;
     litbase += __popc(litm);
   }
-  // ---- block headers and bodies
-  for (uint32_t blk = lane; blk < nb; blk += 32) dst[ncls + nlit + blk] = w.meta[blk].x;
-  uint32_t* bd = dst + head_words;
-  for (uint32_t i = lane; i < body / 4u; i += 32u) bd[i] = w.zb[i];
+
+  // ---- block headers and bodies, 1024 values per step
+  const uint32_t nb = ceil_div_u32(n, kBlockN);
+  uint32_t* hdr = dst + ncls + nlit;
+  uint8_t* body = reinterpret_cast<uint8_t*>(hdr + nb);
+  // every delta below 2^30 in magnitude: 1- and 2-byte samples always (D5),
+  // 4-byte ones when the quantized samples and the carry stay below 2^29
+  const bool fast = at.s <= 2u || (qhi < (1u << 29) && carry + (1u << 29) < (1u << 30));
+  uint32_t body_bytes = 0, pred = carry;
+  for (uint32_t s0 = 0; s0 < n; s0 += kStepVal)
+    body_bytes += code_step<STAGED>(w.zb, s0, n, pred, fast, st, hdr, body, body_bytes);
+  if (lane == 0) {
+    p.row_bytes[k] = 4u * (ncls + nlit + nb) + body_bytes;
+    p.row_nnz[k] = n;
+    p.row_carry[k] = carry;
+  }
   __syncwarp();
 }
 
@@ -804,15 +856,17 @@ __global__ void __launch_bounds__(WPC * 32, 24 / WPC) k_encode(EncParams p) {
   EncWarp w;
   w.zb = reinterpret_cast<uint32_t*>(wb + lay.zb);
   w.mb = wb + lay.mb;
-  w.meta = reinterpret_cast<uint2*>(wb + lay.meta);
-  w.xpos = wb + lay.xpos;
-  w.xhv = reinterpret_cast<uint32_t*>(wb + lay.xhv);
-  while (true) {
-    uint32_t k = 0;
-    if (lane == 0) k = atomicAdd(p.ticket, 1u);
-    k = __shfl_sync(0xffffffffu, k, 0);
-    if (k >= p.n_items) break;
+  // the next ticket is requested before the current item is coded, so its
+  // round trip overlaps the work (an item still waits only on items handed
+  // out before it: a warp holding an unstarted ticket is coding a smaller one)
+  uint32_t k = 0;
+  if (lane == 0) k = atomicAdd(p.ticket, 1u);
+  k = __shfl_sync(kFull, k, 0);
+  while (k < p.n_items) {
+    uint32_t next = 0;
+    if (lane == 0) next = atomicAdd(p.ticket, 1u);
     encode_item<STAGED>(p, k, w);
+    k = __shfl_sync(kFull, next, 0);
   }
 }
 
@@ -960,7 +1014,7 @@ static cudaError_t rows_occupancy(size_t smem, bool staged, int* per_sm) {
 
 int encode_rows_launch(const EncParams& p, RowsLaunch* out) {
   const EncWarpLayout L = enc_warp_layout(p.max_W);
-  if ((L.mb | L.meta | L.xpos | L.xhv | L.bytes) & 15u) return (int)cudaErrorInvalidValue;  // 16-byte aligned regions
+  if ((L.mb | L.bytes) & 15u) return (int)cudaErrorInvalidValue;  // 16-byte aligned regions
   uint32_t wpc = p.wpc;
   if ((wpc != 1 && wpc != 2 && wpc != 4) || wpc * L.bytes > kRowsSmemMax) wpc = 0;
   if (!wpc) wpc = 4 * L.bytes <= kRowsSmemAuto ? 4u : (2 * L.bytes <= kRowsSmemAuto ? 2u : 1u);
@@ -985,7 +1039,7 @@ int encode_rows_launch(const EncParams& p, RowsLaunch* out) {
   return 0;
 }
 
-size_t trial_smem_bytes_host(uint32_t W) { return 2ull * 4u * ceil_div_u32(W, kStepVal) * kStepVal; }
+size_t trial_smem_bytes_host(uint32_t W) { return 2ull * 4u * zbuf_words(W); }
 
 int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

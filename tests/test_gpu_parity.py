@@ -343,14 +343,16 @@ def test_bounded_wait_runs_out_and_the_stream_recovers():
 
 
 def test_encoder_carry_wait_runs_out_and_the_stream_recovers():
-    # every row ends in 300 zero samples, so each row's delta carry comes from
-    # the look-back over the earlier rows' last residuals; one row withholds
-    # its status (host-side hook), the next row gives up after the bounded
-    # wait, the call reports a timeout and leaves the stream as it was
+    # only row 0 has nonzero samples, so a row r >= 5 finds no kept sample
+    # among the 2048 samples before it (the direct search) and its delta
+    # carry comes from the look-back over the earlier rows' last residuals;
+    # one row withholds its status (host-side hook), the rows after it give
+    # up after the bounded wait, the call reports a timeout and leaves the
+    # stream as it was
     rng = np.random.default_rng(78)
-    H, W, attrs = 6, 512, [(2, 1)]
+    H, W, attrs = 8, 512, [(2, 1)]
     v = rand_scan(rng, H, W, 2, 0.05)
-    v[:, W - 300:] = 0
+    v[1:, :] = 0
     gpu = GpuCodec(H, W, attrs)
     J.jiffy_stream_test_withhold_row(gpu.enc, 2)  # scan 0, row 2
     with pytest.raises(J.JiffyError) as ei:
