@@ -162,6 +162,35 @@ jiffy_status jiffy_decode(jiffy_stream* s, const void* in, size_t in_len, void* 
 jiffy_status jiffy_decode_seq(jiffy_stream* s, uint32_t n_scans, const void* in, size_t in_len,
                               const uint64_t* frame_offsets, void* const* planes_out, void* cuda_stream);
 
+/* Enqueue-only forms of jiffy_encode_seq / jiffy_decode_seq, for a pipeline
+ * that stays on the device: an encode followed by a decode on the same CUDA
+ * stream needs no host round trip in between. Each returns once its work is
+ * on cuda_stream, without waiting.
+ *
+ * jiffy_encode_seq_async: as jiffy_encode_seq, but the n_scans + 1 frame
+ * offsets (the last one = the bytes written) go to frame_offsets_dev, a
+ * device array of uint64 (8-byte aligned; nullable), and no length comes
+ * back to the host. jiffy_decode_seq_async: as jiffy_decode_seq, but
+ * frame_offsets_dev is a device array (as written by jiffy_encode_seq_async)
+ * and in_capacity the bytes readable at `in`; the kernel checks every offset
+ * (aligned, increasing by at least a frame header, inside in_capacity) before
+ * reading, so a bad offset is CORRUPT, never an out-of-bounds read.
+ *
+ * The stream's state advances at once; a stream may take several
+ * enqueue-only calls in a row. Argument errors are returned at once; errors
+ * found on the device (CORRUPT, CAPACITY, TIMEOUT) are reported by the next
+ * jiffy_stream_wait, after which a stream that failed holds no usable
+ * previous scan and must be reset. The device buffers must stay valid until
+ * the work is done; a synchronous call on the stream waits first. */
+jiffy_status jiffy_encode_seq_async(jiffy_stream* s, uint32_t n_scans, const void* const* planes, void* out,
+                                    size_t out_capacity, uint64_t* frame_offsets_dev, void* cuda_stream);
+jiffy_status jiffy_decode_seq_async(jiffy_stream* s, uint32_t n_scans, const void* in, size_t in_capacity,
+                                    const uint64_t* frame_offsets_dev, void* const* planes_out, void* cuda_stream);
+
+/* Waits for the stream's enqueue-only calls and returns JIFFY_OK, or the
+ * error the device reported for any of them (then reset the stream). */
+jiffy_status jiffy_stream_wait(jiffy_stream* s);
+
 /* ---- Many streams in one pass (serving many sensors). A batch context owns
  * the scratch of batched calls on one device. In one call every stream
  * codes its own consecutive scans; all rows of all streams run in the same
@@ -259,8 +288,9 @@ jiffy_status jiffy_stream_set_profiling(jiffy_stream* s, int enable);
 
 /* Device milliseconds of each kernel launched by the stream's last
  * successful call, in launch order (encode: trial, rows, placement; decode:
- * rows). Writes min(n, count) values to ms (host) and returns the
- * count (0 if profiling is off or no call completed). */
+ * rows); after jiffy_stream_wait, the averages over the enqueue-only calls
+ * since the previous wait. Writes min(n, count) values to ms (host) and
+ * returns the count (0 if profiling is off or no call completed). */
 uint32_t jiffy_stream_kernel_times(const jiffy_stream* s, float* ms, uint32_t n);
 
 /* Allocation-free decode of one frame, for callers that may not allocate

@@ -38,6 +38,8 @@ struct EncJob {
   uint64_t* frame_offsets;    // host, T+1, nullable
   size_t* out_len;            // host
   jiffy_status* status;       // host
+  bool async = false;         // enqueue only: errors to the stream's device word
+  uint64_t* dev_offsets = nullptr;  // device, T+1, nullable (async)
 };
 
 struct DecJob {
@@ -45,9 +47,10 @@ struct DecJob {
   uint32_t T;
   const void* in;
   size_t in_len;
-  const uint64_t* frame_offsets;  // host, T+1
+  const uint64_t* frame_offsets;  // host, T+1 (device with async)
   void* const* planes_out;        // T*A device pointers
   jiffy_status* status;           // host
+  bool async = false;             // enqueue only: offsets on the device, checked by the kernel
 };
 
 // A call enqueued on the device whose results are not read yet.
@@ -87,6 +90,18 @@ struct Workspace {
   RowsLaunch fixed[2] = {};  // launch requests set by the caller (encode, decode); 0 = automatic
   uint64_t calls = 0, captures = 0, replays = 0, tunings = 0;
   Pending pend;
+  cudaEvent_t uploaded = nullptr;  // the last call's segment table has reached the device
+  bool upload_pending = false;     // an enqueue-only call may still read the pinned table
+  // kernel timing of enqueue-only calls: a ring of event sets, harvested as
+  // they complete and averaged at jiffy_stream_wait
+  struct EvSet {
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint32_t nk = 0;
+  };
+  std::vector<EvSet> ring;
+  size_t ring_tail = 0, ring_count = 0;
+  double acc_ms[3] = {0, 0, 0};
+  uint32_t acc_calls = 0, acc_nk = 0;
 };
 
 }  // namespace
@@ -105,6 +120,9 @@ struct jiffy_stream {
   uint32_t frame = 0;                         // frames since create/reset
   bool in_flight = false;                     // part of an enqueued, unfinished call
   uint32_t withhold = UINT32_MAX;             // test hook: row item of the next decode call left unpublished
+  uint32_t* d_err = nullptr;                  // error bits of enqueue-only calls (device)
+  cudaEvent_t async_done = nullptr;           // recorded after the last enqueue-only call
+  bool async_out = false;                     // enqueue-only calls not yet waited for
 };
 
 struct jiffy_batch {
@@ -143,6 +161,8 @@ void drop_graph(GraphCache& g) {
 }
 
 jiffy_status ensure_scratch(Workspace& w, size_t dev_bytes, size_t host_bytes) {
+  // enqueue-only calls may still use the buffers about to be replaced
+  if ((dev_bytes > w.scratch_cap || host_bytes > w.pinned_cap) && w.upload_pending) cudaDeviceSynchronize();
   if (dev_bytes > w.scratch_cap) {
     drop_graph(w.g_enc);  // the captured sequences point into the old buffers
     drop_graph(w.g_dec);
@@ -164,6 +184,64 @@ jiffy_status ensure_scratch(Workspace& w, size_t dev_bytes, size_t host_bytes) {
     w.pinned_cap = cap;
   }
   if (!w.done && cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming) != cudaSuccess) return JIFFY_ERR_CUDA;
+  if (!w.uploaded && cudaEventCreateWithFlags(&w.uploaded, cudaEventDisableTiming) != cudaSuccess)
+    return JIFFY_ERR_CUDA;
+  return JIFFY_OK;
+}
+
+// Moves the kernel times of completed enqueue-only calls into the running
+// sums (block: wait for all of them).
+void harvest(Workspace& w, bool block) {
+  while (w.ring_count) {
+    Workspace::EvSet& es = w.ring[w.ring_tail];
+    const cudaError_t q = block ? cudaEventSynchronize(es.e[es.nk]) : cudaEventQuery(es.e[es.nk]);
+    if (q != cudaSuccess) break;
+    for (uint32_t k = 0; k < es.nk; k++) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, es.e[k], es.e[k + 1]) == cudaSuccess) w.acc_ms[k] += ms;
+    }
+    w.acc_nk = es.nk;
+    w.acc_calls++;
+    w.ring_tail = (w.ring_tail + 1) % w.ring.size();
+    w.ring_count--;
+  }
+}
+
+// An event set for the next timed enqueue-only call of nk kernels.
+void* const* next_evset(Workspace& w, uint32_t nk) {
+  if (w.ring.empty()) {
+    w.ring.resize(16);
+    for (Workspace::EvSet& es : w.ring)
+      for (cudaEvent_t& e : es.e)
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  }
+  harvest(w, false);
+  if (w.ring_count == w.ring.size()) {  // the device is 16 calls behind: wait for the oldest
+    Workspace::EvSet& old = w.ring[w.ring_tail];
+    cudaEventSynchronize(old.e[old.nk]);
+    harvest(w, false);
+  }
+  Workspace::EvSet& es = w.ring[(w.ring_tail + w.ring_count) % w.ring.size()];
+  es.nk = nk;
+  w.ring_count++;
+  return reinterpret_cast<void* const*>(es.e);
+}
+
+// Records ev on st; inside a stream capture it becomes an event-record node
+// of the graph, so a replay records it too.
+cudaError_t record_ev(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    return cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+  return cudaEventRecord(ev, st);
+}
+
+// Before the host rewrites the pinned segment table: an enqueue-only call
+// may not have copied it to the device yet.
+jiffy_status wait_upload(Workspace& w) {
+  if (!w.upload_pending) return JIFFY_OK;
+  if (cudaEventSynchronize(w.uploaded) != cudaSuccess) return JIFFY_ERR_CUDA;
+  w.upload_pending = false;
   return JIFFY_OK;
 }
 
@@ -176,6 +254,10 @@ void release(Workspace& w) {
     if (e) cudaEventDestroy(e);
   if (w.done) cudaEventDestroy(w.done);
   if (w.capture) cudaStreamDestroy(w.capture);
+  if (w.uploaded) cudaEventDestroy(w.uploaded);
+  for (Workspace::EvSet& es : w.ring)
+    for (cudaEvent_t e : es.e)
+      if (e) cudaEventDestroy(e);
   w = Workspace{};
 }
 
@@ -336,8 +418,9 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     *j.status = JIFFY_OK;
     jiffy_stream* s = j.s;
     ss[i] = s;
-    if (!s || !j.planes || !j.out || !j.out_len || j.T == 0) return JIFFY_ERR_INVALID_ARG;
+    if (!s || !j.planes || !j.out || (!j.out_len && !j.async) || j.T == 0) return JIFFY_ERR_INVALID_ARG;
     if (s->role != JIFFY_ENCODER || s->ws.device != ws.device || s->in_flight) return JIFFY_ERR_STATE;
+    if (j.async && (reinterpret_cast<uintptr_t>(j.dev_offsets) & 7u)) return JIFFY_ERR_INVALID_ARG;
     if (reinterpret_cast<uintptr_t>(j.out) & 15u) return JIFFY_ERR_INVALID_ARG;
     for (size_t q = 0; q < (size_t)j.T * s->A; q++)
       if (!j.planes[q]) return JIFFY_ERR_INVALID_ARG;
@@ -392,6 +475,7 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   const size_t o_slots = c.take(slots_total);
   const size_t h_res = align_up(up.off, 256);
   jiffy_status r = ensure_scratch(ws, c.off, h_res + rs.off);
+  if (r == JIFFY_OK) r = wait_upload(ws);
   if (r != JIFFY_OK) return r;
   uint8_t* d = ws.d_scratch;
   uint8_t* h = ws.h_pinned;
@@ -443,8 +527,9 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     g.state_next = reinterpret_cast<uint8_t* const*>(dp + 16ull * T * A);
     g.out = static_cast<uint8_t*>(j.out);
     g.cap = j.cap;
-    g.frame_off = reinterpret_cast<unsigned long long*>(d + o_res + r_off[i]);
-    g.err = reinterpret_cast<uint32_t*>(d + o_res + r_err[i]);
+    g.frame_off = (j.async && j.dev_offsets) ? reinterpret_cast<unsigned long long*>(j.dev_offsets)
+                                             : reinterpret_cast<unsigned long long*>(d + o_res + r_off[i]);
+    g.err = j.async ? s->d_err : reinterpret_cast<uint32_t*>(d + o_res + r_err[i]);
     segs[i] = g;
     ib[i] = item_base;
     sb[i] = sec_base;
@@ -459,6 +544,8 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   key.push_back(staged);
   key.push_back(withhold);
   sig.push_back(staged);
+  bool async = false;
+  for (const EncJob& j : jobs) async |= j.async;
 
   jiffy::EncParams p{};
   p.n_seg = n;
@@ -486,6 +573,7 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   // the whole call on one stream: upload, clear, kernels, results
   auto enqueue = [&](cudaStream_t s, const jiffy::EncParams& pp, void* const* evs) -> int {
     cudaError_t ce = cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess && async) ce = record_ev(ws.uploaded, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, s);
     if (ce != cudaSuccess) return (int)ce;
     const int rc = jiffy::launch_encode(pp, s, evs);
@@ -509,14 +597,31 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   if (jiffy::encode_rows_launch(p, &ws.last) != 0) return JIFFY_ERR_CUDA;
   key.push_back(((uint64_t)p.wpc << 32) | p.ctas_per_sm);
   key.push_back(trial_rows);
+  key.push_back(async ? 1u : 0u);
+  for (const EncJob& j : jobs) key.push_back((uint64_t)(uintptr_t)j.dev_offsets);
   const bool timed = ws.profile;
   key.push_back(timed ? 1u : 0u);
   void* evs[4] = {ws.ev[0], ws.ev[1], ws.ev[2], ws.ev[3]};
-  r = run_sequence(ws, ws.g_enc, key, st, ws.graphs,
-                   [&](cudaStream_t s) { return enqueue(s, p, timed ? evs : nullptr); });
+  void* const* tev = timed ? (async ? next_evset(ws, 3) : evs) : nullptr;
+  if (timed && !tev) return JIFFY_ERR_CUDA;
+  // (a timed enqueue-only call uses the next event set of the ring: launched
+  // directly, not replayed from the graph, whose events are fixed)
+  r = run_sequence(ws, ws.g_enc, key, st, ws.graphs && !(async && timed),
+                   [&](cudaStream_t s) { return enqueue(s, p, tev); });
   if (r != JIFFY_OK) return r;
   if (cudaEventRecord(ws.done, st) != cudaSuccess) return JIFFY_ERR_CUDA;
   ws.calls++;
+  if (async) {  // enqueue only: nothing to read back; errors go to the stream's device word
+    ws.upload_pending = true;
+    for (EncJob& j : jobs) {
+      j.s->cur = 1 - j.s->cur;
+      j.s->frame += j.T;
+      j.s->async_out = true;
+      if (cudaEventRecord(j.s->async_done, st) != cudaSuccess) return JIFFY_ERR_CUDA;
+    }
+    ws.n_kernel_ms = 0;
+    return JIFFY_OK;
+  }
   // the streams advance now; finish() rolls back those that failed
   for (EncJob& j : jobs) {
     j.s->cur = 1 - j.s->cur;
@@ -549,6 +654,12 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
     if (reinterpret_cast<uintptr_t>(j.in) & 3u) return JIFFY_ERR_INVALID_ARG;
     for (size_t q = 0; q < (size_t)j.T * s->A; q++)
       if (!j.planes_out[q]) return JIFFY_ERR_INVALID_ARG;
+    if (j.async) {  // the offsets are on the device: the kernel checks them
+      if (reinterpret_cast<uintptr_t>(j.frame_offsets) & 7u) return JIFFY_ERR_INVALID_ARG;
+      items += (unsigned long long)j.T * s->A * s->H;
+      if (s->W > max_W) max_W = s->W;
+      continue;
+    }
     // frame offsets: aligned, increasing by at least a frame header, inside `in`
     const uint64_t* fo = j.frame_offsets;
     const uint32_t fh = frame_header_bytes(s->A);
@@ -594,6 +705,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   const size_t o_masks = c.take(4ull * mask_words);
   const size_t h_res = align_up(up.off, 256);
   jiffy_status r = ensure_scratch(ws, c.off, h_res + rs.off);
+  if (r == JIFFY_OK) r = wait_upload(ws);
   if (r != JIFFY_OK) return r;
   uint8_t* d = ws.d_scratch;
   uint8_t* h = ws.h_pinned;
@@ -614,7 +726,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
       hp[(size_t)T * A + a] = reinterpret_cast<uint64_t>(s->d_state[s->cur] + s->plane_off[a]);
       hp[(size_t)T * A + A + a] = reinterpret_cast<uint64_t>(s->d_state[1 - s->cur] + s->plane_off[a]);
     }
-    std::memcpy(hp + (size_t)(T + 2) * A, j.frame_offsets, 8ull * (T + 1));
+    if (!j.async) std::memcpy(hp + (size_t)(T + 2) * A, j.frame_offsets, 8ull * (T + 1));
     const uint8_t* dp = d + o_up + u_ptrs[i];
     jiffy::DecSeg g{};
     g.H = s->H;
@@ -634,8 +746,9 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
     g.outp = reinterpret_cast<uint8_t* const*>(dp);
     g.state = reinterpret_cast<const uint8_t* const*>(dp + 8ull * T * A);
     g.state_next = reinterpret_cast<uint8_t* const*>(dp + 8ull * (T + 1) * A);
-    g.off = reinterpret_cast<const unsigned long long*>(dp + 8ull * (T + 2) * A);
-    g.err = reinterpret_cast<uint32_t*>(d + o_res + r_err[i]);
+    g.off = j.async ? reinterpret_cast<const unsigned long long*>(j.frame_offsets)
+                    : reinterpret_cast<const unsigned long long*>(dp + 8ull * (T + 2) * A);
+    g.err = j.async ? s->d_err : reinterpret_cast<uint32_t*>(d + o_res + r_err[i]);
     g.mask_base = mask_base[i];
     segs[i] = g;
     ib[i] = item_base;
@@ -648,6 +761,12 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   }
   key.push_back(staged);
   sig.push_back(staged);
+  bool async = false;
+  for (const DecJob& j : jobs) {
+    async |= j.async;
+    if (j.async) key.push_back((uint64_t)(uintptr_t)j.frame_offsets);
+  }
+  key.push_back(async ? 1u : 0u);
 
   jiffy::DecParams p{};
   p.n_seg = n;
@@ -665,6 +784,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
 
   auto enqueue = [&](cudaStream_t s, const jiffy::DecParams& pp, void* const* evs) -> int {
     cudaError_t ce = cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, s);
+    if (ce == cudaSuccess && async) ce = record_ev(ws.uploaded, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, s);
     if (ce != cudaSuccess) return (int)ce;
     const int rc = jiffy::launch_decode(pp, s, evs);
@@ -693,11 +813,24 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   const bool timed = ws.profile;
   key.push_back(timed ? 1u : 0u);
   void* evs[2] = {ws.ev[0], ws.ev[1]};
-  r = run_sequence(ws, ws.g_dec, key, st, ws.graphs,
-                   [&](cudaStream_t s) { return enqueue(s, p, timed ? evs : nullptr); });
+  void* const* tev = timed ? (async ? next_evset(ws, 1) : evs) : nullptr;
+  if (timed && !tev) return JIFFY_ERR_CUDA;
+  r = run_sequence(ws, ws.g_dec, key, st, ws.graphs && !(async && timed),
+                   [&](cudaStream_t s) { return enqueue(s, p, tev); });
   if (r != JIFFY_OK) return r;
   if (cudaEventRecord(ws.done, st) != cudaSuccess) return JIFFY_ERR_CUDA;
   ws.calls++;
+  if (async) {  // enqueue only: nothing to read back; errors go to the stream's device word
+    ws.upload_pending = true;
+    for (DecJob& j : jobs) {
+      j.s->cur = 1 - j.s->cur;
+      j.s->frame += j.T;
+      j.s->async_out = true;
+      if (cudaEventRecord(j.s->async_done, st) != cudaSuccess) return JIFFY_ERR_CUDA;
+    }
+    ws.n_kernel_ms = 0;
+    return JIFFY_OK;
+  }
   for (DecJob& j : jobs) {
     j.s->cur = 1 - j.s->cur;
     j.s->frame += j.T;
@@ -845,8 +978,11 @@ jiffy_status jiffy_stream_create(jiffy_stream** out, jiffy_role role, uint32_t H
   jiffy_status st = JIFFY_OK;
   if (cudaMalloc(&s->d_attrs, sizeof(AttrDev) * n_attr) != cudaSuccess ||
       cudaMalloc(&s->d_state[0], state_bytes) != cudaSuccess ||
-      cudaMalloc(&s->d_state[1], state_bytes) != cudaSuccess) {
+      cudaMalloc(&s->d_state[1], state_bytes) != cudaSuccess || cudaMalloc(&s->d_err, 4) != cudaSuccess) {
     st = JIFFY_ERR_NOMEM;
+  } else if (cudaEventCreateWithFlags(&s->async_done, cudaEventDisableTiming) != cudaSuccess ||
+             cudaMemset(s->d_err, 0, 4) != cudaSuccess) {
+    st = JIFFY_ERR_CUDA;
   } else if (cudaMemcpy(s->d_attrs, s->attrs.data(), sizeof(AttrDev) * n_attr, cudaMemcpyHostToDevice) !=
                  cudaSuccess ||
              cudaMemset(s->d_state[0], 0, state_bytes) != cudaSuccess ||
@@ -868,6 +1004,8 @@ void jiffy_stream_destroy(jiffy_stream* s) {
   if (s->d_attrs) cudaFree(s->d_attrs);
   if (s->d_state[0]) cudaFree(s->d_state[0]);
   if (s->d_state[1]) cudaFree(s->d_state[1]);
+  if (s->d_err) cudaFree(s->d_err);
+  if (s->async_done) cudaEventDestroy(s->async_done);
   release(s->ws);
   delete s;
 }
@@ -917,11 +1055,62 @@ uint32_t jiffy_stream_kernel_times(const jiffy_stream* s, float* ms, uint32_t n)
   return s->ws.n_kernel_ms;
 }
 
+jiffy_status jiffy_stream_wait(jiffy_stream* s) {
+  if (!s) return JIFFY_ERR_INVALID_ARG;
+  if (!s->async_out) return JIFFY_OK;
+  DeviceGuard g(s->ws.device);
+  if (!g.ok) return JIFFY_ERR_CUDA;
+  uint32_t err = 0;
+  if (cudaEventSynchronize(s->async_done) != cudaSuccess || cudaMemcpy(&err, s->d_err, 4, cudaMemcpyDeviceToHost) !=
+      cudaSuccess || cudaMemset(s->d_err, 0, 4) != cudaSuccess)
+    return JIFFY_ERR_CUDA;
+  s->async_out = false;
+  s->ws.upload_pending = false;
+  Workspace& w = s->ws;  // kernel times: averages over the calls since the last wait
+  harvest(w, true);
+  if (w.acc_calls) {
+    for (uint32_t k = 0; k < w.acc_nk; k++) w.kernel_ms[k] = (float)(w.acc_ms[k] / w.acc_calls);
+    w.n_kernel_ms = w.acc_nk;
+  }
+  w.acc_ms[0] = w.acc_ms[1] = w.acc_ms[2] = 0;
+  w.acc_calls = 0;
+  return map_device_error(err);
+}
+
+jiffy_status jiffy_encode_seq_async(jiffy_stream* s, uint32_t n_scans, const void* const* planes, void* out,
+                                    size_t out_capacity, uint64_t* frame_offsets_dev, void* cuda_stream) {
+  if (!s) return JIFFY_ERR_INVALID_ARG;
+  DeviceGuard g(s->ws.device);
+  if (!g.ok) return JIFFY_ERR_CUDA;
+  jiffy_status st = JIFFY_OK;
+  EncJob job{s, n_scans, planes, out, out_capacity, nullptr, nullptr, &st};
+  job.async = true;
+  job.dev_offsets = frame_offsets_dev;
+  std::vector<EncJob> jobs{job};
+  return enqueue_encode(s->ws, jobs, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
+jiffy_status jiffy_decode_seq_async(jiffy_stream* s, uint32_t n_scans, const void* in, size_t in_capacity,
+                                    const uint64_t* frame_offsets_dev, void* const* planes_out, void* cuda_stream) {
+  if (!s) return JIFFY_ERR_INVALID_ARG;
+  DeviceGuard g(s->ws.device);
+  if (!g.ok) return JIFFY_ERR_CUDA;
+  jiffy_status st = JIFFY_OK;
+  DecJob job{s, n_scans, in, in_capacity, frame_offsets_dev, planes_out, &st};
+  job.async = true;
+  std::vector<DecJob> jobs{job};
+  return enqueue_decode(s->ws, jobs, reinterpret_cast<cudaStream_t>(cuda_stream));
+}
+
 jiffy_status jiffy_encode_seq(jiffy_stream* s, uint32_t n_scans, const void* const* planes, void* out,
                               size_t out_capacity, uint64_t* frame_offsets, size_t* out_len, void* cuda_stream) {
   if (!s) return JIFFY_ERR_INVALID_ARG;
   DeviceGuard g(s->ws.device);
   if (!g.ok) return JIFFY_ERR_CUDA;
+  if (s->async_out) {  // earlier enqueue-only calls first
+    const jiffy_status w = jiffy_stream_wait(s);
+    if (w != JIFFY_OK) return w;
+  }
   jiffy_status st = JIFFY_OK;
   std::vector<EncJob> jobs{EncJob{s, n_scans, planes, out, out_capacity, frame_offsets, out_len, &st}};
   return run_encode(s->ws, jobs, reinterpret_cast<cudaStream_t>(cuda_stream));
@@ -937,6 +1126,10 @@ jiffy_status jiffy_decode_seq(jiffy_stream* s, uint32_t n_scans, const void* in,
   if (!s) return JIFFY_ERR_INVALID_ARG;
   DeviceGuard g(s->ws.device);
   if (!g.ok) return JIFFY_ERR_CUDA;
+  if (s->async_out) {  // earlier enqueue-only calls first
+    const jiffy_status w = jiffy_stream_wait(s);
+    if (w != JIFFY_OK) return w;
+  }
   jiffy_status st = JIFFY_OK;
   std::vector<DecJob> jobs{DecJob{s, n_scans, in, in_len, frame_offsets, planes_out, &st}};
   return run_decode(s->ws, jobs, reinterpret_cast<cudaStream_t>(cuda_stream));

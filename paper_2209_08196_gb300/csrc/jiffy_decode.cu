@@ -114,10 +114,13 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   const unsigned long long key = ((unsigned long long)(si + 1u) << 32) | ta;
   if (sc.key != key) {
     const unsigned long long f0 = sg.off[t], f1 = sg.off[t + 1];
-    bool hbad = false;
+    // offsets in range before any read: 4-byte aligned, a whole frame header,
+    // inside `in`, after the stream header for a stream's first frame
+    const unsigned long long first = (t == 0 && sg.check_shdr) ? 16ull + 8ull * A : 0ull;
+    bool hbad = f0 < first || (f0 & 3ull) || f1 < f0 + sg.fhdr || f1 > sg.in_len || ((f1 - f0) >> 32);
     unsigned long long sb_before = 0, sb_total = 0;
     uint32_t my_mode = 0, my_sb = 0;
-    for (uint32_t aa = lane; aa < A; aa += 32) {
+    for (uint32_t aa = lane; aa < A && !hbad; aa += 32) {
       const uint32_t m = ld_in_u32(sg.in, f0 + 8ull + 12ull * aa);
       const uint32_t sb = ld_in_u32(sg.in, f0 + 12ull + 12ull * aa);
       if ((m & 0xffffff00u) || (m & 0xffu) > 1u || sb < 8u * H || (sb & 3u)) hbad = true;
@@ -132,9 +135,11 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
     }
     sc.mode = __shfl_sync(0xffffffffu, my_mode, a & 31u);
     my_sb = __shfl_sync(0xffffffffu, my_sb, a & 31u);
-    const uint32_t frame_bytes = ld_in_u32(sg.in, f0);
-    const uint32_t scan = ld_in_u32(sg.in, f0 + 4);
-    if (frame_bytes != f1 - f0 || scan != sg.frame0 + t || sb_total + sg.fhdr != frame_bytes) hbad = true;
+    if (!hbad) {
+      const uint32_t frame_bytes = ld_in_u32(sg.in, f0);
+      const uint32_t scan = ld_in_u32(sg.in, f0 + 4);
+      if (frame_bytes != f1 - f0 || scan != sg.frame0 + t || sb_total + sg.fhdr != frame_bytes) hbad = true;
+    }
     if (sc.mode == 1u && sg.frame0 + t == 0) hbad = true;
     sc.bad = hbad ? 1u : 0u;
     sc.sec = f0 + sg.fhdr + sb_before;

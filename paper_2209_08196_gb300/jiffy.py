@@ -93,6 +93,12 @@ def _lib() -> ctypes.CDLL:
         L.jiffy_decode_seq.restype = ctypes.c_int
         L.jiffy_decode_seq.argtypes = [vp, u32, vp, sz, u64p, ctypes.POINTER(vp), vp]
         L.jiffy_decode_frame_noalloc.restype = ctypes.c_int
+        L.jiffy_encode_seq_async.argtypes = [vp, u32, ctypes.POINTER(vp), vp, sz, vp, vp]
+        L.jiffy_encode_seq_async.restype = ctypes.c_int
+        L.jiffy_decode_seq_async.argtypes = [vp, u32, vp, sz, vp, ctypes.POINTER(vp), vp]
+        L.jiffy_decode_seq_async.restype = ctypes.c_int
+        L.jiffy_stream_wait.argtypes = [vp]
+        L.jiffy_stream_wait.restype = ctypes.c_int
         L.jiffy_decode_frame_noalloc.argtypes = [vp, sz, u32, u32, u32, ctypes.POINTER(_AttrDesc), u32,
                                                  ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         L.jiffy_batch_create.restype = ctypes.c_int
@@ -296,6 +302,42 @@ def jiffy_encode_seq(h: Handle, planes, out: torch.Tensor, stream=None):
     if st != 0:
         raise JiffyError(st, "jiffy_encode_seq", required=n.value if st == 2 else None)
     return n.value, list(offs)
+
+
+def jiffy_encode_seq_async(h: Handle, planes, out: torch.Tensor, offsets_dev: torch.Tensor, stream=None):
+    """Enqueues the encode of T consecutive scans without waiting; the T + 1
+    frame offsets (the last = bytes written) go to offsets_dev, a device
+    int64 tensor of at least T + 1 entries. Device errors come back from
+    jiffy_stream_wait."""
+    T, arr = _seq_ptrs(h, planes, "plane")
+    if offsets_dev.numel() < T + 1 or offsets_dev.element_size() != 8 or not offsets_dev.is_cuda:
+        raise ValueError("offsets_dev: a device tensor of T + 1 64-bit entries")
+    st = _lib().jiffy_encode_seq_async(h.ptr, T, arr, out.data_ptr(), out.numel() * out.element_size(),
+                                       offsets_dev.data_ptr(), _stream_ptr(stream))
+    if st != 0:
+        raise JiffyError(st, "jiffy_encode_seq_async")
+
+
+def jiffy_decode_seq_async(h: Handle, buf: torch.Tensor, offsets_dev: torch.Tensor, planes_out, stream=None):
+    """Enqueues the decode of T frames of buf whose offsets are in the device
+    tensor offsets_dev (as jiffy_encode_seq_async writes them); the kernel
+    checks them against buf's size. Device errors come back from
+    jiffy_stream_wait."""
+    T, arr = _seq_ptrs(h, planes_out, "output plane")
+    if offsets_dev.numel() < T + 1 or offsets_dev.element_size() != 8 or not offsets_dev.is_cuda:
+        raise ValueError("offsets_dev: a device tensor of T + 1 64-bit entries")
+    st = _lib().jiffy_decode_seq_async(h.ptr, T, buf.data_ptr(), buf.numel() * buf.element_size(),
+                                       offsets_dev.data_ptr(), arr, _stream_ptr(stream))
+    if st != 0:
+        raise JiffyError(st, "jiffy_decode_seq_async")
+
+
+def jiffy_stream_wait(h: Handle):
+    """Waits for the stream's enqueue-only calls; raises the error the device
+    reported for any of them (the stream must then be reset)."""
+    st = _lib().jiffy_stream_wait(h.ptr)
+    if st != 0:
+        raise JiffyError(st, "jiffy_stream_wait")
 
 
 def jiffy_decode(h: Handle, buf: torch.Tensor, length: int, planes_out, stream=None):
