@@ -299,20 +299,21 @@ uint32_t jiffy_stream_kernel_times(const jiffy_stream* s, float* ms, uint32_t n)
  * device's memory. The paper has no counterpart; it exists for those callers.
  * Decodes the frame in `in` (in_len bytes, device, 4-byte aligned, preceded
  * by the stream header when scan_index == 0) into planes_out (host array of
- * n_attr device pointers, H x W). prev_planes (host array of n_attr device
+ * n_attr device pointers, H x W). stages: the stream's stage switches
+ * (jiffy_options.stages, 0 for the full codec; for scan 0 they must match the
+ * stream header, else CORRUPT). prev_planes (host array of n_attr device
  * pointers, nullable) must hold the previous frame's decoded planes when the
- * frame has P attributes (JIFFY_ERR_STATE if it is NULL then). No handle is
- * needed and nothing is allocated: scratch is a fixed device array in the
- * library, shared by every call (calls that overlap on the GPU race on it).
- * The first call on each device looks up that array's address; make it before
- * any stream capture. Limits: n_attr <= 16, n_attr * H <= 16384, W <= 16384;
- * beyond them JIFFY_ERR_INVALID_ARG. Frames of the full codec only (streams
- * without stage switches; a stream header with stage flags is CORRUPT).
+ * frame has P attributes (JIFFY_ERR_STATE if it is NULL then); it may be
+ * planes_out itself (in-place decode: every previous pixel is read before the
+ * same pixel is written). No handle is needed and nothing is allocated:
+ * scratch is a fixed device array in the library, shared by every call (calls
+ * that overlap on the GPU race on it). The first call on each device looks up
+ * that array's address; make it before any stream capture. Limits: n_attr <=
+ * 16, n_attr * H <= 16384, W <= 16384; beyond them JIFFY_ERR_INVALID_ARG.
  * Synchronizes cuda_stream. */
 jiffy_status jiffy_decode_frame_noalloc(const void* in, size_t in_len, uint32_t H, uint32_t W, uint32_t n_attr,
-                                        const jiffy_attr_desc* attrs, uint32_t scan_index,
-                                        const void* const* prev_planes, void* const* planes_out,
-                                        void* cuda_stream);
+                                        const jiffy_attr_desc* attrs, uint32_t scan_index, uint32_t stages,
+                                        const void* const* prev_planes, void* const* planes_out, void* cuda_stream);
 
 /* Copies src's previous scan and frame counter into dst (same H, W,
  * attributes and stage switches, same device, any roles), so that dst continues src's stream.

@@ -34,7 +34,7 @@ namespace jiffy {
 
 namespace {
 
-constexpr uint32_t kDecBatch = 4;  // row items per ticket unless the launch asks otherwise
+constexpr uint32_t kDecBatch = 1;  // row items per ticket unless the launch asks otherwise (1 balances the tail best)
 
 __device__ __forceinline__ uint32_t ld_in_u32(const uint8_t* in, unsigned long long at) {
   return __ldg(reinterpret_cast<const unsigned int*>(in + at));
@@ -65,7 +65,7 @@ __device__ __forceinline__ uint32_t find_seg(const uint32_t* base, uint32_t n, u
 constexpr uint32_t kRing = 512;
 
 struct DecWarpLayout {
-  uint32_t ring, patch, desc, mbytes, bytes;
+  uint32_t ring, patch, desc, mbytes, lits, bytes;
 };
 
 __host__ __device__ inline DecWarpLayout dec_warp_layout(uint32_t W) {
@@ -74,7 +74,8 @@ __host__ __device__ inline DecWarpLayout dec_warp_layout(uint32_t W) {
   L.patch = L.ring + 4u * kRing;
   L.desc = L.patch + 4u * kBlockN;
   L.mbytes = L.desc + ((8u * ceil_div_u32(W, kBlockN) + 15u) & ~15u);
-  L.bytes = (L.mbytes + ceil_div_u32(W, 8u) + 15u) & ~15u;
+  L.lits = (L.mbytes + ceil_div_u32(W, 8u) + 15u) & ~15u;
+  L.bytes = (L.lits + 4u * ceil_div_u32(W, 32u) + 15u) & ~15u;
   return L;
 }
 
@@ -86,6 +87,7 @@ struct SecCache {
   unsigned long long key;       // (1 + segment) << 32 | section in the segment; 0 = empty
   uint32_t mode, bad;           // the section's mode; 1 = malformed frame header
   uint32_t data_len;            // bytes of the section's row chunks
+  uint32_t next_p;              // the call's next frame codes this attribute as P (its rows read this frame's masks)
   unsigned long long sec;       // byte offset of the section (its row table)
 };
 
@@ -93,7 +95,8 @@ struct SecCache {
 // (else both are read as 0).
 template <bool STAGED>
 __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k, uint32_t* ring,
-                                            uint32_t* patch, uint2* desc, uint8_t* mbytes, SecCache& sc) {
+                                            uint32_t* patch, uint2* desc, uint8_t* mbytes, uint32_t* lits,
+                                            SecCache& sc) {
   const uint32_t si = find_seg(p.seg_item_base, p.n_seg, k);
   const DecSeg& sg = p.seg[si];
   const uint32_t lane = lane_id();
@@ -141,6 +144,13 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
       if (frame_bytes != f1 - f0 || scan != sg.frame0 + t || sb_total + sg.fhdr != frame_bytes) hbad = true;
     }
     if (sc.mode == 1u && sg.frame0 + t == 0) hbad = true;
+    sc.next_p = 1u;  // unless the next frame's header says I (or there is none)
+    if (t + 1 == sg.T) {
+      sc.next_p = 0u;
+    } else if (!hbad) {
+      const unsigned long long g1 = sg.off[t + 2];
+      if (g1 >= f1 + sg.fhdr && g1 <= sg.in_len && !(g1 & 3ull)) sc.next_p = ld_in_u32(sg.in, f1 + 8ull + 12ull * a) == 1u;
+    }
     sc.bad = hbad ? 1u : 0u;
     sc.sec = f0 + sg.fhdr + sb_before;
     sc.data_len = my_sb - 8u * H;
@@ -226,13 +236,17 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   const uint32_t litpre = litincl - lit;
   const uint32_t nlit = __shfl_sync(0xffffffffu, litincl, 31);
   bad = __any_sync(0xffffffffu, bad) || 4u * (ncls + nlit) > clen;
+  if (!bad) {  // the row's literal mask words, one coalesced read into shared memory
+    for (uint32_t i = lane; i < nlit; i += 32u) lits[i] = chunk[ncls + i];
+    __syncwarp();
+  }
   {  // a literal last mask word may not set bits past W
     const uint32_t j = nw - 1;
     const uint32_t cwj = __shfl_sync(0xffffffffu, cw, (j >> 4) & 31u);
     const uint32_t lpj = __shfl_sync(0xffffffffu, litpre, (j >> 4) & 31u);
     if (!bad && (W & 31u) && ((cwj >> (2u * (j & 15u))) & 3u) == 2u) {
       const uint32_t li = lpj + __popc(literal_bits(cwj) & ((1u << (2u * (j & 15u))) - 1u));
-      if (chunk[ncls + li] & ~valid_word_bits(W, nw, j)) bad = true;
+      if (lits[li] & ~valid_word_bits(W, nw, j)) bad = true;
     }
   }
 
@@ -258,7 +272,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
     const uint8_t* pmask = (xor_prev && t > 0)
                                ? reinterpret_cast<const uint8_t*>(p.masks + sg.mask_base + (size_t)(kl - H) * nw)
                                : nullptr;
-    uint8_t* omask = (t + 1 < sg.T && !(stages & kStageNoMask))
+    uint8_t* omask = (sc.next_p && !(stages & kStageNoMask))
                          ? reinterpret_cast<uint8_t*>(p.masks + sg.mask_base + (size_t)kl * nw)
                          : nullptr;
     for (uint32_t it = 0; it < niter; it++) {
@@ -270,7 +284,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
         const uint32_t sl = 2u * (j & 15u), cls = (cwj >> sl) & 3u;
         uint32_t X = 0;
         if (cls == 1u) X = valid_word_bits(W, nw, j);
-        else if (cls == 2u) X = chunk[ncls + lpj + __popc(literal_bits(cwj) & ((1u << sl) - 1u))];
+        else if (cls == 2u) X = lits[lpj + __popc(literal_bits(cwj) & ((1u << sl) - 1u))];
         const uint32_t nv = min(8u, W - x0), vm = (1u << nv) - 1u;
         uint32_t mb = (X >> (x0 & 31u)) & 0xffu;
         if (pmask) {
@@ -461,7 +475,8 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
   uint32_t* patch = reinterpret_cast<uint32_t*>(wb + lay.patch);
   uint2* desc = reinterpret_cast<uint2*>(wb + lay.desc);
   uint8_t* mbytes = wb + lay.mbytes;
-  SecCache sc{0ull, 0u, 0u, 0u, 0ull};
+  uint32_t* lits = reinterpret_cast<uint32_t*>(wb + lay.lits);
+  SecCache sc{0ull, 0u, 0u, 0u, 0u, 0ull};
   while (true) {
     uint32_t kb = 0;
     if (lane == 0) kb = atomicAdd(p.ticket, p.items_per_ticket);
@@ -469,7 +484,7 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
     if (kb >= p.n_items) break;
     const uint32_t kend = min(kb + p.items_per_ticket, p.n_items);
     for (uint32_t k = kb; k < kend; k++) {
-      decode_item<STAGED>(p, k, ring, patch, desc, mbytes, sc);
+      decode_item<STAGED>(p, k, ring, patch, desc, mbytes, lits, sc);
     }
   }
 }
@@ -489,7 +504,7 @@ static cudaError_t dec_occupancy(size_t smem, bool staged, int* per_sm) {
 
 int decode_rows_launch(const DecParams& p, RowsLaunch* out) {
   const DecWarpLayout L = dec_warp_layout(p.max_W);
-  if ((L.ring | L.patch | L.desc | L.mbytes | L.bytes) & 15u) return (int)cudaErrorInvalidValue;  // 16-byte aligned regions
+  if ((L.ring | L.patch | L.desc | L.mbytes | L.lits | L.bytes) & 15u) return (int)cudaErrorInvalidValue;  // 16-byte aligned regions
   uint32_t wpc = p.wpc;
   if ((wpc != 1 && wpc != 2 && wpc != 4 && wpc != 8) || wpc * L.bytes > kDecSmemMax) wpc = 0;
   if (!wpc) wpc = 4 * L.bytes <= kDecSmemAuto ? 4u : (2 * L.bytes <= kDecSmemAuto ? 2u : 1u);

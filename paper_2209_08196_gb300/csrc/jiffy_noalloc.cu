@@ -16,6 +16,11 @@
 // start at zero are cleared on each call; calls that overlap on the GPU (on
 // different streams, or from several host threads) race on it.
 //
+// In-place decode (prev_planes[a] == planes_out[a]) is allowed: a row's
+// previous-scan pixels are read by the warp that writes the same pixels of
+// that row, each before it is overwritten (the mask pass reads the whole
+// previous row first, then every 256-pixel step loads before it stores).
+//
 // Set-up: the first call on a device looks up the array's device address with
 // cudaGetSymbolAddress while that device is current (in host code the array's
 // name is only a host-side stand-in, not a device address) and caches it.
@@ -74,10 +79,12 @@ cudaError_t scratch_address(int device, unsigned char** out) {
 
 extern "C" jiffy_status jiffy_decode_frame_noalloc(const void* in, size_t in_len, uint32_t H, uint32_t W,
                                                    uint32_t n_attr, const jiffy_attr_desc* attrs,
-                                                   uint32_t scan_index, const void* const* prev_planes,
-                                                   void* const* planes_out, void* cuda_stream) {
+                                                   uint32_t scan_index, uint32_t stages,
+                                                   const void* const* prev_planes, void* const* planes_out,
+                                                   void* cuda_stream) {
   using namespace jiffy;
   if (!in || !attrs || !planes_out || H == 0 || W == 0 || n_attr == 0) return JIFFY_ERR_INVALID_ARG;
+  if (stages & ~kStageAll) return JIFFY_ERR_INVALID_ARG;
   if (H > kMaxH || W > kMaxW || n_attr > kNoAllocMaxAttr || (uint64_t)n_attr * H > kNoAllocMaxRows)
     return JIFFY_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(in) & 3u) return JIFFY_ERR_INVALID_ARG;
@@ -86,11 +93,7 @@ extern "C" jiffy_status jiffy_decode_frame_noalloc(const void* in, size_t in_len
     const uint32_t s = attrs[a].dtype_bytes, P = attrs[a].precision;
     if (!(s == 1 || s == 2 || s == 4) || P == 0 || !planes_out[a]) return JIFFY_ERR_INVALID_ARG;
     if (prev_planes && !prev_planes[a]) return JIFFY_ERR_INVALID_ARG;
-    const uint32_t maxv = s == 4 ? 0xffffffffu : ((1u << (8 * s)) - 1u);
-    ad[a].s = s;
-    ad[a].P = P;
-    ad[a].qmax = maxv / P;
-    ad[a].magic = (P >= 2 && P <= 0x80000000u) ? (~0ull) / P + 1ull : 0ull;
+    ad[a] = make_attr(s, P);
   }
   const uint32_t shdr = scan_index == 0 ? 16u + 8u * n_attr : 0u;
   const uint32_t fhdr = 8u + 12u * n_attr;
@@ -133,7 +136,8 @@ extern "C" jiffy_status jiffy_decode_frame_noalloc(const void* in, size_t in_len
   DecSeg g{};
   g.H = H; g.W = W; g.A = n_attr; g.T = 1;
   g.nw = (W + 31) / 32;
-  g.ncls = (g.nw + 15) / 16;
+  g.ncls = (stages & kStageNoMask) ? 0u : (g.nw + 15) / 16;
+  g.stages = stages;
   g.frame0 = scan_index;
   g.fhdr = fhdr;
   g.check_shdr = scan_index == 0;
@@ -159,6 +163,7 @@ extern "C" jiffy_status jiffy_decode_frame_noalloc(const void* in, size_t in_len
   p.seg_item_base = reinterpret_cast<const uint32_t*>(scratch + kOffSegKey);
   p.done = reinterpret_cast<uint32_t*>(scratch + kOffDone);
   p.ticket = reinterpret_cast<uint32_t*>(scratch + kOffTicket);
+  p.staged = stages ? 1u : 0u;  // the decoder instance that reads the stage switches
   if (launch_decode(p, cuda_stream, nullptr) != 0) return JIFFY_ERR_CUDA;
 
   uint32_t res[2] = {0, 0};

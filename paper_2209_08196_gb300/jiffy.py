@@ -99,7 +99,7 @@ def _lib() -> ctypes.CDLL:
         L.jiffy_decode_seq_async.restype = ctypes.c_int
         L.jiffy_stream_wait.argtypes = [vp]
         L.jiffy_stream_wait.restype = ctypes.c_int
-        L.jiffy_decode_frame_noalloc.argtypes = [vp, sz, u32, u32, u32, ctypes.POINTER(_AttrDesc), u32,
+        L.jiffy_decode_frame_noalloc.argtypes = [vp, sz, u32, u32, u32, ctypes.POINTER(_AttrDesc), u32, u32,
                                                  ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         L.jiffy_batch_create.restype = ctypes.c_int
         L.jiffy_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
@@ -361,11 +361,12 @@ def jiffy_decode_seq(h: Handle, buf: torch.Tensor, length: int, offsets, planes_
 
 
 def jiffy_decode_frame_noalloc(buf: torch.Tensor, length: int, H: int, W: int, attrs, scan_index: int,
-                               prev_planes, planes_out, stream=None):
+                               prev_planes, planes_out, stream=None, stages: int = 0):
     """Decodes one frame without a stream handle and without allocating
     device memory (for callers that may not allocate once running). Pass the
     previous frame's decoded planes as prev_planes (or None when the frame has
-    no P attribute)."""
+    no P attribute; planes_out itself decodes in place) and the stream's stage
+    switches."""
     for a, (p, (s, _)) in enumerate(zip(planes_out, attrs)):
         _check_plane(p, H, W, s, "output plane %d" % a)
     prev = None
@@ -374,7 +375,7 @@ def jiffy_decode_frame_noalloc(buf: torch.Tensor, length: int, H: int, W: int, a
             _check_plane(p, H, W, s, "previous plane %d" % a)
         prev = _ptr_array(prev_planes)
     st = _lib().jiffy_decode_frame_noalloc(buf.data_ptr(), length, H, W, len(attrs), _attrs(attrs), scan_index,
-                                           prev, _ptr_array(planes_out), _stream_ptr(stream))
+                                           stages, prev, _ptr_array(planes_out), _stream_ptr(stream))
     if st != 0:
         raise JiffyError(st, "jiffy_decode_frame_noalloc")
 
