@@ -16,6 +16,13 @@ the timed region); roofline = the dominant kernel's algorithmic bytes
 measured HBM copy bandwidth; cpu_baseline = the oracle on host cores on a
 bounded sample of the same scans.
 
+Further legs, each in its own key (compact copies of their headline figures
+sit inside `roofline` and `e2e`): the small single-stream case (16 scans of
+64 x 1024, CUDA-graph replay), the stream-size sweep of the low-coherence
+workload (64 MiB to 4 GiB of raw planes), the many-stream batch, the serving
+loop, the trial heuristic against brute force, the precision sweep, the
+ablated codecs and point-cloud standardization.
+
 --impl reference times the oracle alone (the reference arm).
 Multi-GPU (torchrun): independent replicas, one stream per GPU, no collective
 on the data path; value = all ranks' pixels / max time.
@@ -462,6 +469,183 @@ def max_over_ranks(ms: float, world: int, device) -> float:
     return float(t.item())
 
 
+def sweep_leg(J, torch, dev, local, max_mib=4096, reps=3, seed=7):
+    """Encode and decode throughput against total stream size on the
+    high-sparsity, low-coherence workload: 128 x 2048 range (u32 mm, 1 mm
+    precision) + reflectivity (u8), 40 % zeros in random discs, random yaw
+    (+-30 deg/s) and 3 m/s translation in a random direction, so I frames are
+    chosen often. One random walk is continued until its raw planes reach each
+    size (64 MiB, doubling up to max_mib); each size is one encode call over
+    its scans and one decode call over their stream, both enqueue-only on one
+    CUDA stream, timed with CUDA events after a warm-up pair, with a 256 MiB
+    write between calls so that no input starts in L2. Precision 1 makes the
+    round trip the identity: the decoded planes must equal the input."""
+    from paper_2209_08196_gb300 import synth
+    H, W = 128, 2048
+    raw_scan = H * W * (4 + 1)
+    sizes, mib = [], 64
+    while mib <= max_mib:
+        sizes.append(mib)
+        mib *= 2
+    if not sizes:
+        return None
+    n_of = {m: -(-m * 2**20 // raw_scan) for m in sizes}
+    n_max = n_of[sizes[-1]]
+    cfg = synth.config_low_coherence(seed=seed, n_scans=n_max)
+    attrs = synth.attr_descs(cfg)
+    t_gen = time.perf_counter()
+    seq = synth.ScanSequence(cfg, device=dev)
+    planes = [torch.empty((n_max, H, W), dtype=torch.int32, device=dev),
+              torch.empty((n_max, H, W), dtype=torch.uint8, device=dev)]
+    for t in range(n_max):
+        for a, p in enumerate(seq.scan(t, as_numpy=False)):
+            planes[a][t].copy_(p)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    enc = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, attrs, device=local)
+    dec = J.jiffy_stream_create(J.JIFFY_DECODER, H, W, attrs, device=local)
+    J.jiffy_stream_set_profiling(enc, True)
+    J.jiffy_stream_set_profiling(dec, True)
+    out = torch.empty(J.jiffy_max_encoded_size(H, W, attrs, n_max), dtype=torch.uint8, device=dev)
+    outs = J.empty_planes(dec, n_max)
+    d_offs = torch.zeros(n_max + 1, dtype=torch.int64, device=dev)
+    flush = torch.empty(64 * 2**20, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    peak, _ = peaks()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    rows = []
+    for m in sizes:
+        n = n_of[m]
+        src = [p[:n] for p in planes]
+        dst = [o[:n] for o in outs]
+        raw = n * raw_scan
+        t_enc, t_dec, k_enc, k_dec = [], [], [], []
+        for rep in range(reps + 1):
+            J.jiffy_stream_reset(enc)
+            J.jiffy_stream_reset(dec)
+            flush.fill_(rep)
+            ev[0].record(stream)
+            J.jiffy_encode_seq_async(enc, src, out, d_offs, stream)
+            ev[1].record(stream)
+            flush.fill_(rep + 1)
+            ev[2].record(stream)
+            J.jiffy_decode_seq_async(dec, out, d_offs, dst, stream)
+            ev[3].record(stream)
+            J.jiffy_stream_wait(enc)
+            J.jiffy_stream_wait(dec)
+            if rep:
+                t_enc.append(ev[0].elapsed_time(ev[1]))
+                t_dec.append(ev[2].elapsed_time(ev[3]))
+                k_enc.append(J.jiffy_stream_kernel_times(enc)[1])
+                k_dec.append(J.jiffy_stream_kernel_times(dec)[0])
+        nb = int(d_offs[n])
+        exact = all(torch.equal(d, s_) for d, s_ in zip(dst, src))
+        # share of I sections, from the frame headers (mode byte of each attribute)
+        idx = d_offs[:n, None] + 8 + 12 * torch.arange(2, device=dev)[None, :]
+        i_share = float((out[idx.reshape(-1)] == 0).float().mean())
+        te, td = statistics.mean(t_enc), statistics.mean(t_dec)
+        ke, kd = statistics.mean(k_enc), statistics.mean(k_dec)
+        moved = raw + nb  # algorithmic bytes of either direction: raw planes + stream
+        rows.append({"MiB": m, "scans": n, "stream_bytes": nb, "ratio": raw / nb, "i_share": i_share,
+                     "encode_gpoints_s": n * H * W / te / 1e6, "decode_gpoints_s": n * H * W / td / 1e6,
+                     "encode_ms": te, "decode_ms": td, "k_encode_ms": ke, "k_decode_ms": kd,
+                     "k_encode_frac": moved / ke / 1e6 / peak, "k_decode_frac": moved / kd / 1e6 / peak,
+                     "exact": bool(exact)})
+    J.jiffy_stream_destroy(enc)
+    J.jiffy_stream_destroy(dec)
+    del planes, out, outs, flush
+    torch.cuda.empty_cache()
+    return {"workload": "low-coherence 128x2048 range u32 (P=1) + reflectivity u8, 40%% zeros in discs, "
+                        "random yaw +-30 deg/s and 3 m/s; seed %d" % seed,
+            "l2": "256 MiB write before each timed call", "reps": reps, "generate_s": t_gen,
+            "peak_GBps": peak, "sizes": rows}
+
+
+def small_stream_leg(J, torch, dev, local, steps=200, warmup=5):
+    """The small single-stream case: 16 consecutive scans of 64 x 1024, range
+    only (u32 mm at 10 mm precision, 8 % dropouts), about 1 M points. Its
+    kernels are short, so the launch sequence of each call is replayed from a
+    CUDA graph captured by the stream on its first call of this shape. A step
+    is the encode of the 16 scans and the decode of their stream, enqueue-only
+    on one CUDA stream. Timed two ways with CUDA events: steps one at a time
+    after a 256 MiB write that evicts L2 (cold), and steps back to back with
+    the 4 MB of inputs left in L2 (hot). With profiling on (no graph for the
+    timed enqueue-only calls) the per-kernel times show how much of a step
+    the kernels fill."""
+    from paper_2209_08196_gb300 import synth
+    cfg = synth.config_small_range(seed=0)
+    attrs = synth.attr_descs(cfg)
+    T, H, W = cfg.n_scans, cfg.H, cfg.W
+    seq = synth.ScanSequence(cfg, device=dev)
+    planes = [torch.stack([seq.scan(t, as_numpy=False)[0] for t in range(T)])]
+    enc = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, attrs, device=local)
+    dec = J.jiffy_stream_create(J.JIFFY_DECODER, H, W, attrs, device=local)
+    out = torch.empty(J.jiffy_max_encoded_size(H, W, attrs, T), dtype=torch.uint8, device=dev)
+    outs = J.empty_planes(dec, T)
+    d_offs = torch.zeros(T + 1, dtype=torch.int64, device=dev)
+    flush = torch.empty(64 * 2**20, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        J.jiffy_stream_reset(enc)
+        J.jiffy_stream_reset(dec)
+        J.jiffy_encode_seq_async(enc, planes, out, d_offs, stream)
+        J.jiffy_decode_seq_async(dec, out, d_offs, outs, stream)
+
+    for _ in range(warmup):
+        step()
+    J.jiffy_stream_wait(enc)
+    J.jiffy_stream_wait(dec)
+    m = 0xFFFFFFFF
+    q = torch.clamp(((planes[0].to(torch.int64) & m) + 5) // 10, max=m // 10) * 10
+    exact = torch.equal(outs[0].to(torch.int64) & m, q)
+    nb = int(d_offs[T])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cold = []
+    for i in range(steps // 4):
+        flush.fill_(i)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        J.jiffy_stream_wait(enc)
+        J.jiffy_stream_wait(dec)
+        cold.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    J.jiffy_stream_wait(enc)
+    J.jiffy_stream_wait(dec)
+    hot = e0.elapsed_time(e1) / steps
+    # per-kernel device time of the same step
+    J.jiffy_stream_set_profiling(enc, True)
+    J.jiffy_stream_set_profiling(dec, True)
+    for _ in range(warmup):
+        step()
+    J.jiffy_stream_wait(enc)
+    J.jiffy_stream_wait(dec)
+    for _ in range(steps // 4):
+        step()
+    J.jiffy_stream_wait(enc)
+    J.jiffy_stream_wait(dec)
+    ke, kd = J.jiffy_stream_kernel_times(enc), J.jiffy_stream_kernel_times(dec)
+    px = T * H * W
+    cold_ms = statistics.median(cold)
+    J.jiffy_stream_destroy(enc)
+    J.jiffy_stream_destroy(dec)
+    return {"workload": "16 scans x 64 x 1024, range u32 (10 mm), 8% dropouts", "points_per_step": px,
+            "stream_bytes": nb, "ratio": px * 4 / nb, "exact": bool(exact),
+            "cold_gpoints_s": px / cold_ms / 1e6, "cold_us_per_step": 1e3 * cold_ms,
+            "hot_gpoints_s": px / hot / 1e6, "hot_us_per_step": 1e3 * hot,
+            "kernels_us_per_step": 1e3 * (sum(ke) + sum(kd)),
+            "kernel_us": {"k_trial": 1e3 * ke[0], "k_encode": 1e3 * ke[1], "k_finalize": 1e3 * ke[2],
+                          "k_decode": 1e3 * kd[0]},
+            "graphs": "each call's launch sequence replayed from a CUDA graph (not with profiling on)",
+            "l2": "cold: 256 MiB write before each step; hot: back-to-back steps, inputs in L2",
+            "launches_per_step": 5}
+
+
 def whole_job_gpoints(px_per_rank: int, world: int, ms: float) -> float:
     """All ranks' pixels over the slowest rank's time, in Gpoints/s."""
     return px_per_rank * world / (ms / 1e3) / 1e9
@@ -481,6 +665,9 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg")
     ap.add_argument("--no-ablation", action="store_true", help="skip the ablated-codec leg")
     ap.add_argument("--no-standardize", action="store_true", help="skip the point-cloud standardization leg")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the stream-size sweep leg")
+    ap.add_argument("--no-small", action="store_true", help="skip the 16 x 64 x 1024 single-stream leg")
+    ap.add_argument("--sweep-max-mib", type=int, default=4096, help="largest raw size of the sweep")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-sat-seconds", type=float, default=5.0)
     args = ap.parse_args()
@@ -732,47 +919,58 @@ def main():
             "paper": "96 % agreement on 22,877 range scans (0.5 % sub-optimal I, 3.5 % sub-optimal P)"}
         del out_bf
 
-    # precision sweep on the range plane (Fig. 4, Sec. IV-G): bits per sample as
-    # the quantization precision doubles (the paper: about one bit saved per
-    # doubling once the precision exceeds the sensor noise)
-    precision = None
-    if not args.no_heuristic:
-        n_t = min(T, 20)
-        rng_planes = [planes_in[0][:n_t]]
-        rows = []
-        for P in (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024):
-            pe = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, [(4, P)], device=local)
-            pbuf = torch.empty(J.jiffy_max_encoded_size(H, W, [(4, P)], n_t), dtype=torch.uint8, device=dev)
-            nb_p, _ = J.jiffy_encode_seq(pe, rng_planes, pbuf, stream)
-            rows.append({"precision_mm": P, "bits_per_sample": 8.0 * nb_p / (n_t * H * W)})
-            del pe, pbuf
-        precision = {"scans": n_t, "attribute": "range (uint32 mm)", "sweep": rows,
-                     "bits_saved_per_doubling_above_16mm": (rows[4]["bits_per_sample"] - rows[-1]["bits_per_sample"]) / 6.0}
-
-    # ablated codecs (Sec. IV-H, Table IV) on the first scans of the workload
-    # and on the same scene seen from a parked sensor (the paper's ablation
-    # data is a fixed infrastructure-monitoring sensor: here 90 % of the
-    # dropouts hit the same pixels every scan and the range has 10 mm of
-    # Gaussian noise): compression ratio and encode time of each stage set
-    ablation = None
-    if not args.no_ablation:
+    # the same scene seen from a parked sensor (the paper's ablation data is a
+    # fixed infrastructure-monitoring sensor): 90 % of the dropouts hit the
+    # same pixels every scan and the range has 10 mm of Gaussian noise
+    parked = None
+    if not (args.no_heuristic and args.no_ablation):
         from paper_2209_08196_gb300 import synth
         n_t = min(T, 20)
-        ladder = [("SIMD-PFOR", 7, 0), ("Delta -> SIMD-PFOR", 5, 0), ("Delta -> ZigZag -> SIMD-PFOR", 1, 0),
-                  ("Mask -> Delta -> ZigZag -> SIMD-PFOR", 0, 0),
-                  ("Mask -> Predict -> Delta -> ZigZag -> SIMD-PFOR (Jiffy)", 0, -1)]
         scfg = synth.config_multi_attr(seed=0, n_scans=n_t)
         scfg.speed_mps = 0.0
         scfg.persistent_dropout = 0.9
         scfg.range_noise_mm = 10.0
         sseq = synth.ScanSequence(scfg, device=dev)
         sscans = [sseq.scan(t, as_numpy=False) for t in range(n_t)]
-        scenes = {"moving (10 m/s)": [p[:n_t] for p in planes_in],
-                  "parked": [torch.stack([sscans[t][a] for t in range(n_t)]) for a in range(A)]}
+        parked = [torch.stack([sscans[t][a] for t in range(n_t)]) for a in range(A)]
         del sscans
+
+    # precision sweep on the range plane (Fig. 4, Sec. IV-G): bits per sample as
+    # the quantization precision doubles, on the noise-free moving scene and on
+    # the parked scene with 10 mm range noise (the paper: about one bit saved
+    # per doubling once the precision exceeds the sensor noise)
+    precision = None
+    if not args.no_heuristic:
+        n_t = min(T, 20)
+        precs = (1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024)
+        precision = {"scans": n_t, "attribute": "range (uint32 mm)", "precisions_mm": list(precs)}
+        for scene, rng_planes in (("moving", [planes_in[0][:n_t]]), ("parked_10mm_noise", [parked[0]])):
+            bits = []
+            for P in precs:
+                pe = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, [(4, P)], device=local)
+                pbuf = torch.empty(J.jiffy_max_encoded_size(H, W, [(4, P)], n_t), dtype=torch.uint8, device=dev)
+                nb_p, _ = J.jiffy_encode_seq(pe, rng_planes, pbuf, stream)
+                bits.append(8.0 * nb_p / (n_t * H * W))
+                del pe, pbuf
+            # bits saved per doubling, from 16 mm and from 32 mm up to 1024 mm
+            precision[scene] = {"bits_per_sample": bits,
+                                "bits_saved_per_doubling_16_to_1024mm": (bits[4] - bits[-1]) / 6.0,
+                                "bits_saved_per_doubling_32_to_1024mm": (bits[5] - bits[-1]) / 5.0,
+                                "bits_saved_per_doubling_1_to_16mm": (bits[0] - bits[4]) / 4.0}
+
+    # ablated codecs (Sec. IV-H, Table IV) on the first scans of the workload
+    # and on the parked scene: compression ratio and encode time of each
+    # stage set
+    ablation = None
+    if not args.no_ablation:
+        n_t = min(T, 20)
+        ladder = [("SIMD-PFOR", 7, 0), ("Delta -> SIMD-PFOR", 5, 0), ("Delta -> ZigZag -> SIMD-PFOR", 1, 0),
+                  ("Mask -> Delta -> ZigZag -> SIMD-PFOR", 0, 0),
+                  ("Mask -> Predict -> Delta -> ZigZag -> SIMD-PFOR (Jiffy)", 0, -1)]
+        scenes = {"moving (10 m/s)": [p[:n_t] for p in planes_in], "parked": parked}
         abuf = torch.empty(J.jiffy_max_encoded_size(H, W, attrs, n_t), dtype=torch.uint8, device=dev)
         raw_t = sum(p.numel() * p.element_size() for p in scenes["parked"])
-        ablation = {"scans": n_t, "attributes": [a for a in scfg.attrs], "codecs": []}
+        ablation = {"scans": n_t, "attributes": list(cfg.attrs), "codecs": []}
         for name, stages, force in ladder:
             row = {"codec": name, "stages": stages, "force_mode": force}
             for scene, pl in scenes.items():
@@ -842,6 +1040,14 @@ def main():
                        "launches_per_call": 2, "scans_per_call": n_s, "all_scans_within_1_unit": bool(ok)}
         del s_xyz, s_vals, s_range, s_attr, std
 
+    small = None
+    if not args.no_small:
+        small = small_stream_leg(J, torch, dev, local)
+
+    sweep = None
+    if not args.no_sweep:
+        sweep = sweep_leg(J, torch, dev, local, args.sweep_max_mib)
+
     batched = served = None
     if not args.no_batched:
         batched = batched_leg(J, torch, dev, local, args.steps, args.warmup)
@@ -858,6 +1064,24 @@ def main():
             except Exception as ex:  # a reported extra; the run goes on without it
                 cpu_n = {"value": None, "error": "%s: %s" % (type(ex).__name__, ex)}
         modes = {"ratio": raw_bytes / n}
+        # compact copies of the other legs' headline figures inside the keys the
+        # contract defines (the full legs follow as their own keys)
+        if sweep is not None:
+            roofline["sweep"] = {
+                "columns": ["MiB", "encode_gpoints_s", "decode_gpoints_s", "k_encode_frac", "k_decode_frac", "exact"],
+                "rows": [[r["MiB"], round(r["encode_gpoints_s"], 2), round(r["decode_gpoints_s"], 2),
+                          round(r["k_encode_frac"], 3), round(r["k_decode_frac"], 3), r["exact"]]
+                         for r in sweep["sizes"]]}
+        if batched is not None:
+            roofline["batched"] = {"gpoints_s": batched["gpoints_s"], "seq_gpoints_s": batched.get("seq_gpoints_s"),
+                                   "encode_rows_frac": batched.get("encode_rows_frac"),
+                                   "decode_rows_frac": batched.get("decode_rows_frac")}
+        if small is not None:
+            roofline["small_stream"] = {"cold_gpoints_s": small["cold_gpoints_s"], "hot_gpoints_s": small["hot_gpoints_s"],
+                                        "kernels_us_per_step": small["kernels_us_per_step"]}
+        if e2e is not None and served is not None:
+            e2e["served"] = {"p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"], "gpoints_s": served["gpoints_s"],
+                             "saturated_gpoints_s": served["saturated"]["gpoints_s"]}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -868,7 +1092,11 @@ def main():
                 "clocks": clocks,
                 "gpu_launches": 5 * args.steps * (2 if e2e else 1),
                 "batched": batched, "served": served, "heuristic": heuristic, "precision": precision,
-                "ablation": ablation, "standardize": standardize,
+                "ablation": ablation, "standardize": standardize, "small_stream": small,
+                "sweep": None if sweep is None else roofline["sweep"]["rows"], "sweep_detail": sweep,
+                "batched_gpoints_s": None if batched is None else batched["gpoints_s"],
+                "served_p50_ms": None if served is None else served["p50_ms"],
+                "served_p99_ms": None if served is None else served["p99_ms"],
                 "detail": {"kernels": kernels, "compression": modes, "stream_bytes": n,
                            "gsamples_s": value * A,
                            "encode_gpoints_s": px_step / (avg["k_trial"] + avg["k_encode"] + avg["k_finalize"]) / 1e6,

@@ -152,6 +152,11 @@ class ScanSequence:
 
     # -- geometry -----------------------------------------------------------
     def _cast(self, t: int):
+        """First and second hit distance along every ray and the reflectivity
+        of the first hit. Boxes are intersected a group at a time (slab test
+        on a box x H x W grid); the nearest and second nearest of ground,
+        boxes and wall are kept as running minima, ties going to the earlier
+        surface (ground, then boxes in order, then wall)."""
         cfg = self.cfg
         dev = self.device
         ox, oy = float(self.pos[t, 0]), float(self.pos[t, 1])
@@ -161,43 +166,54 @@ class ScanSequence:
         dy = ce * torch.sin(az)[None, :]
         dz = torch.sin(self._el)[:, None].expand_as(dx)
         big = torch.tensor(float("inf"), device=dev)
-        best = torch.full(dx.shape, float("inf"), device=dev)
-        second = torch.full(dx.shape, float("inf"), device=dev)
-        refl = torch.zeros(dx.shape, device=dev)
         # ground plane z = -1.8
         tg = torch.where(dz < -1e-6, -1.8 / torch.where(dz < -1e-6, dz, -torch.ones_like(dz)), big)
-        best = torch.minimum(best, tg)
-        refl = torch.where(tg <= best, torch.full_like(refl, self.ground_refl), refl)
         # boxes, recycled modulo a 160 m window around the sensor
         inv = [1.0 / torch.where(d.abs() < 1e-9, torch.full_like(d, 1e-9), d) for d in (dx, dy, dz)]
-        for k in range(self.box_c.shape[0]):
-            cx = ox + ((self.box_c[k, 0] - ox + 80.0) % 160.0) - 80.0
-            cy = oy + ((self.box_c[k, 1] - oy + 80.0) % 160.0) - 80.0
-            sx, sy, sz = self.box_size[k]
-            lo = (cx - sx / 2 - ox, cy - sy / 2 - oy, -1.8)
-            hi = (cx + sx / 2 - ox, cy + sy / 2 - oy, -1.8 + sz)
-            tmin = None
-            tmax = None
+        # box bounds relative to the sensor, in float32 like the box tables
+        c, sz = self.box_c, self.box_size
+        cx = ox + ((c[:, 0] - ox + 80.0) % 160.0) - 80.0
+        cy = oy + ((c[:, 1] - oy + 80.0) % 160.0) - 80.0
+        lo = np.stack([cx - sz[:, 0] / 2 - ox, cy - sz[:, 1] / 2 - oy, np.full(len(cx), -1.8, np.float32)], 1)
+        hi = np.stack([cx + sz[:, 0] / 2 - ox, cy + sz[:, 1] / 2 - oy, -1.8 + sz[:, 2]], 1)
+        lo = torch.tensor(lo, dtype=torch.float32, device=dev)[:, :, None, None]
+        hi = torch.tensor(hi, dtype=torch.float32, device=dev)[:, :, None, None]
+        refl_tab = torch.tensor([self.ground_refl] + [float(r) for r in self.box_refl] + [self.wall_refl],
+                                dtype=torch.float32, device=dev)
+        best, second, first = tg, torch.full_like(tg, float("inf")), torch.zeros(tg.shape, dtype=torch.int64,
+                                                                                 device=dev)
+        nb = lo.shape[0]
+        step = nb if dev.type == "cuda" else 40  # boxes per slab test (CPU: cache-sized groups)
+
+        def merge(hits, base):
+            # fold a group of surfaces (in order) into the running nearest and
+            # second nearest; a tie keeps the earlier surface as the nearest
+            nonlocal best, second, first
+            gb, gi = hits.min(0)
+            if hits.shape[0] > 1:
+                idx = torch.arange(hits.shape[0], device=dev)[:, None, None]
+                gs = torch.where(idx == gi[None], big, hits).min(0).values
+            else:
+                gs = torch.full_like(gb, float("inf"))
+            closer = gb < best
+            second = torch.where(closer, torch.minimum(best, gs), torch.minimum(second, gb))
+            first = torch.where(closer, gi + base, first)
+            best = torch.where(closer, gb, best)
+
+        for k0 in range(0, nb, step):
+            tmin = tmax = None
             for ax in range(3):
-                t1 = lo[ax] * inv[ax]
-                t2 = hi[ax] * inv[ax]
+                t1 = lo[k0:k0 + step, ax] * inv[ax]
+                t2 = hi[k0:k0 + step, ax] * inv[ax]
                 a, b = torch.minimum(t1, t2), torch.maximum(t1, t2)
                 tmin = a if tmin is None else torch.maximum(tmin, a)
                 tmax = b if tmax is None else torch.minimum(tmax, b)
-            hit = (tmax >= tmin) & (tmin > 0)
-            th = torch.where(hit, tmin, big)
-            closer = th < best
-            second = torch.where(closer, best, torch.minimum(second, th))
-            refl = torch.where(closer, torch.full_like(refl, float(self.box_refl[k])), refl)
-            best = torch.minimum(best, th)
+            merge(torch.where((tmax >= tmin) & (tmin > 0), tmin, big), 1 + k0)
         if cfg.wall:  # enclosing wall of radius 110 m, 60 m tall
             ch = torch.sqrt(dx * dx + dy * dy).clamp_min(1e-6)
             tw = 110.0 / ch
-            tw = torch.where(dz * tw < 60.0, tw, big)
-            closer = tw < best
-            second = torch.where(closer, best, torch.minimum(second, tw))
-            refl = torch.where(closer, torch.full_like(refl, self.wall_refl), refl)
-            best = torch.minimum(best, tw)
+            merge(torch.where(dz * tw < 60.0, tw, big)[None], 1 + nb)
+        refl = refl_tab[first]
         return best, second, refl
 
     # -- attributes ----------------------------------------------------------
@@ -275,19 +291,27 @@ class ScanSequence:
         return out
 
     def _discs(self, g: torch.Generator, frac: float):
+        """Clustered dropouts: random discs (radius 5..40 px, centres uniform
+        over the image) are added until they cover at least `frac` of the
+        pixels. Each disc only touches its bounding window."""
         H, W = self.cfg.H, self.cfg.W
-        m = torch.zeros((H, W), dtype=torch.bool)
-        rows = torch.arange(H)[:, None].float()
-        cols = torch.arange(W)[None, :].float()
-        # add random discs (radius 5..40 px) until the target fraction is reached
+        m = np.zeros((H, W), dtype=bool)
+        covered, need = 0, frac * (H * W)
         for _ in range(100000):
-            if float(m.float().mean()) >= frac:
+            if covered >= need:
                 break
             cy = float(torch.randint(0, H, (1,), generator=g))
             cx = float(torch.randint(0, W, (1,), generator=g))
             rad = 5.0 + 35.0 * float(torch.rand(1, generator=g))
-            m |= (rows - cy) ** 2 + (cols - cx) ** 2 <= rad * rad
-        return m
+            r0, r1 = max(0, int(math.floor(cy - rad))), min(H, int(math.ceil(cy + rad)) + 1)
+            c0, c1 = max(0, int(math.floor(cx - rad))), min(W, int(math.ceil(cx + rad)) + 1)
+            rows = np.arange(r0, r1, dtype=np.float32)[:, None]
+            cols = np.arange(c0, c1, dtype=np.float32)[None, :]
+            disc = (rows - np.float32(cy)) ** 2 + (cols - np.float32(cx)) ** 2 <= np.float32(rad * rad)
+            win = m[r0:r1, c0:c1]
+            covered += int(np.count_nonzero(disc & ~win))
+            win |= disc
+        return torch.from_numpy(m)
 
     def scans(self, as_numpy: bool = True):
         return [self.scan(t, as_numpy) for t in range(self.cfg.n_scans)]
