@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes
 import os
 
+import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -58,6 +59,7 @@ STAGE_NO_ZIGZAG = 4
 
 
 _L = None
+_ENC_BATCH_ADDR = _DEC_BATCH_ADDR = None
 
 
 def _lib() -> ctypes.CDLL:
@@ -122,6 +124,10 @@ def _lib() -> ctypes.CDLL:
         L.jiffy_decode_batch_async.argtypes = L.jiffy_decode_batch.argtypes
         L.jiffy_batch_wait.restype = ctypes.c_int
         L.jiffy_batch_wait.argtypes = [vp]
+        # the same batched entry points over plain addresses (array-marshalled calls)
+        global _ENC_BATCH_ADDR, _DEC_BATCH_ADDR
+        _ENC_BATCH_ADDR = ctypes.CFUNCTYPE(ctypes.c_int, vp, u32, *([vp] * 9))(("jiffy_encode_batch_async", L))
+        _DEC_BATCH_ADDR = ctypes.CFUNCTYPE(ctypes.c_int, vp, u32, *([vp] * 8))(("jiffy_decode_batch_async", L))
         L.jiffy_batch_set_graphs.restype = ctypes.c_int
         L.jiffy_batch_set_graphs.argtypes = [vp, ctypes.c_int]
         L.jiffy_batch_set_autotune.restype = ctypes.c_int
@@ -422,10 +428,11 @@ class BatchError(JiffyError):
     """A batched call failed for some streams; .statuses has one code per
     stream (0 = that stream succeeded and advanced)."""
 
-    def __init__(self, status, what, statuses, required=None):
+    def __init__(self, status, what, statuses, required=None, result=None):
         super().__init__(status, what)
         self.statuses = list(statuses)
         self.required = required
+        self.result = result  # array-marshalled encode: (bytes, offsets, starts) of the streams that succeeded
 
 
 def jiffy_batch_set_graphs(b: Batch, enable: bool = True):
@@ -568,15 +575,99 @@ def jiffy_decode_batch_async(b: Batch, handles, bufs, lengths, offsets, planes_o
     b.pending = ("decode", c)
 
 
+class _ArrayCall:
+    """A batched call marshalled from numpy arrays of addresses (kept alive
+    until it ends). Frame offsets of stream i sit in offs[starts[i]:]."""
+
+    def __init__(self, n, keep, offs, starts, lens, sts):
+        self.n, self.keep, self.offs, self.starts, self.lens, self.sts = n, keep, offs, starts, lens, sts
+
+    def result(self):
+        return self.lens, self.offs, self.starts
+
+
+def _u64(a):
+    return np.ascontiguousarray(a, dtype=np.uint64)
+
+
+def jiffy_encode_batch_async_arrays(b: Batch, streams, n_scans, plane_tables, outs, caps, stream=None):
+    """jiffy_encode_batch_async with its per-stream arguments given as numpy
+    arrays, for callers that issue many batches over fixed buffers (a serving
+    engine): stream handle addresses (Handle.ptr), scan counts, addresses of
+    plane pointer tables (each holds n_scans[i] * A device pointers,
+    scan-major, kept alive by the caller), output buffer addresses and
+    capacities in bytes. Nothing is checked here beyond what the C ABI checks.
+    jiffy_batch_wait(b) then returns (bytes per stream, frame offsets,
+    start of each stream's offsets) as numpy arrays."""
+    _lib()
+    streams, tables, outs, caps = _u64(streams), _u64(plane_tables), _u64(outs), _u64(caps)
+    n_scans = np.ascontiguousarray(n_scans, dtype=np.uint32)
+    n = len(streams)
+    if not (len(n_scans) == len(tables) == len(outs) == len(caps) == n):
+        raise ValueError("per-stream arrays differ in length")
+    starts = np.zeros(n, dtype=np.int64)
+    np.cumsum(n_scans[:-1].astype(np.int64) + 1, out=starts[1:])
+    offs = np.zeros(int(n_scans.sum()) + n, dtype=np.uint64)
+    offs_pp = _u64(offs.ctypes.data + 8 * starts)
+    lens = np.zeros(n, dtype=np.uint64)
+    sts = np.zeros(n, dtype=np.int32)
+    keep = (streams, n_scans, tables, outs, caps, offs_pp)
+    st = _ENC_BATCH_ADDR(b.ptr, n, streams.ctypes.data, n_scans.ctypes.data, tables.ctypes.data, outs.ctypes.data,
+                         caps.ctypes.data, offs_pp.ctypes.data, lens.ctypes.data, sts.ctypes.data,
+                         _stream_ptr(stream))
+    if st != 0:
+        raise BatchError(st, "jiffy_encode_batch_async", sts.tolist())
+    b.pending = ("encode", _ArrayCall(n, keep, offs, starts, lens, sts))
+
+
+def jiffy_decode_batch_async_arrays(b: Batch, streams, n_frames, ins, in_lens, offsets, offset_starts, plane_tables,
+                                    stream=None):
+    """jiffy_decode_batch_async with numpy arrays: stream handle addresses,
+    frame counts, input buffer addresses and lengths, all streams' frame
+    offsets in one uint64 array (stream i's n_frames[i] + 1 offsets start at
+    offset_starts[i]) and addresses of output plane pointer tables
+    (n_frames[i] * A pointers each, kept alive by the caller)."""
+    _lib()
+    streams, ins, in_lens, tables = _u64(streams), _u64(ins), _u64(in_lens), _u64(plane_tables)
+    n_frames = np.ascontiguousarray(n_frames, dtype=np.uint32)
+    offsets = _u64(offsets)
+    n = len(streams)
+    if not (len(n_frames) == len(ins) == len(in_lens) == len(tables) == len(offset_starts) == n):
+        raise ValueError("per-stream arrays differ in length")
+    starts = np.asarray(offset_starts, dtype=np.int64)
+    if n and (starts.min() < 0 or (starts + n_frames.astype(np.int64) + 1).max() > len(offsets)):
+        raise ValueError("frame offsets out of range")
+    offs_pp = _u64(offsets.ctypes.data + 8 * starts)
+    sts = np.zeros(n, dtype=np.int32)
+    keep = (streams, n_frames, ins, in_lens, offsets, offs_pp, tables)
+    st = _DEC_BATCH_ADDR(b.ptr, n, streams.ctypes.data, n_frames.ctypes.data, ins.ctypes.data, in_lens.ctypes.data,
+                         offs_pp.ctypes.data, tables.ctypes.data, sts.ctypes.data, _stream_ptr(stream))
+    if st != 0:
+        raise BatchError(st, "jiffy_decode_batch_async", sts.tolist())
+    b.pending = ("decode", _ArrayCall(n, keep, offsets, starts, None, sts))
+
+
+def plane_table(planes):
+    """A ctypes table of device pointers (for the array-marshalled calls);
+    its address is ctypes.addressof(table). The caller keeps the planes and
+    the table alive."""
+    return (ctypes.c_void_p * len(planes))(*[p.data_ptr() for p in planes])
+
+
 def jiffy_batch_wait(b: Batch):
     """Waits for the batch's enqueued call; returns the encode result (list of
-    (bytes, frame offsets)) or None for a decode."""
+    (bytes, frame offsets), or for an array-marshalled call (bytes, offsets,
+    starts) as numpy arrays) or None for a decode."""
     kind, c = getattr(b, "pending", None) or (None, None)
     st = _lib().jiffy_batch_wait(b.ptr)
     b.pending = None
     if st != 0:
-        raise BatchError(st, "jiffy_batch_wait", list(c.sts) if c else [],
-                         required=list(c.lens) if kind == "encode" else None)
+        sts = c.sts.tolist() if isinstance(c, _ArrayCall) else (list(c.sts) if c else [])
+        req = res = None
+        if kind == "encode":
+            req = c.lens.tolist() if isinstance(c, _ArrayCall) else list(c.lens)
+            res = c.result() if isinstance(c, _ArrayCall) else None
+        raise BatchError(st, "jiffy_batch_wait", sts, required=req, result=res)
     return c.result() if kind == "encode" else None
 
 

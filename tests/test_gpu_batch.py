@@ -298,6 +298,45 @@ def test_decoder_takes_over_from_encoder_state():
         J.jiffy_stream_copy_state(other, enc)
 
 
+def test_array_marshalled_calls_match_oracle_over_calls():
+    # jiffy_*_batch_async_arrays: per-stream arguments as numpy arrays of
+    # addresses, plane tables built once; bytes, offsets and decoded planes
+    # equal the oracle's over calls of different scan counts
+    import ctypes
+    rng = np.random.default_rng(17)
+    fleet = Fleet(SENSORS)
+    for Ts in ([2, 1, 3, 1], [1, 2, 1, 3]):
+        scans = [make_scans(rng, H, W, a, T) for (H, W, a), T in zip(SENSORS, Ts)]
+        dev = [[to_dev(p) for sc in ss for p in sc] for ss in scans]  # scan-major planes per stream
+        tabs = [J.plane_table(d) for d in dev]
+        outs = [torch.zeros(J.jiffy_max_encoded_size(H, W, a, T), dtype=torch.uint8, device="cuda")
+                for (H, W, a), T in zip(SENSORS, Ts)]
+        J.jiffy_encode_batch_async_arrays(fleet.b, [h.ptr for h in fleet.enc], Ts,
+                                          [ctypes.addressof(t) for t in tabs], [o.data_ptr() for o in outs],
+                                          [o.numel() for o in outs])
+        lens, offs, starts = J.jiffy_batch_wait(fleet.b)
+        bufs = []
+        for i, ((H, W, a), sc) in enumerate(zip(SENSORS, scans)):
+            want = b"".join(fleet.ref[i].encode(s) for s in sc)
+            got = outs[i][:int(lens[i])].cpu().numpy().tobytes()
+            assert got == want, "stream %d" % i
+            o = offs[starts[i]:starts[i] + Ts[i] + 1].tolist()
+            assert o[-1] == len(want)
+            bufs.append(got)
+        planes_out = [[torch.empty((H, W), dtype=TORCH_DT[s], device="cuda") for _ in range(T) for s, _ in a]
+                      for (H, W, a), T in zip(SENSORS, Ts)]
+        dtabs = [J.plane_table(p) for p in planes_out]
+        J.jiffy_decode_batch_async_arrays(fleet.b, [h.ptr for h in fleet.dec], Ts, [o.data_ptr() for o in outs],
+                                          lens, offs, starts, [ctypes.addressof(t) for t in dtabs])
+        assert J.jiffy_batch_wait(fleet.b) is None
+        for i, ((H, W, a), sc) in enumerate(zip(SENSORS, scans)):
+            o = offs[starts[i]:starts[i] + Ts[i] + 1].tolist()
+            for t in range(Ts[i]):
+                want, _ = fleet.refd[i].decode(bufs[i][(o[t] if t else 0):o[t + 1]])
+                for k, (s, _) in enumerate(a):
+                    assert np.array_equal(to_np(planes_out[i][t * len(a) + k], s), want[k]), (i, t, k)
+
+
 def test_many_stream_workload_sampled_against_oracle():
     # the many-stream configuration (uneven shapes from 16x1024 to 128x4096,
     # attribute sets {range}, {range, signal}, all five; 8 scans each) in one

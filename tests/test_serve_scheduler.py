@@ -22,8 +22,8 @@ class FakeClock:
 class FakeBackend:
     """Each context finishes its call `latency` seconds after submission."""
 
-    def __init__(self, clock, n_contexts=2, latency=0.004, fail=()):
-        self.clock, self.n_contexts, self.latency = clock, n_contexts, latency
+    def __init__(self, clock, n_contexts=2, latency=0.004, fail=(), max_group=4):
+        self.clock, self.n_contexts, self.latency, self.max_group = clock, n_contexts, latency, max_group
         self.done_at = {}
         self.calls = []              # (kind, ctx, [(sid, seq)], t_submit)
         self.admitted, self.peak_used, self.used = set(), 0, 0
@@ -46,7 +46,7 @@ class FakeBackend:
         self.admitted.remove(s.sid)
         self.used -= self.footprint(s)
 
-    def _submit(self, kind, ctx, items):
+    def _submit(self, kind, ctx, items, pairs):
         assert ctx not in self.in_flight, "context reused while busy"
         for sid, _ in items:
             assert sid in self.admitted
@@ -55,20 +55,24 @@ class FakeBackend:
         assert len({sid for sid, _ in items}) == len(items), "sensor twice in one batch"
         self.in_flight[ctx] = items
         self.done_at[ctx] = self.clock.t + self.latency
-        self.calls.append((kind, ctx, [(sid, r.seq) for sid, r in items], self.clock.t))
+        self.calls.append((kind, ctx, pairs, self.clock.t))
 
     def submit_encode(self, ctx, items):
-        self._submit("encode", ctx, items)
+        for sid, reqs in items:
+            assert 1 <= len(reqs) <= self.max_group
+            assert [r.seq for r in reqs] == list(range(reqs[0].seq, reqs[0].seq + len(reqs)))
+            assert not any(r.decode for r in reqs[1:]), "a scan to decode must start its group"
+        self._submit("encode", ctx, items, [(sid, r.seq) for sid, reqs in items for r in reqs])
 
     def submit_decode(self, ctx, items):
-        self._submit("decode", ctx, items)
+        self._submit("decode", ctx, items, [(sid, r.seq) for sid, r in items])
 
     def ready(self, ctx):
         return self.clock.t >= self.done_at[ctx]
 
     def finish_encode(self, ctx):
         items = self.in_flight.pop(ctx)
-        return [(100, 3 if (sid, r.seq) in self.fail else 0) for sid, r in items]
+        return [([100] * len(reqs), 3 if any((sid, r.seq) in self.fail for r in reqs) else 0) for sid, reqs in items]
 
     def finish_decode(self, ctx):
         return [0 for _ in self.in_flight.pop(ctx)]
@@ -150,7 +154,37 @@ def test_failed_encode_is_counted_and_does_not_stall():
     bad = (reqs[0].sensor, reqs[0].seq)
     be = FakeBackend(clock, fail={bad})
     st = Server(be, sensors, budget_bytes=1 << 40, clock=clock, sleep=clock.sleep).run(reqs, realtime=True)
-    assert st.failed == 1 and st.encoded == len(reqs) - 1
+    # the failing scan's group fails with it; everything else is served
+    assert st.failed >= 1 and st.encoded + st.failed == len(reqs)
+    assert reqs[0].status == 3
+
+
+def test_backlog_is_coded_in_groups_when_the_device_is_slow():
+    # saturation: every scan is available at once; each batch takes up to
+    # max_group queued scans per sensor (one segment), in order, with decode
+    # scans only at the start of a group
+    clock = FakeClock()
+    sensors = _sensors(16, seed=9)
+    reqs = poisson_arrivals(sensors, 2.0, 0.1, seed=10)
+    be = FakeBackend(clock, latency=0.01, max_group=4)
+    st = Server(be, sensors, budget_bytes=1 << 40, clock=clock, sleep=clock.sleep).run(reqs, realtime=False)
+    assert st.encoded == len(reqs) and st.failed == 0
+    assert st.decoded == sum(r.decode for r in reqs)
+    s = st.summary()
+    assert s["mean_group"] > 2.0
+    seen = {}
+    for kind, _, items, _ in be.calls:
+        if kind == "encode":
+            for sid, seq in items:
+                assert seq == seen.get(sid, -1) + 1
+                seen[sid] = seq
+    # max_group = 1 keeps one scan per sensor per batch
+    clock = FakeClock()
+    be1 = FakeBackend(clock, latency=0.01, max_group=1)
+    st1 = Server(be1, sensors, budget_bytes=1 << 40, clock=clock, sleep=clock.sleep).run(
+        poisson_arrivals(sensors, 2.0, 0.1, seed=10), realtime=False)
+    assert st1.encoded == len(reqs) and st1.summary()["mean_group"] == 1.0
+    assert st1.batches > st.batches
 
 
 def test_arrivals_are_poisson_at_the_sensor_rates():
