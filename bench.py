@@ -707,6 +707,93 @@ def small_stream_leg(J, torch, dev, local, steps=200, warmup=5):
             "launches_per_step": 5}
 
 
+def _zstd():
+    """libzstd through ctypes (compress, decompress, error check), or None."""
+    import ctypes
+    import ctypes.util
+    path = ctypes.util.find_library("zstd")
+    if path is None:
+        return None
+    z = ctypes.CDLL(path)
+    sz, vp = ctypes.c_size_t, ctypes.c_void_p
+    z.ZSTD_compressBound.restype, z.ZSTD_compressBound.argtypes = sz, [sz]
+    z.ZSTD_compress.restype, z.ZSTD_compress.argtypes = sz, [vp, sz, vp, sz, ctypes.c_int]
+    z.ZSTD_decompress.restype, z.ZSTD_decompress.argtypes = sz, [vp, sz, vp, sz]
+    z.ZSTD_isError.restype, z.ZSTD_isError.argtypes = ctypes.c_uint, [sz]
+    z.ZSTD_versionNumber.restype = ctypes.c_uint
+    return z
+
+
+def mask_codec_leg(J, torch, dev, local, levels=(1, 3, 19)):
+    """The zero-mask part of the stream (Sec. III-C: the mask of zero samples,
+    for P XORed with the previous scan's, Sec. III-D) in this codec's per-row
+    class/literal form against the paper's form: the section's mask packed
+    into bytes (one bit per sample, row-major) and compressed with Zstd
+    (libzstd through ctypes, on the host). Our bytes are read from the GPU's
+    own stream; every Zstd frame is decompressed and checked."""
+    import ctypes
+
+    import numpy as np
+
+    from paper_2209_08196_gb300 import streaminfo, synth
+    z = _zstd()
+    if z is None:
+        return {"unavailable": "libzstd is not installed on this host"}
+    cases = [("16 x 64x1024 range, 8% dropouts", synth.config_small_range(seed=0)),
+             ("20 x 128x2048 five attributes, 12% zeros in range", synth.config_multi_attr(seed=0, n_scans=20)),
+             ("50 x 128x2048 range + reflectivity, 40% zeros in discs", synth.config_low_coherence(seed=7, n_scans=50))]
+    rows = []
+    for name, cfg in cases:
+        attrs = synth.attr_descs(cfg)
+        T, H, W, A = cfg.n_scans, cfg.H, cfg.W, len(attrs)
+        seq = synth.ScanSequence(cfg, device=dev)
+        sc = [seq.scan(t, as_numpy=False) for t in range(T)]
+        planes = [torch.stack([sc[t][a] for t in range(T)]) for a in range(A)]
+        del sc
+        enc = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, attrs, device=local)
+        out = torch.empty(J.jiffy_max_encoded_size(H, W, attrs, T), dtype=torch.uint8, device=dev)
+        n, _ = J.jiffy_encode_seq(enc, planes, out)
+        _, secs = streaminfo.sections(out[:n].cpu().numpy().tobytes())
+        # the zero masks of the quantized samples, packed 8 per byte (LSB first)
+        wts = torch.tensor([1, 2, 4, 8, 16, 32, 64, 128], dtype=torch.int32, device=dev)
+        packed = []
+        for a, (s_, P) in enumerate(attrs):
+            m = (1 << (8 * s_)) - 1
+            q = torch.clamp(((planes[a].to(torch.int64) & m) + P // 2) // P, max=m // P)
+            bits = (q == 0).to(torch.int32).reshape(T, H * W // 8, 8)
+            packed.append((bits * wts).sum(-1).to(torch.uint8).cpu().numpy())
+            del q, bits
+        zb = {lv: 0 for lv in levels}
+        for sinfo in secs:
+            src = packed[sinfo.attr][sinfo.frame]
+            if sinfo.mode == 1:
+                src = src ^ packed[sinfo.attr][sinfo.frame - 1]
+            src = np.ascontiguousarray(src)
+            cap = z.ZSTD_compressBound(src.nbytes)
+            dst = np.empty(cap, dtype=np.uint8)
+            back = np.empty(src.nbytes, dtype=np.uint8)
+            for lv in levels:
+                k = z.ZSTD_compress(dst.ctypes.data, cap, src.ctypes.data, src.nbytes, lv)
+                if z.ZSTD_isError(k):
+                    raise SystemExit("ZSTD_compress failed")
+                r = z.ZSTD_decompress(back.ctypes.data, back.nbytes, dst.ctypes.data, k)
+                if z.ZSTD_isError(r) or r != src.nbytes or not np.array_equal(back, src):
+                    raise SystemExit("Zstd round trip failed")
+                zb[lv] += k
+        ours = sum(x.mask_bytes for x in secs)
+        rows.append({"workload": name, "scans": T, "sections": len(secs),
+                     "p_share": sum(x.mode for x in secs) / len(secs),
+                     "packed_mask_bytes_per_scan": H * W * A / 8,
+                     "class_literal_bytes_per_scan": ours / T,
+                     "zstd_bytes_per_scan": {str(lv): zb[lv] / T for lv in levels},
+                     "mask_share_of_stream": ours / n,
+                     "stream_bytes_per_scan": n / T})
+        del planes, out, enc
+    v = z.ZSTD_versionNumber()
+    return {"zstd_version": "%d.%d.%d" % (v // 10000, v // 100 % 100, v % 100), "levels": list(levels),
+            "bit_order": "row-major, least significant bit first", "cases": rows}
+
+
 def whole_job_gpoints(px_per_rank: int, world: int, ms: float) -> float:
     """All ranks' pixels over the slowest rank's time, in Gpoints/s."""
     return px_per_rank * world / (ms / 1e3) / 1e9
@@ -728,6 +815,7 @@ def main():
     ap.add_argument("--no-standardize", action="store_true", help="skip the point-cloud standardization leg")
     ap.add_argument("--no-sweep", action="store_true", help="skip the stream-size sweep leg")
     ap.add_argument("--no-small", action="store_true", help="skip the 16 x 64 x 1024 single-stream leg")
+    ap.add_argument("--no-mask-codec", action="store_true", help="skip the Zstd mask comparison leg")
     ap.add_argument("--sweep-max-mib", type=int, default=4096, help="largest raw size of the sweep")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-sat-seconds", type=float, default=5.0)
@@ -1105,6 +1193,10 @@ def main():
     if not args.no_small:
         small = small_stream_leg(J, torch, dev, local)
 
+    mask_codec = None
+    if not args.no_mask_codec:
+        mask_codec = mask_codec_leg(J, torch, dev, local)
+
     sweep = None
     if not args.no_sweep:
         sweep = sweep_leg(J, torch, dev, local, args.sweep_max_mib)
@@ -1153,7 +1245,7 @@ def main():
                 "clocks": clocks,
                 "gpu_launches": 5 * args.steps * (2 if e2e else 1),
                 "batched": batched, "served": served, "heuristic": heuristic, "precision": precision,
-                "ablation": ablation, "standardize": standardize, "small_stream": small,
+                "ablation": ablation, "standardize": standardize, "small_stream": small, "mask_codec": mask_codec,
                 "sweep": None if sweep is None else roofline["sweep"]["rows"], "sweep_detail": sweep,
                 "batched_gpoints_s": None if batched is None else batched["gpoints_s"],
                 "served_p50_ms": None if served is None else served["p50_ms"],
