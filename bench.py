@@ -55,8 +55,8 @@ WORKLOAD = ("single stream, 100 scans x 128 beams x 2048 columns; range u32 (10 
 TRAFFIC = {
     "k_encode": (343683584 + 53487616, ("jiffy_encode.cu", "jiffy_device.cuh", "jiffy_kernels.h", "jiffy_types.h"),
                  "16ff4c760fe1264a"),
-    "k_decode": (78796800 + 293601792, ("jiffy_decode.cu", "jiffy_device.cuh", "jiffy_kernels.h", "jiffy_types.h"),
-                 "c9f83514574b48c3"),
+    "k_decode": (78800640 + 292420864, ("jiffy_decode.cu", "jiffy_device.cuh", "jiffy_kernels.h", "jiffy_types.h"),
+                 "ffa394a3069939f3"),
 }
 
 

@@ -9,19 +9,21 @@
 // on a done flag) and reads it back from the previous frame's output. There
 // is no CTA-wide barrier: a warp never waits for another warp of its CTA.
 //
-// Per row, each lane owns 8 consecutive pixels (one byte of the zero bitmask)
-// in each 256-pixel step:
+// Per row:
 //   lane 0   parses and bounds-checks the frame header and row-table entry
 //   lanes    class words -> literal prefix (Sec. III-C mask code)
-//   pass 1   own mask byte from its class code / literal, XOR with the
-//            previous scan's bits for P (Sec. III-D); nonzero counts
+//   mask     a mask word (32 pixels) per lane at a time: its class code or
+//            literal, XOR with the previous scan's word for P (Sec. III-D);
+//            one warp scan per 32 words gives each word's first compacted
+//            index
 //   lanes    block headers validated and sized (Sec. II, PFOR blocks)
-//   then, per 256-pixel step, interleaved:
+//   then, per 256-pixel step (lane l owning the 8 consecutive pixels
+//   8l .. 8l+7 of the step), interleaved:
 //   unpack   the blocks the step needs, lane l owning the 4 consecutive
 //            values 4l..4l+3: a window of the body words they occupy,
 //            funnel-shift extraction, exception high parts via a patch
 //            buffer, inverse ZigZag (Eq. 1), into a ring of deltas
-//   scatter  warp scan of counts -> compacted index of each own pixel; the
+//   scatter  compacted index of each own pixel from its mask word's; the
 //            lane's running sum of its deltas + a warp scan of the lanes'
 //            sums from the row's carry = the residuals (inverse delta); +
 //            previous pixel for P; x precision (Sec. III-A); vector stores
@@ -61,11 +63,12 @@ __device__ __forceinline__ uint32_t find_seg(const uint32_t* base, uint32_t n, u
 
 // Per-warp shared memory (byte offsets): a ring of 512 deltas (unpacked
 // ahead of the scatter), a 128-word exception patch buffer, the row's block
-// descriptors and mask bytes.
+// descriptors, zero mask words (1 = zero sample), each mask word's first
+// compacted index and literal mask words.
 constexpr uint32_t kRing = 512;
 
 struct DecWarpLayout {
-  uint32_t ring, patch, desc, mbytes, lits, bytes;
+  uint32_t ring, patch, desc, mw, wbase, lits, bytes;
 };
 
 __host__ __device__ inline DecWarpLayout dec_warp_layout(uint32_t W) {
@@ -73,8 +76,9 @@ __host__ __device__ inline DecWarpLayout dec_warp_layout(uint32_t W) {
   L.ring = 0;
   L.patch = L.ring + 4u * kRing;
   L.desc = L.patch + 4u * kBlockN;
-  L.mbytes = L.desc + ((8u * ceil_div_u32(W, kBlockN) + 15u) & ~15u);
-  L.lits = (L.mbytes + ceil_div_u32(W, 8u) + 15u) & ~15u;
+  L.mw = L.desc + ((8u * ceil_div_u32(W, kBlockN) + 15u) & ~15u);
+  L.wbase = L.mw + ((4u * ceil_div_u32(W, 32u) + 15u) & ~15u);
+  L.lits = L.wbase + ((4u * ceil_div_u32(W, 32u) + 15u) & ~15u);
   L.bytes = (L.lits + 4u * ceil_div_u32(W, 32u) + 15u) & ~15u;
   return L;
 }
@@ -95,8 +99,8 @@ struct SecCache {
 // (else both are read as 0).
 template <bool STAGED>
 __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k, uint32_t* ring,
-                                            uint32_t* patch, uint2* desc, uint8_t* mbytes, uint32_t* lits,
-                                            SecCache& sc) {
+                                            uint32_t* patch, uint2* desc, uint32_t* mw, uint32_t* wbase,
+                                            uint32_t* lits, SecCache& sc) {
   const uint32_t si = find_seg(p.seg_item_base, p.n_seg, k);
   const DecSeg& sg = p.seg[si];
   const uint32_t lane = lane_id();
@@ -262,50 +266,61 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   }
   const bool vec_out = vec_ok(orow, S) && (!srow || vec_ok(srow, S));
 
-  // ---- pass 1: own mask bytes (1 = zero sample) and nonzero counts. For P
-  //      (Sec. III-D) the previous scan's mask comes from the mask words the
-  //      previous frame's row wrote in this call, else from its samples.
-  //      Without the mask stage (no class words) every sample is coded.
-  uint32_t cnt = 0;
+  // ---- zero mask, a word (32 pixels) per lane at a time: class code or
+  //      literal (Sec. III-C); for P (Sec. III-D) the XOR with the previous
+  //      scan's mask is undone, that mask taken from the words the previous
+  //      frame's row wrote in this call, else from its samples. Without the
+  //      mask stage (no class words) every sample is coded. One warp scan per
+  //      32 words gives each word's first compacted index.
+  uint32_t n = 0;
   if (!bad) {
     const bool xor_prev = mode == 1u && !(stages & kStageNoMask);
-    const uint8_t* pmask = (xor_prev && t > 0)
-                               ? reinterpret_cast<const uint8_t*>(p.masks + sg.mask_base + (size_t)(kl - H) * nw)
-                               : nullptr;
-    uint8_t* omask = (sc.next_p && !(stages & kStageNoMask))
-                         ? reinterpret_cast<uint8_t*>(p.masks + sg.mask_base + (size_t)kl * nw)
-                         : nullptr;
-    for (uint32_t it = 0; it < niter; it++) {
-      const uint32_t x0 = 256u * it + 8u * lane;
-      const uint32_t j = x0 >> 5;
-      const uint32_t cwj = __shfl_sync(0xffffffffu, cw, (j >> 4) & 31u);
-      const uint32_t lpj = __shfl_sync(0xffffffffu, litpre, (j >> 4) & 31u);
-      if (x0 < W) {
-        const uint32_t sl = 2u * (j & 15u), cls = (cwj >> sl) & 3u;
-        uint32_t X = 0;
-        if (cls == 1u) X = valid_word_bits(W, nw, j);
-        else if (cls == 2u) X = lits[lpj + __popc(literal_bits(cwj) & ((1u << sl) - 1u))];
-        const uint32_t nv = min(8u, W - x0), vm = (1u << nv) - 1u;
-        uint32_t mb = (X >> (x0 & 31u)) & 0xffu;
-        if (pmask) {
-          mb ^= __ldcg(pmask + (x0 >> 3));  // Sec. III-D: undo the XOR with the previous scan's mask
-        } else if (xor_prev) {
+    const uint32_t* pmask = (xor_prev && t > 0) ? p.masks + sg.mask_base + (size_t)(kl - H) * nw : nullptr;
+    uint32_t* omask = (sc.next_p && !(stages & kStageNoMask)) ? p.masks + sg.mask_base + (size_t)kl * nw : nullptr;
+    const bool prev_samples = xor_prev && !pmask;
+    if (prev_samples) {  // the previous scan's zero bits, 8 pixels per lane per step, into mw
+      uint8_t* pb = reinterpret_cast<uint8_t*>(mw);
+      for (uint32_t it = 0; it < niter; it++) {
+        const uint32_t x0 = 256u * it + 8u * lane;
+        if (x0 < W) {
+          const uint32_t nv = min(8u, W - x0);
           uint32_t pv[8];
           load8<true>(prow, S, x0, nv, vec_prev, pv);
           uint32_t pm = 0;
 #pragma unroll
           for (int i = 0; i < 8; i++) pm |= (uint32_t)(pv[i] == 0u) << i;
-          mb ^= pm;
+          pb[x0 >> 3] = (uint8_t)pm;
         }
-        mb &= vm;
-        if (omask) omask[x0 >> 3] = (uint8_t)mb;
-        mb |= 0xffu & ~vm;  // pixels past W count as zero samples
-        mbytes[x0 >> 3] = (uint8_t)mb;
-        cnt += __popc(~mb & 0xffu);
       }
+      __syncwarp();
+    }
+    for (uint32_t j0 = 0; j0 < nw; j0 += 32u) {
+      const uint32_t j = j0 + lane;
+      const uint32_t cwj = __shfl_sync(0xffffffffu, cw, (j >> 4) & 31u);
+      const uint32_t lpj = __shfl_sync(0xffffffffu, litpre, (j >> 4) & 31u);
+      uint32_t kept = 0;
+      if (j < nw) {
+        const uint32_t valid = valid_word_bits(W, nw, j);
+        uint32_t X = 0;
+        if (ncls) {
+          const uint32_t sl = 2u * (j & 15u), cls = (cwj >> sl) & 3u;
+          if (cls == 1u) X = valid;
+          else if (cls == 2u) X = lits[lpj + __popc(literal_bits(cwj) & ((1u << sl) - 1u))];
+          if (pmask) X ^= __ldcg(pmask + j);
+          else if (prev_samples) X ^= mw[j];  // bits past W are cleared below
+          X &= valid;
+          if (omask) omask[j] = X;
+        }
+        mw[j] = X;
+        kept = __popc(~X & valid);
+      }
+      uint32_t tot;
+      const uint32_t ex = warp_excl_scan(kept, tot);
+      if (j < nw) wbase[j] = n + ex;
+      n += tot;
     }
   }
-  const uint32_t n = warp_sum(cnt);
+  __syncwarp();
   const uint32_t nb = ceil_div_u32(n, kBlockN);
 
   // ---- block headers (lane l: blocks 4l .. 4l+3): validate, size the
@@ -355,16 +370,18 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
     const uint32_t Pq = at.P;
     const bool no_delta = (stages & kStageNoDelta) != 0u, no_zz = (stages & kStageNoZigzag) != 0u;
     const uint32_t last_word = clen / 4u - 1u;
-    uint32_t erun = carry, blk = 0, unpacked = 0, kbase = 0;
+    uint32_t erun = carry, blk = 0, unpacked = 0;
     bool xbad = false;
     for (uint32_t it = 0; it < niter && !xbad; it++) {
       const uint32_t x0 = 256u * it + 8u * lane;
       const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
-      const uint32_t mb = nv ? mbytes[x0 >> 3] : 0xffu;
-      const uint32_t nzm = ~mb & 0xffu;
-      uint32_t segn;
-      uint32_t kk = kbase + warp_excl_scan(__popc(nzm), segn);
-      while (unpacked < kbase + segn) {
+      // own pixels' mask byte (pixels past W count as zero samples) and the
+      // compacted index of the first; the step ends at the next word group
+      const uint32_t X = nv ? mw[x0 >> 5] : 0xffffffffu;
+      const uint32_t nzm = ~(X >> (x0 & 31u)) & ((1u << nv) - 1u);
+      uint32_t kk = nv ? wbase[x0 >> 5] + __popc(~X & ((1u << (x0 & 31u)) - 1u)) : n;
+      const uint32_t kend = 8u * it + 8u < nw ? wbase[8u * it + 8u] : n;
+      while (unpacked < kend) {
         const uint2 dsc = desc[blk];
         const uint32_t b = dsc.y & 0xffu, e = (dsc.y >> 8) & 0xffu, hb = (dsc.y >> 16) & 0xffu;
         const uint32_t bm = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
@@ -454,7 +471,6 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
         store8(orow, S, x0, nv, vec_out, out);
         if (srow) store8(srow, S, x0, nv, vec_out, out);
       }
-      kbase += segn;
       __syncwarp();
     }
     bad = xbad;
@@ -474,7 +490,8 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
   uint32_t* ring = reinterpret_cast<uint32_t*>(wb + lay.ring);
   uint32_t* patch = reinterpret_cast<uint32_t*>(wb + lay.patch);
   uint2* desc = reinterpret_cast<uint2*>(wb + lay.desc);
-  uint8_t* mbytes = wb + lay.mbytes;
+  uint32_t* mw = reinterpret_cast<uint32_t*>(wb + lay.mw);
+  uint32_t* wbase = reinterpret_cast<uint32_t*>(wb + lay.wbase);
   uint32_t* lits = reinterpret_cast<uint32_t*>(wb + lay.lits);
   SecCache sc{0ull, 0u, 0u, 0u, 0u, 0ull};
   while (true) {
@@ -484,7 +501,7 @@ __global__ void __launch_bounds__(WPC * 32) k_decode(DecParams p) {
     if (kb >= p.n_items) break;
     const uint32_t kend = min(kb + p.items_per_ticket, p.n_items);
     for (uint32_t k = kb; k < kend; k++) {
-      decode_item<STAGED>(p, k, ring, patch, desc, mbytes, lits, sc);
+      decode_item<STAGED>(p, k, ring, patch, desc, mw, wbase, lits, sc);
     }
   }
 }
@@ -504,7 +521,7 @@ static cudaError_t dec_occupancy(size_t smem, bool staged, int* per_sm) {
 
 int decode_rows_launch(const DecParams& p, RowsLaunch* out) {
   const DecWarpLayout L = dec_warp_layout(p.max_W);
-  if ((L.ring | L.patch | L.desc | L.mbytes | L.lits | L.bytes) & 15u) return (int)cudaErrorInvalidValue;  // 16-byte aligned regions
+  if ((L.ring | L.patch | L.desc | L.mw | L.wbase | L.lits | L.bytes) & 15u) return (int)cudaErrorInvalidValue;  // 16-byte aligned regions
   uint32_t wpc = p.wpc;
   if ((wpc != 1 && wpc != 2 && wpc != 4 && wpc != 8) || wpc * L.bytes > kDecSmemMax) wpc = 0;
   if (!wpc) wpc = 4 * L.bytes <= kDecSmemAuto ? 4u : (2 * L.bytes <= kDecSmemAuto ? 2u : 1u);
