@@ -131,6 +131,10 @@ struct jiffy_batch {
 
 namespace {
 
+// Rows of at most this many columns fit 6 encoder CTAs of 4 warps per SM;
+// a call that also codes wider rows runs them in a rows launch of their own.
+constexpr uint32_t kNarrowW = 2048;
+
 struct DeviceGuard {
   int prev = -1;
   bool ok = false;
@@ -487,7 +491,24 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   std::vector<uint32_t> sig{1, max_W, log2_ceil(items)};
   uint32_t staged = 0, withhold = 0;
   uint32_t item_base = 0, sec_base = 0;
-  for (uint32_t i = 0; i < n; i++) {
+  // segment order: streams of rows up to kNarrowW columns first, so that the
+  // rows kernel can run them in a launch of its own with shared memory (and
+  // so occupancy) sized for them (segments are independent; the search keys
+  // stay ascending)
+  std::vector<uint32_t> ord;
+  uint32_t split = 0, split_W = 1;
+  for (int pass = 0; pass < 2; pass++)
+    for (uint32_t i = 0; i < n; i++)
+      if ((jobs[i].s->W <= kNarrowW) == (pass == 0)) {
+        ord.push_back(i);
+        if (pass == 0) {
+          split += jobs[i].T * jobs[i].s->A * jobs[i].s->H;
+          split_W = std::max(split_W, jobs[i].s->W);
+        }
+      }
+  if (split == items) split = 0;  // one width class: one launch
+  for (uint32_t si = 0; si < n; si++) {
+    const uint32_t i = ord[si];
     EncJob& j = jobs[i];
     jiffy_stream* s = j.s;
     const uint32_t T = j.T, A = s->A;
@@ -530,9 +551,9 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     g.frame_off = (j.async && j.dev_offsets) ? reinterpret_cast<unsigned long long*>(j.dev_offsets)
                                              : reinterpret_cast<unsigned long long*>(d + o_res + r_off[i]);
     g.err = j.async ? s->d_err : reinterpret_cast<uint32_t*>(d + o_res + r_err[i]);
-    segs[i] = g;
-    ib[i] = item_base;
-    sb[i] = sec_base;
+    segs[si] = g;
+    ib[si] = item_base;
+    sb[si] = sec_base;
     if (s->withhold < T * A * s->H) withhold = item_base + s->withhold + 1u;
     s->withhold = UINT32_MAX;  // one call
     item_base += T * A * s->H;
@@ -552,6 +573,8 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   p.n_items = (uint32_t)items;
   p.n_sec = (uint32_t)secs;
   p.max_W = max_W;
+  p.split = split;
+  p.split_W = split_W;
   p.seg = reinterpret_cast<const jiffy::EncSeg*>(d + o_up + u_seg);
   p.seg_item_base = reinterpret_cast<const uint32_t*>(d + o_up + u_ib);
   p.seg_sec_base = reinterpret_cast<const uint32_t*>(d + o_up + u_sb);

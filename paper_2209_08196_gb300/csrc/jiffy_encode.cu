@@ -860,11 +860,11 @@ __global__ void __launch_bounds__(WPC * 32, 24 / WPC) k_encode(EncParams p) {
   // round trip overlaps the work (an item still waits only on items handed
   // out before it: a warp holding an unstarted ticket is coding a smaller one)
   uint32_t k = 0;
-  if (lane == 0) k = atomicAdd(p.ticket, 1u);
+  if (lane == 0) k = p.item_lo + atomicAdd(p.ticket, 1u);
   k = __shfl_sync(kFull, k, 0);
   while (k < p.n_items) {
     uint32_t next = 0;
-    if (lane == 0) next = atomicAdd(p.ticket, 1u);
+    if (lane == 0) next = p.item_lo + atomicAdd(p.ticket, 1u);
     encode_item<STAGED>(p, k, w);
     k = __shfl_sync(kFull, next, 0);
   }
@@ -1031,7 +1031,7 @@ int encode_rows_launch(const EncParams& p, RowsLaunch* out) {
   uint32_t ctas = (uint32_t)max(per_sm, 1);
   if (p.ctas_per_sm) ctas = min(ctas, p.ctas_per_sm);
   // enough warps to fill the GPU; warps beyond the work find the ticket spent
-  const uint32_t want = ceil_div_u32(p.n_items, wpc);
+  const uint32_t want = ceil_div_u32(p.n_items - p.item_lo, wpc);
   out->wpc = wpc;
   out->ctas_per_sm = ctas;
   out->items_per_ticket = 1;
@@ -1057,16 +1057,34 @@ int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   mark(0);
   if (p.trial_rows) k_trial<<<p.n_sec * p.trial_rows, 32, s_trial, st>>>(p);
   mark(1);
-  const size_t smem = (size_t)rl.wpc * enc_warp_layout(p.max_W).bytes;
-  if (p.staged) {
-    if (rl.wpc == 4) k_encode<4, true><<<rl.grid, 4 * 32, smem, st>>>(p);
-    else if (rl.wpc == 2) k_encode<2, true><<<rl.grid, 2 * 32, smem, st>>>(p);
-    else k_encode<1, true><<<rl.grid, 32, smem, st>>>(p);
+  // rows of narrow segments first, with shared memory (and so occupancy) for
+  // their own width, then the wider ones: one rows launch per width class
+  // (each launch sets its own shared-memory limit first: resolving another
+  // launch's configuration changes it)
+  auto rows = [&](const EncParams& q, const RowsLaunch& r) -> cudaError_t {
+    const size_t smem = (size_t)r.wpc * enc_warp_layout(q.max_W).bytes;
+    void (*f)(EncParams) = q.staged ? (r.wpc == 4 ? k_encode<4, true> : r.wpc == 2 ? k_encode<2, true> : k_encode<1, true>)
+                                    : (r.wpc == 4 ? k_encode<4, false> : r.wpc == 2 ? k_encode<2, false> : k_encode<1, false>);
+    cudaError_t ce = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ce != cudaSuccess) return ce;
+    f<<<r.grid, r.wpc * 32, smem, st>>>(q);
+    return cudaGetLastError();
+  };
+  if (p.split > 0 && p.split < p.n_items) {
+    EncParams lo = p, hi = p;
+    lo.n_items = p.split;
+    lo.max_W = p.split_W;
+    hi.item_lo = p.split;
+    hi.ticket = p.ticket + 1;
+    RowsLaunch rlo{};
+    rc = encode_rows_launch(lo, &rlo);
+    if (rc != 0) return rc;
+    e = rows(lo, rlo);
+    if (e == cudaSuccess) e = rows(hi, rl);
   } else {
-    if (rl.wpc == 4) k_encode<4, false><<<rl.grid, 4 * 32, smem, st>>>(p);
-    else if (rl.wpc == 2) k_encode<2, false><<<rl.grid, 2 * 32, smem, st>>>(p);
-    else k_encode<1, false><<<rl.grid, 32, smem, st>>>(p);
+    e = rows(p, rl);
   }
+  if (e != cudaSuccess) return (int)e;  // the placement kernels would read row sizes never written
   mark(2);
   k_sec_sizes<<<p.n_sec, kThreads, 0, st>>>(p);
   k_place<<<p.n_sec * kPlaceSplit, kThreads, s_place, st>>>(p);

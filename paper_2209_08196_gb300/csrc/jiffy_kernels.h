@@ -61,6 +61,11 @@ struct EncParams {
   uint32_t ctas_per_sm;          // rows kernel: resident CTAs per SM (0 = occupancy limit)
   uint32_t staged;               // 1: launch the rows kernel that reads stage switches and the test hook
   uint32_t withhold;             // test hook: 1 + the row item that does not publish its carry status (0: none)
+  // rows kernel launches: items [item_lo, n_items) from ticket word ticket[0];
+  // split > 0: the launcher runs two rows launches, items [0, split) sized for
+  // rows of at most split_W columns, then [split, n_items) from ticket[1]
+  uint32_t item_lo;
+  uint32_t split, split_W;
 };
 
 struct DecSeg {

@@ -108,6 +108,33 @@ def test_batch_encode_decode_matches_oracle_over_calls(stages):
     assert saw_p, "the sequences should select P for some attribute"
 
 
+def test_mixed_row_widths_in_one_call_match_oracle():
+    # rows wider than 2048 columns next to narrower ones: the encoder runs the
+    # narrow segments' rows in a launch of their own (wide ones after), and
+    # the segments are numbered narrow first whatever the call's order
+    rng = np.random.default_rng(19)
+    sensors = [(4, 3000, [(4, 10), (2, 1)]), (8, 500, [(4, 4)]), (2, 5000, [(1, 1)]), (6, 2048, [(2, 3)]),
+               (3, 2049, [(4, 1)])]
+    fleet = Fleet(sensors)
+    for Ts in ([2, 1, 3, 1, 2], [1, 2, 1, 2, 1]):
+        scans = [make_scans(rng, H, W, a, T) for (H, W, a), T in zip(sensors, Ts)]
+        got = fleet.encode(scans)
+        bufs, offsets, planes_out = [], [], []
+        for i, ((H, W, a), sc) in enumerate(zip(sensors, scans)):
+            want = b"".join(fleet.ref[i].encode(x) for x in sc)
+            assert got[i][0] == want, "stream %d" % i
+            bufs.append(torch.from_numpy(np.frombuffer(got[i][0], dtype=np.uint8).copy()).cuda())
+            offsets.append(got[i][1])
+            planes_out.append([torch.empty((len(sc), H, W), dtype=TORCH_DT[x], device="cuda") for x, _ in a])
+        J.jiffy_decode_batch(fleet.b, fleet.dec, bufs, [len(x) for x, _ in got], offsets, planes_out)
+        for i, ((H, W, a), sc) in enumerate(zip(sensors, scans)):
+            buf, offs = got[i]
+            for t in range(len(sc)):
+                want, _ = fleet.refd[i].decode(buf[(offs[t] if t else 0):offs[t + 1]])
+                for k, (x, _) in enumerate(a):
+                    assert np.array_equal(to_np(planes_out[i][k][t], x), want[k]), (i, t, k)
+
+
 def test_batch_equals_per_stream_calls():
     rng = np.random.default_rng(12)
     scans = [make_scans(rng, H, W, a, 3) for H, W, a in SENSORS]
