@@ -241,6 +241,39 @@ def _oracle_worker(conn, start, H, W, attrs, repeats):
     conn.close()
 
 
+def cpu_baseline_configs(budget_s: float = 4.0):
+    """The oracle, single-threaded, on the small single-stream case (16 x
+    64x1024 range at 10 mm) and on the low-coherence case (128x2048 range at
+    1 mm + reflectivity, 40 % zeros in discs): scans generated on the host,
+    encode then decode of each, until about budget_s of CPU work per case."""
+    import oracle
+    from paper_2209_08196_gb300 import synth
+    out = {}
+    for name, cfg in (("16 x 64x1024 range", synth.config_small_range(seed=0)),
+                      ("128x2048 low coherence", synth.config_low_coherence(seed=7, n_scans=12))):
+        attrs = synth.attr_descs(cfg)
+        seq = synth.ScanSequence(cfg)
+        enc = oracle.Codec(cfg.H, cfg.W, attrs)
+        dec = oracle.Codec(cfg.H, cfg.W, attrs)
+        n_scans, t_enc, t_dec = 0, 0.0, 0.0
+        for t in range(cfg.n_scans):
+            planes = seq.scan(t)
+            t0 = time.perf_counter()
+            b = enc.encode(planes)
+            t1 = time.perf_counter()
+            dec.decode(b)
+            t2 = time.perf_counter()
+            t_enc += t1 - t0
+            t_dec += t2 - t1
+            n_scans += 1
+            if t_enc + t_dec >= budget_s:
+                break
+        px = n_scans * cfg.H * cfg.W
+        out[name] = {"scans": n_scans, "cores": 1, "mpoints_s": px / (t_enc + t_dec) / 1e6,
+                     "encode_mpoints_s": px / t_enc / 1e6, "decode_mpoints_s": px / t_dec / 1e6}
+    return out
+
+
 def cpu_baseline_ncore(cfg, attrs, scans, repeats: int = 6):
     """The oracle, as it stands, on every host core at once: the scans split
     into one independent stream per core (spawned processes, so no forked
@@ -1208,7 +1241,7 @@ def main():
         served = serve_leg(J, torch, dev, local, args.serve_seconds, args.serve_sat_seconds)
 
     if rank == 0:
-        cpu = cpu_n = None
+        cpu = cpu_n = cpu_cfg = None
         if not args.no_cpu_baseline and world == 1:
             host_scans = [[planes_in[a][t] for a in range(A)] for t in range(T)]
             cpu = cpu_baseline(cfg, attrs, host_scans)
@@ -1216,6 +1249,7 @@ def main():
                 cpu_n = cpu_baseline_ncore(cfg, attrs, host_scans)
             except Exception as ex:  # a reported extra; the run goes on without it
                 cpu_n = {"value": None, "error": "%s: %s" % (type(ex).__name__, ex)}
+            cpu_cfg = cpu_baseline_configs()
         modes = {"ratio": raw_bytes / n}
         # compact copies of the other legs' headline figures inside the keys the
         # contract defines (the full legs follow as their own keys)
@@ -1241,7 +1275,8 @@ def main():
                 "config": {"workload": WORKLOAD, "scans": T, "H": H, "W": W, "attributes": A, "seed": rank,
                            "raw_bytes_per_step": raw_bytes, "l2": "inputs larger than L2 (no flush)",
                            "parallelism": "replicas" if world > 1 else "single GPU"},
-                "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_n, "e2e": e2e,
+                "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_n,
+                "cpu_baseline_configs": cpu_cfg, "e2e": e2e,
                 "clocks": clocks,
                 "gpu_launches": 5 * args.steps * (2 if e2e else 1),
                 "batched": batched, "served": served, "heuristic": heuristic, "precision": precision,
