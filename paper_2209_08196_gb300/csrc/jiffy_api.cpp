@@ -66,6 +66,9 @@ struct Pending {
 struct GraphCache {
   std::vector<uint64_t> key;
   cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;            // kept while exec lives: its nodes address the exec's
+  std::vector<cudaGraphNode_t> ev_nodes;  // the event record nodes of the kernel timing events
+  std::vector<cudaEvent_t> ev_now;        // the events they record in the exec
 };
 
 // Device scratch, pinned host staging, timing events, graph cache and tuned
@@ -160,7 +163,11 @@ struct Carver {
 
 void drop_graph(GraphCache& g) {
   if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
   g.exec = nullptr;
+  g.graph = nullptr;
+  g.ev_nodes.clear();
+  g.ev_now.clear();
   g.key.clear();
 }
 
@@ -378,10 +385,13 @@ jiffy_status tune(Workspace& ws, bool encode, const Params& p0, cudaStream_t st,
 
 // Enqueues the call through the graph cache when graphs are on: replays the
 // captured sequence if the call's shape and buffers match the last capture,
-// else captures it anew on the workspace's capture stream.
+// else captures it anew on the workspace's capture stream. tev: the call's n_tev
+// kernel timing events (or null); a replay points the graph's timing event
+// nodes at them, so calls that time their kernels with different event sets
+// (enqueue-only calls take the next set of a ring) share one graph.
 template <class Enqueue>
 jiffy_status run_sequence(Workspace& ws, GraphCache& gc, const std::vector<uint64_t>& key, cudaStream_t st,
-                          bool use_graph, Enqueue enqueue) {
+                          bool use_graph, void* const* tev, uint32_t n_tev, Enqueue enqueue) {
   if (!use_graph) return enqueue(st) == 0 ? JIFFY_OK : JIFFY_ERR_CUDA;
   if (!(gc.exec && gc.key == key)) {
     drop_graph(gc);
@@ -395,15 +405,53 @@ jiffy_status run_sequence(Workspace& ws, GraphCache& gc, const std::vector<uint6
       if (graph) cudaGraphDestroy(graph);
       return JIFFY_ERR_CUDA;
     }
+    // the timing events' record nodes, in the order of tev
+    gc.ev_nodes.assign(n_tev, nullptr);
+    gc.ev_now.assign(n_tev, nullptr);
+    if (n_tev) {
+      size_t nn = 0;
+      std::vector<cudaGraphNode_t> nodes;
+      bool ok = cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess;
+      if (ok) {
+        nodes.resize(nn);
+        ok = cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess;
+      }
+      for (size_t i = 0; ok && i < nn; i++) {
+        cudaGraphNodeType ty;
+        cudaEvent_t e = nullptr;
+        if (cudaGraphNodeGetType(nodes[i], &ty) != cudaSuccess) ok = false;
+        else if (ty == cudaGraphNodeTypeEventRecord && cudaGraphEventRecordNodeGetEvent(nodes[i], &e) == cudaSuccess)
+          for (uint32_t k = 0; k < n_tev; k++)
+            if (e == static_cast<cudaEvent_t>(tev[k])) {
+              gc.ev_nodes[k] = nodes[i];
+              gc.ev_now[k] = e;
+            }
+      }
+      for (uint32_t k = 0; k < n_tev; k++) ok = ok && gc.ev_nodes[k] != nullptr;
+      if (!ok) {
+        cudaGraphDestroy(graph);
+        gc.ev_nodes.clear();
+        gc.ev_now.clear();
+        return JIFFY_ERR_CUDA;
+      }
+    }
     const cudaError_t ie = cudaGraphInstantiate(&gc.exec, graph, 0);
-    cudaGraphDestroy(graph);
     if (ie != cudaSuccess) {
+      cudaGraphDestroy(graph);
       gc.exec = nullptr;
       return JIFFY_ERR_CUDA;
     }
+    gc.graph = graph;
     gc.key = key;
     ws.captures++;
   } else {
+    for (uint32_t k = 0; k < n_tev && k < gc.ev_nodes.size(); k++) {
+      cudaEvent_t e = static_cast<cudaEvent_t>(tev[k]);
+      if (gc.ev_now[k] != e) {
+        if (cudaGraphExecEventRecordNodeSetEvent(gc.exec, gc.ev_nodes[k], e) != cudaSuccess) return JIFFY_ERR_CUDA;
+        gc.ev_now[k] = e;
+      }
+    }
     ws.replays++;
   }
   return cudaGraphLaunch(gc.exec, st) == cudaSuccess ? JIFFY_OK : JIFFY_ERR_CUDA;
@@ -627,9 +675,8 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   void* evs[4] = {ws.ev[0], ws.ev[1], ws.ev[2], ws.ev[3]};
   void* const* tev = timed ? (async ? next_evset(ws, 3) : evs) : nullptr;
   if (timed && !tev) return JIFFY_ERR_CUDA;
-  // (a timed enqueue-only call uses the next event set of the ring: launched
-  // directly, not replayed from the graph, whose events are fixed)
-  r = run_sequence(ws, ws.g_enc, key, st, ws.graphs && !(async && timed),
+  // (a timed enqueue-only call uses the next event set of the ring)
+  r = run_sequence(ws, ws.g_enc, key, st, ws.graphs, tev, timed ? 4u : 0u,
                    [&](cudaStream_t s) { return enqueue(s, p, tev); });
   if (r != JIFFY_OK) return r;
   if (cudaEventRecord(ws.done, st) != cudaSuccess) return JIFFY_ERR_CUDA;
@@ -838,7 +885,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   void* evs[2] = {ws.ev[0], ws.ev[1]};
   void* const* tev = timed ? (async ? next_evset(ws, 1) : evs) : nullptr;
   if (timed && !tev) return JIFFY_ERR_CUDA;
-  r = run_sequence(ws, ws.g_dec, key, st, ws.graphs && !(async && timed),
+  r = run_sequence(ws, ws.g_dec, key, st, ws.graphs, tev, timed ? 2u : 0u,
                    [&](cudaStream_t s) { return enqueue(s, p, tev); });
   if (r != JIFFY_OK) return r;
   if (cudaEventRecord(ws.done, st) != cudaSuccess) return JIFFY_ERR_CUDA;

@@ -58,6 +58,40 @@ def test_async_round_trip_matches_oracle_over_steps():
             assert np.array_equal(to_np(outs[a][t], s), want_planes[t][a]), (t, a)
 
 
+def test_timed_async_calls_replay_graphs_with_their_own_timing_events():
+    # kernel timing on: every enqueue-only call records its kernel times with
+    # the next event set of a ring of 16, while the call's launch sequence is
+    # replayed from one captured graph whose timing nodes are pointed at that
+    # set; 20 steps in flight go round the ring, and the bytes, planes and
+    # kernel times stay right
+    cfg, attrs, scans = workload(4, seed=12)
+    H, W, T = cfg.H, cfg.W, len(scans)
+    want, _, _ = oracle.encode_sequence(H, W, attrs, scans)
+    want_planes, _ = oracle.decode_sequence(H, W, attrs, want, T)
+    enc = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, attrs)
+    dec = J.jiffy_stream_create(J.JIFFY_DECODER, H, W, attrs)
+    J.jiffy_stream_set_profiling(enc, True)
+    J.jiffy_stream_set_profiling(dec, True)
+    planes = stacked(scans, attrs)
+    out = torch.zeros(J.jiffy_max_encoded_size(H, W, attrs, T), dtype=torch.uint8, device="cuda")
+    d_offs = torch.zeros(T + 1, dtype=torch.int64, device="cuda")
+    outs = J.empty_planes(dec, T)
+    for _ in range(20):
+        J.jiffy_stream_reset(enc)
+        J.jiffy_stream_reset(dec)
+        J.jiffy_encode_seq_async(enc, planes, out, d_offs)
+        J.jiffy_decode_seq_async(dec, out, d_offs, outs)
+    J.jiffy_stream_wait(enc)
+    J.jiffy_stream_wait(dec)
+    te, td = J.jiffy_stream_kernel_times(enc), J.jiffy_stream_kernel_times(dec)
+    assert len(te) == 3 and all(t > 0 for t in te) and len(td) == 1 and td[0] > 0
+    offs = [int(x) for x in d_offs.cpu()]
+    assert out[:offs[-1]].cpu().numpy().tobytes() == want
+    for t in range(T):
+        for a, (s, _) in enumerate(attrs):
+            assert np.array_equal(to_np(outs[a][t], s), want_planes[t][a]), (t, a)
+
+
 def test_async_calls_chain_p_frames_across_calls():
     # two calls of 3 scans each, no reset between them: the second call's
     # first frame predicts from the first call's last scan (Sec. III-D)
