@@ -216,21 +216,21 @@ __device__ __noinline__ void state_row(const uint8_t* cur, uint8_t* st_row, cons
 // to zi, P to zp).
 template <int QU>
 __device__ __forceinline__ uint32_t pass_a_trial(const uint8_t* cur, const uint8_t* prv, const AttrDev at, uint32_t W,
-                                              uint32_t kz, uint32_t* zi, uint32_t* zp) {
+                                              uint32_t kz, bool pmode, uint32_t* zb) {
   const uint32_t lane = lane_id(), S = at.s;
   const bool vc = vec_ok(cur, S), vp = vec_ok(prv, S);
   uint32_t n = 0;
   for (uint32_t base = 0; base < W; base += kStepPx) {
     const uint32_t x0 = base + 8u * lane;
     const uint32_t nv = x0 < W ? min(8u, W - x0) : 0u;
-    uint32_t v[8], pv[8];
+    uint32_t v[8], pv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     load8<false>(cur, S, x0, nv, vc, v);
-    load8<false>(prv, S, x0, nv, vp, pv);
+    if (pmode) load8<false>(prv, S, x0, nv, vp, pv);
     uint32_t zm = 0;
 #pragma unroll
     for (int i = 0; i < 8; i++) {
       v[i] = quant<QU>(v[i], at);
-      pv[i] = v[i] - quant<QU>(pv[i], at);
+      if (pmode) pv[i] = v[i] - quant<QU>(pv[i], at);
       zm |= (v[i] == 0u ? 1u : 0u) << i;
     }
     const uint32_t nz = ~(zm & kz) & ((1u << nv) - 1u);
@@ -239,8 +239,7 @@ __device__ __forceinline__ uint32_t pass_a_trial(const uint8_t* cur, const uint8
 #pragma unroll
     for (int i = 0; i < 8; i++) {
       if ((nz >> i) & 1u) {
-        zi[zaddr(kk)] = v[i];
-        zp[zaddr(kk)] = pv[i];
+        zb[zaddr(kk)] = pmode ? pv[i] : v[i];
         kk++;
       }
     }
@@ -627,7 +626,11 @@ __device__ __forceinline__ uint32_t code_step(uint32_t* zb, uint32_t s0, uint32_
 // ----------------------------------------------------------------------------
 __global__ void __launch_bounds__(32) k_trial(EncParams p) {
   extern __shared__ __align__(16) uint32_t smem[];
-  const uint32_t gs = blockIdx.x / p.trial_rows, ti = blockIdx.x % p.trial_rows;
+  // one mode per CTA (I: even blocks, P: odd), so a CTA needs one buffer and
+  // twice as many fit an SM
+  const bool pmode = (blockIdx.x & 1u) != 0u;
+  const uint32_t gsr = blockIdx.x >> 1;
+  const uint32_t gs = gsr / p.trial_rows, ti = gsr % p.trial_rows;
   const EncSeg& sg = p.seg[find_seg(p.seg_sec_base, p.n_seg, gs)];
   const uint32_t ta = gs - sg.sec_base;
   const uint32_t t = ta / sg.A, a = ta % sg.A;
@@ -647,15 +650,14 @@ __global__ void __launch_bounds__(32) k_trial(EncParams p) {
   const uint8_t* prv = sg.prev[ta];
   const uint32_t st = sg.stages;
   const bool all = (st & kStageNoMask) != 0u;
-  uint32_t* zi = smem;
-  uint32_t* zp = smem + zbuf_words(W);
-  if (lane_id() == 0) {  // fetch the test row (both scans) and the earlier test row's tail into L2 at once
+  uint32_t* zb = smem;
+  if (lane_id() == 0) {  // fetch the test row and the earlier test row's tail into L2 at once
     prefetch_l2(cur + test_row(ti) * rowb, rowb);
-    prefetch_l2(prv + test_row(ti) * rowb, rowb);
+    if (pmode) prefetch_l2(prv + test_row(ti) * rowb, rowb);
     if (ti > 0) {
       const size_t tail = min(rowb, (size_t)kStepPx * at.s);
       prefetch_l2(cur + test_row(ti - 1) * rowb + rowb - tail, tail);
-      prefetch_l2(prv + test_row(ti - 1) * rowb + rowb - tail, tail);
+      if (pmode) prefetch_l2(prv + test_row(ti - 1) * rowb + rowb - tail, tail);
     }
   }
   // carry: the last residual of the nearest earlier test row that has one
@@ -673,21 +675,14 @@ __global__ void __launch_bounds__(32) k_trial(EncParams p) {
   const uint8_t* p1 = prv + test_row(ti) * rowb;
   uint32_t n;
   const uint32_t kz = all ? 0u : 0xffu;
-  if (at.qkind == 0) n = pass_a_trial<0>(c1, p1, at, W, kz, zi, zp);
-  else if (at.qkind == 1) n = pass_a_trial<1>(c1, p1, at, W, kz, zi, zp);
-  else n = pass_a_trial<2>(c1, p1, at, W, kz, zi, zp);
+  if (at.qkind == 0) n = pass_a_trial<0>(c1, p1, at, W, kz, pmode, zb);
+  else if (at.qkind == 1) n = pass_a_trial<1>(c1, p1, at, W, kz, pmode, zb);
+  else n = pass_a_trial<2>(c1, p1, at, W, kz, pmode, zb);
   __syncwarp();
   const bool nd = (st & kStageNoDelta) != 0u;
-  if (n) {
-    fill_tail(zi, n, nd ? 0u : zi[zaddr(n - 1)]);
-    fill_tail(zp, n, nd ? 0u : zp[zaddr(n - 1)]);
-  }
-  const uint32_t cost_i = price_row(zi, n, ci, st);
-  const uint32_t cost_p = price_row(zp, n, cp, st);
-  if (lane_id() == 0) {
-    atomicAdd(p.cost + 2 * gs, cost_i);
-    atomicAdd(p.cost + 2 * gs + 1, cost_p);
-  }
+  if (n) fill_tail(zb, n, nd ? 0u : zb[zaddr(n - 1)]);
+  const uint32_t cost = price_row(zb, n, pmode ? cp : ci, st);
+  if (lane_id() == 0) atomicAdd(p.cost + 2 * gs + (pmode ? 1u : 0u), cost);
 }
 
 // ----------------------------------------------------------------------------
@@ -1039,7 +1034,7 @@ int encode_rows_launch(const EncParams& p, RowsLaunch* out) {
   return 0;
 }
 
-size_t trial_smem_bytes_host(uint32_t W) { return 2ull * 4u * zbuf_words(W); }
+size_t trial_smem_bytes_host(uint32_t W) { return 4ull * zbuf_words(W); }
 
 int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1055,7 +1050,7 @@ int launch_encode(const EncParams& p, void* stream, void* const* ev) {
     if (ev) record_event(ev[i], st);
   };
   mark(0);
-  if (p.trial_rows) k_trial<<<p.n_sec * p.trial_rows, 32, s_trial, st>>>(p);
+  if (p.trial_rows) k_trial<<<2u * p.n_sec * p.trial_rows, 32, s_trial, st>>>(p);
   mark(1);
   // rows of narrow segments first, with shared memory (and so occupancy) for
   // their own width, then the wider ones: one rows launch per width class
