@@ -126,7 +126,8 @@ class Server:
       footprint(sensor) -> device bytes the sensor needs once admitted
       reserve() -> fixed device bytes of the engine (batch scratch)
       admit(sensor), release(sensor); optional trim(limit_bytes): give back
-        cached memory beyond limit_bytes
+        cached memory beyond limit_bytes, and reusable(sensor): admitting the
+        sensor reuses cached memory (needs none new)
       n_contexts -> number of batch contexts that may be in flight
       max_group -> most scans of one sensor per batch (optional, default 1)
       submit_encode(ctx, [(sensor, [requests])]) ; ready(ctx) -> bool
@@ -161,7 +162,10 @@ class Server:
         if self.used + need > self.budget:
             return False
         trim = getattr(self.be, "trim", None)
-        if trim is not None:  # memory the backend keeps from released sensors counts against the budget
+        reusable = getattr(self.be, "reusable", None)
+        if trim is not None and not (reusable is not None and reusable(self.sensors[sid])):
+            # memory the backend keeps from released sensors counts against the
+            # budget: a sensor that cannot reuse some of it makes room first
             trim(self.budget - self.used - need)
         self.be.admit(self.sensors[sid])
         self.used += need
@@ -420,6 +424,9 @@ class GpuBackend:
         d["plen"] = len(self.pools[sensor.pool])
         self.s[sensor.sid] = d
         return d
+
+    def reusable(self, sensor):
+        return bool(self.free.get(self._key(sensor)))
 
     def release(self, sensor):
         d = self.s.pop(sensor.sid, None)

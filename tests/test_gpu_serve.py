@@ -53,3 +53,37 @@ def test_each_result_is_the_same_alone_and_in_the_mix(realtime, graphs):
                 for k, (b, _) in enumerate(s.attrs):
                     got = be.decoded[(s.sid, seq)][k].numpy().view(NP_DT[b])
                     assert np.array_equal(got, planes[k]), (s.sid, seq, k)
+
+
+def test_results_hold_when_sensors_wait_for_budget_and_reuse_handles():
+    # a budget of about three sensors: sensors wait to be admitted, released
+    # sensors' handles are kept, reused by sensors of the same shape (reset
+    # first) and freed when the budget needs the memory; every frame and
+    # decode must still be the oracle's for that sensor alone
+    rng = np.random.default_rng(23)
+    pools_np = [make_scans(rng, H, W, a, 6) for H, W, a in CLASSES]
+    pools = [[[to_dev(p) for p in sc] for sc in pool] for pool in pools_np]
+    sensors = []
+    for i in range(9):
+        c = i % len(CLASSES)
+        H, W, a = CLASSES[c]
+        sensors.append(Sensor(i, H, W, a, float(rng.uniform(10, 20)), pool=c, pool_offset=int(rng.integers(6))))
+    reqs = poisson_arrivals(sensors, 0.5, 0.3, seed=24)
+    be = GpuBackend(pools, keep=True)
+    budget = 3 * max(be.footprint(s) for s in sensors)
+    st = Server(be, sensors, budget_bytes=budget).run(reqs, realtime=False)
+    assert st.failed == 0 and st.encoded == len(reqs)
+    assert st.deferred > 0 and st.admitted == len(sensors)
+    assert be.cached_bytes + sum(be.footprint(be.s[sid]["sensor"]) for sid in be.s) <= budget
+    for s in sensors:
+        ref = oracle.Codec(s.H, s.W, s.attrs)
+        refd = oracle.Codec(s.H, s.W, s.attrs)
+        mine = sorted(r.seq for r in reqs if r.sensor == s.sid)
+        for seq in mine:
+            want = ref.encode(pools_np[s.pool][(s.pool_offset + seq) % 6])
+            assert be.frames[(s.sid, seq)] == want, (s.sid, seq)
+            planes, _ = refd.decode(want)
+            if (s.sid, seq) in be.decoded:
+                for k, (b, _) in enumerate(s.attrs):
+                    got = be.decoded[(s.sid, seq)][k].numpy().view(NP_DT[b])
+                    assert np.array_equal(got, planes[k]), (s.sid, seq, k)

@@ -187,6 +187,61 @@ def test_backlog_is_coded_in_groups_when_the_device_is_slow():
     assert st1.batches > st.batches
 
 
+class CachingBackend(FakeBackend):
+    """Keeps a released sensor's memory for the next sensor of the same shape
+    (as the GPU backend keeps its handles) and frees it when trimmed."""
+
+    def __init__(self, clock, **kw):
+        super().__init__(clock, **kw)
+        self.cache = {}              # shape -> cached footprints
+        self.cached = 0
+        self.peak_held = 0           # admitted + cached
+        self.reused = self.trimmed = 0
+
+    def _held(self):
+        self.peak_held = max(self.peak_held, self.used + self.cached)
+
+    def admit(self, s):
+        key = (s.H, s.W)
+        if self.cache.get(key):
+            self.cache[key].pop()
+            self.cached -= self.footprint(s)
+            self.reused += 1
+        super().admit(s)
+        self._held()
+
+    def release(self, s):
+        super().release(s)
+        self.cache.setdefault((s.H, s.W), []).append(self.footprint(s))
+        self.cached += self.footprint(s)
+        self._held()
+
+    def reusable(self, s):
+        return bool(self.cache.get((s.H, s.W)))
+
+    def trim(self, limit):
+        for lst in self.cache.values():
+            while lst and self.cached > limit:
+                self.cached -= lst.pop()
+                self.trimmed += 1
+
+
+def test_cached_memory_counts_against_the_budget():
+    # sensors come and go under a budget of three at a time; released memory
+    # is cached for reuse, and the server trims the cache whenever a new
+    # admission would otherwise exceed the budget
+    clock = FakeClock()
+    shapes = [(64, 1024), (32, 1024), (64, 2048)]
+    sensors = [Sensor(i, *shapes[i % 3], [(4, 1)], 15.0) for i in range(12)]
+    reqs = poisson_arrivals(sensors, 1.0, 0.1, seed=12)
+    budget = 2 * 64 * 2048 + 64 * 1024
+    be = CachingBackend(clock)
+    st = Server(be, sensors, budget_bytes=budget, clock=clock, sleep=clock.sleep).run(reqs, realtime=False)
+    assert st.encoded == len(reqs) and st.failed == 0
+    assert be.peak_held <= budget
+    assert be.reused > 0 and be.trimmed > 0 and st.deferred > 0
+
+
 def test_arrivals_are_poisson_at_the_sensor_rates():
     sensors = [Sensor(i, 16, 1024, [(4, 1)], r) for i, r in enumerate([10.0, 20.0])]
     reqs = poisson_arrivals(sensors, 200.0, 0.1, seed=8)
