@@ -315,6 +315,25 @@ jiffy_status jiffy_decode_frame_noalloc(const void* in, size_t in_len, uint32_t 
                                         const jiffy_attr_desc* attrs, uint32_t scan_index, uint32_t stages,
                                         const void* const* prev_planes, void* const* planes_out, void* cuda_stream);
 
+/* Checkpoint / resume. A stream's whole state is its previous scan as
+ * decoded (q * P, the P predictor of the next frame, Sec. III-D) and its
+ * frame counter; I frames need none of it. jiffy_stream_save_state writes it
+ * to host memory host_buf (jiffy_stream_state_size(s) bytes: a header with
+ * "JFYS", version 1, H, W, the attribute count, stage switches, frame counter
+ * and each attribute's sample bytes and precision, then the previous scan's
+ * planes), waiting for the copy; jiffy_stream_load_state restores such a
+ * state into a stream of the same H, W, attributes and stage switches (either
+ * role: encoders and decoders hold the same state), whose next frame then
+ * continues the saved stream, P frames included. Errors: a null handle or
+ * buffer, or a state of another configuration -> JIFFY_ERR_INVALID_ARG; too
+ * small a buffer -> JIFFY_ERR_CAPACITY; a stream with an unfinished call or
+ * enqueue-only calls not yet waited for -> JIFFY_ERR_STATE; a buffer that is
+ * not a saved state of that size -> JIFFY_ERR_CORRUPT. The state of a stream
+ * that has coded no frame since create/reset loads as such (next frame I). */
+size_t jiffy_stream_state_size(const jiffy_stream* s);
+jiffy_status jiffy_stream_save_state(jiffy_stream* s, void* host_buf, size_t capacity);
+jiffy_status jiffy_stream_load_state(jiffy_stream* s, const void* host_buf, size_t len);
+
 /* Copies src's previous scan and frame counter into dst (same H, W,
  * attributes and stage switches, same device, any roles), so that dst continues src's stream.
  * Encoders and decoders hold the same state, the previous scan as decoded

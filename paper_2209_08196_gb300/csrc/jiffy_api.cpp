@@ -1108,6 +1108,63 @@ jiffy_status jiffy_stream_copy_state(jiffy_stream* dst, const jiffy_stream* src,
   return JIFFY_OK;
 }
 
+// Saved state: "JFYS", version 1, H, W, A, stages, frame counter (u32 each),
+// then (bytes per sample, precision) per attribute, then the state planes as
+// they lie in the state buffer.
+namespace {
+constexpr uint32_t kStateMagic = 0x5359464Au;  // "JFYS"
+size_t state_header_bytes(uint32_t A) { return 28ull + 8ull * A; }
+void put32(uint8_t* b, size_t at, uint32_t v) { std::memcpy(b + at, &v, 4); }
+uint32_t get32(const uint8_t* b, size_t at) {
+  uint32_t v;
+  std::memcpy(&v, b + at, 4);
+  return v;
+}
+}  // namespace
+
+size_t jiffy_stream_state_size(const jiffy_stream* s) {
+  return s ? state_header_bytes(s->A) + s->state_bytes : 0;
+}
+
+jiffy_status jiffy_stream_save_state(jiffy_stream* s, void* host_buf, size_t capacity) {
+  if (!s || !host_buf) return JIFFY_ERR_INVALID_ARG;
+  if (capacity < jiffy_stream_state_size(s)) return JIFFY_ERR_CAPACITY;
+  if (s->in_flight || s->async_out) return JIFFY_ERR_STATE;
+  DeviceGuard g(s->ws.device);
+  if (!g.ok) return JIFFY_ERR_CUDA;
+  uint8_t* b = static_cast<uint8_t*>(host_buf);
+  const uint32_t head[7] = {kStateMagic, 1u, s->H, s->W, s->A, s->opt.stages, s->frame};
+  for (uint32_t i = 0; i < 7; i++) put32(b, 4ull * i, head[i]);
+  for (uint32_t a = 0; a < s->A; a++) {
+    put32(b, 28ull + 8ull * a, s->attrs[a].s);
+    put32(b, 32ull + 8ull * a, s->attrs[a].P);
+  }
+  if (cudaMemcpy(b + state_header_bytes(s->A), s->d_state[s->cur], s->state_bytes, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return JIFFY_ERR_CUDA;
+  return JIFFY_OK;
+}
+
+jiffy_status jiffy_stream_load_state(jiffy_stream* s, const void* host_buf, size_t len) {
+  if (!s || !host_buf) return JIFFY_ERR_INVALID_ARG;
+  if (s->in_flight || s->async_out) return JIFFY_ERR_STATE;
+  const uint8_t* b = static_cast<const uint8_t*>(host_buf);
+  if (len < 28 || get32(b, 0) != kStateMagic || get32(b, 4) != 1u) return JIFFY_ERR_CORRUPT;
+  if (get32(b, 8) != s->H || get32(b, 12) != s->W || get32(b, 16) != s->A || get32(b, 20) != s->opt.stages)
+    return JIFFY_ERR_INVALID_ARG;
+  if (len != jiffy_stream_state_size(s)) return JIFFY_ERR_CORRUPT;
+  for (uint32_t a = 0; a < s->A; a++)
+    if (get32(b, 28ull + 8ull * a) != s->attrs[a].s || get32(b, 32ull + 8ull * a) != s->attrs[a].P)
+      return JIFFY_ERR_INVALID_ARG;
+  DeviceGuard g(s->ws.device);
+  if (!g.ok) return JIFFY_ERR_CUDA;
+  if (cudaMemcpy(s->d_state[s->cur], b + state_header_bytes(s->A), s->state_bytes, cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return JIFFY_ERR_CUDA;
+  s->frame = get32(b, 24);
+  return JIFFY_OK;
+}
+
 jiffy_status jiffy_stream_test_withhold_row(jiffy_stream* s, uint32_t row_item) {
   if (!s) return JIFFY_ERR_INVALID_ARG;
   s->withhold = row_item;

@@ -138,6 +138,12 @@ def _lib() -> ctypes.CDLL:
         L.jiffy_batch_info.argtypes = [vp, u64p, u32]
         L.jiffy_stream_copy_state.restype = ctypes.c_int
         L.jiffy_stream_copy_state.argtypes = [vp, vp, vp]
+        L.jiffy_stream_state_size.restype = sz
+        L.jiffy_stream_state_size.argtypes = [vp]
+        L.jiffy_stream_save_state.restype = ctypes.c_int
+        L.jiffy_stream_save_state.argtypes = [vp, vp, sz]
+        L.jiffy_stream_load_state.restype = ctypes.c_int
+        L.jiffy_stream_load_state.argtypes = [vp, vp, sz]
         L.jiffy_stream_device_bytes.restype = sz
         L.jiffy_stream_device_bytes.argtypes = [vp]
         L.jiffy_stream_test_withhold_row.argtypes = [vp, u32]
@@ -470,6 +476,26 @@ def jiffy_stream_copy_state(dst: Handle, src: Handle, stream=None):
     st = _lib().jiffy_stream_copy_state(dst.ptr, src.ptr, _stream_ptr(stream))
     if st != 0:
         raise JiffyError(st, "jiffy_stream_copy_state")
+
+
+def jiffy_stream_save_state(h: Handle) -> bytes:
+    """The stream's state (previous scan as decoded and frame counter) as
+    bytes, for checkpoint / resume."""
+    n = _lib().jiffy_stream_state_size(h.ptr)
+    buf = (ctypes.c_uint8 * n)()
+    st = _lib().jiffy_stream_save_state(h.ptr, buf, n)
+    if st != 0:
+        raise JiffyError(st, "jiffy_stream_save_state")
+    return bytes(buf)
+
+
+def jiffy_stream_load_state(h: Handle, state: bytes):
+    """Restores a state saved by jiffy_stream_save_state into a stream of the
+    same configuration; its next frame continues the saved stream."""
+    buf = (ctypes.c_uint8 * len(state)).from_buffer_copy(state) if state else (ctypes.c_uint8 * 1)()
+    st = _lib().jiffy_stream_load_state(h.ptr, buf, len(state))
+    if st != 0:
+        raise JiffyError(st, "jiffy_stream_load_state")
 
 
 def jiffy_stream_test_withhold_row(h: Handle, row_item: int):
