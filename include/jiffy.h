@@ -260,7 +260,12 @@ jiffy_status jiffy_batch_set_graphs(jiffy_batch* b, int enable);
  * log2 of the row count) the batch times the rows kernel under each
  * candidate launch configuration (warps per CTA, resident CTAs per SM, row
  * items per ticket), repeating the call's kernels on the same inputs, and
- * keeps the fastest for later calls of that class. Off by default. */
+ * keeps the fastest for later calls of that class. Off by default.
+ * If the environment variable JIFFY_TUNE_CACHE names a file, enabling loads
+ * the configurations tuned earlier on this kind of device (SM count and
+ * compute capability) from it, and each new tuning rewrites it (a text file,
+ * one line per shape class, replaced atomically); an unreadable or foreign
+ * file only means tuning anew. */
 jiffy_status jiffy_batch_set_autotune(jiffy_batch* b, int enable);
 
 /* Fixes the launch configuration of the role's rows kernel for the batch's

@@ -14,11 +14,17 @@
 #include "jiffy.h"
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
+
+#include <unistd.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <string>
 #include <new>
 #include <vector>
 
@@ -133,6 +139,15 @@ struct jiffy_batch {
 };
 
 namespace {
+
+// A named range around a public call, for timeline tools (NVTX: no cost
+// unless a tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
 
 // Rows of at most this many columns fit 6 encoder CTAs of 4 warps per SM;
 // a call that also codes wider rows runs them in a rows launch of their own.
@@ -309,6 +324,73 @@ jiffy_status check_distinct(const std::vector<jiffy_stream*>& ss) {
     for (size_t k = i + 1; k < ss.size(); k++)
       if (ss[i] == ss[k]) return JIFFY_ERR_INVALID_ARG;  // a stream at most once per call
   return JIFFY_OK;
+}
+
+// Tuned launch configurations kept across processes in the file named by
+// JIFFY_TUNE_CACHE: one line per shape class, "jiffy-tune 1 <device> <n>
+// <n key words> <warps per CTA> <CTAs per SM> <items per ticket>", device =
+// SM count * 1000 + compute capability (lines of another device are ignored;
+// a configuration that does not fit falls back to the automatic one).
+using TuneKey = std::pair<uint32_t, std::vector<uint32_t>>;
+
+const char* tune_cache_path() {
+  const char* p = std::getenv("JIFFY_TUNE_CACHE");
+  return (p && *p) ? p : nullptr;
+}
+
+uint32_t device_tag(int dev) {
+  int sms = 0, maj = 0, mnr = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&mnr, cudaDevAttrComputeCapabilityMinor, dev);
+  return (uint32_t)sms * 1000u + (uint32_t)(maj * 10 + mnr);
+}
+
+std::map<TuneKey, RowsLaunch> tune_cache_read(const char* path) {
+  std::map<TuneKey, RowsLaunch> out;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return out;
+  char tag[16];
+  unsigned ver, dev, n;
+  while (std::fscanf(f, "%15s %u %u %u", tag, &ver, &dev, &n) == 4) {
+    if (std::strcmp(tag, "jiffy-tune") != 0 || ver != 1u || n > 16u) break;
+    std::vector<uint32_t> key(n);
+    bool ok = true;
+    for (uint32_t& x : key) ok = ok && std::fscanf(f, "%u", &x) == 1;
+    unsigned w = 0, c = 0, ipt = 0;
+    ok = ok && std::fscanf(f, "%u %u %u", &w, &c, &ipt) == 3;
+    if (!ok) break;
+    out[TuneKey(dev, key)] = RowsLaunch{w, c, ipt, 0};
+  }
+  std::fclose(f);
+  return out;
+}
+
+void tune_cache_load(Workspace& ws) {
+  const char* path = tune_cache_path();
+  if (!path) return;
+  const uint32_t tag = device_tag(ws.device);
+  for (const auto& kv : tune_cache_read(path))
+    if (kv.first.first == tag) ws.tuned.emplace(kv.first.second, kv.second);
+}
+
+void tune_cache_store(const Workspace& ws) {
+  const char* path = tune_cache_path();
+  if (!path) return;
+  std::map<TuneKey, RowsLaunch> all = tune_cache_read(path);
+  const uint32_t tag = device_tag(ws.device);
+  for (const auto& kv : ws.tuned) all[TuneKey(tag, kv.first)] = kv.second;
+  const std::string tmp = std::string(path) + ".tmp." + std::to_string((long)getpid());
+  FILE* f = std::fopen(tmp.c_str(), "w");
+  if (!f) return;
+  for (const auto& kv : all) {
+    std::fprintf(f, "jiffy-tune 1 %u %u", kv.first.first, (unsigned)kv.first.second.size());
+    for (uint32_t x : kv.first.second) std::fprintf(f, " %u", x);
+    std::fprintf(f, " %u %u %u\n", kv.second.wpc, kv.second.ctas_per_sm, kv.second.items_per_ticket);
+  }
+  const bool ok = std::fclose(f) == 0;
+  if (ok) std::rename(tmp.c_str(), path);
+  else std::remove(tmp.c_str());
 }
 
 uint32_t log2_ceil(uint64_t x) {
@@ -659,6 +741,7 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
                enqueue, &best);
       if (r != JIFFY_OK) return r;
       it = ws.tuned.emplace(sig, best).first;
+      tune_cache_store(ws);
     }
     p.wpc = it->second.wpc;
     p.ctas_per_sm = it->second.ctas_per_sm;
@@ -869,6 +952,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
                enqueue, &best);
       if (r != JIFFY_OK) return r;
       it = ws.tuned.emplace(sig, best).first;
+      tune_cache_store(ws);
     }
     p.wpc = it->second.wpc;
     p.ctas_per_sm = it->second.ctas_per_sm;
@@ -1183,6 +1267,7 @@ uint32_t jiffy_stream_kernel_times(const jiffy_stream* s, float* ms, uint32_t n)
 }
 
 jiffy_status jiffy_stream_wait(jiffy_stream* s) {
+  TraceRange trace("jiffy_stream_wait");
   if (!s) return JIFFY_ERR_INVALID_ARG;
   if (!s->async_out) return JIFFY_OK;
   DeviceGuard g(s->ws.device);
@@ -1206,6 +1291,7 @@ jiffy_status jiffy_stream_wait(jiffy_stream* s) {
 
 jiffy_status jiffy_encode_seq_async(jiffy_stream* s, uint32_t n_scans, const void* const* planes, void* out,
                                     size_t out_capacity, uint64_t* frame_offsets_dev, void* cuda_stream) {
+  TraceRange trace("jiffy_encode_seq_async");
   if (!s) return JIFFY_ERR_INVALID_ARG;
   DeviceGuard g(s->ws.device);
   if (!g.ok) return JIFFY_ERR_CUDA;
@@ -1219,6 +1305,7 @@ jiffy_status jiffy_encode_seq_async(jiffy_stream* s, uint32_t n_scans, const voi
 
 jiffy_status jiffy_decode_seq_async(jiffy_stream* s, uint32_t n_scans, const void* in, size_t in_capacity,
                                     const uint64_t* frame_offsets_dev, void* const* planes_out, void* cuda_stream) {
+  TraceRange trace("jiffy_decode_seq_async");
   if (!s) return JIFFY_ERR_INVALID_ARG;
   DeviceGuard g(s->ws.device);
   if (!g.ok) return JIFFY_ERR_CUDA;
@@ -1231,6 +1318,7 @@ jiffy_status jiffy_decode_seq_async(jiffy_stream* s, uint32_t n_scans, const voi
 
 jiffy_status jiffy_encode_seq(jiffy_stream* s, uint32_t n_scans, const void* const* planes, void* out,
                               size_t out_capacity, uint64_t* frame_offsets, size_t* out_len, void* cuda_stream) {
+  TraceRange trace("jiffy_encode_seq");
   if (!s) return JIFFY_ERR_INVALID_ARG;
   DeviceGuard g(s->ws.device);
   if (!g.ok) return JIFFY_ERR_CUDA;
@@ -1245,11 +1333,13 @@ jiffy_status jiffy_encode_seq(jiffy_stream* s, uint32_t n_scans, const void* con
 
 jiffy_status jiffy_encode(jiffy_stream* s, const void* const* planes, void* out, size_t out_capacity,
                           size_t* out_len, void* cuda_stream) {
+  TraceRange trace("jiffy_encode");
   return jiffy_encode_seq(s, 1, planes, out, out_capacity, nullptr, out_len, cuda_stream);
 }
 
 jiffy_status jiffy_decode_seq(jiffy_stream* s, uint32_t n_scans, const void* in, size_t in_len,
                               const uint64_t* frame_offsets, void* const* planes_out, void* cuda_stream) {
+  TraceRange trace("jiffy_decode_seq");
   if (!s) return JIFFY_ERR_INVALID_ARG;
   DeviceGuard g(s->ws.device);
   if (!g.ok) return JIFFY_ERR_CUDA;
@@ -1264,6 +1354,7 @@ jiffy_status jiffy_decode_seq(jiffy_stream* s, uint32_t n_scans, const void* in,
 
 jiffy_status jiffy_decode(jiffy_stream* s, const void* in, size_t in_len, void* const* planes_out,
                           void* cuda_stream) {
+  TraceRange trace("jiffy_decode");
   if (!s) return JIFFY_ERR_INVALID_ARG;
   const uint64_t off[2] = {s->frame == 0 ? stream_header_bytes(s->A) : 0u, in_len};
   return jiffy_decode_seq(s, 1, in, in_len, off, planes_out, cuda_stream);
@@ -1316,6 +1407,11 @@ jiffy_status jiffy_batch_set_graphs(jiffy_batch* b, int enable) {
 jiffy_status jiffy_batch_set_autotune(jiffy_batch* b, int enable) {
   if (!b) return JIFFY_ERR_INVALID_ARG;
   b->ws.autotune = enable != 0;
+  if (b->ws.autotune) {  // configurations an earlier process tuned on this kind of device
+    DeviceGuard g(b->ws.device);
+    if (!g.ok) return JIFFY_ERR_CUDA;
+    tune_cache_load(b->ws);
+  }
   return JIFFY_OK;
 }
 
@@ -1341,6 +1437,7 @@ jiffy_status jiffy_encode_batch_async(jiffy_batch* b, uint32_t n, jiffy_stream* 
                                       const uint32_t* n_scans, const void* const* const* planes, void* const* outs,
                                       const size_t* caps, uint64_t* const* frame_offsets, size_t* out_lens,
                                       jiffy_status* statuses, void* cuda_stream) {
+  TraceRange trace("jiffy_encode_batch_async");
   if (!b || n == 0 || !streams || !n_scans || !planes || !outs || !caps || !out_lens || !statuses)
     return JIFFY_ERR_INVALID_ARG;
   DeviceGuard g(b->ws.device);
@@ -1356,6 +1453,7 @@ jiffy_status jiffy_decode_batch_async(jiffy_batch* b, uint32_t n, jiffy_stream* 
                                       const uint32_t* n_frames, const void* const* ins, const size_t* in_lens,
                                       const uint64_t* const* frame_offsets, void* const* const* planes_out,
                                       jiffy_status* statuses, void* cuda_stream) {
+  TraceRange trace("jiffy_decode_batch_async");
   if (!b || n == 0 || !streams || !n_frames || !ins || !in_lens || !frame_offsets || !planes_out || !statuses)
     return JIFFY_ERR_INVALID_ARG;
   DeviceGuard g(b->ws.device);
@@ -1367,6 +1465,7 @@ jiffy_status jiffy_decode_batch_async(jiffy_batch* b, uint32_t n, jiffy_stream* 
 }
 
 jiffy_status jiffy_batch_wait(jiffy_batch* b) {
+  TraceRange trace("jiffy_batch_wait");
   if (!b) return JIFFY_ERR_INVALID_ARG;
   DeviceGuard g(b->ws.device);
   if (!g.ok) return JIFFY_ERR_CUDA;
@@ -1377,6 +1476,7 @@ jiffy_status jiffy_encode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const*
                                 const void* const* const* planes, void* const* outs, const size_t* caps,
                                 uint64_t* const* frame_offsets, size_t* out_lens, jiffy_status* statuses,
                                 void* cuda_stream) {
+  TraceRange trace("jiffy_encode_batch");
   const jiffy_status r = jiffy_encode_batch_async(b, n, streams, n_scans, planes, outs, caps, frame_offsets,
                                                   out_lens, statuses, cuda_stream);
   return r != JIFFY_OK ? r : jiffy_batch_wait(b);
@@ -1385,6 +1485,7 @@ jiffy_status jiffy_encode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const*
 jiffy_status jiffy_decode_batch(jiffy_batch* b, uint32_t n, jiffy_stream* const* streams, const uint32_t* n_frames,
                                 const void* const* ins, const size_t* in_lens, const uint64_t* const* frame_offsets,
                                 void* const* const* planes_out, jiffy_status* statuses, void* cuda_stream) {
+  TraceRange trace("jiffy_decode_batch");
   const jiffy_status r = jiffy_decode_batch_async(b, n, streams, n_frames, ins, in_lens, frame_offsets, planes_out,
                                                   statuses, cuda_stream);
   return r != JIFFY_OK ? r : jiffy_batch_wait(b);

@@ -364,6 +364,36 @@ def test_array_marshalled_calls_match_oracle_over_calls():
                     assert np.array_equal(to_np(planes_out[i][t * len(a) + k], s), want[k]), (i, t, k)
 
 
+def test_tune_cache_keeps_tuned_launches_for_the_next_batch(tmp_path, monkeypatch):
+    # JIFFY_TUNE_CACHE: the first batch tunes its shape classes and writes
+    # them out; a batch created afterwards loads them and tunes nothing,
+    # coding the same bytes
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("JIFFY_TUNE_CACHE", str(path))
+    rng = np.random.default_rng(18)
+    scans = [make_scans(rng, H, W, a, 2) for H, W, a in SENSORS]
+    first = Fleet(SENSORS)
+    J.jiffy_batch_set_autotune(first.b, True)
+    got1 = first.encode(scans)
+    assert J.jiffy_batch_info(first.b)["tunings"] >= 1
+    lines = path.read_text().splitlines()
+    assert lines and all(ln.startswith("jiffy-tune 1 ") for ln in lines)
+    second = Fleet(SENSORS)
+    J.jiffy_batch_set_autotune(second.b, True)
+    got2 = second.encode(scans)
+    info = J.jiffy_batch_info(second.b)
+    assert info["tunings"] == 0 and info["tuned_classes"] >= 1
+    assert [b for b, _ in got2] == [b for b, _ in got1]
+    for i, ((H, W, a), sc) in enumerate(zip(SENSORS, scans)):
+        assert got1[i][0] == b"".join(first.ref[i].encode(x) for x in sc)
+    # a damaged file only means tuning anew
+    path.write_text("jiffy-tune 1 garbage\n")
+    third = Fleet(SENSORS)
+    J.jiffy_batch_set_autotune(third.b, True)
+    assert [b for b, _ in third.encode(scans)] == [b for b, _ in got1]
+    assert J.jiffy_batch_info(third.b)["tunings"] >= 1
+
+
 def test_many_stream_workload_sampled_against_oracle():
     # the many-stream configuration (uneven shapes from 16x1024 to 128x4096,
     # attribute sets {range}, {range, signal}, all five; 8 scans each) in one
