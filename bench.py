@@ -862,6 +862,11 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if world > 1:
+        # replicas: the scaling figure is the main step's; the other legs
+        # measure single-GPU properties and run in the one-GPU invocation
+        for leg in ("small", "sweep", "batched", "serve", "heuristic", "ablation", "standardize", "mask_codec"):
+            setattr(args, "no_" + leg, True)
 
     import torch
     import torch.distributed as dist
