@@ -533,19 +533,16 @@ def serve_leg(J, torch, dev, local, seconds, sat_seconds, n_sensors=512, base_se
             serve.poisson_arrivals(sensors, sat_seconds, 0.1, seed=base_seed + 3), realtime=False).summary()
         if graphs:
             del be
-    # real time on the faster backend kind
-    use_graphs = sat[True]["gpoints_s"] > sat[False]["gpoints_s"]
-    if use_graphs:
-        be = serve.GpuBackend(pools, device=local, graphs=True, max_batch_px=max_px)
-        serve.Server(be, sensors, budget_bytes=40e9).run(
-            serve.poisson_arrivals(sensors, 0.5, 0.1, seed=base_seed + 1), realtime=False)
+    # real time without graphs: every batch is a new composition, so a graph
+    # would be captured for it and never replayed, which costs latency
+    use_graphs = False
     rt = serve.Server(be, sensors, budget_bytes=40e9).run(
         serve.poisson_arrivals(sensors, seconds, 0.1, seed=base_seed + 2), realtime=True).summary()
     return {"workload": "%d sensors, Poisson 10-20 Hz, %g s real time, 10%% decode requests, 40 GB budget"
                         % (n_sensors, seconds),
             "p50_ms": rt["p50_ms"], "p99_ms": rt["p99_ms"], "decode_p50_ms": rt["decode_p50_ms"],
             "decode_p99_ms": rt["decode_p99_ms"], "gpoints_s": rt["gpoints_s"], "graphs": use_graphs,
-            "realtime": rt, "saturated": sat[use_graphs],
+            "realtime": rt, "saturated": max(sat.values(), key=lambda x: x["gpoints_s"]),
             "saturated_graphs_on_gpoints_s": sat[True]["gpoints_s"],
             "saturated_graphs_off_gpoints_s": sat[False]["gpoints_s"],
             "max_group": be.max_group, "autotune": False, "gen_s": t_gen}

@@ -257,10 +257,13 @@ class Server:
                 self.stats.decoded_points += s.H * s.W
                 self.stats.dec_latency_ms.append((now - r.t_arrival) * 1e3)
 
-    def run(self, requests, realtime=True, poll_sleep_s=0.0002):
+    def run(self, requests, realtime=True, poll_sleep_s=0.0):
         """Serves the requests (sorted by arrival). realtime: a request
         becomes available at its arrival time on the wall clock; otherwise
-        all are available at once (saturation). Returns the statistics."""
+        all are available at once (saturation). poll_sleep_s: pause when a
+        pass made no progress while work is on the device (0: poll without
+        pausing, the lowest latency; the loop then keeps one host core
+        busy). Returns the statistics."""
         pending = list(requests)
         pending.reverse()
         for r in pending:
