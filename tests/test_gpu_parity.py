@@ -289,6 +289,42 @@ def test_full_size_multi_attribute_sequence_sampled_against_oracle():
             assert host[:offs[1]] == want
 
 
+@pytest.mark.parametrize("force", [-1, 1])
+def test_full_width_parked_scene_with_p_frames_against_oracle(force):
+    """The parked scene (sensor at rest, 90 % of the dropouts on fixed pixels,
+    10 mm range noise) at full width, through the enqueue-only calls: the P
+    path (Sec. III-D: temporal residuals, mask XOR) at the benchmark's row
+    width. With the trial, the second-return range is coded P in every frame
+    after the first; forced, every attribute is. Whole stream compared with
+    the oracle's, every frame decoded exactly."""
+    cfg = synth.config_multi_attr(n_scans=8)
+    cfg.speed_mps = 0.0
+    cfg.persistent_dropout = 0.9
+    cfg.range_noise_mm = 10.0
+    seq = synth.ScanSequence(cfg, device="cuda")
+    attrs = synth.attr_descs(cfg)
+    T, H, W = cfg.n_scans, cfg.H, cfg.W
+    scans = [seq.scan(t, as_numpy=False) for t in range(T)]
+    host = [[p.cpu().numpy().view(DT[s]) for p, (s, _) in zip(sc, attrs)] for sc in scans]
+    want, _, modes = oracle.encode_sequence(H, W, attrs, host, force_mode=force)
+    assert all(modes[t][1] == 1 for t in range(1, T))
+    want_planes, _ = oracle.decode_sequence(H, W, attrs, want, T)
+    enc = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, attrs, force_mode=force)
+    dec = J.jiffy_stream_create(J.JIFFY_DECODER, H, W, attrs, force_mode=force)
+    planes = [torch.stack([scans[t][a] for t in range(T)]) for a in range(len(attrs))]
+    out = torch.empty(J.jiffy_max_encoded_size(H, W, attrs, T), dtype=torch.uint8, device="cuda")
+    d_offs = torch.zeros(T + 1, dtype=torch.int64, device="cuda")
+    outs = J.empty_planes(dec, T)
+    J.jiffy_encode_seq_async(enc, planes, out, d_offs)
+    J.jiffy_decode_seq_async(dec, out, d_offs, outs)
+    J.jiffy_stream_wait(enc)
+    J.jiffy_stream_wait(dec)
+    assert out[:int(d_offs[-1])].cpu().numpy().tobytes() == want
+    for t in range(T):
+        for a, (s, _) in enumerate(attrs):
+            assert np.array_equal(outs[a][t].cpu().numpy().view(DT[s]), want_planes[t][a]), (t, a)
+
+
 @pytest.mark.parametrize("stages", range(1, 8))
 @pytest.mark.parametrize("force", [-1, 0, 1])
 def test_ablated_codecs_match_oracle(stages, force):
