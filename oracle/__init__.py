@@ -22,6 +22,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "jiffy_oracle.c")
 _SRC_STD = os.path.join(_HERE, "jiffy_std_oracle.c")
+_SRC_ZSTD = os.path.join(_HERE, "jiffy_zstd_oracle.c")
 _LIB = os.path.join(_HERE, "libjiffy_oracle.so")
 
 ERR_CAPACITY = 2
@@ -31,17 +32,19 @@ ERR_CORRUPT = 3
 NO_MASK = 1
 NO_DELTA = 2
 NO_ZIGZAG = 4
+# not an ablation: the mask coded the paper's way, one Zstandard frame per section (Sec. III-C)
+ZSTD_MASK = 8
 
 _DT = {1: np.uint8, 2: np.uint16, 4: np.uint32}
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain C99, no target-specific flags)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_STD))
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_STD), os.path.getmtime(_SRC_ZSTD))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp,
-                               _SRC, _SRC_STD, "-lm"])
+                               _SRC, _SRC_STD, _SRC_ZSTD, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -81,6 +84,14 @@ def lib() -> ctypes.CDLL:
         L.jo_trial_cost.argtypes = [u32, u32, u32, u32, u32, vp, vp, ctypes.c_int]
         L.jo_section_split.restype = u64
         L.jo_section_split.argtypes = [u32, u32, u32, u32, vp, vp, ctypes.c_int, vp, vp]
+        L.jz_frame_bound.restype = sz
+        L.jz_frame_bound.argtypes = [sz]
+        L.jz_block_count.restype = sz
+        L.jz_block_count.argtypes = [sz]
+        L.jz_write_frame.restype = sz
+        L.jz_write_frame.argtypes = [vp, sz, vp, vp]
+        L.jz_read_frame.restype = sz
+        L.jz_read_frame.argtypes = [vp, sz, vp, sz, vp, sz]
         L.js_azimuth.restype = u32
         L.js_azimuth.argtypes = [i64, i64]
         L.js_elevation.restype = i32
@@ -240,6 +251,30 @@ def decode_sequence(H, W, attrs, buf: bytes, n_scans: int, stages: int = 0):
 
 # ---------------------------------------------------------------- standardization (Sec. III-A)
 ANGLE_UNITS = 1 << 32  # binary angle units per turn
+
+
+def zstd_frame(data: bytes):
+    """The oracle's Zstandard frame of data (the mask frames of Sec. III-C):
+    (frame bytes, [end of each block, from the frame's start])."""
+    src = np.frombuffer(bytes(data), dtype=np.uint8).copy()
+    n = len(src)
+    L = lib()
+    out = np.zeros(L.jz_frame_bound(n), dtype=np.uint8)
+    ends = np.zeros(max(1, L.jz_block_count(n)), dtype=np.uint32)
+    k = L.jz_write_frame(_ptr(src), n, _ptr(out), _ptr(ends))
+    return out[:k].tobytes(), [int(e) for e in ends]
+
+
+def zstd_read(frame: bytes, n: int):
+    """The oracle's reader of its own frames: n bytes, or None when the frame
+    is malformed or outside the subset the writer uses."""
+    src = np.frombuffer(bytes(frame), dtype=np.uint8).copy()
+    out = np.zeros(max(1, n), dtype=np.uint8)
+    L = lib()
+    nb = L.jz_block_count(n)
+    ends = np.zeros(nb, dtype=np.uint32)
+    k = L.jz_read_frame(_ptr(src) if len(src) else None, len(src), _ptr(out), n, _ptr(ends), nb)
+    return out[:n].tobytes() if k and k == len(src) else None
 
 
 def azimuth(X: int, Y: int) -> int:

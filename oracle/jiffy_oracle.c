@@ -50,8 +50,22 @@
 
 enum { JO_OK = 0, JO_ERR_INVALID_ARG = 1, JO_ERR_CAPACITY = 2, JO_ERR_CORRUPT = 3 };
 
-/* Stage switches of a stream (Table IV ablations); 0 = the full codec. */
-enum { JO_NO_MASK = 1, JO_NO_DELTA = 2, JO_NO_ZIGZAG = 4 };
+/* Stage switches of a stream (Table IV ablations); 0 = the full codec.
+ * JO_ZSTD_MASK is not an ablation: it codes the mask the paper's way, one
+ * Zstandard frame per section (Sec. III-C), instead of per-row class words. */
+enum { JO_NO_MASK = 1, JO_NO_DELTA = 2, JO_NO_ZIGZAG = 4, JO_ZSTD_MASK = 8 };
+
+/* the Zstandard writer and reader (jiffy_zstd_oracle.c) */
+size_t jz_frame_bound(size_t n);
+size_t jz_block_count(size_t n);
+size_t jz_write_frame(const uint8_t* src, size_t n, uint8_t* dst, uint32_t* ends);
+size_t jz_read_frame(const uint8_t* src, size_t len, uint8_t* dst, size_t n, uint32_t* ends, size_t max_blocks);
+
+/* stage-flag byte of the stream header: bit 0 no mask, bit 1 no delta,
+ * bit 2 Zstandard mask */
+static uint8_t header_flags(uint32_t stages) {
+  return (uint8_t)((stages & (JO_NO_MASK | JO_NO_DELTA)) | ((stages & JO_ZSTD_MASK) ? 4u : 0u));
+}
 
 /* ------------------------------------------------------------------ */
 /* small helpers                                                       */
@@ -334,6 +348,16 @@ static uint64_t trial_cost(uint32_t H, uint32_t W, const uint32_t* q, const uint
 /*   Mask words: bit x%32 of word x/32 is 1 where sample x of the row is */
 /*   zero; bits past W are 0. The coded word is the mask word (I) or     */
 /*   the mask word XOR the previous scan's (P).                          */
+/* With the Zstandard mask (JO_ZSTD_MASK) the rows carry no mask part;   */
+/* the mask of the whole section follows the row table instead:         */
+/*     u32 frame bytes F                                                 */
+/*     u32 end of each of the frame's B = ceil(H ceil(W/8) / 8192) blocks, */
+/*       in bytes from the frame's start                                */
+/*     the Zstandard frame of the section's mask bytes: row r's bits,   */
+/*       LSB first, in bytes r*ceil(W/8) .. (r+1)*ceil(W/8)-1 (padding   */
+/*       bits 0), XORed with the previous scan's for P                  */
+/*     zero bytes up to a multiple of 4                                  */
+/*   and the row ends count from the first row chunk after it.          */
 /* ------------------------------------------------------------------ */
 
 static uint32_t valid_bits(uint32_t W, uint32_t j) {
@@ -348,7 +372,30 @@ static size_t section_bound(uint32_t H, uint32_t W) {
    * of m values has no exceptions and needs at most 4*m bytes, and the
    * chosen b never needs more than that */
   size_t row = 4u * ceil_div(nw, 16u) + 4u * nw + 4u * ceil_div(W, 128u) + (size_t)W * 4u;
-  return (size_t)H * 8u + (size_t)H * row;
+  size_t zm = (size_t)H * ((W + 7u) / 8u);
+  return (size_t)H * 8u + (size_t)H * row + 8u + 4u * jz_block_count(zm) + jz_frame_bound(zm);
+}
+
+/* Zstandard mask part of a section (layout above); returns its bytes */
+static size_t write_zstd_mask(uint32_t H, uint32_t W, const uint8_t* M, const uint32_t* pq, int mode, uint8_t* out) {
+  size_t rb = (W + 7u) / 8u, n = (size_t)H * rb;
+  uint8_t* bytes = (uint8_t*)calloc(n, 1);
+  for (uint32_t r = 0; r < H; r++) {
+    for (uint32_t x = 0; x < W; x++) {
+      size_t i = (size_t)r * W + x;
+      uint32_t bit = M[i];
+      if (mode == 1) bit ^= (pq[i] == 0); /* Sec. III-D */
+      bytes[(size_t)r * rb + x / 8u] |= (uint8_t)(bit << (x % 8u));
+    }
+  }
+  size_t nblk = jz_block_count(n);
+  uint32_t* ends = (uint32_t*)malloc(sizeof(uint32_t) * nblk);
+  uint8_t* f = out + 4u + 4u * nblk;
+  size_t fb = jz_write_frame(bytes, n, f, ends);
+  put_u32(out, (uint32_t)fb);
+  for (size_t j = 0; j < nblk; j++) put_u32(out + 4u + 4u * j, ends[j]);
+  free(bytes); free(ends);
+  return (4u + 4u * nblk + fb + 3u) & ~(size_t)3u; /* the caller's buffer is zeroed: pad bytes are 0 */
 }
 
 /* Encodes one section into out (zeroed by the caller, at least
@@ -357,7 +404,7 @@ static size_t section_bound(uint32_t H, uint32_t W) {
 static size_t encode_section(uint32_t H, uint32_t W, const uint32_t* q, const uint32_t* pq, int mode,
                              uint32_t stages, uint8_t* out, uint32_t* nnz_out, uint64_t* mask_bytes,
                              uint64_t* data_bytes) {
-  uint32_t nw = (stages & JO_NO_MASK) ? 0u : ceil_div(W, 32u); /* mask words per row */
+  uint32_t nw = (stages & (JO_NO_MASK | JO_ZSTD_MASK)) ? 0u : ceil_div(W, 32u); /* class-coded mask words per row */
   size_t HW = (size_t)H * W;
   /* zero bitmask, one entry per sample (Sec. III-C): 1 = zero sample */
   uint8_t* M = (uint8_t*)malloc(HW ? HW : 1);
@@ -374,8 +421,13 @@ static size_t encode_section(uint32_t H, uint32_t W, const uint32_t* q, const ui
 
   uint8_t* table = out;
   uint8_t* data = out + (size_t)H * 8u;
-  size_t pos = 0;
+  size_t pos = 0, zpart = 0;
   uint64_t mbytes = 0, dbytes = 0;
+  if (stages & JO_ZSTD_MASK) {
+    zpart = write_zstd_mask(H, W, M, pq, mode, data);
+    data += zpart;
+    mbytes += zpart;
+  }
   for (uint32_t r = 0; r < H; r++) {
     /* mask part */
     uint32_t ncls = ceil_div(nw, 16u);
@@ -423,18 +475,36 @@ static size_t encode_section(uint32_t H, uint32_t W, const uint32_t* q, const ui
   if (nnz_out) *nnz_out = nnz;
   if (mask_bytes) *mask_bytes = mbytes;
   if (data_bytes) *data_bytes = dbytes;
-  return (size_t)H * 8u + pos;
+  return (size_t)H * 8u + zpart + pos;
 }
 
 /* Decodes one section into q_out. Returns 0 or JO_ERR_CORRUPT. */
 static int decode_section(uint32_t H, uint32_t W, const uint8_t* sec, size_t len, int mode, uint32_t stages,
                           const uint32_t* pq, uint32_t* q_out, uint32_t expect_nnz) {
   uint32_t nw = ceil_div(W, 32u);
-  uint32_t nmw = (stages & JO_NO_MASK) ? 0u : nw; /* coded mask words per row */
+  uint32_t nmw = (stages & (JO_NO_MASK | JO_ZSTD_MASK)) ? 0u : nw; /* class-coded mask words per row */
   if (len < (size_t)H * 8u) return JO_ERR_CORRUPT;
   const uint8_t* table = sec;
   const uint8_t* data = sec + (size_t)H * 8u;
   size_t data_len = len - (size_t)H * 8u;
+  uint8_t* zm = NULL; /* Zstandard mask bytes of the section (the coded, XORed form) */
+  size_t rb = (W + 7u) / 8u;
+  if (stages & JO_ZSTD_MASK) {
+    size_t n = (size_t)H * rb, nblk = jz_block_count(n);
+    if (data_len < 4u + 4u * nblk) return JO_ERR_CORRUPT;
+    size_t fb = get_u32(data), part = (4u + 4u * nblk + fb + 3u) & ~(size_t)3u;
+    if (fb > data_len || part > data_len) return JO_ERR_CORRUPT;
+    zm = (uint8_t*)malloc(n);
+    uint32_t* ends = (uint32_t*)malloc(sizeof(uint32_t) * nblk);
+    size_t got = jz_read_frame(data + 4u + 4u * nblk, fb, zm, n, ends, nblk);
+    int bad = got != fb;
+    for (size_t j = 0; j < nblk && !bad; j++) bad = ends[j] != get_u32(data + 4u + 4u * j);
+    for (size_t i = 4u + 4u * nblk + fb; i < part && !bad; i++) bad = data[i] != 0;
+    free(ends);
+    if (bad) { free(zm); return JO_ERR_CORRUPT; }
+    data += part;
+    data_len -= part;
+  }
   uint32_t* z = (uint32_t*)malloc(sizeof(uint32_t) * (W + 128u));
   uint32_t* word = (uint32_t*)malloc(sizeof(uint32_t) * (nw ? nw : 1));
   size_t begin = 0;
@@ -451,9 +521,21 @@ static int decode_section(uint32_t H, uint32_t W, const uint8_t* sec, size_t len
     if (4u * ncls > clen) { rc = JO_ERR_CORRUPT; break; }
     p = 4u * ncls;
     uint32_t n = 0;
-    if (nmw == 0) { /* no mask stage: every sample was coded */
+    if (nmw == 0 && !zm) { /* no mask stage: every sample was coded */
       for (uint32_t j = 0; j < nw; j++) word[j] = 0;
       n = W;
+    }
+    if (zm) { /* the row's bits from the section's Zstandard mask */
+      for (uint32_t j = 0; j < nw; j++) word[j] = 0;
+      for (uint32_t x = 0; x < W; x++) {
+        uint32_t bit = (zm[(size_t)r * rb + x / 8u] >> (x % 8u)) & 1u;
+        if (mode == 1) bit ^= (pq[(size_t)r * W + x] == 0); /* undo the XOR with the previous mask */
+        word[x / 32u] |= bit << (x % 32u);
+        n += bit == 0;
+      }
+      for (uint32_t x = W; x < 8u * (uint32_t)rb; x++)
+        if ((zm[(size_t)r * rb + x / 8u] >> (x % 8u)) & 1u) rc = JO_ERR_CORRUPT; /* padding bits are 0 */
+      if (rc != JO_OK) break;
     }
     for (uint32_t j = 0; j < nmw && rc == JO_OK; j++) {
       uint32_t c = (get_u32(chunk + 4u * (j / 16u)) >> (2u * (j % 16u))) & 3u;
@@ -504,7 +586,7 @@ static int decode_section(uint32_t H, uint32_t W, const uint8_t* sec, size_t len
     begin = end;
   }
   if (rc == JO_OK && (begin != data_len || total != expect_nnz)) rc = JO_ERR_CORRUPT;
-  free(z); free(word);
+  free(z); free(word); free(zm);
   return rc;
 }
 
@@ -513,8 +595,9 @@ static int decode_section(uint32_t H, uint32_t W, const uint8_t* sec, size_t len
 /*   stream header (first frame after create/reset), 16 + 8A bytes:     */
 /*     "JFY1", u16 version = 1, u16 A, u32 H, u32 W,                     */
 /*     per attribute: u8 dtype_bytes, u8 zigzag variant (1 = Eq. 1,      */
-/*     0 = none), u8 stage flags (bit 0: no zero mask, bit 1: no delta), */
-/*     u8 0, u32 precision (Sec. III-A: the precision is stored)         */
+/*     0 = none), u8 stage flags (bit 0: no zero mask, bit 1: no delta, */
+/*     bit 2: Zstandard mask), u8 0, u32 precision (Sec. III-A: the      */
+/*     precision is stored)                                             */
 /*   frame, header 8 + 12A bytes:                                       */
 /*     u32 frame_bytes (header included), u32 scan_index,               */
 /*     per attribute: u8 mode (0 = I, 1 = P), 3 bytes 0,                 */
@@ -534,7 +617,8 @@ typedef struct {
 
 jo_codec* jo_create(uint32_t H, uint32_t W, uint32_t A, const uint8_t* dtypes, const uint32_t* precs,
                     uint32_t test_lines, int32_t force_mode, uint32_t stages) {
-  if (H == 0 || W == 0 || A == 0 || A > JO_MAX_ATTR || test_lines == 0 || stages > 7u) return NULL;
+  if (H == 0 || W == 0 || A == 0 || A > JO_MAX_ATTR || test_lines == 0 || stages > 15u) return NULL;
+  if ((stages & JO_NO_MASK) && (stages & JO_ZSTD_MASK)) return NULL; /* no mask to code */
   for (uint32_t a = 0; a < A; a++) {
     if (!(dtypes[a] == 1 || dtypes[a] == 2 || dtypes[a] == 4) || precs[a] == 0) return NULL;
   }
@@ -574,7 +658,7 @@ int64_t jo_encode(jo_codec* c, const void* const* planes, uint8_t* out, size_t c
       uint8_t* p = buf + 16 + 8 * a;
       p[0] = c->dtype[a];
       p[1] = (c->stages & JO_NO_ZIGZAG) ? 0 : 1;
-      p[2] = (uint8_t)(c->stages & (JO_NO_MASK | JO_NO_DELTA));
+      p[2] = header_flags(c->stages);
       p[3] = 0;
       put_u32(p + 4, c->prec[a]);
     }
@@ -629,7 +713,7 @@ int64_t jo_decode(jo_codec* c, const uint8_t* in, size_t len, void* const* plane
     for (uint32_t a = 0; a < c->A; a++) {
       const uint8_t* p = in + 16 + 8 * a;
       if (p[0] != c->dtype[a] || p[1] != ((c->stages & JO_NO_ZIGZAG) ? 0 : 1) ||
-          p[2] != (c->stages & (JO_NO_MASK | JO_NO_DELTA)) || p[3] != 0 || get_u32(p + 4) != c->prec[a])
+          p[2] != header_flags(c->stages) || p[3] != 0 || get_u32(p + 4) != c->prec[a])
         return -JO_ERR_CORRUPT;
     }
     pos = stream_header_bytes(c->A);

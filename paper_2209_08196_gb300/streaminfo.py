@@ -3,19 +3,41 @@
 Walks the stream's structures (stream header, frame headers, per-attribute
 sections with their row tables and row chunks) and reports, per section, the
 mode (I or P, Sec. III-C / III-D) and how its bytes split into the row table,
-the zero-mask part (class words and literal mask words), the packing blocks'
-headers and their bodies. This is a reader of the byte layout, for reports
-and analysis (for instance the size of the mask part against another mask
-coder); it decodes no values and checks only what it needs to walk.
+the zero-mask part (class words and literal mask words, or the section's
+Zstandard frame), the packing blocks' headers and their bodies. This is a
+reader of the byte layout, for reports and analysis (for instance the size of
+the mask part against another mask coder); it decodes no values and checks
+only what it needs to walk. Streams with the Zstandard mask are read with the
+host's libzstd (through ctypes), which must then be installed.
 """
 from __future__ import annotations
 
+import ctypes
+import ctypes.util
 from dataclasses import dataclass
 
 import numpy as np
 
 MAGIC = 0x3159464A  # "JFY1"
 STAGE_NO_MASK = 1
+FLAG_ZSTD_MASK = 4   # stage-flag bit of the stream header: the mask is one Zstandard frame per section
+ZSTD_BLOCK = 8192    # mask bytes per block of that frame
+
+
+def _zstd_decompress(frame: bytes, n: int) -> np.ndarray:
+    path = ctypes.util.find_library("zstd")
+    if path is None:
+        raise RuntimeError("reading a stream with the Zstandard mask needs libzstd")
+    z = ctypes.CDLL(path)
+    sz, vp = ctypes.c_size_t, ctypes.c_void_p
+    z.ZSTD_decompress.restype, z.ZSTD_decompress.argtypes = sz, [vp, sz, vp, sz]
+    z.ZSTD_isError.restype, z.ZSTD_isError.argtypes = ctypes.c_uint, [sz]
+    src = np.frombuffer(frame, dtype=np.uint8).copy()
+    out = np.zeros(max(n, 1), dtype=np.uint8)
+    k = z.ZSTD_decompress(out.ctypes.data, out.nbytes, src.ctypes.data, len(src))
+    if z.ZSTD_isError(k) or k != n:
+        raise ValueError("a mask frame does not decompress to the section's mask")
+    return out[:n]
 
 
 @dataclass
@@ -59,6 +81,8 @@ def sections(buf: bytes, n_frames: int | None = None) -> tuple[dict, list[Sectio
     nw = (W + 31) // 32
     last_valid = (1 << (W % 32)) - 1 if W % 32 else 0xFFFFFFFF
     prev = [np.zeros((H, nw), dtype=np.uint32) for _ in range(A)]  # each attribute's last zero masks
+    prev_bits = [np.zeros((H, W), dtype=bool) for _ in range(A)]     # the same, with the Zstandard mask
+    rb = (W + 7) // 8
     at = 16 + 8 * A
     out = []
     t = 0
@@ -71,12 +95,31 @@ def sections(buf: bytes, n_frames: int | None = None) -> tuple[dict, list[Sectio
             sbytes = int(w[fw + 3 + 3 * a])
             nnz = int(w[fw + 4 + 3 * a])
             no_mask = head["stages"][a] & STAGE_NO_MASK
-            ncls = 0 if no_mask else (nw + 15) // 16
+            zmask = head["stages"][a] & FLAG_ZSTD_MASK
+            ncls = 0 if (no_mask or zmask) else (nw + 15) // 16
             ends = w[sec // 4:sec // 4 + 2 * H:2].astype(np.int64)
             starts = np.concatenate([[0], ends[:-1]])
             data = sec + 8 * H
             mask_b = head_b = coded = 0
             masks = prev[a]
+            if zmask:  # u32 frame bytes, u32 block ends, the frame, padding
+                nblk = max(1, -(-(H * rb) // ZSTD_BLOCK))
+                fb = int(w[data // 4])
+                f0 = data + 4 + 4 * nblk
+                part = (4 + 4 * nblk + fb + 3) & ~3
+                packed = _zstd_decompress(buf[f0:f0 + fb], H * rb).reshape(H, rb)
+                bits = np.unpackbits(packed, axis=1, bitorder="little")[:, :W].astype(bool)
+                if mode == 1:
+                    bits ^= prev_bits[a]
+                prev_bits[a] = bits
+                n_rows = W - bits.sum(axis=1)
+                mask_b = part
+                head_b = int(sum(4 * ((int(n) + 127) // 128) for n in n_rows))
+                coded = int(n_rows.sum())
+                chunks = int(ends[-1]) if H else 0
+                out.append(SectionInfo(t, a, mode, nnz, sbytes, 8 * H, mask_b, head_b, chunks - head_b, coded))
+                sec += sbytes
+                continue
             for r in range(H):
                 c0 = (data + int(starts[r])) // 4
                 if no_mask:

@@ -420,5 +420,9 @@ def test_stage_set_is_part_of_the_stream_header():
     buf = oracle.Codec(2, 64, [(2, 1)], stages=3).encode([v])
     with pytest.raises(oracle.OracleError):  # a decoder of the full codec refuses it
         oracle.Codec(2, 64, [(2, 1)]).decode(buf)
-    with pytest.raises(ValueError):
-        oracle.Codec(2, 64, [(2, 1)], stages=8)
+    zbuf = oracle.Codec(2, 64, [(2, 1)], stages=oracle.ZSTD_MASK).encode([v])
+    with pytest.raises(oracle.OracleError):  # and a stream with the Zstandard mask
+        oracle.Codec(2, 64, [(2, 1)]).decode(zbuf)
+    for bad in (16, oracle.ZSTD_MASK | oracle.NO_MASK):
+        with pytest.raises(ValueError):
+            oracle.Codec(2, 64, [(2, 1)], stages=bad)

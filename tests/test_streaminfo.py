@@ -4,6 +4,7 @@ section's mask part, block headers and bodies read off the byte listing) and
 oracle streams, where the coded counts recovered from the zero masks must equal the frame
 headers' nnz."""
 import numpy as np
+import pytest
 
 import oracle
 from paper_2209_08196_gb300 import streaminfo
@@ -69,3 +70,30 @@ def test_oracle_streams_parts_add_up_and_counts_match_nnz():
             assert s.header_bytes >= 4 * ((s.nnz + 127) // 128) and s.body_bytes >= 0
         per = streaminfo.mask_bytes_per_frame(buf)
         assert len(per) == len(scans) and all(m > 0 for m in per)
+
+
+def test_zstd_mask_streams_parts_add_up():
+    # the section's mask as one Zstandard frame (Sec. III-C): the masks read
+    # back from the frames give each row's coded count, and they add up to nnz
+    import ctypes.util
+    if ctypes.util.find_library("zstd") is None:
+        pytest.skip("libzstd is not installed")
+    rng = np.random.default_rng(4)
+    H, W, attrs = 9, 300, [(4, 10), (1, 1)]
+    base = [rng.integers(1, 1 << (8 * s), size=(H, W)).astype(np.int64) for s, _ in attrs]
+    scans = []
+    for t in range(4):
+        planes = []
+        for (s, _), b in zip(attrs, base):
+            x = b.copy()
+            x[rng.random(x.shape) < 0.25] = 0
+            planes.append(x.astype({1: np.uint8, 2: np.uint16, 4: np.uint32}[s]))
+        scans.append(planes)
+    for force in (-1, 0, 1):
+        buf, _, modes = oracle.encode_sequence(H, W, attrs, scans, force_mode=force, stages=oracle.ZSTD_MASK)
+        head, secs = streaminfo.sections(buf)
+        assert head["stages"] == [4, 4]
+        assert [s.mode for s in secs] == [m for mm in modes for m in mm]
+        for s in secs:
+            assert s.coded == s.nnz
+            assert s.bytes == s.table_bytes + s.mask_bytes + s.header_bytes + s.body_bytes
