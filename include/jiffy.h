@@ -43,6 +43,17 @@
  *   sample is coded (frame nnz = H * W), without the delta the residuals are
  *   packed directly (row carries are still recorded), without ZigZag the
  *   32-bit two's complement words are packed.
+ *   With JIFFY_STAGE_ZSTD_MASK the row chunks have no mask part either; the
+ *   section's mask follows its row table as one Zstandard frame (RFC 8878,
+ *   the mask coding of Sec. III-C): u32 frame bytes F, u32 end of each of
+ *   its ceil(H ceil(W/8) / 8192) blocks (from the frame's start), the F
+ *   frame bytes, zero bytes up to a multiple of 4; the row ends count from
+ *   the first chunk after it. The frame holds the coded mask bits (the XOR
+ *   with the previous scan's for P), LSB first, each row in ceil(W/8) bytes
+ *   with zero padding bits; any Zstandard decoder restores it. Its blocks,
+ *   one per 8192 bytes, are RLE, Raw or Compressed (Huffman-coded literals,
+ *   one stream up to 1023 bytes and four above, direct or FSE-coded
+ *   weights, no sequences).
  *
  * Errors: every function returns a jiffy_status; nothing aborts. A failed
  * call leaves the stream's state (previous scan, frame counter) unchanged.
@@ -89,6 +100,11 @@ typedef struct {
 #define JIFFY_STAGE_NO_MASK 1u   /* no zero mask: every sample is coded, zeros too */
 #define JIFFY_STAGE_NO_DELTA 2u  /* residuals packed without the horizontal delta */
 #define JIFFY_STAGE_NO_ZIGZAG 4u /* deltas packed as 32-bit two's complement words */
+/* Not an ablation: the zero mask coded as Sec. III-C describes, packed into
+ * bytes and compressed as one Zstandard frame per section, in place of the
+ * per-row class words (the layout is above). Cannot be combined with
+ * JIFFY_STAGE_NO_MASK. The allocation-free decode does not take it. */
+#define JIFFY_STAGE_ZSTD_MASK 8u
 
 /* test_lines: number of scanlines of the trial compression (Sec. III-E;
  * Sec. IV-E uses 4); rows floor((2k+1)H/(2L)), k < L, >= 1. test_lines >= H
@@ -314,7 +330,8 @@ uint32_t jiffy_stream_kernel_times(const jiffy_stream* s, float* ms, uint32_t n)
  * scratch is a fixed device array in the library, shared by every call (calls
  * that overlap on the GPU race on it). The first call on each device looks up
  * that array's address; make it before any stream capture. Limits: n_attr <=
- * 16, n_attr * H <= 16384, W <= 16384; beyond them JIFFY_ERR_INVALID_ARG.
+ * 16, n_attr * H <= 16384, W <= 16384; beyond them JIFFY_ERR_INVALID_ARG, and
+ * so is JIFFY_STAGE_ZSTD_MASK (its frames need scratch of their own).
  * Synchronizes cuda_stream. */
 jiffy_status jiffy_decode_frame_noalloc(const void* in, size_t in_len, uint32_t H, uint32_t W, uint32_t n_attr,
                                         const jiffy_attr_desc* attrs, uint32_t scan_index, uint32_t stages,

@@ -36,7 +36,9 @@
  *     block is stored Raw if that leaves it below 1;
  *   - FSE initial states: the lowest table position holding the symbol.
  * The reader accepts exactly what the writer can produce (and the parts of
- * the literals-section header any writer may choose) and rejects the rest.
+ * the literals-section header any writer may choose) and rejects the rest;
+ * in particular block j must hold input bytes 8192 j .. 8192 (j+1) - 1, so
+ * that a block-end index lets every block be decoded on its own.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -516,14 +518,16 @@ size_t jz_read_frame(const uint8_t* src, size_t len, uint8_t* dst, size_t n, uin
     if (pos + 3 > len || nb >= max_blocks) return 0;
     uint32_t bh = (uint32_t)get_le(src + pos, 3);
     uint32_t last = bh & 1u, type = (bh >> 1) & 3u, bsize = bh >> 3;
+    size_t want = n - out < JZ_BLOCK ? n - out : JZ_BLOCK; /* this block's share of the input */
+    if (want == 0 || last != (out + want == n)) return 0;
     pos += 3;
     if (type == 0) {
-      if (bsize > JZ_BLOCK || bsize > n - out || bsize > len - pos) return 0;
+      if (bsize != want || bsize > len - pos) return 0;
       memcpy(dst + out, src + pos, bsize);
       out += bsize;
       pos += bsize;
     } else if (type == 1) {
-      if (bsize > JZ_BLOCK || bsize > n - out || pos + 1 > len) return 0;
+      if (bsize != want || pos + 1 > len) return 0;
       memset(dst + out, src[pos], bsize);
       out += bsize;
       pos += 1;
@@ -538,7 +542,7 @@ size_t jz_read_frame(const uint8_t* src, size_t len, uint8_t* dst, size_t n, uin
       uint32_t bits = sf <= 1 ? 10u : (sf == 2 ? 14u : 18u);
       rs = (uint32_t)((h >> 4) & ((1u << bits) - 1u));
       cs = (uint32_t)((h >> (4 + bits)) & ((1u << bits) - 1u));
-      if (rs == 0 || rs > JZ_BLOCK || rs > n - out || (uint64_t)lhdr + cs + 1u != bsize || b[lhdr + cs] != 0) return 0;
+      if (rs != want || (uint64_t)lhdr + cs + 1u != bsize || b[lhdr + cs] != 0) return 0;
       const uint8_t* l = b + lhdr;
       uint8_t weight[256];
       uint32_t maxbits = 0;

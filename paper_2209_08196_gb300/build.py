@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libjiffy_gb300.so")
-SOURCES = ["jiffy_api.cpp", "jiffy_encode.cu", "jiffy_decode.cu", "jiffy_noalloc.cu", "jiffy_standardize.cu"]
+SOURCES = ["jiffy_api.cpp", "jiffy_encode.cu", "jiffy_decode.cu", "jiffy_zstd.cu", "jiffy_noalloc.cu",
+           "jiffy_standardize.cu"]
 GENCODE = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -607,6 +607,22 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     slots_total += (unsigned long long)slot_bytes_for(s->W) * jobs[i].T * s->A * s->H;
   }
   const size_t o_slots = c.take(slots_total);
+  // Zstandard mask sections: coded mask bytes, block slots and sizes
+  std::vector<unsigned long long> zm_base(n), zb_base(n);
+  unsigned long long zm_total = 0, zb_total = 0;
+  uint32_t zmax_blk = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    const jiffy_stream* s = jobs[i].s;
+    if (!(s->opt.stages & jiffy::kStageZstdMask)) continue;
+    const uint32_t nblk = jiffy::zmask_blocks(s->H, s->W);
+    zm_base[i] = zm_total;
+    zb_base[i] = zb_total;
+    zm_total += align_up((size_t)s->H * ((s->W + 7) / 8), 16) * jobs[i].T * s->A;
+    zb_total += (unsigned long long)nblk * jobs[i].T * s->A;
+    zmax_blk = std::max(zmax_blk, nblk);
+  }
+  const size_t o_zm = c.take(zm_total), o_zblk = c.take(zb_total * jiffy::kZSlot);
+  const size_t o_zbb = c.take(4ull * zb_total), o_zfr = c.take(zmax_blk ? 4ull * secs : 0ull);
   const size_t h_res = align_up(up.off, 256);
   jiffy_status r = ensure_scratch(ws, c.off, h_res + rs.off);
   if (r == JIFFY_OK) r = wait_upload(ws);
@@ -661,8 +677,15 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     g.A = A;
     g.T = T;
     g.nw = (s->W + 31) / 32;
-    g.ncls = (s->opt.stages & jiffy::kStageNoMask) ? 0u : (g.nw + 15) / 16;
+    g.ncls = (s->opt.stages & (jiffy::kStageNoMask | jiffy::kStageZstdMask)) ? 0u : (g.nw + 15) / 16;
     g.stages = s->opt.stages;
+    if (s->opt.stages & jiffy::kStageZstdMask) {
+      g.zm_rb = (s->W + 7) / 8;
+      g.zm_nblk = jiffy::zmask_blocks(s->H, s->W);
+      g.zm_stride = align_up((size_t)s->H * g.zm_rb, 16);
+      g.zm_base = zm_base[i];
+      g.zb_base = zb_base[i];
+    }
     g.frame0 = s->frame;
     g.shdr = s->frame == 0 ? stream_header_bytes(A) : 0u;
     g.fhdr = frame_header_bytes(A);
@@ -691,6 +714,7 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     staged |= s->opt.stages ? 1u : 0u;
     key.push_back(((uint64_t)s->H << 32) | s->W);
     key.push_back(((uint64_t)A << 32) | T);
+    key.push_back(s->opt.stages);
   }
   key.push_back(staged);
   key.push_back(withhold);
@@ -721,6 +745,13 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
   p.staged = staged | (withhold ? 1u : 0u);
   p.withhold = withhold;
+  if (zmax_blk) {
+    p.zmask = d + o_zm;
+    p.zblk = d + o_zblk;
+    p.zblk_bytes = reinterpret_cast<uint32_t*>(d + o_zbb);
+    p.zfr_bytes = reinterpret_cast<uint32_t*>(d + o_zfr);
+    p.zmax_blk = zmax_blk;
+  }
   uint8_t* hres = h + h_res;
 
   // the whole call on one stream: upload, clear, kernels, results
@@ -835,7 +866,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   if (items > 0x7fffffffull) return JIFFY_ERR_INVALID_ARG;
 
   Carver up;
-  const size_t u_seg = up.take(sizeof(jiffy::DecSeg) * n), u_ib = up.take(4ull * n);
+  const size_t u_seg = up.take(sizeof(jiffy::DecSeg) * n), u_ib = up.take(4ull * n), u_sb = up.take(4ull * n);
   std::vector<size_t> u_ptrs(n);
   for (uint32_t i = 0; i < n; i++)
     u_ptrs[i] = up.take(8ull * ((size_t)(jobs[i].T + 2) * jobs[i].s->A + jobs[i].T + 1));
@@ -856,6 +887,19 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
     mask_words += (unsigned long long)jobs[i].T * s->A * s->H * ((s->W + 31) / 32);
   }
   const size_t o_masks = c.take(4ull * mask_words);
+  // Zstandard mask sections: their decoded (still XORed) mask bytes
+  std::vector<unsigned long long> zm_base(n);
+  unsigned long long zm_total = 0, n_sec = 0;
+  uint32_t zmax_blk = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    const jiffy_stream* s = jobs[i].s;
+    n_sec += (unsigned long long)jobs[i].T * s->A;
+    if (!(s->opt.stages & jiffy::kStageZstdMask)) continue;
+    zm_base[i] = zm_total;
+    zm_total += align_up((size_t)s->H * ((s->W + 7) / 8), 16) * jobs[i].T * s->A;
+    zmax_blk = std::max(zmax_blk, jiffy::zmask_blocks(s->H, s->W));
+  }
+  const size_t o_zdec = c.take(zm_total);
   const size_t h_res = align_up(up.off, 256);
   jiffy_status r = ensure_scratch(ws, c.off, h_res + rs.off);
   if (r == JIFFY_OK) r = wait_upload(ws);
@@ -865,10 +909,11 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
 
   jiffy::DecSeg* segs = reinterpret_cast<jiffy::DecSeg*>(h + u_seg);
   uint32_t* ib = reinterpret_cast<uint32_t*>(h + u_ib);
+  uint32_t* sbk = reinterpret_cast<uint32_t*>(h + u_sb);
   std::vector<uint64_t> key{2, n, (uint64_t)(uintptr_t)d, (uint64_t)(uintptr_t)h};
   std::vector<uint32_t> sig{2, max_W, log2_ceil(items)};
   uint32_t staged = 0, withhold = 0;
-  uint32_t item_base = 0;
+  uint32_t item_base = 0, sec_base = 0;
   for (uint32_t i = 0; i < n; i++) {
     DecJob& j = jobs[i];
     jiffy_stream* s = j.s;
@@ -887,8 +932,15 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
     g.A = A;
     g.T = T;
     g.nw = (s->W + 31) / 32;
-    g.ncls = (s->opt.stages & jiffy::kStageNoMask) ? 0u : (g.nw + 15) / 16;
+    g.ncls = (s->opt.stages & (jiffy::kStageNoMask | jiffy::kStageZstdMask)) ? 0u : (g.nw + 15) / 16;
     g.stages = s->opt.stages;
+    g.sec_base = sec_base;
+    if (s->opt.stages & jiffy::kStageZstdMask) {
+      g.zm_rb = (s->W + 7) / 8;
+      g.zm_nblk = jiffy::zmask_blocks(s->H, s->W);
+      g.zm_stride = align_up((size_t)s->H * g.zm_rb, 16);
+      g.zm_base = zm_base[i];
+    }
     g.frame0 = s->frame;
     g.fhdr = frame_header_bytes(A);
     g.check_shdr = s->frame == 0;
@@ -905,12 +957,15 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
     g.mask_base = mask_base[i];
     segs[i] = g;
     ib[i] = item_base;
+    sbk[i] = sec_base;
     if (s->withhold < T * A * s->H) withhold = item_base + s->withhold + 1u;
     s->withhold = UINT32_MAX;  // one call
     item_base += T * A * s->H;
+    sec_base += T * A;
     staged |= s->opt.stages ? 1u : 0u;
     key.push_back(((uint64_t)s->H << 32) | s->W);
     key.push_back(((uint64_t)A << 32) | T);
+    key.push_back(s->opt.stages);
   }
   key.push_back(staged);
   sig.push_back(staged);
@@ -932,6 +987,12 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   p.ticket = reinterpret_cast<uint32_t*>(d + o_tick);
   p.staged = staged | (withhold ? 1u : 0u);
   p.withhold = withhold;
+  p.n_sec = (uint32_t)n_sec;
+  p.seg_sec_base = reinterpret_cast<const uint32_t*>(d + o_up + u_sb);
+  if (zmax_blk) {
+    p.zdec = d + o_zdec;
+    p.zmax_blk = zmax_blk;
+  }
   key.push_back(withhold);
   uint8_t* hres = h + h_res;
 
@@ -1088,7 +1149,9 @@ size_t jiffy_max_encoded_size(uint32_t H, uint32_t W, uint32_t n_attr, const jif
                               uint32_t n_scans) {
   (void)attrs;
   if (H == 0 || W == 0 || n_attr == 0) return 0;
-  const size_t section = 8ull * H + (size_t)H * jiffy::row_bound_bytes(W);
+  // (with the Zstandard mask the rows carry no mask words; its index, frame
+  // header, block headers and padding stay within the 16 + 8 per block added)
+  const size_t section = 8ull * H + (size_t)H * jiffy::row_bound_bytes(W) + 16ull + 8ull * jiffy::zmask_blocks(H, W);
   const size_t frame = frame_header_bytes(n_attr) + (size_t)n_attr * section;
   return stream_header_bytes(n_attr) + (size_t)n_scans * frame;
 }
@@ -1104,6 +1167,7 @@ jiffy_status jiffy_stream_create(jiffy_stream** out, jiffy_role role, uint32_t H
   if (opt) o = *opt;
   if (o.test_lines == 0 || o.force_mode < -1 || o.force_mode > 1 || (o.stages & ~jiffy::kStageAll))
     return JIFFY_ERR_INVALID_ARG;
+  if ((o.stages & jiffy::kStageNoMask) && (o.stages & jiffy::kStageZstdMask)) return JIFFY_ERR_INVALID_ARG;
   for (uint32_t a = 0; a < n_attr; a++) {
     const uint32_t sz = attrs[a].dtype_bytes;
     if (!(sz == 1 || sz == 2 || sz == 4) || attrs[a].precision == 0) return JIFFY_ERR_INVALID_ARG;

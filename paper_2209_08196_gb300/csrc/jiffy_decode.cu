@@ -92,6 +92,7 @@ struct SecCache {
   uint32_t mode, bad;           // the section's mode; 1 = malformed frame header
   uint32_t data_len;            // bytes of the section's row chunks
   uint32_t next_p;              // the call's next frame codes this attribute as P (its rows read this frame's masks)
+  uint32_t zpart;               // bytes of the Zstandard mask part after the row table (0 without it)
   unsigned long long sec;       // byte offset of the section (its row table)
 };
 
@@ -155,9 +156,21 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
       const unsigned long long g1 = sg.off[t + 2];
       if (g1 >= f1 + sg.fhdr && g1 <= sg.in_len && !(g1 & 3ull)) sc.next_p = ld_in_u32(sg.in, f1 + 8ull + 12ull * a) == 1u;
     }
+    sc.zpart = 0;
+    if (STAGED && (stages & kStageZstdMask) && !hbad) {  // index + frame + padding before the row chunks
+      const unsigned long long idx = 4ull + 4ull * sg.zm_nblk;
+      if (my_sb - 8ull * H < idx) {
+        hbad = true;
+      } else {
+        const uint32_t F = ld_in_u32(sg.in, f0 + sg.fhdr + sb_before + 8ull * H);
+        const unsigned long long part = (idx + F + 3ull) & ~3ull;
+        if (part > my_sb - 8ull * H) hbad = true;
+        else sc.zpart = (uint32_t)part;
+      }
+    }
     sc.bad = hbad ? 1u : 0u;
     sc.sec = f0 + sg.fhdr + sb_before;
-    sc.data_len = my_sb - 8u * H;
+    sc.data_len = my_sb - 8u * H - sc.zpart;
     sc.key = key;
   }
   const uint32_t mode = sc.mode;
@@ -175,7 +188,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
           end - start > row_bound_bytes(W) || end - start < 4u * ncls)
         bad = true;
       clen = end - start;
-      chunk_off = sec + 8ull * H + start;
+      chunk_off = sec + 8ull * H + sc.zpart + start;
     }
     if (kl == 0 && sg.check_shdr && !bad) {  // stream header: shape, dtypes, precisions
       if (ld_in_u32(sg.in, 0) != 0x3159464Au || ld_in_u32(sg.in, 4) != (1u | (A << 16)) ||
@@ -273,11 +286,18 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
   //      mask stage (no class words) every sample is coded. One warp scan per
   //      32 words gives each word's first compacted index.
   uint32_t n = 0;
+  bool zbad = false;
   if (!bad) {
     const bool xor_prev = mode == 1u && !(stages & kStageNoMask);
     const uint32_t* pmask = (xor_prev && t > 0) ? p.masks + sg.mask_base + (size_t)(kl - H) * nw : nullptr;
     uint32_t* omask = (sc.next_p && !(stages & kStageNoMask)) ? p.masks + sg.mask_base + (size_t)kl * nw : nullptr;
     const bool prev_samples = xor_prev && !pmask;
+    // the row's coded mask bytes from the section's Zstandard frame (decoded
+    // by k_zstd_dec); a bit past W is malformed
+    const uint8_t* zrow = (STAGED && (stages & kStageZstdMask))
+                              ? p.zdec + sg.zm_base + (size_t)ta * sg.zm_stride + (size_t)r * sg.zm_rb
+                              : nullptr;
+    const uint32_t zrb = sg.zm_rb;
     if (prev_samples) {  // the previous scan's zero bits, 8 pixels per lane per step, into mw
       uint8_t* pb = reinterpret_cast<uint8_t*>(mw);
       for (uint32_t it = 0; it < niter; it++) {
@@ -310,6 +330,17 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
           else if (prev_samples) X ^= mw[j];  // bits past W are cleared below
           X &= valid;
           if (omask) omask[j] = X;
+        } else if (zrow) {
+          if ((zrb & 3u) == 0u) {
+            X = __ldcg(reinterpret_cast<const uint32_t*>(zrow) + j);
+          } else {
+            for (uint32_t q = 0; q < 4u && 4u * j + q < zrb; q++) X |= (uint32_t)__ldcg(zrow + 4u * j + q) << (8u * q);
+          }
+          zbad |= (X & ~valid) != 0u;
+          if (pmask) X ^= __ldcg(pmask + j);
+          else if (prev_samples) X ^= mw[j];
+          X &= valid;
+          if (omask) omask[j] = X;
         }
         mw[j] = X;
         kept = __popc(~X & valid);
@@ -320,6 +351,7 @@ __device__ __forceinline__ void decode_item(const DecParams& p, const uint32_t k
       n += tot;
     }
   }
+  bad = bad || __any_sync(0xffffffffu, zbad);
   __syncwarp();
   const uint32_t nb = ceil_div_u32(n, kBlockN);
 
@@ -558,6 +590,8 @@ int launch_decode(const DecParams& p0, void* stream, void* const* ev) {
   p.items_per_ticket = rl.items_per_ticket;
   const size_t smem = (size_t)rl.wpc * dec_warp_layout(p.max_W).bytes;
   if (ev) record_event(ev[0], st);
+  rc = launch_zstd_decode(p, st);
+  if (rc != 0) return rc;
   if (p.staged) {
     if (rl.wpc == 8) k_decode<8, true><<<rl.grid, 8 * 32, smem, st>>>(p);
     else if (rl.wpc == 4) k_decode<4, true><<<rl.grid, 4 * 32, smem, st>>>(p);

@@ -773,6 +773,16 @@ __device__ __forceinline__ void encode_item(const EncParams& p, const uint32_t k
   const uint32_t n = pass_a(cur, prv, at, W, kz, w.zb, w.mb, qhi);
   if (t + 1 == sg.T) state_row(cur, sg.state_next[a] + r * rowb, at, W);
   __syncwarp();
+  if (STAGED && (st & kStageZstdMask)) {  // the row's coded mask bytes, for the section's Zstandard frame
+    const uint32_t rb = sg.zm_rb;
+    uint8_t* zrow = p.zmask + sg.zm_base + (size_t)ta * sg.zm_stride + (size_t)r * rb;
+    if ((rb & 3u) == 0u) {
+      for (uint32_t i = lane; i < rb / 4u; i += 32u)
+        reinterpret_cast<uint32_t*>(zrow)[i] = reinterpret_cast<const uint32_t*>(w.mb)[i];
+    } else {
+      for (uint32_t i = lane; i < rb; i += 32u) zrow[i] = w.mb[i];
+    }
+  }
   const uint32_t last_e = n ? w.zb[zaddr(n - 1)] : 0u;
   // (the failure-detection test hook, read by the STAGED instance only, may
   // withhold this row's status)
@@ -880,6 +890,12 @@ __device__ __forceinline__ void put_u32_guarded(uint8_t* out, unsigned long long
   else atomicOr(err, kErrCapacity);
 }
 
+__device__ __forceinline__ void put_u8_guarded(uint8_t* out, unsigned long long cap, unsigned long long at, uint32_t v,
+                                               uint32_t* err) {
+  if (at < cap) out[at] = (uint8_t)v;
+  else atomicOr(err, kErrCapacity);
+}
+
 __device__ __forceinline__ unsigned long long cta_sum_u64(unsigned long long v, unsigned long long* s_red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   if (lane_id() == 0) s_red[warp_id()] = v;
@@ -903,8 +919,17 @@ __global__ void __launch_bounds__(kThreads) k_sec_sizes(EncParams p) {
   }
   bytes = cta_sum_u64(bytes, s_red);
   nnz = cta_sum_u64(nnz, s_red);
+  unsigned long long zpart = 0;
+  if (sg.stages & kStageZstdMask) {  // the Zstandard mask part: index, frame, padding
+    const uint32_t nblk = sg.zm_nblk;
+    unsigned long long fb = 0;
+    for (uint32_t j = threadIdx.x; j < nblk; j += kThreads) fb += p.zblk_bytes[sg.zb_base + (size_t)ta * nblk + j];
+    fb = cta_sum_u64(fb, s_red) + kZFrameHdr;
+    zpart = zmask_part_bytes(nblk, (uint32_t)fb);
+    if (threadIdx.x == 0) p.zfr_bytes[gs] = (uint32_t)fb;
+  }
   if (threadIdx.x == 0) {
-    p.sec_bytes[gs] = 8ull * H + bytes;
+    p.sec_bytes[gs] = 8ull * H + zpart + bytes;
     p.sec_nnz[gs] = (uint32_t)nnz;
   }
 }
@@ -934,6 +959,41 @@ __global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
   attr_before = cta_sum_u64(attr_before, s_red);
   const unsigned long long frame_at = sg.shdr + (unsigned long long)t * sg.fhdr + frame_before;
   const unsigned long long sec_at = frame_at + sg.fhdr + attr_before;
+  // the Zstandard mask part after the row table: u32 frame bytes, u32 end of
+  // each block, the frame (header, then the blocks from their slots), zero
+  // bytes up to a multiple of 4
+  uint32_t zpart = 0;
+  if (sg.stages & kStageZstdMask) {
+    const uint32_t nblk = sg.zm_nblk, fb = p.zfr_bytes[gs];
+    const size_t b0 = sg.zb_base + (size_t)ta * nblk;
+    uint32_t* bstart = smem + kMaxH;
+    zpart = zmask_part_bytes(nblk, fb);
+    for (uint32_t j = threadIdx.x; j < nblk; j += kThreads) bstart[j] = p.zblk_bytes[b0 + j];
+    __syncthreads();
+    block_excl_scan(bstart, nblk, s_tmp);
+    const unsigned long long zp = sec_at + 8ull * H, fz = zp + 4ull + 4ull * nblk;
+    if (part == 0) {
+      for (uint32_t j = threadIdx.x; j < nblk; j += kThreads)
+        put_u32_guarded(out, cap, zp + 4ull + 4ull * j, kZFrameHdr + bstart[j] + p.zblk_bytes[b0 + j], sg.err);
+      if (threadIdx.x == 0) {
+        put_u32_guarded(out, cap, zp, fb, sg.err);
+        const uint32_t hdr[9] = {0x28, 0xB5, 0x2F, 0xFD, 0xA0, 0, 0, 0, 0};
+        const uint32_t n = sg.H * sg.zm_rb;
+        for (uint32_t i = 0; i < 9; i++) put_u8_guarded(out, cap, fz + i, i < 5 ? hdr[i] : (n >> (8 * (i - 5))) & 0xffu, sg.err);
+        for (unsigned long long i = fz + fb; i < zp + zpart; i++) put_u8_guarded(out, cap, i, 0u, sg.err);
+      }
+    }
+    for (uint32_t j = part; j < nblk; j += kPlaceSplit) {
+      const uint32_t nb = p.zblk_bytes[b0 + j];
+      const unsigned long long at = fz + kZFrameHdr + bstart[j];
+      const uint8_t* src = p.zblk + (b0 + j) * (size_t)kZSlot;
+      if (at + nb > cap) {
+        if (threadIdx.x == 0) atomicOr(sg.err, kErrCapacity);
+        continue;
+      }
+      for (uint32_t i = threadIdx.x; i < nb; i += kThreads) out[at + i] = src[i];
+    }
+  }
   // row table: end offsets (prefix of chunk sizes) and carries
   for (uint32_t r = threadIdx.x; r < H; r += kThreads) smem[r] = p.row_bytes[item0 + r];
   __syncthreads();
@@ -946,7 +1006,7 @@ __global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
     }
   }
   // row chunks: a warp per row, slot -> stream, 4 words in flight per lane
-  const unsigned long long data_at = sec_at + 8ull * H;
+  const unsigned long long data_at = sec_at + 8ull * H + zpart;
   const uint32_t lane = lane_id();
   for (uint32_t r = part * kWarps + warp_id(); r < H; r += kWarps * kPlaceSplit) {
     const uint32_t words = p.row_bytes[item0 + r] / 4u;
@@ -1042,7 +1102,7 @@ int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   RowsLaunch rl{};
   int rc = encode_rows_launch(p, &rl);
   if (rc != 0) return rc;
-  const size_t s_place = 4ull * kMaxH;
+  const size_t s_place = 4ull * kMaxH + 4ull * zmask_blocks(kMaxH, kMaxW);  // row starts, block starts
   cudaError_t e = cudaFuncSetAttribute(k_trial, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_trial);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_place, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_place);
   if (e != cudaSuccess) return (int)e;
@@ -1081,6 +1141,8 @@ int launch_encode(const EncParams& p, void* stream, void* const* ev) {
   }
   if (e != cudaSuccess) return (int)e;  // the placement kernels would read row sizes never written
   mark(2);
+  rc = launch_zstd_encode(p, st);
+  if (rc != 0) return rc;
   k_sec_sizes<<<p.n_sec, kThreads, 0, st>>>(p);
   k_place<<<p.n_sec * kPlaceSplit, kThreads, s_place, st>>>(p);
   mark(3);

@@ -36,6 +36,12 @@ struct EncSeg {
   unsigned long long cap;
   unsigned long long* frame_off; // [T+1]
   uint32_t* err;                 // the segment's error word
+  // Zstandard mask (stages & kStageZstdMask): each section's coded mask
+  // bytes (rows of zm_rb = ceil(W/8) bytes) at zm_base + section * zm_stride
+  // in EncParams::zmask, its zm_nblk blocks in slots zb_base + section *
+  // zm_nblk + j of EncParams::zblk
+  uint32_t zm_rb, zm_nblk;
+  unsigned long long zm_base, zm_stride, zb_base;
 };
 
 struct EncParams {
@@ -66,6 +72,12 @@ struct EncParams {
   // rows of at most split_W columns, then [split, n_items) from ticket[1]
   uint32_t item_lo;
   uint32_t split, split_W;
+  // Zstandard mask sections (null when no segment codes its mask that way)
+  uint8_t* zmask;                // coded mask bytes of the sections
+  uint8_t* zblk;                 // block slots, kZSlot bytes each
+  uint32_t* zblk_bytes;          // [blocks] bytes of each block (header included)
+  uint32_t* zfr_bytes;           // [n_sec] frame bytes of each section
+  uint32_t zmax_blk;             // most blocks of a section
 };
 
 struct DecSeg {
@@ -85,6 +97,9 @@ struct DecSeg {
   uint8_t* const* state_next;    // [A] receives the last frame's planes
   uint32_t* err;                 // the segment's error word
   unsigned long long mask_base;  // word offset of the segment's first row in DecParams::masks
+  uint32_t sec_base;             // first global section (scan t, attribute a) of the segment
+  uint32_t zm_rb, zm_nblk;       // Zstandard mask: bytes per row, blocks per section
+  unsigned long long zm_base, zm_stride;  // its decoded mask bytes in DecParams::zdec
 };
 
 struct DecParams {
@@ -101,6 +116,11 @@ struct DecParams {
   uint32_t items_per_ticket;     // row items a warp takes per ticket (0 = 4)
   uint32_t staged;               // as in EncParams
   uint32_t withhold;             // test hook: 1 + the row item that does not publish its done flag (0: none)
+  // Zstandard mask sections (null when no segment codes its mask that way)
+  uint32_t n_sec;                // sections of all segments
+  const uint32_t* seg_sec_base;  // [n_seg] (search key for sections)
+  uint8_t* zdec;                 // decoded (still XORed) mask bytes of the sections
+  uint32_t zmax_blk;             // most blocks of a section
 };
 
 // Launch configuration of a rows kernel as resolved for given parameters
@@ -121,5 +141,11 @@ int decode_rows_launch(const DecParams& p, RowsLaunch* out);
 // decode: 2).
 int launch_encode(const EncParams& p, void* stream, void* const* ev);
 int launch_decode(const DecParams& p, void* stream, void* const* ev);
+
+// Zstandard mask kernels (jiffy_zstd.cu): the writer of every block of the
+// Zstandard sections (after the rows kernel, before the placement kernels)
+// and the reader of them (before the rows kernel of a decode).
+int launch_zstd_encode(const EncParams& p, void* stream);
+int launch_zstd_decode(const DecParams& p, void* stream);
 
 }  // namespace jiffy

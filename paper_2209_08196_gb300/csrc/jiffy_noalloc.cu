@@ -84,7 +84,7 @@ extern "C" jiffy_status jiffy_decode_frame_noalloc(const void* in, size_t in_len
                                                    void* cuda_stream) {
   using namespace jiffy;
   if (!in || !attrs || !planes_out || H == 0 || W == 0 || n_attr == 0) return JIFFY_ERR_INVALID_ARG;
-  if (stages & ~kStageAll) return JIFFY_ERR_INVALID_ARG;
+  if ((stages & ~kStageAll) || (stages & kStageZstdMask)) return JIFFY_ERR_INVALID_ARG;  // no scratch for the frames
   if (H > kMaxH || W > kMaxW || n_attr > kNoAllocMaxAttr || (uint64_t)n_attr * H > kNoAllocMaxRows)
     return JIFFY_ERR_INVALID_ARG;
   if (reinterpret_cast<uintptr_t>(in) & 3u) return JIFFY_ERR_INVALID_ARG;

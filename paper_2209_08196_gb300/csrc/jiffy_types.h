@@ -19,14 +19,35 @@ constexpr uint32_t kMaxH = 4096;       // rows
 constexpr uint32_t kMaxAttr = 64;
 constexpr uint32_t kBlockN = 128;      // values per packing block (Sec. II frames of 128)
 
-// Stage switches of a stream: each removes one step of the codec, for the
-// ablated codecs of Sec. IV-H (Table IV). 0 = the full codec.
-enum : uint32_t { kStageNoMask = 1u, kStageNoDelta = 2u, kStageNoZigzag = 4u, kStageAll = 7u };
+// Stage switches of a stream: the first three each remove one step of the
+// codec, for the ablated codecs of Sec. IV-H (Table IV); kStageZstdMask codes
+// the zero mask the way Sec. III-C does, one Zstandard frame per section,
+// instead of the per-row class words. 0 = the full codec with class words.
+enum : uint32_t { kStageNoMask = 1u, kStageNoDelta = 2u, kStageNoZigzag = 4u, kStageZstdMask = 8u, kStageAll = 15u };
 
 // First word of an attribute's stream-header entry: dtype bytes, ZigZag
-// variant (1 = Eq. 1, 0 = none), stage flags (no mask | no delta), 0.
+// variant (1 = Eq. 1, 0 = none), stage flags (bit 0 no mask, bit 1 no delta,
+// bit 2 Zstandard mask), 0.
 JIFFY_HD inline uint32_t attr_header_word(uint32_t s, uint32_t stages) {
-  return s | (((stages & kStageNoZigzag) ? 0u : 1u) << 8) | ((stages & (kStageNoMask | kStageNoDelta)) << 16);
+  const uint32_t flags = (stages & (kStageNoMask | kStageNoDelta)) | ((stages & kStageZstdMask) ? 4u : 0u);
+  return s | (((stages & kStageNoZigzag) ? 0u : 1u) << 8) | (flags << 16);
+}
+
+// Zstandard mask (RFC 8878 frames): mask bytes per block, bytes of the frame
+// header (magic, descriptor, 4-byte content size), bytes of a block's slot in
+// the encoder's scratch (the largest block, Raw, is 3 + kZBlock bytes).
+constexpr uint32_t kZBlock = 8192;
+constexpr uint32_t kZFrameHdr = 9;
+constexpr uint32_t kZSlot = kZBlock + 16;
+
+// Zstandard mask part of a section: u32 frame bytes, u32 end of each block,
+// the frame, zero bytes up to a multiple of 4.
+JIFFY_HD inline uint32_t zmask_blocks(uint32_t H, uint32_t W) {
+  const uint32_t n = H * ((W + 7u) / 8u);
+  return n ? (n + kZBlock - 1u) / kZBlock : 1u;
+}
+JIFFY_HD inline uint32_t zmask_part_bytes(uint32_t nblk, uint32_t frame_bytes) {
+  return (4u + 4u * nblk + frame_bytes + 3u) & ~3u;
 }
 
 // bits of the device error word

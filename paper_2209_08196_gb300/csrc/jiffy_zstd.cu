@@ -1,0 +1,677 @@
+// Zstandard mask kernels (sm_103a). Sec. III-C packs the zero bitmask into
+// bytes and compresses it with Zstd; for a P scan (Sec. III-D) the mask is
+// the XOR with the previous scan's first. A stream with kStageZstdMask codes
+// each section's mask that way: the rows' coded mask bits, LSB first, rows of
+// ceil(W/8) bytes, as one Zstandard frame (RFC 8878) that any Zstandard
+// decoder restores. The part of the format written here:
+//   frame header: magic, descriptor 0xA0 (single segment, 4-byte content
+//     size), the content size; one block per 8192 mask bytes, each
+//     RLE         when its bytes are all equal,
+//     Compressed  a Huffman-coded literals section and no sequences, when
+//                 that is smaller than the input,
+//     Raw         otherwise;
+//   Huffman code lengths: the two-queue construction over the present byte
+//     values sorted by (count, value), a tie taking the leaf; while a code is
+//     longer than 11 bits every count c becomes ceil(c/2) and the
+//     construction is repeated;
+//   tree description: 4-bit weights when at most 128 weights are listed,
+//     else FSE-compressed weights (accuracy log 6, two interleaved states,
+//     normalised counts max(1, floor(64 c / N)) with the rest on the most
+//     frequent weight value, the smaller one among ties; initial states at the
+//     lowest table position of their symbol); a block whose weights fit
+//     neither form is Raw;
+//   one Huffman stream for blocks of at most 1023 bytes, four above.
+// Beside the frame the section keeps the end of every block, so that each
+// block is located, and decoded, on its own.
+//
+// k_zstd_enc: one CTA per (section, block), after the rows kernel has stored
+//   the section's coded mask bytes. The block is staged in shared memory;
+//   histogram; code lengths and the tree description on thread 0 (at most
+//   256 symbols and 255 weights); then every thread codes 32 consecutive
+//   literals: their bit positions from a CTA-wide scan of the code lengths,
+//   their codes ORed into the block image in shared memory. The image goes to
+//   the block's slot; the placement kernel assembles the frame.
+// k_zstd_dec: one warp per (section, block), before the rows kernel. Checks
+//   the block-end index, the frame and block headers, stages a Compressed
+//   block in shared memory, reads the tree (lane 0), builds the decoding
+//   table and decodes the streams (one lane per stream) into the section's
+//   mask bytes; the rows kernel reads its rows from there. Anything that is
+//   not what the writer can produce sets the segment's CORRUPT flag.
+#include "jiffy_device.cuh"
+#include "jiffy_kernels.h"
+
+namespace jiffy {
+
+namespace {
+
+constexpr uint32_t kZT = 256;       // threads of a writer CTA (= kThreads: block_excl_scan)
+constexpr uint32_t kZMaxBits = 11;  // longest Huffman code (RFC 8878)
+constexpr uint32_t kZFseLog = 6;    // accuracy log of the weights' FSE table
+constexpr uint32_t kZTree = 136;    // tree description buffer (a description is at most 128 bytes)
+static_assert(kZT == (uint32_t)kThreads, "block_excl_scan runs on kThreads threads");
+
+__device__ __forceinline__ uint32_t hibit(uint32_t x) { return 31u - __clz(x); }
+
+__device__ __forceinline__ uint32_t sec_segment(const uint32_t* base, uint32_t n, uint32_t key) {
+  uint32_t lo = 0, hi = n;  // base[lo] <= key < base[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (__ldg(base + mid) <= key) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ----------------------------------------------------------------------------
+// FSE decoding table of a normalised distribution (RFC 8878 4.1.1): symbols
+// spread with step 64/2 + 64/8 + 3; position u holding symbol s gets the next
+// of s's counters x (from norm[s]), nb = 6 - highbit(x), base = (x << nb) - 64.
+// ----------------------------------------------------------------------------
+struct FseTable {
+  uint8_t sym[64], nb[64];
+  uint16_t base[64];
+};
+
+__device__ void fse_table(const uint32_t* norm, uint32_t nsym, FseTable& t) {
+  uint32_t pos = 0;
+  for (uint32_t s = 0; s < nsym; s++) {
+    for (uint32_t i = 0; i < norm[s]; i++) {
+      t.sym[pos] = (uint8_t)s;
+      pos = (pos + 43u) & 63u;
+    }
+  }
+  uint32_t next[16];
+  for (uint32_t s = 0; s < 16; s++) next[s] = s < nsym ? norm[s] : 0u;
+  for (uint32_t u = 0; u < 64; u++) {
+    const uint32_t x = next[t.sym[u]]++;
+    t.nb[u] = (uint8_t)(kZFseLog - hibit(x));
+    t.base[u] = (uint16_t)((x << t.nb[u]) - 64u);
+  }
+}
+
+// Bit writer into a byte buffer (bits LSB first), writes past cap dropped.
+struct BitPut {
+  uint8_t* buf;
+  uint32_t cap, bits;
+  __device__ void put(uint32_t v, uint32_t n) {
+    for (uint32_t i = 0; i < n; i++, bits++)
+      if ((v >> i) & 1u && (bits >> 3) < cap) buf[bits >> 3] |= (uint8_t)(1u << (bits & 7u));
+  }
+};
+
+// ----------------------------------------------------------------------------
+// Writer
+// ----------------------------------------------------------------------------
+struct ZEnc {
+  uint8_t in[kZBlock];
+  uint32_t img[kZSlot / 4];       // the block being assembled (header first)
+  uint32_t hist[kZT / 32][256];   // per-warp histograms
+  uint32_t cnt[256], len[256], code[256];
+  uint32_t wnode[511];            // Huffman node weights: leaves (sorted), then internal nodes
+  uint16_t parent[511];
+  uint8_t depth[511];
+  uint8_t leaf[256];              // leaf i's symbol
+  uint8_t weight[256];
+  uint8_t tree[kZTree];
+  uint8_t fenc[16][64];           // FSE encoding: (symbol, next state) -> state
+  FseTable ft;
+  uint32_t pre[kZT + kWarps + 1];  // per-thread literal bits -> exclusive prefix; scan scratch
+  uint32_t pb[5];                 // literal bits before each stream boundary
+  uint32_t maxd, last, tree_len;
+};
+
+// FSE-compressed Huffman weights (RFC 8878 4.2.1.2) of weight[0..n) into
+// z.tree (header byte first); returns its bytes or 0 if they cannot be
+// written that way. Thread 0 only.
+__device__ uint32_t fse_weights(ZEnc& z, uint32_t n) {
+  uint32_t hist[16];
+  for (uint32_t v = 0; v < 16; v++) hist[v] = 0;
+  for (uint32_t i = 0; i < n; i++) hist[z.weight[i]]++;
+  uint32_t distinct = 0, nsym = 0, best = 0;
+  for (uint32_t v = 0; v < 16; v++) {
+    if (!hist[v]) continue;
+    distinct++;
+    nsym = v + 1;
+    if (hist[v] > hist[best]) best = v;
+  }
+  if (distinct < 2 || n < 2) return 0;
+  uint32_t norm[16], sum = 0;
+  for (uint32_t v = 0; v < 16; v++) {
+    norm[v] = 0;
+    if (!hist[v]) continue;
+    norm[v] = max(1u, (hist[v] << kZFseLog) / n);
+    sum += norm[v];
+  }
+  const int rest = (int)norm[best] + 64 - (int)sum;
+  if (rest < 1) return 0;
+  norm[best] = (uint32_t)rest;
+  fse_table(norm, nsym, z.ft);
+  for (uint32_t u = 0; u < 64; u++) {
+    const uint32_t lo = z.ft.base[u], hi = lo + (1u << z.ft.nb[u]);
+    for (uint32_t v = lo; v < hi && v < 64u; v++) z.fenc[z.ft.sym[u]][v] = (uint8_t)u;
+  }
+  for (uint32_t i = 0; i < kZTree; i++) z.tree[i] = 0;
+  // table description, forward: log - 5, then count + 1 per value with the
+  // variable-size code the reader expects, repeat flags after a zero count
+  BitPut w{z.tree + 1, 127u, 0u};
+  w.put(kZFseLog - 5u, 4u);
+  uint32_t remaining = 65, s = 0;
+  while (remaining > 1 && s < nsym) {
+    const uint32_t v = norm[s] + 1u, nbits = hibit(remaining) + 1u, thr = 1u << (nbits - 1u);
+    const uint32_t lo = 2u * thr - 1u - remaining;
+    if (v < lo) w.put(v, nbits - 1u);
+    else if (v < thr) w.put(v, nbits);
+    else w.put(v + lo, nbits);
+    remaining -= norm[s];
+    s++;
+    if (norm[s - 1] == 0) {
+      uint32_t zr = 0;
+      while (s + zr < nsym && norm[s + zr] == 0) zr++;
+      s += zr;
+      while (zr >= 3) {
+        w.put(3u, 2u);
+        zr -= 3;
+      }
+      w.put(zr, 2u);
+    }
+  }
+  const uint32_t head = (w.bits + 7u) >> 3;
+  if (head >= 127u) return 0;
+  // two states from the last weight back: weight i is emitted by state i%2;
+  // the fields come out in the order they are written
+  BitPut b{z.tree + 1 + head, 127u - head, 0u};
+  uint32_t st[2] = {0, 0};
+  for (int i = (int)n - 1; i >= 0; i--) {
+    const uint32_t q = (uint32_t)i & 1u, sy = z.weight[i];
+    if (i >= (int)n - 2) {
+      uint32_t u = 0;
+      while (z.ft.sym[u] != sy) u++;
+      st[q] = u;
+      continue;
+    }
+    const uint32_t v = st[q], u = z.fenc[sy][v];
+    b.put(v - z.ft.base[u], z.ft.nb[u]);
+    st[q] = u;
+  }
+  b.put(st[1], kZFseLog);
+  b.put(st[0], kZFseLog);
+  b.put(1u, 1u);
+  const uint32_t body = (b.bits + 7u) >> 3;
+  if (head + body >= 128u) return 0;
+  z.tree[0] = (uint8_t)(head + body);
+  return 1u + head + body;
+}
+
+__device__ __forceinline__ void img_put_bytes(uint8_t* img, uint32_t at, unsigned long long v, uint32_t nbytes) {
+  for (uint32_t i = 0; i < nbytes; i++) img[at + i] = (uint8_t)(v >> (8u * i));
+}
+
+__global__ void __launch_bounds__(kZT) k_zstd_enc(EncParams p) {
+  __shared__ ZEnc z;
+  const uint32_t gs = blockIdx.x, j = blockIdx.y, tid = threadIdx.x;
+  const EncSeg& sg = p.seg[sec_segment(p.seg_sec_base, p.n_seg, gs)];
+  if (!(sg.stages & kStageZstdMask) || j >= sg.zm_nblk) return;  // the whole CTA
+  const uint32_t ta = gs - sg.sec_base;
+  const uint32_t n = sg.H * sg.zm_rb, lo = j * kZBlock, m = min(kZBlock, n - lo);
+  const uint8_t* src = p.zmask + sg.zm_base + (size_t)ta * sg.zm_stride + lo;
+  const size_t slot = sg.zb_base + (size_t)ta * sg.zm_nblk + j;
+  uint32_t* dst = reinterpret_cast<uint32_t*>(p.zblk + slot * kZSlot);
+  const uint32_t last_blk = j + 1 == sg.zm_nblk ? 1u : 0u;
+  uint8_t* img = reinterpret_cast<uint8_t*>(z.img);
+
+  // ---- stage the block (16-byte aligned: section strides and block starts
+  //      are multiples of 16), clear the image and the histograms
+  const uint32_t m4 = m >> 2;
+  for (uint32_t i = tid; i < m4; i += kZT) reinterpret_cast<uint32_t*>(z.in)[i] = __ldg(reinterpret_cast<const uint32_t*>(src) + i);
+  for (uint32_t i = 4u * m4 + tid; i < m; i += kZT) z.in[i] = src[i];
+  for (uint32_t i = tid; i < kZSlot / 4; i += kZT) z.img[i] = 0;
+  for (uint32_t i = tid; i < (kZT / 32) * 256; i += kZT) (&z.hist[0][0])[i] = 0;
+  __syncthreads();
+  const uint8_t b0 = z.in[0];
+  int diff = 0;
+  for (uint32_t i = tid; i < m; i += kZT) diff |= z.in[i] != b0;
+  if (!__syncthreads_or(diff)) {  // RLE block: header + the byte
+    if (tid == 0) {
+      dst[0] = last_blk | (1u << 1) | (m << 3) | ((uint32_t)b0 << 24);
+      p.zblk_bytes[slot] = 4;
+    }
+    return;
+  }
+
+  // ---- histogram
+  for (uint32_t i = tid; i < m; i += kZT) atomicAdd(&z.hist[tid >> 5][z.in[i]], 1u);
+  __syncthreads();
+  {
+    uint32_t c = 0;
+    for (uint32_t w = 0; w < kZT / 32; w++) c += z.hist[w][tid];
+    z.cnt[tid] = c;
+  }
+  __syncthreads();
+
+  // ---- code lengths: rank the present symbols by (count, value) in
+  //      parallel, merge on thread 0; halve the counts while too deep
+  for (;;) {
+    const uint32_t c = z.cnt[tid];
+    z.len[tid] = 0;
+    if (c) {
+      uint32_t r = 0;
+      for (uint32_t t2 = 0; t2 < 256; t2++) {
+        const uint32_t c2 = z.cnt[t2];
+        r += (c2 != 0u) && (c2 < c || (c2 == c && t2 < tid));
+      }
+      z.leaf[r] = (uint8_t)tid;
+    }
+    const uint32_t nsym = (uint32_t)__syncthreads_count(c != 0u);
+    if (tid == 0) {
+      for (uint32_t i = 0; i < nsym; i++) z.wnode[i] = z.cnt[z.leaf[i]];
+      uint32_t lf = 0, nd = nsym, next = nsym;
+      for (uint32_t k = 0; k + 1 < nsym; k++) {
+        uint32_t pick[2];
+        for (uint32_t q = 0; q < 2; q++) {
+          if (lf < nsym && (nd >= next || z.wnode[lf] <= z.wnode[nd])) pick[q] = lf++;
+          else pick[q] = nd++;
+        }
+        z.wnode[next] = z.wnode[pick[0]] + z.wnode[pick[1]];
+        z.parent[pick[0]] = z.parent[pick[1]] = (uint16_t)next;
+        next++;
+      }
+      z.depth[next - 1] = 0;
+      for (int i = (int)next - 2; i >= 0; i--) z.depth[i] = (uint8_t)(z.depth[z.parent[i]] + 1u);
+      uint32_t maxd = 0;
+      for (uint32_t i = 0; i < nsym; i++) {
+        z.len[z.leaf[i]] = z.depth[i];
+        maxd = max(maxd, (uint32_t)z.depth[i]);
+      }
+      z.maxd = maxd;
+    }
+    __syncthreads();
+    if (z.maxd <= kZMaxBits) break;
+    z.cnt[tid] = (c + 1u) >> 1;
+    __syncthreads();
+  }
+
+  // ---- weights, canonical codes (symbols by weight then value take
+  //      consecutive ranges of the 2^maxbits decoding entries from entry 0)
+  const uint32_t maxb = z.maxd;
+  const uint32_t L = z.len[tid];
+  const uint32_t wt = L ? maxb + 1u - L : 0u;
+  z.weight[tid] = (uint8_t)wt;
+  __syncthreads();
+  if (wt) {
+    uint32_t pos = 0;
+    for (uint32_t t2 = 0; t2 < 256; t2++) {
+      const uint32_t w2 = z.weight[t2];
+      if (w2 && (w2 < wt || (w2 == wt && t2 < tid))) pos += 1u << (w2 - 1u);
+    }
+    z.code[tid] = pos >> (wt - 1u);
+  }
+  if (tid == 0) {  // tree description: weights of symbols 0 .. last-1
+    uint32_t last = 255;
+    while (!z.weight[last]) last--;
+    z.last = last;
+    uint32_t tl;
+    if (last <= 128u) {
+      for (uint32_t i = 0; i < kZTree; i++) z.tree[i] = 0;
+      z.tree[0] = (uint8_t)(127u + last);
+      for (uint32_t i = 0; i < last; i++) z.tree[1 + i / 2] |= (uint8_t)(z.weight[i] << ((i & 1u) ? 0 : 4));
+      tl = 1u + (last + 1u) / 2u;
+    } else {
+      tl = fse_weights(z, last);
+    }
+    z.tree_len = tl;
+  }
+
+  // ---- literal bit counts: per-thread sums, CTA scan, stream boundaries
+  const bool four = m > 1023u;
+  const uint32_t seg = four ? (m + 3u) / 4u : m, ns = four ? 4u : 1u;
+  const uint32_t i0 = min(32u * tid, m), i1 = min(i0 + 32u, m);
+  uint32_t sum = 0;
+  for (uint32_t i = i0; i < i1; i++) sum += z.len[z.in[i]];
+  z.pre[tid] = sum;
+  __syncthreads();
+  const uint32_t total = block_excl_scan(z.pre, kZT, z.pre + kZT);
+  {
+    uint32_t P = z.pre[tid];
+    for (uint32_t i = i0; i < i1; i++) {
+      if (four && i % seg == 0 && i > 0) z.pb[i / seg] = P;
+      P += z.len[z.in[i]];
+    }
+    if (tid == 0) {
+      z.pb[0] = 0;
+      z.pb[ns] = total;
+    }
+  }
+  __syncthreads();
+  const uint32_t tl = z.tree_len, lhdr = four ? 4u : 3u;
+  uint32_t soff[4], bytes_k[4], cs = tl + (four ? 6u : 0u);
+  bool jump_ok = true;
+  for (uint32_t k = 0; k < ns; k++) {
+    bytes_k[k] = (z.pb[k + 1] - z.pb[k] + 8u) >> 3;  // bits + end mark, whole bytes
+    soff[k] = 3u + lhdr + cs;
+    cs += bytes_k[k];
+    if (k < 3 && bytes_k[k] > 0xFFFFu) jump_ok = false;
+  }
+  const uint32_t content = lhdr + cs + 1u;  // literals section + Number_of_Sequences = 0
+  const bool compressed = tl != 0u && jump_ok && content < m;
+
+  uint32_t blk_bytes;
+  if (compressed) {
+    if (tid == 0) {
+      img_put_bytes(img, 0, last_blk | (2u << 1) | (content << 3), 3);
+      const unsigned long long h = four ? (2ull | (2ull << 2) | ((unsigned long long)m << 4) | ((unsigned long long)cs << 18))
+                                        : (2ull | ((unsigned long long)m << 4) | ((unsigned long long)cs << 14));
+      img_put_bytes(img, 3, h, lhdr);
+      for (uint32_t i = 0; i < tl; i++) img[3 + lhdr + i] = z.tree[i];
+      if (four)
+        for (uint32_t k = 0; k < 3; k++) img_put_bytes(img, 3 + lhdr + tl + 2 * k, bytes_k[k], 2);
+    }
+    __syncthreads();  // header bytes before the streams' bits (they may share words)
+    // each stream is read from its end: literal i of stream k sits after the
+    // codes of the stream's later literals; end mark after the last field
+    uint32_t P = z.pre[tid];
+    for (uint32_t i = i0; i < i1; i++) {
+      const uint32_t s = z.in[i], l = z.len[s], k = four ? min(i / seg, 3u) : 0u;
+      const uint32_t g = 8u * soff[k] + (z.pb[k + 1] - P - l);
+      const uint32_t c = z.code[s], sh = g & 31u;
+      atomicOr(&z.img[g >> 5], c << sh);
+      if (sh + l > 32u) atomicOr(&z.img[(g >> 5) + 1u], c >> (32u - sh));
+      P += l;
+    }
+    if (tid < ns) {
+      const uint32_t g = 8u * soff[tid] + (z.pb[tid + 1] - z.pb[tid]);
+      atomicOr(&z.img[g >> 5], 1u << (g & 31u));
+    }
+    blk_bytes = 3u + content;
+  } else {  // Raw block
+    if (tid == 0) img_put_bytes(img, 0, last_blk | (m << 3), 3);
+    for (uint32_t i = tid; i < m; i += kZT) img[3 + i] = z.in[i];
+    blk_bytes = 3u + m;
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < (blk_bytes + 3u) / 4u; i += kZT) dst[i] = z.img[i];
+  if (tid == 0) p.zblk_bytes[slot] = blk_bytes;
+}
+
+// ----------------------------------------------------------------------------
+// Reader
+// ----------------------------------------------------------------------------
+struct ZDec {
+  uint8_t blk[kZBlock + 64];  // a Compressed block's content, zero slack for the peeks
+  uint16_t dt[1u << kZMaxBits];  // decoding table: symbol | code bits << 8
+  uint8_t weight[256];
+  uint32_t start[256];
+  FseTable ft;
+  uint32_t ok, maxbits, tree_len, sf, cs, lhdr;
+};
+
+__device__ __forceinline__ uint8_t in_byte(const uint8_t* in, unsigned long long at) { return __ldg(in + at); }
+
+// n bits (n <= 11) ending at bit position p (exclusive) of a backward stream
+// in shared memory; bits below position 0 read as zero
+__device__ __forceinline__ uint32_t peek_back(const uint8_t* s, int p, uint32_t n) {
+  const int q = p - (int)n;
+  const int b0 = q >= 0 ? (q >> 3) : -((7 - q) >> 3);
+  const uint32_t sh = (uint32_t)(q - 8 * b0);
+  uint32_t w = 0;
+#pragma unroll
+  for (int k = 0; k < 3; k++) {
+    const int bi = b0 + k;
+    w |= (bi >= 0 ? (uint32_t)s[bi] : 0u) << (8 * k);
+  }
+  return (w >> sh) & ((1u << n) - 1u);
+}
+
+// payload bits of a backward stream (the position of its end mark), or -1
+__device__ __forceinline__ int stream_start(const uint8_t* s, uint32_t len) {
+  if (len == 0 || s[len - 1] == 0) return -1;
+  return (int)(8u * (len - 1u) + hibit(s[len - 1]));
+}
+
+// Huffman tree description at s[0..len) (lane 0): weights of all symbols
+// (the implied last one included) into z.weight, z.maxbits; returns its bytes
+// or 0.
+__device__ uint32_t read_tree(ZDec& z, const uint8_t* s, uint32_t len) {
+  if (len < 1) return 0;
+  for (uint32_t i = 0; i < 256; i++) z.weight[i] = 0;
+  const uint32_t hb = s[0];
+  uint32_t n = 0, used;
+  if (hb >= 128u) {
+    n = hb - 127u;
+    used = 1u + (n + 1u) / 2u;
+    if (used > len) return 0;
+    for (uint32_t i = 0; i < n; i++) z.weight[i] = (uint8_t)((s[1 + i / 2] >> ((i & 1u) ? 0 : 4)) & 15u);
+  } else {
+    used = 1u + hb;
+    if (used > len || hb == 0) return 0;
+    const uint8_t* f = s + 1;
+    const uint32_t fbits = 8u * hb;
+    auto get = [&](uint32_t at, uint32_t nb) -> uint32_t {
+      uint32_t v = 0;
+      for (uint32_t i = 0; i < nb; i++) v |= (uint32_t)((f[(at + i) >> 3] >> ((at + i) & 7u)) & 1u) << i;
+      return v;
+    };
+    const uint32_t log = (f[0] & 15u) + 5u;
+    if (log != kZFseLog) return 0;  // only the writer's accuracy log
+    uint32_t bp = 4, norm[16], nsym = 0, remaining = 65;
+    while (remaining > 1) {
+      if (nsym >= 16) return 0;
+      const uint32_t nbits = hibit(remaining) + 1u, thr = 1u << (nbits - 1u), lo = 2u * thr - 1u - remaining;
+      if (bp + nbits > fbits) return 0;
+      uint32_t v = get(bp, nbits);
+      if ((v & (thr - 1u)) < lo) {
+        v &= thr - 1u;
+        bp += nbits - 1u;
+      } else {
+        if (v >= thr) v -= lo;
+        bp += nbits;
+      }
+      if (v == 0 || v - 1u > remaining - 1u) return 0;
+      const uint32_t cnt = v - 1u;
+      norm[nsym++] = cnt;
+      remaining -= cnt;
+      if (cnt == 0) {
+        for (;;) {
+          if (bp + 2u > fbits) return 0;
+          const uint32_t rep = get(bp, 2u);
+          bp += 2u;
+          if (nsym + rep > 16u) return 0;
+          for (uint32_t i = 0; i < rep; i++) norm[nsym++] = 0;
+          if (rep != 3u) break;
+        }
+      }
+    }
+    const uint32_t head = (bp + 7u) >> 3;
+    if (head >= hb) return 0;
+    fse_table(norm, nsym, z.ft);
+    const uint8_t* bs = f + head;
+    int pp = stream_start(bs, hb - head);
+    if (pp < (int)(2u * kZFseLog)) return 0;
+    uint32_t st[2];
+    st[0] = peek_back(bs, pp, kZFseLog);
+    pp -= (int)kZFseLog;
+    st[1] = peek_back(bs, pp, kZFseLog);
+    pp -= (int)kZFseLog;
+    for (uint32_t k = 0;; k ^= 1u) {
+      if (n >= 255u) return 0;
+      z.weight[n++] = z.ft.sym[st[k]];
+      const uint32_t nb = z.ft.nb[st[k]];
+      if (pp < (int)nb) {  // past the start: the other state gives the last weight
+        if (n >= 255u) return 0;
+        z.weight[n++] = z.ft.sym[st[k ^ 1u]];
+        break;
+      }
+      st[k] = z.ft.base[st[k]] + peek_back(bs, pp, nb);
+      pp -= (int)nb;
+    }
+  }
+  uint32_t sum = 0;
+  for (uint32_t i = 0; i < n; i++) {
+    if (z.weight[i] > kZMaxBits) return 0;
+    if (z.weight[i]) sum += 1u << (z.weight[i] - 1u);
+  }
+  if (sum == 0 || n > 255u) return 0;
+  const uint32_t mb = hibit(sum) + 1u, rest = (1u << mb) - sum;
+  if (mb > kZMaxBits || (rest & (rest - 1u))) return 0;
+  z.weight[n] = (uint8_t)(hibit(rest) + 1u);
+  z.maxbits = mb;
+  return used;
+}
+
+// One stream of cnt literals (lanes 0..3); false if malformed.
+__device__ bool read_stream(const ZDec& z, const uint8_t* s, uint32_t len, uint8_t* out, uint32_t cnt) {
+  int pp = stream_start(s, len);
+  if (pp < 0) return false;
+  const uint32_t mb = z.maxbits;
+  for (uint32_t i = 0; i < cnt; i++) {
+    const uint32_t e = z.dt[peek_back(s, pp, mb)];
+    out[i] = (uint8_t)e;
+    pp -= (int)(e >> 8);
+    if (pp < 0) return false;
+  }
+  return pp == 0;
+}
+
+__global__ void __launch_bounds__(32) k_zstd_dec(DecParams p) {
+  __shared__ ZDec z;
+  const uint32_t gs = blockIdx.x, j = blockIdx.y, lane = threadIdx.x;
+  const DecSeg& sg = p.seg[sec_segment(p.seg_sec_base, p.n_seg, gs)];
+  if (!(sg.stages & kStageZstdMask) || j >= sg.zm_nblk) return;
+  const uint32_t ta = gs - sg.sec_base, A = sg.A, t = ta / A, a = ta % A, H = sg.H, nblk = sg.zm_nblk;
+  const uint32_t n = H * sg.zm_rb, lo = j * kZBlock, m = min(kZBlock, n - lo);
+  uint8_t* dst = p.zdec + sg.zm_base + (size_t)ta * sg.zm_stride + lo;
+  const uint8_t* in = sg.in;
+  auto fail = [&]() {
+    if (lane == 0) atomicOr(sg.err, kErrCorrupt);
+  };
+  // ---- the section: frame offsets checked before any read, then the sum of
+  //      the earlier attributes' section bytes
+  const unsigned long long f0 = sg.off[t], f1 = sg.off[t + 1];
+  const unsigned long long first = (t == 0 && sg.check_shdr) ? 16ull + 8ull * A : 0ull;
+  if (f0 < first || (f0 & 3ull) || f1 < f0 + sg.fhdr || f1 > sg.in_len) return fail();
+  unsigned long long before = 0, mine = 0;
+  for (uint32_t aa = lane; aa <= a; aa += 32) {
+    const unsigned long long sb = __ldg(reinterpret_cast<const unsigned int*>(in + f0 + 12ull + 12ull * aa));
+    if (aa < a) before += sb;
+    else mine = sb;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    before += __shfl_xor_sync(0xffffffffu, before, o);
+    mine += __shfl_xor_sync(0xffffffffu, mine, o);
+  }
+  const unsigned long long sec = f0 + sg.fhdr + before;
+  const unsigned long long zp = sec + 8ull * H, idx = 4ull + 4ull * nblk;
+  if (sec + mine > f1 || mine < 8ull * H + idx) return fail();
+  const unsigned long long F = __ldg(reinterpret_cast<const unsigned int*>(in + zp));
+  if (idx + F > mine - 8ull * H) return fail();
+  const unsigned long long fz = zp + idx;  // the frame
+  const uint32_t e1 = __ldg(reinterpret_cast<const unsigned int*>(in + zp + 4ull + 4ull * j));
+  const uint32_t e0 = j ? __ldg(reinterpret_cast<const unsigned int*>(in + zp + 4ull * j)) : kZFrameHdr;
+  if (e0 < kZFrameHdr || e1 <= e0 || e1 > F || e1 - e0 < 4u || e1 - e0 > 3u + kZBlock || (j + 1 == nblk && e1 != F))
+    return fail();
+  if (j == 0) {
+    bool hb = false;
+    const uint8_t want[5] = {0x28, 0xB5, 0x2F, 0xFD, 0xA0};
+    for (uint32_t i = 0; i < 5; i++) hb |= in_byte(in, fz + i) != want[i];
+    uint32_t fcs = 0;
+    for (uint32_t i = 0; i < 4; i++) fcs |= (uint32_t)in_byte(in, fz + 5 + i) << (8 * i);
+    if (hb || fcs != n) return fail();
+  }
+  const unsigned long long b = fz + e0;
+  const uint32_t bh = in_byte(in, b) | ((uint32_t)in_byte(in, b + 1) << 8) | ((uint32_t)in_byte(in, b + 2) << 16);
+  const uint32_t last = bh & 1u, type = (bh >> 1) & 3u, bsize = bh >> 3;
+  if (last != (j + 1 == nblk ? 1u : 0u)) return fail();
+  if (type == 0u) {  // Raw
+    if (bsize != m || e1 - e0 != 3u + m) return fail();
+    for (uint32_t i = lane; i < m; i += 32) dst[i] = in_byte(in, b + 3 + i);
+    return;
+  }
+  if (type == 1u) {  // RLE
+    if (bsize != m || e1 - e0 != 4u) return fail();
+    const uint8_t v = in_byte(in, b + 3);
+    for (uint32_t i = lane; i < m; i += 32) dst[i] = v;
+    return;
+  }
+  if (type != 2u || e1 - e0 != 3u + bsize) return fail();
+  // ---- Compressed: stage the content, headers and tree on lane 0
+  for (uint32_t i = lane; i < bsize + 64u; i += 32) z.blk[i] = i < bsize ? in_byte(in, b + 3 + i) : 0;
+  __syncwarp();
+  if (lane == 0) {
+    uint32_t ok = 0;
+    const uint32_t lt = z.blk[0] & 3u, sf = (z.blk[0] >> 2) & 3u;
+    const uint32_t lhdr = sf <= 1u ? 3u : (sf == 2u ? 4u : 5u), bits = sf <= 1u ? 10u : (sf == 2u ? 14u : 18u);
+    if (lt == 2u && lhdr + 1u <= bsize) {
+      unsigned long long h = 0;
+      for (uint32_t i = 0; i < lhdr; i++) h |= (unsigned long long)z.blk[i] << (8 * i);
+      const uint32_t rs = (uint32_t)((h >> 4) & ((1u << bits) - 1u));
+      const uint32_t cs = (uint32_t)((h >> (4 + bits)) & ((1u << bits) - 1u));
+      if (rs == m && lhdr + cs + 1u == bsize && z.blk[lhdr + cs] == 0) {
+        const uint32_t tu = read_tree(z, z.blk + lhdr, cs);
+        if (tu) {
+          ok = 1;
+          z.tree_len = tu;
+          z.sf = sf;
+          z.cs = cs;
+          z.lhdr = lhdr;
+          uint32_t pos = 0;  // decoding-table ranges: symbols by weight, then value
+          for (uint32_t w = 1; w <= z.maxbits; w++)
+            for (uint32_t s = 0; s < 256; s++)
+              if (z.weight[s] == w) {
+                z.start[s] = pos;
+                pos += 1u << (w - 1u);
+              }
+          if (pos != (1u << z.maxbits)) ok = 0;
+        }
+      }
+    }
+    z.ok = ok;
+  }
+  __syncwarp();
+  if (!z.ok) return fail();
+  for (uint32_t s = lane; s < 256; s += 32) {
+    const uint32_t w = z.weight[s];
+    if (!w) continue;
+    const uint16_t e = (uint16_t)(s | ((z.maxbits + 1u - w) << 8));
+    for (uint32_t i = 0; i < (1u << (w - 1u)); i++) z.dt[z.start[s] + i] = e;
+  }
+  __syncwarp();
+  // ---- the streams, one lane each
+  const uint8_t* lit = z.blk + z.lhdr;
+  const uint32_t tl = z.tree_len, cs = z.cs;
+  bool ok = true;
+  if (z.sf == 0u) {
+    if (lane == 0) ok = read_stream(z, lit + tl, cs - tl, dst, m);
+  } else {
+    if (tl + 6u > cs) return fail();
+    uint32_t sz[4];
+    for (uint32_t k = 0; k < 3; k++) sz[k] = lit[tl + 2 * k] | ((uint32_t)lit[tl + 2 * k + 1] << 8);
+    const uint32_t rest = cs - tl - 6u;
+    const uint32_t seg = (m + 3u) / 4u;
+    if (sz[0] + sz[1] + sz[2] > rest || 3u * seg > m) return fail();
+    sz[3] = rest - sz[0] - sz[1] - sz[2];
+    if (lane < 4) {
+      uint32_t off = tl + 6u;
+      for (uint32_t k = 0; k < lane; k++) off += sz[k];
+      const uint32_t l0 = lane * seg, l1 = lane < 3 ? l0 + seg : m;
+      ok = read_stream(z, lit + off, sz[lane], dst + l0, l1 - l0);
+    }
+  }
+  if (__any_sync(0xffffffffu, !ok)) fail();
+}
+
+}  // namespace
+
+int launch_zstd_encode(const EncParams& p, void* stream) {
+  if (!p.zblk || !p.zmax_blk) return 0;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  k_zstd_enc<<<dim3(p.n_sec, p.zmax_blk), kZT, 0, st>>>(p);
+  return (int)cudaGetLastError();
+}
+
+int launch_zstd_decode(const DecParams& p, void* stream) {
+  if (!p.zdec || !p.zmax_blk) return 0;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  k_zstd_dec<<<dim3(p.n_sec, p.zmax_blk), 32, 0, st>>>(p);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace jiffy

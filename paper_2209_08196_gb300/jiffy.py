@@ -56,6 +56,7 @@ class _PointAttr(ctypes.Structure):
 STAGE_NO_MASK = 1
 STAGE_NO_DELTA = 2
 STAGE_NO_ZIGZAG = 4
+STAGE_ZSTD_MASK = 8  # the zero mask as one Zstandard frame per section (Sec. III-C)
 
 
 _L = None
