@@ -53,10 +53,10 @@ WORKLOAD = ("single stream, 100 scans x 128 beams x 2048 columns; range u32 (10 
 # only for the kernel sources it was taken on (sha256 prefix of the files
 # listed) and is reported as null for any other source or workload.
 TRAFFIC = {
-    "k_encode": (343770624 + 53826048, ("jiffy_encode.cu", "jiffy_device.cuh", "jiffy_kernels.h", "jiffy_types.h"),
-                 "28888dcb8a5d3f59"),
-    "k_decode": (78800640 + 292420864, ("jiffy_decode.cu", "jiffy_device.cuh", "jiffy_kernels.h", "jiffy_types.h"),
-                 "ad7f4d06e04d93f9"),
+    "k_encode": (343736576 + 53601280, ("jiffy_encode.cu", "jiffy_device.cuh", "jiffy_kernels.h", "jiffy_types.h"),
+                 "8372365b9d13e592"),
+    "k_decode": (78800640 + 292559872, ("jiffy_decode.cu", "jiffy_device.cuh", "jiffy_kernels.h", "jiffy_types.h"),
+                 "6c08fca6995251b8"),
 }
 
 
@@ -824,6 +824,87 @@ def mask_codec_leg(J, torch, dev, local, levels=(1, 3, 19)):
             "bit_order": "row-major, least significant bit first", "cases": rows}
 
 
+def zstd_mask_leg(J, torch, dev, local, planes_in, attrs, steps, warmup, base, info_scans=10):
+    """The paper's mask coding as the stream option (Sec. III-C: the zero
+    bitmask packed into bytes and compressed with Zstd; Sec. III-D: XORed with
+    the previous scan's for P): every section's mask one Zstandard frame,
+    written and read by the GPU kernels, on the benchmark's workload and step
+    (enqueue-only encode and decode of all scans on one CUDA stream). Against
+    the class-coded step of the headline: step time, stream bytes, mask bytes
+    per scan (read back by the stream inspector) and the device time of the
+    encoder's placement phase (which holds the Zstandard writer) and of the
+    decode (which holds the reader)."""
+    from paper_2209_08196_gb300 import streaminfo
+    T, H, W = (int(x) for x in planes_in[0].shape)
+    Z = J.STAGE_ZSTD_MASK
+    enc = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, attrs, device=local, stages=Z)
+    dec = J.jiffy_stream_create(J.JIFFY_DECODER, H, W, attrs, device=local, stages=Z)
+    out = torch.empty(J.jiffy_max_encoded_size(H, W, attrs, T), dtype=torch.uint8, device=dev)
+    outs = J.empty_planes(dec, T)
+    d_offs = torch.zeros(T + 1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        J.jiffy_stream_reset(enc)
+        J.jiffy_stream_reset(dec)
+        J.jiffy_encode_seq_async(enc, planes_in, out, d_offs, stream)
+        J.jiffy_decode_seq_async(dec, out, d_offs, outs, stream)
+
+    for _ in range(warmup):
+        step()
+    J.jiffy_stream_wait(enc)
+    J.jiffy_stream_wait(dec)
+    exact = True
+    for a, (s_, P) in enumerate(attrs):
+        m = (1 << (8 * s_)) - 1
+        q = torch.clamp(((planes_in[a].to(torch.int64) & m) + P // 2) // P, max=m // P)
+        exact = exact and torch.equal(outs[a].to(torch.int64) & m, q * P)
+        del q
+    nz = int(d_offs[T])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    J.jiffy_stream_wait(enc)
+    J.jiffy_stream_wait(dec)
+    ms = e0.elapsed_time(e1) / steps
+    J.jiffy_stream_set_profiling(enc, True)
+    J.jiffy_stream_set_profiling(dec, True)
+    for _ in range(steps):
+        step()
+    J.jiffy_stream_wait(enc)
+    J.jiffy_stream_wait(dec)
+    ke, kd = J.jiffy_stream_kernel_times(enc), J.jiffy_stream_kernel_times(dec)
+    # mask bytes of the first scans, both mask codings, from the streams themselves
+    n_i = min(info_scans, T)
+    sub = [p[:n_i] for p in planes_in]
+    per = {}
+    for name, st in (("zstd", Z), ("class_words", 0)):
+        e = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, attrs, device=local, stages=st)
+        b = torch.empty(J.jiffy_max_encoded_size(H, W, attrs, n_i), dtype=torch.uint8, device=dev)
+        nb, _ = J.jiffy_encode_seq(e, sub, b, stream)
+        _, secs = streaminfo.sections(b[:nb].cpu().numpy().tobytes())
+        per[name] = {"mask_bytes_per_scan": sum(x.mask_bytes for x in secs) / n_i, "stream_bytes_per_scan": nb / n_i}
+        del e, b
+    raw = sum(p.numel() * p.element_size() for p in planes_in)
+    px = T * H * W
+    J.jiffy_stream_destroy(enc)
+    J.jiffy_stream_destroy(dec)
+    return {"stages": "JIFFY_STAGE_ZSTD_MASK", "exact": bool(exact), "steps": steps,
+            "gpoints_s": px / ms / 1e6, "ms_per_step": ms, "class_words_ms_per_step": base["ms_per_step"],
+            "stream_bytes": nz, "class_words_stream_bytes": base["stream_bytes"],
+            "ratio": raw / nz, "class_words_ratio": raw / base["stream_bytes"],
+            "first_scans": n_i, "per_scan": per,
+            "kernel_ms": {"k_trial": ke[0], "k_encode": ke[1], "k_finalize_with_zstd_writer": ke[2],
+                          "k_decode_with_zstd_reader": kd[0]},
+            "class_words_kernel_ms": {"k_finalize": base["k_finalize"], "k_decode": base["k_decode"]},
+            "zstd_writer_ms": ke[2] - base["k_finalize"], "zstd_reader_ms": kd[0] - base["k_decode"],
+            "blocks": "one per 8192 mask bytes: RLE, Raw, or Huffman literals (1 or 4 streams) with direct or "
+                      "FSE-coded weights and no sequences; every frame is a standard Zstandard frame"}
+
+
 def whole_job_gpoints(px_per_rank: int, world: int, ms: float) -> float:
     """All ranks' pixels over the slowest rank's time, in Gpoints/s."""
     return px_per_rank * world / (ms / 1e3) / 1e9
@@ -848,6 +929,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="skip the stream-size sweep leg")
     ap.add_argument("--no-small", action="store_true", help="skip the 16 x 64 x 1024 single-stream leg")
     ap.add_argument("--no-mask-codec", action="store_true", help="skip the Zstd mask comparison leg")
+    ap.add_argument("--no-zstd-mask", action="store_true", help="skip the leg run with the Zstandard mask option")
     ap.add_argument("--sweep-max-mib", type=int, default=4096, help="largest raw size of the sweep")
     ap.add_argument("--serve-seconds", type=float, default=60.0)
     ap.add_argument("--serve-sat-seconds", type=float, default=5.0)
@@ -862,7 +944,8 @@ def main():
     if world > 1:
         # replicas: the scaling figure is the main step's; the other legs
         # measure single-GPU properties and run in the one-GPU invocation
-        for leg in ("small", "sweep", "batched", "serve", "heuristic", "ablation", "standardize", "mask_codec"):
+        for leg in ("small", "sweep", "batched", "serve", "heuristic", "ablation", "standardize", "mask_codec",
+                    "zstd_mask"):
             setattr(args, "no_" + leg, True)
 
     import torch
@@ -1245,6 +1328,12 @@ def main():
     if not args.no_mask_codec:
         mask_codec = mask_codec_leg(J, torch, dev, local)
 
+    zstd_mask = None
+    if not args.no_zstd_mask:
+        zstd_mask = zstd_mask_leg(J, torch, dev, local, planes_in, attrs, args.steps, args.warmup,
+                                  {"ms_per_step": ms_step, "stream_bytes": n, "k_finalize": avg["k_finalize"],
+                                   "k_decode": avg["k_decode"]})
+
     sweep = None
     if not args.no_sweep:
         sweep = sweep_leg(J, torch, dev, local, args.sweep_max_mib)
@@ -1280,6 +1369,12 @@ def main():
             roofline["batched"] = {"gpoints_s": batched["gpoints_s"], "seq_gpoints_s": batched.get("seq_gpoints_s"),
                                    "encode_rows_frac": batched.get("encode_rows_frac"),
                                    "decode_rows_frac": batched.get("decode_rows_frac")}
+        if zstd_mask is not None:
+            roofline["zstd_mask"] = {"gpoints_s": zstd_mask["gpoints_s"], "ratio": zstd_mask["ratio"],
+                                     "class_words_ratio": zstd_mask["class_words_ratio"], "exact": zstd_mask["exact"],
+                                     "mask_bytes_per_scan": zstd_mask["per_scan"]["zstd"]["mask_bytes_per_scan"],
+                                     "class_words_mask_bytes_per_scan":
+                                         zstd_mask["per_scan"]["class_words"]["mask_bytes_per_scan"]}
         if small is not None:
             roofline["small_stream"] = {"cold_gpoints_s": small["cold_gpoints_s"], "hot_gpoints_s": small["hot_gpoints_s"],
                                         "kernels_us_per_step": small["kernels_us_per_step"]}
@@ -1298,6 +1393,7 @@ def main():
                 "gpu_launches": 5 * args.steps * (2 if e2e else 1),
                 "batched": batched, "served": served, "heuristic": heuristic, "precision": precision,
                 "ablation": ablation, "standardize": standardize, "small_stream": small, "mask_codec": mask_codec,
+                "zstd_mask": zstd_mask,
                 "sweep": None if sweep is None else roofline["sweep"]["rows"], "sweep_detail": sweep,
                 "batched_gpoints_s": None if batched is None else batched["gpoints_s"],
                 "served_p50_ms": None if served is None else served["p50_ms"],
