@@ -193,7 +193,9 @@ class Codec:
     def bound(self) -> int:
         nw = (self.W + 31) // 32
         row = 4 * ((nw + 15) // 16) + 4 * nw + 4 * ((self.W + 127) // 128) + 4 * self.W
-        return 16 + 8 * self.A + 8 + 12 * self.A + self.A * (8 * self.H + self.H * row)
+        # + 16 + 8 per Zstandard mask block: the option's index, frame and block headers, padding
+        nblk = max(1, -(-(self.H * ((self.W + 7) // 8)) // 8192))
+        return 16 + 8 * self.A + 8 + 12 * self.A + self.A * (8 * self.H + self.H * row + 16 + 8 * nblk)
 
     def encode(self, planes, return_modes: bool = False):
         arrs = []
