@@ -3,10 +3,11 @@ compressed with Zstd, XORed with the previous scan's for P, Sec. III-D) against
 the oracle. Bytes must be identical and the planes must round trip.
 
 Cases: row widths whose byte rows are not whole words, sections of several
-8192-byte blocks, masks that give RLE, Raw and Compressed blocks with direct
-and FSE-coded Huffman weights, one and four streams; I, P and trial modes;
-the single-call, sequence and batched entry points; the stage switches
-combined with it; malformed frames rejected without faults. libzstd restores
+8192-byte blocks (up to 256), masks that give RLE, Raw and Compressed blocks
+with direct and FSE-coded Huffman weights, one and four streams; I, P and
+trial modes; the single-call, sequence, enqueue-only (graph replay) and
+batched entry points; the stage switches combined with it; malformed frames
+rejected without faults. libzstd restores
 every mask frame the GPU writes to the packed zero masks of the inputs."""
 import ctypes
 import ctypes.util
@@ -71,7 +72,7 @@ def test_shapes_and_modes_match_oracle(H, W, force):
 
 @pytest.mark.parametrize("kind", ["sparse", "half", "none", "low7", "rows"])
 def test_block_kinds_match_oracle_and_libzstd(kind):
-    rng = np.random.default_rng(abs(hash(kind)) % 1000)
+    rng = np.random.default_rng(["sparse", "half", "none", "low7", "rows"].index(kind) + 500)
     H, W, attrs = 48, 1400, [(2, 1), (1, 1)]  # 8400 mask bytes: a full block and a short one
     scans = masked_scans(rng, H, W, attrs, 3, kind)
     frames = check_stream(H, W, attrs, scans, stages=Z, seq=True)
@@ -207,3 +208,47 @@ def test_options_that_cannot_be_combined():
     with pytest.raises(J.JiffyError) as ei:
         J.jiffy_decode_frame_noalloc(buf, 64, 4, 64, [(2, 1)], 0, None, out, stages=Z)
     assert ei.value.name == "JIFFY_ERR_INVALID_ARG"
+
+
+def test_large_sections_of_many_blocks():
+    # 1024 x 16384: 2 MiB of mask bytes per section, 256 blocks (the writer's
+    # and the reader's grids run 256 blocks deep; the block-end index has 256
+    # entries); an I frame, then P
+    rng = np.random.default_rng(123)
+    H, W, attrs = 1024, 16384, [(1, 1)]
+    b = rng.integers(1, 256, size=(H, W)).astype(np.uint8)
+    scans = []
+    for t in range(2):
+        x = b.copy()
+        x[rng.random((H, W)) < 0.1] = 0
+        scans.append([x])
+    check_stream(H, W, attrs, scans, force_mode=1, seq=True, stages=Z)
+
+
+def test_enqueue_only_pair_replays_graphs():
+    # the enqueue-only pair with the frame offsets left on the device; calls
+    # after the first replay the stream's captured launch sequence
+    rng = np.random.default_rng(321)
+    H, W, attrs, T = 32, 1000, [(4, 10), (2, 1), (1, 1)], 4
+    scans = masked_scans(rng, H, W, attrs, T, "sparse")
+    want, _, _ = oracle.encode_sequence(H, W, attrs, scans, stages=Z)
+    enc = J.jiffy_stream_create(J.JIFFY_ENCODER, H, W, attrs, stages=Z)
+    dec = J.jiffy_stream_create(J.JIFFY_DECODER, H, W, attrs, stages=Z)
+    planes = [[to_dev(p) for p in s] for s in scans]
+    out = torch.zeros(J.jiffy_max_encoded_size(H, W, attrs, T), dtype=torch.uint8, device="cuda")
+    d_offs = torch.zeros(T + 1, dtype=torch.int64, device="cuda")
+    outs = J.empty_planes(dec, T)
+    for _ in range(3):
+        J.jiffy_stream_reset(enc)
+        J.jiffy_stream_reset(dec)
+        outs[0].zero_()
+        J.jiffy_encode_seq_async(enc, planes, out, d_offs)
+        J.jiffy_decode_seq_async(dec, out, d_offs, outs)
+        J.jiffy_stream_wait(enc)
+        J.jiffy_stream_wait(dec)
+        assert out[:int(d_offs[T])].cpu().numpy().tobytes() == want
+        for t in range(T):
+            for a, (s, P) in enumerate(attrs):
+                m = (1 << (8 * s)) - 1
+                q = np.minimum(((scans[t][a].astype(np.int64) & m) + P // 2) // P, m // P)
+                assert np.array_equal(to_np(outs[a][t], s).astype(np.int64), q * P), (t, a)
