@@ -301,17 +301,30 @@ __global__ void __launch_bounds__(kZT, 8) k_zstd_enc(EncParams p) {
   const uint32_t i0 = kZPer * tid;
   const uint32_t nmine = i0 < m ? min(kZPer, m - i0) : 0u;
 
-  // ---- clear the image and the histograms; are the bytes all equal?
+  // ---- clear the image and the histograms; one pass over the thread's
+  //      bytes (all 16 words requested at once): histogram, and are the
+  //      block's bytes all equal?
   const uint32_t nw4 = (nmine + 3u) / 4u;
   for (uint32_t i = tid; i < kZSlot / 4; i += kZT) z.img[i] = 0;
   for (uint32_t i = tid; i < kZW * 256; i += kZT) (&z.hist[0][0])[i] = 0;
   const uint8_t b0 = __ldg(src);
+  __syncthreads();
   int diff = 0;
-  for (uint32_t k = 0; k < nw4; k++) {
-    const uint32_t w = chunk_word(src, i0, m, k);
+  {
+    uint32_t wv[kZPer / 4];
 #pragma unroll
-    for (uint32_t b = 0; b < 4u; b++)
-      if (4u * k + b < nmine) diff |= ((w >> (8u * b)) & 0xffu) != b0;
+    for (uint32_t k = 0; k < kZPer / 4; k++) wv[k] = k < nw4 ? chunk_word(src, i0, m, k) : 0u;
+#pragma unroll
+    for (uint32_t k = 0; k < kZPer / 4; k++) {
+#pragma unroll
+      for (uint32_t b = 0; b < 4u; b++) {
+        if (4u * k + b < nmine) {
+          const uint32_t v = (wv[k] >> (8u * b)) & 0xffu;
+          diff |= v != b0;
+          atomicAdd(&z.hist[tid >> 5][v], 1u);
+        }
+      }
+    }
   }
   if (!__syncthreads_or(diff)) {  // RLE block: header + the byte
     if (tid == 0) {
@@ -321,14 +334,7 @@ __global__ void __launch_bounds__(kZT, 8) k_zstd_enc(EncParams p) {
     return;
   }
 
-  // ---- histogram
-  for (uint32_t k = 0; k < nw4; k++) {
-    const uint32_t w = chunk_word(src, i0, m, k);
-#pragma unroll
-    for (uint32_t b = 0; b < 4u; b++)
-      if (4u * k + b < nmine) atomicAdd(&z.hist[tid >> 5][(w >> (8u * b)) & 0xffu], 1u);
-  }
-  __syncthreads();
+  // ---- counts of the block
   for (uint32_t s = tid; s < 256; s += kZT) {
     uint32_t c = 0;
     for (uint32_t w = 0; w < kZW; w++) c += z.hist[w][s];
@@ -549,8 +555,10 @@ __global__ void __launch_bounds__(kZT, 8) k_zstd_enc(EncParams p) {
 // ----------------------------------------------------------------------------
 // Reader
 // ----------------------------------------------------------------------------
+constexpr uint32_t kBlkWords = (kZBlock + 128) / 4;  // a block's content (<= 8192 bytes from byte 0..3) + slack
+
 struct ZDec {
-  uint32_t blkw[(kZBlock + 96) / 4];  // a Compressed block's content (from byte blk_at), slack for the peeks
+  uint32_t blkw[kBlkWords];   // a Compressed block's content (from byte blk_at), zero slack for the peeks
   uint16_t dt[1u << kZMaxBits];  // decoding table: symbol | code bits << 8
   uint8_t weight[256];
   uint8_t sorted[256];        // symbols with a weight, by (weight, value)
@@ -782,7 +790,9 @@ __global__ void __launch_bounds__(32) k_zstd_dec(DecParams p) {
   const unsigned long long c0 = b + 3;
   const uint32_t blk_at = (uint32_t)(c0 & 3ull), nwords = (blk_at + bsize + 3u) / 4u;
   const unsigned int* cw = reinterpret_cast<const unsigned int*>(in + (c0 - blk_at));
-  for (uint32_t i = lane; i < (kZBlock + 96) / 4; i += 32) z.blkw[i] = i < nwords ? __ldg(cw + i) : 0u;
+#pragma unroll 8
+  for (uint32_t i = lane; i < nwords; i += 32) z.blkw[i] = __ldg(cw + i);
+  for (uint32_t i = nwords + lane; i < nwords + 24u && i < kBlkWords; i += 32) z.blkw[i] = 0u;  // zero slack for the peeks
   __syncwarp();
   uint8_t* blk = reinterpret_cast<uint8_t*>(z.blkw) + blk_at;
   if (lane == 0) {
