@@ -284,3 +284,29 @@ def test_stream_masks_are_the_packed_zero_masks(H, W, force):
 def test_zstd_mask_needs_the_mask_stage():
     with pytest.raises(ValueError):
         oracle.Codec(2, 8, [(2, 1)], stages=oracle.ZSTD_MASK | oracle.NO_MASK)
+
+
+def test_reader_accepts_only_the_writers_subset():
+    # valid Zstandard frames that the writer never produces are refused by
+    # the reader: a block split other than 8192 bytes, and libzstd's own
+    # frames (LZ sequences); libzstd itself restores both
+    rng = np.random.default_rng(8)
+    data = np.packbits(rng.random(8 * 9000) < 0.1, bitorder="little").tobytes()
+    n = len(data)
+    # two Raw blocks of 4096 bytes and one of 808: 28 b5 2f fd a0 <n>, blocks
+    frame = bytes.fromhex("28b52ffda0") + n.to_bytes(4, "little")
+    cuts = [0, 4096, 8192, n]
+    for j in range(3):
+        size = cuts[j + 1] - cuts[j]
+        frame += (int(j == 2) | (size << 3)).to_bytes(3, "little") + data[cuts[j]:cuts[j + 1]]
+    assert decompress(frame, n) == data
+    assert oracle.zstd_read(frame, n) is None
+    z = _libzstd()
+    sz, vp = ctypes.c_size_t, ctypes.c_void_p
+    z.ZSTD_compress.restype, z.ZSTD_compress.argtypes = sz, [vp, sz, vp, sz, ctypes.c_int]
+    src = np.frombuffer(data, dtype=np.uint8).copy()
+    dst = np.zeros(2 * n + 1024, dtype=np.uint8)
+    k = z.ZSTD_compress(dst.ctypes.data, dst.nbytes, src.ctypes.data, n, 3)
+    lib_frame = dst[:k].tobytes()
+    assert decompress(lib_frame, n) == data
+    assert oracle.zstd_read(lib_frame, n) is None
