@@ -1005,26 +1005,42 @@ __global__ void __launch_bounds__(kThreads) k_place(EncParams p) {
       put_u32_guarded(out, cap, sec_at + 8ull * r + 4, p.row_carry[item0 + r], sg.err);
     }
   }
-  // row chunks: a warp per row, slot -> stream, 4 words in flight per lane
+  // row chunks: slot -> stream, a warp per two rows at a time, 4 words of
+  // each in flight per lane
   const unsigned long long data_at = sec_at + 8ull * H + zpart;
   const uint32_t lane = lane_id();
-  for (uint32_t r = part * kWarps + warp_id(); r < H; r += kWarps * kPlaceSplit) {
+  auto row_span = [&](uint32_t r, const uint32_t*& src, uint32_t*& dst) -> uint32_t {
     const uint32_t words = p.row_bytes[item0 + r] / 4u;
     const unsigned long long at = data_at + smem[r];
     if (at + 4ull * words > cap) {
       if (lane == 0) atomicOr(sg.err, kErrCapacity);
-      continue;
+      return 0u;
     }
-    const uint32_t* src =
-        reinterpret_cast<const uint32_t*>(p.slots + sg.slot_base + (size_t)(local0 + r) * sg.slot_bytes);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(out + at);
-    for (uint32_t i = lane; i < words; i += 128u) {
-      uint32_t v[4];
+    src = reinterpret_cast<const uint32_t*>(p.slots + sg.slot_base + (size_t)(local0 + r) * sg.slot_bytes);
+    dst = reinterpret_cast<uint32_t*>(out + at);
+    return words;
+  };
+  constexpr uint32_t kRowStride = kWarps * kPlaceSplit;
+  for (uint32_t r = part * kWarps + warp_id(); r < H; r += 2u * kRowStride) {
+    const uint32_t* sa = nullptr;
+    const uint32_t* sb = nullptr;
+    uint32_t* da = nullptr;
+    uint32_t* db = nullptr;
+    const uint32_t wa = row_span(r, sa, da);
+    const uint32_t wb = r + kRowStride < H ? row_span(r + kRowStride, sb, db) : 0u;
+    const uint32_t wmax = max(wa, wb);
+    for (uint32_t i = lane; i < wmax; i += 128u) {
+      uint32_t va[4], vb[4];
 #pragma unroll
-      for (uint32_t q = 0; q < 4; q++) v[q] = i + 32u * q < words ? __ldcs(src + i + 32u * q) : 0u;
+      for (uint32_t q = 0; q < 4; q++) {
+        va[q] = i + 32u * q < wa ? __ldcs(sa + i + 32u * q) : 0u;
+        vb[q] = i + 32u * q < wb ? __ldcs(sb + i + 32u * q) : 0u;
+      }
 #pragma unroll
-      for (uint32_t q = 0; q < 4; q++)
-        if (i + 32u * q < words) dst[i + 32u * q] = v[q];
+      for (uint32_t q = 0; q < 4; q++) {
+        if (i + 32u * q < wa) da[i + 32u * q] = va[q];
+        if (i + 32u * q < wb) db[i + 32u * q] = vb[q];
+      }
     }
   }
   if (part == 0 && a == 0 && threadIdx.x == 0) {
