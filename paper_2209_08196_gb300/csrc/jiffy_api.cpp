@@ -761,7 +761,7 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, s);
     if (ce != cudaSuccess) return (int)ce;
     const int rc = jiffy::launch_encode(pp, s, evs);
-    if (rc != 0) return rc;
+    if (rc != 0 || async) return rc;  // enqueue-only: offsets and errors stay on the device
     return (int)cudaMemcpyAsync(hres, d + o_res, rs.off, cudaMemcpyDeviceToHost, s);
   };
   if (ws.autotune) {
@@ -1002,7 +1002,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
     if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, s);
     if (ce != cudaSuccess) return (int)ce;
     const int rc = jiffy::launch_decode(pp, s, evs);
-    if (rc != 0) return rc;
+    if (rc != 0 || async) return rc;  // enqueue-only: errors stay on the device
     return (int)cudaMemcpyAsync(hres, d + o_res, rs.off, cudaMemcpyDeviceToHost, s);
   };
   if (ws.autotune) {
