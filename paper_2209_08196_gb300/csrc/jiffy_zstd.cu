@@ -564,39 +564,20 @@ struct ZDec {
   uint8_t sorted[256];        // symbols with a weight, by (weight, value)
   uint32_t cls_base[kZMaxBits + 1], cls_pos[kZMaxBits + 1], cls_cnt[kZMaxBits + 1];
   uint32_t fnext[16];
+  uint32_t fpack[64];         // FSE decoding table packed: symbol | bits << 8 | baseline << 16
   FseTable ft;
-  uint32_t ok, maxbits, tree_len, sf, cs, lhdr;
+  uint32_t ok, maxbits, tree_len, sf, cs, lhdr, nweights;
 };
 
 __device__ __forceinline__ uint8_t in_byte(const uint8_t* in, unsigned long long at) { return __ldg(in + at); }
 
-// n bits (n <= 11) ending at bit position p (exclusive) of a backward stream
-// in shared memory; bits below position 0 read as zero
-__device__ __forceinline__ uint32_t peek_back(const uint8_t* s, int p, uint32_t n) {
-  const int q = p - (int)n;
-  const int b0 = q >= 0 ? (q >> 3) : -((7 - q) >> 3);
-  const uint32_t sh = (uint32_t)(q - 8 * b0);
-  uint32_t w = 0;
-#pragma unroll
-  for (int k = 0; k < 3; k++) {
-    const int bi = b0 + k;
-    w |= (bi >= 0 ? (uint32_t)s[bi] : 0u) << (8 * k);
-  }
-  return (w >> sh) & ((1u << n) - 1u);
-}
-
-// payload bits of a backward stream (the position of its end mark), or -1
-__device__ __forceinline__ int stream_start(const uint8_t* s, uint32_t len) {
-  if (len == 0 || s[len - 1] == 0) return -1;
-  return (int)(8u * (len - 1u) + hibit(s[len - 1]));
-}
-
-// Huffman tree description at s[0..len) (lane 0): weights of all symbols
-// (the implied last one included) into z.weight, z.maxbits; returns its bytes
-// or 0.
+// Huffman tree description at s[0..len) (lane 0): the listed weights into
+// z.weight[0 .. n) (z.weight zeroed beforehand), n into z.nweights; returns
+// its bytes or 0. The FSE-coded form is read through a 64-bit window of its
+// bit stream, as the literal streams are; the weights are checked afterwards
+// by the whole warp (tree_weights).
 __device__ uint32_t read_tree(ZDec& z, const uint8_t* s, uint32_t len) {
   if (len < 1) return 0;
-  for (uint32_t i = 0; i < 256; i++) z.weight[i] = 0;
   const uint32_t hb = s[0];
   uint32_t n = 0, used;
   if (hb >= 128u) {
@@ -647,38 +628,78 @@ __device__ uint32_t read_tree(ZDec& z, const uint8_t* s, uint32_t len) {
     const uint32_t head = (bp + 7u) >> 3;
     if (head >= hb) return 0;
     fse_table(norm, nsym, z.ft, z.fnext);
+    for (uint32_t u = 0; u < 64; u++) z.fpack[u] = z.ft.sym[u] | ((uint32_t)z.ft.nb[u] << 8) | ((uint32_t)z.ft.base[u] << 16);
+    // the weights' bit stream, read from its end through a 64-bit window
+    // (bits [bot, bot + k) in its low k bits; below the start: zeros)
     const uint8_t* bs = f + head;
-    int pp = stream_start(bs, hb - head);
-    if (pp < (int)(2u * kZFseLog)) return 0;
+    const uint32_t blen = hb - head;
+    if (bs[blen - 1] == 0) return 0;
+    const int p0 = (int)(8u * (blen - 1u) + hibit(bs[blen - 1]));
+    if (p0 < (int)(2u * kZFseLog)) return 0;
+    int bot = p0 & ~7, k = p0 - bot;
+    unsigned long long win = bs[bot >> 3] & ((1u << k) - 1u);
+    auto refill = [&]() {
+      if (k < 32) {
+        const int b = (bot >> 3) - 4;
+        uint32_t w = 0;
+#pragma unroll
+        for (int q = 0; q < 4; q++) w |= (b + q >= 0 ? (uint32_t)bs[b + q] : 0u) << (8 * q);
+        win = (win << 32) | w;
+        bot -= 32;
+        k += 32;
+      }
+    };
+    auto take = [&](uint32_t nb) -> uint32_t {  // nb <= 6 <= k after a refill
+      const uint32_t v = (uint32_t)(win >> (k - (int)nb)) & ((1u << nb) - 1u);
+      k -= (int)nb;
+      return v;
+    };
+    refill();
     uint32_t st[2];
-    st[0] = peek_back(bs, pp, kZFseLog);
-    pp -= (int)kZFseLog;
-    st[1] = peek_back(bs, pp, kZFseLog);
-    pp -= (int)kZFseLog;
-    for (uint32_t k = 0;; k ^= 1u) {
+    st[0] = take(kZFseLog);
+    refill();
+    st[1] = take(kZFseLog);
+    for (uint32_t q = 0;; q ^= 1u) {
       if (n >= 255u) return 0;
-      z.weight[n++] = z.ft.sym[st[k]];
-      const uint32_t nb = z.ft.nb[st[k]];
-      if (pp < (int)nb) {  // past the start: the other state gives the last weight
+      const uint32_t e = z.fpack[st[q]];
+      z.weight[n++] = (uint8_t)e;
+      const uint32_t nb = (e >> 8) & 0xffu;
+      if (bot + k < (int)nb) {  // past the start: the other state gives the last weight
         if (n >= 255u) return 0;
-        z.weight[n++] = z.ft.sym[st[k ^ 1u]];
+        z.weight[n++] = (uint8_t)z.fpack[st[q ^ 1u]];
         break;
       }
-      st[k] = z.ft.base[st[k]] + peek_back(bs, pp, nb);
-      pp -= (int)nb;
+      refill();
+      st[q] = (e >> 16) + take(nb);
     }
   }
-  uint32_t sum = 0;
-  for (uint32_t i = 0; i < n; i++) {
-    if (z.weight[i] > kZMaxBits) return 0;
-    if (z.weight[i]) sum += 1u << (z.weight[i] - 1u);
-  }
-  if (sum == 0 || n > 255u) return 0;
-  const uint32_t mb = hibit(sum) + 1u, rest = (1u << mb) - sum;
-  if (mb > kZMaxBits || (rest & (rest - 1u))) return 0;
-  z.weight[n] = (uint8_t)(hibit(rest) + 1u);
-  z.maxbits = mb;
+  z.nweights = n;
   return used;
+}
+
+// The weights read by read_tree, checked by the whole warp: every weight at
+// most 11, their sum (of 2^(w-1)) completed to a power of two by the implied
+// last weight, whose symbol is n. Sets z.maxbits; false if malformed.
+__device__ bool tree_weights(ZDec& z, uint32_t lane) {
+  const uint32_t n = z.nweights;
+  uint32_t sum = 0;
+  bool bad = false;
+  for (uint32_t i = lane; i < n; i += 32) {
+    const uint32_t w = z.weight[i];
+    bad |= w > kZMaxBits;
+    sum += w ? 1u << (w - 1u) : 0u;
+  }
+  sum = __reduce_add_sync(0xffffffffu, sum);
+  if (__any_sync(0xffffffffu, bad) || sum == 0 || n > 255u) return false;
+  const uint32_t mb = hibit(sum) + 1u, rest = (1u << mb) - sum;
+  if (mb > kZMaxBits || (rest & (rest - 1u))) return false;
+  __syncwarp();
+  if (lane == 0) {
+    z.weight[n] = (uint8_t)(hibit(rest) + 1u);
+    z.maxbits = mb;
+  }
+  __syncwarp();
+  return true;
 }
 
 // One stream of cnt literals (lanes 0..3); false if malformed. The bits
@@ -795,6 +816,8 @@ __global__ void __launch_bounds__(32) k_zstd_dec(DecParams p) {
   for (uint32_t i = nwords + lane; i < nwords + 24u && i < kBlkWords; i += 32) z.blkw[i] = 0u;  // zero slack for the peeks
   __syncwarp();
   uint8_t* blk = reinterpret_cast<uint8_t*>(z.blkw) + blk_at;
+  for (uint32_t i = lane; i < 256; i += 32) z.weight[i] = 0;
+  __syncwarp();
   if (lane == 0) {
     uint32_t ok = 0;
     const uint32_t lt = blk[0] & 3u, sf = (blk[0] >> 2) & 3u;
@@ -818,7 +841,7 @@ __global__ void __launch_bounds__(32) k_zstd_dec(DecParams p) {
     z.ok = ok;
   }
   __syncwarp();
-  if (!z.ok) return fail();
+  if (!z.ok || !tree_weights(z, lane)) return fail();
   // decoding table: the symbols of weight w, by value, take consecutive
   // ranges of 2^(w-1) entries after those of the lower weights
   const uint32_t mb = z.maxbits;
