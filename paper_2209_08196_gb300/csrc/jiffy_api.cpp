@@ -93,7 +93,7 @@ struct Workspace {
   cudaStream_t capture = nullptr;
   float kernel_ms[3] = {0, 0, 0};
   uint32_t n_kernel_ms = 0;
-  GraphCache g_enc, g_dec;
+  GraphCache g_enc[2], g_dec[2];  // one captured sequence per segment-table slot
   std::map<std::vector<uint32_t>, RowsLaunch> tuned;
   RowsLaunch last{};
   RowsLaunch fixed[2] = {};  // launch requests set by the caller (encode, decode); 0 = automatic
@@ -101,6 +101,16 @@ struct Workspace {
   Pending pend;
   cudaEvent_t uploaded = nullptr;  // the last call's segment table has reached the device
   bool upload_pending = false;     // an enqueue-only call may still read the pinned table
+  // Segment tables go to two device slots in turn (a table points into its
+  // own slot). Per slot, the table last copied there and where it went: a
+  // call whose table is the same bytes for the same place skips the copy
+  // (the host waits for the previous copy before it writes a new table, so
+  // every earlier copy is complete on the device). Calls that repeat, whose
+  // tables alternate with the stream's ping-pong state planes, find theirs in
+  // place.
+  std::vector<uint8_t> up_last[2];
+  const uint8_t* up_dev[2] = {nullptr, nullptr};
+  uint32_t up_slot = 1;  // slot of the last call
   // kernel timing of enqueue-only calls: a ring of event sets, harvested as
   // they complete and averaged at jiffy_stream_wait
   struct EvSet {
@@ -186,22 +196,31 @@ void drop_graph(GraphCache& g) {
   g.key.clear();
 }
 
+void drop_graphs(Workspace& w) {
+  for (int k = 0; k < 2; k++) {
+    drop_graph(w.g_enc[k]);
+    drop_graph(w.g_dec[k]);
+  }
+}
+
 jiffy_status ensure_scratch(Workspace& w, size_t dev_bytes, size_t host_bytes) {
   // enqueue-only calls may still use the buffers about to be replaced
   if ((dev_bytes > w.scratch_cap || host_bytes > w.pinned_cap) && w.upload_pending) cudaDeviceSynchronize();
   if (dev_bytes > w.scratch_cap) {
-    drop_graph(w.g_enc);  // the captured sequences point into the old buffers
-    drop_graph(w.g_dec);
+    drop_graphs(w);  // the captured sequences point into the old buffers
     if (w.d_scratch) cudaFree(w.d_scratch);
     w.d_scratch = nullptr;
     w.scratch_cap = 0;
+    for (int k = 0; k < 2; k++) {  // the tables on the device go with the buffer
+      w.up_last[k].clear();
+      w.up_dev[k] = nullptr;
+    }
     size_t cap = align_up(dev_bytes + dev_bytes / 4, 1 << 20);
     if (cudaMalloc(&w.d_scratch, cap) != cudaSuccess) return JIFFY_ERR_NOMEM;
     w.scratch_cap = cap;
   }
   if (host_bytes > w.pinned_cap) {
-    drop_graph(w.g_enc);
-    drop_graph(w.g_dec);
+    drop_graphs(w);
     if (w.h_pinned) cudaFreeHost(w.h_pinned);
     w.h_pinned = nullptr;
     w.pinned_cap = 0;
@@ -271,9 +290,30 @@ jiffy_status wait_upload(Workspace& w) {
   return JIFFY_OK;
 }
 
+// Is the call's segment table (h, bytes) already on the device at dev? (the
+// previous table went there, with the same bytes; wait_upload has made sure
+// its copy is complete)
+bool table_resident(const Workspace& w, uint32_t slot, const uint8_t* dev, const uint8_t* h, size_t bytes) {
+  return w.up_dev[slot] == dev && w.up_last[slot].size() == bytes &&
+         std::memcmp(w.up_last[slot].data(), h, bytes) == 0;
+}
+
+// Records the table a call put on the device (ok), or forgets it (a failed
+// call may not have copied it).
+void table_uploaded(Workspace& w, uint32_t slot, bool ok, bool skipped, const uint8_t* dev, const uint8_t* h,
+                    size_t bytes) {
+  w.up_slot = slot;
+  if (!ok) {
+    w.up_last[slot].clear();
+    w.up_dev[slot] = nullptr;
+  } else if (!skipped) {
+    w.up_last[slot].assign(h, h + bytes);
+    w.up_dev[slot] = dev;
+  }
+}
+
 void release(Workspace& w) {
-  drop_graph(w.g_enc);
-  drop_graph(w.g_dec);
+  drop_graphs(w);
   if (w.d_scratch) cudaFree(w.d_scratch);
   if (w.h_pinned) cudaFreeHost(w.h_pinned);
   for (cudaEvent_t e : w.ev)
@@ -590,7 +630,9 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   // ---- device scratch: upload, zeroed region (look-back words, trial
   //      costs, ticket, results), work arrays, row slots
   Carver c;
-  const size_t o_up = c.take(up.off);
+  const uint32_t slot = 1u - ws.up_slot;  // segment-table slots alternate
+  const size_t o_up_slot[2] = {c.take(up.off), c.take(up.off)};
+  const size_t o_up = o_up_slot[slot];
   const size_t o_zero = c.take(0);
   const size_t o_stc = c.take(8ull * items);
   const size_t o_cost = c.take(8ull * secs), o_tick = c.take(8);
@@ -753,10 +795,12 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     p.zmax_blk = zmax_blk;
   }
   uint8_t* hres = h + h_res;
+  const bool up_same = table_resident(ws, slot, d + o_up, h, up.off);
+  key.push_back(up_same ? 1u : 0u);
 
   // the whole call on one stream: upload, clear, kernels, results
   auto enqueue = [&](cudaStream_t s, const jiffy::EncParams& pp, void* const* evs) -> int {
-    cudaError_t ce = cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, s);
+    cudaError_t ce = up_same ? cudaSuccess : cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess && async) ce = record_ev(ws.uploaded, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, s);
     if (ce != cudaSuccess) return (int)ce;
@@ -790,8 +834,9 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   void* const* tev = timed ? (async ? next_evset(ws, 3) : evs) : nullptr;
   if (timed && !tev) return JIFFY_ERR_CUDA;
   // (a timed enqueue-only call uses the next event set of the ring)
-  r = run_sequence(ws, ws.g_enc, key, st, ws.graphs, tev, timed ? 4u : 0u,
+  r = run_sequence(ws, ws.g_enc[slot], key, st, ws.graphs, tev, timed ? 4u : 0u,
                    [&](cudaStream_t s) { return enqueue(s, p, tev); });
+  table_uploaded(ws, slot, r == JIFFY_OK, up_same, d + o_up, h, up.off);
   if (r != JIFFY_OK) return r;
   if (cudaEventRecord(ws.done, st) != cudaSuccess) return JIFFY_ERR_CUDA;
   ws.calls++;
@@ -874,7 +919,9 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   std::vector<size_t> r_err(n);
   for (uint32_t i = 0; i < n; i++) r_err[i] = rs.take(8);
   Carver c;
-  const size_t o_up = c.take(up.off);
+  const uint32_t slot = 1u - ws.up_slot;  // segment-table slots alternate
+  const size_t o_up_slot[2] = {c.take(up.off), c.take(up.off)};
+  const size_t o_up = o_up_slot[slot];
   const size_t o_zero = c.take(0);
   const size_t o_done = c.take(4ull * items), o_tick = c.take(8);
   const size_t o_res = c.take(rs.off);
@@ -995,9 +1042,11 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   }
   key.push_back(withhold);
   uint8_t* hres = h + h_res;
+  const bool up_same = table_resident(ws, slot, d + o_up, h, up.off);
+  key.push_back(up_same ? 1u : 0u);
 
   auto enqueue = [&](cudaStream_t s, const jiffy::DecParams& pp, void* const* evs) -> int {
-    cudaError_t ce = cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, s);
+    cudaError_t ce = up_same ? cudaSuccess : cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, s);
     if (ce == cudaSuccess && async) ce = record_ev(ws.uploaded, s);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, s);
     if (ce != cudaSuccess) return (int)ce;
@@ -1030,8 +1079,9 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   void* evs[2] = {ws.ev[0], ws.ev[1]};
   void* const* tev = timed ? (async ? next_evset(ws, 1) : evs) : nullptr;
   if (timed && !tev) return JIFFY_ERR_CUDA;
-  r = run_sequence(ws, ws.g_dec, key, st, ws.graphs, tev, timed ? 2u : 0u,
+  r = run_sequence(ws, ws.g_dec[slot], key, st, ws.graphs, tev, timed ? 2u : 0u,
                    [&](cudaStream_t s) { return enqueue(s, p, tev); });
+  table_uploaded(ws, slot, r == JIFFY_OK, up_same, d + o_up, h, up.off);
   if (r != JIFFY_OK) return r;
   if (cudaEventRecord(ws.done, st) != cudaSuccess) return JIFFY_ERR_CUDA;
   ws.calls++;
@@ -1462,8 +1512,7 @@ jiffy_status jiffy_batch_set_graphs(jiffy_batch* b, int enable) {
   b->ws.graphs = enable != 0;
   if (!b->ws.graphs) {
     DeviceGuard g(b->ws.device);
-    drop_graph(b->ws.g_enc);
-    drop_graph(b->ws.g_dec);
+    drop_graphs(b->ws);
   }
   return JIFFY_OK;
 }
