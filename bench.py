@@ -409,6 +409,7 @@ def batched_leg(J, torch, dev, local, steps, warmup, n_streams=256, n_scans=8, b
     # the same steps on the automatic launch configuration (no tuner)
     J.jiffy_batch_set_autotune(b, False)
     step()
+    step()
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(steps):
@@ -465,6 +466,7 @@ def batched_leg(J, torch, dev, local, steps, warmup, n_streams=256, n_scans=8, b
         for h in encs + decs:
             J.jiffy_stream_wait(h)
     per_stream()
+    per_stream()  # both segment-table slots of every stream warm
     torch.cuda.synchronize()
     p0.record(stream)
     for _ in range(3):
@@ -568,7 +570,7 @@ def sweep_leg(J, torch, dev, local, max_mib=4096, reps=3, seed=7):
     chosen often. One random walk is continued until its raw planes reach each
     size (64 MiB, doubling up to max_mib); each size is one encode call over
     its scans and one decode call over their stream, both enqueue-only on one
-    CUDA stream, timed with CUDA events after a warm-up pair, with a 256 MiB
+    CUDA stream, timed with CUDA events after two warm-up pairs, with a 256 MiB
     write between calls so that no input starts in L2. Precision 1 makes the
     round trip the identity: the decoded planes must equal the input."""
     from paper_2209_08196_gb300 import synth
@@ -611,7 +613,7 @@ def sweep_leg(J, torch, dev, local, max_mib=4096, reps=3, seed=7):
         dst = [o[:n] for o in outs]
         raw = n * raw_scan
         t_enc, t_dec, k_enc, k_dec = [], [], [], []
-        for rep in range(reps + 1):
+        for rep in range(reps + 2):  # two warm-up pairs: calls alternate between two segment-table slots
             J.jiffy_stream_reset(enc)
             J.jiffy_stream_reset(dec)
             flush.fill_(rep)
@@ -624,7 +626,7 @@ def sweep_leg(J, torch, dev, local, max_mib=4096, reps=3, seed=7):
             ev[3].record(stream)
             J.jiffy_stream_wait(enc)
             J.jiffy_stream_wait(dec)
-            if rep:
+            if rep >= 2:
                 t_enc.append(ev[0].elapsed_time(ev[1]))
                 t_dec.append(ev[2].elapsed_time(ev[3]))
                 k_enc.append(J.jiffy_stream_kernel_times(enc)[1])

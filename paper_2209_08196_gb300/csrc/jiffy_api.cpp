@@ -19,6 +19,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstdint>
@@ -111,6 +112,7 @@ struct Workspace {
   std::vector<uint8_t> up_last[2];
   const uint8_t* up_dev[2] = {nullptr, nullptr};
   uint32_t up_slot = 1;  // slot of the last call
+  int slots = 0;         // 1 or 2 table slots, decided at the first call (0: not yet)
   // kernel timing of enqueue-only calls: a ring of event sets, harvested as
   // they complete and averaged at jiffy_stream_wait
   struct EvSet {
@@ -194,6 +196,23 @@ void drop_graph(GraphCache& g) {
   g.ev_nodes.clear();
   g.ev_now.clear();
   g.key.clear();
+}
+
+// Workspaces of a process that use two segment-table slots. Alternating
+// launch sequences cost device-side graph state: with a few hundred streams
+// in one process (256 streams, one call each per step: 11.2 -> 8.0 Gpoints/s)
+// that outweighed the copies saved, while up to 64 streams gained (+8 %).
+// Workspaces beyond the first 64 keep one slot.
+constexpr int kTwoSlotWorkspaces = 64;
+std::atomic<int> g_two_slot_ws{0};
+
+// The table slot of a workspace's next call.
+uint32_t next_slot(Workspace& w) {
+  if (!w.slots) {
+    w.slots = g_two_slot_ws.fetch_add(1) < kTwoSlotWorkspaces ? 2 : 1;
+    if (w.slots == 1) g_two_slot_ws.fetch_sub(1);
+  }
+  return w.slots == 2 ? 1u - w.up_slot : 0u;
 }
 
 void drop_graphs(Workspace& w) {
@@ -314,6 +333,8 @@ void table_uploaded(Workspace& w, uint32_t slot, bool ok, bool skipped, const ui
 
 void release(Workspace& w) {
   drop_graphs(w);
+  if (w.slots == 2) g_two_slot_ws.fetch_sub(1);
+  w.slots = 0;
   if (w.d_scratch) cudaFree(w.d_scratch);
   if (w.h_pinned) cudaFreeHost(w.h_pinned);
   for (cudaEvent_t e : w.ev)
@@ -630,7 +651,7 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
   // ---- device scratch: upload, zeroed region (look-back words, trial
   //      costs, ticket, results), work arrays, row slots
   Carver c;
-  const uint32_t slot = 1u - ws.up_slot;  // segment-table slots alternate
+  const uint32_t slot = next_slot(ws);  // segment-table slots alternate
   const size_t o_up_slot[2] = {c.take(up.off), c.take(up.off)};
   const size_t o_up = o_up_slot[slot];
   const size_t o_zero = c.take(0);
@@ -795,14 +816,19 @@ jiffy_status enqueue_encode(Workspace& ws, std::vector<EncJob>& jobs, cudaStream
     p.zmax_blk = zmax_blk;
   }
   uint8_t* hres = h + h_res;
+  // the segment table, copied on the call's stream ahead of the rest (and
+  // outside any captured sequence) unless it is in its slot already
   const bool up_same = table_resident(ws, slot, d + o_up, h, up.off);
-  key.push_back(up_same ? 1u : 0u);
+  if (!up_same && cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    table_uploaded(ws, slot, false, up_same, d + o_up, h, up.off);
+    return JIFFY_ERR_CUDA;
+  }
+  // (the event marks the host table's last copy: calls that copy nothing leave it)
+  if (!up_same && async && record_ev(ws.uploaded, st) != cudaSuccess) return JIFFY_ERR_CUDA;
 
-  // the whole call on one stream: upload, clear, kernels, results
+  // the rest of the call on one stream: clear, kernels, results
   auto enqueue = [&](cudaStream_t s, const jiffy::EncParams& pp, void* const* evs) -> int {
-    cudaError_t ce = up_same ? cudaSuccess : cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, s);
-    if (ce == cudaSuccess && async) ce = record_ev(ws.uploaded, s);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, s);
+    const cudaError_t ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, s);
     if (ce != cudaSuccess) return (int)ce;
     const int rc = jiffy::launch_encode(pp, s, evs);
     if (rc != 0 || async) return rc;  // enqueue-only: offsets and errors stay on the device
@@ -919,7 +945,7 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   std::vector<size_t> r_err(n);
   for (uint32_t i = 0; i < n; i++) r_err[i] = rs.take(8);
   Carver c;
-  const uint32_t slot = 1u - ws.up_slot;  // segment-table slots alternate
+  const uint32_t slot = next_slot(ws);  // segment-table slots alternate
   const size_t o_up_slot[2] = {c.take(up.off), c.take(up.off)};
   const size_t o_up = o_up_slot[slot];
   const size_t o_zero = c.take(0);
@@ -1042,13 +1068,18 @@ jiffy_status enqueue_decode(Workspace& ws, std::vector<DecJob>& jobs, cudaStream
   }
   key.push_back(withhold);
   uint8_t* hres = h + h_res;
+  // the segment table, copied on the call's stream ahead of the rest (and
+  // outside any captured sequence) unless it is in its slot already
   const bool up_same = table_resident(ws, slot, d + o_up, h, up.off);
-  key.push_back(up_same ? 1u : 0u);
+  if (!up_same && cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    table_uploaded(ws, slot, false, up_same, d + o_up, h, up.off);
+    return JIFFY_ERR_CUDA;
+  }
+  // (the event marks the host table's last copy: calls that copy nothing leave it)
+  if (!up_same && async && record_ev(ws.uploaded, st) != cudaSuccess) return JIFFY_ERR_CUDA;
 
   auto enqueue = [&](cudaStream_t s, const jiffy::DecParams& pp, void* const* evs) -> int {
-    cudaError_t ce = up_same ? cudaSuccess : cudaMemcpyAsync(d + o_up, h, up.off, cudaMemcpyHostToDevice, s);
-    if (ce == cudaSuccess && async) ce = record_ev(ws.uploaded, s);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, s);
+    const cudaError_t ce = cudaMemsetAsync(d + o_zero, 0, zero_bytes, s);
     if (ce != cudaSuccess) return (int)ce;
     const int rc = jiffy::launch_decode(pp, s, evs);
     if (rc != 0 || async) return rc;  // enqueue-only: errors stay on the device

