@@ -25,12 +25,13 @@
 // block is located, and decoded, on its own.
 //
 // k_zstd_enc: one CTA of 128 threads per (section, block), after the rows
-//   kernel has stored the section's coded mask bytes. Each thread holds 64
-//   consecutive bytes of the block in registers: histogram; code lengths and
-//   the tree description on thread 0 (at most 256 symbols and 255 weights);
-//   then each thread codes its literals: their bit positions from a CTA-wide
-//   scan of the code lengths, their codes ORed into the block image in shared
-//   memory. The image goes to the block's slot; the placement kernel
+//   kernel has stored the section's coded mask bytes. Each thread owns 64
+//   consecutive bytes of the block (all requested at once for the histogram,
+//   re-read from L1 by the later passes); code lengths (a bitonic sort of the
+//   present symbols, the merge on thread 0) and the tree description (FSE
+//   steps on thread 0: at most 256 symbols and 255 weights); then each thread
+//   codes its literals: their bit positions from a CTA-wide scan of the code
+//   lengths, their codes ORed into the block image in shared memory. The image goes to the block's slot; the placement kernel
 //   assembles the frame. (Small CTAs: the serial steps of many blocks
 //   overlap on an SM.)
 // k_zstd_dec: one warp per (section, block), before the rows kernel. Checks
